@@ -1,0 +1,179 @@
+"""Seeded synthetic inputs shaped like the simulated data of arXiv 2106.09382.
+
+This module draws data only: a true precision matrix Omega0 and n samples
+X ~ N(0, Omega0^{-1}).  It holds none of the estimator's arithmetic (no
+standardization, no Gram, no coordinate descent), so both the CPU oracle and
+the CUDA path consume exactly the same arrays.
+
+Numbering: numpy ``default_rng(seed)``; draws are taken in a fixed order
+(graph, edge values, Gaussian noise) so every array is reproducible.
+
+Sampling: with Omega0 = L L^T (Cholesky, FP64) the rows x^T = z^T L^{-1} with
+z ~ N(0, I) have covariance (L L^T)^{-1} = Omega0^{-1}.
+
+Generators (Section 5 describes the paper's own AR(2) and scale-free designs;
+the sizes and value ranges follow the workloads this library is measured on):
+
+    random_graph   Erdos-Renyi edges with probability `edge_prob`, values
+                   +-U[lo, hi], diagonal = row |sum| + margin (diagonally
+                   dominant, hence positive definite).
+    ar1_extra      AR(1) precision for rho (tridiagonal) plus `n_extra` random
+                   non-band edges, each +-U[lo, hi] with |value| added to both
+                   endpoint diagonals (each added term is PSD).
+    ar2            the paper's AR(2) design (0.45 on the first, 0.4 on the
+                   second off-diagonal, diagonal 1).
+    scale_free     Barabasi-Albert graph (m edges per new vertex), values by
+                   the paper's four steps (uniform on [-1,-0.5] U [0.5,1], row
+                   scaling by 1.25 x the absolute row sum, symmetrization,
+                   magnitude floor 0.1).
+    block_diag     `n_blocks` blocks, within-block edge probability, values
+                   +-U[lo, hi], diagonal dominance margin.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+
+def _signed_uniform(rng, size, lo, hi):
+    mag = rng.uniform(lo, hi, size=size)
+    sgn = np.where(rng.random(size) < 0.5, -1.0, 1.0)
+    return sgn * mag
+
+
+def random_graph(p: int, edge_prob: float = 0.05, lo: float = 0.3, hi: float = 0.6,
+                 margin: float = 0.5, seed: int = 0) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    iu, ju = np.triu_indices(p, 1)
+    keep = rng.random(iu.size) < edge_prob
+    iu, ju = iu[keep], ju[keep]
+    vals = _signed_uniform(rng, iu.size, lo, hi)
+    Om = np.zeros((p, p))
+    Om[iu, ju] = vals
+    Om[ju, iu] = vals
+    np.fill_diagonal(Om, np.abs(Om).sum(axis=1) + margin)
+    return Om
+
+
+def ar1_extra(p: int, rho: float = 0.5, n_extra: int | None = None, lo: float = 0.3,
+              hi: float = 0.6, seed: int = 0) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    if n_extra is None:
+        n_extra = int(round(0.01 * (p - 1)))
+    c = 1.0 / (1.0 - rho * rho)
+    Om = np.zeros((p, p))
+    idx = np.arange(p)
+    Om[idx, idx] = c * (1.0 + rho * rho)
+    Om[0, 0] = c
+    Om[p - 1, p - 1] = c
+    Om[idx[:-1], idx[1:]] = -c * rho
+    Om[idx[1:], idx[:-1]] = -c * rho
+    chosen = set()
+    while len(chosen) < n_extra:
+        i, j = (int(v) for v in rng.integers(0, p, size=2))
+        if i == j:
+            continue
+        a, b = min(i, j), max(i, j)
+        if b - a <= 1 or (a, b) in chosen:
+            continue
+        chosen.add((a, b))
+    for (a, b) in sorted(chosen):
+        v = float(_signed_uniform(rng, 1, lo, hi)[0])
+        Om[a, b] = v
+        Om[b, a] = v
+        Om[a, a] += abs(v)
+        Om[b, b] += abs(v)
+    return Om
+
+
+def ar2(p: int) -> np.ndarray:
+    Om = np.eye(p)
+    i = np.arange(p)
+    Om[i[:-1], i[1:]] = Om[i[1:], i[:-1]] = 0.45
+    Om[i[:-2], i[2:]] = Om[i[2:], i[:-2]] = 0.4
+    return Om
+
+
+def barabasi_albert_edges(p: int, m: int, rng) -> list[tuple[int, int]]:
+    """Preferential attachment: start from a clique on m+1 vertices, then every
+    new vertex attaches to m distinct existing vertices drawn with probability
+    proportional to degree."""
+    edges = []
+    targets_pool: list[int] = []
+    for a in range(m + 1):
+        for b in range(a + 1, m + 1):
+            edges.append((a, b))
+            targets_pool += [a, b]
+    for v in range(m + 1, p):
+        picked: set[int] = set()
+        while len(picked) < m:
+            picked.add(targets_pool[int(rng.integers(0, len(targets_pool)))])
+        for u in sorted(picked):
+            edges.append((u, v))
+            targets_pool += [u, v]
+    return edges
+
+
+def scale_free(p: int, m: int = 2, seed: int = 0) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    edges = barabasi_albert_edges(p, m, rng)
+    T = np.eye(p)
+    for (a, b) in edges:
+        v = float(_signed_uniform(rng, 1, 0.5, 1.0)[0])
+        T[a, b] = T[b, a] = v
+    off = T - np.diag(np.diag(T))
+    rowsum = np.abs(off).sum(axis=1)
+    rowsum[rowsum == 0] = 1.0
+    off = off / (1.25 * rowsum[:, None])
+    Om = (off + off.T) / 2.0
+    mask = Om != 0
+    small = mask & (np.abs(Om) < 0.1)
+    Om[small] = 0.1 * np.sign(Om[small])
+    Om += np.eye(p)
+    return Om
+
+
+def block_diag(p: int, n_blocks: int, edge_prob: float = 0.1, lo: float = 0.3,
+               hi: float = 0.6, margin: float = 0.5, seed: int = 0) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    Om = np.zeros((p, p))
+    bs = p // n_blocks
+    for b in range(n_blocks):
+        s = b * bs
+        e = p if b == n_blocks - 1 else s + bs
+        k = e - s
+        iu, ju = np.triu_indices(k, 1)
+        keep = rng.random(iu.size) < edge_prob
+        vals = _signed_uniform(rng, int(keep.sum()), lo, hi)
+        Om[s + iu[keep], s + ju[keep]] = vals
+        Om[s + ju[keep], s + iu[keep]] = vals
+    np.fill_diagonal(Om, np.abs(Om).sum(axis=1) + margin)
+    return Om
+
+
+def sample(Om0: np.ndarray, n: int, seed: int = 0) -> np.ndarray:
+    """n rows x ~ N(0, Om0^{-1}) as an (n, p) float64 array."""
+    rng = np.random.default_rng(seed + 1_000_003)
+    p = Om0.shape[0]
+    L = np.linalg.cholesky(Om0)
+    Z = rng.standard_normal((n, p))
+    # X = Z L^{-1}  <=>  L^T X^T = Z^T
+    Xt = sla.solve_triangular(L, Z.T, trans="T", lower=True, check_finite=False)
+    return np.ascontiguousarray(Xt.T)
+
+
+# Named workloads -------------------------------------------------------------
+
+def workload_small(seed: int = 0):
+    """p=100, n=200, random graph (edge prob 0.05, +-U[0.3,0.6], margin 0.5),
+    lambda=0.3, tol 1e-6."""
+    Om0 = random_graph(100, 0.05, 0.3, 0.6, 0.5, seed)
+    return dict(name="random-graph p=100 n=200", X=sample(Om0, 200, seed), Om0=Om0,
+                lam=0.3, tol=1e-6)
+
+
+def workload_ar1(p: int = 5000, n: int = 2000, seed: int = 0):
+    """AR(1) rho=0.5 precision plus round(0.01 (p-1)) extra edges, lambda=0.2."""
+    Om0 = ar1_extra(p, 0.5, None, 0.3, 0.6, seed)
+    return dict(name="AR(1)+1%% extra p=%d n=%d" % (p, n), X=sample(Om0, n, seed), Om0=Om0,
+                lam=0.2, tol=1e-5)
