@@ -9,7 +9,8 @@ one computes, and the passage of arXiv 2106.09382 it follows, is stated in the
 C source beside it:
 
     standardize      Section 2.1 (X centered columnwise; unit 1/n variance)
-    gram             Algorithm 1, T <- X^T X (here divided by n)
+    gram, gram_rows  Algorithm 1, T <- X^T X (here divided by n); selected rows
+    eq3, eq2         Eq. 3 / Eq. 2 for one entry from explicit rows
     schedule         Section 3.2 circle method, Algorithm 1 index rotation
     soft             Soft-threshold defined under Eq. 3
     offdiag_update   Eq. 3 with its two direct sums
@@ -45,6 +46,9 @@ _ci, _cd = ctypes.c_int, ctypes.c_double
 _SIGNATURES = {
     "oracle_standardize": ([_dp, _ci, _ci, _ci, _dp], _ci),
     "oracle_gram": ([_dp, _ci, _ci, _dp], None),
+    "oracle_gram_rows": ([_dp, _ci, _ci, _ip, _ci, _dp], None),
+    "oracle_eq3": ([_dp, _dp, ctypes.c_size_t, _dp, _dp, _ci, _ci, _ci, _cd], _cd),
+    "oracle_eq2": ([_dp, _dp, _ci, _ci], _cd),
     "oracle_schedule": ([_ci, _ip], _ci),
     "oracle_soft": ([_cd, _cd], _cd),
     "oracle_offdiag_update": ([_dp, _ci, _cd, _dp, _ci, _ci], _cd),
@@ -117,6 +121,27 @@ class Oracle:
         S = np.empty((p, p), dtype=np.float64)
         self.lib.oracle_gram(_ptr(Z), n, p, _ptr(S))
         return S
+
+    def gram_rows(self, Z, rows) -> np.ndarray:
+        """Rows `rows` of S = Z^T Z / n (same sums as gram)."""
+        Z = _f64(Z)
+        n, p = Z.shape
+        rows = np.ascontiguousarray(rows, dtype=np.int32)
+        out = np.empty((rows.size, p), dtype=np.float64)
+        self.lib.oracle_gram_rows(_ptr(Z), n, p, rows.ctypes.data_as(_ip), rows.size, _ptr(out))
+        return out
+
+    def eq3(self, om_row_i, om_col_j, s_row_i, s_row_j, i: int, j: int, lam: float) -> float:
+        """Eq. 3 for pair (i, j) from row i and column j of Omega and rows i, j of S."""
+        a, b = _f64(om_row_i), _f64(om_col_j)
+        si, sj = _f64(s_row_i), _f64(s_row_j)
+        return self.lib.oracle_eq3(_ptr(a), _ptr(b), 1, _ptr(si), _ptr(sj), a.size, int(i),
+                                   int(j), float(lam))
+
+    def eq2(self, om_row_i, s_row_i, i: int) -> float:
+        """Eq. 2 for vertex i from row i of Omega and of S."""
+        a, si = _f64(om_row_i), _f64(s_row_i)
+        return self.lib.oracle_eq2(_ptr(a), _ptr(si), a.size, int(i))
 
     def schedule(self, p: int) -> np.ndarray:
         """(pe-1, pe/2, 2) int32 table of 0-based pairs; discarded pairs are -1."""
@@ -231,6 +256,18 @@ def gram(Z):
 
 def schedule(p: int):
     return default().schedule(p)
+
+
+def gram_rows(Z, rows):
+    return default().gram_rows(Z, rows)
+
+
+def eq3(om_row_i, om_col_j, s_row_i, s_row_j, i, j, lam):
+    return default().eq3(om_row_i, om_col_j, s_row_i, s_row_j, i, j, lam)
+
+
+def eq2(om_row_i, s_row_i, i):
+    return default().eq2(om_row_i, s_row_i, i)
 
 
 def soft(x, tau):

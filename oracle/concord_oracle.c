@@ -69,17 +69,30 @@ int oracle_standardize(const double *X, int n, int p, int scale, double *Z)
     return OR_OK;
 }
 
+/* Row i of S = Z^T Z / n: out[j] = sum_k Z[k][i] Z[k][j] / n, k ascending. */
+static void gram_row(const double *Z, int n, int p, int i, double *out)
+{
+    for (int j = 0; j < p; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k)
+            acc += Z[(size_t)k * p + i] * Z[(size_t)k * p + j];
+        out[j] = MUTANT(9) ? acc : acc / n;
+    }
+}
+
 /* S = Z^T Z / n, the plain triple loop (Algorithm 1, T <- X^T X, divided by
  * n).  Both triangles are computed independently (no symmetry shortcut). */
 void oracle_gram(const double *Z, int n, int p, double *S)
 {
-    for (int i = 0; i < p; ++i)
-        for (int j = 0; j < p; ++j) {
-            double acc = 0.0;
-            for (int k = 0; k < n; ++k)
-                acc += Z[(size_t)k * p + i] * Z[(size_t)k * p + j];
-            S[(size_t)i * p + j] = MUTANT(9) ? acc : acc / n;
-        }
+    for (int i = 0; i < p; ++i) gram_row(Z, n, p, i, S + (size_t)i * p);
+}
+
+/* Selected rows of S: out[r][j] = S[rows[r]][j], the same sums as
+ * oracle_gram, for checking large p one row at a time. */
+void oracle_gram_rows(const double *Z, int n, int p, const int32_t *rows, int nrows,
+                      double *out)
+{
+    for (int r = 0; r < nrows; ++r) gram_row(Z, n, p, rows[r], out + (size_t)r * p);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -140,39 +153,55 @@ double oracle_soft(double x, double tau)
     return (x > 0.0) != MUTANT(3) ? a : -a;
 }
 
-/* Eq. 3 for the pair (i, j), i != j:
+/* Eq. 3 for the pair (i, j), i != j, from explicit inputs:
  *   omega_ij <- Soft_lambda( - sum_{u != j} omega_iu s_ju
  *                            - sum_{u != i} omega_uj s_iu ) / (s_ii + s_jj)
- * and the symmetric entry omega_ji receives the same value.  Returns the
- * change new - old. */
-double oracle_offdiag_update(const double *S, int p, double lambda, double *Om,
-                             int i, int j)
+ * om_i[u] = omega_iu (row i), om_j[u * stride] = omega_uj (column j),
+ * s_i / s_j = rows i / j of S.  Returns the new value. */
+double oracle_eq3(const double *om_i, const double *om_j, size_t stride,
+                  const double *s_i, const double *s_j, int p, int i, int j,
+                  double lambda)
 {
     double a1 = 0.0, a2 = 0.0;
     for (int u = 0; u < p; ++u)
-        if (u != j || MUTANT(1)) a1 += Om[(size_t)i * p + u] * S[(size_t)j * p + u];
+        if (u != j || MUTANT(1)) a1 += om_i[u] * s_j[u];
     for (int u = 0; u < p; ++u)
-        if (u != i) a2 += Om[(size_t)u * p + j] * S[(size_t)(MUTANT(2) ? j : i) * p + u];
-    double den = S[(size_t)i * p + i] + (MUTANT(4) ? 0.0 : S[(size_t)j * p + j]);
+        if (u != i) a2 += om_j[(size_t)u * stride] * (MUTANT(2) ? s_j : s_i)[u];
+    double den = s_i[i] + (MUTANT(4) ? 0.0 : s_j[j]);
+    return oracle_soft(-a1 - a2, lambda) / den;
+}
+
+/* Eq. 3 applied in place to the pair (i, j) of Om; the symmetric entry
+ * omega_ji receives the same value.  Returns the change new - old. */
+double oracle_offdiag_update(const double *S, int p, double lambda, double *Om,
+                             int i, int j)
+{
     double old = Om[(size_t)i * p + j];
-    double nw = oracle_soft(-a1 - a2, lambda) / den;
+    double nw = oracle_eq3(Om + (size_t)i * p, Om + j, (size_t)p, S + (size_t)i * p,
+                           S + (size_t)j * p, p, i, j, lambda);
     Om[(size_t)i * p + j] = nw;
     Om[(size_t)j * p + i] = nw;
     return nw - old;
 }
 
-/* Eq. 2 for vertex i (divided through by n):
+/* Eq. 2 for vertex i (divided through by n), from row i of Omega and of S:
  *   c = sum_{j != i} omega_ij s_ij,
  *   omega_ii <- (-c + sqrt(c^2 + 4 s_ii)) / (2 s_ii).
- * Returns the change new - old. */
-double oracle_diag_update(const double *S, int p, double *Om, int i)
+ * Returns the new value. */
+double oracle_eq2(const double *om_i, const double *s_i, int p, int i)
 {
     double c = 0.0;
     for (int j = 0; j < p; ++j)
-        if (j != i || MUTANT(5)) c += Om[(size_t)i * p + j] * S[(size_t)i * p + j];
-    double sii = S[(size_t)i * p + i];
+        if (j != i || MUTANT(5)) c += om_i[j] * s_i[j];
+    double sii = s_i[i];
+    return (-c + sqrt(c * c + 4.0 * sii)) / (2.0 * sii);
+}
+
+/* Eq. 2 applied in place to vertex i of Om.  Returns the change new - old. */
+double oracle_diag_update(const double *S, int p, double *Om, int i)
+{
     double old = Om[(size_t)i * p + i];
-    double nw = (-c + sqrt(c * c + 4.0 * sii)) / (2.0 * sii);
+    double nw = oracle_eq2(Om + (size_t)i * p, S + (size_t)i * p, p, i);
     Om[(size_t)i * p + i] = nw;
     return nw - old;
 }
