@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""CONCORD-PCD benchmark on one GB300 (replicas on N GPUs).
+
+Workload: the paper-scale single solve -- p = 5000 variables, n = 2000
+samples, AR(1) (rho = 0.5) precision with round(0.01 (p-1)) extra edges,
+lambda = 0.2, seeded synthetic data (numpy default_rng).  One step = one
+whole solve from the data X resident in HBM: standardize + Gram + edge-
+coloured sweeps until the KKT residual <= 1e-5 (mixed precision: FP32 sweeps
+then FP64 polishing).  Reported beside it: the plain FP64 GPU solve, the
+sweep kernel's updates/s and roofline, a full-update bandwidth microbench,
+an end-to-end number through host buffers, clocks, and the CPU oracle's
+time estimated from a bounded sample.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank solves its own replica; rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to KKT≤1e-5 at p=5000: mixed vs FP64 PCD; updates/s; HBM % peak"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--p", type=int, default=5000)
+    ap.add_argument("--n", type=int, default=2000)
+    ap.add_argument("--lam", type=float, default=0.2)
+    ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--max-sweeps", type=int, default=500)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip FP64 arm, microbench, e2e and CPU baseline")
+    ap.add_argument("--cpu-budget", type=float, default=20.0,
+                    help="seconds of oracle work for the CPU baseline sample")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].lower() == "active"})
+        loaded = [v for v in sm if v >= 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# --------------------------------------------------------------- roofline
+def sweep_bytes(p: int, b: int, active_pairs: float) -> float:
+    """Algorithmic bytes of one sweep (maintained-W design), b = element bytes:
+    5 scalar reads per pair evaluation (w_ij, W_ij, W_ji, s_ii, s_jj),
+    2 S rows read + 2 W rows read and written per changed pair,
+    1 S row read + 1 W row read and written per diagonal update,
+    W and Omega read once by the objective / KKT pass."""
+    pe = p + (p % 2)
+    pairs = (pe - 1) * (pe // 2) - (p % 2) * (pe - 1)
+    return (pairs * 5 * b + active_pairs * p * (2 * b + 4 * b) + p * p * (b + 2 * b)
+            + p * p * 2 * b)
+
+
+def launch_bytes(p: int, b: int, hist_rows) -> float:
+    return float(sum(sweep_bytes(p, b, h[3]) for h in hist_rows))
+
+
+# ------------------------------------------------------------ CPU baseline
+def cpu_baseline(X: np.ndarray, lam: float, sweeps: int, budget: float, sweeps_src: str):
+    """The oracle (single-threaded C, FP64, Eq. 3 as direct sums) timed on a
+    bounded sample of the same workload and scaled to a whole solve."""
+    import oracle as O
+    n, p = X.shape
+    Z = O.standardize(X)
+    m = min(p, 500)
+    t0 = time.perf_counter()
+    O.gram(Z[:, :m])
+    t_gram = (time.perf_counter() - t0) * (p / m) ** 2
+    S = Z.T @ Z / n  # input for the timing sample only
+    pairs = O.schedule(p)
+    Om = np.eye(p)
+    t0 = time.perf_counter()
+    O.colour_steps(S, Om, lam, pairs, 0, 4)
+    per_colour = (time.perf_counter() - t0) / 4
+    k = int(max(4, min(pairs.shape[0] - 4, budget / max(per_colour, 1e-9))))
+    t0 = time.perf_counter()
+    O.colour_steps(S, Om, lam, pairs, 4, 4 + k)
+    per_colour = (time.perf_counter() - t0) / k
+    t0 = time.perf_counter()
+    O.diag_step(S, Om)
+    t_diag = time.perf_counter() - t0
+    per_sweep = per_colour * pairs.shape[0] + t_diag
+    total = t_gram + sweeps * per_sweep
+    upd = p * (p + 1) / 2 / per_sweep
+    return {"value": total, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": ("Gram on %d of %d columns (x%.0f); %d of %d colour steps + 1 diagonal "
+                       "step at p=%d; x %d sweeps (%s)") % (m, p, (p / m) ** 2, k,
+                                                             pairs.shape[0], p, sweeps,
+                                                             sweeps_src),
+            "seconds_per_sweep": per_sweep, "updates_per_s": upd}
+
+
+def golden_sweeps(p: int):
+    path = os.path.join(ROOT, "oracle", "golden", "ar1_p%d.json" % p)
+    try:
+        with open(path) as f:
+            return int(json.load(f)["sweeps"]), "oracle solve record"
+    except Exception:
+        return None, None
+
+
+# ------------------------------------------------------------------ arms
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return
+    from paper_2106_09382_gb300 import synth
+    w = synth.workload_ar1(args.p, args.n, 0)
+    sweeps, src = golden_sweeps(args.p)
+    if sweeps is None:
+        sweeps, src = 1, "no oracle solve record: one sweep, a lower bound"
+    vals = []
+    base = None
+    for s in range(args.warmup + args.steps):
+        base = cpu_baseline(w["X"], args.lam, sweeps, max(2.0, args.cpu_budget / 4), src)
+        if s >= args.warmup:
+            vals.append(base["value"])
+    v = statistics.mean(vals)
+    base["value"] = v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "AR(1)+1%% extra edges, p=%d, n=%d, lambda=%g, KKT<=%g"
+                      % (args.p, args.n, args.lam, args.tol), "p": args.p, "n": args.n},
+           "cpu_baseline": base,
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2106_09382_gb300 import concord as C
+    from paper_2106_09382_gb300 import synth
+
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p, n, lam, tol = args.p, args.n, args.lam, args.tol
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    wl = synth.workload_ar1(p, n, seed=0)
+    Xh = np.ascontiguousarray(wl["X"])
+    X = torch.as_tensor(Xh, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def timed_solves(state, steps):
+        times, recs = [], []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = state.solve_device(X, lam, tol=tol, max_sweeps=args.max_sweeps)
+            e1.record(stream)
+            stream.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            recs.append((r.as_dict(), state.timing(), state.history()))
+        return times, recs
+
+    # ---------------- headline: mixed precision, data resident in HBM
+    st = C.State(p, C.MIXED, n_cap=n, device=local)
+    st.set_stream(stream)
+    for _ in range(args.warmup):
+        st.solve_device(X, lam, tol=tol, max_sweeps=args.max_sweeps)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    l0 = C.kernel_launches()
+    times, recs = timed_solves(st, args.steps)
+    launches = (C.kernel_launches() - l0) / args.steps
+    barrier()
+    clk = clocks.stop()
+    mean_t = statistics.mean(times)
+    value = max_over_ranks(mean_t)
+    r_last, tim_last, hist_last = recs[-1]
+    if r_last["status"] != C.OK:
+        raise SystemExit("mixed solve did not converge: %s" % r_last)
+
+    # dominant kernel: the FP32 sweep launch (launch 0)
+    ms32, sw32 = tim_last[0]
+    h32 = hist_last[:sw32]
+    hbm_peak, peak_src = load_peaks()
+    bytes32 = launch_bytes(p, 4, h32)
+    achieved = bytes32 / (ms32 * 1e-3) / 1e9
+    updates = p * (p + 1) / 2
+    ups = sw32 * updates / (ms32 * 1e-3)
+    polish = [(ms, sw) for ms, sw in tim_last[1:]]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "kernel": "k_sweep<float> (FP32 sweeps of the mixed solve)",
+                "peak_source": "%s hbm_gbs (STREAM-style copy)" % peak_src,
+                "algorithmic_bytes_per_launch": bytes32, "launch_ms": ms32, "sweeps": sw32,
+                "regime": "colour-step latency chain (%d dependent steps per sweep)"
+                          % (p + (p % 2) - 1)}
+
+    out = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+           "data": "synthetic (seeded AR(1)+extras Gaussian data)",
+           "config": {"workload": "AR(1)+1%% extra edges, p=%d, n=%d, lambda=%g, KKT<=%g"
+                      % (p, n, lam, tol), "p": p, "n": n, "lambda": lam, "tol": tol,
+                      "precision": "mixed (tf32x3/fp32 Gram, FP32 sweeps, FP64 polish)",
+                      "l2": "512 MB buffer written between timed steps",
+                      "parallelism": "replicas x%d" % world},
+           "mixed": {"seconds": mean_t, "sweeps": r_last["sweeps"],
+                     "sweeps_fp32": r_last["sweeps_fp32"], "kkt": r_last["kkt"],
+                     "objective": r_last["objective"], "launch_ms": tim_last,
+                     "step_seconds": times},
+           "updates_per_s": ups,
+           "roofline": roofline,
+           "gpu_launches": launches,
+           "clocks": clk}
+
+    if not args.no_extras:
+        # ---------------- plain FP64 GPU PCD, same data
+        st64 = C.State(p, C.FP64, n_cap=n, device=local)
+        st64.set_stream(stream)
+        st64.solve_device(X, lam, tol=tol, max_sweeps=args.max_sweeps)
+        t64, rec64 = timed_solves(st64, max(1, min(args.steps, 2)))
+        r64, tim64, hist64 = rec64[-1]
+        ms64, sw64 = tim64[0]
+        out["fp64"] = {"seconds": max_over_ranks(statistics.mean(t64)), "sweeps": r64["sweeps"],
+                       "kkt": r64["kkt"], "objective": r64["objective"], "launch_ms": tim64,
+                       "updates_per_s": sw64 * updates / (ms64 * 1e-3),
+                       "sweep_GBps": launch_bytes(p, 8, hist64[:sw64]) / (ms64 * 1e-3) / 1e9}
+        out["mixed_vs_fp64_speedup"] = out["fp64"]["seconds"] / value
+        fp64_sweeps = r64["sweeps"]
+        # ---------------- full-update microbench: nearly every pair changes
+        S32 = C.concord_gram(X, C.PREP_STANDARDIZE, C.GRAM_FP32, stream=stream)
+        torch.cuda.synchronize()
+        fu = {}
+        for name, prec, b in (("fp32", C.MIXED, 4), ("fp64", C.FP64, 8)):
+            sfu = C.State(p, prec, device=local)
+            sfu.set_stream(stream)
+            sfu.set_S(S32 if prec == C.MIXED else S32.double())
+            lam_fu = 1e-3 * sfu.lambda_max()
+            sfu.sweep(lam_fu, 1)
+            (ms, sw), = sfu.timing()[:1]
+            h = sfu.history()
+            nb = launch_bytes(p, b, h[:1])
+            gbs = nb / (ms * 1e-3) / 1e9
+            fu[name] = {"lambda": lam_fu, "launch_ms": ms, "active_pairs": float(h[0, 3]),
+                        "algorithmic_bytes": nb, "achieved": gbs, "frac": gbs / hbm_peak,
+                        "updates_per_s": updates / (ms * 1e-3)}
+            sfu.close()
+        out["full_update_sweep"] = dict(fu, peak=hbm_peak, unit="GB/s",
+                                        note="1 sweep from Omega = I at lambda = 1e-3 lambda_max")
+        # ---------------- end to end through host buffers (pinned)
+        Xpin = torch.empty((n, p), dtype=torch.float64, pin_memory=True).numpy()
+        Xpin[:] = Xh
+        Opin = torch.empty((p, p), dtype=torch.float64, pin_memory=True).numpy()
+        st.solve_host(Xpin, lam, tol=tol, max_sweeps=args.max_sweeps, Omega_out=Opin)
+        te = []
+        for _ in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st.solve_host(Xpin, lam, tol=tol, max_sweeps=args.max_sweeps, Omega_out=Opin)
+            te.append(time.perf_counter() - t0)
+        out["e2e"] = {"value": max_over_ranks(statistics.mean(te)), "unit": "s",
+                      "h2d_bytes_per_step": n * p * 8, "d2h_bytes_per_step": p * p * 8,
+                      "api": "concord_solve_host (pinned X in, pinned Omega out)"}
+        # ---------------- CPU oracle, bounded sample (rank 0 only)
+        if rank == 0:
+            gs, src = golden_sweeps(p)
+            if gs is None:
+                gs, src = fp64_sweeps, "sweeps of the FP64 GPU solve on the same data"
+            out["cpu_baseline"] = cpu_baseline(Xh, lam, gs, args.cpu_budget, src)
+        st64.close()
+    st.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,310 @@
+/*
+ * concord.h -- C ABI of libconcord_gb300.so: CONCORD-PCD (arXiv 2106.09382)
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * The library estimates a sparse precision matrix Omega by minimising the
+ * CONCORD objective (Eq. 1) with the edge-coloured parallel coordinate
+ * descent of Algorithm 1:
+ *
+ *   f(Omega) = - sum_i log w_ii + 1/2 tr(Omega S Omega) + lambda sum_{i<j} |w_ij|
+ *
+ * written in "S units": S = Z^T Z / n for the n x p data Z after the chosen
+ * preparation, so the paper's T = X^T X equals n S and lambda is read on the
+ * S scale (the paper's Eq. 1 divided by n, with penalty n * lambda).  The
+ * diagonal update (Eq. 2) is the same on either scale.
+ *
+ * Conventions for every entry point
+ *   - Matrices are dense and row-major.  `ld*` arguments are row strides in
+ *     elements (>= number of columns).
+ *   - `_dev` pointers are device memory on the state's / current device;
+ *     `_host` pointers are host memory (pinned or pageable).  The caller owns
+ *     every pointer it passes; the library never frees or keeps them after
+ *     the call returns (a stream-ordered call has finished reading them once
+ *     the stream reaches the call's end).
+ *   - Device work is enqueued on the given stream (NULL = the legacy default
+ *     stream); calls that return results to host memory synchronise it.
+ *   - Every entry point returns a status (CONCORD_OK = 0, > 0 informational,
+ *     < 0 error).  On error nothing is written to outputs unless stated, and
+ *     concord_last_error() describes the failure (per calling thread).
+ *   - Nothing here falls back to a CPU path: without a usable sm_103a device
+ *     every call that needs one returns CONCORD_E_CUDA.
+ */
+#ifndef CONCORD_GB300_H
+#define CONCORD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define CONCORD_OK 0
+#define CONCORD_NOT_CONVERGED 1     /* max_sweeps reached; outputs are filled */
+#define CONCORD_E_ARG (-1)          /* invalid argument (size, pointer, value) */
+#define CONCORD_E_NONPOS_DIAG (-2)  /* s_ii <= 0 (constant column) or omega_ii <= 0 */
+#define CONCORD_E_NONFINITE (-3)    /* NaN / Inf met in S, Omega or the iteration */
+#define CONCORD_E_CUDA (-4)         /* CUDA runtime / launch failure, no device */
+#define CONCORD_E_TIMEOUT (-5)      /* a bounded device-side wait ran out */
+#define CONCORD_E_NOMEM (-6)        /* device allocation failed */
+#define CONCORD_E_OCCUPANCY (-7)    /* persistent grid cannot be co-resident */
+
+/* --------------------------------------------------------------- options */
+/* Working precision of a solver state. */
+#define CONCORD_FP64 0   /* S, W = Omega S and Omega in FP64 throughout */
+#define CONCORD_MIXED 1  /* FP32 S / W / Omega sweeps; FP64 diagonal root,
+                            objective and KKT; final FP64 polishing sweeps */
+
+/* Element type of caller buffers. */
+#define CONCORD_F64 0
+#define CONCORD_F32 1
+
+/* Data preparation applied to X before the Gram (Section 2.1 assumes X
+ * centered columnwise; the standardized form also scales every column to
+ * unit 1/n variance so that s_ii = 1). */
+#define CONCORD_PREP_NONE 0
+#define CONCORD_PREP_CENTER 1
+#define CONCORD_PREP_STANDARDIZE 2
+
+/* Gram arithmetic. */
+#define CONCORD_GRAM_FP64 0    /* FP64 CUDA-core products, FP64 accumulation */
+#define CONCORD_GRAM_FP32 1    /* FP32 CUDA-core products, FP32 accumulation */
+#define CONCORD_GRAM_TF32X3 2  /* tensor cores (tcgen05, kind::tf32): each FP32
+                                  operand split hi + lo, hi*hi + hi*lo + lo*hi,
+                                  FP32 accumulation in tensor memory */
+
+/* Stopping rule of concord_run / concord_solve*. */
+#define CONCORD_STOP_KKT 0    /* KKT residual <= tol (absolute, S units) */
+#define CONCORD_STOP_DELTA 1  /* the paper's rule: |Omega^(t)-Omega^(t-1)|_inf < tol
+                                 (Algorithm 1, last line) */
+
+/* ------------------------------------------------------------- results */
+/* Filled by concord_sweep / concord_run / concord_solve*.  Plain C layout:
+ * 4 ints, 4 doubles, 1 int64, 1 double, 4 ints (see concord_result_size). */
+typedef struct concord_result {
+    int status;            /* CONCORD_OK, CONCORD_NOT_CONVERGED or an error  */
+    int sweeps;            /* outer iterations of Algorithm 1 done (all phases) */
+    int sweeps_fp32;       /* of which in FP32 (MIXED first phase)            */
+    int first_delta_sweep; /* first sweep with delta < delta_tol (0 = never)  */
+    double objective;      /* f(Omega) at return, FP64 accumulation           */
+    double kkt;            /* KKT residual at return (definition below)       */
+    double delta;          /* |Omega^(t) - Omega^(t-1)|_inf of the last sweep */
+    double lambda;         /* the lambda used                                  */
+    long long active_pairs;/* pairs whose value changed in the last sweep      */
+    double seconds;        /* device time of the call (CUDA events)            */
+    int timeout_vertex;    /* on CONCORD_E_TIMEOUT: vertex whose wait ran out  */
+    int timeout_step;      /*                        and the colour step        */
+    int reserved0;
+    int reserved1;
+} concord_result;
+
+/* KKT residual (absolute, S units), with W = Omega S and G = W + W^T:
+ *   max over i of |W_ii - 1/w_ii|, over i<j with w_ij != 0 of
+ *   |G_ij + lambda sign(w_ij)|, and over i<j with w_ij == 0 of
+ *   max(|G_ij| - lambda, 0):  the subgradient conditions of Eq. 1. */
+
+/* Size of concord_result in bytes (lets bindings check their layout). */
+size_t concord_result_size(void);
+
+/* Text of the last error on the calling thread ("" if none).  The pointer
+ * stays valid until the next library call on the same thread. */
+const char *concord_last_error(void);
+
+/* Library version string. */
+const char *concord_version(void);
+
+/* --------------------------------------------------------------- schedule */
+/*
+ * concord_schedule -- the circle-method edge colouring of K_p (Section 3.2;
+ * Algorithm 1's index rotation; Table 1 shows p = 6).
+ *
+ * pairs_host: host int32 array of (pe-1) * (pe/2) * 2 elements, pe = p + (p
+ *   mod 2).  Entry [(k*(pe/2) + q)*2 + {0,1}] is the 0-based vertex pair of
+ *   slot q of colour k, in Algorithm 1's order; the pair that holds the extra
+ *   vertex of odd p is written as (-1, -1) (step (iii): it is discarded).
+ * n_colours: receives pe - 1 (the minimum by Theorem 1).
+ * Host only; needs no device.  Errors: CONCORD_E_ARG if p < 2 or a pointer
+ * is NULL.
+ */
+int concord_schedule(int p, int32_t *pairs_host, int *n_colours);
+
+/* ------------------------------------------------------------------ gram */
+/*
+ * concord_gram -- S = Z^T Z / n (Algorithm 1, T <- X^T X, divided by n),
+ * Z = X after `prep` (Section 2.1: columns centered; STANDARDIZE also scales
+ * them to unit 1/n variance).
+ *
+ * X_dev: n x p, row stride ldx, element type x_dtype (F64 or F32); not
+ *   modified.
+ * S_dev: p x p output, row stride lds, element type s_dtype; both triangles
+ *   are written, exactly symmetric.  Must not overlap X_dev.
+ * mode: CONCORD_GRAM_FP64 / _FP32 / _TF32X3.
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ * Scratch memory is allocated and freed inside the call (stream-ordered).
+ * Errors: CONCORD_E_ARG (n < 1, p < 2, ld too small, NULL),
+ *   CONCORD_E_NONPOS_DIAG (a constant column under STANDARDIZE, detected on
+ *   the device and reported after a stream synchronisation),
+ *   CONCORD_E_NOMEM, CONCORD_E_CUDA.
+ */
+int concord_gram(const void *X_dev, int x_dtype, int n, int p, int ldx, int prep,
+                 int mode, void *S_dev, int s_dtype, int lds, void *stream);
+
+/* ----------------------------------------------------------- solver state */
+typedef struct concord_state concord_state;
+
+/*
+ * concord_create -- allocate a solver for dimension p (>= 2) on `device`
+ * (-1 = current device) in `precision` (CONCORD_FP64 or CONCORD_MIXED).
+ * n_cap (>= 0) reserves room for data with up to n_cap rows, used by
+ * concord_solve_device / concord_solve_host (0 = none; the data path then
+ * returns CONCORD_E_ARG).
+ *
+ * Device memory held (ld = p rounded up to a multiple of 32 elements,
+ * e = 4 for MIXED, 8 for FP64):  S, W = Omega S, Omega: 3 p ld e bytes, plus
+ * for MIXED the FP64 polishing copies 3 p ld 8 bytes, plus small per-vertex
+ * and per-block arrays and the data workspace.  Omega starts at I.
+ * The state owns one CUDA stream unless concord_set_stream gives another.
+ * Errors: CONCORD_E_ARG, CONCORD_E_NOMEM, CONCORD_E_CUDA.
+ */
+int concord_create(concord_state **out, int p, int precision, int n_cap, int device);
+
+/* Free every device and host resource of the state (NULL is accepted). */
+int concord_destroy(concord_state *st);
+
+/* Use `stream` (a cudaStream_t, NULL = the state's own stream) for all
+ * later work on the state. */
+int concord_set_stream(concord_state *st, void *stream);
+
+/* Upper bound, in seconds (> 0), on every device-side wait (per-vertex
+ * mailboxes, grid barriers).  A wait that runs out sets CONCORD_E_TIMEOUT,
+ * the kernel returns and the context stays usable.  Default 2 s. */
+int concord_set_timeout(concord_state *st, double seconds);
+
+/*
+ * concord_set_S -- load S (p x p, row stride lds, element type s_dtype,
+ * device memory) into the state, converting to the working precision, and
+ * reset Omega to I and W to S.  S must be symmetric with s_ii > 0 (checked
+ * on the diagonal: CONCORD_E_NONPOS_DIAG / CONCORD_E_NONFINITE).
+ */
+int concord_set_S(concord_state *st, const void *S_dev, int s_dtype, int lds);
+
+/*
+ * concord_set_omega -- warm start (Algorithm 1 takes Omega^(0) as input):
+ * copy Omega0 (p x p, device, row stride ld, element type dtype; symmetric,
+ * positive diagonal) into the state and recompute W = Omega S.
+ * Errors: CONCORD_E_ARG (not symmetric), CONCORD_E_NONPOS_DIAG.
+ */
+int concord_set_omega(concord_state *st, const void *Omega0_dev, int dtype, int ld);
+
+/* Copy the current Omega (or W = Omega S, or S) of the state out, converted
+ * to `dtype`, into device memory with row stride ld. */
+int concord_get_omega(concord_state *st, void *Omega_dev, int dtype, int ld);
+int concord_get_W(concord_state *st, void *W_dev, int dtype, int ld);
+
+/*
+ * concord_get_history -- per-sweep record of the last concord_sweep /
+ * concord_run / concord_solve_* on the state: hist_host receives up to
+ * max_rows rows of 4 doubles (delta, KKT residual, objective, pairs whose
+ * value changed), one per sweep in order (FP32 sweeps first for MIXED);
+ * *rows receives the number of sweeps recorded.  hist_host may be NULL to
+ * query *rows only.
+ */
+int concord_get_history(concord_state *st, double *hist_host, int max_rows, int *rows);
+
+/*
+ * concord_get_timing -- device time of each persistent sweep-kernel launch
+ * of the last concord_sweep / concord_run / concord_solve_* (CUDA events
+ * recorded on the state's stream around the launch): launch_ms[q] in
+ * milliseconds and launch_sweeps[q] the sweeps it ran, for q < max_launches
+ * (MIXED runs launch twice: FP32 sweeps, then FP64 polishing).  Either array
+ * may be NULL; *n_launches receives the number of launches (<= 4 recorded).
+ */
+int concord_get_timing(concord_state *st, double *launch_ms, int *launch_sweeps,
+                       int max_launches, int *n_launches);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * states, all entry points): the basis of launch accounting in benchmarks. */
+unsigned long long concord_kernel_launches(void);
+
+/*
+ * concord_set_gram_mode -- Gram arithmetic used by concord_solve_device /
+ * concord_solve_host: CONCORD_GRAM_FP64 (default for FP64 states),
+ * CONCORD_GRAM_FP32 or CONCORD_GRAM_TF32X3 (mixed states only).
+ */
+int concord_set_gram_mode(concord_state *st, int mode);
+
+/*
+ * concord_sweep -- run exactly n_sweeps outer iterations of Algorithm 1 at
+ * penalty lambda (>= 0) on the state, in its working precision (MIXED: FP32
+ * sweeps, no polish):  for colour k = 1..pe-1 all pairs of colour k get the
+ * closed-form update of Eq. 3 at once, then every diagonal entry gets Eq. 2;
+ * W = Omega S is kept current row by row.  One persistent kernel launch.
+ * res (may be NULL) receives the objective, KKT residual and delta after the
+ * last sweep.  Synchronises the state's stream.
+ */
+int concord_sweep(concord_state *st, double lambda, int n_sweeps, concord_result *res);
+
+/*
+ * concord_run -- sweeps at lambda until the stopping rule holds (stop_rule
+ * CONCORD_STOP_KKT: KKT <= tol; CONCORD_STOP_DELTA: delta < tol) or
+ * max_sweeps.  FP64 state: all sweeps in FP64.  MIXED state: FP32 sweeps
+ * until the rule holds at max(tol, switch_tol) (switch_tol <= 0 picks 10 *
+ * tol), then W is rebuilt in FP64 from the FP64 copies of S and Omega and
+ * FP64 sweeps polish to tol.  Returns CONCORD_OK or CONCORD_NOT_CONVERGED
+ * (outputs filled either way) or an error.  Synchronises the stream.
+ */
+int concord_run(concord_state *st, double lambda, double tol, int max_sweeps,
+                int stop_rule, double switch_tol, concord_result *res);
+
+/*
+ * concord_solve_device -- the whole path on resident data: prepare X
+ * (n <= n_cap rows, device, row stride ldx, x_dtype), S = Z^T Z / n (FP64
+ * state: CONCORD_GRAM_FP64; MIXED: CONCORD_GRAM_TF32X3 then an FP64 copy of
+ * the FP32 S), Omega = I, then concord_run.  Omega_dev (may be NULL) receives
+ * Omega in `omega_dtype` with row stride ldo.
+ */
+int concord_solve_device(concord_state *st, const void *X_dev, int x_dtype, int n,
+                         int ldx, int prep, double lambda, double tol, int max_sweeps,
+                         int stop_rule, void *Omega_dev, int omega_dtype, int ldo,
+                         concord_result *res);
+
+/*
+ * concord_solve_host -- as concord_solve_device, with X (n x p, FP64, dense,
+ * host) copied in and Omega (p x p, FP64, dense, host) copied out inside the
+ * call.  Omega_host may be NULL.
+ */
+int concord_solve_host(concord_state *st, const double *X_host, int n, int prep,
+                       double lambda, double tol, int max_sweeps, int stop_rule,
+                       double *Omega_host, concord_result *res);
+
+/*
+ * concord_solve -- one-shot convenience: creates a state, solves from host
+ * data (is_X != 0: X is n x p; is_X == 0: S is p x p and n is ignored), and
+ * destroys the state.  Omega0_host (NULL = I) is an optional warm start.
+ */
+int concord_solve(const double *data_host, int is_X, int n, int p, int prep,
+                  double lambda, double tol, int max_sweeps, int precision,
+                  const double *Omega0_host, double *Omega_host, concord_result *res);
+
+/*
+ * concord_lambda_max -- max_{i<j} |s_ij| (s_ii^{-1/2} + s_jj^{-1/2}) of the
+ * state's S: the smallest lambda at which the diagonal point
+ * diag(s_ii^{-1/2}) satisfies the KKT conditions of Eq. 1 (G_ij = s_ij
+ * (w_ii + w_jj) there).  Synchronises the stream.
+ */
+int concord_lambda_max(concord_state *st, double *lambda_max);
+
+/*
+ * concord_set_fault -- failure-detection testing.  vertex >= 0 makes that
+ * vertex skip publishing its mailbox value at colour step `step` of the next
+ * launch, so its partner's bounded wait runs out (CONCORD_E_TIMEOUT with
+ * the partner and step in the result).  vertex < 0 clears it.  No kernel
+ * faults, traps or hangs: every wait ends at the state's timeout.
+ */
+int concord_set_fault(concord_state *st, int vertex, int step);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CONCORD_GB300_H */

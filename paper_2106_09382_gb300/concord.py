@@ -1,0 +1,318 @@
+"""Python binding of the C ABI in ``include/concord.h`` (ctypes).
+
+Argument marshalling only: every step of the estimator runs in the CUDA
+library ``libconcord_gb300.so``.  Device buffers are torch tensors (used for
+memory and streams only); host buffers are numpy arrays.  Loading raises if
+the library cannot be built or loaded: there is no CPU fallback.
+
+Names follow the C entry points: ``concord_schedule``, ``concord_gram``,
+``State`` (concord_create / _set_S / _set_omega / _sweep / _run /
+_solve_device / _solve_host / _get_omega / _get_W / _get_history /
+_lambda_max / _set_timeout / _set_fault / _destroy) and ``concord_solve``.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+OK, NOT_CONVERGED = 0, 1
+E_ARG, E_NONPOS_DIAG, E_NONFINITE, E_CUDA, E_TIMEOUT, E_NOMEM, E_OCCUPANCY = (
+    -1, -2, -3, -4, -5, -6, -7)
+FP64, MIXED = 0, 1
+F64, F32 = 0, 1
+PREP_NONE, PREP_CENTER, PREP_STANDARDIZE = 0, 1, 2
+GRAM_FP64, GRAM_FP32, GRAM_TF32X3 = 0, 1, 2
+STOP_KKT, STOP_DELTA = 0, 1
+
+STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "E_ARG", -2: "E_NONPOS_DIAG",
+                -3: "E_NONFINITE", -4: "E_CUDA", -5: "E_TIMEOUT", -6: "E_NOMEM",
+                -7: "E_OCCUPANCY"}
+
+
+class ConcordResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("sweeps", ctypes.c_int),
+                ("sweeps_fp32", ctypes.c_int), ("first_delta_sweep", ctypes.c_int),
+                ("objective", ctypes.c_double), ("kkt", ctypes.c_double),
+                ("delta", ctypes.c_double), ("lam", ctypes.c_double),
+                ("active_pairs", ctypes.c_longlong), ("seconds", ctypes.c_double),
+                ("timeout_vertex", ctypes.c_int), ("timeout_step", ctypes.c_int),
+                ("reserved0", ctypes.c_int), ("reserved1", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+class ConcordError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (STATUS_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+_vp, _ci, _cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+_rp = ctypes.POINTER(ConcordResult)
+_ip = ctypes.POINTER(ctypes.c_int)
+_dp = ctypes.POINTER(ctypes.c_double)
+
+# name -> (argtypes, restype); the exported symbols of include/concord.h
+SIGNATURES = {
+    "concord_result_size": ([], ctypes.c_size_t),
+    "concord_last_error": ([], ctypes.c_char_p),
+    "concord_version": ([], ctypes.c_char_p),
+    "concord_schedule": ([_ci, ctypes.POINTER(ctypes.c_int32), _ip], _ci),
+    "concord_gram": ([_vp, _ci, _ci, _ci, _ci, _ci, _ci, _vp, _ci, _ci, _vp], _ci),
+    "concord_create": ([ctypes.POINTER(_vp), _ci, _ci, _ci, _ci], _ci),
+    "concord_destroy": ([_vp], _ci),
+    "concord_set_stream": ([_vp, _vp], _ci),
+    "concord_set_timeout": ([_vp, _cd], _ci),
+    "concord_set_S": ([_vp, _vp, _ci, _ci], _ci),
+    "concord_set_omega": ([_vp, _vp, _ci, _ci], _ci),
+    "concord_get_omega": ([_vp, _vp, _ci, _ci], _ci),
+    "concord_get_W": ([_vp, _vp, _ci, _ci], _ci),
+    "concord_get_history": ([_vp, _dp, _ci, _ip], _ci),
+    "concord_set_gram_mode": ([_vp, _ci], _ci),
+    "concord_sweep": ([_vp, _cd, _ci, _rp], _ci),
+    "concord_run": ([_vp, _cd, _cd, _ci, _ci, _cd, _rp], _ci),
+    "concord_solve_device": ([_vp, _vp, _ci, _ci, _ci, _ci, _cd, _cd, _ci, _ci, _vp, _ci, _ci,
+                              _rp], _ci),
+    "concord_solve_host": ([_vp, _dp, _ci, _ci, _cd, _cd, _ci, _ci, _dp, _rp], _ci),
+    "concord_solve": ([_dp, _ci, _ci, _ci, _ci, _cd, _cd, _ci, _ci, _dp, _dp, _rp], _ci),
+    "concord_lambda_max": ([_vp, _dp], _ci),
+    "concord_set_fault": ([_vp, _ci, _ci], _ci),
+    "concord_get_timing": ([_vp, _dp, _ip, _ci, _ip], _ci),
+    "concord_kernel_launches": ([], ctypes.c_ulonglong),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(build: bool = True) -> ctypes.CDLL:
+    """Load (building first if needed) libconcord_gb300.so."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _build
+        path = _build.build() if build else _build.LIB
+        lib = ctypes.CDLL(path)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        if lib.concord_result_size() != ctypes.sizeof(ConcordResult):
+            raise RuntimeError("concord_result layout mismatch")
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, allow=(OK,)) -> int:
+    if rc in allow:
+        return rc
+    msg = load().concord_last_error().decode(errors="replace")
+    raise ConcordError(rc, msg)
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().concord_kernel_launches())
+
+
+def last_error() -> str:
+    return load().concord_last_error().decode(errors="replace")
+
+
+# ------------------------------------------------------------------ schedule
+def concord_schedule(p: int) -> np.ndarray:
+    """(pe-1, pe/2, 2) int32 pairs of the circle-method colouring (Section 3.2)."""
+    pe = p + (p % 2)
+    out = np.empty((max(pe - 1, 1), max(pe // 2, 1), 2), dtype=np.int32)
+    nc = ctypes.c_int(0)
+    _check(load().concord_schedule(int(p), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   ctypes.byref(nc)))
+    return out
+
+
+# ---------------------------------------------------------------------- gram
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError("float64 or float32 tensor expected, got %s" % t.dtype)
+
+
+def _stream_ptr(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def concord_gram(X, prep: int = PREP_STANDARDIZE, mode: int = GRAM_FP64, out_dtype=None,
+                 stream=None):
+    """S = Z^T Z / n on the device for a CUDA tensor X (n x p, row-major)."""
+    import torch
+    assert X.is_cuda and X.dim() == 2 and X.stride(1) == 1
+    n, p = X.shape
+    out_dtype = out_dtype or (torch.float64 if mode == GRAM_FP64 else torch.float32)
+    S = torch.empty((p, p), dtype=out_dtype, device=X.device)
+    _check(load().concord_gram(X.data_ptr(), _dtype_code(X), n, p, X.stride(0), prep, mode,
+                               S.data_ptr(), _dtype_code(S), p, _stream_ptr(stream)))
+    return S
+
+
+# --------------------------------------------------------------------- state
+class State:
+    """A solver state (concord_create) bound to one device and stream."""
+
+    def __init__(self, p: int, precision: int = FP64, n_cap: int = 0, device: int | None = None):
+        import torch
+        lib = load()
+        dev = torch.cuda.current_device() if device is None else int(device)
+        self._ptr = ctypes.c_void_p()
+        _check(lib.concord_create(ctypes.byref(self._ptr), int(p), int(precision), int(n_cap),
+                                  dev))
+        self.p, self.precision, self.n_cap, self.device = int(p), int(precision), int(n_cap), dev
+        self.last = None
+
+    # lifecycle
+    def close(self):
+        if getattr(self, "_ptr", None) and self._ptr.value:
+            load().concord_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # configuration
+    def set_stream(self, stream=None):
+        _check(load().concord_set_stream(self._ptr, _stream_ptr(stream) if stream is not False
+                                         else None))
+
+    def set_timeout(self, seconds: float):
+        _check(load().concord_set_timeout(self._ptr, float(seconds)))
+
+    def set_fault(self, vertex: int, step: int = 0):
+        _check(load().concord_set_fault(self._ptr, int(vertex), int(step)))
+
+    def set_gram_mode(self, mode: int):
+        _check(load().concord_set_gram_mode(self._ptr, int(mode)))
+
+    # data
+    def set_S(self, S):
+        assert S.is_cuda and S.dim() == 2 and S.stride(1) == 1
+        _check(load().concord_set_S(self._ptr, S.data_ptr(), _dtype_code(S), S.stride(0)))
+
+    def set_omega(self, Om):
+        assert Om.is_cuda and Om.dim() == 2 and Om.stride(1) == 1
+        _check(load().concord_set_omega(self._ptr, Om.data_ptr(), _dtype_code(Om), Om.stride(0)))
+
+    def get_omega(self, dtype=None):
+        import torch
+        out = torch.empty((self.p, self.p), dtype=dtype or torch.float64,
+                          device="cuda:%d" % self.device)
+        _check(load().concord_get_omega(self._ptr, out.data_ptr(), _dtype_code(out), self.p))
+        return out
+
+    def get_W(self, dtype=None):
+        import torch
+        out = torch.empty((self.p, self.p), dtype=dtype or torch.float64,
+                          device="cuda:%d" % self.device)
+        _check(load().concord_get_W(self._ptr, out.data_ptr(), _dtype_code(out), self.p))
+        return out
+
+    def history(self) -> np.ndarray:
+        rows = ctypes.c_int(0)
+        _check(load().concord_get_history(self._ptr, None, 0, ctypes.byref(rows)))
+        h = np.zeros((max(rows.value, 1), 4), dtype=np.float64)
+        _check(load().concord_get_history(self._ptr, h.ctypes.data_as(_dp), rows.value,
+                                          ctypes.byref(rows)))
+        return h[: rows.value]
+
+    def timing(self):
+        """[(milliseconds, sweeps)] of each sweep-kernel launch of the last call."""
+        ms = (ctypes.c_double * 4)()
+        sw = (ctypes.c_int * 4)()
+        n = ctypes.c_int(0)
+        _check(load().concord_get_timing(self._ptr, ms, sw, 4, ctypes.byref(n)))
+        return [(ms[q], sw[q]) for q in range(min(n.value, 4))]
+
+    def lambda_max(self) -> float:
+        v = ctypes.c_double(0)
+        _check(load().concord_lambda_max(self._ptr, ctypes.byref(v)))
+        return v.value
+
+    # iteration
+    def sweep(self, lam: float, n_sweeps: int = 1) -> ConcordResult:
+        r = ConcordResult()
+        rc = load().concord_sweep(self._ptr, float(lam), int(n_sweeps), ctypes.byref(r))
+        self.last = r
+        _check(rc, (OK, NOT_CONVERGED))
+        return r
+
+    def run(self, lam: float, tol: float = 1e-5, max_sweeps: int = 1000,
+            stop_rule: int = STOP_KKT, switch_tol: float = 0.0) -> ConcordResult:
+        r = ConcordResult()
+        rc = load().concord_run(self._ptr, float(lam), float(tol), int(max_sweeps),
+                                int(stop_rule), float(switch_tol), ctypes.byref(r))
+        self.last = r
+        _check(rc, (OK, NOT_CONVERGED))
+        return r
+
+    def solve_device(self, X, lam: float, tol: float = 1e-5, max_sweeps: int = 1000,
+                     prep: int = PREP_STANDARDIZE, stop_rule: int = STOP_KKT, Omega_out=None):
+        assert X.is_cuda and X.dim() == 2 and X.stride(1) == 1
+        r = ConcordResult()
+        optr, odt, old = (None, F64, self.p)
+        if Omega_out is not None:
+            optr, odt, old = Omega_out.data_ptr(), _dtype_code(Omega_out), Omega_out.stride(0)
+        rc = load().concord_solve_device(self._ptr, X.data_ptr(), _dtype_code(X), X.shape[0],
+                                         X.stride(0), int(prep), float(lam), float(tol),
+                                         int(max_sweeps), int(stop_rule), optr, odt, old,
+                                         ctypes.byref(r))
+        self.last = r
+        _check(rc, (OK, NOT_CONVERGED))
+        return r
+
+    def solve_host(self, X: np.ndarray, lam: float, tol: float = 1e-5, max_sweeps: int = 1000,
+                   prep: int = PREP_STANDARDIZE, stop_rule: int = STOP_KKT, Omega_out=None):
+        assert X.dtype == np.float64 and X.flags.c_contiguous and X.shape[1] == self.p
+        r = ConcordResult()
+        optr = None
+        if Omega_out is not None:
+            assert Omega_out.dtype == np.float64 and Omega_out.flags.c_contiguous
+            optr = Omega_out.ctypes.data_as(_dp)
+        rc = load().concord_solve_host(self._ptr, X.ctypes.data_as(_dp), X.shape[0], int(prep),
+                                       float(lam), float(tol), int(max_sweeps), int(stop_rule),
+                                       optr, ctypes.byref(r))
+        self.last = r
+        _check(rc, (OK, NOT_CONVERGED))
+        return r
+
+
+def concord_solve(data: np.ndarray, lam: float, tol: float = 1e-5, max_sweeps: int = 1000,
+                  precision: int = FP64, is_X: bool = True, prep: int = PREP_STANDARDIZE,
+                  Omega0: np.ndarray | None = None):
+    """One-shot solve from host data; returns (Omega (p x p float64), ConcordResult)."""
+    data = np.ascontiguousarray(data, dtype=np.float64)
+    n, p = (data.shape if is_X else (0, data.shape[0]))
+    Om = np.empty((p, p), dtype=np.float64)
+    r = ConcordResult()
+    o0 = None if Omega0 is None else np.ascontiguousarray(Omega0, dtype=np.float64)
+    rc = load().concord_solve(data.ctypes.data_as(_dp), int(bool(is_X)), int(n), int(p),
+                              int(prep), float(lam), float(tol), int(max_sweeps),
+                              int(precision), o0.ctypes.data_as(_dp) if o0 is not None else None,
+                              Om.ctypes.data_as(_dp), ctypes.byref(r))
+    _check(rc, (OK, NOT_CONVERGED))
+    return Om, r

@@ -1,0 +1,929 @@
+// Host side of the C ABI declared in include/concord.h.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/concord.h"
+#include "kernels.h"
+
+using namespace concord;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(expr)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      if (e_ == cudaErrorMemoryAllocation)                                               \
+        return fail(CONCORD_E_NOMEM, "%s: %s", #expr, cudaGetErrorString(e_));           \
+      if (e_ == cudaErrorCooperativeLaunchTooLarge)                                      \
+        return fail(CONCORD_E_OCCUPANCY, "%s: %s", #expr, cudaGetErrorString(e_));       \
+      return fail(CONCORD_E_CUDA, "%s: %s", #expr, cudaGetErrorString(e_));              \
+    }                                                                                    \
+  } while (0)
+
+constexpr int kMailboxDepth = 8;
+constexpr int kHistCap = 8192;
+constexpr int kMaxTimedLaunches = 4;
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+struct concord_state {
+  int device = -1, sms = 0;
+  int p = 0, pe = 0, P = 0, ld = 0, precision = 0, n_cap = 0;
+  cudaStream_t stream = nullptr, own_stream = nullptr;
+  // working set: float for CONCORD_MIXED, double for CONCORD_FP64
+  void *S = nullptr, *W = nullptr, *Om = nullptr, *sdiagT = nullptr;
+  double* sdiag64 = nullptr;
+  double* omdiag64 = nullptr;  // mixed only
+  // FP64 copies (mixed) or aliases of the working set (fp64)
+  double *S64 = nullptr, *W64 = nullptr, *Om64 = nullptr;
+  bool om64_current = false;  // mixed: FP64 copies hold the latest iterate
+  unsigned long long* mbox = nullptr;
+  int depth = kMailboxDepth;
+  unsigned* barrier = nullptr;
+  int* abort_info = nullptr;  // [0] abort word, [1] vertex, [2] step
+  double* partials = nullptr;
+  double* hist = nullptr;
+  double* result = nullptr;
+  int* flag = nullptr;
+  unsigned long long* lmax = nullptr;
+  unsigned tag_base = 1;
+  double timeout_s = 2.0;
+  int fault_vertex = -1, fault_step = -1;
+  int max_grid = 0;
+  int hist_rows = 0;
+  // data workspace
+  double *mean = nullptr, *inv_scale = nullptr;
+  void* Z = nullptr;
+  int ldz = 0;
+  double* Xstage = nullptr;  // n_cap x p FP64, host-data path
+  float *zt_hi = nullptr, *zt_lo = nullptr;
+  int n_pad = 0, p_pad = 0;
+  int gram_mode = CONCORD_GRAM_FP64;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t lev[2 * kMaxTimedLaunches] = {};
+  double launch_ms[kMaxTimedLaunches] = {};
+  int launch_sweeps[kMaxTimedLaunches] = {};
+  int n_launch = 0;
+  // pinned host mirrors
+  double* h_result = nullptr;
+  int* h_abort = nullptr;
+  int* h_flag = nullptr;
+};
+
+namespace {
+
+bool is_mixed(const concord_state* st) { return st->precision == CONCORD_MIXED; }
+
+int check_state(concord_state* st) {
+  if (!st) return fail(CONCORD_E_ARG, "state is NULL");
+  CK(cudaSetDevice(st->device));
+  return CONCORD_OK;
+}
+
+int read_flag(concord_state* st, int* out) {
+  CK(cudaMemcpyAsync(st->h_flag, st->flag, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
+  CK(cudaStreamSynchronize(st->stream));
+  *out = *st->h_flag;
+  return CONCORD_OK;
+}
+
+struct RunOut {
+  int status = CONCORD_OK;
+  int sweeps = 0, first_delta = 0;
+  double kkt = 0, obj = 0, delta = 0, active = 0;
+  int to_vertex = -1, to_step = -1;
+};
+
+// One persistent launch: n_sweeps outer iterations (fewer if the stopping
+// rule holds first), or only the objective / KKT pass when kkt_only.
+template <typename T>
+int launch_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* omdiag64, double lambda,
+               double tol, int stop_rule, int n_sweeps, int kkt_only, int hist_offset, RunOut* out) {
+  const int p = st->p;
+  int block_warps = (p + st->sms - 1) / st->sms;
+  int bw = 1;
+  while (bw < block_warps && bw < 32) bw <<= 1;
+  block_warps = bw;
+  const int block = block_warps * 32;
+  int occ = 0;
+  CK(sweep_occupancy(sizeof(T) == 4, block, &occ));
+  if (occ < 1) return fail(CONCORD_E_OCCUPANCY, "sweep kernel cannot run %d threads per block", block);
+  int grid = st->sms * occ;
+  const int need = (p + block_warps - 1) / block_warps;
+  if (grid > need) grid = need;
+  if (grid > st->max_grid) grid = st->max_grid;
+  const int TW = grid * block_warps;
+  const int R = (p + TW - 1) / TW;
+  if (R > 32) return fail(CONCORD_E_ARG, "p=%d needs %d rows per warp (max 32)", p, R);
+
+  // keep step tags monotone over the state's lifetime; restart them (and
+  // clear the mailboxes) well before 32-bit overflow
+  const unsigned long long span = (unsigned long long)(n_sweeps + 1) * (unsigned)st->P + st->depth;
+  if ((unsigned long long)st->tag_base + span >= (1ull << 31)) {
+    CK(cudaMemsetAsync(st->mbox, 0, sizeof(unsigned long long) * 2 * (size_t)st->depth * st->pe,
+                       st->stream));
+    st->tag_base = 1;
+  }
+  CK(cudaMemsetAsync(st->barrier, 0, sizeof(unsigned), st->stream));
+  CK(cudaMemsetAsync(st->abort_info, 0, 3 * sizeof(int), st->stream));
+
+  SweepArgs<T> a;
+  memset(&a, 0, sizeof a);
+  a.p = p;
+  a.P = st->P;
+  a.ld = st->ld;
+  a.rows_per_warp = R;
+  a.W = W;
+  a.Om = Om;
+  a.S = S;
+  a.sdiag = sdiagT;
+  a.sdiag64 = st->sdiag64;
+  a.omdiag64 = omdiag64;
+  a.mbox = st->mbox;
+  a.depth = st->depth;
+  a.barrier = st->barrier;
+  a.wait.abort = st->abort_info;
+  a.wait.info = st->abort_info + 1;
+  a.wait.timeout_ns = (uint64_t)(st->timeout_s * 1e9);
+  a.partials = st->partials;
+  a.hist = st->hist + (size_t)hist_offset * kHist;
+  a.hist_len = kHistCap - hist_offset;
+  a.result = st->result;
+  a.lambda = lambda;
+  a.tol = tol;
+  a.delta_tol = 1e-5;
+  a.stop_rule = stop_rule;
+  a.n_sweeps = n_sweeps;
+  a.kkt_only = kkt_only;
+  a.tag_base = st->tag_base;
+  a.fault_vertex = st->fault_vertex;
+  a.fault_step = st->fault_step;
+  st->fault_vertex = -1;  // one-shot
+  st->fault_step = -1;
+
+  const int slot_ev = st->n_launch < kMaxTimedLaunches ? st->n_launch : -1;
+  if (slot_ev >= 0) CK(cudaEventRecord(st->lev[2 * slot_ev], st->stream));
+  CK(launch_sweep(a, grid, block, st->stream));
+  if (slot_ev >= 0) CK(cudaEventRecord(st->lev[2 * slot_ev + 1], st->stream));
+  st->tag_base += (unsigned)span;
+
+  CK(cudaMemcpyAsync(st->h_result, st->result, kRes * sizeof(double), cudaMemcpyDeviceToHost,
+                     st->stream));
+  CK(cudaMemcpyAsync(st->h_abort, st->abort_info, 3 * sizeof(int), cudaMemcpyDeviceToHost,
+                     st->stream));
+  CK(cudaStreamSynchronize(st->stream));
+  CK(cudaGetLastError());
+  const double* r = st->h_result;
+  out->sweeps = (int)r[kResSweeps];
+  out->kkt = r[kResKkt];
+  out->obj = r[kResObj];
+  out->delta = r[kResDelta];
+  out->active = r[kResActive];
+  out->first_delta = (int)r[kResFirstDelta];
+  if (slot_ev >= 0) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, st->lev[2 * slot_ev], st->lev[2 * slot_ev + 1]));
+    st->launch_ms[slot_ev] = ms;
+    st->launch_sweeps[slot_ev] = out->sweeps;
+    st->n_launch = slot_ev + 1;
+  }
+  const int code = (int)r[kResStatus];
+  if (st->h_abort[0] != 0) {
+    out->status = CONCORD_E_TIMEOUT;
+    out->to_vertex = st->h_abort[1];
+    out->to_step = st->h_abort[2];
+    return fail(CONCORD_E_TIMEOUT, "device wait ran out (vertex %d, step %d)", st->h_abort[1],
+                st->h_abort[2]);
+  }
+  out->status = code == 0 ? CONCORD_OK
+                          : code == 1 ? CONCORD_NOT_CONVERGED
+                                      : code == 2 ? CONCORD_E_NONFINITE : CONCORD_E_TIMEOUT;
+  if (out->status == CONCORD_E_NONFINITE)
+    return fail(CONCORD_E_NONFINITE, "non-finite objective or KKT residual after sweep %d",
+                out->sweeps);
+  return CONCORD_OK;
+}
+
+void fill_result(concord_result* res, const RunOut& o, int sweeps, int sweeps32, int first_delta,
+                 double lambda, double seconds) {
+  if (!res) return;
+  memset(res, 0, sizeof *res);
+  res->status = o.status;
+  res->sweeps = sweeps;
+  res->sweeps_fp32 = sweeps32;
+  res->first_delta_sweep = first_delta;
+  res->objective = o.obj;
+  res->kkt = o.kkt;
+  res->delta = o.delta;
+  res->lambda = lambda;
+  res->active_pairs = (long long)(o.active + 0.5);
+  res->seconds = seconds;
+  res->timeout_vertex = o.to_vertex;
+  res->timeout_step = o.to_step;
+}
+
+// mixed: FP32 iterate -> FP64 copies (Omega with its FP64 diagonal; W rebuilt
+// in FP64 from Omega and S)
+int promote_to_fp64(concord_state* st) {
+  CK(launch_convert(st->Om, 1, st->ld, st->Om64, 0, st->ld, st->p, st->p, st->stream));
+  CK(cudaMemcpy2DAsync(st->Om64, (size_t)(st->ld + 1) * sizeof(double), st->omdiag64,
+                       sizeof(double), sizeof(double), st->p, cudaMemcpyDeviceToDevice,
+                       st->stream));
+  CK(launch_refresh_w(st->Om64, st->S64, st->W64, st->p, st->ld, st->sms, st->stream));
+  st->om64_current = true;
+  return CONCORD_OK;
+}
+
+// mixed: FP64 copies -> FP32 working set
+int demote_from_fp64(concord_state* st) {
+  CK(launch_convert(st->Om64, 0, st->ld, st->Om, 1, st->ld, st->p, st->p, st->stream));
+  CK(launch_convert(st->W64, 0, st->ld, st->W, 1, st->ld, st->p, st->p, st->stream));
+  CK(cudaMemcpy2DAsync(st->omdiag64, sizeof(double), st->Om64, (size_t)(st->ld + 1) * sizeof(double),
+                       sizeof(double), st->p, cudaMemcpyDeviceToDevice, st->stream));
+  return CONCORD_OK;
+}
+
+int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int stop_rule,
+             double switch_tol, int exact, concord_result* res) {
+  if (!(lambda >= 0.0) || max_sweeps < 0 || (stop_rule != 0 && stop_rule != 1))
+    return fail(CONCORD_E_ARG, "lambda >= 0, max_sweeps >= 0, stop_rule in {0,1} required");
+  if (!exact && !(tol > 0.0)) return fail(CONCORD_E_ARG, "tol must be > 0");
+  const double run_tol = exact ? -1.0 : tol;
+  st->hist_rows = 0;
+  st->n_launch = 0;
+  CK(cudaEventRecord(st->ev0, st->stream));
+  RunOut o1, o2;
+  int rc;
+  if (!is_mixed(st)) {
+    rc = launch_run<double>(st, st->S64, st->W64, st->Om64, (const double*)st->sdiagT, nullptr,
+                            lambda, run_tol, stop_rule, max_sweeps, 0, 0, &o1);
+    CK(cudaEventRecord(st->ev1, st->stream));
+    CK(cudaEventSynchronize(st->ev1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, st->ev0, st->ev1));
+    st->hist_rows = o1.sweeps;
+    fill_result(res, o1, o1.sweeps, 0, o1.first_delta, lambda, ms * 1e-3);
+    return rc != CONCORD_OK ? rc : o1.status;
+  }
+  // mixed precision: FP32 sweeps ...
+  double tol1 = exact ? -1.0 : (switch_tol > 0 ? switch_tol : 10.0 * tol);
+  if (!exact && tol1 < tol) tol1 = tol;
+  rc = launch_run<float>(st, (float*)st->S, (float*)st->W, (float*)st->Om,
+                         (const float*)st->sdiagT, st->omdiag64, lambda, tol1, stop_rule,
+                         max_sweeps, 0, 0, &o1);
+  st->om64_current = false;
+  st->hist_rows = o1.sweeps;
+  if (rc != CONCORD_OK || exact) {
+    CK(cudaEventRecord(st->ev1, st->stream));
+    CK(cudaEventSynchronize(st->ev1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, st->ev0, st->ev1));
+    fill_result(res, o1, o1.sweeps, o1.sweeps, o1.first_delta, lambda, ms * 1e-3);
+    return rc != CONCORD_OK ? rc : o1.status;
+  }
+  // ... then FP64 polishing from W rebuilt in FP64
+  if ((rc = promote_to_fp64(st)) != CONCORD_OK) return rc;
+  const int left = max_sweeps - o1.sweeps;
+  rc = launch_run<double>(st, st->S64, st->W64, st->Om64, st->sdiag64, nullptr, lambda, tol,
+                          stop_rule, left, left == 0 ? 1 : 0, o1.sweeps, &o2);
+  st->hist_rows = o1.sweeps + o2.sweeps;
+  if (rc == CONCORD_OK) rc = demote_from_fp64(st);
+  CK(cudaEventRecord(st->ev1, st->stream));
+  CK(cudaEventSynchronize(st->ev1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, st->ev0, st->ev1));
+  const int fd = o1.first_delta ? o1.first_delta : (o2.first_delta ? o1.sweeps + o2.first_delta : 0);
+  fill_result(res, o2, o1.sweeps + o2.sweeps, o1.sweeps, fd, lambda, ms * 1e-3);
+  return rc != CONCORD_OK ? rc : o2.status;
+}
+
+// Load S (already in the state's S64 for fp64, or S (f32) + S64 for mixed)
+// bookkeeping: diagonals, Omega = I, W = S.
+int reset_iterate(concord_state* st) {
+  const int p = st->p, ld = st->ld;
+  CK(cudaMemsetAsync(st->flag, 0, sizeof(int), st->stream));
+  CK(launch_extract_diag(st->S64, 0, ld, p, st->sdiag64, is_mixed(st) ? st->sdiagT : nullptr, 1,
+                         st->flag, st->stream));
+  if (!is_mixed(st))
+    CK(cudaMemcpyAsync(st->sdiagT, st->sdiag64, sizeof(double) * p, cudaMemcpyDeviceToDevice,
+                       st->stream));
+  if (is_mixed(st)) {
+    CK(launch_set_identity(st->Om, 1, p, ld, st->stream));
+    CK(cudaMemcpyAsync(st->W, st->S, sizeof(float) * (size_t)p * ld, cudaMemcpyDeviceToDevice,
+                       st->stream));
+    CK(launch_fill_f64(st->omdiag64, 1.0, p, st->stream));
+  } else {
+    CK(launch_set_identity(st->Om64, 0, p, ld, st->stream));
+    CK(cudaMemcpyAsync(st->W64, st->S64, sizeof(double) * (size_t)p * ld, cudaMemcpyDeviceToDevice,
+                       st->stream));
+  }
+  st->om64_current = false;
+  int bad = 0;
+  int rc = read_flag(st, &bad);
+  if (rc) return rc;
+  if (bad & 2) return fail(CONCORD_E_NONFINITE, "S has a non-finite diagonal entry");
+  if (bad & 1) return fail(CONCORD_E_NONPOS_DIAG, "S has a diagonal entry <= 0 (constant column?)");
+  return CONCORD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t concord_result_size(void) { return sizeof(concord_result); }
+
+const char* concord_last_error(void) { return g_err.c_str(); }
+
+const char* concord_version(void) { return "concord-gb300 0.1 (sm_103a)"; }
+
+int concord_schedule(int p, int32_t* pairs_host, int* n_colours) {
+  if (p < 2 || !pairs_host || !n_colours) return fail(CONCORD_E_ARG, "p >= 2 and non-NULL outputs");
+  const int pe = p + (p & 1), P = pe - 1, half = pe / 2;
+  // slot q of colour c holds the vertices at facing ring positions; the
+  // 0-based vertex at position m (1-based, m >= 2) during colour c is
+  // ((m - 2 - c) mod P) + 1, and position 1 holds vertex 0
+  for (int c = 0; c < P; ++c)
+    for (int q = 0; q < half; ++q) {
+      int u, v;
+      if (q == 0) {
+        u = 0;
+        v = cm_partner(0, c, P);
+      } else {
+        // position m = q + 1 (1-based) faces position pe - q
+        int m = q + 1;
+        u = ((m - 2 - c) % P + P) % P + 1;
+        v = cm_partner(u, c, P);
+      }
+      int32_t* slot = pairs_host + ((size_t)c * half + q) * 2;
+      if (u >= p || v >= p) {
+        slot[0] = slot[1] = -1;
+      } else {
+        slot[0] = u;
+        slot[1] = v;
+      }
+    }
+  *n_colours = P;
+  return CONCORD_OK;
+}
+
+int concord_create(concord_state** out, int p, int precision, int n_cap, int device) {
+  if (!out) return fail(CONCORD_E_ARG, "out is NULL");
+  *out = nullptr;
+  if (p < 2) return fail(CONCORD_E_ARG, "p must be >= 2 (got %d)", p);
+  if (precision != CONCORD_FP64 && precision != CONCORD_MIXED)
+    return fail(CONCORD_E_ARG, "precision must be CONCORD_FP64 or CONCORD_MIXED");
+  if (n_cap < 0) return fail(CONCORD_E_ARG, "n_cap must be >= 0");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+    return fail(CONCORD_E_CUDA, "no CUDA device");
+  if (device < 0) CK(cudaGetDevice(&device));
+  if (device >= ndev) return fail(CONCORD_E_ARG, "device %d out of range", device);
+  CK(cudaSetDevice(device));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, device));
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(CONCORD_E_CUDA, "library is built for sm_103a; device is sm_%d%d", prop.major,
+                prop.minor);
+  if (!prop.cooperativeLaunch) return fail(CONCORD_E_CUDA, "device lacks cooperative launch");
+
+  concord_state* st = new concord_state();
+  st->device = device;
+  st->sms = prop.multiProcessorCount;
+  st->p = p;
+  st->pe = p + (p & 1);
+  st->P = st->pe - 1;
+  st->ld = round_up(p, kTile);
+  st->precision = precision;
+  st->n_cap = n_cap;
+  const size_t mat = (size_t)p * st->ld;
+  const size_t e = is_mixed(st) ? 4 : 8;
+  int rc = CONCORD_OK;
+#define ALLOC(ptr, bytes)                                                       \
+  do {                                                                          \
+    cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                       \
+    if (e_ != cudaSuccess) {                                                    \
+      rc = fail(CONCORD_E_NOMEM, "cudaMalloc(%zu): %s", (size_t)(bytes),        \
+                cudaGetErrorString(e_));                                        \
+      goto fail_out;                                                            \
+    }                                                                           \
+  } while (0)
+  {
+    if (cudaStreamCreateWithFlags(&st->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      rc = fail(CONCORD_E_CUDA, "cudaStreamCreate failed");
+      goto fail_out;
+    }
+    st->stream = st->own_stream;
+    if (is_mixed(st)) {
+      ALLOC(st->S, mat * e);
+      ALLOC(st->W, mat * e);
+      ALLOC(st->Om, mat * e);
+      ALLOC(st->sdiagT, sizeof(float) * p);
+      ALLOC(st->omdiag64, sizeof(double) * p);
+      ALLOC(st->S64, mat * 8);
+      ALLOC(st->W64, mat * 8);
+      ALLOC(st->Om64, mat * 8);
+    } else {
+      ALLOC(st->S64, mat * 8);
+      ALLOC(st->W64, mat * 8);
+      ALLOC(st->Om64, mat * 8);
+      ALLOC(st->sdiagT, sizeof(double) * p);
+      st->S = st->S64;
+      st->W = st->W64;
+      st->Om = st->Om64;
+    }
+    ALLOC(st->sdiag64, sizeof(double) * p);
+    // mailboxes sized for the FP64 form (2 words) so both precisions fit
+    ALLOC(st->mbox, sizeof(unsigned long long) * 2 * (size_t)st->depth * st->pe);
+    cudaMemset(st->mbox, 0, sizeof(unsigned long long) * 2 * (size_t)st->depth * st->pe);
+    ALLOC(st->barrier, sizeof(unsigned));
+    ALLOC(st->abort_info, 3 * sizeof(int));
+    ALLOC(st->flag, sizeof(int));
+    ALLOC(st->lmax, sizeof(unsigned long long));
+    st->max_grid = st->sms * 32;
+    ALLOC(st->partials, sizeof(double) * kParts * (size_t)st->max_grid);
+    ALLOC(st->hist, sizeof(double) * kHist * (size_t)kHistCap);
+    ALLOC(st->result, sizeof(double) * kRes);
+    ALLOC(st->mean, sizeof(double) * p);
+    ALLOC(st->inv_scale, sizeof(double) * p);
+    if (n_cap > 0) {
+      st->ldz = st->ld;
+      ALLOC(st->Z, (size_t)n_cap * st->ldz * e);
+      ALLOC(st->Xstage, (size_t)n_cap * p * sizeof(double));
+      st->n_pad = round_up(n_cap, 32);
+      st->p_pad = round_up(p, 128);
+      if (is_mixed(st)) {
+        ALLOC(st->zt_hi, sizeof(float) * (size_t)st->n_pad * st->p_pad);
+        ALLOC(st->zt_lo, sizeof(float) * (size_t)st->n_pad * st->p_pad);
+      }
+    }
+    st->gram_mode = is_mixed(st) ? CONCORD_GRAM_FP32 : CONCORD_GRAM_FP64;
+    if (cudaMallocHost((void**)&st->h_result, sizeof(double) * kRes) != cudaSuccess ||
+        cudaMallocHost((void**)&st->h_abort, 3 * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&st->h_flag, sizeof(int)) != cudaSuccess) {
+      rc = fail(CONCORD_E_NOMEM, "cudaMallocHost failed");
+      goto fail_out;
+    }
+    if (cudaEventCreate(&st->ev0) != cudaSuccess || cudaEventCreate(&st->ev1) != cudaSuccess) {
+      rc = fail(CONCORD_E_CUDA, "cudaEventCreate failed");
+      goto fail_out;
+    }
+    for (int q = 0; q < 2 * kMaxTimedLaunches; ++q)
+      if (cudaEventCreate(&st->lev[q]) != cudaSuccess) {
+        rc = fail(CONCORD_E_CUDA, "cudaEventCreate failed");
+        goto fail_out;
+      }
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+      rc = fail(CONCORD_E_CUDA, "device sync after allocation failed");
+      goto fail_out;
+    }
+    // Omega = I, W = S = I until concord_set_S
+    if (is_mixed(st)) {
+      launch_set_identity(st->S, 1, p, st->ld, st->stream);
+      launch_set_identity(st->S64, 0, p, st->ld, st->stream);
+    } else {
+      launch_set_identity(st->S64, 0, p, st->ld, st->stream);
+    }
+    rc = reset_iterate(st);
+    if (rc != CONCORD_OK) goto fail_out;
+    *out = st;
+    return CONCORD_OK;
+  }
+#undef ALLOC
+fail_out:
+  concord_destroy(st);
+  return rc;
+}
+
+int concord_destroy(concord_state* st) {
+  if (!st) return CONCORD_OK;
+  cudaSetDevice(st->device);
+  if (st->stream) cudaStreamSynchronize(st->stream);
+  void* dev[] = {st->mbox, st->barrier, st->abort_info, st->flag, st->lmax, st->partials,
+                 st->hist, st->result, st->mean, st->inv_scale, st->Z, st->Xstage, st->zt_hi,
+                 st->zt_lo, st->sdiag64, st->sdiagT, st->omdiag64, st->S64, st->W64, st->Om64};
+  for (void* d : dev)
+    if (d) cudaFree(d);
+  if (is_mixed(st)) {
+    if (st->S) cudaFree(st->S);
+    if (st->W) cudaFree(st->W);
+    if (st->Om) cudaFree(st->Om);
+  }
+  if (st->h_result) cudaFreeHost(st->h_result);
+  if (st->h_abort) cudaFreeHost(st->h_abort);
+  if (st->h_flag) cudaFreeHost(st->h_flag);
+  if (st->ev0) cudaEventDestroy(st->ev0);
+  if (st->ev1) cudaEventDestroy(st->ev1);
+  for (int q = 0; q < 2 * kMaxTimedLaunches; ++q)
+    if (st->lev[q]) cudaEventDestroy(st->lev[q]);
+  if (st->own_stream) cudaStreamDestroy(st->own_stream);
+  delete st;
+  return CONCORD_OK;
+}
+
+int concord_set_stream(concord_state* st, void* stream) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  st->stream = stream ? (cudaStream_t)stream : st->own_stream;
+  return CONCORD_OK;
+}
+
+int concord_set_timeout(concord_state* st, double seconds) {
+  if (!st) return fail(CONCORD_E_ARG, "state is NULL");
+  if (!(seconds > 0.0) || seconds > 3600.0) return fail(CONCORD_E_ARG, "timeout must be in (0, 3600] s");
+  st->timeout_s = seconds;
+  return CONCORD_OK;
+}
+
+int concord_set_fault(concord_state* st, int vertex, int step) {
+  if (!st) return fail(CONCORD_E_ARG, "state is NULL");
+  if (vertex >= st->p) return fail(CONCORD_E_ARG, "vertex out of range");
+  st->fault_vertex = vertex < 0 ? -1 : vertex;
+  st->fault_step = vertex < 0 ? -1 : step;
+  return CONCORD_OK;
+}
+
+int concord_set_S(concord_state* st, const void* S_dev, int s_dtype, int lds) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  if (!S_dev || (s_dtype != CONCORD_F64 && s_dtype != CONCORD_F32) || lds < st->p)
+    return fail(CONCORD_E_ARG, "S_dev non-NULL, dtype F64/F32, lds >= p required");
+  const int p = st->p, ld = st->ld, f32 = s_dtype == CONCORD_F32;
+  CK(cudaMemsetAsync(st->flag, 0, sizeof(int), st->stream));
+  CK(launch_check_symmetric(S_dev, f32, p, lds, st->flag, st->stream));
+  int bad = 0;
+  if ((rc = read_flag(st, &bad))) return rc;
+  if (bad & 2) return fail(CONCORD_E_NONFINITE, "S has a non-finite entry");
+  if (bad & 1) return fail(CONCORD_E_ARG, "S is not symmetric");
+  CK(launch_convert(S_dev, f32, lds, st->S64, 0, ld, p, p, st->stream));
+  if (is_mixed(st)) CK(launch_convert(S_dev, f32, lds, st->S, 1, ld, p, p, st->stream));
+  return reset_iterate(st);
+}
+
+int concord_set_omega(concord_state* st, const void* Om_dev, int dtype, int ld_in) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  if (!Om_dev || (dtype != CONCORD_F64 && dtype != CONCORD_F32) || ld_in < st->p)
+    return fail(CONCORD_E_ARG, "Omega0 non-NULL, dtype F64/F32, ld >= p required");
+  const int p = st->p, ld = st->ld, f32 = dtype == CONCORD_F32;
+  CK(cudaMemsetAsync(st->flag, 0, sizeof(int), st->stream));
+  CK(launch_check_symmetric(Om_dev, f32, p, ld_in, st->flag, st->stream));
+  CK(launch_extract_diag(Om_dev, f32, ld_in, p, nullptr, nullptr, 0, st->flag, st->stream));
+  int bad = 0;
+  if ((rc = read_flag(st, &bad))) return rc;
+  if (bad & 2) return fail(CONCORD_E_NONFINITE, "Omega0 has a non-finite entry");
+  if (bad & 1) return fail(CONCORD_E_ARG, "Omega0 is not symmetric with a positive diagonal");
+  CK(launch_convert(Om_dev, f32, ld_in, st->Om64, 0, ld, p, p, st->stream));
+  CK(launch_refresh_w(st->Om64, st->S64, st->W64, p, ld, st->sms, st->stream));
+  if (is_mixed(st)) {
+    st->om64_current = true;
+    if ((rc = demote_from_fp64(st))) return rc;
+  }
+  CK(cudaStreamSynchronize(st->stream));
+  return CONCORD_OK;
+}
+
+static int get_matrix(concord_state* st, bool omega, void* out, int dtype, int ld_out) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  if (!out || (dtype != CONCORD_F64 && dtype != CONCORD_F32) || ld_out < st->p)
+    return fail(CONCORD_E_ARG, "out non-NULL, dtype F64/F32, ld >= p required");
+  const int p = st->p, ld = st->ld, f32 = dtype == CONCORD_F32;
+  if (!is_mixed(st) || st->om64_current) {
+    CK(launch_convert(omega ? st->Om64 : st->W64, 0, ld, out, f32, ld_out, p, p, st->stream));
+  } else {
+    CK(launch_convert(omega ? st->Om : st->W, 1, ld, out, f32, ld_out, p, p, st->stream));
+    if (omega && !f32)
+      CK(cudaMemcpy2DAsync(out, (size_t)(ld_out + 1) * sizeof(double), st->omdiag64, sizeof(double),
+                           sizeof(double), p, cudaMemcpyDeviceToDevice, st->stream));
+  }
+  CK(cudaStreamSynchronize(st->stream));
+  return CONCORD_OK;
+}
+
+int concord_get_omega(concord_state* st, void* Om_dev, int dtype, int ld) {
+  return get_matrix(st, true, Om_dev, dtype, ld);
+}
+
+int concord_get_W(concord_state* st, void* W_dev, int dtype, int ld) {
+  return get_matrix(st, false, W_dev, dtype, ld);
+}
+
+int concord_get_history(concord_state* st, double* hist_host, int max_rows, int* rows) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  if (!rows) return fail(CONCORD_E_ARG, "rows is NULL");
+  int n = st->hist_rows < max_rows ? st->hist_rows : max_rows;
+  if (n > kHistCap) n = kHistCap;
+  if (n > 0 && hist_host)
+    CK(cudaMemcpy(hist_host, st->hist, sizeof(double) * kHist * (size_t)n, cudaMemcpyDeviceToHost));
+  *rows = st->hist_rows;
+  return CONCORD_OK;
+}
+
+int concord_get_timing(concord_state* st, double* launch_ms, int* launch_sweeps, int max_launches,
+                       int* n_launches) {
+  if (!st || !n_launches) return fail(CONCORD_E_ARG, "state and n_launches must be non-NULL");
+  const int n = st->n_launch < max_launches ? st->n_launch : max_launches;
+  for (int q = 0; q < n; ++q) {
+    if (launch_ms) launch_ms[q] = st->launch_ms[q];
+    if (launch_sweeps) launch_sweeps[q] = st->launch_sweeps[q];
+  }
+  *n_launches = st->n_launch;
+  return CONCORD_OK;
+}
+
+unsigned long long concord_kernel_launches(void) { return launches_so_far(); }
+
+int concord_sweep(concord_state* st, double lambda, int n_sweeps, concord_result* res) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  return run_impl(st, lambda, -1.0, n_sweeps, CONCORD_STOP_KKT, 0.0, 1, res);
+}
+
+int concord_run(concord_state* st, double lambda, double tol, int max_sweeps, int stop_rule,
+                double switch_tol, concord_result* res) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  return run_impl(st, lambda, tol, max_sweeps, stop_rule, switch_tol, 0, res);
+}
+
+int concord_set_gram_mode(concord_state* st, int mode) {
+  if (!st) return fail(CONCORD_E_ARG, "state is NULL");
+  if (mode != CONCORD_GRAM_FP64 && mode != CONCORD_GRAM_FP32 && mode != CONCORD_GRAM_TF32X3)
+    return fail(CONCORD_E_ARG, "unknown Gram mode %d", mode);
+  if (mode == CONCORD_GRAM_TF32X3 && !is_mixed(st))
+    return fail(CONCORD_E_ARG, "the tensor-core Gram feeds the mixed-precision state only");
+  st->gram_mode = mode;
+  return CONCORD_OK;
+}
+
+// X (device) -> S in the state, per the state's Gram mode.
+static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, int ldx, int prep) {
+  const int p = st->p, ld = st->ld;
+  CK(cudaMemsetAsync(st->flag, 0, sizeof(int), st->stream));
+  CK(launch_col_stats(X, x_f32, n, p, ldx, prep, st->mean, st->inv_scale, st->flag, st->stream));
+  switch (st->gram_mode) {
+    case CONCORD_GRAM_FP64:
+      if (is_mixed(st)) {
+        // FP64 Gram for a mixed state: Z in the FP32 workspace is too narrow,
+        // so stage Z in W64 (free until polishing) when it fits
+        if ((size_t)n * ld > (size_t)p * ld) return fail(CONCORD_E_ARG, "FP64 Gram for mixed state needs n <= p");
+        CK(launch_apply_prep(X, x_f32, n, p, ldx, st->mean, st->inv_scale, st->W64, 0, ld, st->stream));
+        CK(launch_syrk_f64(st->W64, n, p, ld, st->S64, ld, 1.0 / n, st->stream));
+        CK(launch_convert(st->S64, 0, ld, st->S, 1, ld, p, p, st->stream));
+      } else {
+        CK(launch_apply_prep(X, x_f32, n, p, ldx, st->mean, st->inv_scale, st->Z, 0, st->ldz,
+                             st->stream));
+        CK(launch_syrk_f64((const double*)st->Z, n, p, st->ldz, st->S64, ld, 1.0 / n, st->stream));
+      }
+      break;
+    case CONCORD_GRAM_FP32: {
+      float* Zf = (float*)st->Z;
+      if (!is_mixed(st)) return fail(CONCORD_E_ARG, "FP32 Gram feeds the mixed state only");
+      CK(launch_apply_prep(X, x_f32, n, p, ldx, st->mean, st->inv_scale, Zf, 1, st->ldz, st->stream));
+      CK(launch_syrk_f32(Zf, n, p, st->ldz, (float*)st->S, ld, 1.0f / n, st->stream));
+      CK(launch_convert(st->S, 1, ld, st->S64, 0, ld, p, p, st->stream));
+      break;
+    }
+    case CONCORD_GRAM_TF32X3: {
+      CK(launch_split_tf32(X, x_f32, n, p, ldx, st->mean, st->inv_scale, st->zt_hi, st->zt_lo,
+                           round_up(n, 32), st->p_pad, st->stream));
+      cudaError_t e = launch_gram_tf32x3(st->zt_hi, st->zt_lo, round_up(n, 32), st->p_pad, p,
+                                         (float*)st->S, ld, 1.0f / n, st->stream);
+      if (e == cudaErrorNotSupported) return fail(CONCORD_E_CUDA, "tensor-core Gram unavailable");
+      CK(e);
+      CK(launch_convert(st->S, 1, ld, st->S64, 0, ld, p, p, st->stream));
+      break;
+    }
+    default:
+      return fail(CONCORD_E_ARG, "unknown Gram mode");
+  }
+  int bad = 0, rc;
+  if ((rc = read_flag(st, &bad))) return rc;
+  if (bad & 2) return fail(CONCORD_E_NONFINITE, "X has a non-finite entry");
+  if (bad & 1) return fail(CONCORD_E_NONPOS_DIAG, "X has a constant column");
+  return reset_iterate(st);
+}
+
+int concord_gram(const void* X_dev, int x_dtype, int n, int p, int ldx, int prep, int mode,
+                 void* S_dev, int s_dtype, int lds, void* stream) {
+  if (!X_dev || !S_dev || n < 1 || p < 2 || ldx < p || lds < p)
+    return fail(CONCORD_E_ARG, "X/S non-NULL, n >= 1, p >= 2, ldx >= p, lds >= p required");
+  if ((x_dtype != CONCORD_F64 && x_dtype != CONCORD_F32) ||
+      (s_dtype != CONCORD_F64 && s_dtype != CONCORD_F32) || prep < 0 || prep > 2)
+    return fail(CONCORD_E_ARG, "bad dtype or prep");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int x_f32 = x_dtype == CONCORD_F32, s_f32 = s_dtype == CONCORD_F32;
+  const int ld = round_up(p, kTile);
+  double *mean = nullptr, *inv = nullptr;
+  int* bad = nullptr;
+  void* Z = nullptr;
+  void* Sw = nullptr;
+  float *hi = nullptr, *lo = nullptr;
+  int rc = CONCORD_OK, hbad = 0;
+  cudaError_t e = cudaSuccess;
+#define GK(expr)                                                                   \
+  do {                                                                             \
+    e = (expr);                                                                    \
+    if (e != cudaSuccess) {                                                        \
+      rc = fail(e == cudaErrorMemoryAllocation ? CONCORD_E_NOMEM : CONCORD_E_CUDA, \
+                "%s: %s", #expr, cudaGetErrorString(e));                           \
+      goto done;                                                                   \
+    }                                                                              \
+  } while (0)
+  GK(cudaMallocAsync((void**)&mean, sizeof(double) * p, s));
+  GK(cudaMallocAsync((void**)&inv, sizeof(double) * p, s));
+  GK(cudaMallocAsync((void**)&bad, sizeof(int), s));
+  GK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  GK(launch_col_stats(X_dev, x_f32, n, p, ldx, prep, mean, inv, bad, s));
+  if (mode == CONCORD_GRAM_FP64) {
+    GK(cudaMallocAsync(&Z, sizeof(double) * (size_t)n * ld, s));
+    GK(launch_apply_prep(X_dev, x_f32, n, p, ldx, mean, inv, Z, 0, ld, s));
+    if (s_f32) {
+      GK(cudaMallocAsync(&Sw, sizeof(double) * (size_t)p * ld, s));
+      GK(launch_syrk_f64((const double*)Z, n, p, ld, (double*)Sw, ld, 1.0 / n, s));
+      GK(launch_convert(Sw, 0, ld, S_dev, 1, lds, p, p, s));
+    } else {
+      GK(launch_syrk_f64((const double*)Z, n, p, ld, (double*)S_dev, lds, 1.0 / n, s));
+    }
+  } else if (mode == CONCORD_GRAM_FP32) {
+    GK(cudaMallocAsync(&Z, sizeof(float) * (size_t)n * ld, s));
+    GK(launch_apply_prep(X_dev, x_f32, n, p, ldx, mean, inv, Z, 1, ld, s));
+    if (s_f32) {
+      GK(launch_syrk_f32((const float*)Z, n, p, ld, (float*)S_dev, lds, 1.0f / n, s));
+    } else {
+      GK(cudaMallocAsync(&Sw, sizeof(float) * (size_t)p * ld, s));
+      GK(launch_syrk_f32((const float*)Z, n, p, ld, (float*)Sw, ld, 1.0f / n, s));
+      GK(launch_convert(Sw, 1, ld, S_dev, 0, lds, p, p, s));
+    }
+  } else if (mode == CONCORD_GRAM_TF32X3) {
+    const int n_pad = round_up(n, 32), p_pad = round_up(p, 128);
+    GK(cudaMallocAsync((void**)&hi, sizeof(float) * (size_t)n_pad * p_pad, s));
+    GK(cudaMallocAsync((void**)&lo, sizeof(float) * (size_t)n_pad * p_pad, s));
+    GK(launch_split_tf32(X_dev, x_f32, n, p, ldx, mean, inv, hi, lo, n_pad, p_pad, s));
+    if (s_f32) {
+      e = launch_gram_tf32x3(hi, lo, n_pad, p_pad, p, (float*)S_dev, lds, 1.0f / n, s);
+      if (e == cudaErrorNotSupported) {
+        rc = fail(CONCORD_E_CUDA, "tensor-core Gram unavailable on this device");
+        goto done;
+      }
+      GK(e);
+    } else {
+      GK(cudaMallocAsync(&Sw, sizeof(float) * (size_t)p * ld, s));
+      e = launch_gram_tf32x3(hi, lo, n_pad, p_pad, p, (float*)Sw, ld, 1.0f / n, s);
+      if (e == cudaErrorNotSupported) {
+        rc = fail(CONCORD_E_CUDA, "tensor-core Gram unavailable on this device");
+        goto done;
+      }
+      GK(e);
+      GK(launch_convert(Sw, 1, ld, S_dev, 0, lds, p, p, s));
+    }
+  } else {
+    rc = fail(CONCORD_E_ARG, "unknown Gram mode %d", mode);
+    goto done;
+  }
+  GK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GK(cudaStreamSynchronize(s));
+  if (hbad & 2) rc = fail(CONCORD_E_NONFINITE, "X has a non-finite entry");
+  else if (hbad & 1 && prep == CONCORD_PREP_STANDARDIZE)
+    rc = fail(CONCORD_E_NONPOS_DIAG, "X has a constant column");
+done:
+  if (mean) cudaFreeAsync(mean, s);
+  if (inv) cudaFreeAsync(inv, s);
+  if (bad) cudaFreeAsync(bad, s);
+  if (Z) cudaFreeAsync(Z, s);
+  if (Sw) cudaFreeAsync(Sw, s);
+  if (hi) cudaFreeAsync(hi, s);
+  if (lo) cudaFreeAsync(lo, s);
+#undef GK
+  return rc;
+}
+
+int concord_solve_device(concord_state* st, const void* X_dev, int x_dtype, int n, int ldx,
+                         int prep, double lambda, double tol, int max_sweeps, int stop_rule,
+                         void* Omega_dev, int omega_dtype, int ldo, concord_result* res) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  if (!X_dev || n < 1 || n > st->n_cap || ldx < st->p || prep < 0 || prep > 2 ||
+      (x_dtype != CONCORD_F64 && x_dtype != CONCORD_F32))
+    return fail(CONCORD_E_ARG, "X_dev non-NULL, 1 <= n <= n_cap (%d), ldx >= p, prep in 0..2",
+                st->n_cap);
+  cudaEvent_t e0;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventRecord(e0, st->stream));
+  rc = gram_into_state(st, X_dev, x_dtype == CONCORD_F32, n, ldx, prep);
+  if (rc == CONCORD_OK) {
+    concord_result r;
+    rc = run_impl(st, lambda, tol, max_sweeps, stop_rule, 0.0, 0, &r);
+    if ((rc == CONCORD_OK || rc == CONCORD_NOT_CONVERGED) && Omega_dev) {
+      int rc2 = get_matrix(st, true, Omega_dev, omega_dtype, ldo);
+      if (rc2 != CONCORD_OK) rc = rc2;
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, st->ev1);
+    r.seconds = ms * 1e-3;
+    if (res) *res = r;
+  }
+  cudaEventDestroy(e0);
+  return rc;
+}
+
+int concord_solve_host(concord_state* st, const double* X_host, int n, int prep, double lambda,
+                       double tol, int max_sweeps, int stop_rule, double* Omega_host,
+                       concord_result* res) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  if (!X_host || n < 1 || n > st->n_cap) return fail(CONCORD_E_ARG, "X_host non-NULL, 1 <= n <= n_cap");
+  const int p = st->p;
+  CK(cudaMemcpyAsync(st->Xstage, X_host, sizeof(double) * (size_t)n * p, cudaMemcpyHostToDevice,
+                     st->stream));
+  rc = concord_solve_device(st, st->Xstage, CONCORD_F64, n, p, prep, lambda, tol, max_sweeps,
+                            stop_rule, nullptr, CONCORD_F64, p, res);
+  if ((rc == CONCORD_OK || rc == CONCORD_NOT_CONVERGED) && Omega_host) {
+    const double* src = (!is_mixed(st) || st->om64_current) ? st->Om64 : nullptr;
+    if (!src) return fail(CONCORD_E_CUDA, "no FP64 iterate to copy out");
+    CK(cudaMemcpy2DAsync(Omega_host, sizeof(double) * p, src, sizeof(double) * st->ld,
+                         sizeof(double) * p, p, cudaMemcpyDeviceToHost, st->stream));
+    CK(cudaStreamSynchronize(st->stream));
+  }
+  return rc;
+}
+
+int concord_solve(const double* data_host, int is_X, int n, int p, int prep, double lambda,
+                  double tol, int max_sweeps, int precision, const double* Omega0_host,
+                  double* Omega_host, concord_result* res) {
+  if (!data_host || p < 2 || (is_X && n < 1)) return fail(CONCORD_E_ARG, "data non-NULL, p >= 2, n >= 1");
+  concord_state* st = nullptr;
+  int rc = concord_create(&st, p, precision, is_X ? n : 0, -1);
+  if (rc) return rc;
+  double* tmp = nullptr;
+  if (is_X) {
+    if (Omega0_host) {
+      concord_destroy(st);
+      return fail(CONCORD_E_ARG, "a warm start needs S input (is_X = 0)");
+    }
+    rc = concord_solve_host(st, data_host, n, prep, lambda, tol, max_sweeps, CONCORD_STOP_KKT,
+                            Omega_host, res);
+  } else {
+    if (cudaMalloc((void**)&tmp, sizeof(double) * (size_t)p * p) != cudaSuccess) {
+      concord_destroy(st);
+      return fail(CONCORD_E_NOMEM, "cudaMalloc for S");
+    }
+    rc = CONCORD_OK;
+    if (cudaMemcpy(tmp, data_host, sizeof(double) * (size_t)p * p, cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = fail(CONCORD_E_CUDA, "copy of S failed");
+    if (rc == CONCORD_OK) rc = concord_set_S(st, tmp, CONCORD_F64, p);
+    if (rc == CONCORD_OK && Omega0_host) {
+      if (cudaMemcpy(tmp, Omega0_host, sizeof(double) * (size_t)p * p, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = fail(CONCORD_E_CUDA, "copy of Omega0 failed");
+      if (rc == CONCORD_OK) rc = concord_set_omega(st, tmp, CONCORD_F64, p);
+    }
+    if (rc == CONCORD_OK) rc = concord_run(st, lambda, tol, max_sweeps, CONCORD_STOP_KKT, 0.0, res);
+    if ((rc == CONCORD_OK || rc == CONCORD_NOT_CONVERGED) && Omega_host) {
+      int rc2 = concord_get_omega(st, tmp, CONCORD_F64, p);
+      if (rc2 == CONCORD_OK &&
+          cudaMemcpy(Omega_host, tmp, sizeof(double) * (size_t)p * p, cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc2 = fail(CONCORD_E_CUDA, "copy of Omega failed");
+      if (rc2 != CONCORD_OK) rc = rc2;
+    }
+    cudaFree(tmp);
+  }
+  concord_destroy(st);
+  return rc;
+}
+
+int concord_lambda_max(concord_state* st, double* lambda_max) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  if (!lambda_max) return fail(CONCORD_E_ARG, "lambda_max is NULL");
+  CK(cudaMemsetAsync(st->lmax, 0, sizeof(unsigned long long), st->stream));
+  CK(launch_lambda_max(st->S64, st->p, st->ld, st->lmax, st->stream));
+  unsigned long long bits = 0;
+  CK(cudaMemcpyAsync(st->h_result, st->lmax, sizeof bits, cudaMemcpyDeviceToHost, st->stream));
+  CK(cudaStreamSynchronize(st->stream));
+  memcpy(&bits, st->h_result, sizeof bits);
+  memcpy(lambda_max, &bits, sizeof bits);
+  return CONCORD_OK;
+}
+
+}  // extern "C"

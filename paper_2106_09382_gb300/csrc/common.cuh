@@ -1,0 +1,175 @@
+// Device helpers shared by the CONCORD-PCD kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace concord {
+
+constexpr int kTile = 32;  // row-stride granularity (elements) and KKT tile edge
+
+// ---------------------------------------------------------------------------
+// Circle-method partner, closed form (Section 3.2, Algorithm 1).
+//
+// Algorithm 1 keeps vertex 1 fixed and, after every colour, rotates positions
+// 2..pe by one place; colour k pairs position q with position pe-q+1.  In
+// 0-based labels with P = pe - 1 colours: vertex v >= 1 sits at ring index
+// (v - 1 + c) mod P during colour c; ring index P-1 is the position facing
+// vertex 0; ring indices r and P-2-r face each other.  Solving for the vertex
+// at the facing index gives w = ((-v - 1 - 2c) mod P) + 1, which equals v
+// exactly when v faces vertex 0.  For odd p the extra vertex p (1-based p+1)
+// is a real ring member here; whoever faces it sits the colour out.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int cm_partner(int v, int c, int P) {
+  if (v == 0) return (P - 1 - c) % P + 1;
+  int w = (-v - 1 - 2 * c) % P;
+  if (w < 0) w += P;
+  w += 1;
+  return (w == v) ? 0 : w;
+}
+
+// ---------------------------------------------------------------------------
+// Bounded waits.  Every spin in this library ends: on success, when the
+// shared abort word becomes non-zero, or when %globaltimer passes the limit
+// (then it records the code and where it gave up, and returns false).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_volatile_s32(const int* p) {
+  int v;
+  asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_volatile_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.volatile.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void ld_volatile_v2u64(const unsigned long long* p,
+                                                  unsigned long long& a,
+                                                  unsigned long long& b) {
+  asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];"
+               : "=l"(a), "=l"(b)
+               : "l"(p)
+               : "memory");
+}
+
+__device__ __forceinline__ void st_volatile_v2u64(unsigned long long* p, unsigned long long a,
+                                                  unsigned long long b) {
+  asm volatile("st.volatile.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b)
+               : "memory");
+}
+
+// Abort codes written into the shared abort word.
+constexpr int kAbortTimeout = 1;
+
+struct WaitCtl {
+  int* abort;            // shared abort word (0 = running)
+  int* info;             // [0] vertex, [1] step of the first wait that ran out
+  uint64_t timeout_ns;   // per-wait limit
+};
+
+__device__ __forceinline__ void record_timeout(const WaitCtl& w, int vertex, int step) {
+  if (atomicCAS(w.abort, 0, kAbortTimeout) == 0) {
+    w.info[0] = vertex;
+    w.info[1] = step;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-vertex mailboxes (one scalar per vertex per colour step).
+//
+// Slot layout: depth D ring indexed by step mod D, then by vertex.  A 32-bit
+// value travels with its 32-bit step tag in one 64-bit word; a 64-bit value
+// travels as two words (tag|hi, tag|lo), each single-copy atomic, accepted
+// only when both tags match.  No other data crosses between the two owners
+// of a pair, so no release/acquire ordering is needed beyond the atomic word.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Mailbox;
+
+template <>
+struct Mailbox<float> {
+  static constexpr int kWords = 1;
+  __device__ static void publish(unsigned long long* slot, unsigned tag, float v) {
+    st_volatile_u64(slot, ((unsigned long long)tag << 32) | __float_as_uint(v));
+  }
+  __device__ static bool try_read(const unsigned long long* slot, unsigned tag, float& v) {
+    unsigned long long w = ld_volatile_u64(slot);
+    v = __uint_as_float((unsigned)(w & 0xffffffffull));
+    return (unsigned)(w >> 32) == tag;
+  }
+  __device__ static unsigned read_tag(const unsigned long long* slot) {
+    return (unsigned)(ld_volatile_u64(slot) >> 32);
+  }
+};
+
+template <>
+struct Mailbox<double> {
+  static constexpr int kWords = 2;
+  __device__ static void publish(unsigned long long* slot, unsigned tag, double v) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    unsigned long long t = (unsigned long long)tag << 32;
+    st_volatile_v2u64(slot, t | (b >> 32), t | (b & 0xffffffffull));
+  }
+  __device__ static bool try_read(const unsigned long long* slot, unsigned tag, double& v) {
+    unsigned long long hi, lo;
+    ld_volatile_v2u64(slot, hi, lo);
+    unsigned long long b = ((hi & 0xffffffffull) << 32) | (lo & 0xffffffffull);
+    v = __longlong_as_double((long long)b);
+    return (unsigned)(hi >> 32) == tag && (unsigned)(lo >> 32) == tag;
+  }
+  __device__ static unsigned read_tag(const unsigned long long* slot) {
+    return (unsigned)(ld_volatile_u64(slot) >> 32);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Grid barrier for a cooperative (co-resident) launch.  `gen` counts the
+// barriers this launch has passed; the counter is zeroed before the launch.
+// Returns with every CTA past the barrier or with the abort word set.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void grid_barrier(unsigned* counter, unsigned& gen,
+                                             const WaitCtl& w, int where) {
+  __syncthreads();
+  ++gen;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    red_release_add_u32(counter, 1u);
+    const unsigned target = gen * gridDim.x;
+    uint64_t t0 = globaltimer_ns();
+    unsigned it = 0;
+    while (ld_acquire_u32(counter) < target) {
+      if ((++it & 15u) == 0) {
+        if (ld_volatile_s32(w.abort) != 0) break;
+        if (globaltimer_ns() - t0 > w.timeout_ns) {
+          record_timeout(w, -1 - (int)blockIdx.x, where);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+}  // namespace concord

@@ -1,0 +1,105 @@
+// Kernel entry points and argument blocks shared by the host API (capi.cu)
+// and the kernel translation units.  Internal: not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace concord {
+
+// Counts every kernel this library launches (for launch accounting).
+void note_launches(unsigned n);
+unsigned long long launches_so_far();
+
+constexpr int kSweepThreads = 1024;  // upper bound on the sweep kernel's block size
+
+// Per-CTA partial results of the fused objective / KKT pass.
+constexpr int kPartKkt = 0, kPartQuad = 1, kPartPen = 2, kPartLog = 3, kPartDelta = 4,
+              kPartActive = 5, kPartBad = 6;
+constexpr int kParts = 8;
+
+// Final result block written by CTA 0.
+constexpr int kResSweeps = 0, kResKkt = 1, kResObj = 2, kResDelta = 3, kResActive = 4,
+              kResFirstDelta = 5, kResStatus = 6;
+constexpr int kRes = 8;
+constexpr int kHist = 4;  // per sweep: delta, kkt, objective, active pairs
+
+template <typename T>
+struct SweepArgs {
+  int p, P, ld, rows_per_warp;
+  T* W;                      // p x ld, W = Omega S
+  T* Om;                     // p x ld, Omega (symmetric)
+  const T* S;                // p x ld, S (padding columns zero)
+  const T* sdiag;            // s_ii in T
+  const double* sdiag64;     // s_ii in FP64
+  double* omdiag64;          // FP64 diagonal of Omega (mixed precision only)
+  unsigned long long* mbox;  // depth x (P+1) x words
+  int depth;
+  unsigned* barrier;         // zeroed before the launch
+  WaitCtl wait;
+  double* partials;          // gridDim.x x kParts
+  double* hist;              // hist_len x kHist
+  int hist_len;
+  double* result;            // kRes
+  double lambda, tol, delta_tol;
+  int stop_rule, n_sweeps, kkt_only;
+  unsigned tag_base;
+  int fault_vertex, fault_step;
+};
+
+cudaError_t launch_sweep(const SweepArgs<double>& a, int grid, int block, cudaStream_t st);
+cudaError_t launch_sweep(const SweepArgs<float>& a, int grid, int block, cudaStream_t st);
+cudaError_t sweep_occupancy(bool mixed, int block, int* blocks_per_sm);
+
+cudaError_t launch_refresh_w(const double* Om, const double* S, double* W, int p, int ld, int sms,
+                             cudaStream_t st);
+
+// ---- data preparation and Gram (prep_gram.cu)
+// Column statistics of X (n x p, row stride ldx): mean[i] and inv_scale[i]
+// per `prep` (0: mean 0, scale 1; 1: centre; 2: centre and 1/sd, population
+// variance).  bad (int) is set to 1 if a column is constant under prep 2 or
+// non-finite.
+cudaError_t launch_col_stats(const void* X, int x_f32, int n, int p, int ldx, int prep,
+                             double* mean, double* inv_scale, int* bad, cudaStream_t st);
+// Z = (X - mean) * inv_scale into Z (n x ldz, type z_f32 ? float : double);
+// columns p..ldz-1 are zero.
+cudaError_t launch_apply_prep(const void* X, int x_f32, int n, int p, int ldx, const double* mean,
+                              const double* inv_scale, void* Z, int z_f32, int ldz,
+                              cudaStream_t st);
+// S = Z^T Z * scale on CUDA cores (upper-triangle tiles, mirrored).
+cudaError_t launch_syrk_f64(const double* Z, int n, int p, int ldz, double* S, int lds, double scale,
+                            cudaStream_t st);
+cudaError_t launch_syrk_f32(const float* Z, int n, int p, int ldz, float* S, int lds, float scale,
+                            cudaStream_t st);
+
+// ---- small utilities (util.cu)
+// out[r*ldo + c] = (To) in[r*ldi + c] for r < rows, c < cols; zero for cols <= c < ldo.
+cudaError_t launch_convert(const void* in, int in_f32, int ldi, void* out, int out_f32, int ldo,
+                           int rows, int cols, cudaStream_t st);
+// d64[i] = A[i*lda+i]; dT[i] (type t_f32) likewise; bad |= 1 if not > 0, 2 if non-finite.
+cudaError_t launch_extract_diag(const void* A, int a_f32, int lda, int p, double* d64, void* dT,
+                                int t_f32, int* bad, cudaStream_t st);
+// a[0..n) = v.
+cudaError_t launch_fill_f64(double* a, double v, int n, cudaStream_t st);
+// A (p x ld, type) = identity with zero padding.
+cudaError_t launch_set_identity(void* A, int a_f32, int p, int ld, cudaStream_t st);
+// bad |= 1 if |A - A^T| != 0 anywhere or a non-finite entry is met.
+cudaError_t launch_check_symmetric(const void* A, int a_f32, int p, int lda, int* bad,
+                                   cudaStream_t st);
+// out (FP64 bits as u64, must start at 0) = max_{i<j} |s_ij| (s_ii^-1/2 + s_jj^-1/2).
+cudaError_t launch_lambda_max(const double* S, int p, int ld, unsigned long long* out,
+                              cudaStream_t st);
+
+// ---- tensor-core Gram (gram_tc.cu)
+// Splits each standardized element into tf32 hi + lo and writes them
+// transposed: Zt_hi / Zt_lo are p_pad x n_pad (K-major), zero padded.
+cudaError_t launch_split_tf32(const void* X, int x_f32, int n, int p, int ldx, const double* mean,
+                              const double* inv_scale, float* zt_hi, float* zt_lo, int n_pad,
+                              int p_pad, cudaStream_t st);
+// S (p x lds, FP32) = (hi hi^T + hi lo^T + lo hi^T) * scale with tcgen05.mma
+// kind::tf32.  Returns cudaErrorNotSupported if the device is not sm_103.
+cudaError_t launch_gram_tf32x3(const float* zt_hi, const float* zt_lo, int n_pad, int p_pad, int p,
+                               float* S, int lds, float scale, cudaStream_t st);
+
+}  // namespace concord

@@ -1,0 +1,147 @@
+// Small elementwise / reduction kernels used around the sweep.
+#include <atomic>
+
+#include "kernels.h"
+
+namespace concord {
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+template <typename TI, typename TO>
+__global__ void k_convert(const TI* __restrict__ in, int ldi, TO* __restrict__ out, int ldo, int rows,
+                          int cols) {
+  const size_t total = (size_t)rows * ldo;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ldo), c = (int)(e % ldo);
+    out[e] = (c < cols) ? (TO)in[(size_t)r * ldi + c] : (TO)0;
+  }
+}
+
+cudaError_t launch_convert(const void* in, int in_f32, int ldi, void* out, int out_f32, int ldo,
+                           int rows, int cols, cudaStream_t st) {
+  const int grid = 152 * 8, block = 256;
+  if (in_f32 && out_f32)
+    k_convert<float, float><<<grid, block, 0, st>>>((const float*)in, ldi, (float*)out, ldo, rows,
+                                                    cols);
+  else if (in_f32)
+    k_convert<float, double><<<grid, block, 0, st>>>((const float*)in, ldi, (double*)out, ldo, rows,
+                                                     cols);
+  else if (out_f32)
+    k_convert<double, float><<<grid, block, 0, st>>>((const double*)in, ldi, (float*)out, ldo, rows,
+                                                     cols);
+  else
+    k_convert<double, double><<<grid, block, 0, st>>>((const double*)in, ldi, (double*)out, ldo,
+                                                      rows, cols);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename TA>
+__global__ void k_extract_diag(const TA* __restrict__ A, int lda, int p, double* d64, float* d32,
+                               double* dT64, int* bad) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p; i += gridDim.x * blockDim.x) {
+    const double v = (double)A[(size_t)i * lda + i];
+    if (!isfinite(v))
+      atomicOr(bad, 2);
+    else if (!(v > 0.0))
+      atomicOr(bad, 1);
+    if (d64) d64[i] = v;
+    if (d32) d32[i] = (float)v;
+    if (dT64) dT64[i] = v;
+  }
+}
+
+cudaError_t launch_extract_diag(const void* A, int a_f32, int lda, int p, double* d64, void* dT,
+                                int t_f32, int* bad, cudaStream_t st) {
+  const int grid = (p + 255) / 256;
+  float* d32 = t_f32 ? (float*)dT : nullptr;
+  double* dT64 = t_f32 ? nullptr : (double*)dT;
+  if (a_f32)
+    k_extract_diag<float><<<grid, 256, 0, st>>>((const float*)A, lda, p, d64, d32, dT64, bad);
+  else
+    k_extract_diag<double><<<grid, 256, 0, st>>>((const double*)A, lda, p, d64, d32, dT64, bad);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void k_fill_f64(double* a, double v, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
+}
+
+cudaError_t launch_fill_f64(double* a, double v, int n, cudaStream_t st) {
+  k_fill_f64<<<(n + 255) / 256, 256, 0, st>>>(a, v, n);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_set_identity(T* A, int p, int ld) {
+  const size_t total = (size_t)p * ld;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ld), c = (int)(e % ld);
+    A[e] = (r == c) ? (T)1 : (T)0;
+  }
+}
+
+cudaError_t launch_set_identity(void* A, int a_f32, int p, int ld, cudaStream_t st) {
+  if (a_f32)
+    k_set_identity<float><<<152 * 8, 256, 0, st>>>((float*)A, p, ld);
+  else
+    k_set_identity<double><<<152 * 8, 256, 0, st>>>((double*)A, p, ld);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_check_symmetric(const T* __restrict__ A, int p, int lda, int* bad) {
+  const size_t total = (size_t)p * p;
+  int flag = 0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / p), c = (int)(e % p);
+    const T v = A[(size_t)r * lda + c];
+    if (!isfinite((double)v)) flag |= 2;
+    if (r < c && v != A[(size_t)c * lda + r]) flag |= 1;
+  }
+  if (flag) atomicOr(bad, flag);
+}
+
+cudaError_t launch_check_symmetric(const void* A, int a_f32, int p, int lda, int* bad,
+                                   cudaStream_t st) {
+  if (a_f32)
+    k_check_symmetric<float><<<152 * 8, 256, 0, st>>>((const float*)A, p, lda, bad);
+  else
+    k_check_symmetric<double><<<152 * 8, 256, 0, st>>>((const double*)A, p, lda, bad);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void k_lambda_max(const double* __restrict__ S, int p, int ld, unsigned long long* out) {
+  double m = 0.0;
+  const size_t total = (size_t)p * p;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / p), j = (int)(e % p);
+    if (i < j) {
+      const double v = fabs(S[(size_t)i * ld + j]) *
+                       (1.0 / sqrt(S[(size_t)i * ld + i]) + 1.0 / sqrt(S[(size_t)j * ld + j]));
+      m = fmax(m, v);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  // non-negative doubles order like their bit patterns
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+cudaError_t launch_lambda_max(const double* S, int p, int ld, unsigned long long* out,
+                              cudaStream_t st) {
+  k_lambda_max<<<152 * 4, 256, 0, st>>>(S, p, ld, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace concord

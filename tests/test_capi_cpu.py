@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads and exports every symbol include/concord.h
+declares; host-only entry points behave as specified (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2106_09382_gb300 import concord as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "concord.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(concord_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_builds_and_loads():
+    lib = C.load()
+    assert lib.concord_version().startswith(b"concord-gb300")
+    assert lib.concord_result_size() == ctypes.sizeof(C.ConcordResult)
+
+
+def test_every_declared_symbol_is_exported_and_bound():
+    lib = C.load()
+    syms = _declared_symbols()
+    assert len(syms) >= 20
+    for s in syms:
+        assert hasattr(lib, s), s
+        assert s in C.SIGNATURES, "binding lacks %s" % s
+
+
+@pytest.mark.parametrize("p", list(range(2, 30)) + [99, 100, 333, 517, 1000, 4999, 5000])
+def test_schedule_matches_oracle_bit_exact(p):
+    """The library's closed-form colouring equals Algorithm 1's rotation
+    (oracle), slot by slot and in order within each pair."""
+    assert np.array_equal(C.concord_schedule(p), O.schedule(p))
+
+
+def test_schedule_argument_errors():
+    lib = C.load()
+    buf = (ctypes.c_int32 * 8)()
+    nc = ctypes.c_int(0)
+    assert lib.concord_schedule(1, buf, ctypes.byref(nc)) == C.E_ARG
+    assert lib.concord_schedule(4, None, ctypes.byref(nc)) == C.E_ARG
+    assert "p >= 2" in C.last_error()
+
+
+def test_host_side_argument_errors():
+    lib = C.load()
+    assert lib.concord_set_timeout(None, 1.0) == C.E_ARG
+    assert lib.concord_sweep(None, 0.1, 1, None) == C.E_ARG
+    assert lib.concord_destroy(None) == C.OK
+    st = ctypes.c_void_p()
+    assert lib.concord_create(ctypes.byref(st), 1, C.FP64, 0, -1) == C.E_ARG
+    assert lib.concord_create(ctypes.byref(st), 10, 7, 0, -1) == C.E_ARG
+    assert lib.concord_gram(None, 0, 10, 10, 10, 2, 0, None, 0, 10, None) == C.E_ARG
+
+
+def test_no_gpu_means_error_not_fallback():
+    """Without a device the library reports CONCORD_E_CUDA; it never computes
+    on the CPU."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    lib = C.load()
+    st = ctypes.c_void_p()
+    assert lib.concord_create(ctypes.byref(st), 10, C.FP64, 0, -1) == C.E_CUDA
+    data = np.eye(4)
+    r = C.ConcordResult()
+    out = np.zeros((4, 4))
+    rc = lib.concord_solve(data.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0, 0, 4, 2, 0.1,
+                           1e-5, 10, C.FP64, None, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           ctypes.byref(r))
+    assert rc == C.E_CUDA
+    assert np.all(out == 0)

@@ -1,0 +1,409 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle on the same
+seeded inputs.
+
+Tolerances (derivations in the design doc):
+  * FP64 Gram: |dS| <= 1e-13 (both sum n products in FP64, different order).
+  * FP32 Gram: |dS| <= (n + 4) 2^-24 (|s_ij| <= 1 for standardized data).
+  * FP64 sweeps vs oracle, sweep by sweep: max|dOmega| <= 1e-10 max|Omega|
+    (the GPU forms Eq. 3 from a maintained W = Omega S, the oracle from the
+    direct sums: rounding order only).
+  * FP64 converged solve: max|dOmega| <= 1e-6 max|Omega| (relative),
+    objective relative error <= 1e-7, identical support away from the
+    threshold (|G_ij| not within 1e-6 of lambda).
+  * Mixed precision (FP32 sweeps, FP64 polish on the same S): the polished
+    result carries the tolerance of the FP64 solve; FP32 sweeps alone are
+    compared at 1e-4 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2106_09382_gb300 import concord as C
+from paper_2106_09382_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def dev(a, dtype=None):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype or torch.float64, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel_err(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def data(n, p, seed, mix=0.5):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, p))
+    for j in range(1, p):
+        X[:, j] += mix * X[:, j - 1]
+    return X * rng.uniform(0.5, 2.0, p) + rng.uniform(-1, 1, p)
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = synth.workload_small()
+    Z = O.standardize(w["X"])
+    return w, Z, O.gram(Z)
+
+
+# --------------------------------------------------------------------- Gram
+@pytest.mark.parametrize("n,p", [(200, 100), (61, 333), (37, 517), (5, 2)])
+def test_gram_fp64(n, p):
+    X = data(n, p, n + p)
+    S = host(C.concord_gram(dev(X), C.PREP_STANDARDIZE, C.GRAM_FP64))
+    S_or = O.gram(O.standardize(X))
+    assert np.abs(S - S_or).max() <= 1e-13
+    assert np.array_equal(S, S.T)
+
+
+@pytest.mark.parametrize("n,p", [(200, 100), (61, 333)])
+def test_gram_fp32(n, p):
+    X = data(n, p, 7 * n + p)
+    S = host(C.concord_gram(dev(X), C.PREP_STANDARDIZE, C.GRAM_FP32))
+    S_or = O.gram(O.standardize(X))
+    assert np.abs(S - S_or).max() <= (n + 4) * 2.0 ** -24
+    assert np.array_equal(S, S.T)
+
+
+def test_gram_centre_and_none():
+    X = data(40, 50, 3)
+    S1 = host(C.concord_gram(dev(X), C.PREP_CENTER, C.GRAM_FP64))
+    assert np.abs(S1 - O.gram(O.standardize(X, scale=False))).max() <= 1e-12
+    S0 = host(C.concord_gram(dev(X), C.PREP_NONE, C.GRAM_FP64))
+    assert np.abs(S0 - X.T @ X / 40).max() <= 1e-12
+
+
+def test_gram_constant_column_is_an_error():
+    X = data(30, 20, 5)
+    X[:, 4] = 1.25
+    with pytest.raises(C.ConcordError) as e:
+        C.concord_gram(dev(X), C.PREP_STANDARDIZE, C.GRAM_FP64)
+    assert e.value.code == C.E_NONPOS_DIAG
+
+
+# -------------------------------------------------------- sweep-by-sweep parity
+@pytest.mark.parametrize("p,lam,n", [(100, 0.3, 200), (333, 0.15, 400), (517, 0.1, 300),
+                                     (2, 0.1, 20), (3, 0.05, 20), (31, 0.02, 60)])
+def test_sweeps_match_oracle_fp64(p, lam, n):
+    S = O.gram(O.standardize(data(n, p, p)))
+    with C.State(p, C.FP64) as st:
+        st.set_S(dev(S))
+        Om = np.eye(p)
+        pairs = O.schedule(p)
+        for t in range(3):
+            r = st.sweep(lam, 1)
+            d_or, nnz_or = O.sweep(S, Om, lam, pairs)
+            G = host(st.get_omega())
+            assert rel_err(G, Om) <= 1e-10, (t, rel_err(G, Om))
+            assert np.array_equal(G, G.T)
+            W = host(st.get_W())
+            assert np.abs(W - G @ S).max() <= 1e-11 * max(1.0, np.abs(W).max())
+            assert abs(r.objective - O.objective(S, Om, lam)) <= 1e-10 * abs(r.objective)
+            assert abs(r.kkt - O.kkt(S, Om, lam)) <= 1e-9
+            assert abs(r.delta - d_or) <= 1e-10
+            assert r.active_pairs == nnz_or
+
+
+def test_history_is_monotone(small):
+    w, Z, S = small
+    with C.State(100, C.FP64) as st:
+        st.set_S(dev(S))
+        st.run(w["lam"], tol=1e-9, max_sweeps=200)
+        h = st.history()
+        obj = h[:, 2]
+        assert len(obj) == st.last.sweeps
+        assert np.all(np.diff(obj) <= 1e-12 * abs(obj[0]))
+
+
+# -------------------------------------------------------------- converged solve
+def _support_check(G_om, O_om, S, lam):
+    W = O_om @ S
+    Gm = W + W.T
+    near = np.abs(np.abs(Gm) - lam) <= 1e-6
+    off = ~np.eye(S.shape[0], dtype=bool)
+    mism = ((G_om != 0) != (O_om != 0)) & off & ~near
+    assert not mism.any(), "support differs away from the threshold"
+
+
+@pytest.mark.parametrize("precision", [C.FP64, C.MIXED])
+def test_solve_small_workload(small, precision):
+    w, Z, S = small
+    lam, tol = w["lam"], w["tol"]
+    Om_or, info = O.solve(S, lam, tol=tol, max_sweeps=500)
+    with C.State(100, precision) as st:
+        st.set_S(dev(S))
+        r = st.run(lam, tol=tol, max_sweeps=500)
+        G = host(st.get_omega())
+    assert r.status == C.OK and r.kkt <= tol
+    assert rel_err(G, Om_or) <= 1e-6
+    assert abs(r.objective - info["objective"]) <= 1e-7 * abs(info["objective"])
+    assert O.kkt(S, G, lam) <= tol * 1.01
+    _support_check(G, Om_or, S, lam)
+    if precision == C.FP64:
+        assert r.sweeps == info["sweeps"]
+
+
+@pytest.mark.parametrize("p,n,lam", [(333, 400, 0.15), (517, 300, 0.12)])
+def test_solve_ragged_sizes(p, n, lam):
+    S = O.gram(O.standardize(data(n, p, 11 * p)))
+    Om_or, info = O.solve(S, lam, tol=1e-6, max_sweeps=300)
+    for prec in (C.FP64, C.MIXED):
+        with C.State(p, prec) as st:
+            st.set_S(dev(S))
+            r = st.run(lam, tol=1e-6, max_sweeps=300)
+            G = host(st.get_omega())
+        assert r.status == C.OK
+        assert rel_err(G, Om_or) <= 1e-6, (prec, rel_err(G, Om_or))
+        assert abs(r.objective - info["objective"]) <= 1e-7 * abs(info["objective"])
+        _support_check(G, Om_or, S, lam)
+
+
+def test_fp32_sweeps_track_oracle():
+    p, n, lam = 200, 300, 0.1
+    S = O.gram(O.standardize(data(n, p, 99)))
+    with C.State(p, C.MIXED) as st:
+        st.set_S(dev(S))
+        Om = np.eye(p)
+        for t in range(3):
+            st.sweep(lam, 1)
+            O.sweep(S, Om, lam)
+            G = host(st.get_omega())
+            assert rel_err(G, Om) <= 1e-4, rel_err(G, Om)
+
+
+# ------------------------------------------------------------- special cases
+@pytest.mark.parametrize("r,lam", [(0.6, 0.3), (-0.8, 0.1), (0.2, 0.5)])
+@pytest.mark.parametrize("precision", [C.FP64, C.MIXED])
+def test_p2_closed_form_on_gpu(r, lam, precision):
+    S = np.array([[1.0, r], [r, 1.0]])
+    k = 1 - r * r
+    b = lam * abs(r) / 2
+    if abs(r) <= lam / 2:
+        a, c = 1.0, 0.0
+    else:
+        a = (-b + np.sqrt(b * b + 4 * k)) / (2 * k)
+        c = -r * a + lam / 2 * np.sign(r)
+    with C.State(2, precision) as st:
+        st.set_S(dev(S))
+        res = st.run(lam, tol=1e-12, max_sweeps=20000)
+        G = host(st.get_omega())
+    assert res.status == C.OK
+    assert abs(G[0, 0] - a) < 1e-10 and abs(G[0, 1] - c) < 1e-10
+
+
+@pytest.mark.parametrize("p", [3, 5, 8])
+def test_diagonal_S_and_lambda_max(p):
+    d = np.linspace(0.5, 3.0, p)
+    with C.State(p, C.FP64) as st:
+        st.set_S(dev(np.diag(d)))
+        st.run(0.1, tol=1e-14, max_sweeps=5)
+        assert np.allclose(host(st.get_omega()), np.diag(d ** -0.5), atol=1e-15)
+    S = O.gram(O.standardize(data(5 * p, p, p)))
+    with C.State(p, C.FP64) as st:
+        st.set_S(dev(S))
+        lm = st.lambda_max()
+        assert abs(lm - O.lambda_max(S)) <= 1e-14 * lm
+        st.run(lm * 1.000001, tol=1e-13, max_sweeps=100)
+        G = host(st.get_omega())
+        assert np.count_nonzero(G - np.diag(np.diag(G))) == 0
+
+
+def test_lambda_zero_reaches_kkt():
+    p = 40
+    S = O.gram(O.standardize(data(200, p, 1)))
+    Om_or, info = O.solve(S, 0.0, tol=1e-8, max_sweeps=5000)
+    with C.State(p, C.FP64) as st:
+        st.set_S(dev(S))
+        r = st.run(0.0, tol=1e-8, max_sweeps=5000)
+        assert r.status == C.OK
+        assert rel_err(host(st.get_omega()), Om_or) <= 1e-6
+
+
+def test_paper_stopping_rule():
+    w = synth.workload_small()
+    S = O.gram(O.standardize(w["X"]))
+    _, info = O.solve(S, w["lam"], tol=1e-12, max_sweeps=500)
+    with C.State(100, C.FP64) as st:
+        st.set_S(dev(S))
+        r = st.run(w["lam"], tol=1e-5, max_sweeps=500, stop_rule=C.STOP_DELTA)
+        assert r.status == C.OK and r.delta < 1e-5
+        assert r.sweeps == info["first_delta_sweep"]
+
+
+# ---------------------------------------------------------------- data paths
+@pytest.mark.parametrize("precision", [C.FP64, C.MIXED])
+def test_solve_device_and_host_from_X(small, precision):
+    w, Z, S = small
+    lam, tol = w["lam"], w["tol"]
+    Om_or, info = O.solve(S, lam, tol=tol, max_sweeps=500)
+    X = w["X"]
+    gtol = 1e-6 if precision == C.FP64 else 5e-5
+    with C.State(100, precision, n_cap=X.shape[0]) as st:
+        out = torch.empty((100, 100), dtype=torch.float64, device="cuda")
+        r = st.solve_device(dev(X), lam, tol=tol, max_sweeps=500, Omega_out=out)
+        assert r.status == C.OK and r.kkt <= tol
+        assert rel_err(host(out), Om_or) <= gtol
+        Oh = np.empty((100, 100))
+        r2 = st.solve_host(np.ascontiguousarray(X), lam, tol=tol, max_sweeps=500, Omega_out=Oh)
+        assert r2.status == C.OK
+        assert np.array_equal(Oh, host(out))
+
+
+def test_one_shot_solve(small):
+    w, Z, S = small
+    Om_or, info = O.solve(S, w["lam"], tol=1e-6, max_sweeps=500)
+    G, r = C.concord_solve(S, w["lam"], tol=1e-6, is_X=False)
+    assert r.status == C.OK and rel_err(G, Om_or) <= 1e-6
+    G2, r2 = C.concord_solve(S, w["lam"], tol=1e-6, is_X=False, Omega0=Om_or)
+    assert r2.sweeps <= 1
+
+
+def test_warm_start(small):
+    w, Z, S = small
+    Om_or, info = O.solve(S, w["lam"], tol=1e-10, max_sweeps=500)
+    for prec in (C.FP64, C.MIXED):
+        with C.State(100, prec) as st:
+            st.set_S(dev(S))
+            st.set_omega(dev(Om_or))
+            W = host(st.get_W())
+            assert np.abs(W - Om_or @ S).max() <= (1e-12 if prec == C.FP64 else 1e-6)
+            r = st.run(w["lam"], tol=1e-8, max_sweeps=50)
+            assert r.sweeps <= 2
+
+
+# --------------------------------------------------------------- errors, faults
+def test_state_argument_errors():
+    with C.State(6, C.FP64) as st:
+        A = np.eye(6)
+        A[0, 1] = 0.3
+        with pytest.raises(C.ConcordError) as e:
+            st.set_S(dev(A))
+        assert e.value.code == C.E_ARG
+        B = np.eye(6)
+        B[2, 2] = 0.0
+        with pytest.raises(C.ConcordError) as e:
+            st.set_S(dev(B))
+        assert e.value.code == C.E_NONPOS_DIAG
+        N = np.eye(6)
+        N[3, 3] = np.nan
+        with pytest.raises(C.ConcordError) as e:
+            st.set_S(dev(N))
+        assert e.value.code == C.E_NONFINITE
+        with pytest.raises(C.ConcordError):
+            st.run(-1.0)
+
+
+@pytest.mark.parametrize("precision", [C.FP64, C.MIXED])
+def test_wait_timeout_is_reported_and_context_survives(small, precision):
+    """A vertex that never publishes makes its partner's bounded wait run
+    out: the kernel returns CONCORD_E_TIMEOUT and the device stays usable."""
+    w, Z, S = small
+    with C.State(100, precision) as st:
+        st.set_S(dev(S))
+        st.set_timeout(0.25)
+        st.set_fault(17, 3)
+        with pytest.raises(C.ConcordError) as e:
+            st.sweep(w["lam"], 1)
+        assert e.value.code == C.E_TIMEOUT
+        assert st.last.timeout_step >= 3
+        # the context and the state still work
+        st.set_S(dev(S))
+        r = st.run(w["lam"], tol=1e-6, max_sweeps=500)
+        assert r.status == C.OK
+    torch.cuda.synchronize()
+
+
+# --------------------------------------------------- full size, sampled outputs
+def _colour_matrix(p):
+    pairs = O.schedule(p)
+    col = np.full((p, p), -1, dtype=np.int32)
+    for k in range(pairs.shape[0]):
+        ok = pairs[k, :, 0] >= 0
+        a, b = pairs[k, ok, 0], pairs[k, ok, 1]
+        col[a, b] = k
+        col[b, a] = k
+    return col
+
+
+@pytest.mark.parametrize("p", [5000, 4999])
+@pytest.mark.parametrize("precision", [C.FP64, C.MIXED])
+def test_full_size_sampled_parity(p, precision):
+    """At the benchmark size the oracle recomputes sampled outputs one by one:
+    each sampled off-diagonal entry of sweep t+1 from the state the colour
+    order implies (entries of earlier colours from Omega^(t+1), later ones
+    from Omega^(t)), each diagonal from the final off-diagonals (Eq. 2)."""
+    w = synth.workload_ar1(p=p, n=2000, seed=0)
+    X, lam = w["X"], w["lam"]
+    Z = O.standardize(X)
+    rng = np.random.default_rng(p)
+    rows = np.sort(rng.choice(p, 48, replace=False))
+    with C.State(p, precision, n_cap=X.shape[0]) as st:
+        r = st.solve_device(dev(X), lam, tol=1e-5, max_sweeps=3)
+        O3 = host(st.get_omega())
+        st.sweep(lam, 1)
+        O4 = host(st.get_omega())
+        Sg = host(C.concord_gram(dev(X), C.PREP_STANDARDIZE, C.GRAM_FP64))
+    S_rows = O.gram_rows(Z, rows)
+    assert np.abs(S_rows - Sg[rows]).max() <= 1e-12
+    col = _colour_matrix(p)
+    tol = 1e-9 if precision == C.FP64 else 2e-5
+    checked = 0
+    for a, i in enumerate(rows):
+        js = rng.choice(np.delete(np.arange(p), i), 6, replace=False)
+        nz = np.flatnonzero(O4[i])
+        js = np.unique(np.concatenate([js, nz[nz != i][:6]]))
+        for j in js:
+            k = col[i, j]
+            # state before colour k: rows i and column j
+            ri = np.where(col[i] < k, O4[i], O3[i])
+            ri[i] = O3[i, i]
+            cj = np.where(col[:, j] < k, O4[:, j], O3[:, j])
+            cj[j] = O3[j, j]
+            s_j = O.gram_rows(Z, [j])[0]
+            want = O.eq3(ri, cj, S_rows[a], s_j, i, j, lam)
+            assert abs(O4[i, j] - want) <= tol * max(1.0, abs(want)), (i, j, O4[i, j], want)
+            checked += 1
+        d_want = O.eq2(O4[i], S_rows[a], i)
+        assert abs(O4[i, i] - d_want) <= tol * d_want
+    assert checked >= 48 * 6
+    assert np.array_equal(O4, O4.T)
+    assert np.all(np.diag(O4) > 0)
+
+
+@pytest.mark.parametrize("precision", [C.FP64, C.MIXED])
+def test_full_size_converges(precision):
+    w = synth.workload_ar1(p=5000, n=2000, seed=0)
+    with C.State(5000, precision, n_cap=2000) as st:
+        r = st.solve_device(dev(w["X"]), w["lam"], tol=1e-5, max_sweeps=200)
+        assert r.status == C.OK and r.kkt <= 1e-5
+        G = host(st.get_omega())
+    assert np.array_equal(G, G.T)
+    # sampled KKT rows by the oracle's definition: G_ij = W_ij + W_ji
+    Z = O.standardize(w["X"])
+    rows = np.arange(0, 5000, 617)
+    S_rows = O.gram_rows(Z, rows)
+    for a, i in enumerate(rows):
+        # row i of W = sum_u w_iu S_u; column i of W = row i of S Omega
+        supp = np.flatnonzero(G[i])
+        Su = O.gram_rows(Z, supp)
+        W_row = G[i, supp] @ Su
+        W_col = S_rows[a] @ G
+        g = W_row + W_col
+        off = np.arange(5000) != i
+        on = (G[i] != 0) & off
+        zero = (G[i] == 0) & off
+        res = np.concatenate([np.abs(g[on] + lam_sign(G[i, on], w["lam"])),
+                              np.maximum(np.abs(g[zero]) - w["lam"], 0.0),
+                              [abs(W_row[i] - 1.0 / G[i, i])]])
+        assert res.max() <= 1e-5 * 1.05, (i, res.max())
+
+
+def lam_sign(v, lam):
+    return lam * np.sign(v)
