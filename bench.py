@@ -111,16 +111,20 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- roofline
+PEND_CAP = 8  # pending row updates a row collects before it is flushed (kPendCap)
+
+
 def sweep_bytes(p: int, b: int, active_pairs: float) -> float:
-    """Algorithmic bytes of one sweep (maintained-W design), b = element bytes:
-    5 scalar reads per pair evaluation (w_ij, W_ij, W_ji, s_ii, s_jj),
-    2 S rows read + 2 W rows read and written per changed pair,
-    1 S row read + 1 W row read and written per diagonal update,
-    W and Omega read once by the objective / KKT pass."""
+    """Algorithmic bytes of one sweep of this design, b = element bytes:
+    5 scalar reads per pair evaluation and side-independent (w_ij, W_ij, W_ji,
+    s_ii, s_jj); for each changed pair, on each side one S row read when the
+    pending list is flushed and the W row read and written once per PEND_CAP
+    changes; one S row read and one W row read and written per diagonal
+    update; W and Omega read once by the objective / KKT pass."""
     pe = p + (p % 2)
     pairs = (pe - 1) * (pe // 2) - (p % 2) * (pe - 1)
-    return (pairs * 5 * b + active_pairs * p * (2 * b + 4 * b) + p * p * (b + 2 * b)
-            + p * p * 2 * b)
+    per_change = 2 * (p * b + 2 * p * b / PEND_CAP)
+    return (pairs * 5 * b + active_pairs * per_change + p * p * 3 * b + p * p * 2 * b)
 
 
 def launch_bytes(p: int, b: int, hist_rows) -> float:
@@ -255,9 +259,31 @@ def run_ours(args):
             recs.append((r.as_dict(), state.timing(), state.history()))
         return times, recs
 
+    def autotune(state):
+        """Pick the sweep kernel's rows-per-warp layout (results do not depend
+        on it) by the measured sweep-kernel time per sweep on warm-up solves."""
+        trial = {}
+        for var, name in ((C.SWEEP_CLUSTER, "cluster"), (C.SWEEP_GRID, "grid")):
+            for rows in (32, 16, 8, 4):
+                try:
+                    state.set_sweep_variant(var)
+                    state.set_rows_per_warp(rows)
+                    state.solve_device(X, lam, tol=tol, max_sweeps=args.max_sweeps)
+                except C.ConcordError:
+                    continue
+                tim = state.timing()
+                trial["%s/%d" % (name, rows)] = (sum(ms for ms, _ in tim)
+                                                 / max(1, sum(sw for _, sw in tim)))
+        best = min(trial, key=trial.get)
+        name, rows = best.split("/")
+        state.set_sweep_variant(C.SWEEP_CLUSTER if name == "cluster" else C.SWEEP_GRID)
+        state.set_rows_per_warp(int(rows))
+        return best, trial
+
     # ---------------- headline: mixed precision, data resident in HBM
     st = C.State(p, C.MIXED, n_cap=n, device=local)
     st.set_stream(stream)
+    rows_best, rows_trial = autotune(st)
     for _ in range(args.warmup):
         st.solve_device(X, lam, tol=tol, max_sweeps=args.max_sweeps)
     clocks = ClockSampler(local)
@@ -305,6 +331,7 @@ def run_ours(args):
                      "objective": r_last["objective"], "launch_ms": tim_last,
                      "step_seconds": times},
            "updates_per_s": ups,
+           "autotune": {"choice": rows_best, "ms_per_sweep": rows_trial},
            "roofline": roofline,
            "gpu_launches": launches,
            "clocks": clk}
@@ -313,13 +340,14 @@ def run_ours(args):
         # ---------------- plain FP64 GPU PCD, same data
         st64 = C.State(p, C.FP64, n_cap=n, device=local)
         st64.set_stream(stream)
-        st64.solve_device(X, lam, tol=tol, max_sweeps=args.max_sweeps)
+        rows64, trial64 = autotune(st64)
         t64, rec64 = timed_solves(st64, max(1, min(args.steps, 2)))
         r64, tim64, hist64 = rec64[-1]
         ms64, sw64 = tim64[0]
         out["fp64"] = {"seconds": max_over_ranks(statistics.mean(t64)), "sweeps": r64["sweeps"],
                        "kkt": r64["kkt"], "objective": r64["objective"], "launch_ms": tim64,
                        "updates_per_s": sw64 * updates / (ms64 * 1e-3),
+                       "autotune": {"choice": rows64, "ms_per_sweep": trial64},
                        "sweep_GBps": launch_bytes(p, 8, hist64[:sw64]) / (ms64 * 1e-3) / 1e9}
         out["mixed_vs_fp64_speedup"] = out["fp64"]["seconds"] / value
         fp64_sweeps = r64["sweeps"]
@@ -330,6 +358,8 @@ def run_ours(args):
         for name, prec, b in (("fp32", C.MIXED, 4), ("fp64", C.FP64, 8)):
             sfu = C.State(p, prec, device=local)
             sfu.set_stream(stream)
+            sfu.set_rows_per_warp(1)  # every pair changes: one row per warp, all SMs
+            sfu.set_sweep_variant(C.SWEEP_GRID)
             sfu.set_S(S32 if prec == C.MIXED else S32.double())
             lam_fu = 1e-3 * sfu.lambda_max()
             sfu.sweep(lam_fu, 1)

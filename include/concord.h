@@ -74,6 +74,15 @@ extern "C" {
                                   operand split hi + lo, hi*hi + hi*lo + lo*hi,
                                   FP32 accumulation in tensor memory */
 
+/* Sweep-kernel variant (concord_set_sweep_variant). */
+#define CONCORD_SWEEP_AUTO 0     /* FP32 sweeps: cluster when p fits, else grid;
+                                    FP64 sweeps: grid */
+#define CONCORD_SWEEP_GRID 1     /* persistent cooperative grid, one CTA per SM;
+                                    partners swap W scalars through an L2 ring */
+#define CONCORD_SWEEP_CLUSTER 2  /* one thread-block cluster (up to 16 SMs);
+                                    partners swap W scalars through distributed
+                                    shared memory (lowest latency per colour) */
+
 /* Stopping rule of concord_run / concord_solve*. */
 #define CONCORD_STOP_KKT 0    /* KKT residual <= tol (absolute, S units) */
 #define CONCORD_STOP_DELTA 1  /* the paper's rule: |Omega^(t)-Omega^(t-1)|_inf < tol
@@ -228,6 +237,35 @@ int concord_get_timing(concord_state *st, double *launch_ms, int *launch_sweeps,
 unsigned long long concord_kernel_launches(void);
 
 /*
+ * concord_set_sweep_variant -- CONCORD_SWEEP_AUTO (default), _GRID or
+ * _CLUSTER.  The variants compute the same iterates (bit for bit); they trade
+ * latency per colour step (cluster) against memory bandwidth (grid, all SMs).
+ * _CLUSTER fails with CONCORD_E_ARG if p exceeds what one cluster holds
+ * (cluster size x 512 rows).  concord_get_sweep_variant reports the variant
+ * of the last launch and the largest cluster size found (0 = none).
+ */
+int concord_set_sweep_variant(concord_state *st, int variant);
+int concord_get_sweep_variant(concord_state *st, int *variant, int *cluster_size);
+
+/*
+ * concord_set_poll_sleep -- back-off, in nanoseconds (0..100000), between
+ * two polls of a mailbox word in the sweep kernel (__nanosleep); a negative
+ * value restores the default (0).  Trades wake-up latency against the load/store
+ * bandwidth the polling warps take from the working ones.  Results do not
+ * depend on it.
+ */
+int concord_set_poll_sleep(concord_state *st, int ns);
+
+/*
+ * concord_set_rows_per_warp -- work layout of the sweep kernel: each warp
+ * owns up to `rows` rows of Omega and W (one row per lane), so `rows` trades
+ * scalar efficiency (many rows per warp) against row-update bandwidth (many
+ * warps).  0 (default) picks 32 for the cluster variant, 8 for the grid.
+ * Results do not depend on it.
+ */
+int concord_set_rows_per_warp(concord_state *st, int rows);
+
+/*
  * concord_set_gram_mode -- Gram arithmetic used by concord_solve_device /
  * concord_solve_host: CONCORD_GRAM_FP64 (default for FP64 states),
  * CONCORD_GRAM_FP32 or CONCORD_GRAM_TF32X3 (mixed states only).
@@ -249,10 +287,12 @@ int concord_sweep(concord_state *st, double lambda, int n_sweeps, concord_result
  * concord_run -- sweeps at lambda until the stopping rule holds (stop_rule
  * CONCORD_STOP_KKT: KKT <= tol; CONCORD_STOP_DELTA: delta < tol) or
  * max_sweeps.  FP64 state: all sweeps in FP64.  MIXED state: FP32 sweeps
- * until the rule holds at max(tol, switch_tol) (switch_tol <= 0 picks 10 *
- * tol), then W is rebuilt in FP64 from the FP64 copies of S and Omega and
- * FP64 sweeps polish to tol.  Returns CONCORD_OK or CONCORD_NOT_CONVERGED
- * (outputs filled either way) or an error.  Synchronises the stream.
+ * until the rule holds at max(tol, switch_tol) (switch_tol <= 0 picks
+ * max(10 tol, 1e-5)) or until the KKT residual stops falling by 10% for 4
+ * sweeps (FP32 rounding floor); then W is rebuilt in FP64 from the FP64
+ * copies of S and Omega and FP64 sweeps polish to tol.  Returns CONCORD_OK
+ * or CONCORD_NOT_CONVERGED (outputs filled either way) or an error.
+ * Synchronises the stream.
  */
 int concord_run(concord_state *st, double lambda, double tol, int max_sweeps,
                 int stop_rule, double switch_tol, concord_result *res);

@@ -25,6 +25,7 @@ F64, F32 = 0, 1
 PREP_NONE, PREP_CENTER, PREP_STANDARDIZE = 0, 1, 2
 GRAM_FP64, GRAM_FP32, GRAM_TF32X3 = 0, 1, 2
 STOP_KKT, STOP_DELTA = 0, 1
+SWEEP_AUTO, SWEEP_GRID, SWEEP_CLUSTER = 0, 1, 2
 
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "E_ARG", -2: "E_NONPOS_DIAG",
                 -3: "E_NONFINITE", -4: "E_CUDA", -5: "E_TIMEOUT", -6: "E_NOMEM",
@@ -72,6 +73,10 @@ SIGNATURES = {
     "concord_get_W": ([_vp, _vp, _ci, _ci], _ci),
     "concord_get_history": ([_vp, _dp, _ci, _ip], _ci),
     "concord_set_gram_mode": ([_vp, _ci], _ci),
+    "concord_set_rows_per_warp": ([_vp, _ci], _ci),
+    "concord_set_sweep_variant": ([_vp, _ci], _ci),
+    "concord_set_poll_sleep": ([_vp, _ci], _ci),
+    "concord_get_sweep_variant": ([_vp, _ip, _ip], _ci),
     "concord_sweep": ([_vp, _cd, _ci, _rp], _ci),
     "concord_run": ([_vp, _cd, _cd, _ci, _ci, _cd, _rp], _ci),
     "concord_solve_device": ([_vp, _vp, _ci, _ci, _ci, _ci, _cd, _cd, _ci, _ci, _vp, _ci, _ci,
@@ -205,6 +210,21 @@ class State:
 
     def set_fault(self, vertex: int, step: int = 0):
         _check(load().concord_set_fault(self._ptr, int(vertex), int(step)))
+
+    def set_rows_per_warp(self, rows: int):
+        _check(load().concord_set_rows_per_warp(self._ptr, int(rows)))
+
+    def set_poll_sleep(self, ns: int):
+        _check(load().concord_set_poll_sleep(self._ptr, int(ns)))
+
+    def set_sweep_variant(self, variant: int):
+        _check(load().concord_set_sweep_variant(self._ptr, int(variant)))
+
+    def sweep_variant(self):
+        """(variant of the last launch, largest cluster size found)."""
+        v, cs = ctypes.c_int(0), ctypes.c_int(0)
+        _check(load().concord_get_sweep_variant(self._ptr, ctypes.byref(v), ctypes.byref(cs)))
+        return v.value, cs.value
 
     def set_gram_mode(self, mode: int):
         _check(load().concord_set_gram_mode(self._ptr, int(mode)))

@@ -7,7 +7,7 @@
 
 #include <string>
 
-#include "../../include/concord.h"
+#include "concord.h"
 #include "kernels.h"
 
 using namespace concord;
@@ -38,9 +38,10 @@ int fail(int code, const char* fmt, ...) {
     }                                                                                    \
   } while (0)
 
-constexpr int kMailboxDepth = 8;
+constexpr int kMailboxDepth = kDepth;
 constexpr int kHistCap = 8192;
 constexpr int kMaxTimedLaunches = 4;
+constexpr int kDefaultPollNs = 0;
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
@@ -54,6 +55,8 @@ struct concord_state {
   void *S = nullptr, *W = nullptr, *Om = nullptr, *sdiagT = nullptr;
   double* sdiag64 = nullptr;
   double* omdiag64 = nullptr;  // mixed only
+  void *sd1 = nullptr, *sd2 = nullptr;    // sub-diagonal walk vectors, working precision
+  double *sd1_64 = nullptr, *sd2_64 = nullptr;  // FP64 versions (mixed polish)
   // FP64 copies (mixed) or aliases of the working set (fp64)
   double *S64 = nullptr, *W64 = nullptr, *Om64 = nullptr;
   bool om64_current = false;  // mixed: FP64 copies hold the latest iterate
@@ -79,6 +82,11 @@ struct concord_state {
   float *zt_hi = nullptr, *zt_lo = nullptr;
   int n_pad = 0, p_pad = 0;
   int gram_mode = CONCORD_GRAM_FP64;
+  int rows_per_warp = 0;  // 0: automatic (one row per lane)
+  int sweep_variant = 0;  // 0 auto, 1 grid, 2 cluster (CONCORD_SWEEP_*)
+  int poll_ns = -1;       // back-off between mailbox polls (-1: default)
+  int cluster_size = -1;  // largest launchable cluster (-1: not queried yet)
+  int last_variant = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaEvent_t lev[2 * kMaxTimedLaunches] = {};
   double launch_ms[kMaxTimedLaunches] = {};
@@ -112,29 +120,65 @@ struct RunOut {
   int sweeps = 0, first_delta = 0;
   double kkt = 0, obj = 0, delta = 0, active = 0;
   int to_vertex = -1, to_step = -1;
+  bool stalled = false;
 };
 
 // One persistent launch: n_sweeps outer iterations (fewer if the stopping
 // rule holds first), or only the objective / KKT pass when kkt_only.
 template <typename T>
 int launch_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* omdiag64, double lambda,
-               double tol, int stop_rule, int n_sweeps, int kkt_only, int hist_offset, RunOut* out) {
+               double tol, int stop_rule, int n_sweeps, int kkt_only, int hist_offset, int stall_stop,
+               RunOut* out) {
   const int p = st->p;
-  int block_warps = (p + st->sms - 1) / st->sms;
-  int bw = 1;
-  while (bw < block_warps && bw < 32) bw <<= 1;
-  block_warps = bw;
-  const int block = block_warps * 32;
-  int occ = 0;
-  CK(sweep_occupancy(sizeof(T) == 4, block, &occ));
-  if (occ < 1) return fail(CONCORD_E_OCCUPANCY, "sweep kernel cannot run %d threads per block", block);
-  int grid = st->sms * occ;
-  const int need = (p + block_warps - 1) / block_warps;
-  if (grid > need) grid = need;
-  if (grid > st->max_grid) grid = st->max_grid;
-  const int TW = grid * block_warps;
-  const int R = (p + TW - 1) / TW;
+  const bool mixed = sizeof(T) == 4;
+  // `row_warps` warps of each CTA own rows (one row per lane, up to `R` rows
+  // per warp); every warp takes part in the objective / KKT pass.
+  const int block = kSweepThreads;
+  // AUTO: FP32 sweeps take the cluster variant (lowest exchange latency);
+  // FP64 sweeps the grid variant, which spreads the FP64 arithmetic over
+  // every SM.  Rows per warp: 32 in a cluster, 8 on the grid.
+  const int variant = st->sweep_variant != CONCORD_SWEEP_AUTO
+                          ? st->sweep_variant
+                          : (mixed ? CONCORD_SWEEP_CLUSTER : CONCORD_SWEEP_GRID);
+  bool cluster = false;
+  int grid = 0, row_warps = 0, R = 0;
+  int want = st->rows_per_warp > 0 ? st->rows_per_warp : 32;
+  if (variant != CONCORD_SWEEP_GRID) {
+    if (st->cluster_size < 0) {
+      int cs = 0;
+      CK(sweep_cluster_size(mixed, block, block / 32, 32, &cs));
+      st->cluster_size = cs;
+    }
+    const int cs = st->cluster_size;
+    if (cs >= 2 && (long long)cs * (block / 32) * 32 >= p) {
+      cluster = true;
+      grid = cs;
+      row_warps = (p + want * cs - 1) / (want * cs);
+      if (row_warps < 1) row_warps = 1;
+      if (row_warps > block / 32) row_warps = block / 32;
+      R = (p + cs * row_warps - 1) / (cs * row_warps);
+    } else if (st->sweep_variant == CONCORD_SWEEP_CLUSTER) {
+      return fail(CONCORD_E_ARG, "p=%d does not fit one cluster of %d CTAs", p, cs);
+    }
+  }
+  if (!cluster) {
+    if (st->rows_per_warp <= 0) want = 8;
+    int occ = 0;
+    CK(sweep_occupancy(mixed, block, &occ));
+    if (occ < 1)
+      return fail(CONCORD_E_OCCUPANCY, "sweep kernel cannot run %d threads per block", block);
+    grid = st->sms * occ;
+    const int need = (p + 31) / 32;
+    if (grid > need) grid = need;
+    if (grid > st->max_grid) grid = st->max_grid;
+    row_warps = (p + want * grid - 1) / (want * grid);
+    if (row_warps < 1) row_warps = 1;
+    if (row_warps > block / 32) row_warps = block / 32;
+    const int TW = grid * row_warps;
+    R = (p + TW - 1) / TW;
+  }
   if (R > 32) return fail(CONCORD_E_ARG, "p=%d needs %d rows per warp (max 32)", p, R);
+  st->last_variant = cluster ? CONCORD_SWEEP_CLUSTER : CONCORD_SWEEP_GRID;
 
   // keep step tags monotone over the state's lifetime; restart them (and
   // clear the mailboxes) well before 32-bit overflow
@@ -153,10 +197,20 @@ int launch_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* om
   a.P = st->P;
   a.ld = st->ld;
   a.rows_per_warp = R;
+  a.row_warps = row_warps;
+  a.stall_stop = stall_stop;
+  a.poll_ns = (unsigned)(st->poll_ns >= 0 ? st->poll_ns : kDefaultPollNs);
   a.W = W;
   a.Om = Om;
   a.S = S;
   a.sdiag = sdiagT;
+  if (sizeof(T) == 4) {
+    a.sd1 = (const T*)st->sd1;
+    a.sd2 = (const T*)st->sd2;
+  } else {
+    a.sd1 = (const T*)st->sd1_64;
+    a.sd2 = (const T*)st->sd2_64;
+  }
   a.sdiag64 = st->sdiag64;
   a.omdiag64 = omdiag64;
   a.mbox = st->mbox;
@@ -183,7 +237,7 @@ int launch_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* om
 
   const int slot_ev = st->n_launch < kMaxTimedLaunches ? st->n_launch : -1;
   if (slot_ev >= 0) CK(cudaEventRecord(st->lev[2 * slot_ev], st->stream));
-  CK(launch_sweep(a, grid, block, st->stream));
+  CK(launch_sweep(a, grid, block, cluster, st->stream));
   if (slot_ev >= 0) CK(cudaEventRecord(st->lev[2 * slot_ev + 1], st->stream));
   st->tag_base += (unsigned)span;
 
@@ -215,9 +269,11 @@ int launch_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* om
     return fail(CONCORD_E_TIMEOUT, "device wait ran out (vertex %d, step %d)", st->h_abort[1],
                 st->h_abort[2]);
   }
-  out->status = code == 0 ? CONCORD_OK
-                          : code == 1 ? CONCORD_NOT_CONVERGED
-                                      : code == 2 ? CONCORD_E_NONFINITE : CONCORD_E_TIMEOUT;
+  out->stalled = code == 4;
+  out->status = (code == 0) ? CONCORD_OK
+                : (code == 1 || code == 4) ? CONCORD_NOT_CONVERGED
+                : (code == 2) ? CONCORD_E_NONFINITE
+                              : CONCORD_E_TIMEOUT;
   if (out->status == CONCORD_E_NONFINITE)
     return fail(CONCORD_E_NONFINITE, "non-finite objective or KKT residual after sweep %d",
                 out->sweeps);
@@ -276,7 +332,7 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
   int rc;
   if (!is_mixed(st)) {
     rc = launch_run<double>(st, st->S64, st->W64, st->Om64, (const double*)st->sdiagT, nullptr,
-                            lambda, run_tol, stop_rule, max_sweeps, 0, 0, &o1);
+                            lambda, run_tol, stop_rule, max_sweeps, 0, 0, 0, &o1);
     CK(cudaEventRecord(st->ev1, st->stream));
     CK(cudaEventSynchronize(st->ev1));
     float ms = 0;
@@ -285,12 +341,14 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
     fill_result(res, o1, o1.sweeps, 0, o1.first_delta, lambda, ms * 1e-3);
     return rc != CONCORD_OK ? rc : o1.status;
   }
-  // mixed precision: FP32 sweeps ...
-  double tol1 = exact ? -1.0 : (switch_tol > 0 ? switch_tol : 10.0 * tol);
+  // mixed precision: FP32 sweeps until the rule holds at the switch
+  // tolerance (default max(10 tol, 1e-5)) or the FP32 iteration stalls at
+  // its rounding floor ...
+  double tol1 = exact ? -1.0 : (switch_tol > 0 ? switch_tol : (10.0 * tol > 1e-5 ? 10.0 * tol : 1e-5));
   if (!exact && tol1 < tol) tol1 = tol;
   rc = launch_run<float>(st, (float*)st->S, (float*)st->W, (float*)st->Om,
                          (const float*)st->sdiagT, st->omdiag64, lambda, tol1, stop_rule,
-                         max_sweeps, 0, 0, &o1);
+                         max_sweeps, 0, 0, exact ? 0 : 1, &o1);
   st->om64_current = false;
   st->hist_rows = o1.sweeps;
   if (rc != CONCORD_OK || exact) {
@@ -305,7 +363,7 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
   if ((rc = promote_to_fp64(st)) != CONCORD_OK) return rc;
   const int left = max_sweeps - o1.sweeps;
   rc = launch_run<double>(st, st->S64, st->W64, st->Om64, st->sdiag64, nullptr, lambda, tol,
-                          stop_rule, left, left == 0 ? 1 : 0, o1.sweeps, &o2);
+                          stop_rule, left, left == 0 ? 1 : 0, o1.sweeps, 0, &o2);
   st->hist_rows = o1.sweeps + o2.sweeps;
   if (rc == CONCORD_OK) rc = demote_from_fp64(st);
   CK(cudaEventRecord(st->ev1, st->stream));
@@ -327,6 +385,8 @@ int reset_iterate(concord_state* st) {
   if (!is_mixed(st))
     CK(cudaMemcpyAsync(st->sdiagT, st->sdiag64, sizeof(double) * p, cudaMemcpyDeviceToDevice,
                        st->stream));
+  CK(launch_subdiag(st->S64, 0, ld, p, st->P, st->sd1_64, st->sd2_64, st->stream));
+  if (is_mixed(st)) CK(launch_subdiag(st->S, 1, ld, p, st->P, st->sd1, st->sd2, st->stream));
   if (is_mixed(st)) {
     CK(launch_set_identity(st->Om, 1, p, ld, st->stream));
     CK(cudaMemcpyAsync(st->W, st->S, sizeof(float) * (size_t)p * ld, cudaMemcpyDeviceToDevice,
@@ -452,6 +512,12 @@ int concord_create(concord_state** out, int p, int precision, int n_cap, int dev
       st->Om = st->Om64;
     }
     ALLOC(st->sdiag64, sizeof(double) * p);
+    ALLOC(st->sd1_64, sizeof(double) * p);
+    ALLOC(st->sd2_64, sizeof(double) * p);
+    if (is_mixed(st)) {
+      ALLOC(st->sd1, sizeof(float) * p);
+      ALLOC(st->sd2, sizeof(float) * p);
+    }
     // mailboxes sized for the FP64 form (2 words) so both precisions fit
     ALLOC(st->mbox, sizeof(unsigned long long) * 2 * (size_t)st->depth * st->pe);
     cudaMemset(st->mbox, 0, sizeof(unsigned long long) * 2 * (size_t)st->depth * st->pe);
@@ -518,12 +584,14 @@ int concord_destroy(concord_state* st) {
   if (!st) return CONCORD_OK;
   cudaSetDevice(st->device);
   if (st->stream) cudaStreamSynchronize(st->stream);
-  void* dev[] = {st->mbox, st->barrier, st->abort_info, st->flag, st->lmax, st->partials,
+  void* dev[] = {st->sd1_64, st->sd2_64, st->mbox, st->barrier, st->abort_info, st->flag, st->lmax, st->partials,
                  st->hist, st->result, st->mean, st->inv_scale, st->Z, st->Xstage, st->zt_hi,
                  st->zt_lo, st->sdiag64, st->sdiagT, st->omdiag64, st->S64, st->W64, st->Om64};
   for (void* d : dev)
     if (d) cudaFree(d);
   if (is_mixed(st)) {
+    if (st->sd1) cudaFree(st->sd1);
+    if (st->sd2) cudaFree(st->sd2);
     if (st->S) cudaFree(st->S);
     if (st->W) cudaFree(st->W);
     if (st->Om) cudaFree(st->Om);
@@ -665,6 +733,34 @@ int concord_run(concord_state* st, double lambda, double tol, int max_sweeps, in
   int rc = check_state(st);
   if (rc) return rc;
   return run_impl(st, lambda, tol, max_sweeps, stop_rule, switch_tol, 0, res);
+}
+
+int concord_set_poll_sleep(concord_state* st, int ns) {
+  if (!st) return fail(CONCORD_E_ARG, "state is NULL");
+  if (ns > 100000) return fail(CONCORD_E_ARG, "poll sleep must be <= 100000 ns");
+  st->poll_ns = ns < 0 ? -1 : ns;
+  return CONCORD_OK;
+}
+
+int concord_set_sweep_variant(concord_state* st, int variant) {
+  if (!st) return fail(CONCORD_E_ARG, "state is NULL");
+  if (variant < 0 || variant > 2) return fail(CONCORD_E_ARG, "variant must be 0, 1 or 2");
+  st->sweep_variant = variant;
+  return CONCORD_OK;
+}
+
+int concord_get_sweep_variant(concord_state* st, int* variant, int* cluster_size) {
+  if (!st) return fail(CONCORD_E_ARG, "state is NULL");
+  if (variant) *variant = st->last_variant;
+  if (cluster_size) *cluster_size = st->cluster_size;
+  return CONCORD_OK;
+}
+
+int concord_set_rows_per_warp(concord_state* st, int rows) {
+  if (!st) return fail(CONCORD_E_ARG, "state is NULL");
+  if (rows < 0 || rows > 32) return fail(CONCORD_E_ARG, "rows per warp must be in 0..32");
+  st->rows_per_warp = rows;
+  return CONCORD_OK;
 }
 
 int concord_set_gram_mode(concord_state* st, int mode) {

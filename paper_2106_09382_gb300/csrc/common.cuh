@@ -38,9 +38,9 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
-__device__ __forceinline__ int ld_volatile_s32(const int* p) {
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
   int v;
-  asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
@@ -54,28 +54,31 @@ __device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+// Mailbox words use relaxed GPU-scope accesses: they are served by L2 (the
+// GPU's point of coherence), never by a stale L1 line, and need no system-
+// scope coherence.
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
   unsigned long long v;
-  asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
-__device__ __forceinline__ void st_volatile_u64(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.volatile.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ void ld_volatile_v2u64(const unsigned long long* p,
-                                                  unsigned long long& a,
-                                                  unsigned long long& b) {
-  asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];"
+__device__ __forceinline__ void ld_relaxed_v2u64(const unsigned long long* p,
+                                                 unsigned long long& a,
+                                                 unsigned long long& b) {
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];"
                : "=l"(a), "=l"(b)
                : "l"(p)
                : "memory");
 }
 
-__device__ __forceinline__ void st_volatile_v2u64(unsigned long long* p, unsigned long long a,
-                                                  unsigned long long b) {
-  asm volatile("st.volatile.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b)
+__device__ __forceinline__ void st_relaxed_v2u64(unsigned long long* p, unsigned long long a,
+                                                 unsigned long long b) {
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b)
                : "memory");
 }
 
@@ -111,15 +114,15 @@ template <>
 struct Mailbox<float> {
   static constexpr int kWords = 1;
   __device__ static void publish(unsigned long long* slot, unsigned tag, float v) {
-    st_volatile_u64(slot, ((unsigned long long)tag << 32) | __float_as_uint(v));
+    st_relaxed_u64(slot, ((unsigned long long)tag << 32) | __float_as_uint(v));
   }
   __device__ static bool try_read(const unsigned long long* slot, unsigned tag, float& v) {
-    unsigned long long w = ld_volatile_u64(slot);
+    unsigned long long w = ld_relaxed_u64(slot);
     v = __uint_as_float((unsigned)(w & 0xffffffffull));
     return (unsigned)(w >> 32) == tag;
   }
   __device__ static unsigned read_tag(const unsigned long long* slot) {
-    return (unsigned)(ld_volatile_u64(slot) >> 32);
+    return (unsigned)(ld_relaxed_u64(slot) >> 32);
   }
 };
 
@@ -129,17 +132,17 @@ struct Mailbox<double> {
   __device__ static void publish(unsigned long long* slot, unsigned tag, double v) {
     unsigned long long b = (unsigned long long)__double_as_longlong(v);
     unsigned long long t = (unsigned long long)tag << 32;
-    st_volatile_v2u64(slot, t | (b >> 32), t | (b & 0xffffffffull));
+    st_relaxed_v2u64(slot, t | (b >> 32), t | (b & 0xffffffffull));
   }
   __device__ static bool try_read(const unsigned long long* slot, unsigned tag, double& v) {
     unsigned long long hi, lo;
-    ld_volatile_v2u64(slot, hi, lo);
+    ld_relaxed_v2u64(slot, hi, lo);
     unsigned long long b = ((hi & 0xffffffffull) << 32) | (lo & 0xffffffffull);
     v = __longlong_as_double((long long)b);
     return (unsigned)(hi >> 32) == tag && (unsigned)(lo >> 32) == tag;
   }
   __device__ static unsigned read_tag(const unsigned long long* slot) {
-    return (unsigned)(ld_volatile_u64(slot) >> 32);
+    return (unsigned)(ld_relaxed_u64(slot) >> 32);
   }
 };
 
@@ -160,7 +163,7 @@ __device__ __forceinline__ void grid_barrier(unsigned* counter, unsigned& gen,
     unsigned it = 0;
     while (ld_acquire_u32(counter) < target) {
       if ((++it & 15u) == 0) {
-        if (ld_volatile_s32(w.abort) != 0) break;
+        if (ld_relaxed_s32(w.abort) != 0) break;
         if (globaltimer_ns() - t0 > w.timeout_ns) {
           record_timeout(w, -1 - (int)blockIdx.x, where);
           break;

@@ -12,7 +12,19 @@ namespace concord {
 void note_launches(unsigned n);
 unsigned long long launches_so_far();
 
-constexpr int kSweepThreads = 1024;  // upper bound on the sweep kernel's block size
+constexpr int kSweepThreads = 512;   // the sweep kernel's block size
+constexpr int kPendCap = 8;
+constexpr int kDepth = 16;           // mailbox ring depth (a power of two, >= 4)          // pending row updates kept per row before a flush
+
+// Dynamic shared memory of the sweep kernel: pending lists of every owned
+// row; the cluster variant adds its mailbox ring (kDepth x rows x value
+// words) and per-row progress counters.
+inline size_t sweep_dyn_smem(size_t elem, int row_warps, int rows_per_warp, bool cluster) {
+  const size_t rows = (size_t)row_warps * rows_per_warp;
+  size_t b = (elem + sizeof(int)) * rows * kPendCap;
+  if (cluster) b += 8 * (elem / 4) * (size_t)kDepth * rows + 4 * rows;
+  return b;
+}
 
 // Per-CTA partial results of the fused objective / KKT pass.
 constexpr int kPartKkt = 0, kPartQuad = 1, kPartPen = 2, kPartLog = 3, kPartDelta = 4,
@@ -28,14 +40,17 @@ constexpr int kHist = 4;  // per sweep: delta, kkt, objective, active pairs
 template <typename T>
 struct SweepArgs {
   int p, P, ld, rows_per_warp;
+  int row_warps;              // warps per CTA that own rows (the rest join the KKT pass)
   T* W;                      // p x ld, W = Omega S
   T* Om;                     // p x ld, Omega (symmetric)
   const T* S;                // p x ld, S (padding columns zero)
   const T* sdiag;            // s_ii in T
+  const T* sd1;              // sd1[v] = S[v][v-1] (v >= 1)
+  const T* sd2;              // sd2[v] = S[v][next(v)], next(v) = v-2 cyclic on 1..P (0 if a bye)
   const double* sdiag64;     // s_ii in FP64
   double* omdiag64;          // FP64 diagonal of Omega (mixed precision only)
   unsigned long long* mbox;  // depth x (P+1) x words
-  int depth;
+  int depth;                 // must equal kDepth
   unsigned* barrier;         // zeroed before the launch
   WaitCtl wait;
   double* partials;          // gridDim.x x kParts
@@ -44,13 +59,20 @@ struct SweepArgs {
   double* result;            // kRes
   double lambda, tol, delta_tol;
   int stop_rule, n_sweeps, kkt_only;
+  int stall_stop;            // stop when the KKT residual stalls (FP32 phase)
+  unsigned poll_ns;          // back-off between mailbox polls (0: none)
   unsigned tag_base;
   int fault_vertex, fault_step;
 };
 
-cudaError_t launch_sweep(const SweepArgs<double>& a, int grid, int block, cudaStream_t st);
-cudaError_t launch_sweep(const SweepArgs<float>& a, int grid, int block, cudaStream_t st);
+// cluster = true: the whole grid is one thread-block cluster (grid <= 16).
+cudaError_t launch_sweep(const SweepArgs<double>& a, int grid, int block, bool cluster,
+                         cudaStream_t st);
+cudaError_t launch_sweep(const SweepArgs<float>& a, int grid, int block, bool cluster,
+                         cudaStream_t st);
 cudaError_t sweep_occupancy(bool mixed, int block, int* blocks_per_sm);
+// Largest launchable cluster (power of two <= 16; 0 if none).
+cudaError_t sweep_cluster_size(bool mixed, int block, int row_warps, int rows_per_warp, int* cs);
 
 cudaError_t launch_refresh_w(const double* Om, const double* S, double* W, int p, int ld, int sms,
                              cudaStream_t st);
@@ -80,6 +102,11 @@ cudaError_t launch_convert(const void* in, int in_f32, int ldi, void* out, int o
 // d64[i] = A[i*lda+i]; dT[i] (type t_f32) likewise; bad |= 1 if not > 0, 2 if non-finite.
 cudaError_t launch_extract_diag(const void* A, int a_f32, int lda, int p, double* d64, void* dT,
                                 int t_f32, int* bad, cudaStream_t st);
+// Sub-diagonal vectors of the circle-method walk: sd1[v] = S[v][v-1] and
+// sd2[v] = S[v][v-2] for v >= 3, S[1][P-1], S[2][P] (0 where the column is the
+// extra vertex of odd p); entry 0 is 0.
+cudaError_t launch_subdiag(const void* S, int s_f32, int ld, int p, int P, void* sd1, void* sd2,
+                           cudaStream_t st);
 // a[0..n) = v.
 cudaError_t launch_fill_f64(double* a, double v, int n, cudaStream_t st);
 // A (p x ld, type) = identity with zero padding.

@@ -67,6 +67,32 @@ cudaError_t launch_extract_diag(const void* A, int a_f32, int lda, int p, double
   return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void k_subdiag(const T* __restrict__ S, int ld, int p, int P, T* sd1, T* sd2) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < p; v += gridDim.x * blockDim.x) {
+    if (v == 0) {
+      sd1[0] = (T)0;
+      sd2[0] = (T)0;
+      continue;
+    }
+    sd1[v] = S[(size_t)v * ld + (v - 1)];
+    const int nx = (v >= 3) ? v - 2 : v - 2 + P;
+    sd2[v] = (nx < p) ? S[(size_t)v * ld + nx] : (T)0;
+  }
+}
+
+cudaError_t launch_subdiag(const void* S, int s_f32, int ld, int p, int P, void* sd1, void* sd2,
+                           cudaStream_t st) {
+  const int grid = (p + 255) / 256;
+  if (s_f32)
+    k_subdiag<float><<<grid, 256, 0, st>>>((const float*)S, ld, p, P, (float*)sd1, (float*)sd2);
+  else
+    k_subdiag<double><<<grid, 256, 0, st>>>((const double*)S, ld, p, P, (double*)sd1,
+                                             (double*)sd2);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 __global__ void k_fill_f64(double* a, double v, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
 }

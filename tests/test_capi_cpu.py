@@ -78,3 +78,38 @@ def test_no_gpu_means_error_not_fallback():
                            ctypes.byref(r))
     assert rc == C.E_CUDA
     assert np.all(out == 0)
+
+
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 7, 12, 13, 100, 101, 333, 1000, 1001])
+def test_consecutive_partners_walk_the_ring(p):
+    """Row v's partner at colour c + 1 follows from its partner at colour c:
+    v = 0 meets P - c (first sub-diagonal walk); for v >= 1, when neither
+    partner is vertex 0, the next one is next(w) = w - 2 cyclically on 1..P
+    (second sub-diagonal walk).  The sweep kernel reads S[w][next(w)] from a
+    p-vector on this basis."""
+    pairs = C.concord_schedule(p)
+    pe = p + (p % 2)
+    P = pe - 1
+    # partner table including the extra vertex of odd p (index p)
+    part = np.full((pe, P), -1, dtype=np.int64)
+    for c in range(P):
+        used = set()
+        for a_, b_ in pairs[c]:
+            if a_ >= 0:
+                part[a_, c], part[b_, c] = b_, a_
+                used |= {int(a_), int(b_)}
+        missing = [v for v in range(pe) if v not in used]
+        if p % 2:
+            assert len(missing) == 2  # the bye vertex and the extra vertex
+            part[missing[0], c], part[missing[1], c] = missing[1], missing[0]
+
+    def nxt(w):
+        return w - 2 if w >= 3 else w - 2 + P
+
+    for v in range(pe):
+        for c in range(P - 1):
+            w0, w1 = part[v, c], part[v, c + 1]
+            if v == 0:
+                assert w1 == w0 - 1
+            elif w0 != 0 and w1 != 0:
+                assert w1 == nxt(w0), (v, c, w0, w1)
