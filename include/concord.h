@@ -159,6 +159,35 @@ int concord_schedule(int p, int32_t *pairs_host, int *n_colours);
 int concord_gram(const void *X_dev, int x_dtype, int n, int p, int ldx, int prep,
                  int mode, void *S_dev, int s_dtype, int lds, void *stream);
 
+/*
+ * concord_gram_static -- the same S = Z^T Z / n as concord_gram in
+ * CONCORD_GRAM_FP64 mode (Z = X after `prep`; FP64 products and sums; S is
+ * FP64, p x p, row stride lds, both triangles written), but without
+ * allocating any device memory.  The paper has no counterpart: this entry
+ * point exists for callers that may not allocate device memory while they
+ * run -- a framework that owns all device memory through its own pool, a
+ * latency-critical loop in which cudaMalloc / cudaFree would synchronise the
+ * device, or a deployment that forbids dynamic allocation after start-up.
+ *
+ * X is standardized while the tiles are staged, and the per-column
+ * statistics live in a fixed device array of the library (2 x 16384 doubles
+ * plus a status word, held on every device that loads the library until the
+ * process exits).  Hence:
+ *   - p must be <= 16384; larger p returns CONCORD_E_ARG (use concord_gram);
+ *   - the first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) and caches it: make that first call before any
+ *     stream capture that includes it;
+ *   - every call shares the array and it keeps the last call's contents;
+ *     the status word is cleared by each call; calls that overlap on the GPU
+ *     (different streams or host threads at the same time) race on it and
+ *     must be serialised by the caller.
+ * The call synchronises `stream` to report a constant or non-finite column.
+ * Errors: CONCORD_E_ARG, CONCORD_E_NONPOS_DIAG, CONCORD_E_NONFINITE,
+ * CONCORD_E_CUDA.
+ */
+int concord_gram_static(const void *X_dev, int x_dtype, int n, int p, int ldx, int prep,
+                        double *S_dev, int lds, void *stream);
+
 /* ----------------------------------------------------------- solver state */
 typedef struct concord_state concord_state;
 

@@ -63,6 +63,7 @@ SIGNATURES = {
     "concord_version": ([], ctypes.c_char_p),
     "concord_schedule": ([_ci, ctypes.POINTER(ctypes.c_int32), _ip], _ci),
     "concord_gram": ([_vp, _ci, _ci, _ci, _ci, _ci, _ci, _vp, _ci, _ci, _vp], _ci),
+    "concord_gram_static": ([_vp, _ci, _ci, _ci, _ci, _ci, _vp, _ci, _vp], _ci),
     "concord_create": ([ctypes.POINTER(_vp), _ci, _ci, _ci, _ci], _ci),
     "concord_destroy": ([_vp], _ci),
     "concord_set_stream": ([_vp, _vp], _ci),
@@ -165,6 +166,20 @@ def concord_gram(X, prep: int = PREP_STANDARDIZE, mode: int = GRAM_FP64, out_dty
     S = torch.empty((p, p), dtype=out_dtype, device=X.device)
     _check(load().concord_gram(X.data_ptr(), _dtype_code(X), n, p, X.stride(0), prep, mode,
                                S.data_ptr(), _dtype_code(S), p, _stream_ptr(stream)))
+    return S
+
+
+def concord_gram_static(X, prep: int = PREP_STANDARDIZE, out=None, stream=None):
+    """FP64 S = Z^T Z / n through the allocation-free entry point (the device
+    statistics live in the library's fixed array; p <= 16384).  `out` may
+    give the p x p float64 output tensor."""
+    import torch
+    assert X.is_cuda and X.dim() == 2 and X.stride(1) == 1
+    n, p = X.shape
+    S = out if out is not None else torch.empty((p, p), dtype=torch.float64, device=X.device)
+    assert S.dtype == torch.float64 and S.is_cuda and S.stride(1) == 1
+    _check(load().concord_gram_static(X.data_ptr(), _dtype_code(X), n, p, X.stride(0), prep,
+                                      S.data_ptr(), S.stride(0), _stream_ptr(stream)))
     return S
 
 

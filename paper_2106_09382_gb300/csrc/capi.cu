@@ -47,6 +47,8 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 }  // namespace
 
+int concord::set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 struct concord_state {
   int device = -1, sms = 0;
   int p = 0, pe = 0, P = 0, ld = 0, precision = 0, n_cap = 0;

@@ -8,6 +8,10 @@
 
 namespace concord {
 
+// Records `msg` as the calling thread's concord_last_error() text and
+// returns `code` (error reporting for entry points outside capi.cu).
+int set_error(int code, const char* msg);
+
 // Counts every kernel this library launches (for launch accounting).
 void note_launches(unsigned n);
 unsigned long long launches_so_far();
