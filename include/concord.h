@@ -297,7 +297,8 @@ int concord_set_rows_per_warp(concord_state *st, int rows);
 /*
  * concord_set_gram_mode -- Gram arithmetic used by concord_solve_device /
  * concord_solve_host: CONCORD_GRAM_FP64 (default for FP64 states),
- * CONCORD_GRAM_FP32 or CONCORD_GRAM_TF32X3 (mixed states only).
+ * CONCORD_GRAM_FP32 or CONCORD_GRAM_TF32X3 (mixed states only; their
+ * default).
  */
 int concord_set_gram_mode(concord_state *st, int mode);
 
@@ -328,9 +329,10 @@ int concord_run(concord_state *st, double lambda, double tol, int max_sweeps,
 
 /*
  * concord_solve_device -- the whole path on resident data: prepare X
- * (n <= n_cap rows, device, row stride ldx, x_dtype), S = Z^T Z / n (FP64
- * state: CONCORD_GRAM_FP64; MIXED: CONCORD_GRAM_TF32X3 then an FP64 copy of
- * the FP32 S), Omega = I, then concord_run.  Omega_dev (may be NULL) receives
+ * (n <= n_cap rows, device, row stride ldx, x_dtype), S = Z^T Z / n in the
+ * state's Gram mode (FP64 state: CONCORD_GRAM_FP64; MIXED:
+ * CONCORD_GRAM_TF32X3 then an FP64 copy of the FP32 S for polishing),
+ * Omega = I, then concord_run.  Omega_dev (may be NULL) receives
  * Omega in `omega_dtype` with row stride ldo.
  */
 int concord_solve_device(concord_state *st, const void *X_dev, int x_dtype, int n,

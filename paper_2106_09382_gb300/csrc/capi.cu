@@ -544,7 +544,7 @@ int concord_create(concord_state** out, int p, int precision, int n_cap, int dev
         ALLOC(st->zt_lo, sizeof(float) * (size_t)st->n_pad * st->p_pad);
       }
     }
-    st->gram_mode = is_mixed(st) ? CONCORD_GRAM_FP32 : CONCORD_GRAM_FP64;
+    st->gram_mode = is_mixed(st) ? CONCORD_GRAM_TF32X3 : CONCORD_GRAM_FP64;
     if (cudaMallocHost((void**)&st->h_result, sizeof(double) * kRes) != cudaSuccess ||
         cudaMallocHost((void**)&st->h_abort, 3 * sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void**)&st->h_flag, sizeof(int)) != cudaSuccess) {
@@ -807,7 +807,7 @@ static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, i
       CK(launch_split_tf32(X, x_f32, n, p, ldx, st->mean, st->inv_scale, st->zt_hi, st->zt_lo,
                            round_up(n, 32), st->p_pad, st->stream));
       cudaError_t e = launch_gram_tf32x3(st->zt_hi, st->zt_lo, round_up(n, 32), st->p_pad, p,
-                                         (float*)st->S, ld, 1.0f / n, st->stream);
+                                         (float*)st->S, ld, 1.0f / n, st->flag, st->stream);
       if (e == cudaErrorNotSupported) return fail(CONCORD_E_CUDA, "tensor-core Gram unavailable");
       CK(e);
       CK(launch_convert(st->S, 1, ld, st->S64, 0, ld, p, p, st->stream));
@@ -818,6 +818,7 @@ static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, i
   }
   int bad = 0, rc;
   if ((rc = read_flag(st, &bad))) return rc;
+  if (bad & 4) return fail(CONCORD_E_TIMEOUT, "tensor-core Gram: a device-side wait ran out");
   if (bad & 2) return fail(CONCORD_E_NONFINITE, "X has a non-finite entry");
   if (bad & 1) return fail(CONCORD_E_NONPOS_DIAG, "X has a constant column");
   return reset_iterate(st);
@@ -880,7 +881,7 @@ int concord_gram(const void* X_dev, int x_dtype, int n, int p, int ldx, int prep
     GK(cudaMallocAsync((void**)&lo, sizeof(float) * (size_t)n_pad * p_pad, s));
     GK(launch_split_tf32(X_dev, x_f32, n, p, ldx, mean, inv, hi, lo, n_pad, p_pad, s));
     if (s_f32) {
-      e = launch_gram_tf32x3(hi, lo, n_pad, p_pad, p, (float*)S_dev, lds, 1.0f / n, s);
+      e = launch_gram_tf32x3(hi, lo, n_pad, p_pad, p, (float*)S_dev, lds, 1.0f / n, bad, s);
       if (e == cudaErrorNotSupported) {
         rc = fail(CONCORD_E_CUDA, "tensor-core Gram unavailable on this device");
         goto done;
@@ -888,7 +889,7 @@ int concord_gram(const void* X_dev, int x_dtype, int n, int p, int ldx, int prep
       GK(e);
     } else {
       GK(cudaMallocAsync(&Sw, sizeof(float) * (size_t)p * ld, s));
-      e = launch_gram_tf32x3(hi, lo, n_pad, p_pad, p, (float*)Sw, ld, 1.0f / n, s);
+      e = launch_gram_tf32x3(hi, lo, n_pad, p_pad, p, (float*)Sw, ld, 1.0f / n, bad, s);
       if (e == cudaErrorNotSupported) {
         rc = fail(CONCORD_E_CUDA, "tensor-core Gram unavailable on this device");
         goto done;
@@ -902,7 +903,8 @@ int concord_gram(const void* X_dev, int x_dtype, int n, int p, int ldx, int prep
   }
   GK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
   GK(cudaStreamSynchronize(s));
-  if (hbad & 2) rc = fail(CONCORD_E_NONFINITE, "X has a non-finite entry");
+  if (hbad & 4) rc = fail(CONCORD_E_TIMEOUT, "tensor-core Gram: a device-side wait ran out");
+  else if (hbad & 2) rc = fail(CONCORD_E_NONFINITE, "X has a non-finite entry");
   else if (hbad & 1 && prep == CONCORD_PREP_STANDARDIZE)
     rc = fail(CONCORD_E_NONPOS_DIAG, "X has a constant column");
 done:

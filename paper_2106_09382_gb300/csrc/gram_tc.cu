@@ -1,5 +1,27 @@
 // Tensor-core Gram for the mixed-precision path: S = Z^T Z / n from FP32
-// operands split into tf32 hi + lo parts (3xTF32: hi*hi + hi*lo + lo*hi).
+// operands split into tf32 hi + lo parts (3xTF32: hi*hi + hi*lo + lo*hi, FP32
+// accumulation in tensor memory), on 5th-generation tensor cores (tcgen05).
+//
+// Layout: the split kernel writes Zt_hi / Zt_lo as p_pad x n_pad row-major
+// FP32 (K-major operands: the reduction index k is contiguous), zero padded.
+// Each CTA computes one 128 x 128 tile (bi, bj), bi <= bj, of the upper
+// triangle and writes it and its mirror, so S is exactly symmetric.
+//   * thread 0 streams 32-wide K blocks of A_hi, A_lo (rows of tile bi) and
+//     B_hi, B_lo (rows of tile bj) with TMA (128-byte swizzle) into a
+//     3-stage shared-memory ring guarded by mbarriers;
+//   * thread 32 issues, per K block, 4 x 3 tcgen05.mma (K = 8 each) into one
+//     of two 128-column FP32 accumulators in tensor memory (a new one every
+//     4 K blocks) and commits each stage back to its producer barrier;
+//   * eight epilogue warps drain each finished accumulator (tcgen05.ld, each
+//     warp its own 32 lanes and 64 columns) into FP64 registers, then scale
+//     by 1/n and store S[i][j] and S[j][i] for i <= j.
+// Every wait is bounded (%globaltimer); a wait that runs out sets bit 4 of
+// the caller's status word.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "kernels.h"
 
 namespace concord {
@@ -55,9 +77,334 @@ cudaError_t launch_split_tf32(const void* X, int x_f32, int n, int p, int ldx, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_gram_tf32x3(const float*, const float*, int, int, int, float*, int, float,
-                               cudaStream_t) {
-  return cudaErrorNotSupported;
+// ----------------------------------------------------------------- tcgen05
+constexpr int kTM = 128;                          // tile rows (M) and columns (N)
+constexpr int kTK = 32;                           // K block: 32 FP32 = 128 bytes
+constexpr int kStages = 3;
+constexpr int kOpBytes = kTM * kTK * 4;           // one operand tile: 16 KB
+constexpr int kStageBytes = 4 * kOpBytes;         // A_hi, A_lo, B_hi, B_lo
+constexpr int kChunkKb = 4;                       // K blocks summed per FP32 accumulator chunk
+constexpr int kEpiWarps = 8;                      // epilogue warps (2 per TMEM lane quadrant)
+constexpr int kGramThreads = 32 * (2 + kEpiWarps);  // producer, MMA issuer, epilogue
+constexpr int kTmemCols = 256;                    // two 128-column FP32 accumulators
+constexpr size_t kGramSmem = (size_t)kStages * kStageBytes + 1024;  // + alignment slack
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false (and status bit 4)
+// if it has not completed within 2 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  unsigned it = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++it & 255u) == 0 && globaltimer_ns() - t0 > 2000000000ull) {
+      atomicOr(status, 4);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile stored in the
+// 128-byte swizzled layout TMA writes (rows of 128 bytes, 8-row groups 1024
+// bytes apart): start address >> 4, leading offset (unused for swizzled
+// K-major) 16 B, stride offset 1024 B, descriptor version 1, layout
+// SWIZZLE_128B.
+__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of tcgen05.mma kind::tf32: D FP32, A and B TF32,
+// both K-major, N = 128, M = 128.
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTM >> 3) << 17) |
+                                ((uint32_t)(kTM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\t"
+      "setp.ne.b32 q, %3, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %4, q;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(accumulate), "r"(kIdescTf32)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+        "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+        "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// One CTA per 128 x 128 tile of the upper triangle.  The K reduction is cut
+// into chunks of kChunkKb blocks (128 elements): each chunk accumulates in
+// FP32 in one of two tensor-memory buffers while the epilogue warps add the
+// previous chunk into FP64 registers, so FP32 rounding only ever covers 128
+// products and the tensor pipe never waits for the drain.
+__global__ void __launch_bounds__(kGramThreads, 1)
+    k_gram_tf32x3(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
+                  int nkb, int p, float* __restrict__ S, int lds, float scale, int nbt, int* status) {
+  extern __shared__ unsigned char gsm_raw[];
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ __align__(8) uint64_t empty[kStages];
+  __shared__ __align__(8) uint64_t acc_full[2];
+  __shared__ __align__(8) uint64_t acc_empty[2];
+  __shared__ uint32_t tmem_base;
+  // 1024-byte aligned operand ring (the 128-byte swizzle repeats every 1024)
+  unsigned char* ring = (unsigned char*)(((uintptr_t)gsm_raw + 1023) & ~(uintptr_t)1023);
+
+  // tile index -> (bi, bj), bi <= bj, row-major over the upper triangle
+  int tt = blockIdx.x, bi = 0;
+  while (tt >= nbt - bi) {
+    tt -= nbt - bi;
+    ++bi;
+  }
+  const int bj = bi + tt;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunks = (nkb + kChunkKb - 1) / kChunkKb;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 32) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], kEpiWarps * 32);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = tmem_base;
+
+  if (warp == 0) {
+    // ---- producer: TMA loads of the four operand tiles per K block
+    if (lane == 0) {
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % kStages;
+        if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1, status)) break;
+        unsigned char* st = ring + (size_t)s * kStageBytes;
+        mbar_expect_tx(&full[s], kStageBytes);
+        tma_load_2d(st, &tm_hi, &full[s], kb * kTK, bi * kTM);
+        tma_load_2d(st + kOpBytes, &tm_lo, &full[s], kb * kTK, bi * kTM);
+        tma_load_2d(st + 2 * kOpBytes, &tm_hi, &full[s], kb * kTK, bj * kTM);
+        tma_load_2d(st + 3 * kOpBytes, &tm_lo, &full[s], kb * kTK, bj * kTM);
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer: per K block hi*hi + hi*lo + lo*hi on four K = 8 slices
+    if (lane == 0) {
+      bool ok = true;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int b = c & 1;
+        if (c >= 2) {
+          ok = mbar_wait(&acc_empty[b], ((c >> 1) - 1) & 1, status);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        const uint32_t d = tbase + (uint32_t)(b * kTM);
+        const int kb_end = min(nkb, (c + 1) * kChunkKb);
+        for (int kb = c * kChunkKb; kb < kb_end; ++kb) {
+          const int s = kb % kStages;
+          ok = mbar_wait(&full[s], (kb / kStages) & 1, status);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = smem_u32(ring + (size_t)s * kStageBytes);
+          const uint64_t ah = sw128_kmajor_desc(st), al = sw128_kmajor_desc(st + kOpBytes);
+          const uint64_t bh = sw128_kmajor_desc(st + 2 * kOpBytes);
+          const uint64_t bl = sw128_kmajor_desc(st + 3 * kOpBytes);
+#pragma unroll
+          for (int kk = 0; kk < kTK / 8; ++kk) {
+            const uint64_t adv = (uint64_t)(kk * 32 >> 4);  // 8 TF32 = 32 bytes along K
+            const uint32_t first = (kb == c * kChunkKb && kk == 0) ? 0u : 1u;
+            mma_tf32(d, ah + adv, bh + adv, first);
+            mma_tf32(d, ah + adv, bl + adv, 1u);
+            mma_tf32(d, al + adv, bh + adv, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        mma_commit(&acc_full[b]);
+      }
+    }
+  } else {
+    // ---- epilogue: warp e owns TMEM lanes 32 (warp % 4) .. +31 (tile rows)
+    //      and tile columns 64 * (e / 4) .. +63; FP64 sums across chunks
+    const int e = warp - 2;
+    const int quad = warp & 3;
+    const int col0 = 64 * (e >> 2);
+    double acc[64];
+#pragma unroll
+    for (int q = 0; q < 64; ++q) acc[q] = 0.0;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int b = c & 1;
+      ok = __all_sync(0xffffffffu, ok && mbar_wait(&acc_full[b], (c >> 1) & 1, status));
+      __syncwarp();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (ok) {
+        const uint32_t ta = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * kTM + col0);
+        uint32_t v[32];
+        tmem_ld_32x32b_x32(ta, v);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) acc[q] += (double)__uint_as_float(v[q]);
+        tmem_ld_32x32b_x32(ta + 32, v);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) acc[32 + q] += (double)__uint_as_float(v[q]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&acc_empty[b]);
+      if (!ok) break;
+    }
+    if (ok) {
+      const int i = bi * kTM + quad * 32 + lane;
+      if (i < p) {
+#pragma unroll
+        for (int q = 0; q < 64; ++q) {
+          const int j = bj * kTM + col0 + q;
+          if (j < p && i <= j) {
+            const float val = (float)(acc[q] * (double)scale);
+            S[(size_t)i * lds + j] = val;
+            S[(size_t)j * lds + i] = val;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
+                 "r"(kTmemCols)
+                 : "memory");
+}
+
+namespace {
+
+std::mutex g_tma_mu;
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+cudaError_t encode_fn(PFN_cuTensorMapEncodeTiled_v12000* out) {
+  std::lock_guard<std::mutex> lock(g_tma_mu);
+  if (!g_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  *out = g_encode;
+  return cudaSuccess;
+}
+
+// 2-D tensor map over a p_pad x n_pad FP32 array, box 32 (K) x 128 (rows),
+// 128-byte swizzle.
+cudaError_t make_map(CUtensorMap* map, const float* base, int n_pad, int p_pad) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc;
+  cudaError_t e = encode_fn(&enc);
+  if (e != cudaSuccess) return e;
+  cuuint64_t dims[2] = {(cuuint64_t)n_pad, (cuuint64_t)p_pad};
+  cuuint64_t strides[1] = {(cuuint64_t)n_pad * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)kTM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_gram_tf32x3(const float* zt_hi, const float* zt_lo, int n_pad, int p_pad, int p,
+                               float* S, int lds, float scale, int* status, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (major != 10 || minor != 3) return cudaErrorNotSupported;
+  if (n_pad % kTK != 0 || p_pad % kTM != 0 || n_pad <= 0 || p_pad <= 0) return cudaErrorInvalidValue;
+  if (((uintptr_t)zt_hi & 15) || ((uintptr_t)zt_lo & 15)) return cudaErrorInvalidValue;
+  CUtensorMap m_hi, m_lo;
+  if ((e = make_map(&m_hi, zt_hi, n_pad, p_pad)) != cudaSuccess) return e;
+  if ((e = make_map(&m_lo, zt_lo, n_pad, p_pad)) != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_gram_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kGramSmem);
+  if (e != cudaSuccess) return e;
+  const int nbt = p_pad / kTM;
+  const int tiles = nbt * (nbt + 1) / 2;
+  k_gram_tf32x3<<<tiles, kGramThreads, kGramSmem, st>>>(m_hi, m_lo, n_pad / kTK, p, S, lds, scale,
+                                                        nbt, status);
+  note_launches(1);
+  return cudaGetLastError();
 }
 
 }  // namespace concord

@@ -129,8 +129,9 @@ cudaError_t launch_split_tf32(const void* X, int x_f32, int n, int p, int ldx, c
                               const double* inv_scale, float* zt_hi, float* zt_lo, int n_pad,
                               int p_pad, cudaStream_t st);
 // S (p x lds, FP32) = (hi hi^T + hi lo^T + lo hi^T) * scale with tcgen05.mma
-// kind::tf32.  Returns cudaErrorNotSupported if the device is not sm_103.
+// kind::tf32 (n_pad a multiple of 32, p_pad of 128).  A device-side wait that
+// runs out sets bit 4 of *status.  cudaErrorNotSupported if not sm_103.
 cudaError_t launch_gram_tf32x3(const float* zt_hi, const float* zt_lo, int n_pad, int p_pad, int p,
-                               float* S, int lds, float scale, cudaStream_t st);
+                               float* S, int lds, float scale, int* status, cudaStream_t st);
 
 }  // namespace concord

@@ -72,6 +72,23 @@ def test_gram_fp32(n, p):
     assert np.array_equal(S, S.T)
 
 
+@pytest.mark.parametrize("n,p", [(200, 100), (61, 333), (300, 517), (37, 2)])
+def test_gram_tf32x3_tensor_cores(n, p):
+    """tcgen05 kind::tf32 Gram with hi + lo operands: hi*hi + hi*lo + lo*hi.
+    Each standardized value is split into 11 + 11 significant bits (error
+    <= 2^-22 relative), so each product is off by <= 2^-21 |z_i z_k| once the
+    lo*lo term is dropped; products are summed in FP32 over chunks of 128
+    (error <= 128 * 2^-24 of the chunk's absolute sum) and the chunks in FP64.
+    With sum_k |z_i z_k| <= n for standardized columns the error of S is at
+    most 128 * 2^-24 + 2^-20, whatever n."""
+    X = data(n, p, 13 * n + p)
+    S = host(C.concord_gram(dev(X), C.PREP_STANDARDIZE, C.GRAM_TF32X3))
+    S_or = O.gram(O.standardize(X))
+    assert np.array_equal(S, S.T)
+    err = np.abs(S - S_or).max()
+    assert err <= 128 * 2.0 ** -24 + 2.0 ** -20, err
+
+
 def test_gram_centre_and_none():
     X = data(40, 50, 3)
     S1 = host(C.concord_gram(dev(X), C.PREP_CENTER, C.GRAM_FP64))
