@@ -34,7 +34,7 @@ METRIC = "time to KKT≤1e-5 at p=5000: mixed vs FP64 PCD; updates/s; HBM % peak
 FALLBACK_HBM_GBS = 6800.0
 
 
-def parse():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -49,7 +49,7 @@ def parse():
                     help="skip FP64 arm, microbench, e2e and CPU baseline")
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle work for the CPU baseline sample")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def load_peaks():
@@ -131,6 +131,38 @@ def launch_bytes(p: int, b: int, hist_rows) -> float:
     return float(sum(sweep_bytes(p, b, h[3]) for h in hist_rows))
 
 
+SWEEP_SOURCES = ("sweep.cu", "kernels.h", "common.cuh")
+SWEEP_PROFILE = os.path.join(ROOT, "profiles", "k_sweep_fp32_cluster_p5000.md")
+
+
+def sweep_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_2106_09382_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(variant: str):
+    """DRAM bytes per sweep of the FP32 sweep kernel from the committed ncu
+    summary (dram__bytes_read.sum + dram__bytes_write.sum of one launch,
+    divided by its sweeps), if that summary was taken from the current kernel
+    source and the same launch variant; else None."""
+    try:
+        with open(SWEEP_PROFILE) as f:
+            kv = dict(line.split(":", 1) for line in f.read().splitlines()
+                      if line.startswith(("traffic_per_sweep_bytes:", "source_sha256:",
+                                          "variant:")))
+    except (OSError, ValueError):
+        return None
+    if kv.get("source_sha256", "").strip() != sweep_source_hash():
+        return None
+    if kv.get("variant", "").strip() != variant:
+        return None
+    return float(kv["traffic_per_sweep_bytes"])
+
+
 # ------------------------------------------------------------ CPU baseline
 def cpu_baseline(X: np.ndarray, lam: float, sweeps: int, budget: float, sweeps_src: str):
     """The oracle (single-threaded C, FP64, Eq. 3 as direct sums) timed on a
@@ -176,6 +208,17 @@ def golden_sweeps(p: int):
 
 
 # ------------------------------------------------------------------ arms
+def reduce_max(v: float, world: int, device=None) -> float:
+    """Max of a per-rank scalar over the process group (identity at world 1)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -232,11 +275,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, world, dev)
 
     wl = synth.workload_ar1(p, n, seed=0)
     Xh = np.ascontiguousarray(wl["X"])
@@ -309,8 +348,14 @@ def run_ours(args):
     updates = p * (p + 1) / 2
     ups = sw32 * updates / (ms32 * 1e-3)
     polish = [(ms, sw) for ms, sw in tim_last[1:]]
+    vname = rows_best  # variant/rows of the FP32 sweeps (autotune choice)
+    tps = profiled_traffic(vname)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None,
+                "frac": achieved / hbm_peak, "traffic": None if tps is None else tps * sw32,
+                "traffic_source": ("ncu DRAM bytes per sweep of the same kernel source and "
+                                   "variant x sweeps of this launch" if tps is not None else
+                                   "no ncu capture of the current kernel source / variant"),
+                "variant": vname,
                 "kernel": "k_sweep<float> (FP32 sweeps of the mixed solve)",
                 "peak_source": "%s hbm_gbs (STREAM-style copy)" % peak_src,
                 "algorithmic_bytes_per_launch": bytes32, "launch_ms": ms32, "sweeps": sw32,
@@ -402,7 +447,7 @@ def run_ours(args):
 
 
 def main():
-    args = parse()
+    args = parse_args()
     if args.impl == "reference":
         run_reference(args)
     else:

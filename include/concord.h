@@ -270,8 +270,11 @@ unsigned long long concord_kernel_launches(void);
  * _CLUSTER.  The variants compute the same iterates (bit for bit); they trade
  * latency per colour step (cluster) against memory bandwidth (grid, all SMs).
  * _CLUSTER fails with CONCORD_E_ARG if p exceeds what one cluster holds
- * (cluster size x 512 rows).  concord_get_sweep_variant reports the variant
- * of the last launch and the largest cluster size found (0 = none).
+ * (cluster size x 512 rows).  Explicit settings (this one and
+ * concord_set_rows_per_warp) apply to sweeps in the state's working
+ * precision; the FP64 polishing sweeps of a MIXED state use the FP64
+ * defaults.  concord_get_sweep_variant reports the variant of the last
+ * launch and the largest cluster size found (0 = none).
  */
 int concord_set_sweep_variant(concord_state *st, int variant);
 int concord_get_sweep_variant(concord_state *st, int *variant, int *cluster_size);

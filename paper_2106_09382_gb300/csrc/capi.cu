@@ -138,13 +138,16 @@ int launch_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* om
   const int block = kSweepThreads;
   // AUTO: FP32 sweeps take the cluster variant (lowest exchange latency);
   // FP64 sweeps the grid variant, which spreads the FP64 arithmetic over
-  // every SM.  Rows per warp: 32 in a cluster, 8 on the grid.
-  const int variant = st->sweep_variant != CONCORD_SWEEP_AUTO
+  // every SM.  Rows per warp: 32 in a cluster, 8 on the grid.  Explicit
+  // settings apply to sweeps in the state's working precision; the FP64
+  // polishing sweeps of a mixed state keep the FP64 defaults.
+  const bool own = mixed == is_mixed(st);
+  const int variant = (own && st->sweep_variant != CONCORD_SWEEP_AUTO)
                           ? st->sweep_variant
                           : (mixed ? CONCORD_SWEEP_CLUSTER : CONCORD_SWEEP_GRID);
   bool cluster = false;
   int grid = 0, row_warps = 0, R = 0;
-  int want = st->rows_per_warp > 0 ? st->rows_per_warp : 32;
+  int want = (own && st->rows_per_warp > 0) ? st->rows_per_warp : 32;
   if (variant != CONCORD_SWEEP_GRID) {
     if (st->cluster_size < 0) {
       int cs = 0;
@@ -159,12 +162,12 @@ int launch_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* om
       if (row_warps < 1) row_warps = 1;
       if (row_warps > block / 32) row_warps = block / 32;
       R = (p + cs * row_warps - 1) / (cs * row_warps);
-    } else if (st->sweep_variant == CONCORD_SWEEP_CLUSTER) {
+    } else if (variant == CONCORD_SWEEP_CLUSTER && own && st->sweep_variant == CONCORD_SWEEP_CLUSTER) {
       return fail(CONCORD_E_ARG, "p=%d does not fit one cluster of %d CTAs", p, cs);
     }
   }
   if (!cluster) {
-    if (st->rows_per_warp <= 0) want = 8;
+    if (!(own && st->rows_per_warp > 0)) want = 8;
     int occ = 0;
     CK(sweep_occupancy(mixed, block, &occ));
     if (occ < 1)

@@ -463,3 +463,51 @@ def test_full_size_converges(precision):
 
 def lam_sign(v, lam):
     return lam * np.sign(v)
+
+
+# ----------------------------------------------- full size vs the oracle's solve
+def _golden(p):
+    import json
+    import os
+    base = os.path.join(os.path.dirname(O.__file__), "golden", "ar1_p%d" % p)
+    with open(base + ".json") as f:
+        rec = json.load(f)
+    z = np.load(base + "_omega.npz")
+    return rec, z["ij"], z["v"]
+
+
+@pytest.mark.parametrize("precision", [C.FP64, C.MIXED])
+def test_full_size_matches_oracle_solve_record(precision):
+    """The oracle's own FP64 solve of the p = 5000 workload (written by
+    oracle/make_golden.py): same sweeps and per-sweep (delta, KKT, objective,
+    changed pairs) for the FP64 path, same converged Omega and objective for
+    both paths."""
+    rec, ij, v = _golden(5000)
+    w = synth.workload_ar1(p=5000, n=2000, seed=0)
+    with C.State(5000, precision, n_cap=2000) as st:
+        if precision == C.MIXED:
+            st.set_gram_mode(C.GRAM_FP64)  # same S as the oracle's
+        r = st.solve_device(dev(w["X"]), rec["lambda"], tol=rec["tol"], max_sweeps=200)
+        G = host(st.get_omega())
+        hist = st.history()
+    assert r.status == C.OK and r.kkt <= rec["tol"]
+    assert abs(r.objective - rec["objective"]) <= 1e-9 * abs(rec["objective"])
+    if precision == C.FP64:
+        assert r.sweeps == rec["sweeps"]
+        H = np.asarray(rec["history"])
+        assert hist.shape[0] == H.shape[0]
+        np.testing.assert_allclose(hist[:, 0], H[:, 0], rtol=1e-8, atol=1e-12)
+        np.testing.assert_allclose(hist[:, 1], H[:, 1], rtol=1e-8, atol=1e-12)
+        np.testing.assert_allclose(hist[:, 2], H[:, 2], rtol=1e-12)
+        # changed-pair counts are decided in FP64 on both sides with sums in
+        # different orders: a pair sitting within rounding of lambda may flip
+        assert np.abs(hist[:, 3] - H[:, 3]).max() <= 2
+    ref = np.zeros((5000, 5000))
+    ref[ij[:, 0], ij[:, 1]] = v
+    ref = ref + np.triu(ref, 1).T
+    scale = np.abs(ref).max()
+    assert np.abs(G - ref).max() <= 1e-6 * scale
+    # support: identical except entries that are tiny on either side
+    diff = (G != 0) != (ref != 0)
+    small = (np.abs(G) <= 1e-6 * scale) & (np.abs(ref) <= 1e-6 * scale)
+    assert not (diff & ~small).any()
