@@ -47,6 +47,8 @@ def parse_args(argv=None):
     ap.add_argument("--max-sweeps", type=int, default=500)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip FP64 arm, microbench, e2e and CPU baseline")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the default sweep kernel without the variant trials")
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle work for the CPU baseline sample")
     return ap.parse_args(argv)
@@ -127,18 +129,34 @@ def sweep_bytes(p: int, b: int, active_pairs: float) -> float:
     return (pairs * 5 * b + active_pairs * per_change + p * p * 3 * b + p * p * 2 * b)
 
 
-def launch_bytes(p: int, b: int, hist_rows) -> float:
-    return float(sum(sweep_bytes(p, b, h[3]) for h in hist_rows))
+def screened_sweep_bytes(p: int, b: int, changed: float) -> float:
+    """Algorithmic bytes of one screened sweep, b = element bytes: the row
+    pass reads W (start) and S_i and writes W (end) and V for every row, and
+    reads one S row per change on each side (2 per changed pair); the tile
+    pass reads W_ij, W_ji, w_ij, V_ij, V_ji for each of the p^2 / 2 pairs.
+    Candidate lists, sorting and the chain are O(candidates) and left out."""
+    return p * p * b * (4.0 + 2.5) + 2.0 * changed * p * b
 
 
-SWEEP_SOURCES = ("sweep.cu", "kernels.h", "common.cuh")
-SWEEP_PROFILE = os.path.join(ROOT, "profiles", "k_sweep_fp32_cluster_p5000.md")
+def launch_bytes(p: int, b: int, hist_rows, screened: bool = False) -> float:
+    f = screened_sweep_bytes if screened else sweep_bytes
+    return float(sum(f(p, b, h[3]) for h in hist_rows))
 
 
-def sweep_source_hash() -> str:
+KERNEL_SOURCES = {"screened": ("screened.cu", "kernels.h", "common.cuh"),
+                  "dense": ("sweep.cu", "kernels.h", "common.cuh")}
+KERNEL_PROFILES = {"screened": os.path.join(ROOT, "profiles", "k_screened_fp32_p5000.md"),
+                   "dense": os.path.join(ROOT, "profiles", "k_sweep_fp32_cluster_p5000.md")}
+
+
+def kernel_family(variant: str) -> str:
+    return "screened" if variant.startswith("screened") else "dense"
+
+
+def sweep_source_hash(family: str = "dense") -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in SWEEP_SOURCES:
+    for f in KERNEL_SOURCES[family]:
         with open(os.path.join(ROOT, "paper_2106_09382_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -149,14 +167,15 @@ def profiled_traffic(variant: str):
     summary (dram__bytes_read.sum + dram__bytes_write.sum of one launch,
     divided by its sweeps), if that summary was taken from the current kernel
     source and the same launch variant; else None."""
+    fam = kernel_family(variant)
     try:
-        with open(SWEEP_PROFILE) as f:
+        with open(KERNEL_PROFILES[fam]) as f:
             kv = dict(line.split(":", 1) for line in f.read().splitlines()
                       if line.startswith(("traffic_per_sweep_bytes:", "source_sha256:",
                                           "variant:")))
     except (OSError, ValueError):
         return None
-    if kv.get("source_sha256", "").strip() != sweep_source_hash():
+    if kv.get("source_sha256", "").strip() != sweep_source_hash(fam):
         return None
     if kv.get("variant", "").strip() != variant:
         return None
@@ -299,11 +318,13 @@ def run_ours(args):
         return times, recs
 
     def autotune(state):
-        """Pick the sweep kernel's rows-per-warp layout (results do not depend
-        on it) by the measured sweep-kernel time per sweep on warm-up solves."""
+        """Pick the sweep kernel (screened or dense) and the dense kernel's
+        rows-per-warp layout (results do not depend on either) by the
+        measured sweep-kernel time per sweep on warm-up solves."""
         trial = {}
-        for var, name in ((C.SWEEP_CLUSTER, "cluster"), (C.SWEEP_GRID, "grid")):
-            for rows in (32, 16, 8, 4):
+        for var, name in ((C.SWEEP_SCREENED, "screened"), (C.SWEEP_CLUSTER, "cluster"),
+                          (C.SWEEP_GRID, "grid")):
+            for rows in ((0,) if var == C.SWEEP_SCREENED else (32, 16, 8, 4)):
                 try:
                     state.set_sweep_variant(var)
                     state.set_rows_per_warp(rows)
@@ -315,14 +336,18 @@ def run_ours(args):
                                                  / max(1, sum(sw for _, sw in tim)))
         best = min(trial, key=trial.get)
         name, rows = best.split("/")
-        state.set_sweep_variant(C.SWEEP_CLUSTER if name == "cluster" else C.SWEEP_GRID)
+        state.set_sweep_variant({"screened": C.SWEEP_SCREENED, "cluster": C.SWEEP_CLUSTER,
+                                 "grid": C.SWEEP_GRID}[name])
         state.set_rows_per_warp(int(rows))
         return best, trial
 
     # ---------------- headline: mixed precision, data resident in HBM
     st = C.State(p, C.MIXED, n_cap=n, device=local)
     st.set_stream(stream)
-    rows_best, rows_trial = autotune(st)
+    if args.no_autotune:
+        rows_best, rows_trial = "screened/0", {}
+    else:
+        rows_best, rows_trial = autotune(st)
     for _ in range(args.warmup):
         st.solve_device(X, lam, tol=tol, max_sweeps=args.max_sweeps)
     clocks = ClockSampler(local)
@@ -343,7 +368,8 @@ def run_ours(args):
     ms32, sw32 = tim_last[0]
     h32 = hist_last[:sw32]
     hbm_peak, peak_src = load_peaks()
-    bytes32 = launch_bytes(p, 4, h32)
+    screened = rows_best.startswith("screened")
+    bytes32 = launch_bytes(p, 4, h32, screened)
     achieved = bytes32 / (ms32 * 1e-3) / 1e9
     updates = p * (p + 1) / 2
     ups = sw32 * updates / (ms32 * 1e-3)
@@ -356,11 +382,13 @@ def run_ours(args):
                                    "variant x sweeps of this launch" if tps is not None else
                                    "no ncu capture of the current kernel source / variant"),
                 "variant": vname,
-                "kernel": "k_sweep<float> (FP32 sweeps of the mixed solve)",
+                "kernel": ("k_screened<float>" if screened else "k_sweep<float>")
+                          + " (FP32 sweeps of the mixed solve)",
                 "peak_source": "%s hbm_gbs (STREAM-style copy)" % peak_src,
                 "algorithmic_bytes_per_launch": bytes32, "launch_ms": ms32, "sweeps": sw32,
-                "regime": "colour-step latency chain (%d dependent steps per sweep)"
-                          % (p + (p % 2) - 1)}
+                "regime": ("candidate chain + p^2 row / tile passes" if screened else
+                           "colour-step latency chain (%d dependent steps per sweep)"
+                           % (p + (p % 2) - 1))}
 
     out = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
@@ -385,7 +413,7 @@ def run_ours(args):
         # ---------------- plain FP64 GPU PCD, same data
         st64 = C.State(p, C.FP64, n_cap=n, device=local)
         st64.set_stream(stream)
-        rows64, trial64 = autotune(st64)
+        rows64, trial64 = ("screened/0", {}) if args.no_autotune else autotune(st64)
         t64, rec64 = timed_solves(st64, max(1, min(args.steps, 2)))
         r64, tim64, hist64 = rec64[-1]
         ms64, sw64 = tim64[0]
@@ -393,7 +421,9 @@ def run_ours(args):
                        "kkt": r64["kkt"], "objective": r64["objective"], "launch_ms": tim64,
                        "updates_per_s": sw64 * updates / (ms64 * 1e-3),
                        "autotune": {"choice": rows64, "ms_per_sweep": trial64},
-                       "sweep_GBps": launch_bytes(p, 8, hist64[:sw64]) / (ms64 * 1e-3) / 1e9}
+                       "sweep_GBps": launch_bytes(p, 8, hist64[:sw64],
+                                                  rows64.startswith("screened"))
+                       / (ms64 * 1e-3) / 1e9}
         out["mixed_vs_fp64_speedup"] = out["fp64"]["seconds"] / value
         fp64_sweeps = r64["sweeps"]
         # ---------------- full-update microbench: nearly every pair changes

@@ -75,13 +75,26 @@ extern "C" {
                                   FP32 accumulation in tensor memory */
 
 /* Sweep-kernel variant (concord_set_sweep_variant). */
-#define CONCORD_SWEEP_AUTO 0     /* FP32 sweeps: cluster when p fits, else grid;
-                                    FP64 sweeps: grid */
-#define CONCORD_SWEEP_GRID 1     /* persistent cooperative grid, one CTA per SM;
+#define CONCORD_SWEEP_AUTO 0     /* screened sweeps; a sweep whose candidate
+                                    pairs overflow the screened kernel's lists
+                                    runs on the dense kernel (_DENSE layout) */
+#define CONCORD_SWEEP_GRID 1     /* dense: every pair of every colour step on a
+                                    persistent cooperative grid, one CTA per SM;
                                     partners swap W scalars through an L2 ring */
-#define CONCORD_SWEEP_CLUSTER 2  /* one thread-block cluster (up to 16 SMs);
-                                    partners swap W scalars through distributed
-                                    shared memory (lowest latency per colour) */
+#define CONCORD_SWEEP_CLUSTER 2  /* dense: one thread-block cluster (up to 16
+                                    SMs); partners swap W scalars through
+                                    distributed shared memory (lowest latency
+                                    per colour) */
+#define CONCORD_SWEEP_SCREENED 3 /* screened: only the pairs that can change
+                                    (w_ij != 0 or |W_ij + W_ji| > lambda at the
+                                    sweep start) are visited, in colour-step
+                                    order, by one thread; every other pair is
+                                    verified to stay at zero afterwards, and the
+                                    sweep is redone with the pairs that fail.
+                                    Same iterates as the dense kernels.  Falls
+                                    back to the dense kernel like _AUTO. */
+#define CONCORD_SWEEP_DENSE 4    /* dense, layout chosen by precision: FP32
+                                    cluster when p fits, else grid; FP64 grid */
 
 /* Stopping rule of concord_run / concord_solve*. */
 #define CONCORD_STOP_KKT 0    /* KKT residual <= tol (absolute, S units) */
@@ -104,8 +117,9 @@ typedef struct concord_result {
     double seconds;        /* device time of the call (CUDA events)            */
     int timeout_vertex;    /* on CONCORD_E_TIMEOUT: vertex whose wait ran out  */
     int timeout_step;      /*                        and the colour step        */
-    int reserved0;
-    int reserved1;
+    int screen_redos;      /* screened sweeps redone after a pair outside the
+                              candidates failed the verification */
+    int dense_sweeps;      /* sweeps handed from the screened to the dense kernel */
 } concord_result;
 
 /* KKT residual (absolute, S units), with W = Omega S and G = W + W^T:
@@ -255,8 +269,10 @@ int concord_get_history(concord_state *st, double *hist_host, int max_rows, int 
  * of the last concord_sweep / concord_run / concord_solve_* (CUDA events
  * recorded on the state's stream around the launch): launch_ms[q] in
  * milliseconds and launch_sweeps[q] the sweeps it ran, for q < max_launches
- * (MIXED runs launch twice: FP32 sweeps, then FP64 polishing).  Either array
- * may be NULL; *n_launches receives the number of launches (<= 4 recorded).
+ * (MIXED runs launch at least twice: FP32 sweeps, then FP64 polishing; a
+ * screened run adds one dense launch per sweep handed to the dense kernel,
+ * and the screened launch after it).  Either array
+ * may be NULL; *n_launches receives the number of launches (<= 16 recorded).
  */
 int concord_get_timing(concord_state *st, double *launch_ms, int *launch_sweeps,
                        int max_launches, int *n_launches);
@@ -266,15 +282,20 @@ int concord_get_timing(concord_state *st, double *launch_ms, int *launch_sweeps,
 unsigned long long concord_kernel_launches(void);
 
 /*
- * concord_set_sweep_variant -- CONCORD_SWEEP_AUTO (default), _GRID or
- * _CLUSTER.  The variants compute the same iterates (bit for bit); they trade
- * latency per colour step (cluster) against memory bandwidth (grid, all SMs).
+ * concord_set_sweep_variant -- CONCORD_SWEEP_AUTO (default), _GRID,
+ * _CLUSTER, _SCREENED or _DENSE.  The variants compute the same iterates
+ * (bit for bit); the dense ones trade latency per colour step (cluster)
+ * against memory bandwidth (grid, all SMs); the screened one skips the pairs
+ * that stay at zero, which wins whenever few pairs change per sweep.
  * _CLUSTER fails with CONCORD_E_ARG if p exceeds what one cluster holds
  * (cluster size x 512 rows).  Explicit settings (this one and
  * concord_set_rows_per_warp) apply to sweeps in the state's working
- * precision; the FP64 polishing sweeps of a MIXED state use the FP64
- * defaults.  concord_get_sweep_variant reports the variant of the last
- * launch and the largest cluster size found (0 = none).
+ * precision; the FP64 polishing sweeps of a MIXED state use the defaults.
+ * concord_get_sweep_variant reports the variant of the last launch and the
+ * largest cluster size found (0 = none).  The screened kernel allocates its
+ * scratch (two p x p matrices of the FP64 width and candidate lists of
+ * max(16 p, 65536) pairs, at most all pairs, with up to max(8 x that, 4M)
+ * correction terms) on first use.
  */
 int concord_set_sweep_variant(concord_state *st, int variant);
 int concord_get_sweep_variant(concord_state *st, int *variant, int *cluster_size);

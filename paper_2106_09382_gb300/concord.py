@@ -25,7 +25,7 @@ F64, F32 = 0, 1
 PREP_NONE, PREP_CENTER, PREP_STANDARDIZE = 0, 1, 2
 GRAM_FP64, GRAM_FP32, GRAM_TF32X3 = 0, 1, 2
 STOP_KKT, STOP_DELTA = 0, 1
-SWEEP_AUTO, SWEEP_GRID, SWEEP_CLUSTER = 0, 1, 2
+SWEEP_AUTO, SWEEP_GRID, SWEEP_CLUSTER, SWEEP_SCREENED, SWEEP_DENSE = 0, 1, 2, 3, 4
 
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "E_ARG", -2: "E_NONPOS_DIAG",
                 -3: "E_NONFINITE", -4: "E_CUDA", -5: "E_TIMEOUT", -6: "E_NOMEM",
@@ -39,7 +39,7 @@ class ConcordResult(ctypes.Structure):
                 ("delta", ctypes.c_double), ("lam", ctypes.c_double),
                 ("active_pairs", ctypes.c_longlong), ("seconds", ctypes.c_double),
                 ("timeout_vertex", ctypes.c_int), ("timeout_step", ctypes.c_int),
-                ("reserved0", ctypes.c_int), ("reserved1", ctypes.c_int)]
+                ("screen_redos", ctypes.c_int), ("dense_sweeps", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}

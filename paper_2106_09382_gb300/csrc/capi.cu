@@ -40,7 +40,7 @@ int fail(int code, const char* fmt, ...) {
 
 constexpr int kMailboxDepth = kDepth;
 constexpr int kHistCap = 8192;
-constexpr int kMaxTimedLaunches = 4;
+constexpr int kMaxTimedLaunches = 16;
 constexpr int kDefaultPollNs = 0;
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
@@ -89,6 +89,11 @@ struct concord_state {
   int poll_ns = -1;       // back-off between mailbox polls (-1: default)
   int cluster_size = -1;  // largest launchable cluster (-1: not queried yet)
   int last_variant = 0;
+  // screened-sweep scratch (allocated on first use): W after the sweep, W at
+  // each pair's visit, candidate lists and per-candidate work arrays
+  void *Wb = nullptr, *V = nullptr, *scr = nullptr;
+  int nc_cap = 0, term_cap = 0;
+  int screened_grid = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaEvent_t lev[2 * kMaxTimedLaunches] = {};
   double launch_ms[kMaxTimedLaunches] = {};
@@ -123,14 +128,15 @@ struct RunOut {
   double kkt = 0, obj = 0, delta = 0, active = 0;
   int to_vertex = -1, to_step = -1;
   bool stalled = false;
+  int redos = 0, dense_sweeps = 0;  // screened runs
 };
 
 // One persistent launch: n_sweeps outer iterations (fewer if the stopping
 // rule holds first), or only the objective / KKT pass when kkt_only.
 template <typename T>
-int launch_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* omdiag64, double lambda,
-               double tol, int stop_rule, int n_sweeps, int kkt_only, int hist_offset, int stall_stop,
-               RunOut* out) {
+int launch_dense(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* omdiag64,
+                 double lambda, double tol, int stop_rule, int n_sweeps, int kkt_only,
+                 int hist_offset, int stall_stop, RunOut* out) {
   const int p = st->p;
   const bool mixed = sizeof(T) == 4;
   // `row_warps` warps of each CTA own rows (one row per lane, up to `R` rows
@@ -142,9 +148,10 @@ int launch_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* om
   // settings apply to sweeps in the state's working precision; the FP64
   // polishing sweeps of a mixed state keep the FP64 defaults.
   const bool own = mixed == is_mixed(st);
-  const int variant = (own && st->sweep_variant != CONCORD_SWEEP_AUTO)
-                          ? st->sweep_variant
-                          : (mixed ? CONCORD_SWEEP_CLUSTER : CONCORD_SWEEP_GRID);
+  const bool layout_set = own && (st->sweep_variant == CONCORD_SWEEP_GRID ||
+                                  st->sweep_variant == CONCORD_SWEEP_CLUSTER);
+  const int variant = layout_set ? st->sweep_variant
+                                 : (mixed ? CONCORD_SWEEP_CLUSTER : CONCORD_SWEEP_GRID);
   bool cluster = false;
   int grid = 0, row_warps = 0, R = 0;
   int want = (own && st->rows_per_warp > 0) ? st->rows_per_warp : 32;
@@ -285,6 +292,267 @@ int launch_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* om
   return CONCORD_OK;
 }
 
+// Screened-sweep scratch, allocated on first use: Wb and V (p x ld of the
+// FP64 width, so both precisions fit) and one block holding the candidate
+// lists and per-candidate arrays, carved below.
+struct ScreenLayout {
+  size_t ctr, cand0, cand1, fail, cnt_c, off_c, cur_c, cnt_r, off_r, cur_r, nd_i, nd_j, nd_c,
+      nd_pi, nd_pj, row_ent, term_ptr, term_pred, term_s, nd_rec, nd_delta, nd_new, nd_d2, jac,
+      diag_old, omdiag_old, total;
+};
+
+ScreenLayout screen_layout(int p, int P, int nc, int tc) {
+  ScreenLayout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off += (bytes + 255) / 256 * 256;
+    return at;
+  };
+  L.ctr = take(sizeof(int) * kCtrs);
+  L.cand0 = take(sizeof(int2) * (size_t)nc);
+  L.cand1 = take(sizeof(int2) * (size_t)nc);
+  L.fail = take(sizeof(int2) * (size_t)nc);
+  L.cnt_c = take(sizeof(int) * (size_t)(P + 1));
+  L.off_c = take(sizeof(int) * (size_t)(P + 1));
+  L.cur_c = take(sizeof(int) * (size_t)(P + 1));
+  L.cnt_r = take(sizeof(int) * (size_t)(p + 1));
+  L.off_r = take(sizeof(int) * (size_t)(p + 1));
+  L.cur_r = take(sizeof(int) * (size_t)(p + 1));
+  L.nd_i = take(sizeof(int) * (size_t)nc);
+  L.nd_j = take(sizeof(int) * (size_t)nc);
+  L.nd_c = take(sizeof(int) * (size_t)nc);
+  L.nd_pi = take(sizeof(int) * (size_t)nc);
+  L.nd_pj = take(sizeof(int) * (size_t)nc);
+  L.row_ent = take(sizeof(int) * 2 * (size_t)nc);
+  L.term_ptr = take(sizeof(int) * ((size_t)nc + 1));
+  L.term_pred = take(sizeof(int) * (size_t)tc);
+  L.term_s = take(sizeof(double) * (size_t)tc);
+  L.nd_rec = take(sizeof(double) * 4 * (size_t)nc);
+  L.nd_delta = take(sizeof(double) * (size_t)nc);
+  L.nd_new = take(sizeof(double) * (size_t)nc);
+  L.nd_d2 = take(sizeof(double) * (size_t)nc);
+  L.jac = take(sizeof(int) * kJacMax);
+  L.diag_old = take(sizeof(double) * (size_t)p);
+  L.omdiag_old = take(sizeof(double) * (size_t)p);
+  L.total = off;
+  return L;
+}
+
+int ensure_screen(concord_state* st) {
+  if (st->scr) return CONCORD_OK;
+  const int p = st->p;
+  const long long pairs = (long long)p * (p - 1) / 2;
+  // every pair when there are at most 64k of them, else 16 per row
+  long long nc = 16LL * p;
+  if (nc < 65536) nc = 65536;
+  if (nc > pairs) nc = pairs > 0 ? pairs : 1;
+  st->nc_cap = (int)nc;
+  // a row with k candidates carries k (k - 1) / 2 correction terms
+  st->term_cap = (int)(8 * nc > (1 << 22) ? 8 * nc : (1 << 22));
+  const ScreenLayout L = screen_layout(p, st->P, st->nc_cap, st->term_cap);
+  const size_t mat = (size_t)p * st->ld * sizeof(double);
+  CK(cudaMalloc(&st->Wb, mat));
+  CK(cudaMalloc(&st->V, mat));
+  CK(cudaMalloc(&st->scr, L.total));
+  CK(cudaMemsetAsync(st->Wb, 0, mat, st->stream));
+  CK(cudaMemsetAsync(st->V, 0, mat, st->stream));
+  int occ = 0;
+  CK(screened_occupancy(is_mixed(st), &occ));
+  if (occ < 1) return fail(CONCORD_E_OCCUPANCY, "screened sweep kernel cannot be resident");
+  st->screened_grid = st->sms;  // one CTA per SM
+  return CONCORD_OK;
+}
+
+template <typename T>
+ScreenWork<T> screen_work(concord_state* st) {
+  const ScreenLayout L = screen_layout(st->p, st->P, st->nc_cap, st->term_cap);
+  char* b = (char*)st->scr;
+  ScreenWork<T> w;
+  w.ctr = (int*)(b + L.ctr);
+  w.cand[0] = (int2*)(b + L.cand0);
+  w.cand[1] = (int2*)(b + L.cand1);
+  w.fail = (int2*)(b + L.fail);
+  w.cnt_c = (int*)(b + L.cnt_c);
+  w.off_c = (int*)(b + L.off_c);
+  w.cur_c = (int*)(b + L.cur_c);
+  w.cnt_r = (int*)(b + L.cnt_r);
+  w.off_r = (int*)(b + L.off_r);
+  w.cur_r = (int*)(b + L.cur_r);
+  w.nd_i = (int*)(b + L.nd_i);
+  w.nd_j = (int*)(b + L.nd_j);
+  w.nd_c = (int*)(b + L.nd_c);
+  w.nd_pi = (int*)(b + L.nd_pi);
+  w.nd_pj = (int*)(b + L.nd_pj);
+  w.row_ent = (int*)(b + L.row_ent);
+  w.term_ptr = (int*)(b + L.term_ptr);
+  w.term_pred = (int*)(b + L.term_pred);
+  w.term_s = (T*)(b + L.term_s);
+  w.nd_rec = (T*)(b + L.nd_rec);
+  w.nd_delta = (T*)(b + L.nd_delta);
+  w.nd_new = (T*)(b + L.nd_new);
+  w.nd_d2 = (T*)(b + L.nd_d2);
+  w.jac = (int*)(b + L.jac);
+  w.diag_old = (T*)(b + L.diag_old);
+  w.omdiag_old = (double*)(b + L.omdiag_old);
+  w.nc_cap = st->nc_cap;
+  w.term_cap = st->term_cap;
+  w.fail_cap = st->nc_cap;
+  return w;
+}
+
+// One persistent launch of the screened sweep kernel; out->status_code is
+// the kernel's status (kStatusDense: hand the next sweep to the dense kernel).
+template <typename T>
+int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* omdiag64,
+                        double lambda, double tol, int stop_rule, int n_sweeps, int kkt_only,
+                        int hist_offset, int stall_stop, RunOut* out, int* code) {
+  int rc = ensure_screen(st);
+  if (rc != CONCORD_OK) return rc;
+  const ScreenLayout L = screen_layout(st->p, st->P, st->nc_cap, st->term_cap);
+  CK(cudaMemsetAsync(st->barrier, 0, sizeof(unsigned), st->stream));
+  CK(cudaMemsetAsync(st->abort_info, 0, 3 * sizeof(int), st->stream));
+  CK(cudaMemsetAsync((char*)st->scr + L.ctr, 0, sizeof(int) * kCtrs, st->stream));
+  ScreenArgs<T> a;
+  memset(&a, 0, sizeof a);
+  a.p = st->p;
+  a.P = st->P;
+  a.ld = st->ld;
+  a.W = W;
+  a.Wb = (T*)st->Wb;
+  a.V = (T*)st->V;
+  a.Om = Om;
+  a.S = S;
+  a.sdiag = sdiagT;
+  a.sdiag64 = st->sdiag64;
+  a.omdiag64 = omdiag64;
+  a.w = screen_work<T>(st);
+  a.barrier = st->barrier;
+  a.wait.abort = st->abort_info;
+  a.wait.info = st->abort_info + 1;
+  a.wait.timeout_ns = (uint64_t)(st->timeout_s * 1e9);
+  a.partials = st->partials;
+  a.hist = st->hist + (size_t)hist_offset * kHist;
+  a.hist_len = kHistCap - hist_offset;
+  a.result = st->result;
+  a.lambda = lambda;
+  a.tol = tol;
+  a.delta_tol = 1e-5;
+  a.stop_rule = stop_rule;
+  a.n_sweeps = n_sweeps;
+  a.kkt_only = kkt_only;
+  a.stall_stop = stall_stop;
+  a.max_redo = 8;
+  st->last_variant = CONCORD_SWEEP_SCREENED;
+
+  const int slot_ev = st->n_launch < kMaxTimedLaunches ? st->n_launch : -1;
+  if (slot_ev >= 0) CK(cudaEventRecord(st->lev[2 * slot_ev], st->stream));
+  CK(launch_screened(a, st->screened_grid, st->stream));
+  if (slot_ev >= 0) CK(cudaEventRecord(st->lev[2 * slot_ev + 1], st->stream));
+  CK(cudaMemcpyAsync(st->h_result, st->result, kRes * sizeof(double), cudaMemcpyDeviceToHost,
+                     st->stream));
+  CK(cudaMemcpyAsync(st->h_abort, st->abort_info, 3 * sizeof(int), cudaMemcpyDeviceToHost,
+                     st->stream));
+  CK(cudaStreamSynchronize(st->stream));
+  CK(cudaGetLastError());
+  const double* r = st->h_result;
+  out->sweeps = (int)r[kResSweeps];
+  out->kkt = r[kResKkt];
+  out->obj = r[kResObj];
+  out->delta = r[kResDelta];
+  out->active = r[kResActive];
+  out->first_delta = (int)r[kResFirstDelta];
+  out->redos = (int)r[kResRedo];
+  if (slot_ev >= 0) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, st->lev[2 * slot_ev], st->lev[2 * slot_ev + 1]));
+    st->launch_ms[slot_ev] = ms;
+    st->launch_sweeps[slot_ev] = out->sweeps;
+    st->n_launch = slot_ev + 1;
+  }
+  *code = (int)r[kResStatus];
+  if (st->h_abort[0] != 0) {
+    out->status = CONCORD_E_TIMEOUT;
+    out->to_vertex = st->h_abort[1];
+    out->to_step = st->h_abort[2];
+    return fail(CONCORD_E_TIMEOUT, "device wait ran out (phase %d)", st->h_abort[2]);
+  }
+  out->stalled = *code == 4;
+  out->status = (*code == 0) ? CONCORD_OK
+                : (*code == 1 || *code == 4 || *code == kStatusDense) ? CONCORD_NOT_CONVERGED
+                : (*code == 2) ? CONCORD_E_NONFINITE
+                               : CONCORD_E_TIMEOUT;
+  if (out->status == CONCORD_E_NONFINITE)
+    return fail(CONCORD_E_NONFINITE, "non-finite objective or KKT residual after sweep %d",
+                out->sweeps);
+  return CONCORD_OK;
+}
+
+// Sweeps in the state's chosen variant.  Screened launches run until the
+// stopping rule, the sweep budget, or a sweep whose candidates overflow the
+// lists; such a sweep (and any following sweep that still changes more than
+// half the list capacity) runs on the dense kernel, then screening resumes.
+template <typename T>
+int launch_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* omdiag64, double lambda,
+               double tol, int stop_rule, int n_sweeps, int kkt_only, int hist_offset, int stall_stop,
+               RunOut* out) {
+  const bool mixed = sizeof(T) == 4;
+  const bool own = mixed == is_mixed(st);
+  const int sv = st->sweep_variant;
+  const bool screened = st->fault_vertex < 0 &&
+                        (!own || sv == CONCORD_SWEEP_AUTO || sv == CONCORD_SWEEP_SCREENED);
+  if (!screened)
+    return launch_dense<T>(st, S, W, Om, sdiagT, omdiag64, lambda, tol, stop_rule, n_sweeps,
+                           kkt_only, hist_offset, stall_stop, out);
+  int done = 0, first_delta = 0, redos = 0, dense = 0;
+  RunOut o;
+  for (;;) {
+    int code = 0;
+    RunOut q;
+    int rc = launch_screened_run<T>(st, S, W, Om, sdiagT, omdiag64, lambda, tol, stop_rule,
+                                    n_sweeps - done, kkt_only, hist_offset + done, stall_stop, &q,
+                                    &code);
+    if (q.first_delta && !first_delta) first_delta = done + q.first_delta;
+    done += q.sweeps;
+    redos += q.redos;
+    if (q.sweeps > 0 || kkt_only || code != kStatusDense) o = q;
+    o.sweeps = done;
+    o.first_delta = first_delta;
+    o.redos = redos;
+    o.dense_sweeps = dense;
+    if (rc != CONCORD_OK || code != kStatusDense) {
+      *out = o;
+      if (rc == CONCORD_OK) out->status = q.status;
+      return rc;
+    }
+    // dense sweeps until few enough pairs change
+    for (;;) {
+      if (done >= n_sweeps) {
+        *out = o;
+        out->status = CONCORD_NOT_CONVERGED;
+        return CONCORD_OK;
+      }
+      RunOut dq;
+      rc = launch_dense<T>(st, S, W, Om, sdiagT, omdiag64, lambda, tol, stop_rule, 1, 0,
+                           hist_offset + done, 0, &dq);
+      if (dq.first_delta && !first_delta) first_delta = done + dq.first_delta;
+      done += dq.sweeps;
+      dense += dq.sweeps;
+      o = dq;
+      o.sweeps = done;
+      o.first_delta = first_delta;
+      o.redos = redos;
+      o.dense_sweeps = dense;
+      if (rc != CONCORD_OK || dq.status != CONCORD_NOT_CONVERGED || dq.stalled ||
+          done >= n_sweeps) {
+        *out = o;
+        return rc;
+      }
+      if (dq.active < 0.5 * st->nc_cap) break;
+    }
+  }
+}
+
 void fill_result(concord_result* res, const RunOut& o, int sweeps, int sweeps32, int first_delta,
                  double lambda, double seconds) {
   if (!res) return;
@@ -301,6 +569,8 @@ void fill_result(concord_result* res, const RunOut& o, int sweeps, int sweeps32,
   res->seconds = seconds;
   res->timeout_vertex = o.to_vertex;
   res->timeout_step = o.to_step;
+  res->screen_redos = o.redos;
+  res->dense_sweeps = o.dense_sweeps;
 }
 
 // mixed: FP32 iterate -> FP64 copies (Omega with its FP64 diagonal; W rebuilt
@@ -376,6 +646,8 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
   float ms = 0;
   CK(cudaEventElapsedTime(&ms, st->ev0, st->ev1));
   const int fd = o1.first_delta ? o1.first_delta : (o2.first_delta ? o1.sweeps + o2.first_delta : 0);
+  o2.redos += o1.redos;
+  o2.dense_sweeps += o1.dense_sweeps;
   fill_result(res, o2, o1.sweeps + o2.sweeps, o1.sweeps, fd, lambda, ms * 1e-3);
   return rc != CONCORD_OK ? rc : o2.status;
 }
@@ -589,7 +861,7 @@ int concord_destroy(concord_state* st) {
   if (!st) return CONCORD_OK;
   cudaSetDevice(st->device);
   if (st->stream) cudaStreamSynchronize(st->stream);
-  void* dev[] = {st->sd1_64, st->sd2_64, st->mbox, st->barrier, st->abort_info, st->flag, st->lmax, st->partials,
+  void* dev[] = {st->Wb, st->V, st->scr, st->sd1_64, st->sd2_64, st->mbox, st->barrier, st->abort_info, st->flag, st->lmax, st->partials,
                  st->hist, st->result, st->mean, st->inv_scale, st->Z, st->Xstage, st->zt_hi,
                  st->zt_lo, st->sdiag64, st->sdiagT, st->omdiag64, st->S64, st->W64, st->Om64};
   for (void* d : dev)
@@ -749,7 +1021,7 @@ int concord_set_poll_sleep(concord_state* st, int ns) {
 
 int concord_set_sweep_variant(concord_state* st, int variant) {
   if (!st) return fail(CONCORD_E_ARG, "state is NULL");
-  if (variant < 0 || variant > 2) return fail(CONCORD_E_ARG, "variant must be 0, 1 or 2");
+  if (variant < 0 || variant > 4) return fail(CONCORD_E_ARG, "variant must be 0..4 (CONCORD_SWEEP_*)");
   st->sweep_variant = variant;
   return CONCORD_OK;
 }

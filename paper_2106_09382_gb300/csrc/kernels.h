@@ -17,8 +17,8 @@ void note_launches(unsigned n);
 unsigned long long launches_so_far();
 
 constexpr int kSweepThreads = 512;   // the sweep kernel's block size
-constexpr int kPendCap = 8;
-constexpr int kDepth = 16;           // mailbox ring depth (a power of two, >= 4)          // pending row updates kept per row before a flush
+constexpr int kPendCap = 8;          // pending row updates kept per row before a flush
+constexpr int kDepth = 16;           // mailbox ring depth (a power of two, >= 4)
 
 // Dynamic shared memory of the sweep kernel: pending lists of every owned
 // row; the cluster variant adds its mailbox ring (kDepth x rows x value
@@ -37,7 +37,7 @@ constexpr int kParts = 8;
 
 // Final result block written by CTA 0.
 constexpr int kResSweeps = 0, kResKkt = 1, kResObj = 2, kResDelta = 3, kResActive = 4,
-              kResFirstDelta = 5, kResStatus = 6;
+              kResFirstDelta = 5, kResStatus = 6, kResRedo = 7;  // kResRedo: screened only
 constexpr int kRes = 8;
 constexpr int kHist = 4;  // per sweep: delta, kkt, objective, active pairs
 
@@ -77,6 +77,72 @@ cudaError_t launch_sweep(const SweepArgs<float>& a, int grid, int block, bool cl
 cudaError_t sweep_occupancy(bool mixed, int block, int* blocks_per_sm);
 // Largest launchable cluster (power of two <= 16; 0 if none).
 cudaError_t sweep_cluster_size(bool mixed, int block, int row_warps, int rows_per_warp, int* cs);
+
+// ---- screened sweep (screened.cu)
+// One persistent cooperative launch of Algorithm 1's outer iterations that
+// visits only the candidate pairs of each sweep (the pairs that can change)
+// and verifies every other pair afterwards; see screened.cu.
+constexpr int kScreenThreads = 512;
+constexpr int kSeqNodes = 256;    // candidate pairs staged per chunk of the chain pass
+constexpr int kSeqTerms = 2048;   // correction terms staged per chunk
+constexpr int kSeqRing = 8192;    // most recent changes kept in shared memory (power of two)
+constexpr int kRowList = 64;      // changes of one row staged per warp in the row pass
+constexpr int kCtrCand = 0;       // ctr[0], ctr[1]: lengths of the two candidate lists
+constexpr int kCtrFail = 2;       // failing pairs found by the verification
+constexpr int kCtrTerms = 3;      // correction terms of the current candidate set
+constexpr int kCtrs = 8;
+constexpr int kJacMax = 64;       // fixed-point iterations of the chain before the serial walk
+constexpr int kStatusDense = 5;   // result status: the next sweep needs the dense kernel
+
+template <typename T>
+struct ScreenWork {
+  int* ctr;                 // kCtrs counters (zeroed before the launch)
+  int2* cand[2];            // candidate pairs (i < j): current sweep / next sweep
+  int2* fail;               // non-candidate pairs that failed the verification
+  int *cnt_c, *off_c, *cur_c;  // [P + 1] colour buckets: counts, offsets, cursors
+  int *cnt_r, *off_r, *cur_r;  // [p + 1] row buckets
+  int *nd_i, *nd_j, *nd_c;     // candidates sorted by colour step (then by i)
+  int *nd_pi, *nd_pj;          // position of each candidate in the lists of rows i and j
+  int* row_ent;             // [2 nc_cap] candidates of each row, in step order
+  int* term_ptr;            // [nc_cap + 1] first correction term of each candidate
+  int* term_pred;           // [term_cap] earlier candidate whose change the term carries
+  T* term_s;                // [term_cap] the S entry it multiplies
+  T* nd_rec;                // [4 nc_cap] per candidate: W_ij, W_ji, w_ij at the sweep start, s_ii + s_jj
+  T *nd_delta, *nd_new;     // change and new value of each candidate
+  T* nd_d2;                 // [nc_cap] second buffer of the fixed-point iteration
+  int* jac;                 // [kJacMax] candidates whose change moved, per iteration
+  T* diag_old;              // [p] diagonal before the sweep (for a redo)
+  double* omdiag_old;       // [p] FP64 diagonal before the sweep (mixed precision)
+  int nc_cap, term_cap, fail_cap;
+};
+
+template <typename T>
+struct ScreenArgs {
+  int p, P, ld;
+  T* W;                     // p x ld, W = Omega S (in and out)
+  T* Wb;                    // p x ld scratch: W after the sweep
+  T* V;                     // p x ld scratch: W_ij when pair (i, j) is visited
+  T* Om;                    // p x ld, Omega
+  const T* S;               // p x ld, S (padding columns zero)
+  const T* sdiag;           // s_ii in T
+  const double* sdiag64;    // s_ii in FP64
+  double* omdiag64;         // FP64 diagonal of Omega (mixed precision only)
+  ScreenWork<T> w;
+  unsigned* barrier;        // zeroed before the launch
+  WaitCtl wait;
+  double* partials;         // gridDim.x x kParts
+  double* hist;             // hist_len x kHist
+  int hist_len;
+  double* result;           // kRes
+  double lambda, tol, delta_tol;
+  int stop_rule, n_sweeps, kkt_only, stall_stop;
+  int max_redo;             // verification rounds per sweep before giving up (status 5)
+};
+
+size_t screened_dyn_smem(bool mixed);
+cudaError_t launch_screened(const ScreenArgs<double>& a, int grid, cudaStream_t st);
+cudaError_t launch_screened(const ScreenArgs<float>& a, int grid, cudaStream_t st);
+cudaError_t screened_occupancy(bool mixed, int* blocks_per_sm);
 
 cudaError_t launch_refresh_w(const double* Om, const double* S, double* W, int p, int ld, int sms,
                              cudaStream_t st);

@@ -1,0 +1,1008 @@
+// Screened CONCORD-PCD sweep: the same iterates as Algorithm 1, computed by
+// visiting only the pairs that can change.
+//
+// Why: in a colour step a pair (i, j) reads W_ij and W_ji as they stand after
+// every earlier change of rows i and j in the sweep (Eq. 3 in W form), and
+// nothing else (Lemma 1).  A pair whose soft-threshold stays at zero from
+// w_ij = 0 changes nothing, so it can be skipped without affecting any other
+// pair.  Near a solution only the support (a few per row) changes; the
+// remaining ~p^2/2 pairs are zero and stay zero.  The colour loop then turns
+// into a short dependency chain through the changed pairs, which one thread
+// walks at register speed instead of the whole grid paying one exchange
+// latency per colour step.
+//
+// One sweep (all CTAs, grid barriers between phases):
+//   screen   every pair with w_ij != 0 or |W_ij + W_ji| > lambda at the sweep
+//            start is a candidate (fused into the previous sweep's KKT pass);
+//   build    candidates sorted by the colour step that visits them
+//            (closed form of the circle method), per-row candidate lists in
+//            step order, and for each candidate the S entries that carry the
+//            earlier changes of its two rows into W_ij and W_ji;
+//   chain    one thread evaluates Eq. 3 for the candidates in step order:
+//            W_ij = W_ij(start) + sum over earlier changes (i, u, d) of d S_uj
+//            (the lazily applied row updates, in step order);
+//   rows     per row: W after the colour steps, the diagonal root (Eq. 2),
+//            W += dw S_i, and V_ij = W_ij at the step that visits (i, j);
+//   verify   every non-candidate pair must satisfy |V_ij + V_ji| <= lambda,
+//            i.e. Eq. 3 leaves it at zero given the candidates' changes.  If
+//            one does not, the sweep is undone, the failing pairs join the
+//            candidates and the sweep is redone; the verification pass also
+//            computes the objective and KKT residual and screens the next
+//            sweep.
+// The floating-point operations per pair are those of the dense sweep kernel
+// (same FMA chains in the same order), so both kernels produce the same
+// iterates.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace concord {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Colour step (0-based) at which the circle method pairs i < j (Section 3.2,
+// Algorithm 1): solving the closed form of cm_partner for the colour gives
+// 2c = -(i + j) (mod P) for i >= 1, and c = P - j for i = 0.  P is odd, so
+// halving mod P is n / 2 for even n and (n + P) / 2 for odd n.
+__device__ __forceinline__ int pair_step(int i, int j, int P) {
+  if (i == 0) return P - j;
+  int s = i + j;  // i, j <= P, so s < 2P
+  if (s >= P) s -= P;
+  if (s >= P) s -= P;
+  const int neg = s == 0 ? 0 : P - s;
+  return (neg & 1) ? (neg + P) >> 1 : neg >> 1;
+}
+
+template <typename T>
+__device__ __forceinline__ T soft(T x, T tau) {
+  T a = fabs(x) - tau;
+  if (!(a > (T)0)) return (T)0;
+  return x > (T)0 ? a : -a;
+}
+
+__device__ __forceinline__ float fma_t(float d, float s, float w) { return fmaf(d, s, w); }
+__device__ __forceinline__ double fma_t(double d, double s, double w) { return ::fma(d, s, w); }
+
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using V = float4;
+  static constexpr int N = 4;
+  __device__ static void split(const V& v, float* o) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+  __device__ static V join(const float* o) { return make_float4(o[0], o[1], o[2], o[3]); }
+};
+template <>
+struct Vec<double> {
+  using V = double2;
+  static constexpr int N = 2;
+  __device__ static void split(const V& v, double* o) { o[0] = v.x; o[1] = v.y; }
+  __device__ static V join(const double* o) { return make_double2(o[0], o[1]); }
+};
+
+__device__ __forceinline__ bool same_bits(float a, float b) { return __float_as_uint(a) == __float_as_uint(b); }
+__device__ __forceinline__ bool same_bits(double a, double b) {
+  return __double_as_longlong(a) == __double_as_longlong(b);
+}
+
+__device__ __forceinline__ float nan_t(float) { return __int_as_float(0x7fffffff); }
+__device__ __forceinline__ double nan_t(double) { return __longlong_as_double(0x7fffffffffffffffll); }
+
+// Appends (i, j) for every lane whose predicate holds (all 32 lanes call).
+__device__ __forceinline__ void push_pair(bool pred, int i, int j, int2* list, int* count, int cap,
+                                          int lane) {
+  const unsigned m = __ballot_sync(FULL, pred);
+  if (!m) return;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(FULL, base, leader);
+  if (pred) {
+    const int r = base + __popc(m & ((1u << lane) - 1u));
+    if (r < cap) list[r] = make_int2(i, j);
+  }
+}
+
+// Exclusive prefix sum by one CTA: out[k] = sum_{q<k} f(q) for k <= n (and
+// the same into out2 when given).
+template <typename F>
+__device__ void cta_scan(F f, int n, int* out, int* out2, int* s_tmp) {
+  const int nt = blockDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int per = (n + nt - 1) / nt;
+  const int b = min(n, threadIdx.x * per), e = min(n, b + per);
+  int sum = 0;
+  for (int k = b; k < e; ++k) sum += f(k);
+  int x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_tmp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int v = lane < (nt >> 5) ? s_tmp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane < (nt >> 5)) s_tmp[lane] = v;
+  }
+  __syncthreads();
+  int run = x - sum + (wid > 0 ? s_tmp[wid - 1] : 0);
+  for (int k = b; k < e; ++k) {
+    const int c = f(k);
+    out[k] = run;
+    if (out2) out2[k] = run;
+    run += c;
+  }
+  if (threadIdx.x == nt - 1) {
+    out[n] = run;
+    if (out2) out2[n] = run;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int ldi(const int* p) { return __ldcg(p); }
+
+template <typename T>
+__device__ __forceinline__ void load8(const T* src, T (&o)[8]) {
+  using VT = Vec<T>;
+  using V = typename VT::V;
+  const V* v = reinterpret_cast<const V*>(src);
+#pragma unroll
+  for (int q = 0; q < 8 / VT::N; ++q) VT::split(__ldcg(v + q), o + q * VT::N);
+}
+
+// Block reduction of the per-thread partials into partials[blockIdx.x*kParts+k].
+__device__ __forceinline__ void reduce_parts(double (&v)[kParts], double* out,
+                                             double (*red)[kParts]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kParts; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(FULL, x, o);
+      x = (k == kPartKkt || k == kPartDelta) ? fmax(x, y) : x + y;
+    }
+    if (lane == 0) red[wid][k] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kParts; ++k) {
+      double x = red[0][k];
+      for (int w = 1; w < nw; ++w)
+        x = (k == kPartKkt || k == kPartDelta) ? fmax(x, red[w][k]) : x + red[w][k];
+      out[(size_t)blockIdx.x * kParts + k] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// Pass over the upper triangle in 8-row chunks of 32 x 32 tiles (lane l takes
+// column j = tb*32 + l; W_ji / V_ji come from row j as one 8-element vector):
+//   * verify (V != null): a non-candidate pair (V_ij not NaN) fails when
+//     |(0 - V_ij) - V_ji| > lambda, Eq. 3's test for leaving w_ij = 0;
+//   * screen: (i, j) is a candidate of the next sweep when w_ij != 0 or
+//     |(0 - W_ij) - W_ji| > lambda;
+//   * objective / KKT terms (as the dense kernel's pass) when do_kkt.
+template <typename T, bool MIXED>
+__device__ void tile_pass(const ScreenArgs<T>& a, const T* __restrict__ W, const T* __restrict__ V,
+                          int nxt, bool do_kkt, double (&v)[kParts], int lane, int gwarp,
+                          int gwarps) {
+  const int p = a.p, ld = a.ld;
+  const ScreenWork<T>& w = a.w;
+  const int nb = (p + kTile - 1) / kTile;
+  const double lamd = a.lambda;
+  const float lamf = (float)a.lambda;
+  const T lam = (T)a.lambda;
+  const int units = nb * nb * 4;
+  for (int u = gwarp; u < units; u += gwarps) {
+    const int tau = u >> 2, r0 = (u & 3) * 8;
+    const int ta = tau / nb, tb = tau % nb;
+    if (ta > tb) continue;
+    const int j = tb * kTile + lane;
+    const int i0 = ta * kTile + r0;
+    if (i0 >= p) continue;
+    const bool jv = j < p;
+    T w1[8], om8[8], wt[8], v1[8], vt[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = i0 + r;
+      const bool ok = jv && i < p;
+      w1[r] = ok ? __ldcg(W + (size_t)i * ld + j) : (T)0;
+      om8[r] = ok ? __ldcg(a.Om + (size_t)i * ld + j) : (T)0;
+      v1[r] = (ok && V) ? __ldcg(V + (size_t)i * ld + j) : (T)0;
+    }
+    if (jv) {
+      load8(W + (size_t)j * ld + i0, wt);
+      if (V) load8(V + (size_t)j * ld + i0, vt);
+    }
+    if (!jv || !V) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        if (!jv) wt[r] = (T)0;
+        vt[r] = (T)0;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = i0 + r;
+      const bool pair = jv && i < p && i < j;
+      if (V) {
+        const T x = ((T)0 - v1[r]) - vt[r];
+        const bool bad = pair && !isnan(v1[r]) && (fabs(x) - lam > (T)0);
+        push_pair(bad, i, j, w.fail, w.ctr + kCtrFail, w.fail_cap, lane);
+      }
+      const T x0 = ((T)0 - w1[r]) - wt[r];
+      const bool cand = pair && (om8[r] != (T)0 || fabs(x0) - lam > (T)0);
+      push_pair(cand, i, j, w.cand[nxt], w.ctr + kCtrCand + nxt, w.nc_cap, lane);
+    }
+    if (!do_kkt) continue;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = i0 + r;
+      if (!jv || i >= p) continue;
+      if (i < j) {
+        const T om_t = om8[r];
+        const float w1f = (float)w1[r], w2f = (float)wt[r];
+        const float gf = w1f + w2f;
+        if (om_t == (T)0 && fabsf(gf) <= lamf - 1e-5f * (1.0f + fabsf(w1f) + fabsf(w2f))) continue;
+        const double om = (double)om_t;
+        const double g = (double)w1[r] + (double)wt[r];
+        double res;
+        if (om > 0.0)
+          res = fabs(g + lamd);
+        else if (om < 0.0)
+          res = fabs(g - lamd);
+        else
+          res = fmax(fabs(g) - lamd, 0.0);
+        v[kPartKkt] = fmax(v[kPartKkt], res);
+        v[kPartQuad] += om * g;
+        v[kPartPen] += fabs(om);
+        if (!isfinite(g) || !isfinite(om)) v[kPartBad] += 1.0;
+      } else if (i == j) {
+        const double wii = (double)w1[r];
+        const double oii = MIXED ? __ldcg(a.omdiag64 + i) : (double)om8[r];
+        if (oii > 0.0 && isfinite(wii) && isfinite(oii)) {
+          v[kPartKkt] = fmax(v[kPartKkt], fabs(wii - 1.0 / oii));
+          v[kPartQuad] += oii * wii;
+          v[kPartLog] += log(oii);
+        } else {
+          v[kPartBad] += 1.0;
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T, bool MIXED>
+__global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs<T> a) {
+  using VT = Vec<T>;
+  using VV = typename VT::V;
+  constexpr int VN = VT::N;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
+  const int gwarp = blockIdx.x * nwarps + wid, gwarps = gridDim.x * nwarps;
+  const int p = a.p, P = a.P, ld = a.ld;
+  const ScreenWork<T>& w = a.w;
+  const WaitCtl& wc = a.wait;
+  const T lam = (T)a.lambda;
+
+  __shared__ double red[kScreenThreads / 32][kParts];
+  __shared__ int s_tmp[32];
+  __shared__ double s_res[kRes];
+  __shared__ int s_stop;
+  extern __shared__ __align__(16) unsigned char dyn[];
+
+  unsigned gen = 0;
+  int where = 0;
+  T* Wa = a.W;
+  T* Wn = a.Wb;
+  int cur = 0;
+  int t = 0, first_delta = 0, since_best = 0;
+  double best_kkt = 1e300;
+  int status = -1;  // set when the launch ends early (overflow: kStatusDense)
+  const bool kkt0 = a.kkt_only || a.n_sweeps <= 0;  // objective / KKT only
+  int redo_total = 0;
+
+  // ---------------- screen the starting point (and its KKT for kkt_only)
+  {
+    double v[kParts];
+#pragma unroll
+    for (int k = 0; k < kParts; ++k) v[k] = 0.0;
+    for (int k = gtid; k <= P; k += gthreads) w.cnt_c[k] = 0;
+    for (int k = gtid; k <= p; k += gthreads) w.cnt_r[k] = 0;
+    tile_pass<T, MIXED>(a, Wa, nullptr, cur, kkt0, v, lane, gwarp, gwarps);
+    if (kkt0) reduce_parts(v, a.partials, red);
+    grid_barrier(a.barrier, gen, wc, ++where);
+  }
+
+  for (;;) {
+    const bool do_sweep = !kkt0 && t < a.n_sweeps;
+    double v[kParts];
+#pragma unroll
+    for (int k = 0; k < kParts; ++k) v[k] = 0.0;
+    if (do_sweep) {
+      int redo = 0;
+      for (;;) {  // until the verification passes
+        const int N = ldi(w.ctr + kCtrCand + cur);
+        if (N > w.nc_cap || ld_relaxed_s32(wc.abort) != 0) {
+          status = kStatusDense;
+          break;
+        }
+        const int2* cand = w.cand[cur];
+        // ---- build: colour and row buckets
+        for (int e = gtid; e < N; e += gthreads) {
+          const int2 pr = __ldcg(cand + e);
+          atomicAdd(w.cnt_c + pair_step(pr.x, pr.y, P), 1);
+          atomicAdd(w.cnt_r + pr.x, 1);
+          atomicAdd(w.cnt_r + pr.y, 1);
+        }
+        grid_barrier(a.barrier, gen, wc, ++where);
+        if (blockIdx.x == 0)
+          cta_scan([&](int k) { return ldi(w.cnt_c + k); }, P, w.off_c, w.cur_c, s_tmp);
+        if (blockIdx.x == (gridDim.x > 1 ? 1 : 0))
+          cta_scan([&](int k) { return ldi(w.cnt_r + k); }, p, w.off_r, w.cur_r, s_tmp);
+        grid_barrier(a.barrier, gen, wc, ++where);
+        for (int e = gtid; e < N; e += gthreads) {
+          const int2 pr = __ldcg(cand + e);
+          const int c = pair_step(pr.x, pr.y, P);
+          const int pos = atomicAdd(w.cur_c + c, 1);
+          w.nd_i[pos] = pr.x;
+          w.nd_j[pos] = pr.y;
+          w.nd_c[pos] = c;
+        }
+        grid_barrier(a.barrier, gen, wc, ++where);
+        // one colour's candidates in row order (deterministic numbering)
+        for (int c = gtid; c < P; c += gthreads) {
+          const int b = ldi(w.off_c + c), e = ldi(w.off_c + c + 1);
+          for (int x = b + 1; x < e; ++x) {
+            const int ki = ldi(w.nd_i + x), kj = ldi(w.nd_j + x);
+            int y = x - 1;
+            while (y >= b && ldi(w.nd_i + y) > ki) {
+              w.nd_i[y + 1] = ldi(w.nd_i + y);
+              w.nd_j[y + 1] = ldi(w.nd_j + y);
+              --y;
+            }
+            w.nd_i[y + 1] = ki;
+            w.nd_j[y + 1] = kj;
+          }
+        }
+        grid_barrier(a.barrier, gen, wc, ++where);
+        for (int k = gtid; k < N; k += gthreads) {
+          const int i = ldi(w.nd_i + k), j = ldi(w.nd_j + k);
+          w.row_ent[atomicAdd(w.cur_r + i, 1)] = k;
+          w.row_ent[atomicAdd(w.cur_r + j, 1)] = k;
+        }
+        grid_barrier(a.barrier, gen, wc, ++where);
+        // each row's candidates in step order (= candidate order)
+        for (int r = gtid; r < p; r += gthreads) {
+          const int b = ldi(w.off_r + r), e = ldi(w.off_r + r + 1);
+          for (int x = b + 1; x < e; ++x) {
+            const int key = ldi(w.row_ent + x);
+            int y = x - 1;
+            while (y >= b && ldi(w.row_ent + y) > key) {
+              w.row_ent[y + 1] = ldi(w.row_ent + y);
+              --y;
+            }
+            w.row_ent[y + 1] = key;
+          }
+          for (int x = b; x < e; ++x) {
+            const int k = ldi(w.row_ent + x);
+            if (ldi(w.nd_i + k) == r)
+              w.nd_pi[k] = x - b;
+            else
+              w.nd_pj[k] = x - b;
+          }
+        }
+        grid_barrier(a.barrier, gen, wc, ++where);
+        if (blockIdx.x == 0) {
+          cta_scan([&](int k) { return ldi(w.nd_pi + k) + ldi(w.nd_pj + k); }, N, w.term_ptr,
+                   nullptr, s_tmp);
+          if (threadIdx.x == 0) w.ctr[kCtrTerms] = ldi(w.term_ptr + N);
+        }
+        grid_barrier(a.barrier, gen, wc, ++where);
+        if (ldi(w.ctr + kCtrTerms) > w.term_cap) {
+          status = kStatusDense;
+          break;
+        }
+        // ---- operands of every candidate: W_ij, W_ji, w_ij at the sweep
+        //      start, s_ii + s_jj, and the S entries of the corrections
+        for (int k = gtid; k < N; k += gthreads) {
+          const int i = ldi(w.nd_i + k), j = ldi(w.nd_j + k);
+          T* rec = w.nd_rec + 4 * (size_t)k;
+          rec[0] = __ldcg(Wa + (size_t)i * ld + j);
+          rec[1] = __ldcg(Wa + (size_t)j * ld + i);
+          rec[2] = __ldcg(a.Om + (size_t)i * ld + j);
+          rec[3] = a.sdiag[i] + a.sdiag[j];
+          int tp = ldi(w.term_ptr + k);
+          const int bi = ldi(w.off_r + i), pi = ldi(w.nd_pi + k);
+          for (int m = 0; m < pi; ++m, ++tp) {
+            const int q = ldi(w.row_ent + bi + m);
+            const int qi = ldi(w.nd_i + q), qj = ldi(w.nd_j + q);
+            const int u = qi == i ? qj : qi;
+            w.term_pred[tp] = q;
+            w.term_s[tp] = __ldg(a.S + (size_t)u * ld + j);
+          }
+          const int bj = ldi(w.off_r + j), pj = ldi(w.nd_pj + k);
+          for (int m = 0; m < pj; ++m, ++tp) {
+            const int q = ldi(w.row_ent + bj + m);
+            const int qi = ldi(w.nd_i + q), qj = ldi(w.nd_j + q);
+            const int u = qi == j ? qj : qi;
+            w.term_pred[tp] = q;
+            w.term_s[tp] = __ldg(a.S + (size_t)u * ld + i);
+          }
+          w.nd_delta[k] = (T)0;  // the fixed-point iteration starts from no change
+        }
+        if (gtid < kJacMax) w.jac[gtid] = 0;
+        grid_barrier(a.barrier, gen, wc, ++where);
+        // ---- chain, in parallel: the changes d solve d_k = F_k(d of the
+        //      earlier candidates sharing row i or j), a system over a DAG in
+        //      colour-step order whose unique solution is the sequential
+        //      walk's.  Iterating d <- F(d) from d = 0 over all candidates at
+        //      once reaches it exactly: once an iteration leaves every d
+        //      unchanged (bit for bit) the iterate satisfies the system.  Each
+        //      link scales a perturbation by |s_uj| / (s_ii + s_jj), so the
+        //      iteration settles after a few dozen rounds instead of one
+        //      round per link.  Thread gtid owns candidate gtid (operands in
+        //      registers); further candidates (N > threads) reload theirs.
+        bool converged = false;
+        {
+          const int k0 = gtid;
+          const bool own = k0 < N;
+          T w1 = (T)0, w2 = (T)0, om = (T)0, ss = (T)1;
+          int t0 = 0, ts = 0, nt = 0;
+          int tpr[4] = {0, 0, 0, 0};
+          T tsv[4] = {(T)0, (T)0, (T)0, (T)0};
+          if (own) {
+            const T* rec = w.nd_rec + 4 * (size_t)k0;
+            w1 = __ldcg(rec);
+            w2 = __ldcg(rec + 1);
+            om = __ldcg(rec + 2);
+            ss = __ldcg(rec + 3);
+            t0 = ldi(w.term_ptr + k0);
+            ts = t0 + ldi(w.nd_pi + k0);
+            nt = ldi(w.term_ptr + k0 + 1) - t0;
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+              if (x < nt) {
+                tpr[x] = ldi(w.term_pred + t0 + x);
+                tsv[x] = __ldcg(w.term_s + t0 + x);
+              }
+          }
+          T dmine = (T)0;
+          const T* dcur = w.nd_delta;
+          T* dnext = w.nd_d2;
+          for (int r = 0; r < kJacMax; ++r) {
+            bool changed = false;
+            if (own) {
+              T vij = w1, vji = w2;
+#pragma unroll
+              for (int x = 0; x < 4; ++x)
+                if (x < nt) {
+                  const T d = __ldcg(dcur + tpr[x]);
+                  if (d != (T)0) {
+                    if (t0 + x < ts)
+                      vij = fma_t(d, tsv[x], vij);
+                    else
+                      vji = fma_t(d, tsv[x], vji);
+                  }
+                }
+              for (int x = 4; x < nt; ++x) {
+                const T d = __ldcg(dcur + ldi(w.term_pred + t0 + x));
+                if (d != (T)0) {
+                  if (t0 + x < ts)
+                    vij = fma_t(d, __ldcg(w.term_s + t0 + x), vij);
+                  else
+                    vji = fma_t(d, __ldcg(w.term_s + t0 + x), vji);
+                }
+              }
+              const T xv = (ss * om - vij) - vji;
+              const T sx = soft(xv, lam);
+              T nw = (T)0;
+              if (sx != (T)0) nw = sx / ss;
+              const T delta = nw - om;
+              changed = !same_bits(delta, dmine);
+              dmine = delta;
+              dnext[k0] = delta;
+              w.nd_new[k0] = nw;
+            }
+            for (int k = gtid + gthreads; k < N; k += gthreads) {
+              const T* rec = w.nd_rec + 4 * (size_t)k;
+              const int u0 = ldi(w.term_ptr + k), us = u0 + ldi(w.nd_pi + k),
+                        u1 = ldi(w.term_ptr + k + 1);
+              T vij = __ldcg(rec), vji = __ldcg(rec + 1);
+              const T omk = __ldcg(rec + 2), ssk = __ldcg(rec + 3);
+              for (int x = u0; x < u1; ++x) {
+                const T d = __ldcg(dcur + ldi(w.term_pred + x));
+                if (d != (T)0) {
+                  if (x < us)
+                    vij = fma_t(d, __ldcg(w.term_s + x), vij);
+                  else
+                    vji = fma_t(d, __ldcg(w.term_s + x), vji);
+                }
+              }
+              const T xv = (ssk * omk - vij) - vji;
+              const T sx = soft(xv, lam);
+              T nw = (T)0;
+              if (sx != (T)0) nw = sx / ssk;
+              const T delta = nw - omk;
+              changed |= !same_bits(delta, __ldcg(dcur + k));
+              dnext[k] = delta;
+              w.nd_new[k] = nw;
+            }
+            if (__syncthreads_or(changed) && threadIdx.x == 0) atomicAdd(w.jac + r, 1);
+            grid_barrier(a.barrier, gen, wc, ++where);
+            const T* tmp = dcur;
+            dcur = dnext;
+            dnext = const_cast<T*>(tmp);
+            if (ldi(w.jac + r) == 0) {
+              converged = true;
+              break;
+            }
+          }
+          // the solution sits in dcur; keep it in nd_delta
+          if (converged && dcur != w.nd_delta)
+            for (int k = gtid; k < N; k += gthreads) w.nd_delta[k] = __ldcg(dcur + k);
+        }
+        // ---- chain: Eq. 3 for the candidates in colour-step order.  Warp 0
+        //      of CTA 0 stages chunks of candidate records and terms into
+        //      shared memory; lane 0 walks them.  The change of the previous
+        //      candidate (the usual predecessor) stays in a register, older
+        //      ones come from a shared-memory ring (global memory beyond it).
+        if (!converged && blockIdx.x == 0 && wid == 0) {
+          T* ring = reinterpret_cast<T*>(dyn);
+          T* s_rec = ring + kSeqRing;
+          T* s_ts = s_rec + 4 * kSeqNodes;
+          int* s_tp = reinterpret_cast<int*>(s_ts + kSeqTerms);
+          int* s_pi = s_tp + kSeqNodes + 1;
+          int* s_pred = s_pi + kSeqNodes;
+          T dprev = (T)0;
+          for (int base = 0; base < N;) {
+            int end = min(N, base + kSeqNodes);
+            const int tp0 = ldi(w.term_ptr + base);
+            while (end > base + 1 && ldi(w.term_ptr + end) - tp0 > kSeqTerms)
+              end = base + ((end - base) >> 1);
+            const int tp1 = ldi(w.term_ptr + end);
+            const bool staged = tp1 - tp0 <= kSeqTerms;  // else one candidate, terms in place
+            const int nn = end - base;
+            for (int q = lane; q < 4 * nn; q += 32) s_rec[q] = __ldcg(w.nd_rec + 4 * (size_t)base + q);
+            for (int q = lane; q < nn; q += 32) {
+              s_tp[q] = ldi(w.term_ptr + base + q) - tp0;
+              s_pi[q] = ldi(w.nd_pi + base + q);
+            }
+            if (lane == 0) s_tp[nn] = tp1 - tp0;
+            if (staged)
+              for (int q = lane; q < tp1 - tp0; q += 32) {
+                s_pred[q] = ldi(w.term_pred + tp0 + q);
+                s_ts[q] = __ldcg(w.term_s + tp0 + q);
+              }
+            __syncwarp();
+            if (lane == 0) {
+              const int* tpred = staged ? s_pred : w.term_pred + tp0;
+              const T* tval = staged ? s_ts : w.term_s + tp0;
+              for (int q = 0; q < nn; ++q) {
+                const int k = base + q;
+                const T w1 = s_rec[4 * q], w2 = s_rec[4 * q + 1];
+                const T om = s_rec[4 * q + 2], ss = s_rec[4 * q + 3];
+                const int t0 = s_tp[q], ts = t0 + s_pi[q], t1 = s_tp[q + 1];
+                T vij = w1, vji = w2;
+                for (int x = t0; x < t1; ++x) {
+                  const int pr = tpred[x];
+                  const T sv = tval[x];
+                  T d;
+                  if (pr == k - 1)
+                    d = dprev;
+                  else if (k - pr <= kSeqRing)
+                    d = ring[pr & (kSeqRing - 1)];
+                  else
+                    d = __ldcg(w.nd_delta + pr);
+                  if (d != (T)0) {
+                    if (x < ts)
+                      vij = fma_t(d, sv, vij);
+                    else
+                      vji = fma_t(d, sv, vji);
+                  }
+                }
+                const T xv = (ss * om - vij) - vji;
+                const T sx = soft(xv, lam);
+                T nw = (T)0;
+                if (sx != (T)0) nw = sx / ss;
+                const T delta = nw - om;
+                dprev = delta;
+                ring[k & (kSeqRing - 1)] = delta;
+                w.nd_delta[k] = delta;
+                w.nd_new[k] = nw;
+              }
+            }
+            __syncwarp();
+            base = end;
+          }
+        }
+        grid_barrier(a.barrier, gen, wc, ++where);
+        // ---- rows: W after the colour steps, Eq. 2, W += dw S_i, V
+        if (gtid == 0) {
+          w.ctr[kCtrCand + (1 - cur)] = 0;
+          w.ctr[kCtrFail] = 0;
+        }
+        {
+          int* l_u = reinterpret_cast<int*>(dyn) + wid * kRowList * 2;
+          int* l_c = l_u + kRowList;
+          T* l_d = reinterpret_cast<T*>(reinterpret_cast<int*>(dyn) + nwarps * kRowList * 2) +
+                   wid * kRowList;
+          for (int i = gwarp; i < p; i += gwarps) {
+            const int b = ldi(w.off_r + i), ne = ldi(w.off_r + i + 1) - b;
+            // diagonal: W_ii after the row's changes (lanes load the changes
+            // and their S_ui in parallel; the FMAs run in step order on
+            // every lane), then the root (Eq. 2) on lane 0
+            T wii = __ldcg(Wa + (size_t)i * ld + i);
+            int my_u = -1;  // lane m < 32: partner of the row's m-th candidate
+            for (int m0 = 0; m0 < ne; m0 += 32) {
+              const int m = m0 + lane;
+              T d = (T)0, sv = (T)0;
+              if (m < ne) {
+                const int q = ldi(w.row_ent + b + m);
+                const int qi = ldi(w.nd_i + q), qj = ldi(w.nd_j + q);
+                const int u = qi == i ? qj : qi;
+                if (m0 == 0) my_u = u;
+                d = __ldcg(w.nd_delta + q);
+                if (d != (T)0) sv = __ldg(a.S + (size_t)u * ld + i);
+              }
+              const int nm = min(32, ne - m0);
+              for (int r = 0; r < nm; ++r) {
+                const T dr = __shfl_sync(FULL, d, r), sr = __shfl_sync(FULL, sv, r);
+                if (dr != (T)0) wii = fma_t(dr, sr, wii);
+              }
+            }
+            double dd64 = 0.0;
+            T dd = (T)0;
+            if (lane == 0) {
+              const double sii = a.sdiag64[i];
+              const T o_old = __ldcg(a.Om + (size_t)i * ld + i);
+              const double oii = MIXED ? __ldcg(a.omdiag64 + i) : (double)o_old;
+              const double ci = (double)wii - oii * sii;
+              const double nw = (-ci + sqrt(ci * ci + 4.0 * sii)) / (2.0 * sii);
+              w.diag_old[i] = o_old;
+              if (MIXED) {
+                w.omdiag_old[i] = oii;
+                a.omdiag64[i] = nw;
+              }
+              a.Om[(size_t)i * ld + i] = (T)nw;
+              dd = (T)(nw - oii);
+              dd64 = fabs(nw - oii);
+            }
+            dd = __shfl_sync(FULL, dd, 0);
+            v[kPartDelta] = fmax(v[kPartDelta], dd64);
+            // the row's changes in step order, in chunks of kRowList
+            const T* Srow = a.S + (size_t)i * ld;
+            const int nv = ld / VN;
+            int c_last = -1;  // step of the last change of the previous chunks
+            int done = 0;
+            bool first = true;
+            do {
+              int cnt = 0;
+              int m0 = done;
+              // compact the next changes (d != 0) into the warp's list
+              while (m0 < ne && cnt < kRowList) {
+                const int m = m0 + lane;
+                int q = -1;
+                T d = (T)0;
+                if (m < ne) {
+                  q = ldi(w.row_ent + b + m);
+                  d = __ldcg(w.nd_delta + q);
+                }
+                const bool nz = m < ne && d != (T)0;
+                const unsigned bal = __ballot_sync(FULL, nz);
+                const int room = kRowList - cnt;
+                // take whole 32-entry groups only when they fit
+                if (__popc(bal) > room) break;
+                if (nz) {
+                  const int slot = cnt + __popc(bal & ((1u << lane) - 1u));
+                  const int qi = ldi(w.nd_i + q), qj = ldi(w.nd_j + q);
+                  l_u[slot] = qi == i ? qj : qi;
+                  l_c[slot] = ldi(w.nd_c + q);
+                  l_d[slot] = d;
+                }
+                cnt += __popc(bal);
+                m0 = min(ne, m0 + 32);
+              }
+              __syncwarp();
+              const bool last = m0 >= ne;
+              const T* src = (first ? Wa : Wn) + (size_t)i * ld;
+              // U 16-byte vectors per lane per iteration (memory-level
+              // parallelism); lane l takes vectors q0 + 32 u, u < U
+              constexpr int U = sizeof(T) == 8 ? 2 : 4;
+              for (int q0 = lane; q0 < nv; q0 += 32 * U) {
+                T acc[U][VN], vv[U][VN];
+                int cx[U][VN];
+                bool cap[U][VN];  // V captured (in this chunk or an earlier one)
+#pragma unroll
+                for (int uu = 0; uu < U; ++uu) {
+                  const int q = q0 + 32 * uu;
+                  if (q < nv)
+                    VT::split(__ldcg(reinterpret_cast<const VV*>(src) + q), acc[uu]);
+                  else
+#pragma unroll
+                    for (int e = 0; e < VN; ++e) acc[uu][e] = (T)0;
+#pragma unroll
+                  for (int e = 0; e < VN; ++e) {
+                    const int x = q * VN + e;
+                    cx[uu][e] = (x < p && x != i) ? pair_step(min(i, x), max(i, x), P) : 0x7fffffff;
+                    cap[uu][e] = c_last >= cx[uu][e];
+                    vv[uu][e] = (T)0;
+                  }
+                }
+                for (int m = 0; m < cnt; ++m) {
+                  const int u = l_u[m], cm = l_c[m];
+                  const T d = l_d[m];
+                  const VV* su = reinterpret_cast<const VV*>(a.S + (size_t)u * ld);
+                  T sv[U][VN];
+#pragma unroll
+                  for (int uu = 0; uu < U; ++uu) {
+                    const int q = q0 + 32 * uu;
+                    if (q < nv) VT::split(__ldg(su + q), sv[uu]);
+                    else
+#pragma unroll
+                      for (int e = 0; e < VN; ++e) sv[uu][e] = (T)0;
+                  }
+#pragma unroll
+                  for (int uu = 0; uu < U; ++uu)
+#pragma unroll
+                    for (int e = 0; e < VN; ++e) {
+                      // V: W before the first change at or after the pair's step
+                      if (!cap[uu][e] && cm >= cx[uu][e]) {
+                        vv[uu][e] = acc[uu][e];
+                        cap[uu][e] = true;
+                      }
+                      acc[uu][e] = fma_t(d, sv[uu][e], acc[uu][e]);
+                    }
+                }
+                T si[U][VN];
+                if (last && dd != (T)0) {
+#pragma unroll
+                  for (int uu = 0; uu < U; ++uu) {
+                    const int q = q0 + 32 * uu;
+                    if (q < nv) VT::split(__ldg(reinterpret_cast<const VV*>(Srow) + q), si[uu]);
+                  }
+                }
+#pragma unroll
+                for (int uu = 0; uu < U; ++uu) {
+                  const int q = q0 + 32 * uu;
+                  if (q >= nv) continue;
+                  T out[VN];
+                  T* vrow = a.V + (size_t)i * ld + q * VN;
+#pragma unroll
+                  for (int e = 0; e < VN; ++e) {
+                    // not captured: every change so far precedes the pair's step
+                    if (!cap[uu][e]) vv[uu][e] = acc[uu][e];
+                    out[e] = (last && dd != (T)0) ? fma_t(dd, si[uu][e], acc[uu][e]) : acc[uu][e];
+                    if (c_last < cx[uu][e]) vrow[e] = vv[uu][e];
+                  }
+                  reinterpret_cast<VV*>(Wn + (size_t)i * ld)[q] = VT::join(out);
+                }
+              }
+              if (cnt > 0) c_last = l_c[cnt - 1];
+              __syncwarp();
+              first = false;
+              done = m0;
+              if (last) break;
+            } while (true);
+            // candidates of this row (changed or not) and the diagonal are not verified
+            __syncwarp();
+            if (ne <= 32) {
+              if (my_u >= 0) a.V[(size_t)i * ld + my_u] = nan_t((T)0);
+            } else {
+              for (int m = lane; m < ne; m += 32) {
+                const int q = ldi(w.row_ent + b + m);
+                const int qi = ldi(w.nd_i + q), qj = ldi(w.nd_j + q);
+                a.V[(size_t)i * ld + (qi == i ? qj : qi)] = nan_t((T)0);
+              }
+            }
+            if (lane == 0) a.V[(size_t)i * ld + i] = nan_t((T)0);
+            __syncwarp();
+          }
+        }
+        // ---- commit the candidates' new values (both triangles)
+        for (int k = gtid; k < N; k += gthreads) {
+          const T d = __ldcg(w.nd_delta + k);
+          if (d != (T)0) {
+            const int i = ldi(w.nd_i + k), j = ldi(w.nd_j + k);
+            const T nw = __ldcg(w.nd_new + k);
+            a.Om[(size_t)i * ld + j] = nw;
+            a.Om[(size_t)j * ld + i] = nw;
+            v[kPartDelta] = fmax(v[kPartDelta], (double)fabs(d));
+            v[kPartActive] += 2.0;  // counted per owner, as the dense pass does
+          }
+        }
+        grid_barrier(a.barrier, gen, wc, ++where);
+        // ---- verify + objective / KKT + screen of the next sweep
+        for (int k = gtid; k <= P; k += gthreads) w.cnt_c[k] = 0;
+        for (int k = gtid; k <= p; k += gthreads) w.cnt_r[k] = 0;
+        tile_pass<T, MIXED>(a, Wn, a.V, 1 - cur, true, v, lane, gwarp, gwarps);
+        grid_barrier(a.barrier, gen, wc, ++where);
+        const int nf = ldi(w.ctr + kCtrFail);
+        if (nf == 0) break;
+        // ---- undo the sweep, add the failing pairs, redo
+        for (int k = gtid; k < N; k += gthreads) {
+          if (__ldcg(w.nd_delta + k) != (T)0) {
+            const int i = ldi(w.nd_i + k), j = ldi(w.nd_j + k);
+            const T om = __ldcg(w.nd_rec + 4 * (size_t)k + 2);
+            a.Om[(size_t)i * ld + j] = om;
+            a.Om[(size_t)j * ld + i] = om;
+          }
+        }
+        for (int i = gtid; i < p; i += gthreads) {
+          a.Om[(size_t)i * ld + i] = __ldcg(w.diag_old + i);
+          if (MIXED) a.omdiag64[i] = __ldcg(w.omdiag_old + i);
+        }
+        const int add = min(min(nf, w.fail_cap), w.nc_cap - N);
+        for (int f = gtid; f < add; f += gthreads) w.cand[cur][N + f] = __ldcg(w.fail + f);
+        if (gtid == 0) {
+          w.ctr[kCtrCand + cur] = N + add;
+          w.ctr[kCtrFail] = 0;
+        }
+#pragma unroll
+        for (int k = 0; k < kParts; ++k) v[k] = 0.0;
+        grid_barrier(a.barrier, gen, wc, ++where);
+        ++redo_total;
+        if (add < min(nf, w.fail_cap) || ++redo > a.max_redo) {
+          status = kStatusDense;
+          break;
+        }
+      }
+      if (status == kStatusDense) {
+        // nothing of this sweep was kept; report the state as it stands
+        break;
+      }
+      reduce_parts(v, a.partials, red);
+      grid_barrier(a.barrier, gen, wc, ++where);
+    }
+
+    // ---------------- every CTA reduces the partials identically (warp 0:
+    //                  lanes stride over the CTAs, then a fixed shuffle tree)
+    double kkt = 0.0, quad = 0.0, pen = 0.0, lg = 0.0, dl = 0.0, ac = 0.0, bad = 0.0;
+    if (wid == 0) {
+      for (int b = lane; b < (int)gridDim.x; b += 32) {
+        const double* q = a.partials + (size_t)b * kParts;
+        kkt = fmax(kkt, __ldcg(q + kPartKkt));
+        quad += __ldcg(q + kPartQuad);
+        pen += __ldcg(q + kPartPen);
+        lg += __ldcg(q + kPartLog);
+        dl = fmax(dl, __ldcg(q + kPartDelta));
+        ac += __ldcg(q + kPartActive);
+        bad += __ldcg(q + kPartBad);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        kkt = fmax(kkt, __shfl_xor_sync(FULL, kkt, o));
+        dl = fmax(dl, __shfl_xor_sync(FULL, dl, o));
+        quad += __shfl_xor_sync(FULL, quad, o);
+        pen += __shfl_xor_sync(FULL, pen, o);
+        lg += __shfl_xor_sync(FULL, lg, o);
+        ac += __shfl_xor_sync(FULL, ac, o);
+        bad += __shfl_xor_sync(FULL, bad, o);
+      }
+    }
+    if (threadIdx.x == 0) {
+      const double obj = -lg + 0.5 * quad + a.lambda * pen;
+      const bool aborted = ld_relaxed_s32(wc.abort) != 0;
+      const bool nonfinite = bad > 0.0 || !isfinite(obj) || !isfinite(kkt);
+      const int sweeps_done = do_sweep ? t + 1 : t;
+      if (do_sweep && first_delta == 0 && dl < a.delta_tol) first_delta = sweeps_done;
+      const bool conv = (a.stop_rule == 1) ? (do_sweep && dl < a.tol) : (kkt <= a.tol);
+      bool stalled = false;
+      if (do_sweep) {
+        if (kkt < 0.9 * best_kkt) {
+          best_kkt = kkt;
+          since_best = 0;
+        } else if (++since_best >= 4 && a.stall_stop) {
+          stalled = true;
+        }
+      }
+      // the next sweep's candidates overflowed: hand over to the dense kernel
+      const bool dense_next = ldi(w.ctr + kCtrCand + (1 - cur)) > w.nc_cap;
+      s_res[kResSweeps] = sweeps_done;
+      s_res[kResKkt] = kkt;
+      s_res[kResObj] = obj;
+      s_res[kResDelta] = dl;
+      s_res[kResActive] = ac * 0.5;
+      s_res[kResFirstDelta] = first_delta;
+      s_res[kResRedo] = redo_total;
+      s_res[kResStatus] = aborted      ? 3.0
+                          : nonfinite  ? 2.0
+                          : conv       ? 0.0
+                          : stalled    ? 4.0
+                          : (dense_next && sweeps_done < a.n_sweeps && !kkt0)
+                              ? (double)kStatusDense
+                              : 1.0;
+      s_stop = (aborted || nonfinite || conv || stalled || kkt0 ||
+                sweeps_done >= a.n_sweeps || dense_next)
+                   ? 1
+                   : 0;
+      if (blockIdx.x == 0) {
+        if (do_sweep && t < a.hist_len) {
+          double* h = a.hist + (size_t)t * kHist;
+          h[0] = dl;
+          h[1] = kkt;
+          h[2] = obj;
+          h[3] = ac * 0.5;
+        }
+        if (s_stop)
+          for (int k = 0; k < kRes; ++k) a.result[k] = s_res[k];
+      }
+    }
+    __syncthreads();
+    if (kkt0) break;
+    // the accepted sweep's W becomes current
+    T* tmp = Wa;
+    Wa = Wn;
+    Wn = tmp;
+    cur = 1 - cur;
+    if (s_stop) break;
+    ++t;
+  }
+
+  if (status == kStatusDense && blockIdx.x == 0 && threadIdx.x == 0) {
+    // the sweep in progress was undone or never started: t sweeps are done
+    a.result[kResSweeps] = t;
+    a.result[kResKkt] = t > 0 ? s_res[kResKkt] : 1e300;
+    a.result[kResObj] = t > 0 ? s_res[kResObj] : 0.0;
+    a.result[kResDelta] = t > 0 ? s_res[kResDelta] : 0.0;
+    a.result[kResActive] = t > 0 ? s_res[kResActive] : 0.0;
+    a.result[kResFirstDelta] = first_delta;
+    a.result[kResRedo] = redo_total;
+    a.result[kResStatus] = ld_relaxed_s32(wc.abort) != 0 ? 3.0 : (double)kStatusDense;
+  }
+  // leave W in the caller's buffer
+  if (Wa != a.W) {
+    const size_t n = (size_t)p * ld / VN;
+    const VV* s = reinterpret_cast<const VV*>(Wa);
+    VV* d = reinterpret_cast<VV*>(a.W);
+    for (size_t k = gtid; k < n; k += gthreads) d[k] = __ldcg(s + k);
+  }
+}
+
+size_t screened_dyn_smem(bool mixed) {
+  const size_t e = mixed ? 4 : 8;
+  const size_t chain = e * (kSeqRing + 4 * kSeqNodes + kSeqTerms) +
+                       4 * ((kSeqNodes + 1) + kSeqNodes + kSeqTerms);
+  const size_t rows = (size_t)(kScreenThreads / 32) * kRowList * (8 + e);
+  return chain > rows ? chain : rows;
+}
+
+template <typename T, bool MIXED>
+cudaError_t launch_screened_impl(const ScreenArgs<T>& a, int grid, cudaStream_t st) {
+  const size_t dyn = screened_dyn_smem(MIXED);
+  const void* fn = (const void*)k_screened<T, MIXED>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (e != cudaSuccess) return e;
+  note_launches(1);
+  void* kargs[] = {(void*)&a};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kScreenThreads), kargs, dyn, st);
+}
+
+cudaError_t launch_screened(const ScreenArgs<double>& a, int grid, cudaStream_t st) {
+  return launch_screened_impl<double, false>(a, grid, st);
+}
+cudaError_t launch_screened(const ScreenArgs<float>& a, int grid, cudaStream_t st) {
+  return launch_screened_impl<float, true>(a, grid, st);
+}
+
+cudaError_t screened_occupancy(bool mixed, int* blocks_per_sm) {
+  const size_t dyn = screened_dyn_smem(mixed);
+  const void* fn = mixed ? (const void*)k_screened<float, true> : (const void*)k_screened<double, false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (e != cudaSuccess) return e;
+  return mixed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_screened<float, true>,
+                                                              kScreenThreads, dyn)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                     blocks_per_sm, k_screened<double, false>, kScreenThreads, dyn);
+}
+
+}  // namespace concord

@@ -205,6 +205,7 @@ def test_rows_per_warp_does_not_change_results(small, rows):
     ref = None
     for prec in (C.FP64, C.MIXED):
         with C.State(100, prec) as st:
+            st.set_sweep_variant(C.SWEEP_DENSE)
             st.set_rows_per_warp(rows)
             st.set_S(dev(S))
             st.sweep(w["lam"], 3)

@@ -1,0 +1,163 @@
+"""Screened sweep kernel (CONCORD_SWEEP_SCREENED, the default) against the
+dense colour-loop kernel and the FP64 oracle.
+
+The screened kernel visits only the candidate pairs of each sweep and
+verifies that every other pair stays at zero; it applies the same FMA chains
+in the same order as the dense kernel, so the two must agree bit for bit
+after every sweep, in both precisions -- including sweeps that the
+verification sends back for a redo and sweeps handed to the dense kernel
+when the candidates overflow.  Against the oracle the FP64 tolerance of the
+dense path applies (max|dOmega| <= 1e-10 max|Omega| per sweep, identical
+changed-pair counts).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2106_09382_gb300 import concord as C
+from paper_2106_09382_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def correlated(seed, p, n):
+    """Gaussian data mixed through a sparse random matrix: strongly correlated
+    columns, the regime where changes propagate to pairs outside the
+    candidates and the verification forces redos."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, p))
+    L = np.eye(p)
+    for _ in range(p // 4):
+        a, b = rng.integers(0, p, 2)
+        L[a, b] += rng.uniform(0.5, 1.5)
+    return X @ L
+
+
+def plain(seed, p, n):
+    """Gaussian data mixed through I + a dense strictly upper-triangular
+    matrix of small entries: moderate correlations everywhere."""
+    rng = np.random.default_rng(seed)
+    U = np.triu(rng.uniform(-0.3, 0.3, (p, p)) / np.sqrt(p), 1)
+    return rng.standard_normal((n, p)) @ (np.eye(p) + U)
+
+
+def _pair(p, precision, S):
+    a = C.State(p, precision)
+    b = C.State(p, precision)
+    a.set_sweep_variant(C.SWEEP_SCREENED)
+    b.set_sweep_variant(C.SWEEP_GRID)
+    Sd = dev(S, torch.float32 if precision == C.MIXED else torch.float64)
+    a.set_S(Sd)
+    b.set_S(Sd)
+    return a, b
+
+
+@pytest.mark.parametrize("precision", [C.FP64, C.MIXED])
+@pytest.mark.parametrize("p,n,lam,kind", [(100, 200, 0.3, "plain"), (333, 400, 0.15, "plain"),
+                                          (517, 300, 0.1, "plain"), (2, 20, 0.1, "plain"),
+                                          (3, 20, 0.05, "plain"), (31, 60, 0.02, "plain"),
+                                          (100, 60, 0.2, "corr"), (64, 60, 0.1, "corr"),
+                                          (101, 30, 0.05, "corr")])
+def test_screened_equals_dense_bit_for_bit(precision, p, n, lam, kind):
+    X = correlated(p, p, n) if kind == "corr" else plain(p, p, n)
+    S = O.gram(O.standardize(X))
+    a, b = _pair(p, precision, S)
+    redos = 0
+    try:
+        for t in range(4):
+            ra = a.sweep(lam, 1)
+            rb = b.sweep(lam, 1)
+            redos += ra.screen_redos
+            assert np.array_equal(host(a.get_omega()), host(b.get_omega())), t
+            assert np.array_equal(host(a.get_W()), host(b.get_W())), t
+            assert ra.active_pairs == rb.active_pairs
+            assert ra.kkt == rb.kkt and ra.delta == rb.delta
+            # the objective sums per-CTA partials: the grids differ, so only
+            # the summation order (last bits) may
+            assert abs(ra.objective - rb.objective) <= 1e-13 * abs(rb.objective)
+    finally:
+        a.close()
+        b.close()
+    if kind == "corr" and p >= 64:
+        assert redos > 0  # the undo / redo path ran
+
+
+@pytest.mark.parametrize("p,n,lam", [(100, 60, 0.2), (64, 60, 0.1)])
+def test_screened_redo_sweeps_match_oracle(p, n, lam):
+    S = O.gram(O.standardize(correlated(p, p, n)))
+    pairs = O.schedule(p)
+    Om = np.eye(p)
+    redos = 0
+    with C.State(p, C.FP64) as st:
+        st.set_S(dev(S))
+        for t in range(4):
+            r = st.sweep(lam, 1)
+            redos += r.screen_redos
+            d_or, nnz_or = O.sweep(S, Om, lam, pairs)
+            G = host(st.get_omega())
+            assert np.abs(G - Om).max() <= 1e-10 * np.abs(Om).max(), t
+            assert r.active_pairs == nnz_or
+            assert abs(r.delta - d_or) <= 1e-10
+    assert redos > 0
+
+
+@pytest.mark.parametrize("precision", [C.FP64, C.MIXED])
+def test_candidate_overflow_hands_sweeps_to_dense_kernel(precision):
+    """At lambda = 1e-3 lambda_max nearly every pair changes: the candidate
+    lists (16 p pairs) overflow and those sweeps run on the dense kernel; the
+    iterates stay those of the dense kernel."""
+    p, n = 300, 400
+    S = O.gram(O.standardize(plain(7, p, n)))
+    a, b = _pair(p, precision, S)
+    try:
+        lam = 1e-3 * a.lambda_max()
+        ra = a.sweep(lam, 3)
+        b.sweep(lam, 3)
+        assert ra.dense_sweeps >= 1
+        assert np.array_equal(host(a.get_omega()), host(b.get_omega()))
+        assert np.array_equal(host(a.get_W()), host(b.get_W()))
+    finally:
+        a.close()
+        b.close()
+
+
+@pytest.mark.parametrize("precision", [C.FP64, C.MIXED])
+def test_screened_solve_matches_dense_solve(precision):
+    w = synth.workload_small()
+    S = O.gram(O.standardize(w["X"]))
+    out = []
+    for variant in (C.SWEEP_SCREENED, C.SWEEP_DENSE):
+        with C.State(S.shape[0], precision) as st:
+            st.set_sweep_variant(variant)
+            st.set_S(dev(S))
+            r = st.run(w["lam"], tol=w["tol"], max_sweeps=500)
+            out.append((r, host(st.get_omega())))
+    (ra, Ga), (rb, Gb) = out
+    assert ra.status == C.OK and rb.status == C.OK
+    assert ra.sweeps == rb.sweeps
+    assert np.array_equal(Ga, Gb)
+    assert abs(ra.objective - rb.objective) <= 1e-13 * abs(rb.objective)
+
+
+def test_screened_warm_start_and_kkt_only():
+    w = synth.workload_small()
+    S = O.gram(O.standardize(w["X"]))
+    with C.State(S.shape[0], C.FP64) as st:
+        st.set_S(dev(S))
+        r1 = st.run(w["lam"], tol=1e-9, max_sweeps=500)
+        assert r1.status == C.OK
+        G = host(st.get_omega())
+        r0 = st.run(w["lam"], tol=1e-9, max_sweeps=0)  # objective / KKT of the iterate only
+        assert r0.sweeps == 0 and r0.kkt <= 1e-9
+        assert abs(r0.objective - r1.objective) <= 1e-12 * abs(r1.objective)
+        assert np.array_equal(host(st.get_omega()), G)
