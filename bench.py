@@ -425,6 +425,16 @@ def run_ours(args):
                                                   rows64.startswith("screened"))
                        / (ms64 * 1e-3) / 1e9}
         out["mixed_vs_fp64_speedup"] = out["fp64"]["seconds"] / value
+        # accuracy of the mixed result against the FP64 one (same data)
+        Om_mix = st.get_omega().cpu().numpy()
+        Om_64 = st64.get_omega().cpu().numpy()
+        scale = float(np.abs(Om_64).max())
+        supp_diff = int(np.count_nonzero((Om_mix != 0) != (Om_64 != 0)))
+        out["mixed_vs_fp64_error"] = {
+            "max_abs_dOmega_rel": float(np.abs(Om_mix - Om_64).max()) / scale,
+            "objective_rel": abs(r_last["objective"] - r64["objective"]) / abs(r64["objective"]),
+            "support_entries_differing": supp_diff,
+            "note": "mixed uses the tensor-core (3xTF32) Gram; FP64 uses the FP64 Gram"}
         fp64_sweeps = r64["sweeps"]
         # ---------------- full-update microbench: nearly every pair changes
         S32 = C.concord_gram(X, C.PREP_STANDARDIZE, C.GRAM_FP32, stream=stream)

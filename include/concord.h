@@ -293,7 +293,7 @@ unsigned long long concord_kernel_launches(void);
  * precision; the FP64 polishing sweeps of a MIXED state use the defaults.
  * concord_get_sweep_variant reports the variant of the last launch and the
  * largest cluster size found (0 = none).  The screened kernel allocates its
- * scratch (two p x p matrices of the FP64 width and candidate lists of
+ * scratch (two p x p matrices of the FP64 width, candidate lists of
  * max(16 p, 65536) pairs, at most all pairs, with up to max(8 x that, 4M)
  * correction terms) on first use.
  */
@@ -342,7 +342,7 @@ int concord_sweep(concord_state *st, double lambda, int n_sweeps, concord_result
  * CONCORD_STOP_KKT: KKT <= tol; CONCORD_STOP_DELTA: delta < tol) or
  * max_sweeps.  FP64 state: all sweeps in FP64.  MIXED state: FP32 sweeps
  * until the rule holds at max(tol, switch_tol) (switch_tol <= 0 picks
- * max(10 tol, 1e-5)) or until the KKT residual stops falling by 10% for 4
+ * max(3 tol, 1e-5)) or until the KKT residual stops falling by 10% for 4
  * sweeps (FP32 rounding floor); then W is rebuilt in FP64 from the FP64
  * copies of S and Omega and FP64 sweeps polish to tol.  Returns CONCORD_OK
  * or CONCORD_NOT_CONVERGED (outputs filled either way) or an error.

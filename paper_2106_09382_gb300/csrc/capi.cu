@@ -296,8 +296,7 @@ int launch_dense(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* 
 // FP64 width, so both precisions fit) and one block holding the candidate
 // lists and per-candidate arrays, carved below.
 struct ScreenLayout {
-  size_t ctr, cand0, cand1, fail, cnt_c, off_c, cur_c, cnt_r, off_r, cur_r, nd_i, nd_j, nd_c,
-      nd_pi, nd_pj, row_ent, term_ptr, term_pred, term_s, nd_rec, nd_delta, nd_new, nd_d2, jac,
+  size_t ctr, cand0, cand1, cnt_r0, cnt_r1, fail, off_r, cur_r, nd_pi, nd_pj, row_ent, term_ptr, term_pred, term_s, nd_rec, nd_delta, nd_new, nd_d2, jac,
       diag_old, omdiag_old, total;
 };
 
@@ -312,16 +311,11 @@ ScreenLayout screen_layout(int p, int P, int nc, int tc) {
   L.ctr = take(sizeof(int) * kCtrs);
   L.cand0 = take(sizeof(int2) * (size_t)nc);
   L.cand1 = take(sizeof(int2) * (size_t)nc);
+  L.cnt_r0 = take(sizeof(int) * (size_t)(p + 1));
+  L.cnt_r1 = take(sizeof(int) * (size_t)(p + 1));
   L.fail = take(sizeof(int2) * (size_t)nc);
-  L.cnt_c = take(sizeof(int) * (size_t)(P + 1));
-  L.off_c = take(sizeof(int) * (size_t)(P + 1));
-  L.cur_c = take(sizeof(int) * (size_t)(P + 1));
-  L.cnt_r = take(sizeof(int) * (size_t)(p + 1));
   L.off_r = take(sizeof(int) * (size_t)(p + 1));
   L.cur_r = take(sizeof(int) * (size_t)(p + 1));
-  L.nd_i = take(sizeof(int) * (size_t)nc);
-  L.nd_j = take(sizeof(int) * (size_t)nc);
-  L.nd_c = take(sizeof(int) * (size_t)nc);
   L.nd_pi = take(sizeof(int) * (size_t)nc);
   L.nd_pj = take(sizeof(int) * (size_t)nc);
   L.row_ent = take(sizeof(int) * 2 * (size_t)nc);
@@ -334,6 +328,7 @@ ScreenLayout screen_layout(int p, int P, int nc, int tc) {
   L.nd_d2 = take(sizeof(double) * (size_t)nc);
   L.jac = take(sizeof(int) * kJacMax);
   L.diag_old = take(sizeof(double) * (size_t)p);
+
   L.omdiag_old = take(sizeof(double) * (size_t)p);
   L.total = off;
   return L;
@@ -372,16 +367,11 @@ ScreenWork<T> screen_work(concord_state* st) {
   w.ctr = (int*)(b + L.ctr);
   w.cand[0] = (int2*)(b + L.cand0);
   w.cand[1] = (int2*)(b + L.cand1);
+  w.cnt_r[0] = (int*)(b + L.cnt_r0);
+  w.cnt_r[1] = (int*)(b + L.cnt_r1);
   w.fail = (int2*)(b + L.fail);
-  w.cnt_c = (int*)(b + L.cnt_c);
-  w.off_c = (int*)(b + L.off_c);
-  w.cur_c = (int*)(b + L.cur_c);
-  w.cnt_r = (int*)(b + L.cnt_r);
   w.off_r = (int*)(b + L.off_r);
   w.cur_r = (int*)(b + L.cur_r);
-  w.nd_i = (int*)(b + L.nd_i);
-  w.nd_j = (int*)(b + L.nd_j);
-  w.nd_c = (int*)(b + L.nd_c);
   w.nd_pi = (int*)(b + L.nd_pi);
   w.nd_pj = (int*)(b + L.nd_pj);
   w.row_ent = (int*)(b + L.row_ent);
@@ -394,6 +384,7 @@ ScreenWork<T> screen_work(concord_state* st) {
   w.nd_d2 = (T*)(b + L.nd_d2);
   w.jac = (int*)(b + L.jac);
   w.diag_old = (T*)(b + L.diag_old);
+
   w.omdiag_old = (double*)(b + L.omdiag_old);
   w.nc_cap = st->nc_cap;
   w.term_cap = st->term_cap;
@@ -413,6 +404,8 @@ int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, d
   CK(cudaMemsetAsync(st->barrier, 0, sizeof(unsigned), st->stream));
   CK(cudaMemsetAsync(st->abort_info, 0, 3 * sizeof(int), st->stream));
   CK(cudaMemsetAsync((char*)st->scr + L.ctr, 0, sizeof(int) * kCtrs, st->stream));
+  CK(cudaMemsetAsync((char*)st->scr + L.cnt_r0, 0, sizeof(int) * (size_t)(st->p + 1), st->stream));
+  CK(cudaMemsetAsync((char*)st->scr + L.cnt_r1, 0, sizeof(int) * (size_t)(st->p + 1), st->stream));
   ScreenArgs<T> a;
   memset(&a, 0, sizeof a);
   a.p = st->p;
@@ -617,10 +610,12 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
     return rc != CONCORD_OK ? rc : o1.status;
   }
   // mixed precision: FP32 sweeps until the rule holds at the switch
-  // tolerance (default max(10 tol, 1e-5)) or the FP32 iteration stalls at
+  // tolerance (default max(3 tol, 1e-5)) or the FP32 iteration stalls at
   // its rounding floor ...
-  double tol1 = exact ? -1.0 : (switch_tol > 0 ? switch_tol : (10.0 * tol > 1e-5 ? 10.0 * tol : 1e-5));
+  double tol1 = exact ? -1.0 : (switch_tol > 0 ? switch_tol : (3.0 * tol > 1e-5 ? 3.0 * tol : 1e-5));
   if (!exact && tol1 < tol) tol1 = tol;
+  // the FP32 working set follows the FP64 copies lazily (after a polish)
+  if (st->om64_current && (rc = demote_from_fp64(st)) != CONCORD_OK) return rc;
   rc = launch_run<float>(st, (float*)st->S, (float*)st->W, (float*)st->Om,
                          (const float*)st->sdiagT, st->omdiag64, lambda, tol1, stop_rule,
                          max_sweeps, 0, 0, exact ? 0 : 1, &o1);
@@ -640,7 +635,8 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
   rc = launch_run<double>(st, st->S64, st->W64, st->Om64, st->sdiag64, nullptr, lambda, tol,
                           stop_rule, left, left == 0 ? 1 : 0, o1.sweeps, 0, &o2);
   st->hist_rows = o1.sweeps + o2.sweeps;
-  if (rc == CONCORD_OK) rc = demote_from_fp64(st);
+  // the FP64 copies now hold the iterate (om64_current); the FP32 working
+  // set is refreshed from them when an FP32 phase next needs it
   CK(cudaEventRecord(st->ev1, st->stream));
   CK(cudaEventSynchronize(st->ev1));
   float ms = 0;

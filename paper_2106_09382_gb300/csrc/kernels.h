@@ -83,27 +83,26 @@ cudaError_t sweep_cluster_size(bool mixed, int block, int row_warps, int rows_pe
 // visits only the candidate pairs of each sweep (the pairs that can change)
 // and verifies every other pair afterwards; see screened.cu.
 constexpr int kScreenThreads = 512;
-constexpr int kSeqNodes = 256;    // candidate pairs staged per chunk of the chain pass
-constexpr int kSeqTerms = 2048;   // correction terms staged per chunk
-constexpr int kSeqRing = 8192;    // most recent changes kept in shared memory (power of two)
 constexpr int kRowList = 64;      // changes of one row staged per warp in the row pass
 constexpr int kCtrCand = 0;       // ctr[0], ctr[1]: lengths of the two candidate lists
 constexpr int kCtrFail = 2;       // failing pairs found by the verification
 constexpr int kCtrTerms = 3;      // correction terms of the current candidate set
+constexpr int kCtrJacBar = 4;     // barrier counter of the fixed-point iteration
+constexpr int kCtrJacDone = 5;    // the fixed-point iteration settled
 constexpr int kCtrs = 8;
-constexpr int kJacMax = 64;       // fixed-point iterations of the chain before the serial walk
+constexpr int kJacMax = 64;       // fixed-point iterations of the chain before the dense kernel takes the sweep
 constexpr int kStatusDense = 5;   // result status: the next sweep needs the dense kernel
 
 template <typename T>
 struct ScreenWork {
   int* ctr;                 // kCtrs counters (zeroed before the launch)
-  int2* cand[2];            // candidate pairs (i < j): current sweep / next sweep
+  int2* cand[2];            // candidate pairs (i < j): current sweep / next sweep; a
+                            // candidate's number is its position in the list
+  int* cnt_r[2];            // [p + 1] candidates per row of each list (counted at the push)
   int2* fail;               // non-candidate pairs that failed the verification
-  int *cnt_c, *off_c, *cur_c;  // [P + 1] colour buckets: counts, offsets, cursors
-  int *cnt_r, *off_r, *cur_r;  // [p + 1] row buckets
-  int *nd_i, *nd_j, *nd_c;     // candidates sorted by colour step (then by i)
-  int *nd_pi, *nd_pj;          // position of each candidate in the lists of rows i and j
-  int* row_ent;             // [2 nc_cap] candidates of each row, in step order
+  int *off_r, *cur_r;       // [p + 1] row buckets of the current list: offsets, cursors
+  int *nd_pi, *nd_pj;       // position of each candidate in the lists of rows i and j
+  int* row_ent;             // [2 nc_cap] candidates of each row, in colour-step order
   int* term_ptr;            // [nc_cap + 1] first correction term of each candidate
   int* term_pred;           // [term_cap] earlier candidate whose change the term carries
   T* term_s;                // [term_cap] the S entry it multiplies
@@ -121,7 +120,7 @@ struct ScreenArgs {
   int p, P, ld;
   T* W;                     // p x ld, W = Omega S (in and out)
   T* Wb;                    // p x ld scratch: W after the sweep
-  T* V;                     // p x ld scratch: W_ij when pair (i, j) is visited
+  T* V;                     // p x ld scratch: W_ij when pair (i, j) is visited (NaN: candidate)
   T* Om;                    // p x ld, Omega
   const T* S;               // p x ld, S (padding columns zero)
   const T* sdiag;           // s_ii in T

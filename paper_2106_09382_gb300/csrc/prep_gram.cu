@@ -10,46 +10,55 @@ __device__ __forceinline__ double ld_x(const TX* X, size_t i) {
   return (double)__ldg(X + i);
 }
 
-// One CTA per 32 columns; 8 row groups per column reduced in a fixed order,
-// so the statistics are deterministic.  Two passes (mean, then centered sum
-// of squares) in FP64.
+// One CTA per 32 columns; kStatThreads / 32 row groups per column sum
+// disjoint row strides and are reduced in a fixed order, so the statistics
+// are deterministic.  Two passes (mean, then centered sum of squares) in FP64.
+constexpr int kStatThreads = 1024;
+
 template <typename TX>
-__global__ void __launch_bounds__(256) k_col_stats(const TX* __restrict__ X, int n, int p, int ldx,
-                                                   int prep, double* __restrict__ mean,
-                                                   double* __restrict__ inv_scale, int* bad) {
-  __shared__ double part[8][33];
+__global__ void __launch_bounds__(kStatThreads) k_col_stats(const TX* __restrict__ X, int n, int p,
+                                                            int ldx, int prep,
+                                                            double* __restrict__ mean,
+                                                            double* __restrict__ inv_scale,
+                                                            int* bad) {
+  constexpr int G = kStatThreads / 32;  // row groups per column block
+  __shared__ double part[G][33];
   __shared__ double s_mean[32];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int col = blockIdx.x * 32 + tx;
   double acc = 0.0;
   int nonfinite = 0;
-  if (col < p)
-    for (int k = ty; k < n; k += 8) {
+  if (col < p) {
+#pragma unroll 4
+    for (int k = ty; k < n; k += G) {
       const double v = ld_x(X, (size_t)k * ldx + col);
       acc += v;
       if (!isfinite(v)) nonfinite = 1;
     }
+  }
   part[ty][tx] = acc;
   __syncthreads();
   if (ty == 0) {
     double s = 0.0;
-    for (int g = 0; g < 8; ++g) s += part[g][tx];
+    for (int g = 0; g < G; ++g) s += part[g][tx];
     s_mean[tx] = (prep >= 1) ? s / n : 0.0;
   }
   __syncthreads();
   const double mu = s_mean[tx];
   acc = 0.0;
-  if (col < p && prep == 2)
-    for (int k = ty; k < n; k += 8) {
+  if (col < p && prep == 2) {
+#pragma unroll 4
+    for (int k = ty; k < n; k += G) {
       const double d = ld_x(X, (size_t)k * ldx + col) - mu;
       acc += d * d;
     }
+  }
   __syncthreads();
   part[ty][tx] = acc;
   __syncthreads();
   if (ty == 0 && col < p) {
     double s = 0.0;
-    for (int g = 0; g < 8; ++g) s += part[g][tx];
+    for (int g = 0; g < G; ++g) s += part[g][tx];
     double inv = 1.0;
     if (prep == 2) {
       const double sd = sqrt(s / n);
@@ -78,10 +87,11 @@ cudaError_t launch_col_stats(const void* X, int x_f32, int n, int p, int ldx, in
                              double* mean, double* inv_scale, int* bad, cudaStream_t st) {
   const int grid = (p + 31) / 32;
   if (x_f32)
-    k_col_stats<float><<<grid, 256, 0, st>>>((const float*)X, n, p, ldx, prep, mean, inv_scale, bad);
+    k_col_stats<float><<<grid, kStatThreads, 0, st>>>((const float*)X, n, p, ldx, prep, mean,
+                                                      inv_scale, bad);
   else
-    k_col_stats<double><<<grid, 256, 0, st>>>((const double*)X, n, p, ldx, prep, mean, inv_scale,
-                                              bad);
+    k_col_stats<double><<<grid, kStatThreads, 0, st>>>((const double*)X, n, p, ldx, prep, mean,
+                                                       inv_scale, bad);
   note_launches(1);
   return cudaGetLastError();
 }

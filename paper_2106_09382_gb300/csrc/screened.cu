@@ -88,20 +88,19 @@ __device__ __forceinline__ bool same_bits(double a, double b) {
 __device__ __forceinline__ float nan_t(float) { return __int_as_float(0x7fffffff); }
 __device__ __forceinline__ double nan_t(double) { return __longlong_as_double(0x7fffffffffffffffll); }
 
-// Appends (i, j) for every lane whose predicate holds (all 32 lanes call).
-__device__ __forceinline__ void push_pair(bool pred, int i, int j, int2* list, int* count, int cap,
-                                          int lane) {
-  const unsigned m = __ballot_sync(FULL, pred);
-  if (!m) return;
-  const int leader = __ffs(m) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(count, __popc(m));
-  base = __shfl_sync(FULL, base, leader);
-  if (pred) {
-    const int r = base + __popc(m & ((1u << lane) - 1u));
-    if (r < cap) list[r] = make_int2(i, j);
-  }
+// High 32 bits of |v| as an unsigned integer: for finite values their order
+// is the order of the magnitudes (IEEE layout), up to the low mantissa bits
+// of doubles, which only makes the test below conservative.
+__device__ __forceinline__ unsigned mag_hi(float v) { return __float_as_uint(v) & 0x7fffffffu; }
+__device__ __forceinline__ unsigned mag_hi(double v) {
+  return (unsigned)((unsigned long long)__double_as_longlong(v) >> 32) & 0x7fffffffu;
 }
+// Largest high word whose magnitudes are all below `bound` (> 0).
+__device__ __forceinline__ unsigned mag_hi_below(float bound) { return __float_as_uint(bound) - 1u; }
+__device__ __forceinline__ unsigned mag_hi_below(double bound) {
+  return (unsigned)((unsigned long long)__double_as_longlong(bound) >> 32) - 1u;
+}
+
 
 // Exclusive prefix sum by one CTA: out[k] = sum_{q<k} f(q) for k <= n (and
 // the same into out2 when given).
@@ -146,6 +145,33 @@ __device__ void cta_scan(F f, int n, int* out, int* out2, int* s_tmp) {
 
 __device__ __forceinline__ int ldi(const int* p) { return __ldcg(p); }
 
+// Barrier among the CTAs that increment `counter` (zeroed before first use):
+// returns when it reaches `target` (participants x rounds so far) or the
+// abort word is set; a wait that runs out records a timeout.
+__device__ __forceinline__ void sub_barrier(unsigned* counter, unsigned target, const WaitCtl& w,
+                                            int where) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    red_release_add_u32(counter, 1u);
+    const uint64_t t0 = globaltimer_ns();
+    unsigned it = 0;
+    while (ld_acquire_u32(counter) < target) {
+      if ((++it & 15u) == 0) {
+        if (ld_relaxed_s32(w.abort) != 0) break;
+        if (globaltimer_ns() - t0 > w.timeout_ns) {
+          record_timeout(w, -1 - (int)blockIdx.x, where);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+
+
 template <typename T>
 __device__ __forceinline__ void load8(const T* src, T (&o)[8]) {
   using VT = Vec<T>;
@@ -181,22 +207,60 @@ __device__ __forceinline__ void reduce_parts(double (&v)[kParts], double* out,
   __syncthreads();
 }
 
-// Pass over the upper triangle in 8-row chunks of 32 x 32 tiles (lane l takes
-// column j = tb*32 + l; W_ji / V_ji come from row j as one 8-element vector):
-//   * verify (V != null): a non-candidate pair (V_ij not NaN) fails when
-//     |(0 - V_ij) - V_ji| > lambda, Eq. 3's test for leaving w_ij = 0;
-//   * screen: (i, j) is a candidate of the next sweep when w_ij != 0 or
-//     |(0 - W_ij) - W_ji| > lambda;
-//   * objective / KKT terms (as the dense kernel's pass) when do_kkt.
+// Appends (i, j) for every lane whose predicate holds (all 32 lanes call).
+__device__ __forceinline__ void push_list(bool pred, int i, int j, int2* list, int* count, int cap,
+                                          int lane) {
+  const unsigned m = __ballot_sync(FULL, pred);
+  if (!m) return;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(FULL, base, leader);
+  if (pred) {
+    const int r = base + __popc(m & ((1u << lane) - 1u));
+    if (r < cap) list[r] = make_int2(i, j);
+  }
+}
+
+// Appends (i, j) to a candidate list and counts it for both rows.
+__device__ __forceinline__ void push_cand(bool pred, int i, int j, int2* list, int* count,
+                                          int* cnt_r, int cap, int lane) {
+  const unsigned m = __ballot_sync(FULL, pred);
+  if (!m) return;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(FULL, base, leader);
+  if (pred) {
+    const int r = base + __popc(m & ((1u << lane) - 1u));
+    if (r < cap) {
+      list[r] = make_int2(i, j);
+      atomicAdd(cnt_r + i, 1);
+      atomicAdd(cnt_r + j, 1);
+    }
+  }
+}
+
+// KKT residual term of an off-diagonal pair (absolute, S units) with
+// G = W_ij + W_ji in FP64.
+__device__ __forceinline__ double kkt_offdiag(double om, double g, double lam) {
+  if (om > 0.0) return fabs(g + lam);
+  if (om < 0.0) return fabs(g - lam);
+  return fmax(fabs(g) - lam, 0.0);
+}
+
+// Screen of a launch's starting point over the upper triangle, in 8-row
+// chunks of 32 x 32 tiles (lane l takes column j = tb*32 + l; W_ji comes from
+// row j as one 8-element vector): (i, j) is a candidate when w_ij != 0 or
+// |(0 - W_ij) - W_ji| > lambda.  With do_kkt it also forms the objective and
+// KKT terms of the whole matrix (diagonal included).
 template <typename T, bool MIXED>
-__device__ void tile_pass(const ScreenArgs<T>& a, const T* __restrict__ W, const T* __restrict__ V,
-                          int nxt, bool do_kkt, double (&v)[kParts], int lane, int gwarp,
-                          int gwarps) {
+__device__ void screen_pass(const ScreenArgs<T>& a, const T* __restrict__ W, int lst, bool do_kkt,
+                            double (&v)[kParts], int lane, int gwarp, int gwarps) {
   const int p = a.p, ld = a.ld;
   const ScreenWork<T>& w = a.w;
   const int nb = (p + kTile - 1) / kTile;
   const double lamd = a.lambda;
-  const float lamf = (float)a.lambda;
   const T lam = (T)a.lambda;
   const int units = nb * nb * 4;
   for (int u = gwarp; u < units; u += gwarps) {
@@ -207,38 +271,26 @@ __device__ void tile_pass(const ScreenArgs<T>& a, const T* __restrict__ W, const
     const int i0 = ta * kTile + r0;
     if (i0 >= p) continue;
     const bool jv = j < p;
-    T w1[8], om8[8], wt[8], v1[8], vt[8];
+    T w1[8], om8[8], wt[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const int i = i0 + r;
       const bool ok = jv && i < p;
       w1[r] = ok ? __ldcg(W + (size_t)i * ld + j) : (T)0;
       om8[r] = ok ? __ldcg(a.Om + (size_t)i * ld + j) : (T)0;
-      v1[r] = (ok && V) ? __ldcg(V + (size_t)i * ld + j) : (T)0;
     }
-    if (jv) {
+    if (jv)
       load8(W + (size_t)j * ld + i0, wt);
-      if (V) load8(V + (size_t)j * ld + i0, vt);
-    }
-    if (!jv || !V) {
+    else
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        if (!jv) wt[r] = (T)0;
-        vt[r] = (T)0;
-      }
-    }
+      for (int r = 0; r < 8; ++r) wt[r] = (T)0;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const int i = i0 + r;
       const bool pair = jv && i < p && i < j;
-      if (V) {
-        const T x = ((T)0 - v1[r]) - vt[r];
-        const bool bad = pair && !isnan(v1[r]) && (fabs(x) - lam > (T)0);
-        push_pair(bad, i, j, w.fail, w.ctr + kCtrFail, w.fail_cap, lane);
-      }
       const T x0 = ((T)0 - w1[r]) - wt[r];
       const bool cand = pair && (om8[r] != (T)0 || fabs(x0) - lam > (T)0);
-      push_pair(cand, i, j, w.cand[nxt], w.ctr + kCtrCand + nxt, w.nc_cap, lane);
+      push_cand(cand, i, j, w.cand[lst], w.ctr + kCtrCand + lst, w.cnt_r[lst], w.nc_cap, lane);
     }
     if (!do_kkt) continue;
 #pragma unroll
@@ -246,20 +298,9 @@ __device__ void tile_pass(const ScreenArgs<T>& a, const T* __restrict__ W, const
       const int i = i0 + r;
       if (!jv || i >= p) continue;
       if (i < j) {
-        const T om_t = om8[r];
-        const float w1f = (float)w1[r], w2f = (float)wt[r];
-        const float gf = w1f + w2f;
-        if (om_t == (T)0 && fabsf(gf) <= lamf - 1e-5f * (1.0f + fabsf(w1f) + fabsf(w2f))) continue;
-        const double om = (double)om_t;
+        const double om = (double)om8[r];
         const double g = (double)w1[r] + (double)wt[r];
-        double res;
-        if (om > 0.0)
-          res = fabs(g + lamd);
-        else if (om < 0.0)
-          res = fabs(g - lamd);
-        else
-          res = fmax(fabs(g) - lamd, 0.0);
-        v[kPartKkt] = fmax(v[kPartKkt], res);
+        v[kPartKkt] = fmax(v[kPartKkt], kkt_offdiag(om, g, lamd));
         v[kPartQuad] += om * g;
         v[kPartPen] += fabs(om);
         if (!isfinite(g) || !isfinite(om)) v[kPartBad] += 1.0;
@@ -272,6 +313,81 @@ __device__ void tile_pass(const ScreenArgs<T>& a, const T* __restrict__ W, const
           v[kPartLog] += log(oii);
         } else {
           v[kPartBad] += 1.0;
+        }
+      }
+    }
+  }
+}
+
+// After a sweep, over the pairs outside the candidates (V_ij not NaN; every
+// such pair has w_ij = 0): the verification |(0 - V_ij) - V_ji| <= lambda
+// (Eq. 3's test for staying at zero; a failing pair joins the fail list),
+// their KKT terms max(|G_ij| - lambda, 0), and the screen of the next sweep.
+// Only W and V are read; the candidates' own terms come from the candidate
+// list and the diagonal's from the row pass.
+template <typename T>
+__device__ void verify_pass(const ScreenArgs<T>& a, const T* __restrict__ W,
+                            const T* __restrict__ V, int nxt, double (&v)[kParts], int lane,
+                            int gwarp, int gwarps) {
+  const int p = a.p, ld = a.ld;
+  const ScreenWork<T>& w = a.w;
+  const int nb = (p + kTile - 1) / kTile;
+  const double lamd = a.lambda;
+  const float lamf = (float)a.lambda;
+  const T lam = (T)a.lambda;
+  const int units = nb * nb * 4;
+  // |a|, |b| < lambda / 2 (slightly less, covering the rounding of a + b)
+  // decides the common case without floating-point work: |a + b| <= lambda,
+  // so no failure, no candidate and a zero KKT term
+  const unsigned small = mag_hi_below((T)(0.5 * a.lambda * (1.0 - 1e-6)));
+  for (int u = gwarp; u < units; u += gwarps) {
+    const int tau = u >> 2, r0 = (u & 3) * 8;
+    const int ta = tau / nb, tb = tau % nb;
+    if (ta > tb) continue;
+    const int j = tb * kTile + lane;
+    const int i0 = ta * kTile + r0;
+    if (i0 >= p) continue;
+    const bool jv = j < p;
+    T w1[8], v1[8], wt[8], vt[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = i0 + r;
+      const bool ok = jv && i < p && i < j;
+      w1[r] = ok ? __ldcg(W + (size_t)i * ld + j) : (T)0;
+      v1[r] = ok ? __ldcg(V + (size_t)i * ld + j) : nan_t((T)0);
+    }
+    if (jv && i0 < j) {
+      load8(W + (size_t)j * ld + i0, wt);
+      load8(V + (size_t)j * ld + i0, vt);
+    } else {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) wt[r] = vt[r] = (T)0;
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = i0 + r;
+      const bool pair = jv && i < p && i < j && !isnan(v1[r]);
+      const bool vsmall = mag_hi(v1[r]) <= small && mag_hi(vt[r]) <= small;
+      const bool wsmall = mag_hi(w1[r]) <= small && mag_hi(wt[r]) <= small;
+      bool bad = false, next = false;
+      if (pair && !vsmall) {
+        const T x = ((T)0 - v1[r]) - vt[r];
+        bad = fabs(x) - lam > (T)0;
+      }
+      push_list(bad, i, j, w.fail, w.ctr + kCtrFail, w.fail_cap, lane);
+      if (pair && !wsmall) {
+        const T x0 = ((T)0 - w1[r]) - wt[r];
+        next = fabs(x0) - lam > (T)0;
+      }
+      push_cand(next, i, j, w.cand[nxt], w.ctr + kCtrCand + nxt, w.cnt_r[nxt], w.nc_cap, lane);
+      if (pair && !wsmall) {
+        // residual exactly 0 when |G| is below lambda by more than FP32
+        // rounding; otherwise evaluated in FP64
+        const float w1f = (float)w1[r], w2f = (float)wt[r];
+        if (!(fabsf(w1f + w2f) <= lamf - 1e-5f * (1.0f + fabsf(w1f) + fabsf(w2f)))) {
+          const double g = (double)w1[r] + (double)wt[r];
+          v[kPartKkt] = fmax(v[kPartKkt], fmax(fabs(g) - lamd, 0.0));
+          if (!isfinite(g)) v[kPartBad] += 1.0;
         }
       }
     }
@@ -293,12 +409,13 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
   const ScreenWork<T>& w = a.w;
   const WaitCtl& wc = a.wait;
   const T lam = (T)a.lambda;
+  const double lamd = a.lambda;
 
   __shared__ double red[kScreenThreads / 32][kParts];
   __shared__ int s_tmp[32];
   __shared__ double s_res[kRes];
   __shared__ int s_stop;
-  extern __shared__ __align__(16) unsigned char dyn[];
+  extern __shared__ __align__(128) unsigned char dyn[];
 
   unsigned gen = 0;
   int where = 0;
@@ -310,15 +427,15 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
   int status = -1;  // set when the launch ends early (overflow: kStatusDense)
   const bool kkt0 = a.kkt_only || a.n_sweeps <= 0;  // objective / KKT only
   int redo_total = 0;
+  bool need_scan = true;  // row offsets of the current list still to be computed
 
-  // ---------------- screen the starting point (and its KKT for kkt_only)
+  // ---------------- screen the starting point (and its KKT for kkt_only);
+  //                  the host zeroed the counters and row counts
   {
     double v[kParts];
 #pragma unroll
     for (int k = 0; k < kParts; ++k) v[k] = 0.0;
-    for (int k = gtid; k <= P; k += gthreads) w.cnt_c[k] = 0;
-    for (int k = gtid; k <= p; k += gthreads) w.cnt_r[k] = 0;
-    tile_pass<T, MIXED>(a, Wa, nullptr, cur, kkt0, v, lane, gwarp, gwarps);
+    screen_pass<T, MIXED>(a, Wa, cur, kkt0, v, lane, gwarp, gwarps);
     if (kkt0) reduce_parts(v, a.partials, red);
     grid_barrier(a.barrier, gen, wc, ++where);
   }
@@ -337,57 +454,32 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
           break;
         }
         const int2* cand = w.cand[cur];
-        // ---- build: colour and row buckets
-        for (int e = gtid; e < N; e += gthreads) {
-          const int2 pr = __ldcg(cand + e);
-          atomicAdd(w.cnt_c + pair_step(pr.x, pr.y, P), 1);
-          atomicAdd(w.cnt_r + pr.x, 1);
-          atomicAdd(w.cnt_r + pr.y, 1);
+        // ---- build: row buckets of the current list (counted at the push),
+        //      each row's candidates in colour-step order, and per candidate
+        //      its record and correction terms
+        if (need_scan) {  // else the previous sweep's reduce phase scanned the counts
+          if (blockIdx.x == 0)
+            cta_scan([&](int k) { return ldi(w.cnt_r[cur] + k); }, p, w.off_r, w.cur_r, s_tmp);
+          grid_barrier(a.barrier, gen, wc, ++where);
         }
-        grid_barrier(a.barrier, gen, wc, ++where);
-        if (blockIdx.x == 0)
-          cta_scan([&](int k) { return ldi(w.cnt_c + k); }, P, w.off_c, w.cur_c, s_tmp);
-        if (blockIdx.x == (gridDim.x > 1 ? 1 : 0))
-          cta_scan([&](int k) { return ldi(w.cnt_r + k); }, p, w.off_r, w.cur_r, s_tmp);
-        grid_barrier(a.barrier, gen, wc, ++where);
-        for (int e = gtid; e < N; e += gthreads) {
-          const int2 pr = __ldcg(cand + e);
-          const int c = pair_step(pr.x, pr.y, P);
-          const int pos = atomicAdd(w.cur_c + c, 1);
-          w.nd_i[pos] = pr.x;
-          w.nd_j[pos] = pr.y;
-          w.nd_c[pos] = c;
-        }
-        grid_barrier(a.barrier, gen, wc, ++where);
-        // one colour's candidates in row order (deterministic numbering)
-        for (int c = gtid; c < P; c += gthreads) {
-          const int b = ldi(w.off_c + c), e = ldi(w.off_c + c + 1);
-          for (int x = b + 1; x < e; ++x) {
-            const int ki = ldi(w.nd_i + x), kj = ldi(w.nd_j + x);
-            int y = x - 1;
-            while (y >= b && ldi(w.nd_i + y) > ki) {
-              w.nd_i[y + 1] = ldi(w.nd_i + y);
-              w.nd_j[y + 1] = ldi(w.nd_j + y);
-              --y;
-            }
-            w.nd_i[y + 1] = ki;
-            w.nd_j[y + 1] = kj;
-          }
-        }
-        grid_barrier(a.barrier, gen, wc, ++where);
+        need_scan = true;
+        if (gtid == 0) w.ctr[kCtrTerms] = 0;  // allocated from two phases later
         for (int k = gtid; k < N; k += gthreads) {
-          const int i = ldi(w.nd_i + k), j = ldi(w.nd_j + k);
-          w.row_ent[atomicAdd(w.cur_r + i, 1)] = k;
-          w.row_ent[atomicAdd(w.cur_r + j, 1)] = k;
+          const int2 pr = __ldcg(cand + k);
+          w.row_ent[atomicAdd(w.cur_r + pr.x, 1)] = k;
+          w.row_ent[atomicAdd(w.cur_r + pr.y, 1)] = k;
         }
         grid_barrier(a.barrier, gen, wc, ++where);
-        // each row's candidates in step order (= candidate order)
         for (int r = gtid; r < p; r += gthreads) {
           const int b = ldi(w.off_r + r), e = ldi(w.off_r + r + 1);
           for (int x = b + 1; x < e; ++x) {
             const int key = ldi(w.row_ent + x);
+            const int2 kp = __ldcg(cand + key);
+            const int kc = pair_step(kp.x, kp.y, P);
             int y = x - 1;
-            while (y >= b && ldi(w.row_ent + y) > key) {
+            while (y >= b) {
+              const int2 yp = __ldcg(cand + ldi(w.row_ent + y));
+              if (pair_step(yp.x, yp.y, P) <= kc) break;
               w.row_ent[y + 1] = ldi(w.row_ent + y);
               --y;
             }
@@ -395,53 +487,55 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
           }
           for (int x = b; x < e; ++x) {
             const int k = ldi(w.row_ent + x);
-            if (ldi(w.nd_i + k) == r)
+            if (__ldcg(cand + k).x == r)
               w.nd_pi[k] = x - b;
             else
               w.nd_pj[k] = x - b;
           }
         }
         grid_barrier(a.barrier, gen, wc, ++where);
-        if (blockIdx.x == 0) {
-          cta_scan([&](int k) { return ldi(w.nd_pi + k) + ldi(w.nd_pj + k); }, N, w.term_ptr,
-                   nullptr, s_tmp);
-          if (threadIdx.x == 0) w.ctr[kCtrTerms] = ldi(w.term_ptr + N);
+        // operands; each candidate's terms (row i's earlier candidates, then
+        // row j's) get a contiguous range from a shared counter -- where the
+        // range lies does not affect any value
+        for (int k = gtid; k < N; k += gthreads) {
+          const int2 pr = __ldcg(cand + k);
+          const int i = pr.x, j = pr.y;
+          T* rec = w.nd_rec + 4 * (size_t)k;
+          rec[0] = __ldcg(Wa + (size_t)i * ld + j);
+          rec[1] = __ldcg(Wa + (size_t)j * ld + i);
+          rec[2] = __ldcg(a.Om + (size_t)i * ld + j);
+          rec[3] = a.sdiag[i] + a.sdiag[j];
+          const int bi = ldi(w.off_r + i), pi = ldi(w.nd_pi + k);
+          const int bj = ldi(w.off_r + j), pj = ldi(w.nd_pj + k);
+          int tp = pi + pj > 0 ? atomicAdd(w.ctr + kCtrTerms, pi + pj) : 0;
+          w.term_ptr[k] = tp;
+          w.nd_delta[k] = (T)0;  // the fixed-point iteration starts from no change
+          if (tp + pi + pj > w.term_cap) continue;  // overflow: the sweep goes dense
+          for (int m = 0; m < pi; ++m, ++tp) {
+            const int q = ldi(w.row_ent + bi + m);
+            const int2 qp = __ldcg(cand + q);
+            const int u = qp.x == i ? qp.y : qp.x;
+            w.term_pred[tp] = q;
+            w.term_s[tp] = __ldg(a.S + (size_t)u * ld + j);
+          }
+          for (int m = 0; m < pj; ++m, ++tp) {
+            const int q = ldi(w.row_ent + bj + m);
+            const int2 qp = __ldcg(cand + q);
+            const int u = qp.x == j ? qp.y : qp.x;
+            w.term_pred[tp] = q;
+            w.term_s[tp] = __ldg(a.S + (size_t)u * ld + i);
+          }
+        }
+        if (gtid < kJacMax) w.jac[gtid] = 0;
+        if (gtid == 0) {
+          w.ctr[kCtrJacBar] = 0;
+          w.ctr[kCtrJacDone] = 0;
         }
         grid_barrier(a.barrier, gen, wc, ++where);
         if (ldi(w.ctr + kCtrTerms) > w.term_cap) {
           status = kStatusDense;
           break;
         }
-        // ---- operands of every candidate: W_ij, W_ji, w_ij at the sweep
-        //      start, s_ii + s_jj, and the S entries of the corrections
-        for (int k = gtid; k < N; k += gthreads) {
-          const int i = ldi(w.nd_i + k), j = ldi(w.nd_j + k);
-          T* rec = w.nd_rec + 4 * (size_t)k;
-          rec[0] = __ldcg(Wa + (size_t)i * ld + j);
-          rec[1] = __ldcg(Wa + (size_t)j * ld + i);
-          rec[2] = __ldcg(a.Om + (size_t)i * ld + j);
-          rec[3] = a.sdiag[i] + a.sdiag[j];
-          int tp = ldi(w.term_ptr + k);
-          const int bi = ldi(w.off_r + i), pi = ldi(w.nd_pi + k);
-          for (int m = 0; m < pi; ++m, ++tp) {
-            const int q = ldi(w.row_ent + bi + m);
-            const int qi = ldi(w.nd_i + q), qj = ldi(w.nd_j + q);
-            const int u = qi == i ? qj : qi;
-            w.term_pred[tp] = q;
-            w.term_s[tp] = __ldg(a.S + (size_t)u * ld + j);
-          }
-          const int bj = ldi(w.off_r + j), pj = ldi(w.nd_pj + k);
-          for (int m = 0; m < pj; ++m, ++tp) {
-            const int q = ldi(w.row_ent + bj + m);
-            const int qi = ldi(w.nd_i + q), qj = ldi(w.nd_j + q);
-            const int u = qi == j ? qj : qi;
-            w.term_pred[tp] = q;
-            w.term_s[tp] = __ldg(a.S + (size_t)u * ld + i);
-          }
-          w.nd_delta[k] = (T)0;  // the fixed-point iteration starts from no change
-        }
-        if (gtid < kJacMax) w.jac[gtid] = 0;
-        grid_barrier(a.barrier, gen, wc, ++where);
         // ---- chain, in parallel: the changes d solve d_k = F_k(d of the
         //      earlier candidates sharing row i or j), a system over a DAG in
         //      colour-step order whose unique solution is the sequential
@@ -452,8 +546,10 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         //      iteration settles after a few dozen rounds instead of one
         //      round per link.  Thread gtid owns candidate gtid (operands in
         //      registers); further candidates (N > threads) reload theirs.
-        bool converged = false;
-        {
+        // only the CTAs that own candidates iterate (barrier among them);
+        // the others wait at the phase's closing grid barrier
+        const int jac_ctas = min((int)gridDim.x, (N + (int)blockDim.x - 1) / (int)blockDim.x);
+        if ((int)blockIdx.x < jac_ctas) {
           const int k0 = gtid;
           const bool own = k0 < N;
           T w1 = (T)0, w2 = (T)0, om = (T)0, ss = (T)1;
@@ -467,8 +563,9 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
             om = __ldcg(rec + 2);
             ss = __ldcg(rec + 3);
             t0 = ldi(w.term_ptr + k0);
-            ts = t0 + ldi(w.nd_pi + k0);
-            nt = ldi(w.term_ptr + k0 + 1) - t0;
+            const int pi = ldi(w.nd_pi + k0);
+            ts = t0 + pi;
+            nt = pi + ldi(w.nd_pj + k0);
 #pragma unroll
             for (int x = 0; x < 4; ++x)
               if (x < nt) {
@@ -516,7 +613,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
             for (int k = gtid + gthreads; k < N; k += gthreads) {
               const T* rec = w.nd_rec + 4 * (size_t)k;
               const int u0 = ldi(w.term_ptr + k), us = u0 + ldi(w.nd_pi + k),
-                        u1 = ldi(w.term_ptr + k + 1);
+                        u1 = us + ldi(w.nd_pj + k);
               T vij = __ldcg(rec), vji = __ldcg(rec + 1);
               const T omk = __ldcg(rec + 2), ssk = __ldcg(rec + 3);
               for (int x = u0; x < u1; ++x) {
@@ -538,99 +635,33 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
               w.nd_new[k] = nw;
             }
             if (__syncthreads_or(changed) && threadIdx.x == 0) atomicAdd(w.jac + r, 1);
-            grid_barrier(a.barrier, gen, wc, ++where);
+            sub_barrier((unsigned*)(w.ctr + kCtrJacBar), (unsigned)(r + 1) * jac_ctas, wc,
+                        ++where);
             const T* tmp = dcur;
             dcur = dnext;
             dnext = const_cast<T*>(tmp);
             if (ldi(w.jac + r) == 0) {
-              converged = true;
+              // the solution sits in dcur; keep it in nd_delta
+              if (dcur != w.nd_delta)
+                for (int k = gtid; k < N; k += jac_ctas * (int)blockDim.x)
+                  w.nd_delta[k] = __ldcg(dcur + k);
+              if (gtid == 0) w.ctr[kCtrJacDone] = 1;
               break;
             }
           }
-          // the solution sits in dcur; keep it in nd_delta
-          if (converged && dcur != w.nd_delta)
-            for (int k = gtid; k < N; k += gthreads) w.nd_delta[k] = __ldcg(dcur + k);
-        }
-        // ---- chain: Eq. 3 for the candidates in colour-step order.  Warp 0
-        //      of CTA 0 stages chunks of candidate records and terms into
-        //      shared memory; lane 0 walks them.  The change of the previous
-        //      candidate (the usual predecessor) stays in a register, older
-        //      ones come from a shared-memory ring (global memory beyond it).
-        if (!converged && blockIdx.x == 0 && wid == 0) {
-          T* ring = reinterpret_cast<T*>(dyn);
-          T* s_rec = ring + kSeqRing;
-          T* s_ts = s_rec + 4 * kSeqNodes;
-          int* s_tp = reinterpret_cast<int*>(s_ts + kSeqTerms);
-          int* s_pi = s_tp + kSeqNodes + 1;
-          int* s_pred = s_pi + kSeqNodes;
-          T dprev = (T)0;
-          for (int base = 0; base < N;) {
-            int end = min(N, base + kSeqNodes);
-            const int tp0 = ldi(w.term_ptr + base);
-            while (end > base + 1 && ldi(w.term_ptr + end) - tp0 > kSeqTerms)
-              end = base + ((end - base) >> 1);
-            const int tp1 = ldi(w.term_ptr + end);
-            const bool staged = tp1 - tp0 <= kSeqTerms;  // else one candidate, terms in place
-            const int nn = end - base;
-            for (int q = lane; q < 4 * nn; q += 32) s_rec[q] = __ldcg(w.nd_rec + 4 * (size_t)base + q);
-            for (int q = lane; q < nn; q += 32) {
-              s_tp[q] = ldi(w.term_ptr + base + q) - tp0;
-              s_pi[q] = ldi(w.nd_pi + base + q);
-            }
-            if (lane == 0) s_tp[nn] = tp1 - tp0;
-            if (staged)
-              for (int q = lane; q < tp1 - tp0; q += 32) {
-                s_pred[q] = ldi(w.term_pred + tp0 + q);
-                s_ts[q] = __ldcg(w.term_s + tp0 + q);
-              }
-            __syncwarp();
-            if (lane == 0) {
-              const int* tpred = staged ? s_pred : w.term_pred + tp0;
-              const T* tval = staged ? s_ts : w.term_s + tp0;
-              for (int q = 0; q < nn; ++q) {
-                const int k = base + q;
-                const T w1 = s_rec[4 * q], w2 = s_rec[4 * q + 1];
-                const T om = s_rec[4 * q + 2], ss = s_rec[4 * q + 3];
-                const int t0 = s_tp[q], ts = t0 + s_pi[q], t1 = s_tp[q + 1];
-                T vij = w1, vji = w2;
-                for (int x = t0; x < t1; ++x) {
-                  const int pr = tpred[x];
-                  const T sv = tval[x];
-                  T d;
-                  if (pr == k - 1)
-                    d = dprev;
-                  else if (k - pr <= kSeqRing)
-                    d = ring[pr & (kSeqRing - 1)];
-                  else
-                    d = __ldcg(w.nd_delta + pr);
-                  if (d != (T)0) {
-                    if (x < ts)
-                      vij = fma_t(d, sv, vij);
-                    else
-                      vji = fma_t(d, sv, vji);
-                  }
-                }
-                const T xv = (ss * om - vij) - vji;
-                const T sx = soft(xv, lam);
-                T nw = (T)0;
-                if (sx != (T)0) nw = sx / ss;
-                const T delta = nw - om;
-                dprev = delta;
-                ring[k & (kSeqRing - 1)] = delta;
-                w.nd_delta[k] = delta;
-                w.nd_new[k] = nw;
-              }
-            }
-            __syncwarp();
-            base = end;
-          }
         }
         grid_barrier(a.barrier, gen, wc, ++where);
+        if (ldi(w.ctr + kCtrJacDone) == 0) {
+          // not settled: nothing changed yet, the dense kernel takes the sweep
+          status = kStatusDense;
+          break;
+        }
         // ---- rows: W after the colour steps, Eq. 2, W += dw S_i, V
         if (gtid == 0) {
           w.ctr[kCtrCand + (1 - cur)] = 0;
           w.ctr[kCtrFail] = 0;
         }
+        for (int k = gtid; k <= p; k += gthreads) w.cnt_r[1 - cur][k] = 0;
         {
           int* l_u = reinterpret_cast<int*>(dyn) + wid * kRowList * 2;
           int* l_c = l_u + kRowList;
@@ -648,8 +679,8 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
               T d = (T)0, sv = (T)0;
               if (m < ne) {
                 const int q = ldi(w.row_ent + b + m);
-                const int qi = ldi(w.nd_i + q), qj = ldi(w.nd_j + q);
-                const int u = qi == i ? qj : qi;
+                const int2 qp = __ldcg(w.cand[cur] + q);
+                const int u = qp.x == i ? qp.y : qp.x;
                 if (m0 == 0) my_u = u;
                 d = __ldcg(w.nd_delta + q);
                 if (d != (T)0) sv = __ldg(a.S + (size_t)u * ld + i);
@@ -676,6 +707,17 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
               a.Om[(size_t)i * ld + i] = (T)nw;
               dd = (T)(nw - oii);
               dd64 = fabs(nw - oii);
+              // objective / KKT terms of the diagonal after the sweep
+              const T wend = dd != (T)0 ? fma_t(dd, __ldg(a.S + (size_t)i * ld + i), wii) : wii;
+              const double wd = (double)wend;
+              const double od = MIXED ? nw : (double)(T)nw;
+              if (od > 0.0 && isfinite(wd) && isfinite(od)) {
+                v[kPartKkt] = fmax(v[kPartKkt], fabs(wd - 1.0 / od));
+                v[kPartQuad] += od * wd;
+                v[kPartLog] += log(od);
+              } else {
+                v[kPartBad] += 1.0;
+              }
             }
             dd = __shfl_sync(FULL, dd, 0);
             v[kPartDelta] = fmax(v[kPartDelta], dd64);
@@ -704,9 +746,10 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
                 if (__popc(bal) > room) break;
                 if (nz) {
                   const int slot = cnt + __popc(bal & ((1u << lane) - 1u));
-                  const int qi = ldi(w.nd_i + q), qj = ldi(w.nd_j + q);
-                  l_u[slot] = qi == i ? qj : qi;
-                  l_c[slot] = ldi(w.nd_c + q);
+                  const int2 qp = __ldcg(w.cand[cur] + q);
+                  const int u = qp.x == i ? qp.y : qp.x;
+                  l_u[slot] = u;
+                  l_c[slot] = pair_step(min(i, u), max(i, u), P);
                   l_d[slot] = d;
                 }
                 cnt += __popc(bal);
@@ -799,9 +842,8 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
               if (my_u >= 0) a.V[(size_t)i * ld + my_u] = nan_t((T)0);
             } else {
               for (int m = lane; m < ne; m += 32) {
-                const int q = ldi(w.row_ent + b + m);
-                const int qi = ldi(w.nd_i + q), qj = ldi(w.nd_j + q);
-                a.V[(size_t)i * ld + (qi == i ? qj : qi)] = nan_t((T)0);
+                const int2 qp = __ldcg(w.cand[cur] + ldi(w.row_ent + b + m));
+                a.V[(size_t)i * ld + (qp.x == i ? qp.y : qp.x)] = nan_t((T)0);
               }
             }
             if (lane == 0) a.V[(size_t)i * ld + i] = nan_t((T)0);
@@ -812,29 +854,50 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         for (int k = gtid; k < N; k += gthreads) {
           const T d = __ldcg(w.nd_delta + k);
           if (d != (T)0) {
-            const int i = ldi(w.nd_i + k), j = ldi(w.nd_j + k);
+            const int2 pr = __ldcg(cand + k);
             const T nw = __ldcg(w.nd_new + k);
-            a.Om[(size_t)i * ld + j] = nw;
-            a.Om[(size_t)j * ld + i] = nw;
+            a.Om[(size_t)pr.x * ld + pr.y] = nw;
+            a.Om[(size_t)pr.y * ld + pr.x] = nw;
             v[kPartDelta] = fmax(v[kPartDelta], (double)fabs(d));
             v[kPartActive] += 2.0;  // counted per owner, as the dense pass does
           }
         }
         grid_barrier(a.barrier, gen, wc, ++where);
-        // ---- verify + objective / KKT + screen of the next sweep
-        for (int k = gtid; k <= P; k += gthreads) w.cnt_c[k] = 0;
-        for (int k = gtid; k <= p; k += gthreads) w.cnt_r[k] = 0;
-        tile_pass<T, MIXED>(a, Wn, a.V, 1 - cur, true, v, lane, gwarp, gwarps);
+        // ---- verify the other pairs; objective / KKT; screen the next sweep
+        verify_pass<T>(a, Wn, a.V, 1 - cur, v, lane, gwarp, gwarps);
+        // the candidates' own terms (and their screen: every nonzero stays a
+        // candidate); warp-uniform trip count for the list pushes
+        for (int k0 = gwarp * 32; k0 < N; k0 += gwarps * 32) {
+          const int k = k0 + lane;
+          bool next = false;
+          int i = 0, j = 0;
+          if (k < N) {
+            const int2 pr = __ldcg(cand + k);
+            i = pr.x;
+            j = pr.y;
+            const T d = __ldcg(w.nd_delta + k);
+            const T omk = d != (T)0 ? __ldcg(w.nd_new + k) : __ldcg(w.nd_rec + 4 * (size_t)k + 2);
+            const T w1 = __ldcg(Wn + (size_t)i * ld + j), w2 = __ldcg(Wn + (size_t)j * ld + i);
+            const double om = (double)omk, g = (double)w1 + (double)w2;
+            next = omk != (T)0 || (fabs(((T)0 - w1) - w2) - lam > (T)0);
+            v[kPartKkt] = fmax(v[kPartKkt], kkt_offdiag(om, g, lamd));
+            v[kPartQuad] += om * g;
+            v[kPartPen] += fabs(om);
+            if (!isfinite(g) || !isfinite(om)) v[kPartBad] += 1.0;
+          }
+          push_cand(next, i, j, w.cand[1 - cur], w.ctr + kCtrCand + 1 - cur, w.cnt_r[1 - cur],
+                    w.nc_cap, lane);
+        }
         grid_barrier(a.barrier, gen, wc, ++where);
         const int nf = ldi(w.ctr + kCtrFail);
         if (nf == 0) break;
         // ---- undo the sweep, add the failing pairs, redo
         for (int k = gtid; k < N; k += gthreads) {
           if (__ldcg(w.nd_delta + k) != (T)0) {
-            const int i = ldi(w.nd_i + k), j = ldi(w.nd_j + k);
+            const int2 pr = __ldcg(cand + k);
             const T om = __ldcg(w.nd_rec + 4 * (size_t)k + 2);
-            a.Om[(size_t)i * ld + j] = om;
-            a.Om[(size_t)j * ld + i] = om;
+            a.Om[(size_t)pr.x * ld + pr.y] = om;
+            a.Om[(size_t)pr.y * ld + pr.x] = om;
           }
         }
         for (int i = gtid; i < p; i += gthreads) {
@@ -842,15 +905,20 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
           if (MIXED) a.omdiag64[i] = __ldcg(w.omdiag_old + i);
         }
         const int add = min(min(nf, w.fail_cap), w.nc_cap - N);
-        for (int f = gtid; f < add; f += gthreads) w.cand[cur][N + f] = __ldcg(w.fail + f);
+        for (int f = gtid; f < add; f += gthreads) {
+          const int2 pr = __ldcg(w.fail + f);
+          w.cand[cur][N + f] = pr;
+          atomicAdd(w.cnt_r[cur] + pr.x, 1);
+          atomicAdd(w.cnt_r[cur] + pr.y, 1);
+        }
         if (gtid == 0) {
           w.ctr[kCtrCand + cur] = N + add;
           w.ctr[kCtrFail] = 0;
         }
 #pragma unroll
         for (int k = 0; k < kParts; ++k) v[k] = 0.0;
-        grid_barrier(a.barrier, gen, wc, ++where);
         ++redo_total;
+        grid_barrier(a.barrier, gen, wc, ++where);
         if (add < min(nf, w.fail_cap) || ++redo > a.max_redo) {
           status = kStatusDense;
           break;
@@ -861,6 +929,10 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         break;
       }
       reduce_parts(v, a.partials, red);
+      // row offsets of the next sweep's list (its pushes are complete)
+      if (blockIdx.x == 0)
+        cta_scan([&](int k) { return ldi(w.cnt_r[1 - cur] + k); }, p, w.off_r, w.cur_r, s_tmp);
+      need_scan = false;
       grid_barrier(a.barrier, gen, wc, ++where);
     }
 
@@ -969,11 +1041,8 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
 }
 
 size_t screened_dyn_smem(bool mixed) {
-  const size_t e = mixed ? 4 : 8;
-  const size_t chain = e * (kSeqRing + 4 * kSeqNodes + kSeqTerms) +
-                       4 * ((kSeqNodes + 1) + kSeqNodes + kSeqTerms);
-  const size_t rows = (size_t)(kScreenThreads / 32) * kRowList * (8 + e);
-  return chain > rows ? chain : rows;
+  // per warp of the row pass: the staged changes (partner, step, delta)
+  return (size_t)(kScreenThreads / 32) * kRowList * (8 + (mixed ? 4 : 8));
 }
 
 template <typename T, bool MIXED>
