@@ -352,6 +352,39 @@ int concord_run(concord_state *st, double lambda, double tol, int max_sweeps,
                 int stop_rule, double switch_tol, concord_result *res);
 
 /*
+ * concord_path -- a warm-started regularisation path (the batched use of
+ * Algorithm 1: each lambda is swept from the previous lambda's Omega and W,
+ * the first from the state's current iterate).  lambdas (host, n_lambda > 0,
+ * each >= 0; usually decreasing from concord_lambda_max) are swept in order
+ * until KKT <= tol or max_sweeps per lambda, in the state's working
+ * precision (MIXED: FP32 sweeps with the FP64 diagonal, KKT and objective,
+ * no FP64 polish; FP64: FP64).  One persistent screened launch walks the
+ * whole path; a lambda whose sweeps overflow the candidate lists runs on the
+ * dense kernel and the path resumes after it.  results (host, nullable)
+ * receives one concord_result per lambda.  omega_out_dev (device, nullable)
+ * receives Omega after each lambda: slice k at offset k * p * ld_out, row
+ * stride ld_out >= p, element type of the working precision (float for
+ * MIXED, double for FP64).  The state ends on the last lambda's iterate.
+ */
+int concord_path(concord_state *st, const double *lambdas, int n_lambda, double tol,
+                 int max_sweeps, concord_result *results, void *omega_out_dev, int ld_out);
+
+/*
+ * concord_stability -- stability selection over subsamples: for each of
+ * n_sets subsamples of the rows of X (device, n x p, row stride ldx, dtype
+ * F64 / F32; subsample b is the set_sizes[b] row indices starting at
+ * rows[sum of earlier sizes], host arrays, each size in 2..n_cap), the
+ * Gram of its rows (prep as concord_solve_device) and the lambda path over
+ * lambdas from Omega = I; freq_dev (device, float, n_lambda x p x p, written
+ * completely) receives for each lambda the fraction of subsamples whose
+ * Omega has w_ij != 0.  The state ends on the last subsample's last lambda.
+ */
+int concord_stability(concord_state *st, const void *X_dev, int x_dtype, int n, int ldx, int prep,
+                      const int *rows, const int *set_sizes, int n_sets, const double *lambdas,
+                      int n_lambda, double tol, int max_sweeps, float *freq_dev);
+
+
+/*
  * concord_solve_device -- the whole path on resident data: prepare X
  * (n <= n_cap rows, device, row stride ldx, x_dtype), S = Z^T Z / n in the
  * state's Gram mode (FP64 state: CONCORD_GRAM_FP64; MIXED:

@@ -88,6 +88,9 @@ SIGNATURES = {
     "concord_set_fault": ([_vp, _ci, _ci], _ci),
     "concord_get_timing": ([_vp, _dp, _ip, _ci, _ip], _ci),
     "concord_kernel_launches": ([], ctypes.c_ulonglong),
+    "concord_path": ([_vp, _dp, _ci, _cd, _ci, _rp, _vp, _ci], _ci),
+    "concord_stability": ([_vp, _vp, _ci, _ci, _ci, _ci, _ip, _ip, _ci, _dp, _ci, _cd, _ci, _vp],
+                          _ci),
 }
 
 _lock = threading.Lock()
@@ -319,6 +322,43 @@ class State:
         self.last = r
         _check(rc, (OK, NOT_CONVERGED))
         return r
+
+    def path(self, lambdas, tol: float = 1e-5, max_sweeps: int = 1000, omega_out=None):
+        """Warm-started lambda path from the current iterate; returns one
+        ConcordResult per lambda.  omega_out (device tensor, n_lambda x p x
+        ldo, float32 for MIXED / float64 for FP64) receives each Omega."""
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        res = (ConcordResult * len(lam))()
+        optr, ldo = None, self.p
+        if omega_out is not None:
+            assert omega_out.is_cuda and omega_out.dim() == 3 and omega_out.stride(2) == 1
+            optr, ldo = omega_out.data_ptr(), omega_out.stride(1)
+        rc = load().concord_path(self._ptr, lam.ctypes.data_as(_dp), len(lam), float(tol),
+                                 int(max_sweeps), res, optr, ldo)
+        _check(rc)
+        return list(res)
+
+    def stability(self, X, subsets, lambdas, tol: float = 1e-5, max_sweeps: int = 1000,
+                  prep: int = PREP_STANDARDIZE, freq_out=None):
+        """Stability selection: for each row subset of X (device tensor), the
+        Gram of its rows and the lambda path from Omega = I; returns the
+        per-lambda edge frequencies (device float32 tensor n_lambda x p x p)."""
+        import torch
+        assert X.is_cuda and X.dim() == 2 and X.stride(1) == 1
+        rows = np.ascontiguousarray(np.concatenate([np.asarray(s, dtype=np.int32)
+                                                    for s in subsets]), dtype=np.int32)
+        sizes = np.ascontiguousarray([len(s) for s in subsets], dtype=np.int32)
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        if freq_out is None:
+            freq_out = torch.empty((len(lam), self.p, self.p), dtype=torch.float32,
+                                   device=X.device)
+        rc = load().concord_stability(self._ptr, X.data_ptr(), _dtype_code(X), X.shape[0],
+                                      X.stride(0), int(prep), rows.ctypes.data_as(_ip),
+                                      sizes.ctypes.data_as(_ip), len(sizes),
+                                      lam.ctypes.data_as(_dp), len(lam), float(tol),
+                                      int(max_sweeps), freq_out.data_ptr())
+        _check(rc)
+        return freq_out
 
     def solve_host(self, X: np.ndarray, lam: float, tol: float = 1e-5, max_sweeps: int = 1000,
                    prep: int = PREP_STANDARDIZE, stop_rule: int = STOP_KKT, Omega_out=None):

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <string>
+#include <vector>
 
 #include "concord.h"
 #include "kernels.h"
@@ -94,6 +95,11 @@ struct concord_state {
   void *Wb = nullptr, *V = nullptr, *scr = nullptr;
   int nc_cap = 0, term_cap = 0;
   int screened_grid = 0;
+  // lambda path / stability selection buffers (allocated on demand)
+  double *path_lam = nullptr, *path_res = nullptr;
+  int path_cap = 0;
+  int* rows_dev = nullptr;
+  size_t rows_cap = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaEvent_t lev[2 * kMaxTimedLaunches] = {};
   double launch_ms[kMaxTimedLaunches] = {};
@@ -392,12 +398,23 @@ ScreenWork<T> screen_work(concord_state* st) {
   return w;
 }
 
+// Optional lambda path of a screened launch (device arrays).
+struct PathArgs {
+  const double* lam;
+  int n, start;
+  double* res;
+  void* om;
+  int ldo;
+  float* cnt;
+};
+
 // One persistent launch of the screened sweep kernel; out->status_code is
 // the kernel's status (kStatusDense: hand the next sweep to the dense kernel).
 template <typename T>
 int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* omdiag64,
                         double lambda, double tol, int stop_rule, int n_sweeps, int kkt_only,
-                        int hist_offset, int stall_stop, RunOut* out, int* code) {
+                        int hist_offset, int stall_stop, RunOut* out, int* code,
+                        const PathArgs* path = nullptr) {
   int rc = ensure_screen(st);
   if (rc != CONCORD_OK) return rc;
   const ScreenLayout L = screen_layout(st->p, st->P, st->nc_cap, st->term_cap);
@@ -436,6 +453,15 @@ int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, d
   a.kkt_only = kkt_only;
   a.stall_stop = stall_stop;
   a.max_redo = 8;
+  if (path) {
+    a.path_lambda = path->lam;
+    a.path_n = path->n;
+    a.path_start = path->start;
+    a.path_res = path->res;
+    a.path_om = (T*)path->om;
+    a.path_ldo = path->ldo;
+    a.path_cnt = path->cnt;
+  }
   st->last_variant = CONCORD_SWEEP_SCREENED;
 
   const int slot_ev = st->n_launch < kMaxTimedLaunches ? st->n_launch : -1;
@@ -564,6 +590,92 @@ void fill_result(concord_result* res, const RunOut& o, int sweeps, int sweeps32,
   res->timeout_step = o.to_step;
   res->screen_redos = o.redos;
   res->dense_sweeps = o.dense_sweeps;
+}
+
+int ensure_path(concord_state* st, int n_lambda, size_t n_rows) {
+  if (n_lambda > st->path_cap) {
+    if (st->path_lam) cudaFree(st->path_lam);
+    if (st->path_res) cudaFree(st->path_res);
+    st->path_lam = nullptr;
+    st->path_res = nullptr;
+    st->path_cap = 0;
+    CK(cudaMalloc(&st->path_lam, sizeof(double) * n_lambda));
+    CK(cudaMalloc(&st->path_res, sizeof(double) * kRes * n_lambda));
+    st->path_cap = n_lambda;
+  }
+  if (n_rows > st->rows_cap) {
+    if (st->rows_dev) cudaFree(st->rows_dev);
+    st->rows_dev = nullptr;
+    st->rows_cap = 0;
+    CK(cudaMalloc(&st->rows_dev, sizeof(int) * n_rows));
+    st->rows_cap = n_rows;
+  }
+  return CONCORD_OK;
+}
+
+void result_from_row(concord_result* r, const double* row, double lambda) {
+  memset(r, 0, sizeof *r);
+  const int code = (int)row[kResStatus];
+  r->status = code == 0 ? CONCORD_OK : (code == 2 ? CONCORD_E_NONFINITE : CONCORD_NOT_CONVERGED);
+  r->sweeps = (int)row[kResSweeps];
+  r->first_delta_sweep = (int)row[kResFirstDelta];
+  r->objective = row[kResObj];
+  r->kkt = row[kResKkt];
+  r->delta = row[kResDelta];
+  r->lambda = lambda;
+  r->active_pairs = (long long)(row[kResActive] + 0.5);
+  r->timeout_vertex = r->timeout_step = -1;
+  r->screen_redos = (int)row[kResRedo];
+}
+
+// The lambda path in the state's working precision (lambdas already in
+// st->path_lam): one screened launch walks the lambdas, warm-starting each
+// from the previous; a lambda whose sweeps need the dense kernel runs through
+// the single-lambda dispatcher and the path resumes after it.
+template <typename T>
+int path_impl(concord_state* st, const double* lambdas, int n, double tol, int max_sweeps,
+              concord_result* results, void* om_out, int ldo, float* cnt) {
+  const bool mixed = sizeof(T) == 4;
+  T* S = (T*)st->S;
+  T* W = (T*)st->W;
+  T* Om = (T*)st->Om;
+  const T* sd = (const T*)st->sdiagT;
+  double* omd = mixed ? st->omdiag64 : nullptr;
+  std::vector<double> rows((size_t)kRes * n);
+  int start = 0;
+  st->n_launch = 0;
+  while (start < n) {
+    RunOut o;
+    int code = 0;
+    PathArgs pa{st->path_lam, n, start, st->path_res, om_out, ldo, cnt};
+    int rc = launch_screened_run<T>(st, S, W, Om, sd, omd, lambdas[start], tol, CONCORD_STOP_KKT,
+                                    max_sweeps, 0, 0, mixed ? 1 : 0, &o, &code, &pa);
+    if (rc != CONCORD_OK && rc != CONCORD_NOT_CONVERGED) return rc;
+    CK(cudaMemcpy(rows.data(), st->path_res, sizeof(double) * kRes * n, cudaMemcpyDeviceToHost));
+    const int stop = code == kStatusDense ? (int)st->h_result[kResPath] : n;
+    for (int k = start; k < stop && k < n; ++k)
+      if (results) result_from_row(results + k, rows.data() + (size_t)kRes * k, lambdas[k]);
+    if (code != kStatusDense) break;
+    // lambda `stop` on the dense-capable dispatcher (after the sweeps the
+    // path launch already did at it), then the rest of the path
+    const int done = (int)st->h_result[kResSweeps];
+    RunOut od;
+    rc = launch_run<T>(st, S, W, Om, sd, omd, lambdas[stop], tol, CONCORD_STOP_KKT,
+                       max_sweeps > done ? max_sweeps - done : 1, 0, 0, mixed ? 1 : 0, &od);
+    if (rc != CONCORD_OK) return rc;
+    if (results) fill_result(results + stop, od, done + od.sweeps, mixed ? done + od.sweeps : 0,
+                             od.first_delta, lambdas[stop], 0.0);
+    if (om_out)
+      CK(cudaMemcpy2DAsync((T*)om_out + (size_t)stop * st->p * ldo, sizeof(T) * ldo, Om,
+                           sizeof(T) * st->ld, sizeof(T) * st->p, st->p, cudaMemcpyDeviceToDevice,
+                           st->stream));
+    if (cnt)
+      CK(launch_support_add(Om, mixed ? 1 : 0, st->ld, st->p, cnt + (size_t)stop * st->p * st->p,
+                            st->stream));
+    start = stop + 1;
+  }
+  CK(cudaStreamSynchronize(st->stream));
+  return CONCORD_OK;
 }
 
 // mixed: FP32 iterate -> FP64 copies (Omega with its FP64 diagonal; W rebuilt
@@ -857,7 +969,7 @@ int concord_destroy(concord_state* st) {
   if (!st) return CONCORD_OK;
   cudaSetDevice(st->device);
   if (st->stream) cudaStreamSynchronize(st->stream);
-  void* dev[] = {st->Wb, st->V, st->scr, st->sd1_64, st->sd2_64, st->mbox, st->barrier, st->abort_info, st->flag, st->lmax, st->partials,
+  void* dev[] = {st->path_lam, st->path_res, st->rows_dev, st->Wb, st->V, st->scr, st->sd1_64, st->sd2_64, st->mbox, st->barrier, st->abort_info, st->flag, st->lmax, st->partials,
                  st->hist, st->result, st->mean, st->inv_scale, st->Z, st->Xstage, st->zt_hi,
                  st->zt_lo, st->sdiag64, st->sdiagT, st->omdiag64, st->S64, st->W64, st->Om64};
   for (void* d : dev)
@@ -1006,6 +1118,74 @@ int concord_run(concord_state* st, double lambda, double tol, int max_sweeps, in
   int rc = check_state(st);
   if (rc) return rc;
   return run_impl(st, lambda, tol, max_sweeps, stop_rule, switch_tol, 0, res);
+}
+
+static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, int ldx, int prep);
+
+int concord_path(concord_state* st, const double* lambdas, int n_lambda, double tol,
+                 int max_sweeps, concord_result* results, void* omega_out_dev, int ld_out) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  if (!lambdas || n_lambda < 1 || !(tol > 0.0) || max_sweeps < 1 ||
+      (omega_out_dev && ld_out < st->p))
+    return fail(CONCORD_E_ARG, "lambdas non-NULL, n_lambda >= 1, tol > 0, max_sweeps >= 1, "
+                               "ld_out >= p when Omega is requested");
+  for (int k = 0; k < n_lambda; ++k)
+    if (!(lambdas[k] >= 0.0)) return fail(CONCORD_E_ARG, "lambda[%d] must be >= 0", k);
+  if ((rc = ensure_screen(st)) || (rc = ensure_path(st, n_lambda, 0))) return rc;
+  CK(cudaMemcpyAsync(st->path_lam, lambdas, sizeof(double) * n_lambda, cudaMemcpyHostToDevice,
+                     st->stream));
+  if (is_mixed(st)) {
+    if (st->om64_current && (rc = demote_from_fp64(st)) != CONCORD_OK) return rc;
+    st->om64_current = false;
+    return path_impl<float>(st, lambdas, n_lambda, tol, max_sweeps, results, omega_out_dev, ld_out,
+                            nullptr);
+  }
+  return path_impl<double>(st, lambdas, n_lambda, tol, max_sweeps, results, omega_out_dev, ld_out,
+                           nullptr);
+}
+
+int concord_stability(concord_state* st, const void* X_dev, int x_dtype, int n, int ldx, int prep,
+                      const int* rows, const int* set_sizes, int n_sets, const double* lambdas,
+                      int n_lambda, double tol, int max_sweeps, float* freq_dev) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  const int p = st->p;
+  if (!X_dev || !rows || !set_sizes || n_sets < 1 || !lambdas || n_lambda < 1 || !freq_dev ||
+      n < 1 || ldx < p || prep < 0 || prep > 2 || !(tol > 0.0) || max_sweeps < 1 ||
+      (x_dtype != CONCORD_F64 && x_dtype != CONCORD_F32))
+    return fail(CONCORD_E_ARG, "bad argument to concord_stability");
+  size_t total = 0;
+  for (int b = 0; b < n_sets; ++b) {
+    if (set_sizes[b] < 2 || set_sizes[b] > st->n_cap)
+      return fail(CONCORD_E_ARG, "subsample %d: size must be in 2..n_cap (%d)", b, st->n_cap);
+    total += (size_t)set_sizes[b];
+  }
+  for (size_t q = 0; q < total; ++q)
+    if (rows[q] < 0 || rows[q] >= n) return fail(CONCORD_E_ARG, "row index out of range");
+  for (int k = 0; k < n_lambda; ++k)
+    if (!(lambdas[k] >= 0.0)) return fail(CONCORD_E_ARG, "lambda[%d] must be >= 0", k);
+  if ((rc = ensure_screen(st)) || (rc = ensure_path(st, n_lambda, total))) return rc;
+  CK(cudaMemcpyAsync(st->path_lam, lambdas, sizeof(double) * n_lambda, cudaMemcpyHostToDevice,
+                     st->stream));
+  CK(cudaMemcpyAsync(st->rows_dev, rows, sizeof(int) * total, cudaMemcpyHostToDevice, st->stream));
+  CK(cudaMemsetAsync(freq_dev, 0, sizeof(float) * (size_t)n_lambda * p * p, st->stream));
+  size_t off = 0;
+  for (int b = 0; b < n_sets; ++b) {
+    const int nb = set_sizes[b];
+    CK(launch_gather_rows(X_dev, x_dtype == CONCORD_F32, ldx, st->rows_dev + off, nb, p,
+                          st->Xstage, st->stream));
+    off += (size_t)nb;
+    if ((rc = gram_into_state(st, st->Xstage, 0, nb, p, prep)) != CONCORD_OK) return rc;
+    rc = is_mixed(st) ? path_impl<float>(st, lambdas, n_lambda, tol, max_sweeps, nullptr, nullptr,
+                                         0, freq_dev)
+                      : path_impl<double>(st, lambdas, n_lambda, tol, max_sweeps, nullptr, nullptr,
+                                          0, freq_dev);
+    if (rc != CONCORD_OK) return rc;
+  }
+  CK(launch_scale_f32(freq_dev, (size_t)n_lambda * p * p, 1.0f / n_sets, st->stream));
+  CK(cudaStreamSynchronize(st->stream));
+  return CONCORD_OK;
 }
 
 int concord_set_poll_sleep(concord_state* st, int ns) {

@@ -37,8 +37,9 @@ constexpr int kParts = 8;
 
 // Final result block written by CTA 0.
 constexpr int kResSweeps = 0, kResKkt = 1, kResObj = 2, kResDelta = 3, kResActive = 4,
-              kResFirstDelta = 5, kResStatus = 6, kResRedo = 7;  // kResRedo: screened only
-constexpr int kRes = 8;
+              kResFirstDelta = 5, kResStatus = 6, kResRedo = 7,  // kResRedo: screened only
+              kResPath = 8;  // screened path: index of the lambda a dense hand-over stopped at
+constexpr int kRes = 9;
 constexpr int kHist = 4;  // per sweep: delta, kkt, objective, active pairs
 
 template <typename T>
@@ -136,6 +137,14 @@ struct ScreenArgs {
   double lambda, tol, delta_tol;
   int stop_rule, n_sweeps, kkt_only, stall_stop;
   int max_redo;             // verification rounds per sweep before giving up (status 5)
+  // lambda path (path_n > 0): lambdas path_lambda[path_start .. path_n), each
+  // swept until its stopping rule, warm-started from the previous one
+  const double* path_lambda;
+  int path_n, path_start;
+  double* path_res;         // [path_n x kRes] result of each lambda
+  T* path_om;               // nullable: Omega after each lambda, slice k at k p ldo
+  int path_ldo;
+  float* path_cnt;          // nullable: slice k (p x p) += [w_ij != 0] after lambda k
 };
 
 size_t screened_dyn_smem(bool mixed);
@@ -186,6 +195,14 @@ cudaError_t launch_check_symmetric(const void* A, int a_f32, int p, int lda, int
 // out (FP64 bits as u64, must start at 0) = max_{i<j} |s_ij| (s_ii^-1/2 + s_jj^-1/2).
 cudaError_t launch_lambda_max(const double* S, int p, int ld, unsigned long long* out,
                               cudaStream_t st);
+
+// ---- lambda path and stability selection helpers (util.cu)
+// out (nr x p, FP64, dense) = rows `rows` of X (row stride ldx).
+cudaError_t launch_gather_rows(const void* X, int x_f32, int ldx, const int* rows, int nr, int p,
+                               double* out, cudaStream_t st);
+// cnt[r * p + c] += 1 where Om[r * ld + c] != 0.
+cudaError_t launch_support_add(const void* Om, int f32, int ld, int p, float* cnt, cudaStream_t st);
+cudaError_t launch_scale_f32(float* a, size_t n, float s, cudaStream_t st);
 
 // ---- tensor-core Gram (gram_tc.cu)
 // Splits each standardized element into tf32 hi + lo and writes them

@@ -256,12 +256,11 @@ __device__ __forceinline__ double kkt_offdiag(double om, double g, double lam) {
 // KKT terms of the whole matrix (diagonal included).
 template <typename T, bool MIXED>
 __device__ void screen_pass(const ScreenArgs<T>& a, const T* __restrict__ W, int lst, bool do_kkt,
-                            double (&v)[kParts], int lane, int gwarp, int gwarps) {
+                            double lamd, double (&v)[kParts], int lane, int gwarp, int gwarps) {
   const int p = a.p, ld = a.ld;
   const ScreenWork<T>& w = a.w;
   const int nb = (p + kTile - 1) / kTile;
-  const double lamd = a.lambda;
-  const T lam = (T)a.lambda;
+  const T lam = (T)lamd;
   const int units = nb * nb * 4;
   for (int u = gwarp; u < units; u += gwarps) {
     const int tau = u >> 2, r0 = (u & 3) * 8;
@@ -327,19 +326,18 @@ __device__ void screen_pass(const ScreenArgs<T>& a, const T* __restrict__ W, int
 // list and the diagonal's from the row pass.
 template <typename T>
 __device__ void verify_pass(const ScreenArgs<T>& a, const T* __restrict__ W,
-                            const T* __restrict__ V, int nxt, double (&v)[kParts], int lane,
-                            int gwarp, int gwarps) {
+                            const T* __restrict__ V, int nxt, double lamd, double (&v)[kParts],
+                            int lane, int gwarp, int gwarps) {
   const int p = a.p, ld = a.ld;
   const ScreenWork<T>& w = a.w;
   const int nb = (p + kTile - 1) / kTile;
-  const double lamd = a.lambda;
-  const float lamf = (float)a.lambda;
-  const T lam = (T)a.lambda;
+  const float lamf = (float)lamd;
+  const T lam = (T)lamd;
   const int units = nb * nb * 4;
   // |a|, |b| < lambda / 2 (slightly less, covering the rounding of a + b)
   // decides the common case without floating-point work: |a + b| <= lambda,
   // so no failure, no candidate and a zero KKT term
-  const unsigned small = mag_hi_below((T)(0.5 * a.lambda * (1.0 - 1e-6)));
+  const unsigned small = mag_hi_below((T)(0.5 * lamd * (1.0 - 1e-6)));
   for (int u = gwarp; u < units; u += gwarps) {
     const int tau = u >> 2, r0 = (u & 3) * 8;
     const int ta = tau / nb, tb = tau % nb;
@@ -408,8 +406,11 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
   const int p = a.p, P = a.P, ld = a.ld;
   const ScreenWork<T>& w = a.w;
   const WaitCtl& wc = a.wait;
-  const T lam = (T)a.lambda;
-  const double lamd = a.lambda;
+  // the lambda being swept (the path's current one)
+  int pk = a.path_n > 0 ? a.path_start : 0;
+  double lamd = a.path_n > 0 ? a.path_lambda[pk] : a.lambda;
+  T lam = (T)lamd;
+  int tt = 0;  // sweeps of the whole launch (history rows)
 
   __shared__ double red[kScreenThreads / 32][kParts];
   __shared__ int s_tmp[32];
@@ -435,7 +436,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
     double v[kParts];
 #pragma unroll
     for (int k = 0; k < kParts; ++k) v[k] = 0.0;
-    screen_pass<T, MIXED>(a, Wa, cur, kkt0, v, lane, gwarp, gwarps);
+    screen_pass<T, MIXED>(a, Wa, cur, kkt0, lamd, v, lane, gwarp, gwarps);
     if (kkt0) reduce_parts(v, a.partials, red);
     grid_barrier(a.barrier, gen, wc, ++where);
   }
@@ -864,7 +865,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         }
         grid_barrier(a.barrier, gen, wc, ++where);
         // ---- verify the other pairs; objective / KKT; screen the next sweep
-        verify_pass<T>(a, Wn, a.V, 1 - cur, v, lane, gwarp, gwarps);
+        verify_pass<T>(a, Wn, a.V, 1 - cur, lamd, v, lane, gwarp, gwarps);
         // the candidates' own terms (and their screen: every nonzero stays a
         // candidate); warp-uniform trip count for the list pushes
         for (int k0 = gwarp * 32; k0 < N; k0 += gwarps * 32) {
@@ -962,7 +963,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
       }
     }
     if (threadIdx.x == 0) {
-      const double obj = -lg + 0.5 * quad + a.lambda * pen;
+      const double obj = -lg + 0.5 * quad + lamd * pen;
       const bool aborted = ld_relaxed_s32(wc.abort) != 0;
       const bool nonfinite = bad > 0.0 || !isfinite(obj) || !isfinite(kkt);
       const int sweeps_done = do_sweep ? t + 1 : t;
@@ -986,6 +987,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
       s_res[kResActive] = ac * 0.5;
       s_res[kResFirstDelta] = first_delta;
       s_res[kResRedo] = redo_total;
+      s_res[kResPath] = pk;
       s_res[kResStatus] = aborted      ? 3.0
                           : nonfinite  ? 2.0
                           : conv       ? 0.0
@@ -998,15 +1000,18 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
                    ? 1
                    : 0;
       if (blockIdx.x == 0) {
-        if (do_sweep && t < a.hist_len) {
-          double* h = a.hist + (size_t)t * kHist;
+        if (do_sweep && tt < a.hist_len) {
+          double* h = a.hist + (size_t)tt * kHist;
           h[0] = dl;
           h[1] = kkt;
           h[2] = obj;
           h[3] = ac * 0.5;
         }
-        if (s_stop)
+        if (s_stop) {
           for (int k = 0; k < kRes; ++k) a.result[k] = s_res[k];
+          if (a.path_n > 0)
+            for (int k = 0; k < kRes; ++k) a.path_res[(size_t)pk * kRes + k] = s_res[k];
+        }
       }
     }
     __syncthreads();
@@ -1016,12 +1021,74 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
     Wa = Wn;
     Wn = tmp;
     cur = 1 - cur;
-    if (s_stop) break;
+    if (do_sweep) ++tt;
+    if (s_stop) {
+      // lambda path: on to the next lambda unless this one ended in an error
+      // or needs the dense kernel
+      const int code = (int)s_res[kResStatus];
+      if (a.path_n == 0 || pk + 1 >= a.path_n || code == 2 || code == 3 || code == kStatusDense)
+        break;
+      // this lambda's Omega (copy and / or support count), the next lambda's
+      // screen from scratch
+      if (a.path_om) {
+        T* out = a.path_om + (size_t)pk * p * a.path_ldo;
+        for (size_t e = gtid; e < (size_t)p * p; e += gthreads) {
+          const int r = (int)(e / p), c = (int)(e % p);
+          out[(size_t)r * a.path_ldo + c] = __ldcg(a.Om + (size_t)r * ld + c);
+        }
+      }
+      if (a.path_cnt) {
+        float* cnt = a.path_cnt + (size_t)pk * p * p;
+        for (size_t e = gtid; e < (size_t)p * p; e += gthreads) {
+          const int r = (int)(e / p), c = (int)(e % p);
+          if (__ldcg(a.Om + (size_t)r * ld + c) != (T)0) cnt[e] += 1.0f;
+        }
+      }
+      ++pk;
+      lamd = a.path_lambda[pk];
+      lam = (T)lamd;
+      t = 0;
+      first_delta = 0;
+      since_best = 0;
+      best_kkt = 1e300;
+      if (gtid == 0) w.ctr[kCtrCand + cur] = 0;
+      for (int k = gtid; k <= p; k += gthreads) w.cnt_r[cur][k] = 0;
+      grid_barrier(a.barrier, gen, wc, ++where);
+      {
+        double vz[kParts];
+#pragma unroll
+        for (int k = 0; k < kParts; ++k) vz[k] = 0.0;
+        screen_pass<T, MIXED>(a, Wa, cur, false, lamd, vz, lane, gwarp, gwarps);
+      }
+      need_scan = true;
+      grid_barrier(a.barrier, gen, wc, ++where);
+      continue;
+    }
     ++t;
+  }
+  // the last lambda's Omega (path)
+  if (a.path_n > 0 && status != kStatusDense && (int)s_res[kResStatus] != 2 &&
+      (int)s_res[kResStatus] != 3) {
+    if (a.path_om) {
+      T* out = a.path_om + (size_t)pk * p * a.path_ldo;
+      for (size_t e = gtid; e < (size_t)p * p; e += gthreads) {
+        const int r = (int)(e / p), c = (int)(e % p);
+        out[(size_t)r * a.path_ldo + c] = __ldcg(a.Om + (size_t)r * ld + c);
+      }
+    }
+    if (a.path_cnt) {
+      float* cnt = a.path_cnt + (size_t)pk * p * p;
+      for (size_t e = gtid; e < (size_t)p * p; e += gthreads) {
+        const int r = (int)(e / p), c = (int)(e % p);
+        if (__ldcg(a.Om + (size_t)r * ld + c) != (T)0) cnt[e] += 1.0f;
+      }
+    }
   }
 
   if (status == kStatusDense && blockIdx.x == 0 && threadIdx.x == 0) {
     // the sweep in progress was undone or never started: t sweeps are done
+    // (for a path: of lambda pk, whose index the host reads from kResPath)
+    a.result[kResPath] = pk;
     a.result[kResSweeps] = t;
     a.result[kResKkt] = t > 0 ? s_res[kResKkt] : 1e300;
     a.result[kResObj] = t > 0 ? s_res[kResObj] : 0.0;

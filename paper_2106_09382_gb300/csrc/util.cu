@@ -171,3 +171,65 @@ cudaError_t launch_lambda_max(const double* S, int p, int ld, unsigned long long
 }
 
 }  // namespace concord
+
+// ---------------------------------------------------------------------------
+// Helpers of the lambda path and stability selection.
+// ---------------------------------------------------------------------------
+namespace concord {
+namespace {
+
+template <typename TX>
+__global__ void k_gather_rows(const TX* __restrict__ X, int ldx, const int* __restrict__ rows,
+                              int nr, int p, double* __restrict__ out) {
+  const size_t total = (size_t)nr * p;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / p), c = (int)(e % p);
+    out[e] = (double)X[(size_t)rows[r] * ldx + c];
+  }
+}
+
+template <typename T>
+__global__ void k_support_add(const T* __restrict__ Om, int ld, int p, float* __restrict__ cnt) {
+  const size_t total = (size_t)p * p;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / p), c = (int)(e % p);
+    if (Om[(size_t)r * ld + c] != (T)0) cnt[e] += 1.0f;
+  }
+}
+
+__global__ void k_scale_f32(float* a, size_t n, float s) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    a[e] *= s;
+}
+
+}  // namespace
+
+cudaError_t launch_gather_rows(const void* X, int x_f32, int ldx, const int* rows, int nr, int p,
+                               double* out, cudaStream_t st) {
+  if (x_f32)
+    k_gather_rows<float><<<152 * 4, 256, 0, st>>>((const float*)X, ldx, rows, nr, p, out);
+  else
+    k_gather_rows<double><<<152 * 4, 256, 0, st>>>((const double*)X, ldx, rows, nr, p, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_support_add(const void* Om, int f32, int ld, int p, float* cnt, cudaStream_t st) {
+  if (f32)
+    k_support_add<float><<<152 * 4, 256, 0, st>>>((const float*)Om, ld, p, cnt);
+  else
+    k_support_add<double><<<152 * 4, 256, 0, st>>>((const double*)Om, ld, p, cnt);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_f32(float* a, size_t n, float s, cudaStream_t st) {
+  k_scale_f32<<<152 * 4, 256, 0, st>>>(a, n, s);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace concord
