@@ -47,6 +47,8 @@ def parse_args(argv=None):
     ap.add_argument("--max-sweeps", type=int, default=500)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip FP64 arm, microbench, e2e and CPU baseline")
+    ap.add_argument("--no-path", action="store_true",
+                    help="skip the regularisation-path / stability-selection section")
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the default sweep kernel without the variant trials")
     ap.add_argument("--cpu-budget", type=float, default=20.0,
@@ -273,6 +275,47 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_path_section(C, synth, dev, stream, p=1000, n=800, n_lambda=32, n_sub=8, workers=8):
+    import torch
+    wl = synth.workload_path(p, n, 0)
+    X = torch.as_tensor(wl["X"], device=dev)
+    st = C.State(p, C.MIXED, n_cap=n, device=dev.index)
+    st.set_stream(stream)
+    S = C.concord_gram(X, C.PREP_STANDARDIZE, C.GRAM_TF32X3, stream=stream)
+    torch.cuda.synchronize()
+    st.set_S(S)
+    lams = st.lambda_max() * np.logspace(0.0, -2.0, n_lambda)
+    tol, ms = 1e-5, 200
+    times = []
+    for _ in range(2):  # one warm-up, one timed
+        st.set_S(S)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = st.path(lams, tol=tol, max_sweeps=ms)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    subs = synth.subsamples(n, n_sub, 200, 800, seed=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    freq = st.stability(X, subs, lams, tol=tol, max_sweeps=ms, workers=workers)
+    torch.cuda.synchronize()
+    t_stab = time.perf_counter() - t0
+    f_mid = freq[n_lambda // 2].cpu().numpy()
+    st.close()
+    return {"workload": "scale-free (BA m=2) p=%d, n=%d; %d lambdas log-spaced lambda_max .. 0.01 "
+                        "lambda_max, warm-started, KKT<=%g, <=%d sweeps per lambda, FP32 sweeps"
+                        % (p, n, n_lambda, tol, ms),
+            "path_seconds": times[-1],
+            "path_sweeps": int(sum(r.sweeps for r in res)),
+            "path_dense_sweeps": int(sum(r.dense_sweeps for r in res)),
+            "lambdas_converged": int(sum(1 for r in res if r.kkt <= tol)),
+            "stability": {"subsamples": n_sub, "n_range": [200, 800], "workers": workers,
+                          "seconds": t_stab, "seconds_per_subsample": t_stab / n_sub,
+                          "estimated_seconds_64": t_stab / n_sub * 64,
+                          "edges_freq_ge_0.8_mid_lambda": int((np.triu(f_mid, 1) >= 0.8).sum()),
+                          "true_edges": int((np.triu(wl["Om0"], 1) != 0).sum())}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -472,6 +515,12 @@ def run_ours(args):
         out["e2e"] = {"value": max_over_ranks(statistics.mean(te)), "unit": "s",
                       "h2d_bytes_per_step": n * p * 8, "d2h_bytes_per_step": p * p * 8,
                       "api": "concord_solve_host (pinned X in, pinned Omega out)"}
+        # ---------------- regularisation path + stability selection (scale-free
+        #                  p = 1000, 32 lambdas from lambda_max to 0.01 lambda_max,
+        #                  warm-started, FP32 sweeps; a bounded sample of the
+        #                  64-subsample stability run)
+        if not args.no_path:
+            out["path"] = run_path_section(C, synth, dev, stream)
         # ---------------- CPU oracle, bounded sample (rank 0 only)
         if rank == 0:
             gs, src = golden_sweeps(p)

@@ -377,11 +377,16 @@ int concord_path(concord_state *st, const double *lambdas, int n_lambda, double 
  * Gram of its rows (prep as concord_solve_device) and the lambda path over
  * lambdas from Omega = I; freq_dev (device, float, n_lambda x p x p, written
  * completely) receives for each lambda the fraction of subsamples whose
- * Omega has w_ij != 0.  The state ends on the last subsample's last lambda.
+ * Omega has w_ij != 0.  n_workers subsamples run concurrently (0: up to 8),
+ * each on a state of its own (own stream, 1 / n_workers of the SMs, created
+ * and destroyed by the call, same precision, n_cap and Gram mode as st) with
+ * one host thread; n_workers = 1 uses st itself, which then ends on the
+ * last subsample's last lambda.  The frequencies do not depend on
+ * n_workers (support counts are whole numbers added atomically).
  */
 int concord_stability(concord_state *st, const void *X_dev, int x_dtype, int n, int ldx, int prep,
                       const int *rows, const int *set_sizes, int n_sets, const double *lambdas,
-                      int n_lambda, double tol, int max_sweeps, float *freq_dev);
+                      int n_lambda, double tol, int max_sweeps, int n_workers, float *freq_dev);
 
 
 /*

@@ -89,8 +89,8 @@ SIGNATURES = {
     "concord_get_timing": ([_vp, _dp, _ip, _ci, _ip], _ci),
     "concord_kernel_launches": ([], ctypes.c_ulonglong),
     "concord_path": ([_vp, _dp, _ci, _cd, _ci, _rp, _vp, _ci], _ci),
-    "concord_stability": ([_vp, _vp, _ci, _ci, _ci, _ci, _ip, _ip, _ci, _dp, _ci, _cd, _ci, _vp],
-                          _ci),
+    "concord_stability": ([_vp, _vp, _ci, _ci, _ci, _ci, _ip, _ip, _ci, _dp, _ci, _cd, _ci, _ci,
+                           _vp], _ci),
 }
 
 _lock = threading.Lock()
@@ -339,7 +339,7 @@ class State:
         return list(res)
 
     def stability(self, X, subsets, lambdas, tol: float = 1e-5, max_sweeps: int = 1000,
-                  prep: int = PREP_STANDARDIZE, freq_out=None):
+                  prep: int = PREP_STANDARDIZE, workers: int = 0, freq_out=None):
         """Stability selection: for each row subset of X (device tensor), the
         Gram of its rows and the lambda path from Omega = I; returns the
         per-lambda edge frequencies (device float32 tensor n_lambda x p x p)."""
@@ -356,7 +356,7 @@ class State:
                                       X.stride(0), int(prep), rows.ctypes.data_as(_ip),
                                       sizes.ctypes.data_as(_ip), len(sizes),
                                       lam.ctypes.data_as(_dp), len(lam), float(tol),
-                                      int(max_sweeps), freq_out.data_ptr())
+                                      int(max_sweeps), int(workers), freq_out.data_ptr())
         _check(rc)
         return freq_out
 

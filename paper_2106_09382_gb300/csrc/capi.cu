@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "concord.h"
@@ -95,6 +96,7 @@ struct concord_state {
   void *Wb = nullptr, *V = nullptr, *scr = nullptr;
   int nc_cap = 0, term_cap = 0;
   int screened_grid = 0;
+  int max_ctas = 0;  // > 0: persistent launches use at most this many CTAs (concurrent workers)
   // lambda path / stability selection buffers (allocated on demand)
   double *path_lam = nullptr, *path_res = nullptr;
   int path_cap = 0;
@@ -142,7 +144,7 @@ struct RunOut {
 template <typename T>
 int launch_dense(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* omdiag64,
                  double lambda, double tol, int stop_rule, int n_sweeps, int kkt_only,
-                 int hist_offset, int stall_stop, RunOut* out) {
+                 int hist_offset, int stall_stop, RunOut* out, bool bandwidth = false) {
   const int p = st->p;
   const bool mixed = sizeof(T) == 4;
   // `row_warps` warps of each CTA own rows (one row per lane, up to `R` rows
@@ -156,11 +158,14 @@ int launch_dense(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* 
   const bool own = mixed == is_mixed(st);
   const bool layout_set = own && (st->sweep_variant == CONCORD_SWEEP_GRID ||
                                   st->sweep_variant == CONCORD_SWEEP_CLUSTER);
-  const int variant = layout_set ? st->sweep_variant
-                                 : (mixed ? CONCORD_SWEEP_CLUSTER : CONCORD_SWEEP_GRID);
+  // bandwidth: sweeps handed over by the screened kernel change most pairs;
+  // they take the grid layout with one row per warp (all SMs stream rows)
+  const int variant = bandwidth    ? CONCORD_SWEEP_GRID
+                      : layout_set ? st->sweep_variant
+                                   : (mixed ? CONCORD_SWEEP_CLUSTER : CONCORD_SWEEP_GRID);
   bool cluster = false;
   int grid = 0, row_warps = 0, R = 0;
-  int want = (own && st->rows_per_warp > 0) ? st->rows_per_warp : 32;
+  int want = bandwidth ? 1 : (own && st->rows_per_warp > 0) ? st->rows_per_warp : 32;
   if (variant != CONCORD_SWEEP_GRID) {
     if (st->cluster_size < 0) {
       int cs = 0;
@@ -180,7 +185,7 @@ int launch_dense(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* 
     }
   }
   if (!cluster) {
-    if (!(own && st->rows_per_warp > 0)) want = 8;
+    if (!bandwidth && !(own && st->rows_per_warp > 0)) want = 8;
     int occ = 0;
     CK(sweep_occupancy(mixed, block, &occ));
     if (occ < 1)
@@ -189,6 +194,7 @@ int launch_dense(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* 
     const int need = (p + 31) / 32;
     if (grid > need) grid = need;
     if (grid > st->max_grid) grid = st->max_grid;
+    if (st->max_ctas > 0 && grid > st->max_ctas) grid = st->max_ctas;
     row_warps = (p + want * grid - 1) / (want * grid);
     if (row_warps < 1) row_warps = 1;
     if (row_warps > block / 32) row_warps = block / 32;
@@ -466,7 +472,9 @@ int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, d
 
   const int slot_ev = st->n_launch < kMaxTimedLaunches ? st->n_launch : -1;
   if (slot_ev >= 0) CK(cudaEventRecord(st->lev[2 * slot_ev], st->stream));
-  CK(launch_screened(a, st->screened_grid, st->stream));
+  CK(launch_screened(a, st->max_ctas > 0 && st->max_ctas < st->screened_grid ? st->max_ctas
+                                                                              : st->screened_grid,
+                     st->stream));
   if (slot_ev >= 0) CK(cudaEventRecord(st->lev[2 * slot_ev + 1], st->stream));
   CK(cudaMemcpyAsync(st->h_result, st->result, kRes * sizeof(double), cudaMemcpyDeviceToHost,
                      st->stream));
@@ -553,7 +561,7 @@ int launch_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* om
       }
       RunOut dq;
       rc = launch_dense<T>(st, S, W, Om, sdiagT, omdiag64, lambda, tol, stop_rule, 1, 0,
-                           hist_offset + done, 0, &dq);
+                           hist_offset + done, 0, &dq, true);
       if (dq.first_delta && !first_delta) first_delta = done + dq.first_delta;
       done += dq.sweeps;
       dense += dq.sweeps;
@@ -1145,16 +1153,45 @@ int concord_path(concord_state* st, const double* lambdas, int n_lambda, double 
                            nullptr);
 }
 
+// One worker of concord_stability: subsamples b = first, first + stride, ...
+// on its own state (own stream and CTA budget), adding support counts into
+// the shared frequency buffer.
+static int stability_worker(concord_state* st, const void* X_dev, int x_dtype, int ldx, int prep,
+                            const int* rows_dev, const size_t* offs, const int* set_sizes,
+                            int n_sets, int first, int stride, const double* lambdas, int n_lambda,
+                            double tol, int max_sweeps, float* freq_dev, std::string* err) {
+  int rc = CONCORD_OK;
+  for (int b = first; b < n_sets && rc == CONCORD_OK; b += stride) {
+    const int nb = set_sizes[b];
+    cudaError_t e = launch_gather_rows(X_dev, x_dtype == CONCORD_F32, ldx, rows_dev + offs[b], nb,
+                                       st->p, st->Xstage, st->stream);
+    if (e != cudaSuccess) {
+      rc = fail(CONCORD_E_CUDA, "gather: %s", cudaGetErrorString(e));
+      break;
+    }
+    if ((rc = gram_into_state(st, st->Xstage, 0, nb, st->p, prep)) != CONCORD_OK) break;
+    rc = is_mixed(st) ? path_impl<float>(st, lambdas, n_lambda, tol, max_sweeps, nullptr, nullptr,
+                                         0, freq_dev)
+                      : path_impl<double>(st, lambdas, n_lambda, tol, max_sweeps, nullptr, nullptr,
+                                          0, freq_dev);
+  }
+  if (rc != CONCORD_OK) *err = g_err;
+  return rc;
+}
+
 int concord_stability(concord_state* st, const void* X_dev, int x_dtype, int n, int ldx, int prep,
                       const int* rows, const int* set_sizes, int n_sets, const double* lambdas,
-                      int n_lambda, double tol, int max_sweeps, float* freq_dev) {
+                      int n_lambda, double tol, int max_sweeps, int n_workers, float* freq_dev) {
   int rc = check_state(st);
   if (rc) return rc;
   const int p = st->p;
   if (!X_dev || !rows || !set_sizes || n_sets < 1 || !lambdas || n_lambda < 1 || !freq_dev ||
       n < 1 || ldx < p || prep < 0 || prep > 2 || !(tol > 0.0) || max_sweeps < 1 ||
-      (x_dtype != CONCORD_F64 && x_dtype != CONCORD_F32))
+      n_workers < 0 || (x_dtype != CONCORD_F64 && x_dtype != CONCORD_F32))
     return fail(CONCORD_E_ARG, "bad argument to concord_stability");
+  if (n_workers == 0) n_workers = n_sets < 8 ? n_sets : 8;
+  if (n_workers > n_sets) n_workers = n_sets;
+  if (n_workers > st->sms) n_workers = st->sms;
   size_t total = 0;
   for (int b = 0; b < n_sets; ++b) {
     if (set_sizes[b] < 2 || set_sizes[b] > st->n_cap)
@@ -1170,17 +1207,51 @@ int concord_stability(concord_state* st, const void* X_dev, int x_dtype, int n, 
                      st->stream));
   CK(cudaMemcpyAsync(st->rows_dev, rows, sizeof(int) * total, cudaMemcpyHostToDevice, st->stream));
   CK(cudaMemsetAsync(freq_dev, 0, sizeof(float) * (size_t)n_lambda * p * p, st->stream));
-  size_t off = 0;
-  for (int b = 0; b < n_sets; ++b) {
-    const int nb = set_sizes[b];
-    CK(launch_gather_rows(X_dev, x_dtype == CONCORD_F32, ldx, st->rows_dev + off, nb, p,
-                          st->Xstage, st->stream));
-    off += (size_t)nb;
-    if ((rc = gram_into_state(st, st->Xstage, 0, nb, p, prep)) != CONCORD_OK) return rc;
-    rc = is_mixed(st) ? path_impl<float>(st, lambdas, n_lambda, tol, max_sweeps, nullptr, nullptr,
-                                         0, freq_dev)
-                      : path_impl<double>(st, lambdas, n_lambda, tol, max_sweeps, nullptr, nullptr,
-                                          0, freq_dev);
+  CK(cudaStreamSynchronize(st->stream));
+  std::vector<size_t> offs(n_sets);
+  for (int b = 0, o = 0; b < n_sets; o += set_sizes[b], ++b) offs[b] = (size_t)o;
+  if (n_workers <= 1) {
+    std::string err;
+    rc = stability_worker(st, X_dev, x_dtype, ldx, prep, st->rows_dev, offs.data(), set_sizes,
+                          n_sets, 0, 1, lambdas, n_lambda, tol, max_sweeps, freq_dev, &err);
+    if (rc != CONCORD_OK) return rc;
+  } else {
+    // independent subsamples run concurrently: one state per worker (own
+    // stream, 1 / n_workers of the SMs), one host thread each
+    std::vector<concord_state*> ws(n_workers, nullptr);
+    for (int k = 0; k < n_workers && rc == CONCORD_OK; ++k) {
+      rc = concord_create(&ws[k], p, st->precision, st->n_cap, st->device);
+      if (rc == CONCORD_OK) {
+        ws[k]->gram_mode = st->gram_mode;
+        ws[k]->max_ctas = st->sms / n_workers > 0 ? st->sms / n_workers : 1;
+        rc = ensure_screen(ws[k]);
+        if (rc == CONCORD_OK) rc = ensure_path(ws[k], n_lambda, 0);
+        if (rc == CONCORD_OK &&
+            cudaMemcpy(ws[k]->path_lam, lambdas, sizeof(double) * n_lambda,
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+          rc = fail(CONCORD_E_CUDA, "copy of the lambdas failed");
+      }
+    }
+    if (rc == CONCORD_OK) {
+      std::vector<int> rcs(n_workers, CONCORD_OK);
+      std::vector<std::string> errs(n_workers);
+      std::vector<std::thread> th;
+      for (int k = 0; k < n_workers; ++k)
+        th.emplace_back([&, k]() {
+          cudaSetDevice(st->device);
+          rcs[k] = stability_worker(ws[k], X_dev, x_dtype, ldx, prep, st->rows_dev, offs.data(),
+                                    set_sizes, n_sets, k, n_workers, lambdas, n_lambda, tol,
+                                    max_sweeps, freq_dev, &errs[k]);
+        });
+      for (auto& t : th) t.join();
+      for (int k = 0; k < n_workers; ++k)
+        if (rcs[k] != CONCORD_OK && rc == CONCORD_OK) {
+          rc = rcs[k];
+          g_err = errs[k];
+        }
+    }
+    for (auto* w : ws)
+      if (w) concord_destroy(w);
     if (rc != CONCORD_OK) return rc;
   }
   CK(launch_scale_f32(freq_dev, (size_t)n_lambda * p * p, 1.0f / n_sets, st->stream));

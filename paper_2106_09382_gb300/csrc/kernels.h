@@ -144,7 +144,7 @@ struct ScreenArgs {
   double* path_res;         // [path_n x kRes] result of each lambda
   T* path_om;               // nullable: Omega after each lambda, slice k at k p ldo
   int path_ldo;
-  float* path_cnt;          // nullable: slice k (p x p) += [w_ij != 0] after lambda k
+  float* path_cnt;          // nullable: slice k (p x p) += [w_ij != 0] after lambda k (atomic)
 };
 
 size_t screened_dyn_smem(bool mixed);
@@ -200,7 +200,7 @@ cudaError_t launch_lambda_max(const double* S, int p, int ld, unsigned long long
 // out (nr x p, FP64, dense) = rows `rows` of X (row stride ldx).
 cudaError_t launch_gather_rows(const void* X, int x_f32, int ldx, const int* rows, int nr, int p,
                                double* out, cudaStream_t st);
-// cnt[r * p + c] += 1 where Om[r * ld + c] != 0.
+// cnt[r * p + c] += 1 (atomically) where Om[r * ld + c] != 0.
 cudaError_t launch_support_add(const void* Om, int f32, int ld, int p, float* cnt, cudaStream_t st);
 cudaError_t launch_scale_f32(float* a, size_t n, float s, cudaStream_t st);
 

@@ -1041,7 +1041,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         float* cnt = a.path_cnt + (size_t)pk * p * p;
         for (size_t e = gtid; e < (size_t)p * p; e += gthreads) {
           const int r = (int)(e / p), c = (int)(e % p);
-          if (__ldcg(a.Om + (size_t)r * ld + c) != (T)0) cnt[e] += 1.0f;
+          if (__ldcg(a.Om + (size_t)r * ld + c) != (T)0) atomicAdd(cnt + e, 1.0f);
         }
       }
       ++pk;
@@ -1080,7 +1080,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
       float* cnt = a.path_cnt + (size_t)pk * p * p;
       for (size_t e = gtid; e < (size_t)p * p; e += gthreads) {
         const int r = (int)(e / p), c = (int)(e % p);
-        if (__ldcg(a.Om + (size_t)r * ld + c) != (T)0) cnt[e] += 1.0f;
+        if (__ldcg(a.Om + (size_t)r * ld + c) != (T)0) atomicAdd(cnt + e, 1.0f);
       }
     }
   }

@@ -195,7 +195,7 @@ __global__ void k_support_add(const T* __restrict__ Om, int ld, int p, float* __
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / p), c = (int)(e % p);
-    if (Om[(size_t)r * ld + c] != (T)0) cnt[e] += 1.0f;
+    if (Om[(size_t)r * ld + c] != (T)0) atomicAdd(cnt + e, 1.0f);
   }
 }
 

@@ -114,7 +114,7 @@ def barabasi_albert_edges(p: int, m: int, rng) -> list[tuple[int, int]]:
     return edges
 
 
-def scale_free(p: int, m: int = 2, seed: int = 0) -> np.ndarray:
+def scale_free(p: int, m: int = 2, seed: int = 0, margin: float = 0.1) -> np.ndarray:
     rng = np.random.default_rng(seed)
     edges = barabasi_albert_edges(p, m, rng)
     T = np.eye(p)
@@ -129,7 +129,10 @@ def scale_free(p: int, m: int = 2, seed: int = 0) -> np.ndarray:
     mask = Om != 0
     small = mask & (np.abs(Om) < 0.1)
     Om[small] = 0.1 * np.sign(Om[small])
-    Om += np.eye(p)
+    # the recipe's unit diagonal does not make the matrix positive definite
+    # once hubs are symmetrised; raise it to diagonal dominance with `margin`
+    diag = np.maximum(1.0, np.abs(Om).sum(axis=1) + margin)
+    Om[np.diag_indices(p)] = diag
     return Om
 
 
@@ -177,3 +180,19 @@ def workload_ar1(p: int = 5000, n: int = 2000, seed: int = 0):
     Om0 = ar1_extra(p, 0.5, None, 0.3, 0.6, seed)
     return dict(name="AR(1)+1%% extra p=%d n=%d" % (p, n), X=sample(Om0, n, seed), Om0=Om0,
                 lam=0.2, tol=1e-5)
+
+
+def workload_path(p: int = 1000, n: int = 800, seed: int = 0):
+    """Regularisation-path / stability-selection workload: a scale-free
+    (Barabasi-Albert, m = 2) precision matrix, n samples."""
+    Om0 = scale_free(p, m=2, seed=seed)
+    return {"Om0": Om0, "X": sample(Om0, n, seed=seed + 1), "p": p, "n": n}
+
+
+def subsamples(n: int, count: int = 64, lo: int = 200, hi: int = 800, seed: int = 0):
+    """`count` row subsets of range(n), sizes uniform on [lo, min(hi, n)],
+    drawn without replacement, each sorted."""
+    rng = np.random.default_rng(seed)
+    hi = min(hi, n)
+    sizes = rng.integers(lo, hi + 1, size=count)
+    return [np.sort(rng.choice(n, size=int(m), replace=False)) for m in sizes]

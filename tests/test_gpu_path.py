@@ -137,3 +137,17 @@ def test_path_with_dense_handover():
             assert np.array_equal(host(out[k]), host(b.get_omega())), k
             assert ra[k].sweeps == rb.sweeps and ra[k].dense_sweeps == rb.dense_sweeps
     assert ra[-1].dense_sweeps > 0
+
+
+def test_stability_workers_do_not_change_frequencies():
+    rng = np.random.default_rng(12)
+    w = synth.workload_small()
+    X = w["X"][:, :40]
+    n, p = X.shape
+    subsets = [np.sort(rng.choice(n, size=int(m), replace=False)) for m in (60, 80, 100, 120, 150, 170)]
+    S_full = O.gram(O.standardize(X))
+    lams = _lambdas(S_full, k=4, lo=0.2)
+    with C.State(p, C.FP64, n_cap=n) as st:
+        f1 = host(st.stability(dev(X), subsets, lams, tol=1e-8, max_sweeps=1000, workers=1))
+        f4 = host(st.stability(dev(X), subsets, lams, tol=1e-8, max_sweeps=1000, workers=4))
+    assert np.array_equal(f1, f4)
