@@ -196,3 +196,12 @@ def subsamples(n: int, count: int = 64, lo: int = 200, hi: int = 800, seed: int 
     hi = min(hi, n)
     sizes = rng.integers(lo, hi + 1, size=count)
     return [np.sort(rng.choice(n, size=int(m), replace=False)) for m in sizes]
+
+
+def workload_adjoint(p: int = 2000, n_train: int = 1000, n_val: int = 500, seed: int = 0):
+    """Differentiable-solve workload: a block-diagonal precision matrix (20
+    blocks, within-block edge probability 0.1, values +-U[0.3, 0.6], margin
+    0.5), n_train training rows and n_val held-out rows drawn independently."""
+    Om0 = block_diag(p, 20, 0.1, 0.3, 0.6, 0.5, seed)
+    return {"Om0": Om0, "X": sample(Om0, n_train, seed), "X_val": sample(Om0, n_val, seed + 7),
+            "p": p, "n": n_train, "n_val": n_val}
