@@ -47,6 +47,8 @@ def parse_args(argv=None):
     ap.add_argument("--max-sweeps", type=int, default=500)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip FP64 arm, microbench, e2e and CPU baseline")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the differentiable-solve (implicit adjoint) section")
     ap.add_argument("--no-path", action="store_true",
                     help="skip the regularisation-path / stability-selection section")
     ap.add_argument("--no-autotune", action="store_true",
@@ -316,6 +318,77 @@ def run_path_section(C, synth, dev, stream, p=1000, n=800, n_lambda=32, n_sub=8,
                           "true_edges": int((np.triu(wl["Om0"], 1) != 0).sum())}}
 
 
+def run_adjoint_section(C, synth, dev, stream, steps=20, lr=0.003):
+    """Differentiable solve on the block-diagonal workload (p = 2000, 20
+    blocks, n = 1000 train / 500 held-out): one solve + held-out loss +
+    adjoint (dL/dlambda, dL/dS) + dL/dX at 0.3 lambda_max, a central
+    difference of the solver as the accuracy check of dL/dlambda, and
+    `steps` hypergradient-descent steps on log lambda from 0.6 lambda_max."""
+    import torch
+    w = synth.workload_adjoint()
+    p, n = w["p"], w["n"]
+    X = torch.as_tensor(w["X"], device=dev)
+    Xv = torch.as_tensor(w["X_val"], device=dev)
+    st = C.State(p, C.MIXED, n_cap=n, device=dev.index)
+    st.set_stream(stream)
+    S = C.concord_gram(X, C.PREP_STANDARDIZE, C.GRAM_TF32X3, stream=stream)
+    Sv = C.concord_gram(Xv, C.PREP_STANDARDIZE, C.GRAM_FP64, stream=stream)
+    dS = torch.empty((p, p), dtype=torch.float64, device=dev)
+    eye = torch.eye(p, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    st.set_S(S)
+    lmax = st.lambda_max()
+    lam = 0.3 * lmax
+    tol = 1e-5
+    rec = None
+    for _ in range(3):  # warm-up, then the last is kept
+        st.set_omega(eye)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = st.run(lam, tol=tol, max_sweeps=5000)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss = st.heldout(Sv)
+        t2 = time.perf_counter()
+        info = st.adjoint(None, tol=1e-10, max_iter=5000, dS_out=dS)
+        t3 = time.perf_counter()
+        st.adjoint_data(X)
+        torch.cuda.synchronize()
+        t4 = time.perf_counter()
+        rec = dict(solve_ms=(t1 - t0) * 1e3, sweeps=r.sweeps, kkt=r.kkt, heldout_ms=(t2 - t1) * 1e3,
+                   adjoint_ms=(t3 - t2) * 1e3, cg_device_ms=info.seconds * 1e3,
+                   cg_iterations=info.iterations, cg_residual=info.residual,
+                   active_pairs=info.active_pairs, dX_ms=(t4 - t3) * 1e3, loss=loss,
+                   dlambda=info.dlambda)
+    # accuracy of dL/dlambda: central difference of the (FP64-polished) solver
+    Om = st.get_omega()
+    h = 1e-5 * lam
+    L = []
+    for lm in (lam + h, lam - h):
+        st.set_omega(Om)
+        st.run(lm, tol=1e-10, max_sweeps=20000)
+        L.append(st.heldout(Sv))
+    fd = (L[0] - L[1]) / (2 * h)
+    rec["dlambda_fd"] = fd
+    rec["dlambda_rel_err_vs_fd"] = abs(rec["dlambda"] - fd) / abs(fd)
+    st.set_omega(eye)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rows = st.tune_lambda(Sv, 0.6 * lmax, steps=steps, lr=lr, tol=tol, max_sweeps=5000,
+                          cg_tol=1e-8)
+    t_tune = time.perf_counter() - t0
+    st.close()
+    rec["per_step_ms"] = rec["solve_ms"] + rec["heldout_ms"] + rec["adjoint_ms"] + rec["dX_ms"]
+    return {"workload": "block-diagonal (20 blocks of 100, edge prob 0.1) p=%d, n=%d train / %d "
+                        "held-out; lambda = 0.3 lambda_max; mixed solve KKT<=%g" % (p, n, w["n_val"], tol),
+            "single": rec,
+            "hypergradient": {"steps": steps, "lr_log_lambda": lr, "lambda0_over_max": 0.6,
+                              "seconds": t_tune,
+                              "lambda_over_max": [round(v / lmax, 6) for v in rows[:, 0]],
+                              "heldout_loss": [round(v, 6) for v in rows[:, 1]],
+                              "cg_iterations": [int(v) for v in rows[:, 4]]}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -521,6 +594,8 @@ def run_ours(args):
         #                  64-subsample stability run)
         if not args.no_path:
             out["path"] = run_path_section(C, synth, dev, stream)
+        if not args.no_adjoint:
+            out["adjoint"] = run_adjoint_section(C, synth, dev, stream)
         # ---------------- CPU oracle, bounded sample (rank 0 only)
         if rank == 0:
             gs, src = golden_sweeps(p)

@@ -437,6 +437,110 @@ int concord_lambda_max(concord_state *st, double *lambda_max);
  */
 int concord_set_fault(concord_state *st, int vertex, int step);
 
+/* ------------------------------------------------ implicit differentiation */
+/*
+ * Gradients of a loss L(Omega) of the estimate with respect to lambda, S and
+ * the data X, by implicit differentiation of the minimiser of Eq. 1.  On the
+ * active set A of the state's current Omega (the diagonal and the pairs with
+ * w_ij != 0) the subgradient conditions hold with equality,
+ *   W_ii - 1/w_ii = 0,   W_ij + W_ji + lambda sign(w_ij) = 0   (W = Omega S),
+ * and with A and the signs held fixed (valid when no inactive pair sits on
+ * the threshold |W_ij + W_ji| = lambda) they define Omega_A(S, lambda)
+ * smoothly.  With b the loss gradient on A (b_ii = dL/dw_ii, b_ij = dL/dw_ij
+ * + dL/dw_ji) and H the Hessian of the smooth part of Eq. 1 on A,
+ *   (H V)_ij = (V S + S V)_ij,   (H V)_ii = (V S)_ii + v_ii / w_ii^2,
+ * the adjoint a = H^{-1} b gives
+ *   dL/dlambda = - sum_{i<j in A} a_ij sign(w_ij),
+ *   dL/dS      = - Omega Ahat   (Ahat: a as a symmetric matrix on A),
+ *   dL/dZ      = Z (dL/dS + dL/dS^T) / n   for S = Z^T Z / n,
+ * and dL/dX through the data preparation (Section 2.1).  Gradients with
+ * respect to matrices use the full-matrix convention: every entry is an
+ * independent variable (a symmetric perturbation of s_ij and s_ji changes L
+ * by G_ij + G_ji).  H is applied matrix-free on A (sparse gathers of S, FP64)
+ * and the system is solved by Jacobi-preconditioned conjugate gradients in
+ * one persistent cooperative launch; no sweep of the solver is stored or
+ * replayed.  Everything here is FP64 on the FP64 copy of S; in MIXED
+ * precision the FP64 iterate of the last polishing phase is used.
+ *
+ * Scratch (allocated on first use, kept by the state): about 84 bytes per
+ * entry of A (both orientations of each pair, plus the diagonal) and, for
+ * concord_adjoint_data, four n x ld FP64 matrices.
+ */
+
+typedef struct concord_adjoint_info {
+    int status;            /* CONCORD_OK, or CONCORD_NOT_CONVERGED (max_iter reached) */
+    int iterations;        /* conjugate-gradient iterations                        */
+    long long active_pairs;/* off-diagonal pairs in A                              */
+    double residual;       /* ||b - H a|| / ||b||, recomputed after the last step  */
+    double dlambda;        /* dL/dlambda                                           */
+    double seconds;        /* device time of the conjugate-gradient launch         */
+} concord_adjoint_info;
+
+/*
+ * concord_heldout -- the held-out loss of the current Omega,
+ *   L = - sum_i log w_ii + 1/2 tr(Omega S_val Omega)
+ * (the smooth part of Eq. 1 with a validation Gram S_val = Z_val^T Z_val /
+ * n_val), into *loss_host, and its gradient on A as the right-hand side of
+ * the next concord_adjoint(st, NULL, ...).  The active set is taken from the
+ * current Omega here.  S_val: p x p device, row stride lds (>= p), element
+ * type s_dtype; symmetric.  Synchronises the stream.
+ * Errors: CONCORD_E_ARG (NULL, lds < p, bad dtype; Omega not symmetric),
+ *   CONCORD_E_NONPOS_DIAG (w_ii <= 0), CONCORD_E_NOMEM, CONCORD_E_CUDA.
+ */
+int concord_heldout(concord_state *st, const void *Sval_dev, int s_dtype, int lds, double *loss_host);
+
+/*
+ * concord_adjoint -- solve H a = b on the active set and return dL/dlambda
+ * (info->dlambda) and optionally dL/dS.
+ * gOmega_dev: dL/dOmega (p x p device, row stride ldg, element type g_dtype,
+ *   full-matrix convention); the active set is taken from the current Omega.
+ *   NULL: use the gradient left by the last concord_heldout (and its active
+ *   set and Omega).
+ * tol (> 0): stop when ||b - H a|| <= tol ||b|| (recursive residual);
+ *   max_iter >= 1 conjugate-gradient iterations at most.
+ * dS_dev: NULL, or p x p FP64 device output (row stride ldds >= p) receiving
+ *   dL/dS = -Omega Ahat (every entry written).
+ * The adjoint a stays in the state for concord_adjoint_data.  A device wait
+ * that runs out returns CONCORD_E_TIMEOUT.  Synchronises the stream.
+ * Errors: CONCORD_E_ARG (NULL info, bad sizes, NULL gOmega without a
+ *   preceding concord_heldout, Omega not symmetric), CONCORD_E_NONFINITE (H
+ *   not positive definite along a search direction, or non-finite values),
+ *   CONCORD_E_TIMEOUT, CONCORD_E_NOMEM, CONCORD_E_CUDA.
+ */
+int concord_adjoint(concord_state *st, const void *gOmega_dev, int g_dtype, int ldg, double tol,
+                    int max_iter, double *dS_dev, int ldds, concord_adjoint_info *info);
+
+/*
+ * concord_adjoint_data -- dL/dX (n x p device output, row stride lddx,
+ * element type dx_dtype) for S = Z^T Z / n, Z = X after `prep`, from the
+ * adjoint of the last concord_adjoint.  X_dev: n x p device data (row
+ * stride ldx, element type x_dtype), the data S was computed from.  The
+ * preparation's statistics are recomputed from X (mean and, for
+ * STANDARDIZE, the population standard deviation) and differentiated too.
+ * Stream-ordered; synchronises only to report a constant column.
+ * Errors: CONCORD_E_ARG (no preceding concord_adjoint, bad sizes),
+ *   CONCORD_E_NONPOS_DIAG (constant column under STANDARDIZE),
+ *   CONCORD_E_NOMEM, CONCORD_E_CUDA.
+ */
+int concord_adjoint_data(concord_state *st, const void *X_dev, int x_dtype, int n, int ldx, int prep,
+                         void *dX_dev, int dx_dtype, int lddx);
+
+/*
+ * concord_tune_lambda -- hypergradient descent on log lambda for the
+ * held-out loss of concord_heldout: `steps` times, solve at lambda
+ * (concord_run warm-started from the current Omega, KKT <= tol, at most
+ * max_sweeps sweeps), take L and dL/dlambda (concord_heldout, then
+ * concord_adjoint with cg_tol and at most 10000 iterations), record the row
+ *   (lambda, L, dL/dlambda, sweeps, CG iterations, KKT residual)
+ * into rows_host[6 k .. 6 k + 5], and move log lambda by
+ * -lr * lambda * dL/dlambda.  The state's S is the training Gram.
+ * Errors: as concord_run, concord_heldout and concord_adjoint; lambda0 > 0,
+ *   steps >= 1, lr >= 0 (CONCORD_E_ARG).
+ */
+int concord_tune_lambda(concord_state *st, const void *Sval_dev, int s_dtype, int lds, double lambda0,
+                        int steps, double lr, double tol, int max_sweeps, double cg_tol,
+                        double *rows_host);
+
 #ifdef __cplusplus
 }
 #endif

@@ -45,6 +45,15 @@ class ConcordResult(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
 
 
+class AdjointInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("active_pairs", ctypes.c_longlong), ("residual", ctypes.c_double),
+                ("dlambda", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class ConcordError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__("%s (%d): %s" % (STATUS_NAMES.get(code, "?"), code, msg))
@@ -91,6 +100,10 @@ SIGNATURES = {
     "concord_path": ([_vp, _dp, _ci, _cd, _ci, _rp, _vp, _ci], _ci),
     "concord_stability": ([_vp, _vp, _ci, _ci, _ci, _ci, _ip, _ip, _ci, _dp, _ci, _cd, _ci, _ci,
                            _vp], _ci),
+    "concord_heldout": ([_vp, _vp, _ci, _ci, _dp], _ci),
+    "concord_adjoint": ([_vp, _vp, _ci, _ci, _cd, _ci, _vp, _ci, ctypes.POINTER(AdjointInfo)], _ci),
+    "concord_adjoint_data": ([_vp, _vp, _ci, _ci, _ci, _ci, _vp, _ci, _ci], _ci),
+    "concord_tune_lambda": ([_vp, _vp, _ci, _ci, _cd, _ci, _cd, _cd, _ci, _cd, _dp], _ci),
 }
 
 _lock = threading.Lock()
@@ -359,6 +372,60 @@ class State:
                                       int(max_sweeps), int(workers), freq_out.data_ptr())
         _check(rc)
         return freq_out
+
+    # implicit differentiation
+    def heldout(self, S_val) -> float:
+        """Held-out loss of the current Omega for the validation Gram S_val;
+        its gradient on the active set becomes the next adjoint's right-hand
+        side."""
+        assert S_val.is_cuda and S_val.dim() == 2 and S_val.stride(1) == 1
+        v = ctypes.c_double(0)
+        _check(load().concord_heldout(self._ptr, S_val.data_ptr(), _dtype_code(S_val),
+                                      S_val.stride(0), ctypes.byref(v)))
+        return v.value
+
+    def adjoint(self, g=None, tol: float = 1e-10, max_iter: int = 10000, dS_out=None):
+        """Adjoint solve on the active set for the loss gradient g (p x p
+        device tensor, full-matrix convention; None: the held-out gradient).
+        Returns AdjointInfo (dL/dlambda in .dlambda); dS_out (p x p float64
+        device tensor) receives dL/dS."""
+        info = AdjointInfo()
+        gptr, gdt, ldg = None, F64, self.p
+        if g is not None:
+            assert g.is_cuda and g.dim() == 2 and g.stride(1) == 1
+            gptr, gdt, ldg = g.data_ptr(), _dtype_code(g), g.stride(0)
+        sptr, lds = None, self.p
+        if dS_out is not None:
+            import torch
+            assert dS_out.is_cuda and dS_out.dtype == torch.float64 and dS_out.stride(1) == 1
+            sptr, lds = dS_out.data_ptr(), dS_out.stride(0)
+        rc = load().concord_adjoint(self._ptr, gptr, gdt, ldg, float(tol), int(max_iter), sptr, lds,
+                                    ctypes.byref(info))
+        _check(rc, (OK, NOT_CONVERGED))
+        return info
+
+    def adjoint_data(self, X, prep: int = PREP_STANDARDIZE, dX_out=None):
+        """dL/dX for the data X that S was computed from (after adjoint())."""
+        import torch
+        assert X.is_cuda and X.dim() == 2 and X.stride(1) == 1
+        if dX_out is None:
+            dX_out = torch.empty(X.shape, dtype=X.dtype, device=X.device)
+        _check(load().concord_adjoint_data(self._ptr, X.data_ptr(), _dtype_code(X), X.shape[0],
+                                           X.stride(0), int(prep), dX_out.data_ptr(),
+                                           _dtype_code(dX_out), dX_out.stride(0)))
+        return dX_out
+
+    def tune_lambda(self, S_val, lam0: float, steps: int = 20, lr: float = 0.5,
+                    tol: float = 1e-5, max_sweeps: int = 1000, cg_tol: float = 1e-10):
+        """Hypergradient descent on log lambda for the held-out loss; returns
+        (steps, 6): lambda, loss, dL/dlambda, sweeps, CG iterations, KKT."""
+        assert S_val.is_cuda and S_val.dim() == 2 and S_val.stride(1) == 1
+        rows = np.zeros((int(steps), 6), dtype=np.float64)
+        _check(load().concord_tune_lambda(self._ptr, S_val.data_ptr(), _dtype_code(S_val),
+                                          S_val.stride(0), float(lam0), int(steps), float(lr),
+                                          float(tol), int(max_sweeps), float(cg_tol),
+                                          rows.ctypes.data_as(_dp)))
+        return rows
 
     def solve_host(self, X: np.ndarray, lam: float, tol: float = 1e-5, max_sweeps: int = 1000,
                    prep: int = PREP_STANDARDIZE, stop_rule: int = STOP_KKT, Omega_out=None):

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "concord.h"
+#include "adjoint.h"
 #include "kernels.h"
 
 using namespace concord;
@@ -102,6 +103,21 @@ struct concord_state {
   int path_cap = 0;
   int* rows_dev = nullptr;
   size_t rows_cap = 0;
+  // implicit differentiation (allocated on demand): CSR of the active set,
+  // the iteration vectors on its entries, and the data-gradient workspace
+  struct {
+    int nnz = 0, cap = 0;
+    int *cnt = nullptr, *rowptr = nullptr, *bad = nullptr;
+    int *col = nullptr, *erow = nullptr, *mirror = nullptr;
+    double *om = nullptr, *minv = nullptr, *b = nullptr, *x = nullptr, *r = nullptr;
+    double *z = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr;
+    double *scal = nullptr;  // [kAdjRes] CG results, then the held-out loss
+    bool rhs_ready = false, solved = false;
+    int n_cap = 0;           // rows of the data workspace
+    double *Z = nullptr, *P = nullptr, *Q = nullptr, *dZ = nullptr;
+    double *part1 = nullptr, *part2 = nullptr, *m1 = nullptr, *m2 = nullptr;
+    double *mean = nullptr, *scale = nullptr;
+  } adj;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaEvent_t lev[2 * kMaxTimedLaunches] = {};
   double launch_ms[kMaxTimedLaunches] = {};
@@ -982,6 +998,13 @@ int concord_destroy(concord_state* st) {
                  st->zt_lo, st->sdiag64, st->sdiagT, st->omdiag64, st->S64, st->W64, st->Om64};
   for (void* d : dev)
     if (d) cudaFree(d);
+  void* adj_dev[] = {st->adj.cnt, st->adj.rowptr, st->adj.bad, st->adj.col, st->adj.erow,
+                     st->adj.mirror, st->adj.om, st->adj.minv, st->adj.b, st->adj.x, st->adj.r,
+                     st->adj.z, st->adj.p0, st->adj.p1, st->adj.q, st->adj.scal, st->adj.Z,
+                     st->adj.P, st->adj.Q, st->adj.dZ, st->adj.part1, st->adj.part2, st->adj.m1,
+                     st->adj.m2, st->adj.mean, st->adj.scale};
+  for (void* d : adj_dev)
+    if (d) cudaFree(d);
   if (is_mixed(st)) {
     if (st->sd1) cudaFree(st->sd1);
     if (st->sd2) cudaFree(st->sd2);
@@ -1545,6 +1568,237 @@ int concord_lambda_max(concord_state* st, double* lambda_max) {
   CK(cudaStreamSynchronize(st->stream));
   memcpy(&bits, st->h_result, sizeof bits);
   memcpy(lambda_max, &bits, sizeof bits);
+  return CONCORD_OK;
+}
+
+// ------------------------------------------------------- implicit differentiation
+
+static int adj_alloc(concord_state* st, void** ptr, size_t bytes) {
+  if (*ptr) cudaFree(*ptr);
+  *ptr = nullptr;
+  CK(cudaMalloc(ptr, bytes));
+  return CONCORD_OK;
+}
+
+// CSR of the active set of the current Omega (FP64 copy when it holds the
+// iterate), its mirror map and the Jacobi preconditioner.
+static int adj_build(concord_state* st) {
+  auto& A = st->adj;
+  const int p = st->p;
+  int rc;
+  if (!A.rowptr) {
+    if ((rc = adj_alloc(st, (void**)&A.cnt, sizeof(int) * p)) ||
+        (rc = adj_alloc(st, (void**)&A.rowptr, sizeof(int) * (p + 1))) ||
+        (rc = adj_alloc(st, (void**)&A.bad, sizeof(int))) ||
+        (rc = adj_alloc(st, (void**)&A.scal, sizeof(double) * (kAdjRes + 2))))
+      return rc;
+  }
+  const bool f64 = !is_mixed(st) || st->om64_current;
+  const void* Om = f64 ? (const void*)st->Om64 : st->Om;
+  const int f32 = f64 ? 0 : 1;
+  CK(launch_adj_count(Om, f32, p, st->ld, A.cnt, st->sms, st->stream));
+  CK(launch_adj_scan(A.cnt, p, A.rowptr, st->stream));
+  int nnz = 0;
+  CK(cudaMemcpyAsync(st->h_flag, A.rowptr + p, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
+  CK(cudaStreamSynchronize(st->stream));
+  nnz = *st->h_flag;
+  if (nnz > A.cap) {
+    const size_t n = (size_t)nnz;
+    int** ints[] = {&A.col, &A.erow, &A.mirror};
+    for (int** q : ints)
+      if ((rc = adj_alloc(st, (void**)q, sizeof(int) * n))) return rc;
+    double** dbl[] = {&A.om, &A.minv, &A.b, &A.x, &A.r, &A.z, &A.p0, &A.p1, &A.q};
+    for (double** q : dbl)
+      if ((rc = adj_alloc(st, (void**)q, sizeof(double) * n))) return rc;
+    A.cap = nnz;
+  }
+  A.nnz = nnz;
+  A.rhs_ready = false;
+  A.solved = false;
+  CK(cudaMemsetAsync(A.bad, 0, sizeof(int), st->stream));
+  CK(launch_adj_fill(Om, f32, p, st->ld, A.rowptr, A.col, A.erow, A.om, st->sms, st->stream));
+  CK(launch_adj_prep(nnz, A.rowptr, A.col, A.erow, A.om, st->sdiag64, A.mirror, A.minv, A.bad,
+                     st->sms, st->stream));
+  CK(cudaMemcpyAsync(st->h_flag, A.bad, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
+  CK(cudaStreamSynchronize(st->stream));
+  if (*st->h_flag)
+    return fail(CONCORD_E_ARG, "Omega is not symmetric or has a non-positive diagonal");
+  return CONCORD_OK;
+}
+
+static bool dtype_ok(int t) { return t == CONCORD_F64 || t == CONCORD_F32; }
+
+int concord_heldout(concord_state* st, const void* Sval_dev, int s_dtype, int lds, double* loss_host) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  if (!Sval_dev || !loss_host || lds < st->p || !dtype_ok(s_dtype))
+    return fail(CONCORD_E_ARG, "S_val and loss must be non-NULL, lds >= p, s_dtype F64 or F32");
+  if ((rc = adj_build(st))) return rc;
+  auto& A = st->adj;
+  // the per-CTA loss partials use the iteration vector r as scratch
+  CK(launch_adj_heldout(A.nnz, A.rowptr, A.col, A.erow, A.mirror, A.om, Sval_dev,
+                        s_dtype == CONCORD_F32, lds, A.b, A.r, A.cap, A.scal + kAdjRes, st->sms,
+                        st->stream));
+  CK(cudaMemcpyAsync(st->h_result, A.scal + kAdjRes, sizeof(double), cudaMemcpyDeviceToHost,
+                     st->stream));
+  CK(cudaStreamSynchronize(st->stream));
+  CK(cudaGetLastError());
+  *loss_host = st->h_result[0];
+  A.rhs_ready = true;
+  if (!isfinite(*loss_host)) return fail(CONCORD_E_NONFINITE, "held-out loss is not finite");
+  return CONCORD_OK;
+}
+
+int concord_adjoint(concord_state* st, const void* gOmega_dev, int g_dtype, int ldg, double tol,
+                    int max_iter, double* dS_dev, int ldds, concord_adjoint_info* info) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  if (!info || !(tol > 0.0) || max_iter < 1 || (dS_dev && ldds < st->p) ||
+      (gOmega_dev && (ldg < st->p || !dtype_ok(g_dtype))))
+    return fail(CONCORD_E_ARG, "info non-NULL, tol > 0, max_iter >= 1, ldg / ldds >= p");
+  auto& A = st->adj;
+  if (gOmega_dev) {
+    if ((rc = adj_build(st))) return rc;
+    CK(launch_adj_rhs_dense(gOmega_dev, g_dtype == CONCORD_F32, ldg, A.nnz, A.col, A.erow, A.b,
+                            st->sms, st->stream));
+  } else if (!A.rhs_ready) {
+    return fail(CONCORD_E_ARG, "gOmega is NULL and no concord_heldout gradient is held");
+  }
+  int occ = 0;
+  CK(adj_cg_occupancy(&occ));
+  if (occ < 1) return fail(CONCORD_E_OCCUPANCY, "adjoint kernel cannot be resident");
+  int grid = st->sms * (occ < 2 ? occ : 2);
+  if (grid > st->max_grid) grid = st->max_grid;
+  if (st->max_ctas > 0 && grid > st->max_ctas) grid = st->max_ctas;
+  AdjArgs a;
+  memset(&a, 0, sizeof a);
+  a.p = st->p;
+  a.ld = st->ld;
+  a.nnz = A.nnz;
+  a.rowptr = A.rowptr;
+  a.col = A.col;
+  a.erow = A.erow;
+  a.mirror = A.mirror;
+  a.om = A.om;
+  a.S = st->S64;
+  a.minv = A.minv;
+  a.b = A.b;
+  a.x = A.x;
+  a.r = A.r;
+  a.z = A.z;
+  a.pb0 = A.p0;
+  a.pb1 = A.p1;
+  a.q = A.q;
+  a.partials = st->partials;
+  a.barrier = st->barrier;
+  a.wait.abort = st->abort_info;
+  a.wait.info = st->abort_info + 1;
+  a.wait.timeout_ns = (uint64_t)(st->timeout_s * 1e9);
+  a.tol = tol;
+  a.max_iter = max_iter;
+  a.result = A.scal;
+  CK(cudaMemsetAsync(st->barrier, 0, sizeof(unsigned), st->stream));
+  CK(cudaMemsetAsync(st->abort_info, 0, 3 * sizeof(int), st->stream));
+  CK(cudaEventRecord(st->ev0, st->stream));
+  CK(launch_adj_cg(a, grid, st->stream));
+  CK(cudaEventRecord(st->ev1, st->stream));
+  if (dS_dev) CK(launch_adj_dS(st->p, A.rowptr, A.col, A.om, A.x, dS_dev, ldds, st->sms, st->stream));
+  CK(cudaMemcpyAsync(st->h_result, A.scal, kAdjRes * sizeof(double), cudaMemcpyDeviceToHost,
+                     st->stream));
+  CK(cudaMemcpyAsync(st->h_abort, st->abort_info, 3 * sizeof(int), cudaMemcpyDeviceToHost,
+                     st->stream));
+  CK(cudaStreamSynchronize(st->stream));
+  CK(cudaGetLastError());
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, st->ev0, st->ev1));
+  const double* r = st->h_result;
+  memset(info, 0, sizeof *info);
+  info->iterations = (int)r[kAdjIters];
+  info->residual = r[kAdjTrue];
+  info->dlambda = r[kAdjDlam];
+  info->active_pairs = (A.nnz - st->p) / 2;
+  info->seconds = ms * 1e-3;
+  if (st->h_abort[0] != 0) {
+    info->status = CONCORD_E_TIMEOUT;
+    return fail(CONCORD_E_TIMEOUT, "device wait ran out in the adjoint (phase %d)", st->h_abort[2]);
+  }
+  const int code = (int)r[kAdjStatus];
+  if (code == 2 || !isfinite(info->dlambda)) {
+    info->status = CONCORD_E_NONFINITE;
+    return fail(CONCORD_E_NONFINITE, "conjugate gradients broke down after %d iterations",
+                info->iterations);
+  }
+  info->status = code == 0 ? CONCORD_OK : CONCORD_NOT_CONVERGED;
+  A.solved = true;
+  return CONCORD_OK;
+}
+
+int concord_adjoint_data(concord_state* st, const void* X_dev, int x_dtype, int n, int ldx, int prep,
+                         void* dX_dev, int dx_dtype, int lddx) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  const int p = st->p;
+  auto& A = st->adj;
+  if (!X_dev || !dX_dev || n < 1 || ldx < p || lddx < p || !dtype_ok(x_dtype) ||
+      !dtype_ok(dx_dtype) || prep < CONCORD_PREP_NONE || prep > CONCORD_PREP_STANDARDIZE)
+    return fail(CONCORD_E_ARG, "X and dX non-NULL, n >= 1, ldx / lddx >= p, valid dtypes and prep");
+  if (!A.solved) return fail(CONCORD_E_ARG, "no adjoint held: call concord_adjoint first");
+  const size_t mat = (size_t)n * st->ld;
+  if (n > A.n_cap) {
+    double** big[] = {&A.Z, &A.P, &A.Q, &A.dZ};
+    for (double** q : big)
+      if ((rc = adj_alloc(st, (void**)q, sizeof(double) * mat))) return rc;
+    A.n_cap = n;
+  }
+  if (!A.m1) {
+    double** small[] = {&A.m1, &A.m2, &A.mean, &A.scale};
+    for (double** q : small)
+      if ((rc = adj_alloc(st, (void**)q, sizeof(double) * p))) return rc;
+    if ((rc = adj_alloc(st, (void**)&A.part1, sizeof(double) * kAdjColChunks * (size_t)p)) ||
+        (rc = adj_alloc(st, (void**)&A.part2, sizeof(double) * kAdjColChunks * (size_t)p)))
+      return rc;
+  }
+  const int xf = x_dtype == CONCORD_F32;
+  CK(cudaMemsetAsync(A.bad, 0, sizeof(int), st->stream));
+  CK(launch_col_stats(X_dev, xf, n, p, ldx, prep, A.mean, A.scale, A.bad, st->stream));
+  CK(launch_apply_prep(X_dev, xf, n, p, ldx, A.mean, A.scale, A.Z, 0, st->ld, st->stream));
+  CK(launch_adj_data(A.Z, A.P, A.Q, A.dZ, st->ld, n, p, prep, A.rowptr, A.col, A.om, A.x, A.scale,
+                     A.part1, A.part2, A.m1, A.m2, dX_dev, dx_dtype == CONCORD_F32, lddx, st->sms,
+                     st->stream));
+  CK(cudaMemcpyAsync(st->h_flag, A.bad, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
+  CK(cudaStreamSynchronize(st->stream));
+  CK(cudaGetLastError());
+  if (*st->h_flag & 2) return fail(CONCORD_E_NONFINITE, "non-finite value in X");
+  if (*st->h_flag) return fail(CONCORD_E_NONPOS_DIAG, "constant column in X under STANDARDIZE");
+  return CONCORD_OK;
+}
+
+int concord_tune_lambda(concord_state* st, const void* Sval_dev, int s_dtype, int lds, double lambda0,
+                        int steps, double lr, double tol, int max_sweeps, double cg_tol,
+                        double* rows_host) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  if (!(lambda0 > 0.0) || steps < 1 || !(lr >= 0.0) || !rows_host || !(cg_tol > 0.0))
+    return fail(CONCORD_E_ARG, "lambda0 > 0, steps >= 1, lr >= 0, cg_tol > 0, rows non-NULL");
+  double log_lam = log(lambda0);
+  for (int k = 0; k < steps; ++k) {
+    const double lam = exp(log_lam);
+    concord_result res;
+    rc = concord_run(st, lam, tol, max_sweeps, CONCORD_STOP_KKT, 0.0, &res);
+    if (rc < 0) return rc;
+    double loss = 0.0;
+    if ((rc = concord_heldout(st, Sval_dev, s_dtype, lds, &loss)) < 0) return rc;
+    concord_adjoint_info info;
+    if ((rc = concord_adjoint(st, nullptr, 0, 0, cg_tol, 10000, nullptr, 0, &info)) < 0) return rc;
+    double* row = rows_host + 6 * (size_t)k;
+    row[0] = lam;
+    row[1] = loss;
+    row[2] = info.dlambda;
+    row[3] = res.sweeps;
+    row[4] = info.iterations;
+    row[5] = res.kkt;
+    log_lam -= lr * lam * info.dlambda;
+  }
   return CONCORD_OK;
 }
 
