@@ -47,6 +47,8 @@ def parse_args(argv=None):
     ap.add_argument("--max-sweeps", type=int, default=500)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip FP64 arm, microbench, e2e and CPU baseline")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the large sparse solve (p = 20000) section")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the differentiable-solve (implicit adjoint) section")
     ap.add_argument("--no-path", action="store_true",
@@ -316,6 +318,52 @@ def run_path_section(C, synth, dev, stream, p=1000, n=800, n_lambda=32, n_sub=8,
                           "estimated_seconds_64": t_stab / n_sub * 64,
                           "edges_freq_ge_0.8_mid_lambda": int((np.triu(f_mid, 1) >= 0.8).sum()),
                           "true_edges": int((np.triu(wl["Om0"], 1) != 0).sum())}}
+
+
+def run_large_section(C, synth, dev, stream, hbm_peak):
+    """Large sparse solve: p = 20000, n = 5000, power-law precision (average
+    degree 4), FP32 data resident in HBM, lambda = 0.15, KKT <= 1e-5.  Mixed
+    (tensor-core Gram, FP32 screened sweeps, FP64 polish) against the FP64
+    GPU solve (FP64 Gram, FP64 sweeps); HBM GB/s of the sweep launches from
+    the screened model's algorithmic bytes."""
+    import torch
+    w = synth.workload_large(device=dev)
+    X, p, n, lam, tol = w["X"], w["p"], w["n"], w["lam"], w["tol"]
+    out = {"workload": "power-law (BA m=2) p=%d, n=%d FP32 data, lambda=%g, KKT<=%g" % (p, n, lam, tol)}
+    for name, prec in (("mixed", C.MIXED), ("fp64", C.FP64)):
+        st = C.State(p, prec, n_cap=n, device=dev.index)
+        st.set_stream(stream)
+        st.set_gram_mode(C.GRAM_TF32X3 if prec == C.MIXED else C.GRAM_FP64)
+        rec = None
+        for _ in range(2):  # warm-up, timed
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = st.solve_device(X, lam, tol=tol, max_sweeps=500)
+            e1.record(stream)
+            stream.synchronize()
+            tm = st.timing()
+            hist = st.history()
+            b = 4 if prec == C.MIXED else 8
+            sweep_ms = sum(ms for ms, _ in tm)
+            rows = hist[: sum(s for _, s in tm[:1])] if tm else hist
+            launch_b = launch_bytes(p, b, rows, screened=True) if len(tm) else 0.0
+            rec = {"seconds": e0.elapsed_time(e1) * 1e-3, "sweeps": r.sweeps,
+                   "sweeps_fp32": r.sweeps_fp32, "dense_sweeps": r.dense_sweeps, "kkt": r.kkt,
+                   "objective": r.objective, "status": r.status,
+                   "sweep_launch_ms": [[ms, s] for ms, s in tm],
+                   "sweeps_per_s": r.sweeps / max(sweep_ms * 1e-3, 1e-12)}
+            if tm and tm[0][0] > 0:
+                ach = launch_b / (tm[0][0] * 1e-3) / 1e9
+                rec["first_launch_GBps"] = ach
+                rec["first_launch_frac_of_hbm"] = ach / hbm_peak
+        out[name] = rec
+        out[name + "_edges"] = int((torch.triu(st.get_omega(), 1) != 0).sum())
+        st.close()
+    out["mixed_vs_fp64_speedup"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    out["true_edges"] = int(len(w["edges"][0]))
+    return out
 
 
 def run_adjoint_section(C, synth, dev, stream, steps=20, lr=0.003):
@@ -596,6 +644,8 @@ def run_ours(args):
             out["path"] = run_path_section(C, synth, dev, stream)
         if not args.no_adjoint:
             out["adjoint"] = run_adjoint_section(C, synth, dev, stream)
+        if not args.no_large:
+            out["large"] = run_large_section(C, synth, dev, stream, hbm_peak)
         # ---------------- CPU oracle, bounded sample (rank 0 only)
         if rank == 0:
             gs, src = golden_sweeps(p)

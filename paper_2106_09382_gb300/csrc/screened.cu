@@ -36,6 +36,14 @@
 #include "kernels.h"
 
 namespace concord {
+
+// Screening margin: a pair is a candidate of the next sweep when its value is
+// nonzero or |G_ij| > (1 - kScreenMargin) lambda at the sweep's start.  Any
+// superset of the pairs that change gives the same iterates (a candidate
+// that stays below the threshold gets a zero change); the margin catches the
+// pairs that cross the threshold during the sweep, which would otherwise
+// fail the verification and force a redo of the sweep.
+constexpr double kScreenMargin = 0.1;
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -260,7 +268,7 @@ __device__ void screen_pass(const ScreenArgs<T>& a, const T* __restrict__ W, int
   const int p = a.p, ld = a.ld;
   const ScreenWork<T>& w = a.w;
   const int nb = (p + kTile - 1) / kTile;
-  const T lam = (T)lamd;
+  const T lam_s = (T)(lamd * (1.0 - kScreenMargin));
   const int units = nb * nb * 4;
   for (int u = gwarp; u < units; u += gwarps) {
     const int tau = u >> 2, r0 = (u & 3) * 8;
@@ -288,7 +296,7 @@ __device__ void screen_pass(const ScreenArgs<T>& a, const T* __restrict__ W, int
       const int i = i0 + r;
       const bool pair = jv && i < p && i < j;
       const T x0 = ((T)0 - w1[r]) - wt[r];
-      const bool cand = pair && (om8[r] != (T)0 || fabs(x0) - lam > (T)0);
+      const bool cand = pair && (om8[r] != (T)0 || fabs(x0) - lam_s > (T)0);
       push_cand(cand, i, j, w.cand[lst], w.ctr + kCtrCand + lst, w.cnt_r[lst], w.nc_cap, lane);
     }
     if (!do_kkt) continue;
@@ -338,6 +346,9 @@ __device__ void verify_pass(const ScreenArgs<T>& a, const T* __restrict__ W,
   // decides the common case without floating-point work: |a + b| <= lambda,
   // so no failure, no candidate and a zero KKT term
   const unsigned small = mag_hi_below((T)(0.5 * lamd * (1.0 - 1e-6)));
+  // the next sweep's screen keeps a margin below lambda (see kScreenMargin)
+  const T lam_s = (T)(lamd * (1.0 - kScreenMargin));
+  const unsigned small_s = mag_hi_below((T)(0.5 * lamd * (1.0 - kScreenMargin) * (1.0 - 1e-6)));
   for (int u = gwarp; u < units; u += gwarps) {
     const int tau = u >> 2, r0 = (u & 3) * 8;
     const int ta = tau / nb, tb = tau % nb;
@@ -366,7 +377,7 @@ __device__ void verify_pass(const ScreenArgs<T>& a, const T* __restrict__ W,
       const int i = i0 + r;
       const bool pair = jv && i < p && i < j && !isnan(v1[r]);
       const bool vsmall = mag_hi(v1[r]) <= small && mag_hi(vt[r]) <= small;
-      const bool wsmall = mag_hi(w1[r]) <= small && mag_hi(wt[r]) <= small;
+      const bool wsmall = mag_hi(w1[r]) <= small_s && mag_hi(wt[r]) <= small_s;
       bool bad = false, next = false;
       if (pair && !vsmall) {
         const T x = ((T)0 - v1[r]) - vt[r];
@@ -375,7 +386,7 @@ __device__ void verify_pass(const ScreenArgs<T>& a, const T* __restrict__ W,
       push_list(bad, i, j, w.fail, w.ctr + kCtrFail, w.fail_cap, lane);
       if (pair && !wsmall) {
         const T x0 = ((T)0 - w1[r]) - wt[r];
-        next = fabs(x0) - lam > (T)0;
+        next = fabs(x0) - lam_s > (T)0;
       }
       push_cand(next, i, j, w.cand[nxt], w.ctr + kCtrCand + nxt, w.cnt_r[nxt], w.nc_cap, lane);
       if (pair && !wsmall) {
@@ -410,6 +421,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
   int pk = a.path_n > 0 ? a.path_start : 0;
   double lamd = a.path_n > 0 ? a.path_lambda[pk] : a.lambda;
   T lam = (T)lamd;
+  T lam_s = (T)(lamd * (1.0 - kScreenMargin));
   int tt = 0;  // sweeps of the whole launch (history rows)
 
   __shared__ double red[kScreenThreads / 32][kParts];
@@ -759,9 +771,10 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
               __syncwarp();
               const bool last = m0 >= ne;
               const T* src = (first ? Wa : Wn) + (size_t)i * ld;
-              // U 16-byte vectors per lane per iteration (memory-level
-              // parallelism); lane l takes vectors q0 + 32 u, u < U
-              constexpr int U = sizeof(T) == 8 ? 2 : 4;
+              // U 16-byte vectors per lane per iteration; lane l takes vectors
+              // q0 + 32 u, u < U (two, so that the paired S-row loads below fit
+              // in registers)
+              constexpr int U = 2;
               for (int q0 = lane; q0 < nv; q0 += 32 * U) {
                 T acc[U][VN], vv[U][VN];
                 int cx[U][VN];
@@ -782,11 +795,19 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
                     vv[uu][e] = (T)0;
                   }
                 }
-                for (int m = 0; m < cnt; ++m) {
-                  const int u = l_u[m], cm = l_c[m];
-                  const T d = l_d[m];
+                // the diagonal's S row (last chunk) and the changes' S rows two
+                // at a time are requested before their values are used, so
+                // each lane keeps several independent loads in flight
+                T si[U][VN];
+                if (last && dd != (T)0) {
+#pragma unroll
+                  for (int uu = 0; uu < U; ++uu) {
+                    const int q = q0 + 32 * uu;
+                    if (q < nv) VT::split(__ldg(reinterpret_cast<const VV*>(Srow) + q), si[uu]);
+                  }
+                }
+                auto load_row = [&](int u, T (&sv)[U][VN]) {
                   const VV* su = reinterpret_cast<const VV*>(a.S + (size_t)u * ld);
-                  T sv[U][VN];
 #pragma unroll
                   for (int uu = 0; uu < U; ++uu) {
                     const int q = q0 + 32 * uu;
@@ -795,6 +816,8 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
 #pragma unroll
                       for (int e = 0; e < VN; ++e) sv[uu][e] = (T)0;
                   }
+                };
+                auto apply = [&](int cm, T d, const T (&sv)[U][VN]) {
 #pragma unroll
                   for (int uu = 0; uu < U; ++uu)
 #pragma unroll
@@ -806,14 +829,19 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
                       }
                       acc[uu][e] = fma_t(d, sv[uu][e], acc[uu][e]);
                     }
+                };
+                int m = 0;
+                for (; m + 1 < cnt; m += 2) {
+                  T sa[U][VN], sb[U][VN];
+                  load_row(l_u[m], sa);
+                  load_row(l_u[m + 1], sb);
+                  apply(l_c[m], l_d[m], sa);
+                  apply(l_c[m + 1], l_d[m + 1], sb);
                 }
-                T si[U][VN];
-                if (last && dd != (T)0) {
-#pragma unroll
-                  for (int uu = 0; uu < U; ++uu) {
-                    const int q = q0 + 32 * uu;
-                    if (q < nv) VT::split(__ldg(reinterpret_cast<const VV*>(Srow) + q), si[uu]);
-                  }
+                if (m < cnt) {
+                  T sa[U][VN];
+                  load_row(l_u[m], sa);
+                  apply(l_c[m], l_d[m], sa);
                 }
 #pragma unroll
                 for (int uu = 0; uu < U; ++uu) {
@@ -880,7 +908,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
             const T omk = d != (T)0 ? __ldcg(w.nd_new + k) : __ldcg(w.nd_rec + 4 * (size_t)k + 2);
             const T w1 = __ldcg(Wn + (size_t)i * ld + j), w2 = __ldcg(Wn + (size_t)j * ld + i);
             const double om = (double)omk, g = (double)w1 + (double)w2;
-            next = omk != (T)0 || (fabs(((T)0 - w1) - w2) - lam > (T)0);
+            next = omk != (T)0 || (fabs(((T)0 - w1) - w2) - lam_s > (T)0);
             v[kPartKkt] = fmax(v[kPartKkt], kkt_offdiag(om, g, lamd));
             v[kPartQuad] += om * g;
             v[kPartPen] += fabs(om);
@@ -1047,6 +1075,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
       ++pk;
       lamd = a.path_lambda[pk];
       lam = (T)lamd;
+      lam_s = (T)(lamd * (1.0 - kScreenMargin));
       t = 0;
       first_delta = 0;
       since_best = 0;

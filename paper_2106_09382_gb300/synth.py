@@ -28,6 +28,17 @@ the sizes and value ranges follow the workloads this library is measured on):
                    magnitude floor 0.1).
     block_diag     `n_blocks` blocks, within-block edge probability, values
                    +-U[lo, hi], diagonal dominance margin.
+    power_law      Barabasi-Albert graph (m edges per new vertex), values
+                   +-U[lo, hi], diagonal dominance margin; kept sparse (edge
+                   lists) for large p, sampled by sample_sparse.
+
+Large sparse sampling (sample_sparse): a diagonally dominant Omega0 is the
+sum of one rank-one term per edge, |v| (e_i + sign(v) e_j)(e_i + sign(v)
+e_j)^T, and the diagonal margin, so Omega0 = B B^T with B sparse; y = B z
+(z ~ N(0, I)) has covariance Omega0 and x = Omega0^{-1} y has covariance
+Omega0^{-1}.  The sparse system is solved by conjugate gradients to a
+relative residual of 1e-13 (torch on the given device; this is sampling, not
+the estimator).
 """
 from __future__ import annotations
 
@@ -205,3 +216,77 @@ def workload_adjoint(p: int = 2000, n_train: int = 1000, n_val: int = 500, seed:
     Om0 = block_diag(p, 20, 0.1, 0.3, 0.6, 0.5, seed)
     return {"Om0": Om0, "X": sample(Om0, n_train, seed), "X_val": sample(Om0, n_val, seed + 7),
             "p": p, "n": n_train, "n_val": n_val}
+
+
+def power_law(p: int, m: int = 2, lo: float = 0.2, hi: float = 0.5, margin: float = 0.5,
+              seed: int = 0):
+    """Sparse power-law precision matrix: Barabasi-Albert edges (i < j), values
+    +-U[lo, hi], diagonal = absolute row sum + margin.  Returns (i, j, v, diag)."""
+    rng = np.random.default_rng(seed)
+    edges = np.array(barabasi_albert_edges(p, m, rng), dtype=np.int64)
+    ei, ej = np.minimum(edges[:, 0], edges[:, 1]), np.maximum(edges[:, 0], edges[:, 1])
+    v = _signed_uniform(rng, len(ei), lo, hi)
+    diag = np.full(p, float(margin))
+    np.add.at(diag, ei, np.abs(v))
+    np.add.at(diag, ej, np.abs(v))
+    return ei, ej, v, diag
+
+
+def sample_sparse(ei, ej, v, diag, n: int, seed: int = 0, device="cuda", dtype=None):
+    """n rows x ~ N(0, Omega0^{-1}) for the sparse diagonally dominant Omega0
+    given by its upper edges (ei < ej, values v) and diagonal; returns an
+    (n, p) torch tensor on `device` (FP64 unless dtype is given)."""
+    import torch
+    p = len(diag)
+    dev = torch.device(device)
+    g = torch.Generator(device=dev)
+    g.manual_seed(int(seed) + 2_000_003)
+    f64 = torch.float64
+    ei_t = torch.as_tensor(ei, device=dev)
+    ej_t = torch.as_tensor(ej, device=dev)
+    v_t = torch.as_tensor(v, dtype=f64, device=dev)
+    rest = torch.as_tensor(diag, dtype=f64, device=dev)
+    rest = rest - torch.zeros(p, dtype=f64, device=dev).index_add_(0, ei_t, v_t.abs()) \
+        .index_add_(0, ej_t, v_t.abs())
+    # y = B z, columns of y are samples (p x n)
+    Y = torch.randn((p, n), generator=g, dtype=f64, device=dev) * rest.clamp_min(0).sqrt()[:, None]
+    ze = torch.randn((len(ei), n), generator=g, dtype=f64, device=dev) * v_t.abs().sqrt()[:, None]
+    Y.index_add_(0, ei_t, ze)
+    Y.index_add_(0, ej_t, ze * torch.sign(v_t)[:, None])
+    del ze
+    rows = torch.cat([ei_t, ej_t, torch.arange(p, device=dev)])
+    cols = torch.cat([ej_t, ei_t, torch.arange(p, device=dev)])
+    vals = torch.cat([v_t, v_t, torch.as_tensor(diag, dtype=f64, device=dev)])
+    A = torch.sparse_coo_tensor(torch.stack([rows, cols]), vals, (p, p),
+                                check_invariants=False).coalesce()
+    # conjugate gradients on A X = Y, all columns at once (Jacobi preconditioner)
+    dinv = 1.0 / torch.as_tensor(diag, dtype=f64, device=dev)[:, None]
+    X = torch.zeros_like(Y)
+    R = Y.clone()
+    Zr = R * dinv
+    P = Zr.clone()
+    rz = (R * Zr).sum(0)
+    ynorm = Y.norm(dim=0)
+    for _ in range(10000):
+        AP = torch.sparse.mm(A, P)
+        alpha = rz / (P * AP).sum(0)
+        X += alpha * P
+        R -= alpha * AP
+        if (R.norm(dim=0) <= 1e-13 * ynorm).all():
+            break
+        Zr = R * dinv
+        rz_new = (R * Zr).sum(0)
+        P = Zr + (rz_new / rz) * P
+        rz = rz_new
+    out = X.t().contiguous()
+    return out if dtype is None else out.to(dtype)
+
+
+def workload_large(p: int = 20000, n: int = 5000, seed: int = 0, device="cuda"):
+    """Large sparse solve: power-law precision (Barabasi-Albert m = 2, average
+    degree 4, +-U[0.2, 0.5], margin 0.5), n samples in FP32 on `device`,
+    lambda = 0.15, tol 1e-5."""
+    import torch
+    ei, ej, v, diag = power_law(p, 2, 0.2, 0.5, 0.5, seed)
+    X = sample_sparse(ei, ej, v, diag, n, seed, device, dtype=torch.float32)
+    return {"X": X, "edges": (ei, ej, v), "diag": diag, "p": p, "n": n, "lam": 0.15, "tol": 1e-5}
