@@ -13,8 +13,9 @@
 //     of two 128-column FP32 accumulators in tensor memory (a new one every
 //     4 K blocks) and commits each stage back to its producer barrier;
 //   * eight epilogue warps drain each finished accumulator (tcgen05.ld, each
-//     warp its own 32 lanes and 64 columns) into FP64 registers, then scale
-//     by 1/n and store S[i][j] and S[j][i] for i <= j.
+//     warp its own 32 lanes and 64 columns) into compensated FP32 running
+//     sums (TwoSum: a high and a low part) kept in the other half of tensor
+//     memory, then scale by 1/n and store S[i][j] and S[j][i] for i <= j.
 // Every wait is bounded (%globaltimer); a wait that runs out sets bit 4 of
 // the caller's status word.
 #include <cuda.h>
@@ -86,7 +87,8 @@ constexpr int kStageBytes = 4 * kOpBytes;         // A_hi, A_lo, B_hi, B_lo
 constexpr int kChunkKb = 4;                       // K blocks summed per FP32 accumulator chunk
 constexpr int kEpiWarps = 8;                      // epilogue warps (2 per TMEM lane quadrant)
 constexpr int kGramThreads = 32 * (2 + kEpiWarps);  // producer, MMA issuer, epilogue
-constexpr int kTmemCols = 256;                    // two 128-column FP32 accumulators
+constexpr int kTmemCols = 512;                    // two 128-column FP32 accumulators + sums
+constexpr int kSumHi = 256, kSumLo = 384;         // tensor-memory columns of the running sums
 constexpr size_t kGramSmem = (size_t)kStages * kStageBytes + 1024;  // + alignment slack
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -193,11 +195,35 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_st_32x32b_x32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]),
+      "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]),
+      "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+
+// hi + lo += x with the rounding error of hi + x kept exactly (Knuth's
+// TwoSum: six FP32 additions, no ordering assumption on |hi| and |x|).
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
 // One CTA per 128 x 128 tile of the upper triangle.  The K reduction is cut
 // into chunks of kChunkKb blocks (128 elements): each chunk accumulates in
 // FP32 in one of two tensor-memory buffers while the epilogue warps add the
-// previous chunk into FP64 registers, so FP32 rounding only ever covers 128
-// products and the tensor pipe never waits for the drain.
+// previous chunk into the compensated running sums, so FP32 rounding only
+// ever covers one chunk's products and the tensor pipe does not wait for the
+// drain.  (FP64 additions in the drain would stall it: this part's FP64 rate
+// is a small fraction of its FP32 rate.)
 __global__ void __launch_bounds__(kGramThreads, 1)
     k_gram_tf32x3(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
                   int nkb, int p, float* __restrict__ S, int lds, float scale, int nbt, int* status) {
@@ -294,13 +320,11 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     }
   } else {
     // ---- epilogue: warp e owns TMEM lanes 32 (warp % 4) .. +31 (tile rows)
-    //      and tile columns 64 * (e / 4) .. +63; FP64 sums across chunks
+    //      and tile columns 64 * (e / 4) .. +63; compensated sums across chunks
     const int e = warp - 2;
     const int quad = warp & 3;
     const int col0 = 64 * (e >> 2);
-    double acc[64];
-#pragma unroll
-    for (int q = 0; q < 64; ++q) acc[q] = 0.0;
+    const uint32_t lanes = (uint32_t)(quad * 32) << 16;
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
       const int b = c & 1;
@@ -308,14 +332,30 @@ __global__ void __launch_bounds__(kGramThreads, 1)
       __syncwarp();
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (ok) {
-        const uint32_t ta = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * kTM + col0);
-        uint32_t v[32];
-        tmem_ld_32x32b_x32(ta, v);
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t cc = (uint32_t)(col0 + 32 * h);
+          uint32_t v[32], hi[32], lo[32];
+          tmem_ld_32x32b_x32(tbase + lanes + (uint32_t)(b * kTM) + cc, v);
+          if (c == 0) {
 #pragma unroll
-        for (int q = 0; q < 32; ++q) acc[q] += (double)__uint_as_float(v[q]);
-        tmem_ld_32x32b_x32(ta + 32, v);
+            for (int q = 0; q < 32; ++q) lo[q] = 0u;
+            tmem_st_32x32b_x32(tbase + lanes + kSumHi + cc, v);
+          } else {
+            tmem_ld_32x32b_x32(tbase + lanes + kSumHi + cc, hi);
+            tmem_ld_32x32b_x32(tbase + lanes + kSumLo + cc, lo);
 #pragma unroll
-        for (int q = 0; q < 32; ++q) acc[32 + q] += (double)__uint_as_float(v[q]);
+            for (int q = 0; q < 32; ++q) {
+              float fh = __uint_as_float(hi[q]), fl = __uint_as_float(lo[q]);
+              two_sum_acc(fh, fl, __uint_as_float(v[q]));
+              hi[q] = __float_as_uint(fh);
+              lo[q] = __float_as_uint(fl);
+            }
+            tmem_st_32x32b_x32(tbase + lanes + kSumHi + cc, hi);
+          }
+          tmem_st_32x32b_x32(tbase + lanes + kSumLo + cc, lo);
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&acc_empty[b]);
@@ -323,14 +363,22 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     }
     if (ok) {
       const int i = bi * kTM + quad * 32 + lane;
-      if (i < p) {
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t cc = (uint32_t)(col0 + 32 * h);
+        uint32_t hi[32], lo[32];
+        tmem_ld_32x32b_x32(tbase + lanes + kSumHi + cc, hi);
+        tmem_ld_32x32b_x32(tbase + lanes + kSumLo + cc, lo);
+        if (i < p) {
 #pragma unroll
-        for (int q = 0; q < 64; ++q) {
-          const int j = bj * kTM + col0 + q;
-          if (j < p && i <= j) {
-            const float val = (float)(acc[q] * (double)scale);
-            S[(size_t)i * lds + j] = val;
-            S[(size_t)j * lds + i] = val;
+          for (int q = 0; q < 32; ++q) {
+            const int j = bj * kTM + (int)cc + q;
+            if (j < p && i <= j) {
+              const double sum = (double)__uint_as_float(hi[q]) + (double)__uint_as_float(lo[q]);
+              const float val = (float)(sum * (double)scale);
+              S[(size_t)i * lds + j] = val;
+              S[(size_t)j * lds + i] = val;
+            }
           }
         }
       }
