@@ -331,9 +331,11 @@ __device__ void screen_pass(const ScreenArgs<T>& a, const T* __restrict__ W, int
 // (Eq. 3's test for staying at zero; a failing pair joins the fail list),
 // their KKT terms max(|G_ij| - lambda, 0), and the screen of the next sweep.
 // Only W and V are read; the candidates' own terms come from the candidate
-// list and the diagonal's from the row pass.
+// list and the diagonal's from the row pass.  Kept out of line: compiled
+// inside the sweep kernel's body its loads were scheduled less well (the
+// pass ran about 10% of a sweep slower).
 template <typename T>
-__device__ void verify_pass(const ScreenArgs<T>& a, const T* __restrict__ W,
+__device__ __noinline__ void verify_pass(const ScreenArgs<T>& a, const T* __restrict__ W,
                             const T* __restrict__ V, int nxt, double lamd, double (&v)[kParts],
                             int lane, int gwarp, int gwarps) {
   const int p = a.p, ld = a.ld;
