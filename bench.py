@@ -47,6 +47,8 @@ def parse_args(argv=None):
     ap.add_argument("--max-sweeps", type=int, default=500)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip FP64 arm, microbench, e2e and CPU baseline")
+    ap.add_argument("--no-gram-study", action="store_true",
+                    help="skip the Gram-variant error study")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the large sparse solve (p = 20000) section")
     ap.add_argument("--no-adjoint", action="store_true",
@@ -318,6 +320,54 @@ def run_path_section(C, synth, dev, stream, p=1000, n=800, n_lambda=32, n_sub=8,
                           "estimated_seconds_64": t_stab / n_sub * 64,
                           "edges_freq_ge_0.8_mid_lambda": int((np.triu(f_mid, 1) >= 0.8).sum()),
                           "true_edges": int((np.triu(wl["Om0"], 1) != 0).sum())}}
+
+
+def run_gram_study(C, X, lam, tol, dev, stream, Om64, obj64):
+    """Gram variants on the benchmark workload: for each Gram of the mixed
+    path (FP32 CUDA cores, 3xTF32 and 3xBF16 tensor cores) its time, its
+    error against the FP64 Gram, and the mixed solve built on it against the
+    FP64 solve (FP64 Gram, FP64 sweeps): Omega, objective and support."""
+    import torch
+    n, p = X.shape
+    S64 = C.concord_gram(X, C.PREP_STANDARDIZE, C.GRAM_FP64, stream=stream)
+    torch.cuda.synchronize()
+    supp64 = Om64 != 0
+    scale = Om64.abs().max().item()
+    out = {}
+    for name, mode in (("fp64", C.GRAM_FP64), ("fp32", C.GRAM_FP32), ("tf32x3", C.GRAM_TF32X3),
+                       ("bf16x3", C.GRAM_BF16X3)):
+        ts = []
+        for _ in range(4):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            S = C.concord_gram(X, C.PREP_STANDARDIZE, mode,
+                               out_dtype=torch.float64 if mode == C.GRAM_FP64 else torch.float32,
+                               stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        rec = {"gram_ms": statistics.median(ts[1:]),
+               "max_abs_dS": (S.double() - S64).abs().max().item()}
+        if mode != C.GRAM_FP64:
+            st = C.State(p, C.MIXED, n_cap=n, device=dev.index)
+            st.set_stream(stream)
+            st.set_gram_mode(mode)
+            st.solve_device(X, lam, tol=tol, max_sweeps=500)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = st.solve_device(X, lam, tol=tol, max_sweeps=500)
+            e1.record(stream)
+            stream.synchronize()
+            Om = st.get_omega()
+            rec.update({"solve_ms": e0.elapsed_time(e1), "sweeps": r.sweeps, "kkt": r.kkt,
+                        "omega_max_abs_err_rel": (Om - Om64).abs().max().item() / scale,
+                        "objective_rel_err": abs(r.objective - obj64) / abs(obj64),
+                        "support_entries_differing": int((Om != 0).ne(supp64).sum().item())})
+            st.close()
+        out[name] = rec
+    return out
 
 
 def run_large_section(C, synth, dev, stream, hbm_peak):
@@ -600,6 +650,9 @@ def run_ours(args):
             "support_entries_differing": supp_diff,
             "note": "mixed uses the tensor-core (3xTF32) Gram; FP64 uses the FP64 Gram"}
         fp64_sweeps = r64["sweeps"]
+        if not args.no_gram_study:
+            out["gram_variants"] = run_gram_study(C, X, lam, tol, dev, stream, st64.get_omega(),
+                                                  r64["objective"])
         # ---------------- full-update microbench: nearly every pair changes
         S32 = C.concord_gram(X, C.PREP_STANDARDIZE, C.GRAM_FP32, stream=stream)
         torch.cuda.synchronize()

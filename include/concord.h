@@ -72,7 +72,12 @@ extern "C" {
 #define CONCORD_GRAM_FP32 1    /* FP32 CUDA-core products, FP32 accumulation */
 #define CONCORD_GRAM_TF32X3 2  /* tensor cores (tcgen05, kind::tf32): each FP32
                                   operand split hi + lo, hi*hi + hi*lo + lo*hi,
-                                  FP32 accumulation in tensor memory */
+                                  FP32 accumulation in tensor memory, chunk sums
+                                  combined with compensated FP32 (TwoSum);
+                                  |dS| <= 128 * 2^-24 + 2^-20 for standardized Z */
+#define CONCORD_GRAM_BF16X3 3  /* the same with bf16 hi + lo parts (tcgen05,
+                                  kind::f16): half the operand bytes, twice the
+                                  MMA rate; |dS| <= 256 * 2^-24 + 2^-14 */
 
 /* Sweep-kernel variant (concord_set_sweep_variant). */
 #define CONCORD_SWEEP_AUTO 0     /* screened sweeps; a sweep whose candidate

@@ -23,7 +23,7 @@ E_ARG, E_NONPOS_DIAG, E_NONFINITE, E_CUDA, E_TIMEOUT, E_NOMEM, E_OCCUPANCY = (
 FP64, MIXED = 0, 1
 F64, F32 = 0, 1
 PREP_NONE, PREP_CENTER, PREP_STANDARDIZE = 0, 1, 2
-GRAM_FP64, GRAM_FP32, GRAM_TF32X3 = 0, 1, 2
+GRAM_FP64, GRAM_FP32, GRAM_TF32X3, GRAM_BF16X3 = 0, 1, 2, 3
 STOP_KKT, STOP_DELTA = 0, 1
 SWEEP_AUTO, SWEEP_GRID, SWEEP_CLUSTER, SWEEP_SCREENED, SWEEP_DENSE = 0, 1, 2, 3, 4
 

@@ -944,7 +944,7 @@ int concord_create(concord_state** out, int p, int precision, int n_cap, int dev
       st->ldz = st->ld;
       ALLOC(st->Z, (size_t)n_cap * st->ldz * e);
       ALLOC(st->Xstage, (size_t)n_cap * p * sizeof(double));
-      st->n_pad = round_up(n_cap, 32);
+      st->n_pad = round_up(n_cap, 64);
       st->p_pad = round_up(p, 128);
       if (is_mixed(st)) {
         ALLOC(st->zt_hi, sizeof(float) * (size_t)st->n_pad * st->p_pad);
@@ -1312,9 +1312,10 @@ int concord_set_rows_per_warp(concord_state* st, int rows) {
 
 int concord_set_gram_mode(concord_state* st, int mode) {
   if (!st) return fail(CONCORD_E_ARG, "state is NULL");
-  if (mode != CONCORD_GRAM_FP64 && mode != CONCORD_GRAM_FP32 && mode != CONCORD_GRAM_TF32X3)
+  if (mode != CONCORD_GRAM_FP64 && mode != CONCORD_GRAM_FP32 && mode != CONCORD_GRAM_TF32X3 &&
+      mode != CONCORD_GRAM_BF16X3)
     return fail(CONCORD_E_ARG, "unknown Gram mode %d", mode);
-  if (mode == CONCORD_GRAM_TF32X3 && !is_mixed(st))
+  if ((mode == CONCORD_GRAM_TF32X3 || mode == CONCORD_GRAM_BF16X3) && !is_mixed(st))
     return fail(CONCORD_E_ARG, "the tensor-core Gram feeds the mixed-precision state only");
   st->gram_mode = mode;
   return CONCORD_OK;
@@ -1353,6 +1354,18 @@ static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, i
                            round_up(n, 32), st->p_pad, st->stream));
       cudaError_t e = launch_gram_tf32x3(st->zt_hi, st->zt_lo, round_up(n, 32), st->p_pad, p,
                                          (float*)st->S, ld, 1.0f / n, st->flag, st->stream);
+      if (e == cudaErrorNotSupported) return fail(CONCORD_E_CUDA, "tensor-core Gram unavailable");
+      CK(e);
+      CK(launch_convert(st->S, 1, ld, st->S64, 0, ld, p, p, st->stream));
+      break;
+    }
+    case CONCORD_GRAM_BF16X3: {
+      uint16_t* hi = (uint16_t*)st->zt_hi;
+      uint16_t* lo = (uint16_t*)st->zt_lo;
+      CK(launch_split_bf16(X, x_f32, n, p, ldx, st->mean, st->inv_scale, hi, lo, round_up(n, 64),
+                           st->p_pad, st->stream));
+      cudaError_t e = launch_gram_bf16x3(hi, lo, round_up(n, 64), st->p_pad, p, (float*)st->S, ld,
+                                         1.0f / n, st->flag, st->stream);
       if (e == cudaErrorNotSupported) return fail(CONCORD_E_CUDA, "tensor-core Gram unavailable");
       CK(e);
       CK(launch_convert(st->S, 1, ld, st->S64, 0, ld, p, p, st->stream));
@@ -1420,28 +1433,33 @@ int concord_gram(const void* X_dev, int x_dtype, int n, int p, int ldx, int prep
       GK(launch_syrk_f32((const float*)Z, n, p, ld, (float*)Sw, ld, 1.0f / n, s));
       GK(launch_convert(Sw, 1, ld, S_dev, 0, lds, p, p, s));
     }
-  } else if (mode == CONCORD_GRAM_TF32X3) {
-    const int n_pad = round_up(n, 32), p_pad = round_up(p, 128);
-    GK(cudaMallocAsync((void**)&hi, sizeof(float) * (size_t)n_pad * p_pad, s));
-    GK(cudaMallocAsync((void**)&lo, sizeof(float) * (size_t)n_pad * p_pad, s));
-    GK(launch_split_tf32(X_dev, x_f32, n, p, ldx, mean, inv, hi, lo, n_pad, p_pad, s));
-    if (s_f32) {
-      e = launch_gram_tf32x3(hi, lo, n_pad, p_pad, p, (float*)S_dev, lds, 1.0f / n, bad, s);
-      if (e == cudaErrorNotSupported) {
-        rc = fail(CONCORD_E_CUDA, "tensor-core Gram unavailable on this device");
-        goto done;
-      }
-      GK(e);
-    } else {
+  } else if (mode == CONCORD_GRAM_TF32X3 || mode == CONCORD_GRAM_BF16X3) {
+    const bool bf = mode == CONCORD_GRAM_BF16X3;
+    const int n_pad = round_up(n, bf ? 64 : 32), p_pad = round_up(p, 128);
+    const size_t esz = bf ? 2 : 4;
+    GK(cudaMallocAsync((void**)&hi, esz * (size_t)n_pad * p_pad, s));
+    GK(cudaMallocAsync((void**)&lo, esz * (size_t)n_pad * p_pad, s));
+    if (bf)
+      GK(launch_split_bf16(X_dev, x_f32, n, p, ldx, mean, inv, (uint16_t*)hi, (uint16_t*)lo, n_pad,
+                           p_pad, s));
+    else
+      GK(launch_split_tf32(X_dev, x_f32, n, p, ldx, mean, inv, hi, lo, n_pad, p_pad, s));
+    float* Sout = (float*)S_dev;
+    int ldo = lds;
+    if (!s_f32) {
       GK(cudaMallocAsync(&Sw, sizeof(float) * (size_t)p * ld, s));
-      e = launch_gram_tf32x3(hi, lo, n_pad, p_pad, p, (float*)Sw, ld, 1.0f / n, bad, s);
-      if (e == cudaErrorNotSupported) {
-        rc = fail(CONCORD_E_CUDA, "tensor-core Gram unavailable on this device");
-        goto done;
-      }
-      GK(e);
-      GK(launch_convert(Sw, 1, ld, S_dev, 0, lds, p, p, s));
+      Sout = (float*)Sw;
+      ldo = ld;
     }
+    e = bf ? launch_gram_bf16x3((const uint16_t*)hi, (const uint16_t*)lo, n_pad, p_pad, p, Sout, ldo,
+                                1.0f / n, bad, s)
+           : launch_gram_tf32x3(hi, lo, n_pad, p_pad, p, Sout, ldo, 1.0f / n, bad, s);
+    if (e == cudaErrorNotSupported) {
+      rc = fail(CONCORD_E_CUDA, "tensor-core Gram unavailable on this device");
+      goto done;
+    }
+    GK(e);
+    if (!s_f32) GK(launch_convert(Sw, 1, ld, S_dev, 0, lds, p, p, s));
   } else {
     rc = fail(CONCORD_E_ARG, "unknown Gram mode %d", mode);
     goto done;

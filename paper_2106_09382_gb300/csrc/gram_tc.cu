@@ -1,15 +1,22 @@
 // Tensor-core Gram for the mixed-precision path: S = Z^T Z / n from FP32
-// operands split into tf32 hi + lo parts (3xTF32: hi*hi + hi*lo + lo*hi, FP32
-// accumulation in tensor memory), on 5th-generation tensor cores (tcgen05).
+// operands split into hi + lo parts and three products hi*hi + hi*lo + lo*hi
+// (FP32 accumulation in tensor memory), on 5th-generation tensor cores
+// (tcgen05), in two operand formats:
+//   3xTF32   tf32 parts (11 significant bits each), tcgen05.mma kind::tf32;
+//   3xBF16   bf16 parts (8 significant bits each), tcgen05.mma kind::f16 --
+//            half the operand bytes and twice the MMA rate of tf32, at an
+//            error of about 2^-16 instead of 2^-22 per product.
+// A 128-byte swizzled row holds 32 tf32 or 64 bf16 values and one MMA covers
+// 32 bytes of K in both formats, so tiles, stages and the MMA loop are shared.
 //
 // Layout: the split kernel writes Zt_hi / Zt_lo as p_pad x n_pad row-major
 // FP32 (K-major operands: the reduction index k is contiguous), zero padded.
 // Each CTA computes one 128 x 128 tile (bi, bj), bi <= bj, of the upper
 // triangle and writes it and its mirror, so S is exactly symmetric.
-//   * thread 0 streams 32-wide K blocks of A_hi, A_lo (rows of tile bi) and
+//   * thread 0 streams K blocks (one 128-byte row) of A_hi, A_lo (rows of tile bi) and
 //     B_hi, B_lo (rows of tile bj) with TMA (128-byte swizzle) into a
 //     3-stage shared-memory ring guarded by mbarriers;
-//   * thread 32 issues, per K block, 4 x 3 tcgen05.mma (K = 8 each) into one
+//   * thread 32 issues, per K block, 4 x 3 tcgen05.mma (32 bytes of K each) into one
 //     of two 128-column FP32 accumulators in tensor memory (a new one every
 //     4 K blocks) and commits each stage back to its producer barrier;
 //   * eight epilogue warps drain each finished accumulator (tcgen05.ld, each
@@ -19,6 +26,7 @@
 // Every wait is bounded (%globaltimer); a wait that runs out sets bit 4 of
 // the caller's status word.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <mutex>
@@ -78,11 +86,56 @@ cudaError_t launch_split_tf32(const void* X, int x_f32, int n, int p, int ldx, c
   return cudaGetLastError();
 }
 
+// The same for the bf16 split: hi = bf16(z), lo = bf16(z - hi), both as raw
+// 16-bit patterns.
+template <typename TX>
+__global__ void __launch_bounds__(256) k_split_bf16(const TX* __restrict__ X, int n, int p, int ldx,
+                                                    const double* __restrict__ mean,
+                                                    const double* __restrict__ inv_scale,
+                                                    uint16_t* __restrict__ hi,
+                                                    uint16_t* __restrict__ lo, int n_pad,
+                                                    int p_pad) {
+  __shared__ uint16_t th[32][34];
+  __shared__ uint16_t tl[32][34];
+  const int k0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int k = k0 + r, i = i0 + tx;
+    float z = 0.f;
+    if (k < n && i < p) z = (float)(((double)X[(size_t)k * ldx + i] - mean[i]) * inv_scale[i]);
+    const __nv_bfloat16 h = __float2bfloat16_rn(z);
+    th[r][tx] = __bfloat16_as_ushort(h);
+    tl[r][tx] = __bfloat16_as_ushort(__float2bfloat16_rn(z - __bfloat162float(h)));
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = i0 + r, k = k0 + tx;
+    if (i < p_pad && k < n_pad) {
+      hi[(size_t)i * n_pad + k] = th[tx][r];
+      lo[(size_t)i * n_pad + k] = tl[tx][r];
+    }
+  }
+}
+
+cudaError_t launch_split_bf16(const void* X, int x_f32, int n, int p, int ldx, const double* mean,
+                              const double* inv_scale, uint16_t* zt_hi, uint16_t* zt_lo, int n_pad,
+                              int p_pad, cudaStream_t st) {
+  dim3 grid((n_pad + 31) / 32, (p_pad + 31) / 32);
+  if (x_f32)
+    k_split_bf16<float><<<grid, 256, 0, st>>>((const float*)X, n, p, ldx, mean, inv_scale, zt_hi,
+                                              zt_lo, n_pad, p_pad);
+  else
+    k_split_bf16<double><<<grid, 256, 0, st>>>((const double*)X, n, p, ldx, mean, inv_scale, zt_hi,
+                                               zt_lo, n_pad, p_pad);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------- tcgen05
 constexpr int kTM = 128;                          // tile rows (M) and columns (N)
-constexpr int kTK = 32;                           // K block: 32 FP32 = 128 bytes
+constexpr int kRowBytes = 128;                    // K block: one 128-byte swizzled row per tile row
 constexpr int kStages = 3;
-constexpr int kOpBytes = kTM * kTK * 4;           // one operand tile: 16 KB
+constexpr int kOpBytes = kTM * kRowBytes;         // one operand tile: 16 KB
 constexpr int kStageBytes = 4 * kOpBytes;         // A_hi, A_lo, B_hi, B_lo
 constexpr int kChunkKb = 4;                       // K blocks summed per FP32 accumulator chunk
 constexpr int kEpiWarps = 8;                      // epilogue warps (2 per TMEM lane quadrant)
@@ -160,10 +213,21 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor of tcgen05.mma kind::tf32: D FP32, A and B TF32,
-// both K-major, N = 128, M = 128.
+// Instruction descriptors: D FP32 (bits 4-5 = 1), A and B format (bits 7-9,
+// 10-12: 2 = TF32 for kind::tf32, 1 = BF16 for kind::f16), both K-major,
+// N = 128 (bits 17-22, N >> 3), M = 128 (bits 24-28, M >> 4).
 constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTM >> 3) << 17) |
                                 ((uint32_t)(kTM >> 4) << 24);
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTM >> 3) << 17) |
+                                ((uint32_t)(kTM >> 4) << 24);
+
+// Operand formats: elements per 128-byte row (the K block).
+struct Tf32Fmt {
+  static constexpr int kTK = 32;
+};
+struct Bf16Fmt {
+  static constexpr int kTK = 64;
+};
 
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
                                          uint32_t accumulate) {
@@ -173,6 +237,22 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint6
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %4, q;\n\t}" ::"r"(d_tmem),
       "l"(a_desc), "l"(b_desc), "r"(accumulate), "r"(kIdescTf32)
       : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\t"
+      "setp.ne.b32 q, %3, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %4, q;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(accumulate), "r"(kIdescBf16)
+      : "memory");
+}
+
+template <typename F>
+__device__ __forceinline__ void mma_fmt(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  if constexpr (F::kTK == Bf16Fmt::kTK) mma_bf16(d, a, b, acc);
+  else mma_tf32(d, a, b, acc);
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -224,9 +304,11 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
 // ever covers one chunk's products and the tensor pipe does not wait for the
 // drain.  (FP64 additions in the drain would stall it: this part's FP64 rate
 // is a small fraction of its FP32 rate.)
+template <typename F>
 __global__ void __launch_bounds__(kGramThreads, 1)
-    k_gram_tf32x3(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
-                  int nkb, int p, float* __restrict__ S, int lds, float scale, int nbt, int* status) {
+    k_gram_3x(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
+              int nkb, int p, float* __restrict__ S, int lds, float scale, int nbt, int* status) {
+  constexpr int kTK = F::kTK;
   extern __shared__ unsigned char gsm_raw[];
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ __align__(8) uint64_t empty[kStages];
@@ -306,12 +388,12 @@ __global__ void __launch_bounds__(kGramThreads, 1)
           const uint64_t bh = sw128_kmajor_desc(st + 2 * kOpBytes);
           const uint64_t bl = sw128_kmajor_desc(st + 3 * kOpBytes);
 #pragma unroll
-          for (int kk = 0; kk < kTK / 8; ++kk) {
-            const uint64_t adv = (uint64_t)(kk * 32 >> 4);  // 8 TF32 = 32 bytes along K
+          for (int kk = 0; kk < kRowBytes / 32; ++kk) {
+            const uint64_t adv = (uint64_t)(kk * 32 >> 4);  // one MMA: 32 bytes along K
             const uint32_t first = (kb == c * kChunkKb && kk == 0) ? 0u : 1u;
-            mma_tf32(d, ah + adv, bh + adv, first);
-            mma_tf32(d, ah + adv, bl + adv, 1u);
-            mma_tf32(d, al + adv, bh + adv, 1u);
+            mma_fmt<F>(d, ah + adv, bh + adv, first);
+            mma_fmt<F>(d, ah + adv, bl + adv, 1u);
+            mma_fmt<F>(d, al + adv, bh + adv, 1u);
           }
           mma_commit(&empty[s]);
         }
@@ -412,17 +494,19 @@ cudaError_t encode_fn(PFN_cuTensorMapEncodeTiled_v12000* out) {
   return cudaSuccess;
 }
 
-// 2-D tensor map over a p_pad x n_pad FP32 array, box 32 (K) x 128 (rows),
-// 128-byte swizzle.
-cudaError_t make_map(CUtensorMap* map, const float* base, int n_pad, int p_pad) {
+// 2-D tensor map over a p_pad x n_pad array of FP32 (bf16 = false) or bf16,
+// box one 128-byte row (K) x 128 rows, 128-byte swizzle.
+cudaError_t make_map(CUtensorMap* map, const void* base, int n_pad, int p_pad, bool bf16) {
   PFN_cuTensorMapEncodeTiled_v12000 enc;
   cudaError_t e = encode_fn(&enc);
   if (e != cudaSuccess) return e;
   cuuint64_t dims[2] = {(cuuint64_t)n_pad, (cuuint64_t)p_pad};
-  cuuint64_t strides[1] = {(cuuint64_t)n_pad * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)kTM};
+  const size_t esz = bf16 ? 2 : 4;
+  cuuint64_t strides[1] = {(cuuint64_t)n_pad * esz};
+  cuuint32_t box[2] = {(cuuint32_t)(kRowBytes / esz), (cuuint32_t)kTM};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
+  CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                   (void*)base, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -430,8 +514,12 @@ cudaError_t make_map(CUtensorMap* map, const float* base, int n_pad, int p_pad) 
 
 }  // namespace
 
-cudaError_t launch_gram_tf32x3(const float* zt_hi, const float* zt_lo, int n_pad, int p_pad, int p,
-                               float* S, int lds, float scale, int* status, cudaStream_t st) {
+namespace {
+
+template <typename F>
+cudaError_t launch_gram_3x(const void* zt_hi, const void* zt_lo, int n_pad, int p_pad, int p, float* S,
+                           int lds, float scale, int* status, cudaStream_t st) {
+  constexpr bool bf16 = F::kTK == Bf16Fmt::kTK;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -439,20 +527,32 @@ cudaError_t launch_gram_tf32x3(const float* zt_hi, const float* zt_lo, int n_pad
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
   if (major != 10 || minor != 3) return cudaErrorNotSupported;
-  if (n_pad % kTK != 0 || p_pad % kTM != 0 || n_pad <= 0 || p_pad <= 0) return cudaErrorInvalidValue;
+  if (n_pad % F::kTK != 0 || p_pad % kTM != 0 || n_pad <= 0 || p_pad <= 0)
+    return cudaErrorInvalidValue;
   if (((uintptr_t)zt_hi & 15) || ((uintptr_t)zt_lo & 15)) return cudaErrorInvalidValue;
   CUtensorMap m_hi, m_lo;
-  if ((e = make_map(&m_hi, zt_hi, n_pad, p_pad)) != cudaSuccess) return e;
-  if ((e = make_map(&m_lo, zt_lo, n_pad, p_pad)) != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_gram_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kGramSmem);
+  if ((e = make_map(&m_hi, zt_hi, n_pad, p_pad, bf16)) != cudaSuccess) return e;
+  if ((e = make_map(&m_lo, zt_lo, n_pad, p_pad, bf16)) != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_gram_3x<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGramSmem);
   if (e != cudaSuccess) return e;
   const int nbt = p_pad / kTM;
   const int tiles = nbt * (nbt + 1) / 2;
-  k_gram_tf32x3<<<tiles, kGramThreads, kGramSmem, st>>>(m_hi, m_lo, n_pad / kTK, p, S, lds, scale,
-                                                        nbt, status);
+  k_gram_3x<F><<<tiles, kGramThreads, kGramSmem, st>>>(m_hi, m_lo, n_pad / F::kTK, p, S, lds, scale,
+                                                      nbt, status);
   note_launches(1);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_gram_tf32x3(const float* zt_hi, const float* zt_lo, int n_pad, int p_pad, int p,
+                               float* S, int lds, float scale, int* status, cudaStream_t st) {
+  return launch_gram_3x<Tf32Fmt>(zt_hi, zt_lo, n_pad, p_pad, p, S, lds, scale, status, st);
+}
+
+cudaError_t launch_gram_bf16x3(const uint16_t* zt_hi, const uint16_t* zt_lo, int n_pad, int p_pad,
+                               int p, float* S, int lds, float scale, int* status, cudaStream_t st) {
+  return launch_gram_3x<Bf16Fmt>(zt_hi, zt_lo, n_pad, p_pad, p, S, lds, scale, status, st);
 }
 
 }  // namespace concord

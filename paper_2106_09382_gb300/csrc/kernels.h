@@ -215,5 +215,12 @@ cudaError_t launch_split_tf32(const void* X, int x_f32, int n, int p, int ldx, c
 // runs out sets bit 4 of *status.  cudaErrorNotSupported if not sm_103.
 cudaError_t launch_gram_tf32x3(const float* zt_hi, const float* zt_lo, int n_pad, int p_pad, int p,
                                float* S, int lds, float scale, int* status, cudaStream_t st);
+// The same split into bf16 hi + lo (raw 16-bit patterns, p_pad x n_pad,
+// n_pad a multiple of 64) and the Gram with tcgen05.mma kind::f16 (3xBF16).
+cudaError_t launch_split_bf16(const void* X, int x_f32, int n, int p, int ldx, const double* mean,
+                              const double* inv_scale, uint16_t* zt_hi, uint16_t* zt_lo, int n_pad,
+                              int p_pad, cudaStream_t st);
+cudaError_t launch_gram_bf16x3(const uint16_t* zt_hi, const uint16_t* zt_lo, int n_pad, int p_pad,
+                               int p, float* S, int lds, float scale, int* status, cudaStream_t st);
 
 }  // namespace concord

@@ -89,6 +89,26 @@ def test_gram_tf32x3_tensor_cores(n, p):
     assert err <= 128 * 2.0 ** -24 + 2.0 ** -20, err
 
 
+@pytest.mark.parametrize("n,p", [(200, 100), (61, 333), (300, 517), (37, 2), (700, 260)])
+def test_gram_bf16x3_tensor_cores(n, p):
+    """tcgen05 kind::f16 Gram with bf16 hi + lo operands.  Each part has 8
+    significant bits, so hi + lo represents z to 2^-16 relative; dropping
+    lo*lo leaves each product off by <= 3 * 2^-16 |z_i z_k| (< 2^-14); the
+    FP32 sums cover chunks of 256 products (<= 256 * 2^-24 of the chunk's
+    absolute sum) and the chunks are combined in compensated FP32.  With
+    sum_k |z_i z_k| <= n the error of S is at most 256 * 2^-24 + 2^-14."""
+    X = data(n, p, 17 * n + p)
+    S = host(C.concord_gram(dev(X), C.PREP_STANDARDIZE, C.GRAM_BF16X3))
+    S_or = O.gram(O.standardize(X))
+    assert np.array_equal(S, S.T)
+    err = np.abs(S - S_or).max()
+    assert err <= 256 * 2.0 ** -24 + 2.0 ** -14, err
+    # bf16 parts are coarser than tf32 parts: the error is well above 3xTF32's
+    S3 = host(C.concord_gram(dev(X), C.PREP_STANDARDIZE, C.GRAM_TF32X3))
+    if p > 2:
+        assert np.abs(S3 - S_or).max() < err
+
+
 def test_gram_centre_and_none():
     X = data(40, 50, 3)
     S1 = host(C.concord_gram(dev(X), C.PREP_CENTER, C.GRAM_FP64))
@@ -512,3 +532,23 @@ def test_full_size_matches_oracle_solve_record(precision):
     diff = (G != 0) != (ref != 0)
     small = (np.abs(G) <= 1e-6 * scale) & (np.abs(ref) <= 1e-6 * scale)
     assert not (diff & ~small).any()
+
+
+@pytest.mark.parametrize("mode", [C.GRAM_TF32X3, C.GRAM_BF16X3])
+def test_mixed_solve_from_tensor_core_grams(mode):
+    """A mixed solve whose S comes from a tensor-core Gram: the answer is the
+    FP64 solution for a perturbed S (|dS| within the Gram's bound), so Omega
+    stays within a small multiple of that bound of the oracle's solution for
+    the exact S, with the same support away from the threshold."""
+    w = synth.workload_small()
+    X = w["X"]
+    S = O.gram(O.standardize(X))
+    Om_or, info = O.solve(S, w["lam"], tol=1e-9, max_sweeps=5000)
+    bound = {C.GRAM_TF32X3: 128 * 2.0 ** -24 + 2.0 ** -20, C.GRAM_BF16X3: 256 * 2.0 ** -24 + 2.0 ** -14}[mode]
+    with C.State(X.shape[1], C.MIXED, n_cap=X.shape[0]) as st:
+        st.set_gram_mode(mode)
+        r = st.solve_device(dev(X), w["lam"], tol=1e-7, max_sweeps=2000)
+        G = host(st.get_omega())
+    assert r.status == C.OK
+    assert np.abs(G - Om_or).max() <= 20 * bound * np.abs(Om_or).max()
+    assert abs(r.objective - info["objective"]) <= 20 * bound * abs(info["objective"])
