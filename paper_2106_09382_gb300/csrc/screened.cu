@@ -44,6 +44,10 @@ namespace concord {
 // pairs that cross the threshold during the sweep, which would otherwise
 // fail the verification and force a redo of the sweep.
 constexpr double kScreenMargin = 0.1;
+
+// Candidates of one row sorted by a warp in shared memory (longer rows: one
+// thread, insertion sort).
+constexpr int kSortCap = 512;
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -485,27 +489,57 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
           w.row_ent[atomicAdd(w.cur_r + pr.y, 1)] = k;
         }
         grid_barrier(a.barrier, gen, wc, ++where);
-        for (int r = gtid; r < p; r += gthreads) {
-          const int b = ldi(w.off_r + r), e = ldi(w.off_r + r + 1);
-          for (int x = b + 1; x < e; ++x) {
-            const int key = ldi(w.row_ent + x);
-            const int2 kp = __ldcg(cand + key);
-            const int kc = pair_step(kp.x, kp.y, P);
-            int y = x - 1;
-            while (y >= b) {
-              const int2 yp = __ldcg(cand + ldi(w.row_ent + y));
-              if (pair_step(yp.x, yp.y, P) <= kc) break;
-              w.row_ent[y + 1] = ldi(w.row_ent + y);
-              --y;
+        // each row's candidates in colour-step order, one warp per row: the
+        // steps of a row are distinct (a colour step pairs the row with one
+        // partner), so a candidate's position is the number of smaller steps;
+        // rows longer than the warp's buffer fall back to an insertion sort
+        {
+          int* sk = reinterpret_cast<int*>(dyn) + wid * 2 * kSortCap;
+          int* ss = sk + kSortCap;
+          for (int r = gwarp; r < p; r += gwarps) {
+            const int b = ldi(w.off_r + r), e = ldi(w.off_r + r + 1), len = e - b;
+            if (len <= kSortCap) {
+              for (int x = lane; x < len; x += 32) {
+                const int key = ldi(w.row_ent + b + x);
+                const int2 kp = __ldcg(cand + key);
+                sk[x] = key;
+                ss[x] = pair_step(kp.x, kp.y, P);
+              }
+              __syncwarp();
+              for (int x = lane; x < len; x += 32) {
+                const int sx = ss[x];
+                int rank = 0;
+                for (int y = 0; y < len; ++y) rank += ss[y] < sx ? 1 : 0;
+                const int key = sk[x];
+                w.row_ent[b + rank] = key;
+                if (__ldcg(cand + key).x == r)
+                  w.nd_pi[key] = rank;
+                else
+                  w.nd_pj[key] = rank;
+              }
+              __syncwarp();
+            } else if (lane == 0) {
+              for (int x = b + 1; x < e; ++x) {
+                const int key = ldi(w.row_ent + x);
+                const int2 kp = __ldcg(cand + key);
+                const int kc = pair_step(kp.x, kp.y, P);
+                int y = x - 1;
+                while (y >= b) {
+                  const int2 yp = __ldcg(cand + ldi(w.row_ent + y));
+                  if (pair_step(yp.x, yp.y, P) <= kc) break;
+                  w.row_ent[y + 1] = ldi(w.row_ent + y);
+                  --y;
+                }
+                w.row_ent[y + 1] = key;
+              }
+              for (int x = b; x < e; ++x) {
+                const int k = ldi(w.row_ent + x);
+                if (__ldcg(cand + k).x == r)
+                  w.nd_pi[k] = x - b;
+                else
+                  w.nd_pj[k] = x - b;
+              }
             }
-            w.row_ent[y + 1] = key;
-          }
-          for (int x = b; x < e; ++x) {
-            const int k = ldi(w.row_ent + x);
-            if (__ldcg(cand + k).x == r)
-              w.nd_pi[k] = x - b;
-            else
-              w.nd_pj[k] = x - b;
           }
         }
         grid_barrier(a.barrier, gen, wc, ++where);
@@ -1139,8 +1173,11 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
 }
 
 size_t screened_dyn_smem(bool mixed) {
-  // per warp of the row pass: the staged changes (partner, step, delta)
-  return (size_t)(kScreenThreads / 32) * kRowList * (8 + (mixed ? 4 : 8));
+  // per warp: the row pass's staged changes (partner, step, delta), or (in
+  // another phase) the row sort's keys and steps
+  const size_t rows = (size_t)kRowList * (8 + (mixed ? 4 : 8));
+  const size_t sort = (size_t)2 * kSortCap * sizeof(int);
+  return (size_t)(kScreenThreads / 32) * (rows > sort ? rows : sort);
 }
 
 template <typename T, bool MIXED>
