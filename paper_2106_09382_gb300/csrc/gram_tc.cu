@@ -456,8 +456,9 @@ __global__ void __launch_bounds__(kGramThreads, 1)
           for (int q = 0; q < 32; ++q) {
             const int j = bj * kTM + (int)cc + q;
             if (j < p && i <= j) {
-              const double sum = (double)__uint_as_float(hi[q]) + (double)__uint_as_float(lo[q]);
-              const float val = (float)(sum * (double)scale);
+              // (hi + lo) * scale in one rounding of hi * scale plus the
+              // (tiny) lo * scale: within an FP32 ulp of the exact product
+              const float val = fmaf(__uint_as_float(hi[q]), scale, __uint_as_float(lo[q]) * scale);
               S[(size_t)i * lds + j] = val;
               S[(size_t)j * lds + i] = val;
             }
