@@ -325,7 +325,7 @@ int launch_dense(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* 
 // lists and per-candidate arrays, carved below.
 struct ScreenLayout {
   size_t ctr, cand0, cand1, cnt_r0, cnt_r1, fail, off_r, cur_r, nd_pi, nd_pj, row_ent, term_ptr, term_pred, term_s, nd_rec, nd_delta, nd_new, nd_d2, jac,
-      diag_old, omdiag_old, total;
+      diag_old, omdiag_old, diag_new, total;
 };
 
 ScreenLayout screen_layout(int p, int P, int nc, int tc) {
@@ -358,6 +358,7 @@ ScreenLayout screen_layout(int p, int P, int nc, int tc) {
   L.diag_old = take(sizeof(double) * (size_t)p);
 
   L.omdiag_old = take(sizeof(double) * (size_t)p);
+  L.diag_new = take(sizeof(double) * (size_t)p);
   L.total = off;
   return L;
 }
@@ -414,6 +415,7 @@ ScreenWork<T> screen_work(concord_state* st) {
   w.diag_old = (T*)(b + L.diag_old);
 
   w.omdiag_old = (double*)(b + L.omdiag_old);
+  w.diag_new = (double*)(b + L.diag_new);
   w.nc_cap = st->nc_cap;
   w.term_cap = st->term_cap;
   w.fail_cap = st->nc_cap;

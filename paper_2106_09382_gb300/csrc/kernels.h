@@ -113,6 +113,7 @@ struct ScreenWork {
   int* jac;                 // [kJacMax] candidates whose change moved, per iteration
   T* diag_old;              // [p] diagonal before the sweep (for a redo)
   double* omdiag_old;       // [p] FP64 diagonal before the sweep (mixed precision)
+  double* diag_new;         // [p] the sweep's new FP64 diagonal, committed after the row pass
   int nc_cap, term_cap, fail_cap;
 };
 

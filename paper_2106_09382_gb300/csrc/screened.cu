@@ -716,7 +716,15 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
           int* l_c = l_u + kRowList;
           T* l_d = reinterpret_cast<T*>(reinterpret_cast<int*>(dyn) + nwarps * kRowList * 2) +
                    wid * kRowList;
-          for (int i = gwarp; i < p; i += gwarps) {
+          // two work items per row, one per half of its columns (vectors
+          // [0, nv/2) and [nv/2, nv)), so rows spread evenly over the warps;
+          // both halves form the row's diagonal root from the same inputs,
+          // the first half records it (committed after the next barrier)
+          const int nv = ld / VN;
+          for (int item = gwarp; item < 2 * p; item += gwarps) {
+            const int i = item >> 1, half = item & 1;
+            const int qbeg = half ? nv / 2 : 0, qend = half ? nv : nv / 2;
+            const int cbeg = qbeg * VN, cend = qend * VN;  // the half's columns
             const int b = ldi(w.off_r + i), ne = ldi(w.off_r + i + 1) - b;
             // diagonal: W_ii after the row's changes (lanes load the changes
             // and their S_ui in parallel; the FMAs run in step order on
@@ -748,31 +756,31 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
               const double oii = MIXED ? __ldcg(a.omdiag64 + i) : (double)o_old;
               const double ci = (double)wii - oii * sii;
               const double nw = (-ci + sqrt(ci * ci + 4.0 * sii)) / (2.0 * sii);
-              w.diag_old[i] = o_old;
-              if (MIXED) {
-                w.omdiag_old[i] = oii;
-                a.omdiag64[i] = nw;
+              if (half == 0) {
+                w.diag_old[i] = o_old;
+                if (MIXED) w.omdiag_old[i] = oii;
+                w.diag_new[i] = nw;
               }
-              a.Om[(size_t)i * ld + i] = (T)nw;
               dd = (T)(nw - oii);
-              dd64 = fabs(nw - oii);
+              dd64 = half == 0 ? fabs(nw - oii) : 0.0;
               // objective / KKT terms of the diagonal after the sweep
               const T wend = dd != (T)0 ? fma_t(dd, __ldg(a.S + (size_t)i * ld + i), wii) : wii;
               const double wd = (double)wend;
               const double od = MIXED ? nw : (double)(T)nw;
-              if (od > 0.0 && isfinite(wd) && isfinite(od)) {
-                v[kPartKkt] = fmax(v[kPartKkt], fabs(wd - 1.0 / od));
-                v[kPartQuad] += od * wd;
-                v[kPartLog] += log(od);
-              } else {
-                v[kPartBad] += 1.0;
+              if (half == 0) {
+                if (od > 0.0 && isfinite(wd) && isfinite(od)) {
+                  v[kPartKkt] = fmax(v[kPartKkt], fabs(wd - 1.0 / od));
+                  v[kPartQuad] += od * wd;
+                  v[kPartLog] += log(od);
+                } else {
+                  v[kPartBad] += 1.0;
+                }
               }
             }
             dd = __shfl_sync(FULL, dd, 0);
             v[kPartDelta] = fmax(v[kPartDelta], dd64);
             // the row's changes in step order, in chunks of kRowList
             const T* Srow = a.S + (size_t)i * ld;
-            const int nv = ld / VN;
             int c_last = -1;  // step of the last change of the previous chunks
             int done = 0;
             bool first = true;
@@ -811,14 +819,14 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
               // q0 + 32 u, u < U (two, so that the paired S-row loads below fit
               // in registers)
               constexpr int U = 2;
-              for (int q0 = lane; q0 < nv; q0 += 32 * U) {
+              for (int q0 = qbeg + lane; q0 < qend; q0 += 32 * U) {
                 T acc[U][VN], vv[U][VN];
                 int cx[U][VN];
                 bool cap[U][VN];  // V captured (in this chunk or an earlier one)
 #pragma unroll
                 for (int uu = 0; uu < U; ++uu) {
                   const int q = q0 + 32 * uu;
-                  if (q < nv)
+                  if (q < qend)
                     VT::split(__ldcg(reinterpret_cast<const VV*>(src) + q), acc[uu]);
                   else
 #pragma unroll
@@ -839,7 +847,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
 #pragma unroll
                   for (int uu = 0; uu < U; ++uu) {
                     const int q = q0 + 32 * uu;
-                    if (q < nv) VT::split(__ldg(reinterpret_cast<const VV*>(Srow) + q), si[uu]);
+                    if (q < qend) VT::split(__ldg(reinterpret_cast<const VV*>(Srow) + q), si[uu]);
                   }
                 }
                 auto load_row = [&](int u, T (&sv)[U][VN]) {
@@ -847,7 +855,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
 #pragma unroll
                   for (int uu = 0; uu < U; ++uu) {
                     const int q = q0 + 32 * uu;
-                    if (q < nv) VT::split(__ldg(su + q), sv[uu]);
+                    if (q < qend) VT::split(__ldg(su + q), sv[uu]);
                     else
 #pragma unroll
                       for (int e = 0; e < VN; ++e) sv[uu][e] = (T)0;
@@ -882,7 +890,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
 #pragma unroll
                 for (int uu = 0; uu < U; ++uu) {
                   const int q = q0 + 32 * uu;
-                  if (q >= nv) continue;
+                  if (q >= qend) continue;
                   T out[VN];
                   T* vrow = a.V + (size_t)i * ld + q * VN;
 #pragma unroll
@@ -904,14 +912,15 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
             // candidates of this row (changed or not) and the diagonal are not verified
             __syncwarp();
             if (ne <= 32) {
-              if (my_u >= 0) a.V[(size_t)i * ld + my_u] = nan_t((T)0);
+              if (my_u >= cbeg && my_u < cend) a.V[(size_t)i * ld + my_u] = nan_t((T)0);
             } else {
               for (int m = lane; m < ne; m += 32) {
                 const int2 qp = __ldcg(w.cand[cur] + ldi(w.row_ent + b + m));
-                a.V[(size_t)i * ld + (qp.x == i ? qp.y : qp.x)] = nan_t((T)0);
+                const int u = qp.x == i ? qp.y : qp.x;
+                if (u >= cbeg && u < cend) a.V[(size_t)i * ld + u] = nan_t((T)0);
               }
             }
-            if (lane == 0) a.V[(size_t)i * ld + i] = nan_t((T)0);
+            if (lane == 0 && i >= cbeg && i < cend) a.V[(size_t)i * ld + i] = nan_t((T)0);
             __syncwarp();
           }
         }
@@ -928,6 +937,12 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
           }
         }
         grid_barrier(a.barrier, gen, wc, ++where);
+        // ---- the new diagonal (both halves of a row read the old one above)
+        for (int k = gtid; k < p; k += gthreads) {
+          const double nw = __ldcg(w.diag_new + k);
+          a.Om[(size_t)k * ld + k] = (T)nw;
+          if (MIXED) a.omdiag64[k] = nw;
+        }
         // ---- verify the other pairs; objective / KKT; screen the next sweep
         verify_pass<T>(a, Wn, a.V, 1 - cur, lamd, v, lane, gwarp, gwarps);
         // the candidates' own terms (and their screen: every nonzero stays a
