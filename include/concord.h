@@ -257,6 +257,20 @@ int concord_set_omega(concord_state *st, const void *Omega0_dev, int dtype, int 
 /* Copy the current Omega (or W = Omega S, or S) of the state out, converted
  * to `dtype`, into device memory with row stride ld. */
 int concord_get_omega(concord_state *st, void *Omega_dev, int dtype, int ld);
+
+/*
+ * concord_get_omega_csr -- the current Omega (FP64 iterate) in compressed
+ * sparse rows, into host (or device) buffers: rowptr[p + 1], col[nnz] (sorted
+ * within each row, diagonal included) and val[nnz] (FP64).  The estimate is
+ * sparse, so this moves (p + 1) * 4 + nnz * 12 bytes instead of p * p * 8.
+ * cap: capacity of col / val in entries; *nnz receives the entry count even
+ * when it exceeds cap (then only rowptr is written and CONCORD_E_ARG is
+ * returned, so a caller can size its buffers and call again).  The copies
+ * are made with cudaMemcpyAsync on the state's stream, which is
+ * synchronised before returning.
+ */
+int concord_get_omega_csr(concord_state *st, int32_t *rowptr, int32_t *col, double *val,
+                          int64_t cap, int64_t *nnz);
 int concord_get_W(concord_state *st, void *W_dev, int dtype, int ld);
 
 /*

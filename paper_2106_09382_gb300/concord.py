@@ -100,6 +100,8 @@ SIGNATURES = {
     "concord_path": ([_vp, _dp, _ci, _cd, _ci, _rp, _vp, _ci], _ci),
     "concord_stability": ([_vp, _vp, _ci, _ci, _ci, _ci, _ip, _ip, _ci, _dp, _ci, _cd, _ci, _ci,
                            _vp], _ci),
+    "concord_get_omega_csr": ([_vp, _ip, _ip, _dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)],
+                              _ci),
     "concord_heldout": ([_vp, _vp, _ci, _ci, _dp], _ci),
     "concord_adjoint": ([_vp, _vp, _ci, _ci, _cd, _ci, _vp, _ci, ctypes.POINTER(AdjointInfo)], _ci),
     "concord_adjoint_data": ([_vp, _vp, _ci, _ci, _ci, _ci, _vp, _ci, _ci], _ci),
@@ -275,6 +277,30 @@ class State:
                           device="cuda:%d" % self.device)
         _check(load().concord_get_omega(self._ptr, out.data_ptr(), _dtype_code(out), self.p))
         return out
+
+    def get_omega_csr(self, cap: int | None = None, out=None):
+        """Omega as host CSR arrays (rowptr int32 [p+1], col int32, val
+        float64).  `out` may pass preallocated (pinned) numpy arrays
+        (rowptr, col, val) whose length sets the capacity."""
+        lib = load()
+        nnz = ctypes.c_int64(0)
+        if out is not None:
+            rowptr, col, val = out
+            cap = len(col)
+        else:
+            rowptr = np.empty(self.p + 1, dtype=np.int32)
+            if cap is None:
+                rc = lib.concord_get_omega_csr(self._ptr, rowptr.ctypes.data_as(_ip), None, None, 0,
+                                               ctypes.byref(nnz))
+                _check(rc, (OK, E_ARG))
+                cap = int(nnz.value)
+            col = np.empty(cap, dtype=np.int32)
+            val = np.empty(cap, dtype=np.float64)
+        _check(lib.concord_get_omega_csr(self._ptr, rowptr.ctypes.data_as(_ip),
+                                         col.ctypes.data_as(_ip), val.ctypes.data_as(_dp), int(cap),
+                                         ctypes.byref(nnz)))
+        k = int(nnz.value)
+        return rowptr, col[:k], val[:k]
 
     def get_W(self, dtype=None):
         import torch

@@ -105,6 +105,10 @@ struct concord_state {
   size_t rows_cap = 0;
   // implicit differentiation (allocated on demand): CSR of the active set,
   // the iteration vectors on its entries, and the data-gradient workspace
+  // CSR readout of Omega (allocated on demand)
+  int *csr_cnt = nullptr, *csr_rowptr = nullptr, *csr_col = nullptr, *csr_row = nullptr;
+  double* csr_val = nullptr;
+  int csr_cap = 0;
   struct {
     int nnz = 0, cap = 0;
     int *cnt = nullptr, *rowptr = nullptr, *bad = nullptr;
@@ -1007,6 +1011,9 @@ int concord_destroy(concord_state* st) {
                      st->adj.m2, st->adj.mean, st->adj.scale};
   for (void* d : adj_dev)
     if (d) cudaFree(d);
+  void* csr_dev[] = {st->csr_cnt, st->csr_rowptr, st->csr_col, st->csr_row, st->csr_val};
+  for (void* d : csr_dev)
+    if (d) cudaFree(d);
   if (is_mixed(st)) {
     if (st->sd1) cudaFree(st->sd1);
     if (st->sd2) cudaFree(st->sd2);
@@ -1819,6 +1826,53 @@ int concord_tune_lambda(concord_state* st, const void* Sval_dev, int s_dtype, in
     row[5] = res.kkt;
     log_lam -= lr * lam * info.dlambda;
   }
+  return CONCORD_OK;
+}
+
+int concord_get_omega_csr(concord_state* st, int32_t* rowptr, int32_t* col, double* val, int64_t cap,
+                          int64_t* nnz_out) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  if (!rowptr || !nnz_out || cap < 0 || (cap > 0 && (!col || !val)))
+    return fail(CONCORD_E_ARG, "rowptr and nnz non-NULL, cap >= 0, col / val non-NULL when cap > 0");
+  const int p = st->p;
+  const bool f64 = !is_mixed(st) || st->om64_current;
+  const void* Om = f64 ? (const void*)st->Om64 : st->Om;
+  if (!st->csr_rowptr) {
+    CK(cudaMalloc(&st->csr_cnt, sizeof(int) * p));
+    CK(cudaMalloc(&st->csr_rowptr, sizeof(int) * (p + 1)));
+  }
+  CK(launch_adj_count(Om, f64 ? 0 : 1, p, st->ld, st->csr_cnt, st->sms, st->stream));
+  CK(launch_adj_scan(st->csr_cnt, p, st->csr_rowptr, st->stream));
+  CK(cudaMemcpyAsync(st->h_flag, st->csr_rowptr + p, sizeof(int), cudaMemcpyDeviceToHost,
+                     st->stream));
+  CK(cudaStreamSynchronize(st->stream));
+  const int nnz = *st->h_flag;
+  *nnz_out = nnz;
+  CK(cudaMemcpyAsync(rowptr, st->csr_rowptr, sizeof(int) * (p + 1), cudaMemcpyDefault, st->stream));
+  if (nnz > cap) {
+    CK(cudaStreamSynchronize(st->stream));
+    return fail(CONCORD_E_ARG, "capacity %lld below the %d entries of Omega", (long long)cap, nnz);
+  }
+  if (nnz > st->csr_cap) {
+    if (st->csr_col) cudaFree(st->csr_col);
+    if (st->csr_row) cudaFree(st->csr_row);
+    if (st->csr_val) cudaFree(st->csr_val);
+    st->csr_col = st->csr_row = nullptr;
+    st->csr_val = nullptr;
+    st->csr_cap = 0;
+    CK(cudaMalloc(&st->csr_col, sizeof(int) * (size_t)nnz));
+    CK(cudaMalloc(&st->csr_row, sizeof(int) * (size_t)nnz));
+    CK(cudaMalloc(&st->csr_val, sizeof(double) * (size_t)nnz));
+    st->csr_cap = nnz;
+  }
+  CK(launch_adj_fill(Om, f64 ? 0 : 1, p, st->ld, st->csr_rowptr, st->csr_col, st->csr_row,
+                     st->csr_val, st->sms, st->stream));
+  CK(cudaMemcpyAsync(col, st->csr_col, sizeof(int) * (size_t)nnz, cudaMemcpyDefault, st->stream));
+  CK(cudaMemcpyAsync(val, st->csr_val, sizeof(double) * (size_t)nnz, cudaMemcpyDefault,
+                     st->stream));
+  CK(cudaStreamSynchronize(st->stream));
+  CK(cudaGetLastError());
   return CONCORD_OK;
 }
 

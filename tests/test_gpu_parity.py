@@ -552,3 +552,25 @@ def test_mixed_solve_from_tensor_core_grams(mode):
     assert r.status == C.OK
     assert np.abs(G - Om_or).max() <= 20 * bound * np.abs(Om_or).max()
     assert abs(r.objective - info["objective"]) <= 20 * bound * abs(info["objective"])
+
+
+@pytest.mark.parametrize("precision", [C.FP64, C.MIXED])
+def test_omega_csr_readout(precision):
+    """The CSR readout holds exactly the nonzeros of the dense Omega."""
+    w = synth.workload_small()
+    X = w["X"]
+    p = X.shape[1]
+    with C.State(p, precision, n_cap=X.shape[0]) as st:
+        st.solve_device(dev(X), w["lam"], tol=1e-6, max_sweeps=500)
+        G = host(st.get_omega())
+        rowptr, col, val = st.get_omega_csr()
+        D = np.zeros((p, p))
+        for i in range(p):
+            sl = slice(rowptr[i], rowptr[i + 1])
+            assert np.all(np.diff(col[sl]) > 0)
+            D[i, col[sl]] = val[sl]
+        assert np.array_equal(D, G)
+        assert rowptr[-1] == np.count_nonzero(G) and len(col) == rowptr[-1]
+        with pytest.raises(C.ConcordError) as e:
+            st.get_omega_csr(cap=3)
+        assert e.value.code == C.E_ARG
