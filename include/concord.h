@@ -479,7 +479,8 @@ int concord_set_fault(concord_state *st, int vertex, int step);
  * and the system is solved by Jacobi-preconditioned conjugate gradients in
  * one persistent cooperative launch; no sweep of the solver is stored or
  * replayed.  Everything here is FP64 on the FP64 copy of S; in MIXED
- * precision the FP64 iterate of the last polishing phase is used.
+ * precision the FP64 iterate of the last polishing phase is used (after a
+ * concord_run / concord_solve_*), else the FP32 iterate widened to FP64.
  *
  * Scratch (allocated on first use, kept by the state): about 84 bytes per
  * entry of A (both orientations of each pair, plus the diagonal) and, for

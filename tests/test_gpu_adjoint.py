@@ -312,3 +312,31 @@ def test_config_size_workload():
             L.append(st.heldout(Svd))
         fd = (L[0] - L[1]) / (2 * h)
         assert abs(info.dlambda - fd) <= 1e-4 * abs(fd)
+
+
+@pytest.mark.parametrize("p", [2, 3, 5])
+def test_adjoint_minimal_sizes(p):
+    """The smallest problems (one pair, a ragged 3 x 3, a 5 x 5), with the
+    pair(s) active, against the dense reference."""
+    rng = np.random.default_rng(40 + p)
+    A0 = np.eye(p) + 0.6 * np.triu(rng.uniform(0.5, 1.0, (p, p)), 1)
+    X = rng.standard_normal((60, p)) @ A0
+    Xv = rng.standard_normal((40, p)) @ A0
+    S = O.gram(O.standardize(X))
+    Sv = O.gram(O.standardize(Xv))
+    lam = 0.2 * O.lambda_max(S)
+    Om_or, _ = O.solve(S, lam, tol=1e-13, max_sweeps=100000)
+    assert len(A.active_set(Om_or)) >= 1
+    ref = A.adjoint(Om_or, S, lam, A.heldout_grad(Om_or, Sv))
+    with C.State(p, C.FP64) as st:
+        st.set_S(dev(S))
+        st.run(lam, tol=1e-13, max_sweeps=100000)
+        assert np.array_equal(host(st.get_omega()) != 0, Om_or != 0)
+        loss = st.heldout(dev(Sv))
+        dS = torch.empty((p, p), dtype=torch.float64, device="cuda")
+        info = st.adjoint(None, tol=1e-13, dS_out=dS)
+        rowptr, col, val = st.get_omega_csr()
+    assert abs(loss - A.heldout_loss(Om_or, Sv)) <= 1e-10 * abs(loss)
+    assert abs(info.dlambda - ref["dlambda"]) <= 1e-7 * max(abs(ref["dlambda"]), 1e-12)
+    assert np.abs(host(dS) - ref["dS"]).max() <= 1e-7 * np.abs(ref["dS"]).max()
+    assert rowptr[-1] == np.count_nonzero(Om_or)
