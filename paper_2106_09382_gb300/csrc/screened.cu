@@ -596,10 +596,19 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         //      round per link.  Thread gtid owns candidate gtid (operands in
         //      registers); further candidates (N > threads) reload theirs.
         // only the CTAs that own candidates iterate (barrier among them);
-        // the others wait at the phase's closing grid barrier
-        const int jac_ctas = min((int)gridDim.x, (N + (int)blockDim.x - 1) / (int)blockDim.x);
+        // the others wait at the phase's closing grid barrier.  In FP64 only
+        // the first kJacThreads threads of a CTA own candidates (enough for
+        // one candidate per thread over all SMs, at least two warps), so
+        // that the rounds' FP64 arithmetic (the division of Eq. 3) is spread
+        // over the SMs (FP64 throughput per SM is small on this part)
+        const int kJacThreads =
+            sizeof(T) == 8 ? min(kScreenThreads, max(64, ((N + (int)gridDim.x - 1) / (int)gridDim.x + 31) / 32 * 32))
+                           : kScreenThreads;
+        const int jac_ctas = min((int)gridDim.x, (N + kJacThreads - 1) / kJacThreads);
+        const int jac_span = jac_ctas * kJacThreads;  // candidates owned one per thread
         if ((int)blockIdx.x < jac_ctas) {
-          const int k0 = gtid;
+          const int k0 = (int)threadIdx.x < kJacThreads ? (int)blockIdx.x * kJacThreads + (int)threadIdx.x
+                                                      : N;
           const bool own = k0 < N;
           T w1 = (T)0, w2 = (T)0, om = (T)0, ss = (T)1;
           int t0 = 0, ts = 0, nt = 0;
@@ -659,7 +668,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
               dnext[k0] = delta;
               w.nd_new[k0] = nw;
             }
-            for (int k = gtid + gthreads; k < N; k += gthreads) {
+            for (int k = k0 + jac_span; k < N; k += jac_span) {
               const T* rec = w.nd_rec + 4 * (size_t)k;
               const int u0 = ldi(w.term_ptr + k), us = u0 + ldi(w.nd_pi + k),
                         u1 = us + ldi(w.nd_pj + k);
