@@ -371,13 +371,24 @@ int ensure_screen(concord_state* st) {
   if (st->scr) return CONCORD_OK;
   const int p = st->p;
   const long long pairs = (long long)p * (p - 1) / 2;
-  // every pair when there are at most 64k of them, else 16 per row
+  // every pair when there are at most 256k of them, else 16 per row
+  // (states with a CTA budget, the concurrent stability workers: 64k)
+  const bool budgeted = st->max_ctas > 0 && st->max_ctas < st->sms;
   long long nc = 16LL * p;
-  if (nc < 65536) nc = 65536;
+  if (nc < (budgeted ? 65536 : (1 << 18))) nc = budgeted ? 65536 : (1 << 18);
   if (nc > pairs) nc = pairs > 0 ? pairs : 1;
   st->nc_cap = (int)nc;
-  // a row with k candidates carries k (k - 1) / 2 correction terms
-  st->term_cap = (int)(8 * nc > (1 << 22) ? 8 * nc : (1 << 22));
+  // a row with k candidates carries k (k - 1) / 2 correction terms (12 bytes
+  // each); a fixed-point round reads every term, so the list grows with p
+  // (where a dense sweep's cost grows too) up to 32 M terms; a sweep whose
+  // count exceeds it is handed to the dense kernel before any term is built.
+  // A budgeted state (a fraction of the SMs) keeps 4 M: with few SMs the
+  // longer screened sweeps lost to the dense kernel (measured on the
+  // stability workload)
+  long long tc = budgeted ? (1LL << 22) : 16384LL * p;
+  if (tc > (1LL << 25)) tc = 1LL << 25;
+  if (tc < 8 * nc) tc = 8 * nc;
+  st->term_cap = (int)tc;
   const ScreenLayout L = screen_layout(p, st->P, st->nc_cap, st->term_cap);
   const size_t mat = (size_t)p * st->ld * sizeof(double);
   CK(cudaMalloc(&st->Wb, mat));

@@ -90,6 +90,7 @@ constexpr int kCtrFail = 2;       // failing pairs found by the verification
 constexpr int kCtrTerms = 3;      // correction terms of the current candidate set
 constexpr int kCtrJacBar = 4;     // barrier counter of the fixed-point iteration
 constexpr int kCtrJacDone = 5;    // the fixed-point iteration settled
+constexpr int kCtrTermsPred = 6;  // correction terms the current list needs (sum over rows of k (k - 1) / 2)
 constexpr int kCtrs = 8;
 constexpr int kJacMax = 64;       // fixed-point iterations of the chain before the dense kernel takes the sweep
 constexpr int kStatusDense = 5;   // result status: the next sweep needs the dense kernel

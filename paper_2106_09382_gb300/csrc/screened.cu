@@ -155,6 +155,28 @@ __device__ void cta_scan(F f, int n, int* out, int* out2, int* s_tmp) {
   __syncthreads();
 }
 
+// Correction terms a list needs (one CTA): a row with k candidates gives its
+// candidates 0 + 1 + ... + (k - 1) terms; written to *out, saturated at
+// INT_MAX, so a sweep whose terms cannot fit goes to the dense kernel before
+// any is built.
+template <typename F>
+__device__ void cta_count_terms(F f, int n, int* out) {
+  __shared__ unsigned long long s_terms;
+  if (threadIdx.x == 0) s_terms = 0ull;
+  __syncthreads();
+  unsigned long long t = 0ull;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const unsigned long long c = (unsigned long long)f(k);
+    t += c * (c - (c > 0 ? 1ull : 0ull)) / 2ull;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(FULL, t, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&s_terms, t);
+  __syncthreads();
+  if (threadIdx.x == 0) *out = s_terms > 0x7fffffffull ? 0x7fffffff : (int)s_terms;
+  __syncthreads();
+}
+
 __device__ __forceinline__ int ldi(const int* p) { return __ldcg(p); }
 
 // Barrier among the CTAs that increment `counter` (zeroed before first use):
@@ -477,11 +499,17 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         //      each row's candidates in colour-step order, and per candidate
         //      its record and correction terms
         if (need_scan) {  // else the previous sweep's reduce phase scanned the counts
-          if (blockIdx.x == 0)
+          if (blockIdx.x == 0) {
             cta_scan([&](int k) { return ldi(w.cnt_r[cur] + k); }, p, w.off_r, w.cur_r, s_tmp);
+            cta_count_terms([&](int k) { return ldi(w.cnt_r[cur] + k); }, p, w.ctr + kCtrTermsPred);
+          }
           grid_barrier(a.barrier, gen, wc, ++where);
         }
         need_scan = true;
+        if (ldi(w.ctr + kCtrTermsPred) > w.term_cap) {  // the terms cannot fit
+          status = kStatusDense;
+          break;
+        }
         if (gtid == 0) w.ctr[kCtrTerms] = 0;  // allocated from two phases later
         for (int k = gtid; k < N; k += gthreads) {
           const int2 pr = __ldcg(cand + k);
@@ -1019,8 +1047,10 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
       }
       reduce_parts(v, a.partials, red);
       // row offsets of the next sweep's list (its pushes are complete)
-      if (blockIdx.x == 0)
+      if (blockIdx.x == 0) {
         cta_scan([&](int k) { return ldi(w.cnt_r[1 - cur] + k); }, p, w.off_r, w.cur_r, s_tmp);
+        cta_count_terms([&](int k) { return ldi(w.cnt_r[1 - cur] + k); }, p, w.ctr + kCtrTermsPred);
+      }
       need_scan = false;
       grid_barrier(a.barrier, gen, wc, ++where);
     }
