@@ -1345,7 +1345,9 @@ int concord_set_gram_mode(concord_state* st, int mode) {
 static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, int ldx, int prep) {
   const int p = st->p, ld = st->ld;
   CK(cudaMemsetAsync(st->flag, 0, sizeof(int), st->stream));
-  CK(launch_col_stats(X, x_f32, n, p, ldx, prep, st->mean, st->inv_scale, st->flag, st->stream));
+  // the FP64 W (free until the iterate is reset below) holds the column partials
+  CK(launch_col_stats_chunked(X, x_f32, n, p, ldx, prep, st->mean, st->inv_scale, st->flag,
+                              st->W64, st->stream));
   switch (st->gram_mode) {
     case CONCORD_GRAM_FP64:
       if (is_mixed(st)) {
@@ -1412,7 +1414,7 @@ int concord_gram(const void* X_dev, int x_dtype, int n, int p, int ldx, int prep
   cudaStream_t s = (cudaStream_t)stream;
   const int x_f32 = x_dtype == CONCORD_F32, s_f32 = s_dtype == CONCORD_F32;
   const int ld = round_up(p, kTile);
-  double *mean = nullptr, *inv = nullptr;
+  double *mean = nullptr, *inv = nullptr, *part = nullptr;
   int* bad = nullptr;
   void* Z = nullptr;
   void* Sw = nullptr;
@@ -1432,7 +1434,8 @@ int concord_gram(const void* X_dev, int x_dtype, int n, int p, int ldx, int prep
   GK(cudaMallocAsync((void**)&inv, sizeof(double) * p, s));
   GK(cudaMallocAsync((void**)&bad, sizeof(int), s));
   GK(cudaMemsetAsync(bad, 0, sizeof(int), s));
-  GK(launch_col_stats(X_dev, x_f32, n, p, ldx, prep, mean, inv, bad, s));
+  GK(cudaMallocAsync((void**)&part, sizeof(double) * (size_t)col_stats_chunks(n) * p, s));
+  GK(launch_col_stats_chunked(X_dev, x_f32, n, p, ldx, prep, mean, inv, bad, part, s));
   if (mode == CONCORD_GRAM_FP64) {
     GK(cudaMallocAsync(&Z, sizeof(double) * (size_t)n * ld, s));
     GK(launch_apply_prep(X_dev, x_f32, n, p, ldx, mean, inv, Z, 0, ld, s));
@@ -1492,6 +1495,7 @@ int concord_gram(const void* X_dev, int x_dtype, int n, int p, int ldx, int prep
     rc = fail(CONCORD_E_NONPOS_DIAG, "X has a constant column");
 done:
   if (mean) cudaFreeAsync(mean, s);
+  if (part) cudaFreeAsync(part, s);
   if (inv) cudaFreeAsync(inv, s);
   if (bad) cudaFreeAsync(bad, s);
   if (Z) cudaFreeAsync(Z, s);
@@ -1798,7 +1802,8 @@ int concord_adjoint_data(concord_state* st, const void* X_dev, int x_dtype, int 
   }
   const int xf = x_dtype == CONCORD_F32;
   CK(cudaMemsetAsync(A.bad, 0, sizeof(int), st->stream));
-  CK(launch_col_stats(X_dev, xf, n, p, ldx, prep, A.mean, A.scale, A.bad, st->stream));
+  // A.P (n x ld, written later) holds the column partials
+  CK(launch_col_stats_chunked(X_dev, xf, n, p, ldx, prep, A.mean, A.scale, A.bad, A.P, st->stream));
   CK(launch_apply_prep(X_dev, xf, n, p, ldx, A.mean, A.scale, A.Z, 0, st->ld, st->stream));
   CK(launch_adj_data(A.Z, A.P, A.Q, A.dZ, st->ld, n, p, prep, A.rowptr, A.col, A.om, A.x, A.scale,
                      A.part1, A.part2, A.m1, A.m2, dX_dev, dx_dtype == CONCORD_F32, lddx, st->sms,

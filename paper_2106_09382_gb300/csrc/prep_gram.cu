@@ -71,6 +71,61 @@ __global__ void __launch_bounds__(kStatThreads) k_col_stats(const TX* __restrict
   if (nonfinite) atomicOr(bad, 2);
 }
 
+// The same statistics over many CTAs: a CTA sums one chunk of rows for 128
+// consecutive columns (coalesced across the CTA) into part[chunk * p + col];
+// a second kernel adds the chunks of each column in chunk order (so the
+// result is deterministic), then the centred sums of squares follow the same
+// way.  Two passes, FP64, as the one-CTA-per-32-columns kernel above.
+constexpr int kStatCols = 128;
+
+template <typename TX, bool SQ>
+__global__ void __launch_bounds__(kStatCols) k_col_partial(const TX* __restrict__ X, int n, int p,
+                                                           int ldx, int rows_per_chunk,
+                                                           const double* __restrict__ mean,
+                                                           double* __restrict__ part,
+                                                           int* __restrict__ bad) {
+  const int col = blockIdx.x * kStatCols + threadIdx.x;
+  if (col >= p) return;
+  const int r0 = blockIdx.y * rows_per_chunk;
+  const int r1 = min(n, r0 + rows_per_chunk);
+  const double mu = SQ ? mean[col] : 0.0;
+  double acc = 0.0;
+  int nonfinite = 0;
+#pragma unroll 8
+  for (int k = r0; k < r1; ++k) {
+    const double v = ld_x(X, (size_t)k * ldx + col);
+    if (SQ) {
+      const double d = v - mu;
+      acc += d * d;
+    } else {
+      acc += v;
+      if (!isfinite(v)) nonfinite = 1;
+    }
+  }
+  part[(size_t)blockIdx.y * p + col] = acc;
+  if (nonfinite) atomicOr(bad, 2);
+}
+
+// SQ = false: mean[col] (prep >= 1, else 0); SQ = true: inv_scale[col]
+// (prep 2: 1 / population sd, flagging a constant column; else 1).
+template <bool SQ>
+__global__ void k_col_final(const double* __restrict__ part, int chunks, int n, int p, int prep,
+                            double* __restrict__ mean, double* __restrict__ inv_scale,
+                            int* __restrict__ bad) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= p) return;
+  double s = 0.0;
+  for (int c = 0; c < chunks; ++c) s += part[(size_t)c * p + col];
+  if (!SQ) {
+    mean[col] = prep >= 1 ? s / n : 0.0;
+    if (prep < 2) inv_scale[col] = 1.0;
+  } else {
+    const double sd = sqrt(s / n);
+    if (!(sd > 0.0)) atomicOr(bad, 1);
+    inv_scale[col] = 1.0 / sd;
+  }
+}
+
 template <typename TX, typename TZ>
 __global__ void k_apply_prep(const TX* __restrict__ X, int n, int p, int ldx,
                              const double* __restrict__ mean, const double* __restrict__ inv_scale,
@@ -93,6 +148,36 @@ cudaError_t launch_col_stats(const void* X, int x_f32, int n, int p, int ldx, in
     k_col_stats<double><<<grid, kStatThreads, 0, st>>>((const double*)X, n, p, ldx, prep, mean,
                                                        inv_scale, bad);
   note_launches(1);
+  return cudaGetLastError();
+}
+
+int col_stats_chunks(int n) { return n < 32 ? n : 32; }
+
+cudaError_t launch_col_stats_chunked(const void* X, int x_f32, int n, int p, int ldx, int prep,
+                                     double* mean, double* inv_scale, int* bad, double* scratch,
+                                     cudaStream_t st) {
+  const int chunks = col_stats_chunks(n);
+  const int rpc = (n + chunks - 1) / chunks;
+  const dim3 grid((p + kStatCols - 1) / kStatCols, chunks);
+  const int fg = (p + 255) / 256;
+  if (x_f32)
+    k_col_partial<float, false><<<grid, kStatCols, 0, st>>>((const float*)X, n, p, ldx, rpc, mean,
+                                                            scratch, bad);
+  else
+    k_col_partial<double, false><<<grid, kStatCols, 0, st>>>((const double*)X, n, p, ldx, rpc, mean,
+                                                             scratch, bad);
+  k_col_final<false><<<fg, 256, 0, st>>>(scratch, chunks, n, p, prep, mean, inv_scale, bad);
+  note_launches(2);
+  if (prep == 2) {
+    if (x_f32)
+      k_col_partial<float, true><<<grid, kStatCols, 0, st>>>((const float*)X, n, p, ldx, rpc, mean,
+                                                             scratch, bad);
+    else
+      k_col_partial<double, true><<<grid, kStatCols, 0, st>>>((const double*)X, n, p, ldx, rpc,
+                                                              mean, scratch, bad);
+    k_col_final<true><<<fg, 256, 0, st>>>(scratch, chunks, n, p, prep, mean, inv_scale, bad);
+    note_launches(2);
+  }
   return cudaGetLastError();
 }
 
