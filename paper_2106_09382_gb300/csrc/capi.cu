@@ -11,6 +11,7 @@
 
 #include "concord.h"
 #include "adjoint.h"
+#include "prep_stats.h"
 #include "kernels.h"
 
 using namespace concord;

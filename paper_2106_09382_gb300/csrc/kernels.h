@@ -164,13 +164,6 @@ cudaError_t launch_refresh_w(const double* Om, const double* S, double* W, int p
 // non-finite.
 cudaError_t launch_col_stats(const void* X, int x_f32, int n, int p, int ldx, int prep,
                              double* mean, double* inv_scale, int* bad, cudaStream_t st);
-// The same statistics spread over many CTAs (row chunks summed per column,
-// then combined in chunk order: deterministic); scratch holds
-// col_stats_chunks(n) x p doubles.
-int col_stats_chunks(int n);
-cudaError_t launch_col_stats_chunked(const void* X, int x_f32, int n, int p, int ldx, int prep,
-                                     double* mean, double* inv_scale, int* bad, double* scratch,
-                                     cudaStream_t st);
 // Z = (X - mean) * inv_scale into Z (n x ldz, type z_f32 ? float : double);
 // columns p..ldz-1 are zero.
 cudaError_t launch_apply_prep(const void* X, int x_f32, int n, int p, int ldx, const double* mean,

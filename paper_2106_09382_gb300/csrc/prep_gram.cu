@@ -1,7 +1,7 @@
 // Data preparation (Section 2.1: columns centered; optionally scaled to unit
 // 1/n variance) and the CUDA-core Gram S = Z^T Z / n (Algorithm 1's
 // T <- X^T X, divided by n).
-#include "kernels.h"
+#include "prep_stats.h"
 
 namespace concord {
 
