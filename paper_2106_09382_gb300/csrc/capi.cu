@@ -66,6 +66,7 @@ struct concord_state {
   // FP64 copies (mixed) or aliases of the working set (fp64)
   double *S64 = nullptr, *W64 = nullptr, *Om64 = nullptr;
   bool om64_current = false;  // mixed: FP64 copies hold the latest iterate
+  int start_list = -1;        // one-shot: the next screened launch starts from this list
   unsigned long long* mbox = nullptr;
   int depth = kMailboxDepth;
   unsigned* barrier = nullptr;
@@ -158,6 +159,7 @@ struct RunOut {
   int to_vertex = -1, to_step = -1;
   bool stalled = false;
   int redos = 0, dense_sweeps = 0;  // screened runs
+  int next_list = -1;               // screened: candidate list left for the next sweep
 };
 
 // One persistent launch: n_sweeps outer iterations (fewer if the stopping
@@ -458,11 +460,16 @@ int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, d
   int rc = ensure_screen(st);
   if (rc != CONCORD_OK) return rc;
   const ScreenLayout L = screen_layout(st->p, st->P, st->nc_cap, st->term_cap);
+  // a list left by the previous launch (one-shot), else screen from scratch
+  const int start_list = (!kkt_only && n_sweeps > 0 && !path) ? st->start_list : -1;
+  st->start_list = -1;
   CK(cudaMemsetAsync(st->barrier, 0, sizeof(unsigned), st->stream));
   CK(cudaMemsetAsync(st->abort_info, 0, 3 * sizeof(int), st->stream));
-  CK(cudaMemsetAsync((char*)st->scr + L.ctr, 0, sizeof(int) * kCtrs, st->stream));
-  CK(cudaMemsetAsync((char*)st->scr + L.cnt_r0, 0, sizeof(int) * (size_t)(st->p + 1), st->stream));
-  CK(cudaMemsetAsync((char*)st->scr + L.cnt_r1, 0, sizeof(int) * (size_t)(st->p + 1), st->stream));
+  if (start_list < 0) {
+    CK(cudaMemsetAsync((char*)st->scr + L.ctr, 0, sizeof(int) * kCtrs, st->stream));
+    CK(cudaMemsetAsync((char*)st->scr + L.cnt_r0, 0, sizeof(int) * (size_t)(st->p + 1), st->stream));
+    CK(cudaMemsetAsync((char*)st->scr + L.cnt_r1, 0, sizeof(int) * (size_t)(st->p + 1), st->stream));
+  }
   ScreenArgs<T> a;
   memset(&a, 0, sizeof a);
   a.p = st->p;
@@ -493,6 +500,7 @@ int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, d
   a.kkt_only = kkt_only;
   a.stall_stop = stall_stop;
   a.max_redo = 8;
+  a.start_list = start_list;
   if (path) {
     a.path_lambda = path->lam;
     a.path_n = path->n;
@@ -524,6 +532,7 @@ int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, d
   out->active = r[kResActive];
   out->first_delta = (int)r[kResFirstDelta];
   out->redos = (int)r[kResRedo];
+  out->next_list = (int)r[kResList];
   if (slot_ev >= 0) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, st->lev[2 * slot_ev], st->lev[2 * slot_ev + 1]));
@@ -783,11 +792,14 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
     fill_result(res, o1, o1.sweeps, o1.sweeps, o1.first_delta, lambda, ms * 1e-3);
     return rc != CONCORD_OK ? rc : o1.status;
   }
-  // ... then FP64 polishing from W rebuilt in FP64
+  // ... then FP64 polishing from W rebuilt in FP64, its first sweep on the
+  // candidate list the FP32 phase left (same lambda)
   if ((rc = promote_to_fp64(st)) != CONCORD_OK) return rc;
   const int left = max_sweeps - o1.sweeps;
+  st->start_list = left > 0 ? o1.next_list : -1;
   rc = launch_run<double>(st, st->S64, st->W64, st->Om64, st->sdiag64, nullptr, lambda, tol,
                           stop_rule, left, left == 0 ? 1 : 0, o1.sweeps, 0, &o2);
+  st->start_list = -1;
   st->hist_rows = o1.sweeps + o2.sweeps;
   // the FP64 copies now hold the iterate (om64_current); the FP32 working
   // set is refreshed from them when an FP32 phase next needs it

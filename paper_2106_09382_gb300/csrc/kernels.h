@@ -38,8 +38,9 @@ constexpr int kParts = 8;
 // Final result block written by CTA 0.
 constexpr int kResSweeps = 0, kResKkt = 1, kResObj = 2, kResDelta = 3, kResActive = 4,
               kResFirstDelta = 5, kResStatus = 6, kResRedo = 7,  // kResRedo: screened only
-              kResPath = 8;  // screened path: index of the lambda a dense hand-over stopped at
-constexpr int kRes = 9;
+              kResPath = 8,  // screened path: index of the lambda a dense hand-over stopped at
+              kResList = 9;  // screened: candidate list of the next sweep (-1: none valid)
+constexpr int kRes = 10;
 constexpr int kHist = 4;  // per sweep: delta, kkt, objective, active pairs
 
 template <typename T>
@@ -139,6 +140,9 @@ struct ScreenArgs {
   double lambda, tol, delta_tol;
   int stop_rule, n_sweeps, kkt_only, stall_stop;
   int max_redo;             // verification rounds per sweep before giving up (status 5)
+  int start_list;           // >= 0: the first sweep uses candidate list start_list as the
+                            // previous launch left it (counts, row offsets, term count);
+                            // -1: screen the starting point
   // lambda path (path_n > 0): lambdas path_lambda[path_start .. path_n), each
   // swept until its stopping rule, warm-started from the previous one
   const double* path_lambda;

@@ -471,8 +471,14 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
   bool need_scan = true;  // row offsets of the current list still to be computed
 
   // ---------------- screen the starting point (and its KKT for kkt_only);
-  //                  the host zeroed the counters and row counts
-  {
+  //                  the host zeroed the counters and row counts.  Or take
+  //                  the list the previous launch left for its next sweep
+  //                  (a superset screen of the same lambda: the verification
+  //                  keeps the iterates exact whatever the list)
+  if (a.start_list >= 0 && !kkt0) {
+    cur = a.start_list;
+    need_scan = false;  // its row offsets and term count are in place
+  } else {
     double v[kParts];
 #pragma unroll
     for (int k = 0; k < kParts; ++k) v[k] = 0.0;
@@ -1106,6 +1112,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
       s_res[kResFirstDelta] = first_delta;
       s_res[kResRedo] = redo_total;
       s_res[kResPath] = pk;
+      s_res[kResList] = (do_sweep && !aborted && !nonfinite && !dense_next) ? (double)(1 - cur) : -1.0;
       s_res[kResStatus] = aborted      ? 3.0
                           : nonfinite  ? 2.0
                           : conv       ? 0.0
@@ -1215,6 +1222,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
     a.result[kResActive] = t > 0 ? s_res[kResActive] : 0.0;
     a.result[kResFirstDelta] = first_delta;
     a.result[kResRedo] = redo_total;
+    a.result[kResList] = -1.0;
     a.result[kResStatus] = ld_relaxed_s32(wc.abort) != 0 ? 3.0 : (double)kStatusDense;
   }
   // leave W in the caller's buffer
