@@ -19,6 +19,9 @@ C source beside it:
     objective        Eq. 1 / n from S; objective_data: Eq. 1 / n from the data
     kkt              subgradient optimality conditions of Eq. 1
     solve            Algorithm 1 repeated until KKT <= tol
+    joint_*          joint two-population CONCORD (the extension closing
+                     Section 6): block update of (omega1_ij, omega2_ij) and of
+                     the diagonal pair, sweep, objective, KKT, solve
 
 ``Oracle(path)`` binds any build of the same source (the planted-mistake
 builds of the pin tests use it); the module-level functions use the normal
@@ -60,6 +63,15 @@ _SIGNATURES = {
     "oracle_objective_data": ([_dp, _ci, _dp, _ci, _cd], _cd),
     "oracle_kkt": ([_dp, _dp, _ci, _cd], _cd),
     "oracle_solve": ([_dp, _ci, _cd, _cd, _cd, _ci, _dp, _dp, _dp, _dp], _ci),
+    "oracle_joint_pair": ([_cd, _cd, _cd, _cd, _cd, _cd, _dp, _dp], None),
+    "oracle_joint_diag": ([_cd, _cd, _cd, _cd, _cd, _dp, _dp], None),
+    "oracle_joint_offdiag_update": ([_dp, _dp, _ci, _cd, _cd, _dp, _dp, _ci, _ci], _cd),
+    "oracle_joint_diag_update": ([_dp, _dp, _ci, _cd, _dp, _dp, _ci], _cd),
+    "oracle_joint_sweep": ([_dp, _dp, _ci, _cd, _cd, _dp, _dp, _ip, _ci, _llp], _cd),
+    "oracle_joint_objective": ([_dp, _dp, _dp, _dp, _ci, _cd, _cd], _cd),
+    "oracle_joint_kkt": ([_dp, _dp, _dp, _dp, _ci, _cd, _cd], _cd),
+    "oracle_joint_solve": ([_dp, _dp, _ci, _cd, _cd, _cd, _cd, _ci, _dp, _dp, _dp, _dp, _dp,
+                            _dp], _ci),
 }
 
 
@@ -228,6 +240,85 @@ class Oracle:
             info["history"] = hist[: info["sweeps"]].copy()
         return Om, info
 
+    # ---- joint two-population CONCORD
+    def joint_pair(self, c1, g1, c2, g2, l1, l2):
+        """Minimiser (x, y) of the two-variable block problem of the joint
+        objective (see oracle_joint_pair)."""
+        x, y = ctypes.c_double(), ctypes.c_double()
+        self.lib.oracle_joint_pair(float(c1), float(g1), float(c2), float(g2), float(l1),
+                                   float(l2), ctypes.byref(x), ctypes.byref(y))
+        return x.value, y.value
+
+    def joint_diag(self, s1, b1, s2, b2, l2):
+        """Minimiser (d1, d2) of the diagonal block problem."""
+        x, y = ctypes.c_double(), ctypes.c_double()
+        self.lib.oracle_joint_diag(float(s1), float(b1), float(s2), float(b2), float(l2),
+                                   ctypes.byref(x), ctypes.byref(y))
+        return x.value, y.value
+
+    def joint_offdiag_update(self, S1, S2, Om1, Om2, l1, l2, i, j) -> float:
+        S1, S2 = _f64(S1), _f64(S2)
+        for Om in (Om1, Om2):
+            assert Om.dtype == np.float64 and Om.flags.c_contiguous
+        return self.lib.oracle_joint_offdiag_update(_ptr(S1), _ptr(S2), S1.shape[0], float(l1),
+                                                    float(l2), _ptr(Om1), _ptr(Om2), int(i),
+                                                    int(j))
+
+    def joint_diag_update(self, S1, S2, Om1, Om2, l2, i) -> float:
+        S1, S2 = _f64(S1), _f64(S2)
+        return self.lib.oracle_joint_diag_update(_ptr(S1), _ptr(S2), S1.shape[0], float(l2),
+                                                 _ptr(Om1), _ptr(Om2), int(i))
+
+    def joint_sweep(self, S1, S2, Om1, Om2, l1, l2, pairs=None):
+        """One joint sweep in place; returns (delta, #pairs that moved)."""
+        S1, S2 = _f64(S1), _f64(S2)
+        p = S1.shape[0]
+        if pairs is None:
+            pairs = self.schedule(p)
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32)
+        nnz = ctypes.c_longlong(0)
+        d = self.lib.oracle_joint_sweep(_ptr(S1), _ptr(S2), p, float(l1), float(l2), _ptr(Om1),
+                                        _ptr(Om2), pairs.ctypes.data_as(_ip), pairs.shape[0],
+                                        ctypes.byref(nnz))
+        return d, nnz.value
+
+    def joint_objective(self, S1, S2, Om1, Om2, l1, l2) -> float:
+        S1, S2, Om1, Om2 = _f64(S1), _f64(S2), _f64(Om1), _f64(Om2)
+        return self.lib.oracle_joint_objective(_ptr(S1), _ptr(S2), _ptr(Om1), _ptr(Om2),
+                                               S1.shape[0], float(l1), float(l2))
+
+    def joint_kkt(self, S1, S2, Om1, Om2, l1, l2) -> float:
+        S1, S2, Om1, Om2 = _f64(S1), _f64(S2), _f64(Om1), _f64(Om2)
+        return self.lib.oracle_joint_kkt(_ptr(S1), _ptr(S2), _ptr(Om1), _ptr(Om2), S1.shape[0],
+                                         float(l1), float(l2))
+
+    def joint_solve(self, S1, S2, l1, l2, tol=1e-5, max_sweeps=1000, Om0=None,
+                    delta_tol=1e-5, history=False):
+        """Joint sweeps until the joint KKT residual <= tol.  Returns
+        (Omega1, Omega2, info dict); Om0 is None or a pair of starting points."""
+        S1, S2 = _f64(S1), _f64(S2)
+        p = S1.shape[0]
+        Om1 = np.empty((p, p), dtype=np.float64)
+        Om2 = np.empty((p, p), dtype=np.float64)
+        stats = np.zeros(6, dtype=np.float64)
+        hist = np.zeros((max(max_sweeps, 1), 3), dtype=np.float64) if history else None
+        i1 = _f64(Om0[0]) if Om0 is not None else None
+        i2 = _f64(Om0[1]) if Om0 is not None else None
+        rc = self.lib.oracle_joint_solve(_ptr(S1), _ptr(S2), p, float(l1), float(l2), float(tol),
+                                         float(delta_tol), int(max_sweeps),
+                                         _ptr(i1) if i1 is not None else None,
+                                         _ptr(i2) if i2 is not None else None,
+                                         _ptr(Om1), _ptr(Om2), _ptr(stats),
+                                         _ptr(hist) if hist is not None else None)
+        if rc < 0:
+            raise ValueError("oracle_joint_solve: status %d" % rc)
+        info = dict(converged=(rc == 0), sweeps=int(stats[0]), objective=float(stats[1]),
+                    kkt=float(stats[2]), delta=float(stats[3]),
+                    first_delta_sweep=int(stats[4]), nonzero_changes=int(stats[5]))
+        if hist is not None:
+            info["history"] = hist[: info["sweeps"]].copy()
+        return Om1, Om2, info
+
 
 _lock = threading.Lock()
 _default: Oracle | None = None
@@ -319,3 +410,28 @@ def lambda_max(S) -> float:
     M = np.abs(S) * (r[:, None] + r[None, :])
     np.fill_diagonal(M, 0.0)
     return float(M.max())
+
+
+def joint_pair(c1, g1, c2, g2, l1, l2):
+    return default().joint_pair(c1, g1, c2, g2, l1, l2)
+
+
+def joint_diag(s1, b1, s2, b2, l2):
+    return default().joint_diag(s1, b1, s2, b2, l2)
+
+
+def joint_sweep(S1, S2, Om1, Om2, l1, l2, pairs=None):
+    return default().joint_sweep(S1, S2, Om1, Om2, l1, l2, pairs)
+
+
+def joint_objective(S1, S2, Om1, Om2, l1, l2):
+    return default().joint_objective(S1, S2, Om1, Om2, l1, l2)
+
+
+def joint_kkt(S1, S2, Om1, Om2, l1, l2):
+    return default().joint_kkt(S1, S2, Om1, Om2, l1, l2)
+
+
+def joint_solve(S1, S2, l1, l2, tol=1e-5, max_sweeps=1000, Om0=None, delta_tol=1e-5,
+                history=False):
+    return default().joint_solve(S1, S2, l1, l2, tol, max_sweeps, Om0, delta_tol, history)

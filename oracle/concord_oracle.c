@@ -158,15 +158,27 @@ double oracle_soft(double x, double tau)
  *                            - sum_{u != i} omega_uj s_iu ) / (s_ii + s_jj)
  * om_i[u] = omega_iu (row i), om_j[u * stride] = omega_uj (column j),
  * s_i / s_j = rows i / j of S.  Returns the new value. */
-double oracle_eq3(const double *om_i, const double *om_j, size_t stride,
-                  const double *s_i, const double *s_j, int p, int i, int j,
-                  double lambda)
+/* The two direct sums of Eq. 3: a1 = sum_{u != j} omega_iu s_ju and
+ * a2 = sum_{u != i} omega_uj s_iu. */
+static void eq3_sums(const double *om_i, const double *om_j, size_t stride,
+                     const double *s_i, const double *s_j, int p, int i, int j,
+                     double *a1_out, double *a2_out)
 {
     double a1 = 0.0, a2 = 0.0;
     for (int u = 0; u < p; ++u)
         if (u != j || MUTANT(1)) a1 += om_i[u] * s_j[u];
     for (int u = 0; u < p; ++u)
         if (u != i) a2 += om_j[(size_t)u * stride] * (MUTANT(2) ? s_j : s_i)[u];
+    *a1_out = a1;
+    *a2_out = a2;
+}
+
+double oracle_eq3(const double *om_i, const double *om_j, size_t stride,
+                  const double *s_i, const double *s_j, int p, int i, int j,
+                  double lambda)
+{
+    double a1, a2;
+    eq3_sums(om_i, om_j, stride, s_i, s_j, p, i, j, &a1, &a2);
     double den = s_i[i] + (MUTANT(4) ? 0.0 : s_j[j]);
     return oracle_soft(-a1 - a2, lambda) / den;
 }
@@ -188,11 +200,18 @@ double oracle_offdiag_update(const double *S, int p, double lambda, double *Om,
  *   c = sum_{j != i} omega_ij s_ij,
  *   omega_ii <- (-c + sqrt(c^2 + 4 s_ii)) / (2 s_ii).
  * Returns the new value. */
-double oracle_eq2(const double *om_i, const double *s_i, int p, int i)
+/* The direct sum of Eq. 2: c = sum_{j != i} omega_ij s_ij. */
+static double eq2_sum(const double *om_i, const double *s_i, int p, int i)
 {
     double c = 0.0;
     for (int j = 0; j < p; ++j)
         if (j != i || MUTANT(5)) c += om_i[j] * s_i[j];
+    return c;
+}
+
+double oracle_eq2(const double *om_i, const double *s_i, int p, int i)
+{
+    double c = eq2_sum(om_i, s_i, p, i);
     double sii = s_i[i];
     return (-c + sqrt(c * c + 4.0 * sii)) / (2.0 * sii);
 }
@@ -405,6 +424,326 @@ int oracle_solve(const double *S, int p, double lambda, double tol,
     if (max_sweeps == 0 && kkt <= tol) status = 0;
     stats[0] = t;
     stats[1] = oracle_objective(S, Om, p, lambda);
+    stats[2] = kkt;
+    stats[3] = delta;
+    stats[4] = first_delta;
+    stats[5] = (double)nnz;
+    free(pairs);
+    return status;
+}
+
+/* ======================================================================== */
+/* Joint two-population CONCORD (the extension at the end of Section 6).     */
+/* ======================================================================== */
+/*
+ * Two precision matrices Omega1, Omega2 (one per population, Grams S1, S2 in
+ * S units) minimise the sum of the two populations' Eq. 1 objectives with
+ * the lasso weight lambda1 on every off-diagonal entry of each matrix, plus
+ * the fusion penalty lambda2 sum_{i <= j} |omega1_ij - omega2_ij| (the
+ * diagonal included, as the joint objective writes it).  With a common n the
+ * joint objective divided by n is exactly this; penalties are on the S scale.
+ *
+ * Block coordinate descent moves the pair (omega1_ij, omega2_ij) jointly, in
+ * the colour order of Algorithm 1 (disjoint pairs do not interact, the same
+ * argument as Lemma 1), then the diagonal blocks (omega1_ii, omega2_ii).
+ */
+
+/* Minimiser of the strictly convex two-variable block problem
+ *   q(x, y) = c1 x^2 / 2 + g1 x + c2 y^2 / 2 + g2 y
+ *             + l1 (|x| + |y|) + l2 |x - y|,        c1, c2 > 0.
+ * If the minimiser has x > y, |x - y| = x - y near it and q separates into
+ * two lasso problems: x = Soft_l1(-(g1 + l2)) / c1, y = Soft_l1(-(g2 - l2)) / c2;
+ * conversely, if those values satisfy x > y they meet every subgradient
+ * condition of q and are its minimiser.  The same holds with the signs of l2
+ * swapped for x < y.  Otherwise x = y = t with t the minimiser of q on the
+ * line x = y: t = Soft_{2 l1}(-(g1 + g2)) / (c1 + c2).  Exactly one of the
+ * three cases holds in exact arithmetic. */
+void oracle_joint_pair(double c1, double g1, double c2, double g2, double l1,
+                       double l2, double *x, double *y)
+{
+    double xa = oracle_soft(-(g1 + l2), l1) / c1;
+    double ya = oracle_soft(-(g2 - (MUTANT(11) ? -l2 : l2)), l1) / c2;
+    if (xa > ya) {
+        *x = xa;
+        *y = ya;
+        return;
+    }
+    double xb = oracle_soft(-(g1 - l2), l1) / c1;
+    double yb = oracle_soft(-(g2 + l2), l1) / c2;
+    if (xb < yb) {
+        *x = xb;
+        *y = yb;
+        return;
+    }
+    double t = oracle_soft(-(g1 + g2), 2.0 * l1) / (c1 + c2);
+    *x = t;
+    *y = t;
+}
+
+/* Positive root of s d^2 + b d - 1 = 0, i.e. of -1/d + s d + b = 0 (the
+ * stationarity condition Eq. 2 solves). */
+static double joint_root(double s, double b)
+{
+    return (-b + sqrt(b * b + 4.0 * s)) / (2.0 * s);
+}
+
+/* Minimiser over d1, d2 > 0 of the diagonal block problem
+ *   -log d1 + s1 d1^2 / 2 + b1 d1 - log d2 + s2 d2^2 / 2 + b2 d2 + l2 |d1 - d2|.
+ * The same three cases as oracle_joint_pair: d1 > d2 gives the two Eq. 2
+ * roots with b1 + l2 and b2 - l2; d1 < d2 the roots with b1 - l2 and b2 + l2;
+ * otherwise d1 = d2 = d, the positive root of
+ * (s1 + s2) d^2 + (b1 + b2) d - 2 = 0. */
+void oracle_joint_diag(double s1, double b1, double s2, double b2, double l2,
+                       double *d1, double *d2)
+{
+    double ua = joint_root(s1, b1 + l2), va = joint_root(s2, b2 - l2);
+    if (ua > va) {
+        *d1 = ua;
+        *d2 = va;
+        return;
+    }
+    double ub = joint_root(s1, b1 - l2), vb = joint_root(s2, b2 + l2);
+    if (ub < vb) {
+        *d1 = ub;
+        *d2 = vb;
+        return;
+    }
+    double ss = s1 + s2, bb = b1 + b2;
+    double d = (-bb + sqrt(bb * bb + (MUTANT(12) ? 4.0 : 8.0) * ss)) / (2.0 * ss);
+    *d1 = d;
+    *d2 = d;
+}
+
+/* The joint update of the pair (i, j): for population m the direct sums of
+ * Eq. 3 give g_m = sum_{u != j} omega^m_iu s^m_ju + sum_{u != i} omega^m_uj s^m_iu
+ * and c_m = s^m_ii + s^m_jj; the block minimiser is written to both triangles
+ * of both matrices.  Returns the larger |change|. */
+double oracle_joint_offdiag_update(const double *S1, const double *S2, int p,
+                                   double l1, double l2, double *Om1,
+                                   double *Om2, int i, int j)
+{
+    const double *S[2] = {S1, S2};
+    double *Om[2] = {Om1, Om2};
+    double g[2], c[2], old[2];
+    for (int m = 0; m < 2; ++m) {
+        double a1, a2;
+        eq3_sums(Om[m] + (size_t)i * p, Om[m] + j, (size_t)p, S[m] + (size_t)i * p,
+                 S[m] + (size_t)j * p, p, i, j, &a1, &a2);
+        g[m] = a1 + a2;
+        c[m] = S[m][(size_t)i * p + i] + S[m][(size_t)j * p + j];
+        old[m] = Om[m][(size_t)i * p + j];
+    }
+    double nw[2];
+    oracle_joint_pair(c[0], g[0], c[1], g[1], l1, l2, &nw[0], &nw[1]);
+    double dmax = 0.0;
+    for (int m = 0; m < 2; ++m) {
+        Om[m][(size_t)i * p + j] = nw[m];
+        Om[m][(size_t)j * p + i] = nw[m];
+        double d = fabs(nw[m] - old[m]);
+        if (d > dmax) dmax = d;
+    }
+    return dmax;
+}
+
+/* The joint diagonal update of vertex i: b_m is the direct sum of Eq. 2 for
+ * population m.  Returns the larger |change|. */
+double oracle_joint_diag_update(const double *S1, const double *S2, int p,
+                                double l2, double *Om1, double *Om2, int i)
+{
+    size_t ii = (size_t)i * p + i;
+    double b1 = eq2_sum(Om1 + (size_t)i * p, S1 + (size_t)i * p, p, i);
+    double b2 = eq2_sum(Om2 + (size_t)i * p, S2 + (size_t)i * p, p, i);
+    double d1, d2;
+    oracle_joint_diag(S1[ii], b1, S2[ii], b2, l2, &d1, &d2);
+    double c1 = fabs(d1 - Om1[ii]), c2 = fabs(d2 - Om2[ii]);
+    Om1[ii] = d1;
+    Om2[ii] = d2;
+    return c1 > c2 ? c1 : c2;
+}
+
+/* One joint sweep: every colour of `pairs` in order (slot order within a
+ * colour), then every diagonal block.  Returns the largest |change| of any
+ * entry of either matrix; *n_nonzero counts the pairs that moved. */
+double oracle_joint_sweep(const double *S1, const double *S2, int p, double l1,
+                          double l2, double *Om1, double *Om2,
+                          const int32_t *pairs, int n_colours, long long *n_nonzero)
+{
+    int half = (n_colours + 1) / 2;
+    double dmax = 0.0;
+    for (int k = 0; k < n_colours; ++k)
+        for (int q = 0; q < half; ++q) {
+            const int32_t *slot = pairs + ((size_t)k * half + q) * 2;
+            if (slot[0] < 0) continue;
+            double d = oracle_joint_offdiag_update(S1, S2, p, l1, l2, Om1, Om2,
+                                                   slot[0], slot[1]);
+            if (d > dmax) dmax = d;
+            if (n_nonzero && d != 0.0) ++*n_nonzero;
+        }
+    for (int i = 0; i < p; ++i) {
+        double d = oracle_joint_diag_update(S1, S2, p, l2, Om1, Om2, i);
+        if (d > dmax) dmax = d;
+    }
+    return dmax;
+}
+
+/* Joint objective (S units): the two populations' Eq. 1 objectives with
+ * lasso weight l1, plus l2 sum_{i <= j} |omega1_ij - omega2_ij|. */
+double oracle_joint_objective(const double *S1, const double *S2, const double *Om1,
+                              const double *Om2, int p, double l1, double l2)
+{
+    double f = oracle_objective(S1, Om1, p, l1) + oracle_objective(S2, Om2, p, l1);
+    double fus = 0.0;
+    for (int i = 0; i < p; ++i)
+        for (int j = (MUTANT(13) ? i + 1 : i); j < p; ++j)
+            fus += fabs(Om1[(size_t)i * p + j] - Om2[(size_t)i * p + j]);
+    return f + l2 * fus;
+}
+
+static double clampd(double v, double lo, double hi)
+{
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+/* Distance from -g to the set l1 * d|x| (the lasso subdifferential). */
+static double lasso_residual(double g, double x, double l1)
+{
+    if (x > 0.0) return fabs(g + l1);
+    if (x < 0.0) return fabs(g - l1);
+    double r = fabs(g) - l1;
+    return r > 0.0 ? r : 0.0;
+}
+
+/* Largest violation of the subgradient optimality conditions of the joint
+ * objective (absolute, S units).  W_m = Omega_m S_m by the plain product.
+ * For a pair (i < j) with smooth gradients G_m = W^m_ij + W^m_ji, the
+ * conditions ask for u = l2 z, z in d|x - y|, with
+ *   0 in G1 + u + l1 d|x|   and   0 in G2 - u + l1 d|y|;
+ * the residual is the smallest, over admissible u, of the larger of the two
+ * distances.  If x != y, u = l2 sign(x - y) is fixed.  If x = y both
+ * distances are |A + u| and |B - u| (A, B the gradients with the lasso term
+ * of a nonzero x folded in; for x = y = 0 the distances are those minus l1,
+ * floored at 0), whose maximum is convex in u and smallest at
+ * u = (B - A) / 2, so the admissible optimum is that u clamped to
+ * [-l2, l2].  Diagonal blocks: G_m = W^m_ii - 1 / omega^m_ii, no lasso term,
+ * the same rule for u. */
+double oracle_joint_kkt(const double *S1, const double *S2, const double *Om1,
+                        const double *Om2, int p, double l1, double l2)
+{
+    const double *S[2] = {S1, S2};
+    const double *Om[2] = {Om1, Om2};
+    double *W[2];
+    for (int m = 0; m < 2; ++m) {
+        W[m] = (double *)malloc(sizeof(double) * (size_t)p * p);
+        if (!W[m]) {
+            if (m) free(W[0]);
+            return NAN;
+        }
+        for (int i = 0; i < p; ++i)
+            for (int j = 0; j < p; ++j) {
+                double acc = 0.0;
+                for (int u = 0; u < p; ++u) {
+                    double o = Om[m][(size_t)i * p + u];
+                    if (o != 0.0) acc += o * S[m][(size_t)u * p + j];
+                }
+                W[m][(size_t)i * p + j] = acc;
+            }
+    }
+    double worst = 0.0;
+    for (int i = 0; i < p; ++i) {
+        size_t ii = (size_t)i * p + i;
+        double d1 = Om1[ii], d2 = Om2[ii];
+        double r;
+        if (!(d1 > 0.0) || !(d2 > 0.0)) {
+            r = INFINITY;
+        } else {
+            double a = W[0][ii] - 1.0 / d1, b = W[1][ii] - 1.0 / d2;
+            double u;
+            if (d1 != d2)
+                u = d1 > d2 ? l2 : -l2;
+            else
+                u = MUTANT(14) ? 0.0 : clampd(0.5 * (b - a), -l2, l2);
+            double ra = fabs(a + u), rb = fabs(b - u);
+            r = ra > rb ? ra : rb;
+        }
+        if (r > worst) worst = r;
+        for (int j = i + 1; j < p; ++j) {
+            size_t ij = (size_t)i * p + j, ji = (size_t)j * p + i;
+            double x = Om1[ij], y = Om2[ij];
+            double g1 = W[0][ij] + W[0][ji], g2 = W[1][ij] + W[1][ji];
+            double v;
+            if (x != y) {
+                double u = x > y ? l2 : -l2;
+                double r1 = lasso_residual(g1 + u, x, l1), r2 = lasso_residual(g2 - u, y, l1);
+                v = r1 > r2 ? r1 : r2;
+            } else if (x != 0.0) {
+                double sg = x > 0.0 ? l1 : -l1;
+                double A = g1 + sg, B = g2 + sg;
+                double u = MUTANT(14) ? 0.0 : clampd(0.5 * (B - A), -l2, l2);
+                double ra = fabs(A + u), rb = fabs(B - u);
+                v = ra > rb ? ra : rb;
+            } else {
+                double u = MUTANT(14) ? 0.0 : clampd(0.5 * (g2 - g1), -l2, l2);
+                double ra = fabs(g1 + u), rb = fabs(g2 - u);
+                double m = (ra > rb ? ra : rb) - l1;
+                v = m > 0.0 ? m : 0.0;
+            }
+            if (v > worst) worst = v;
+        }
+    }
+    free(W[0]);
+    free(W[1]);
+    return worst;
+}
+
+/* Joint driver: joint sweeps until the joint KKT residual <= tol or
+ * max_sweeps.  stats / history as oracle_solve (history rows: delta, KKT,
+ * joint objective).  Om0_1 / Om0_2 may be NULL (identity).  Returns 0 if
+ * converged, 1 if not, < 0 on argument errors. */
+int oracle_joint_solve(const double *S1, const double *S2, int p, double l1,
+                       double l2, double tol, double delta_tol, int max_sweeps,
+                       const double *Om0_1, const double *Om0_2, double *Om1,
+                       double *Om2, double *stats, double *history)
+{
+    if (p < 2 || !(l1 >= 0.0) || !(l2 >= 0.0) || !(tol > 0.0) || max_sweeps < 0)
+        return OR_E_ARG;
+    for (int i = 0; i < p; ++i)
+        if (!(S1[(size_t)i * p + i] > 0.0) || !(S2[(size_t)i * p + i] > 0.0))
+            return OR_E_NONPOS_DIAG;
+    int pe = (p % 2 == 0) ? p : p + 1;
+    int32_t *pairs = (int32_t *)malloc(sizeof(int32_t) * (size_t)(pe - 1) * (pe / 2) * 2);
+    if (!pairs) return OR_E_ARG;
+    int nc = oracle_schedule(p, pairs);
+    const double *init[2] = {Om0_1, Om0_2};
+    double *Om[2] = {Om1, Om2};
+    for (int m = 0; m < 2; ++m) {
+        if (init[m])
+            memcpy(Om[m], init[m], sizeof(double) * (size_t)p * p);
+        else
+            for (int i = 0; i < p; ++i)
+                for (int j = 0; j < p; ++j) Om[m][(size_t)i * p + j] = (i == j) ? 1.0 : 0.0;
+    }
+    int t = 0, first_delta = 0, status = 1;
+    double delta = 0.0, kkt = oracle_joint_kkt(S1, S2, Om1, Om2, p, l1, l2);
+    long long nnz = 0;
+    while (t < max_sweeps) {
+        nnz = 0;
+        delta = oracle_joint_sweep(S1, S2, p, l1, l2, Om1, Om2, pairs, nc, &nnz);
+        ++t;
+        kkt = oracle_joint_kkt(S1, S2, Om1, Om2, p, l1, l2);
+        if (history) {
+            history[3 * (t - 1) + 0] = delta;
+            history[3 * (t - 1) + 1] = kkt;
+            history[3 * (t - 1) + 2] = oracle_joint_objective(S1, S2, Om1, Om2, p, l1, l2);
+        }
+        if (!first_delta && delta < delta_tol) first_delta = t;
+        if (kkt <= tol) {
+            status = 0;
+            break;
+        }
+    }
+    if (max_sweeps == 0 && kkt <= tol) status = 0;
+    stats[0] = t;
+    stats[1] = oracle_joint_objective(S1, S2, Om1, Om2, p, l1, l2);
     stats[2] = kkt;
     stats[3] = delta;
     stats[4] = first_delta;

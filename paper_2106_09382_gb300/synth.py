@@ -28,6 +28,9 @@ the sizes and value ranges follow the workloads this library is measured on):
                    magnitude floor 0.1).
     block_diag     `n_blocks` blocks, within-block edge probability, values
                    +-U[lo, hi], diagonal dominance margin.
+    joint_ar1      two related precision matrices for the joint estimator:
+                   one AR(1) band, extra edges shared by both, and extra
+                   edges of each population's own.
     power_law      Barabasi-Albert graph (m edges per new vertex), values
                    +-U[lo, hi], diagonal dominance margin; kept sparse (edge
                    lists) for large p, sampled by sample_sparse.
@@ -95,6 +98,48 @@ def ar1_extra(p: int, rho: float = 0.5, n_extra: int | None = None, lo: float = 
         Om[a, a] += abs(v)
         Om[b, b] += abs(v)
     return Om
+
+
+def _extra_edges(rng, p: int, count: int, taken: set) -> list:
+    """`count` distinct non-band pairs (a < b, b - a > 1) not in `taken`."""
+    out = []
+    while len(out) < count:
+        i, j = (int(v) for v in rng.integers(0, p, size=2))
+        a, b = min(i, j), max(i, j)
+        if b - a <= 1 or (a, b) in taken:
+            continue
+        taken.add((a, b))
+        out.append((a, b))
+    return out
+
+
+def joint_ar1(p: int, rho: float = 0.5, n_shared: int | None = None,
+              n_own: int | None = None, lo: float = 0.3, hi: float = 0.6, seed: int = 0):
+    """Two precision matrices (Om1, Om2) with a common AR(1) band (as
+    ar1_extra), n_shared extra edges present in both with the same value,
+    and n_own extra edges in each one alone; every extra edge adds |value| to
+    both endpoint diagonals (a PSD term), so both stay positive definite.
+    Defaults: n_shared = n_own = round(0.01 (p - 1))."""
+    rng = np.random.default_rng(seed)
+    if n_shared is None:
+        n_shared = int(round(0.01 * (p - 1)))
+    if n_own is None:
+        n_own = int(round(0.01 * (p - 1)))
+    base = ar1_extra(p, rho, 0, lo, hi, seed)
+    taken: set = set()
+    shared = _extra_edges(rng, p, n_shared, taken)
+    own = [_extra_edges(rng, p, n_own, taken) for _ in range(2)]
+    out = []
+    vs = _signed_uniform(rng, len(shared), lo, hi)
+    for m in range(2):
+        Om = base.copy()
+        vo = _signed_uniform(rng, len(own[m]), lo, hi)
+        for (a, b), v in list(zip(shared, vs)) + list(zip(own[m], vo)):
+            Om[a, b] = Om[b, a] = v
+            Om[a, a] += abs(v)
+            Om[b, b] += abs(v)
+        out.append(Om)
+    return out[0], out[1]
 
 
 def ar2(p: int) -> np.ndarray:
@@ -207,6 +252,14 @@ def subsamples(n: int, count: int = 64, lo: int = 200, hi: int = 800, seed: int 
     hi = min(hi, n)
     sizes = rng.integers(lo, hi + 1, size=count)
     return [np.sort(rng.choice(n, size=int(m), replace=False)) for m in sizes]
+
+
+def workload_joint(p: int = 1000, n: int = 500, seed: int = 0):
+    """Joint two-population workload: joint_ar1(p) with n samples drawn
+    independently from each population; lambda1 = 0.2, lambda2 = 0.05."""
+    Om1, Om2 = joint_ar1(p, seed=seed)
+    return {"Om0": (Om1, Om2), "X1": sample(Om1, n, seed), "X2": sample(Om2, n, seed + 11),
+            "p": p, "n": n, "lam1": 0.2, "lam2": 0.05, "tol": 1e-5}
 
 
 def workload_adjoint(p: int = 2000, n_train: int = 1000, n_val: int = 500, seed: int = 0):
