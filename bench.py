@@ -53,6 +53,8 @@ def parse_args(argv=None):
                     help="skip the large sparse solve (p = 20000) section")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the differentiable-solve (implicit adjoint) section")
+    ap.add_argument("--no-joint", action="store_true",
+                    help="skip the joint two-population section")
     ap.add_argument("--no-path", action="store_true",
                     help="skip the regularisation-path / stability-selection section")
     ap.add_argument("--no-autotune", action="store_true",
@@ -487,6 +489,93 @@ def run_adjoint_section(C, synth, dev, stream, steps=20, lr=0.003):
                               "cg_iterations": [int(v) for v in rows[:, 4]]}}
 
 
+def run_joint_section(C, synth, dev, stream, hbm_peak, reps=3):
+    """Joint two-population CONCORD (the extension closing Section 6) on the
+    joint AR(1) workload (p = 1000, n = 500 per population, lambda1 = 0.2,
+    lambda2 = 0.05, joint KKT <= 1e-5): mixed (FP32 sweeps + FP64 polish)
+    and FP64 solves from Omega = I, a few grid sizes of the persistent
+    launch, and the algorithmic bytes of the FP32 sweeps against HBM."""
+    import torch
+    w = synth.workload_joint()
+    p, n = w["p"], w["n"]
+    l1, l2, tol = w["lam1"], w["lam2"], w["tol"]
+    S = [C.concord_gram(torch.as_tensor(w[k], device=dev), C.PREP_STANDARDIZE, C.GRAM_FP64,
+                        stream=stream) for k in ("X1", "X2")]
+    eye = torch.eye(p, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    P = p + (p % 2) - 1
+    ld = (p + 31) // 32 * 32
+    out = {"workload": "joint AR(1): shared band + %d shared / %d own extra edges, p=%d, n=%d per "
+                       "population; lambda1=%g, lambda2=%g, joint KKT<=%g"
+                       % (round(0.01 * (p - 1)), round(0.01 * (p - 1)), p, n, l1, l2, tol)}
+    omegas = {}
+    for name, prec in (("mixed", C.MIXED), ("fp64", C.FP64)):
+        J = C.Joint(p, prec, device=dev.index)
+        J.set_stream(stream)
+        J.set_S(0, S[0])
+        J.set_S(1, S[1])
+        grids = {}
+        for g in ((0, 16, 32, 64, 152) if prec == C.MIXED else (0,)):
+            J.set_grid(g)
+            times = []
+            for _ in range(reps + 1):  # the first is a warm-up
+                J.set_omega(0, eye)
+                J.set_omega(1, eye)
+                r = J.run(l1, l2, tol=tol, max_sweeps=2000)
+                times.append(r.seconds)
+            grids[g] = (statistics.mean(times[1:]), r)
+        best_g = min(grids, key=lambda g: grids[g][0])
+        sec, r = grids[0]
+        hist = J.history()
+        rec = {"seconds": sec, "sweeps": r.sweeps, "sweeps_fp32": r.sweeps_fp32, "kkt": r.kkt,
+               "objective": r.objective, "status": r.status,
+               "ms_per_grid": {str(g): round(v[0] * 1e3, 4) for g, v in grids.items()},
+               "best_grid": best_g}
+        J.set_grid(0)
+        if prec == C.MIXED:
+            # algorithmic bytes of the FP32 sweeps (element b = 4): per colour
+            # step the ten scalars of each pair; per moved pair four W rows
+            # read + written and two S rows read; the diagonal step two W
+            # rows + one S row per population and row; the evaluation pass W
+            # and Omega of both populations
+            b = 4
+            moved = float(hist[: r.sweeps_fp32, 3].sum()) if r.sweeps_fp32 else 0.0
+            sweeps32 = max(r.sweeps_fp32, 1)
+            per_sweep_fixed = (P * ((P + 1) // 2) * 10 * b + 2 * p * 3 * ld * b
+                               + 2 * 2 * p * ld * b)
+            bytes32 = sweeps32 * per_sweep_fixed + moved * 2 * (4 * ld * b + 2 * ld * b)
+            # time of the FP32 phase alone: a run capped at the FP32 sweeps
+            J.set_omega(0, eye)
+            J.set_omega(1, eye)
+            r32 = J.sweep(l1, l2, r.sweeps_fp32)
+            rec["fp32_phase_ms"] = r32.seconds * 1e3
+            rec["ms_per_fp32_sweep"] = r32.seconds * 1e3 / sweeps32
+            rec["us_per_colour_step"] = r32.seconds * 1e6 / sweeps32 / P
+            rec["fp32_roofline"] = {"bound": "latency (one grid barrier per colour step)",
+                                    "algorithmic_bytes": bytes32,
+                                    "achieved_GBps": bytes32 / r32.seconds / 1e9,
+                                    "frac_of_hbm": bytes32 / r32.seconds / 1e9 / hbm_peak,
+                                    "pairs_moved": moved}
+            J.set_omega(0, eye)
+            J.set_omega(1, eye)
+            J.run(l1, l2, tol=tol, max_sweeps=2000)
+        O1 = J.get_omega(0).cpu().numpy()
+        O2 = J.get_omega(1).cpu().numpy()
+        omegas[name] = (O1, O2)
+        iu = np.triu_indices(p, 1)
+        a, b_ = O1[iu], O2[iu]
+        rec.update({"edges": [int(np.count_nonzero(a)), int(np.count_nonzero(b_))],
+                    "fused_edges": int(np.count_nonzero((a != 0) & (a == b_))),
+                    "differing_edges": int(np.count_nonzero(a != b_))})
+        out[name] = rec
+        J.close()
+    d = max(float(np.abs(omegas["mixed"][m] - omegas["fp64"][m]).max()) for m in (0, 1))
+    scale = max(float(np.abs(omegas["fp64"][m]).max()) for m in (0, 1))
+    out["mixed_vs_fp64"] = {"max_abs_dOmega_rel": d / scale,
+                            "speedup": out["fp64"]["seconds"] / out["mixed"]["seconds"]}
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -720,6 +809,8 @@ def run_ours(args):
             out["adjoint"] = run_adjoint_section(C, synth, dev, stream)
         if not args.no_large:
             out["large"] = run_large_section(C, synth, dev, stream, hbm_peak)
+        if not args.no_joint:
+            out["joint"] = run_joint_section(C, synth, dev, stream, hbm_peak)
         # ---------------- CPU oracle, bounded sample (rank 0 only)
         if rank == 0:
             gs, src = golden_sweeps(p)

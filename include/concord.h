@@ -561,6 +561,85 @@ int concord_tune_lambda(concord_state *st, const void *Sval_dev, int s_dtype, in
                         int steps, double lr, double tol, int max_sweeps, double cg_tol,
                         double *rows_host);
 
+/* ------------------------------------ joint two-population CONCORD */
+/*
+ * The extension that closes Section 6: two precision matrices Omega1, Omega2
+ * (one per population, Grams S1, S2 in S units) minimise
+ *
+ *   sum_m [ - sum_i log w^m_ii + 1/2 tr(Omega_m S_m Omega_m)
+ *           + lambda1 sum_{i<j} |w^m_ij| ]
+ *   + lambda2 sum_{i<=j} |w^1_ij - w^2_ij|
+ *
+ * (the joint objective divided by the common n; the fusion penalty covers
+ * the diagonal, as the joint objective writes it).  Block coordinate descent
+ * moves the pair (w^1_ij, w^2_ij) jointly in Algorithm 1's colour order --
+ * blocks of one colour touch disjoint rows, so they are independent as in
+ * Lemma 1 -- then the diagonal blocks (w^1_ii, w^2_ii).  Every block update
+ * has a closed form: with the sign of the difference fixed the block problem
+ * separates into two lasso problems (pairs) or two Eq. 2 roots (diagonal);
+ * when neither sign is consistent, the minimiser lies on w^1 = w^2.
+ *
+ * Joint KKT residual (absolute, S units; the stopping rule): with
+ * W_m = Omega_m S_m and, per pair, the smooth gradients G_m = W^m_ij + W^m_ji
+ * (diagonal: W^m_ii - 1/w^m_ii), the largest over blocks of
+ *   min over admissible u of max(dist(-(G_1 + u), lambda1 d|w^1|),
+ *                                dist(-(G_2 - u), lambda1 d|w^2|)),
+ * u = lambda2 sign(w^1 - w^2) where the two differ, u in [-lambda2, lambda2]
+ * where they are equal (no lasso term on the diagonal).  lambda2 = 0 gives
+ * the larger of the two populations' Eq. 1 residuals.
+ *
+ * Precision: CONCORD_FP64 runs FP64 sweeps; CONCORD_MIXED runs FP32 sweeps
+ * (FP64 block arithmetic) until the residual meets tol or stops falling,
+ * then FP64 sweeps from the promoted iterate (W rebuilt in FP64).
+ *
+ * One persistent cooperative launch per phase: one grid barrier per colour
+ * step, a fused KKT / objective pass after every sweep.
+ */
+typedef struct concord_joint concord_joint;
+
+/* Allocates the working set for dimension p on `device` (-1 = current): for
+ * each population S, W and Omega (p x round_up(p, 32)) in FP64, plus FP32
+ * copies under CONCORD_MIXED.  Errors: CONCORD_E_ARG (p < 2, precision),
+ * CONCORD_E_CUDA (no sm_103 device), CONCORD_E_NOMEM. */
+int concord_joint_create(concord_joint **out, int p, int precision, int device);
+int concord_joint_destroy(concord_joint *jt);   /* NULL is accepted */
+/* Stream for every later call (NULL = the state's own stream). */
+int concord_joint_set_stream(concord_joint *jt, void *stream);
+/* Limit of each device-side wait (default 2 s); see concord_set_timeout. */
+int concord_joint_set_timeout(concord_joint *jt, double seconds);
+/* CTAs of the persistent launch (0 = automatic: one warp per pair of a
+ * colour, at least 16 CTAs, at most one per SM). */
+int concord_joint_set_grid(concord_joint *jt, int ctas);
+
+/* Copies S of population m (0 or 1; p x p, element type s_dtype, row stride
+ * lds) into the state and resets Omega_m to I (W_m = S_m).  Synchronises.
+ * Errors: CONCORD_E_NONPOS_DIAG (s_ii <= 0 or S not symmetric),
+ * CONCORD_E_NONFINITE, CONCORD_E_ARG. */
+int concord_joint_set_S(concord_joint *jt, int m, const void *S_dev, int s_dtype, int lds);
+/* Warm start: Omega_m from a device buffer (symmetric, positive diagonal);
+ * W_m is rebuilt.  On a rejected Omega the state's Omega_m is reset to I. */
+int concord_joint_set_omega(concord_joint *jt, int m, const void *Om_dev, int dtype, int ld);
+/* Omega_m of the latest iterate into a device buffer (dtype, row stride ld). */
+int concord_joint_get_omega(concord_joint *jt, int m, void *Om_dev, int dtype, int ld);
+
+/* Exactly n_sweeps joint sweeps (FP32 under CONCORD_MIXED, FP64 otherwise),
+ * no stopping rule; res receives the residual and objective after them
+ * (res->lambda = lambda1).  n_sweeps = 0 only evaluates.
+ * Errors: CONCORD_E_ARG (S not set, lambdas < 0), CONCORD_E_NONFINITE,
+ * CONCORD_E_TIMEOUT, CONCORD_E_CUDA. */
+int concord_joint_sweep(concord_joint *jt, double lambda1, double lambda2, int n_sweeps,
+                        concord_result *res);
+/* Joint sweeps until the joint KKT residual <= tol or max_sweeps (mixed: FP32
+ * phase, then FP64 polish; res->sweeps_fp32 counts the FP32 sweeps).
+ * Returns CONCORD_OK or CONCORD_NOT_CONVERGED (outputs filled), or an error as
+ * concord_joint_sweep. */
+int concord_joint_run(concord_joint *jt, double lambda1, double lambda2, double tol,
+                      int max_sweeps, concord_result *res);
+/* Per-sweep rows (delta, KKT residual, objective, pairs moved) of the last
+ * concord_joint_sweep / _run call: min(max_rows, rows) rows into hist_host
+ * (4 doubles each); *rows receives the number recorded. */
+int concord_joint_get_history(concord_joint *jt, double *hist_host, int max_rows, int *rows);
+
 #ifdef __cplusplus
 }
 #endif

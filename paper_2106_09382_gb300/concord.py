@@ -8,7 +8,9 @@ the library cannot be built or loaded: there is no CPU fallback.
 Names follow the C entry points: ``concord_schedule``, ``concord_gram``,
 ``State`` (concord_create / _set_S / _set_omega / _sweep / _run /
 _solve_device / _solve_host / _get_omega / _get_W / _get_history /
-_lambda_max / _set_timeout / _set_fault / _destroy) and ``concord_solve``.
+_lambda_max / _set_timeout / _set_fault / _destroy), ``concord_solve`` and
+``Joint`` (the concord_joint_* entry points of the two-population joint
+estimator).
 """
 from __future__ import annotations
 
@@ -106,6 +108,17 @@ SIGNATURES = {
     "concord_adjoint": ([_vp, _vp, _ci, _ci, _cd, _ci, _vp, _ci, ctypes.POINTER(AdjointInfo)], _ci),
     "concord_adjoint_data": ([_vp, _vp, _ci, _ci, _ci, _ci, _vp, _ci, _ci], _ci),
     "concord_tune_lambda": ([_vp, _vp, _ci, _ci, _cd, _ci, _cd, _cd, _ci, _cd, _dp], _ci),
+    "concord_joint_create": ([ctypes.POINTER(_vp), _ci, _ci, _ci], _ci),
+    "concord_joint_destroy": ([_vp], _ci),
+    "concord_joint_set_stream": ([_vp, _vp], _ci),
+    "concord_joint_set_timeout": ([_vp, _cd], _ci),
+    "concord_joint_set_grid": ([_vp, _ci], _ci),
+    "concord_joint_set_S": ([_vp, _ci, _vp, _ci, _ci], _ci),
+    "concord_joint_set_omega": ([_vp, _ci, _vp, _ci, _ci], _ci),
+    "concord_joint_get_omega": ([_vp, _ci, _vp, _ci, _ci], _ci),
+    "concord_joint_sweep": ([_vp, _cd, _cd, _ci, _rp], _ci),
+    "concord_joint_run": ([_vp, _cd, _cd, _cd, _ci, _rp], _ci),
+    "concord_joint_get_history": ([_vp, _dp, _ci, _ip], _ci),
 }
 
 _lock = threading.Lock()
@@ -484,3 +497,92 @@ def concord_solve(data: np.ndarray, lam: float, tol: float = 1e-5, max_sweeps: i
                               Om.ctypes.data_as(_dp), ctypes.byref(r))
     _check(rc, (OK, NOT_CONVERGED))
     return Om, r
+
+
+# --------------------------------------------------------- joint estimator
+class Joint:
+    """Joint two-population CONCORD state (concord_joint_create): two
+    precision matrices with lasso weight lambda1 and fusion weight lambda2."""
+
+    def __init__(self, p: int, precision: int = FP64, device: int | None = None):
+        import torch
+        lib = load()
+        dev = torch.cuda.current_device() if device is None else int(device)
+        self._ptr = ctypes.c_void_p()
+        _check(lib.concord_joint_create(ctypes.byref(self._ptr), int(p), int(precision), dev))
+        self.p, self.precision, self.device = int(p), int(precision), dev
+        self.last = None
+
+    def close(self):
+        if getattr(self, "_ptr", None) and self._ptr.value:
+            load().concord_joint_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream=None):
+        _check(load().concord_joint_set_stream(self._ptr, _stream_ptr(stream)
+                                               if stream is not False else None))
+
+    def set_timeout(self, seconds: float):
+        _check(load().concord_joint_set_timeout(self._ptr, float(seconds)))
+
+    def set_grid(self, ctas: int):
+        _check(load().concord_joint_set_grid(self._ptr, int(ctas)))
+
+    def set_S(self, m: int, S):
+        assert S.is_cuda and S.dim() == 2 and S.stride(1) == 1
+        _check(load().concord_joint_set_S(self._ptr, int(m), S.data_ptr(), _dtype_code(S),
+                                          S.stride(0)))
+
+    def set_omega(self, m: int, Om):
+        assert Om.is_cuda and Om.dim() == 2 and Om.stride(1) == 1
+        _check(load().concord_joint_set_omega(self._ptr, int(m), Om.data_ptr(), _dtype_code(Om),
+                                              Om.stride(0)))
+
+    def get_omega(self, m: int, out=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.p, self.p), dtype=torch.float64,
+                              device="cuda:%d" % self.device)
+        assert out.is_cuda and out.stride(1) == 1
+        _check(load().concord_joint_get_omega(self._ptr, int(m), out.data_ptr(), _dtype_code(out),
+                                              out.stride(0)))
+        return out
+
+    def sweep(self, lam1: float, lam2: float, n_sweeps: int = 1) -> ConcordResult:
+        r = ConcordResult()
+        rc = load().concord_joint_sweep(self._ptr, float(lam1), float(lam2), int(n_sweeps),
+                                        ctypes.byref(r))
+        self.last = r
+        _check(rc, (OK, NOT_CONVERGED))
+        return r
+
+    def run(self, lam1: float, lam2: float, tol: float = 1e-5,
+            max_sweeps: int = 1000) -> ConcordResult:
+        r = ConcordResult()
+        rc = load().concord_joint_run(self._ptr, float(lam1), float(lam2), float(tol),
+                                      int(max_sweeps), ctypes.byref(r))
+        self.last = r
+        _check(rc, (OK, NOT_CONVERGED))
+        return r
+
+    def history(self) -> np.ndarray:
+        """(rows, 4): delta, KKT residual, objective, pairs moved per sweep."""
+        n = ctypes.c_int(0)
+        _check(load().concord_joint_get_history(self._ptr, None, 0, ctypes.byref(n)))
+        out = np.zeros((n.value, 4), dtype=np.float64)
+        if n.value:
+            _check(load().concord_joint_get_history(self._ptr, out.ctypes.data_as(_dp), n.value,
+                                                    ctypes.byref(n)))
+        return out

@@ -102,6 +102,8 @@ def ar1_extra(p: int, rho: float = 0.5, n_extra: int | None = None, lo: float = 
 
 def _extra_edges(rng, p: int, count: int, taken: set) -> list:
     """`count` distinct non-band pairs (a < b, b - a > 1) not in `taken`."""
+    if count > (p - 1) * (p - 2) // 2 - len(taken):
+        raise ValueError("p = %d has too few non-band pairs for %d more edges" % (p, count))
     out = []
     while len(out) < count:
         i, j = (int(v) for v in rng.integers(0, p, size=2))
