@@ -52,10 +52,19 @@ struct JVec<double> {
   }
 };
 
-__device__ __forceinline__ double jsoft(double x, double tau) {
-  const double a = fabs(x) - tau;
-  if (!(a > 0.0)) return 0.0;
-  return x > 0.0 ? a : -a;
+// The block arithmetic runs in the working precision T: FP32 for the FP32
+// sweeps (whose result the FP64 polish refines), FP64 for the FP64 sweeps.
+// FP64 issues at a small fraction of the FP32 rate on this part and every
+// colour step waits for its slowest block, so the block minimiser divides
+// only in the branch it takes: the sign test x > y of the separated
+// solutions is made on the numerators, cross-multiplied by the (positive)
+// denominators.
+
+template <typename T>
+__device__ __forceinline__ T jsoft(T x, T tau) {
+  const T a = fabs(x) - tau;
+  if (!(a > (T)0)) return (T)0;
+  return x > (T)0 ? a : -a;
 }
 
 // Minimiser of the block problem
@@ -63,85 +72,91 @@ __device__ __forceinline__ double jsoft(double x, double tau) {
 // With the sign of x - y fixed, the problem separates into two lasso
 // problems whose solutions are the minimiser when they agree with that sign;
 // if neither sign is consistent, the minimiser lies on x = y.
-__device__ __forceinline__ void block_pair(double c1, double g1, double c2, double g2, double l1,
-                                           double l2, double& x, double& y) {
-  const double xa = jsoft(-(g1 + l2), l1) / c1, ya = jsoft(-(g2 - l2), l1) / c2;
-  if (xa > ya) {
-    x = xa;
-    y = ya;
+template <typename T>
+__device__ __forceinline__ void block_pair(T c1, T g1, T c2, T g2, T l1, T l2, T& x, T& y) {
+  const T na = jsoft<T>(-(g1 + l2), l1), nb = jsoft<T>(-(g2 - l2), l1);
+  if (na * c2 > nb * c1) {  // na / c1 > nb / c2
+    x = na / c1;
+    y = nb / c2;
     return;
   }
-  const double xb = jsoft(-(g1 - l2), l1) / c1, yb = jsoft(-(g2 + l2), l1) / c2;
-  if (xb < yb) {
-    x = xb;
-    y = yb;
+  const T nc = jsoft<T>(-(g1 - l2), l1), nd = jsoft<T>(-(g2 + l2), l1);
+  if (nc * c2 < nd * c1) {  // nc / c1 < nd / c2
+    x = nc / c1;
+    y = nd / c2;
     return;
   }
-  x = y = jsoft(-(g1 + g2), 2.0 * l1) / (c1 + c2);
+  const T nt = jsoft<T>(-(g1 + g2), (T)2 * l1);
+  x = y = (nt == (T)0) ? (T)0 : nt / (c1 + c2);
 }
 
 // Positive root of s d^2 + b d - 1 = 0 (the stationarity condition of Eq. 2).
-__device__ __forceinline__ double pos_root(double s, double b) {
-  return (-b + sqrt(b * b + 4.0 * s)) / (2.0 * s);
+template <typename T>
+__device__ __forceinline__ T pos_root(T s, T b) {
+  return (-b + sqrt(b * b + (T)4 * s)) / ((T)2 * s);
 }
 
 // Minimiser over d1, d2 > 0 of
 //   -log d1 + s1 d1^2 / 2 + b1 d1 - log d2 + s2 d2^2 / 2 + b2 d2 + l2 |d1 - d2|
 // by the same three cases; the fused root solves (s1 + s2) d^2 + (b1 + b2) d = 2.
-__device__ __forceinline__ void block_diag(double s1, double b1, double s2, double b2, double l2,
-                                           double& d1, double& d2) {
-  const double ua = pos_root(s1, b1 + l2), va = pos_root(s2, b2 - l2);
+template <typename T>
+__device__ __forceinline__ void block_diag(T s1, T b1, T s2, T b2, T l2, T& d1, T& d2) {
+  const T ua = pos_root<T>(s1, b1 + l2), va = pos_root<T>(s2, b2 - l2);
   if (ua > va) {
     d1 = ua;
     d2 = va;
     return;
   }
-  const double ub = pos_root(s1, b1 - l2), vb = pos_root(s2, b2 + l2);
+  const T ub = pos_root<T>(s1, b1 - l2), vb = pos_root<T>(s2, b2 + l2);
   if (ub < vb) {
     d1 = ub;
     d2 = vb;
     return;
   }
-  const double ss = s1 + s2, bb = b1 + b2;
-  d1 = d2 = (-bb + sqrt(bb * bb + 8.0 * ss)) / (2.0 * ss);
+  const T ss = s1 + s2, bb = b1 + b2;
+  d1 = d2 = (-bb + sqrt(bb * bb + (T)8 * ss)) / ((T)2 * ss);
 }
 
 // max that propagates NaN (fmax would drop it).
-__device__ __forceinline__ double nmax(double a, double b) { return (a != a || a > b) ? a : b; }
+template <typename T>
+__device__ __forceinline__ T nmax(T a, T b) { return (a != a || a > b) ? a : b; }
 
-__device__ __forceinline__ double clampd(double v, double l) { return fmin(fmax(v, -l), l); }
+template <typename T>
+__device__ __forceinline__ T clampt(T v, T l) { return fmin(fmax(v, -l), l); }
 
-__device__ __forceinline__ double lasso_res(double g, double x, double l1) {
-  if (x > 0.0) return fabs(g + l1);
-  if (x < 0.0) return fabs(g - l1);
-  return fmax(fabs(g) - l1, 0.0);
+template <typename T>
+__device__ __forceinline__ T lasso_res(T g, T x, T l1) {
+  if (x > (T)0) return fabs(g + l1);
+  if (x < (T)0) return fabs(g - l1);
+  return fmax(fabs(g) - l1, (T)0);
 }
 
 // Joint KKT residual of one pair block (smooth gradients g1, g2): the
 // smallest, over the admissible fusion subgradient u = l2 z, of the larger of
 // the two lasso residuals.  For x = y the larger residual is convex in u and
 // smallest at the midpoint of the two gradients, clamped to [-l2, l2].
-__device__ __forceinline__ double pair_kkt(double g1, double g2, double x, double y, double l1,
-                                           double l2) {
+template <typename T>
+__device__ __forceinline__ T pair_kkt(T g1, T g2, T x, T y, T l1, T l2) {
   if (x != y) {
-    const double u = x > y ? l2 : -l2;
-    return nmax(lasso_res(g1 + u, x, l1), lasso_res(g2 - u, y, l1));
+    const T u = x > y ? l2 : -l2;
+    return nmax<T>(lasso_res<T>(g1 + u, x, l1), lasso_res<T>(g2 - u, y, l1));
   }
-  if (x != 0.0) {
-    const double sg = x > 0.0 ? l1 : -l1;
-    const double A = g1 + sg, B = g2 + sg;
-    const double u = clampd(0.5 * (B - A), l2);
-    return nmax(fabs(A + u), fabs(B - u));
+  if (x != (T)0) {
+    const T sg = x > (T)0 ? l1 : -l1;
+    const T A = g1 + sg, B = g2 + sg;
+    const T u = clampt<T>((T)0.5 * (B - A), l2);
+    return nmax<T>(fabs(A + u), fabs(B - u));
   }
-  const double u = clampd(0.5 * (g2 - g1), l2);
-  const double m = nmax(fabs(g1 + u), fabs(g2 - u)) - l1;
-  return m != m ? m : fmax(m, 0.0);
+  const T u = clampt<T>((T)0.5 * (g2 - g1), l2);
+  const T m = nmax<T>(fabs(g1 + u), fabs(g2 - u)) - l1;
+  return m != m ? m : fmax(m, (T)0);
 }
 
 // Diagonal block: a = W1_ii - 1/d1, b = W2_ii - 1/d2, no lasso term.
-__device__ __forceinline__ double diag_kkt(double a, double b, double d1, double d2, double l2) {
-  const double u = (d1 != d2) ? (d1 > d2 ? l2 : -l2) : clampd(0.5 * (b - a), l2);
-  return nmax(fabs(a + u), fabs(b - u));
+template <typename T>
+__device__ __forceinline__ T diag_kkt(T a, T b, T d1, T d2, T l2) {
+  const T u = (d1 != d2) ? (d1 > d2 ? l2 : -l2) : clampt<T>((T)0.5 * (b - a), l2);
+  return nmax<T>(fabs(a + u), fabs(b - u));
 }
 
 // The pair of slot q of colour c (Algorithm 1's rotation in closed form):
@@ -206,6 +221,7 @@ __global__ void __launch_bounds__(kJointThreads, 1) k_joint(const JointArgs<T> a
   const int half = (P + 1) / 2;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const double l1 = a.lambda1, l2 = a.lambda2;
+  const T l1t = (T)l1, l2t = (T)l2;
 
   __shared__ int s_i[kJointWarps], s_j[kJointWarps];
   __shared__ T s_d[kJointWarps][2];
@@ -223,7 +239,8 @@ __global__ void __launch_bounds__(kJointThreads, 1) k_joint(const JointArgs<T> a
   for (;;) {
     const bool initial = evals == 0 && a.eval_first;
     const bool swept = !initial && t < a.n_sweeps;
-    double dmax = 0.0, moved = 0.0;  // lane-0 / thread-local contributions
+    T dmax = (T)0;  // lane-0 / thread-local contributions, kept in T (FP64 is slow here)
+    int moved = 0;
     if (swept) {
       // ---- colour steps
       for (int c = 0; c < P; ++c) {
@@ -256,12 +273,11 @@ __global__ void __launch_bounds__(kJointThreads, 1) k_joint(const JointArgs<T> a
             const T s2i = __shfl_sync(kFull, v, 8), s2j = __shfl_sync(kFull, v, 9);
             // smooth gradient without the pair's own quadratic term (the two
             // direct sums of Eq. 3): W_ij + W_ji - (s_ii + s_jj) w_ij
-            const double c1 = (double)s1i + (double)s1j, c2 = (double)s2i + (double)s2j;
-            const double g1 = ((double)w1ij + (double)w1ji) - c1 * (double)o1;
-            const double g2 = ((double)w2ij + (double)w2ji) - c2 * (double)o2;
-            double x, y;
-            block_pair(c1, g1, c2, g2, l1, l2, x, y);
-            const T xn = (T)x, yn = (T)y;
+            const T c1 = s1i + s1j, c2 = s2i + s2j;
+            const T g1 = (w1ij + w1ji) - c1 * o1;
+            const T g2 = (w2ij + w2ji) - c2 * o2;
+            T xn, yn;
+            block_pair<T>(c1, g1, c2, g2, l1t, l2t, xn, yn);
             d0 = xn - o1;
             d1 = yn - o2;
             if (lane == 0) {
@@ -273,8 +289,8 @@ __global__ void __launch_bounds__(kJointThreads, 1) k_joint(const JointArgs<T> a
                 a.Om[1][ij] = yn;
                 a.Om[1][ji] = yn;
               }
-              dmax = nmax(dmax, nmax(fabs((double)d0), fabs((double)d1)));
-              if (d0 != (T)0 || d1 != (T)0) moved += 1.0;
+              dmax = nmax<T>(dmax, nmax<T>(fabs(d0), fabs(d1)));
+              if (d0 != (T)0 || d1 != (T)0) ++moved;
             }
           }
           if (lane == 0) {
@@ -318,16 +334,15 @@ __global__ void __launch_bounds__(kJointThreads, 1) k_joint(const JointArgs<T> a
         const T o1 = __shfl_sync(kFull, v, 2), o2 = __shfl_sync(kFull, v, 3);
         const T s1 = __shfl_sync(kFull, v, 4), s2 = __shfl_sync(kFull, v, 5);
         // the direct sum of Eq. 2: W_ii - w_ii s_ii
-        const double b1 = (double)w1 - (double)o1 * (double)s1;
-        const double b2 = (double)w2 - (double)o2 * (double)s2;
-        double e1, e2;
-        block_diag((double)s1, b1, (double)s2, b2, l2, e1, e2);
-        const T n1 = (T)e1, n2 = (T)e2;
+        const T b1 = w1 - o1 * s1;
+        const T b2 = w2 - o2 * s2;
+        T n1, n2;
+        block_diag<T>(s1, b1, s2, b2, l2t, n1, n2);
         const T d0 = n1 - o1, d1 = n2 - o2;
         if (lane == 0) {
           if (d0 != (T)0) a.Om[0][ii] = n1;
           if (d1 != (T)0) a.Om[1][ii] = n2;
-          dmax = nmax(dmax, nmax(fabs((double)d0), fabs((double)d1)));
+          dmax = nmax<T>(dmax, nmax<T>(fabs(d0), fabs(d1)));
         }
         if (d0 != (T)0) warp_axpy<T>(a.W[0] + (size_t)i * ld, a.S[0] + (size_t)i * ld, d0, ld, lane);
         if (d1 != (T)0) warp_axpy<T>(a.W[1] + (size_t)i * ld, a.S[1] + (size_t)i * ld, d1, ld, lane);
@@ -336,7 +351,8 @@ __global__ void __launch_bounds__(kJointThreads, 1) k_joint(const JointArgs<T> a
     }
 
     // ---- fused KKT / objective pass over the upper-triangle tiles
-    double kk = 0.0, quad = 0.0, logs = 0.0, pen = 0.0, fuse = 0.0;
+    // per-thread partials in T (a few dozen terms each), combined in FP64
+    T kk = (T)0, quad = (T)0, logs = (T)0, pen = (T)0, fuse = (T)0;
     const int nt = (p + 31) / 32;
     for (int k = blockIdx.x; k < nt * nt; k += gridDim.x) {
       const int bi = k / nt, bj = k % nt;
@@ -353,17 +369,17 @@ __global__ void __launch_bounds__(kJointThreads, 1) k_joint(const JointArgs<T> a
         const int i = 32 * bi + ty, j = 32 * bj + tx;
         if (i >= p || j >= p || i > j) continue;
         const size_t ij = (size_t)i * ld + j;
-        const double x = (double)a.Om[0][ij], y = (double)a.Om[1][ij];
-        const double wa = (double)a.W[0][ij], wb = (double)a.W[1][ij];
+        const T x = a.Om[0][ij], y = a.Om[1][ij];
+        const T wa = a.W[0][ij], wb = a.W[1][ij];
         if (i == j) {
-          const double ga = wa - 1.0 / x, gb = wb - 1.0 / y;
-          kk = nmax(kk, diag_kkt(ga, gb, x, y, l2));
+          const T ga = wa - (T)1 / x, gb = wb - (T)1 / y;
+          kk = nmax<T>(kk, diag_kkt<T>(ga, gb, x, y, l2t));
           quad += x * wa + y * wb;
           logs += log(x) + log(y);
           fuse += fabs(x - y);
         } else {
-          const double g1 = wa + (double)wt[0][ty][tx], g2 = wb + (double)wt[1][ty][tx];
-          kk = nmax(kk, pair_kkt(g1, g2, x, y, l1, l2));
+          const T g1 = wa + wt[0][ty][tx], g2 = wb + wt[1][ty][tx];
+          kk = nmax<T>(kk, pair_kkt<T>(g1, g2, x, y, l1t, l2t));
           quad += x * g1 + y * g2;
           pen += fabs(x) + fabs(y);
           fuse += fabs(x - y);
@@ -373,14 +389,15 @@ __global__ void __launch_bounds__(kJointThreads, 1) k_joint(const JointArgs<T> a
     }
     // block reduction of the partials
     {
-      double v[kJParts] = {kk, quad, logs, pen, fuse, dmax, moved, 0.0};
+      double v[kJParts] = {(double)kk, (double)quad, (double)logs, (double)pen, (double)fuse,
+                           (double)dmax, (double)moved, 0.0};
 #pragma unroll
       for (int q = 0; q < kJParts; ++q) {
         double x = v[q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           const double y = __shfl_down_sync(kFull, x, o);
-          x = (q == kJPartKkt || q == kJPartDelta) ? nmax(x, y) : x + y;
+          x = (q == kJPartKkt || q == kJPartDelta) ? nmax<double>(x, y) : x + y;
         }
         if (lane == 0) red[wid][q] = x;
       }
@@ -389,7 +406,7 @@ __global__ void __launch_bounds__(kJointThreads, 1) k_joint(const JointArgs<T> a
         const int q = threadIdx.x;
         double x = red[0][q];
         for (int w = 1; w < kJointWarps; ++w)
-          x = (q == kJPartKkt || q == kJPartDelta) ? nmax(x, red[w][q]) : x + red[w][q];
+          x = (q == kJPartKkt || q == kJPartDelta) ? nmax<double>(x, red[w][q]) : x + red[w][q];
         a.partials[((size_t)(evals & 1) * gridDim.x + blockIdx.x) * kJParts + q] = x;
       }
     }
@@ -403,12 +420,12 @@ __global__ void __launch_bounds__(kJointThreads, 1) k_joint(const JointArgs<T> a
         double x = 0.0;
         for (int b = lane; b < (int)gridDim.x; b += 32) {
           const double y = part[(size_t)b * kJParts + q];
-          x = mx ? nmax(x, y) : x + y;
+          x = mx ? nmax<double>(x, y) : x + y;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           const double y = __shfl_xor_sync(kFull, x, o);
-          x = mx ? nmax(x, y) : x + y;
+          x = mx ? nmax<double>(x, y) : x + y;
         }
         if (lane == 0) s_tot[q] = x;
       }
