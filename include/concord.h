@@ -592,8 +592,9 @@ int concord_tune_lambda(concord_state *st, const void *Sval_dev, int s_dtype, in
  * (FP64 block arithmetic) until the residual meets tol or stops falling,
  * then FP64 sweeps from the promoted iterate (W rebuilt in FP64).
  *
- * One persistent cooperative launch per phase: one grid barrier per colour
- * step, a fused KKT / objective pass after every sweep.
+ * One persistent cooperative launch per phase: colour steps synchronised by
+ * per-row version flags (or one grid barrier per colour step), a fused
+ * KKT / objective pass after every sweep.
  */
 typedef struct concord_joint concord_joint;
 
@@ -610,6 +611,12 @@ int concord_joint_set_timeout(concord_joint *jt, double seconds);
 /* CTAs of the persistent launch (0 = automatic: one warp per pair of a
  * colour, at least 16 CTAs, at most one per SM). */
 int concord_joint_set_grid(concord_joint *jt, int ctas);
+/* Synchronisation between colour steps (same iterates either way). */
+#define CONCORD_JOINT_ROWFLAGS 0  /* default: a pair waits only for its two rows'
+                                     previous-colour updates (per-row version
+                                     flags, release / acquire) */
+#define CONCORD_JOINT_BARRIER 1   /* one grid-wide barrier per colour step */
+int concord_joint_set_variant(concord_joint *jt, int variant);
 
 /* Copies S of population m (0 or 1; p x p, element type s_dtype, row stride
  * lds) into the state and resets Omega_m to I (W_m = S_m).  Synchronises.

@@ -28,6 +28,7 @@ PREP_NONE, PREP_CENTER, PREP_STANDARDIZE = 0, 1, 2
 GRAM_FP64, GRAM_FP32, GRAM_TF32X3, GRAM_BF16X3 = 0, 1, 2, 3
 STOP_KKT, STOP_DELTA = 0, 1
 SWEEP_AUTO, SWEEP_GRID, SWEEP_CLUSTER, SWEEP_SCREENED, SWEEP_DENSE = 0, 1, 2, 3, 4
+JOINT_ROWFLAGS, JOINT_BARRIER = 0, 1
 
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", -1: "E_ARG", -2: "E_NONPOS_DIAG",
                 -3: "E_NONFINITE", -4: "E_CUDA", -5: "E_TIMEOUT", -6: "E_NOMEM",
@@ -113,6 +114,7 @@ SIGNATURES = {
     "concord_joint_set_stream": ([_vp, _vp], _ci),
     "concord_joint_set_timeout": ([_vp, _cd], _ci),
     "concord_joint_set_grid": ([_vp, _ci], _ci),
+    "concord_joint_set_variant": ([_vp, _ci], _ci),
     "concord_joint_set_S": ([_vp, _ci, _vp, _ci, _ci], _ci),
     "concord_joint_set_omega": ([_vp, _ci, _vp, _ci, _ci], _ci),
     "concord_joint_get_omega": ([_vp, _ci, _vp, _ci, _ci], _ci),
@@ -539,6 +541,9 @@ class Joint:
 
     def set_grid(self, ctas: int):
         _check(load().concord_joint_set_grid(self._ptr, int(ctas)))
+
+    def set_variant(self, variant: int):
+        _check(load().concord_joint_set_variant(self._ptr, int(variant)))
 
     def set_S(self, m: int, S):
         assert S.is_cuda and S.dim() == 2 and S.stride(1) == 1

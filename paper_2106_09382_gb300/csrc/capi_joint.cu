@@ -48,6 +48,8 @@ struct concord_joint {
   bool have_S[2] = {false, false};
   bool f32_current = false;  // the latest iterate lives in the FP32 arrays
   unsigned* barrier = nullptr;
+  unsigned* row_ver = nullptr;  // [p] row versions of the dataflow colour loop
+  int variant = CONCORD_JOINT_ROWFLAGS;
   int* abort_info = nullptr;  // [0] abort word, [1] vertex, [2] step
   int* bad = nullptr;
   double* scratch = nullptr;  // p doubles (diagonal checks)
@@ -76,8 +78,8 @@ int default_grid(const concord_joint* jt) {
 void free_all(concord_joint* jt) {
   void* dev[] = {jt->S64[0], jt->S64[1], jt->W64[0], jt->W64[1], jt->Om64[0], jt->Om64[1],
                  jt->S32[0], jt->S32[1], jt->W32[0], jt->W32[1], jt->Om32[0], jt->Om32[1],
-                 jt->barrier,  jt->abort_info, jt->bad, jt->scratch, jt->partials, jt->hist,
-                 jt->result};
+                 jt->barrier,  jt->row_ver,    jt->abort_info, jt->bad, jt->scratch, jt->partials,
+                 jt->hist,     jt->result};
   for (void* d : dev)
     if (d) cudaFree(d);
   if (jt->h_result) cudaFreeHost(jt->h_result);
@@ -124,7 +126,11 @@ int run_phase(concord_joint* jt, bool f32, double l1, double l2, double tol, int
   JCK(joint_occupancy(f32, &bps));
   if (bps < 1 || grid > bps * jt->sms)
     return jfail(CONCORD_E_OCCUPANCY, "joint sweep: %d CTAs cannot be co-resident", grid);
+  if ((long long)n_sweeps * jt->P >= (1ll << 31))
+    return jfail(CONCORD_E_ARG, "n_sweeps x colours must stay below 2^31 per launch");
   JCK(cudaMemsetAsync(jt->barrier, 0, sizeof(unsigned), jt->stream));
+  unsigned* rv = jt->variant == CONCORD_JOINT_ROWFLAGS ? jt->row_ver : nullptr;
+  if (rv) JCK(cudaMemsetAsync(rv, 0, sizeof(unsigned) * jt->p, jt->stream));
   JCK(cudaMemsetAsync(jt->abort_info, 0, 3 * sizeof(int), jt->stream));
   WaitCtl w;
   w.abort = jt->abort_info;
@@ -149,6 +155,7 @@ int run_phase(concord_joint* jt, bool f32, double l1, double l2, double tol, int
     a.stall_stop = stall_stop ? 1 : 0;
     a.eval_first = eval_first ? 1 : 0;
     a.barrier = jt->barrier;
+    a.row_ver = rv;
     a.wait = w;
     a.partials = jt->partials;
     a.hist = jt->hist + (size_t)jt->hist_rows * kJHist;
@@ -173,6 +180,7 @@ int run_phase(concord_joint* jt, bool f32, double l1, double l2, double tol, int
     a.stall_stop = stall_stop ? 1 : 0;
     a.eval_first = eval_first ? 1 : 0;
     a.barrier = jt->barrier;
+    a.row_ver = rv;
     a.wait = w;
     a.partials = jt->partials;
     a.hist = jt->hist + (size_t)jt->hist_rows * kJHist;
@@ -298,6 +306,7 @@ int concord_joint_create(concord_joint** out, int p, int precision, int device) 
       }
     }
     JALLOC(jt->barrier, sizeof(unsigned));
+    JALLOC(jt->row_ver, sizeof(unsigned) * p);
     JALLOC(jt->abort_info, 3 * sizeof(int));
     JALLOC(jt->bad, sizeof(int));
     JALLOC(jt->scratch, sizeof(double) * p);
@@ -342,6 +351,14 @@ int concord_joint_set_timeout(concord_joint* jt, double seconds) {
   if (!(seconds > 0.0) || seconds > 3600.0)
     return jfail(CONCORD_E_ARG, "timeout must be in (0, 3600] s");
   jt->timeout_s = seconds;
+  return CONCORD_OK;
+}
+
+int concord_joint_set_variant(concord_joint* jt, int variant) {
+  if (!jt) return jfail(CONCORD_E_ARG, "joint state is NULL");
+  if (variant != CONCORD_JOINT_ROWFLAGS && variant != CONCORD_JOINT_BARRIER)
+    return jfail(CONCORD_E_ARG, "variant must be CONCORD_JOINT_ROWFLAGS or CONCORD_JOINT_BARRIER");
+  jt->variant = variant;
   return CONCORD_OK;
 }
 

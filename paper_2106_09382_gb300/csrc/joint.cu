@@ -163,8 +163,10 @@ __device__ __forceinline__ T diag_kkt(T a, T b, T d1, T d2, T l2) {
 // vertex 0 stays put and meets the vertex at ring index P - 1; ring indices
 // r and P - 2 - r face each other; during colour c the vertex at ring index r
 // is ((r - c) mod P) + 1.  Returns (i, j) with i < j, or i = -1 for the bye
-// of an odd p (the pair that holds vertex p).
-__device__ __forceinline__ void slot_pair(int q, int c, int P, int p, int& i, int& j) {
+// of an odd p (the pair that holds vertex p); (ra, rb) are the slot's two
+// vertices as they are (one of them is p for a bye).
+__device__ __forceinline__ void slot_pair(int q, int c, int P, int p, int& i, int& j, int& ra,
+                                          int& rb) {
   int a, b;
   if (q == 0) {
     a = 0;
@@ -174,9 +176,40 @@ __device__ __forceinline__ void slot_pair(int q, int c, int P, int p, int& i, in
     a = ((r - c) % P + P) % P + 1;
     b = ((P - 2 - r - c) % P + P) % P + 1;
   }
+  ra = a;
+  rb = b;
   i = min(a, b);
   j = max(a, b);
   if (j >= p) i = -1;
+}
+
+// Row versions (dataflow between colour steps).  A row's version is the
+// number of colour steps of this launch whose update of that row is complete
+// and visible.  The pair of colour c of sweep t reads rows i and j only after
+// both carry version t P + c; after its own update the CTA publishes
+// t P + c + 1 for them (release after the CTA-wide barrier, so the writes of
+// every thread of the CTA are covered).  Each vertex sits in exactly one slot
+// of every colour (byes included), so every row is published every colour;
+// waits only ever point to earlier colours, so the earliest CTA can always
+// proceed.  Waits are bounded like every other wait of this library.
+__device__ __forceinline__ void jst_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void wait_version(const unsigned* f, unsigned v, const WaitCtl& w,
+                                             int row, int step) {
+  if (ld_acquire_u32(f) >= v) return;
+  const uint64_t t0 = globaltimer_ns();
+  unsigned it = 0;
+  while (ld_acquire_u32(f) < v) {
+    if ((++it & 15u) == 0) {
+      if (ld_relaxed_s32(w.abort) != 0) return;
+      if (globaltimer_ns() - t0 > w.timeout_ns) {
+        record_timeout(w, row, step);
+        return;
+      }
+    }
+  }
 }
 
 template <typename T>
@@ -192,7 +225,7 @@ __device__ __forceinline__ void cta_axpy2(T* __restrict__ wi, T* __restrict__ wj
   const V* sjv = reinterpret_cast<const V*>(sj);
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
     const V a = __ldg(sjv + v), b = __ldg(siv + v);
-    V x = wiv[v], y = wjv[v];
+    V x = __ldcg(wiv + v), y = __ldcg(wjv + v);
     VT::fma(x, d, a);
     VT::fma(y, d, b);
     wiv[v] = x;
@@ -246,20 +279,26 @@ __global__ void __launch_bounds__(kJointThreads, 1) k_joint(const JointArgs<T> a
       for (int c = 0; c < P; ++c) {
         for (int base = blockIdx.x * kJointWarps; base < half; base += gridDim.x * kJointWarps) {
           const int q = base + wid;
-          int i = -1, j = -1;
-          if (q < half) slot_pair(q, c, P, p, i, j);
+          int i = -1, j = -1, ra = p, rb = p;
+          if (q < half) slot_pair(q, c, P, p, i, j, ra, rb);
+          const unsigned vin = (unsigned)(t * P + c);
+          if (a.row_ver != nullptr && q < half) {
+            const int r = lane == 0 ? ra : rb;
+            if (lane < 2 && r < p) wait_version(a.row_ver + r, vin, a.wait, r, c);
+            __syncwarp();
+          }
           T d0 = (T)0, d1 = (T)0;
           if (i >= 0) {
             const size_t ij = (size_t)i * ld + j, ji = (size_t)j * ld + i;
             const size_t ii = (size_t)i * ld + i, jj = (size_t)j * ld + j;
             T v = (T)0;
             switch (lane) {
-              case 0: v = a.W[0][ij]; break;
-              case 1: v = a.W[0][ji]; break;
-              case 2: v = a.W[1][ij]; break;
-              case 3: v = a.W[1][ji]; break;
-              case 4: v = a.Om[0][ij]; break;
-              case 5: v = a.Om[1][ij]; break;
+              case 0: v = __ldcg(a.W[0] + ij); break;
+              case 1: v = __ldcg(a.W[0] + ji); break;
+              case 2: v = __ldcg(a.W[1] + ij); break;
+              case 3: v = __ldcg(a.W[1] + ji); break;
+              case 4: v = __ldcg(a.Om[0] + ij); break;
+              case 5: v = __ldcg(a.Om[1] + ij); break;
               case 6: v = __ldg(a.S[0] + ii); break;
               case 7: v = __ldg(a.S[0] + jj); break;
               case 8: v = __ldg(a.S[1] + ii); break;
@@ -313,9 +352,14 @@ __global__ void __launch_bounds__(kJointThreads, 1) k_joint(const JointArgs<T> a
             }
           }
           __syncthreads();
+          if (a.row_ver != nullptr && lane == 0 && q < half) {
+            if (ra < p) jst_release_u32(a.row_ver + ra, vin + 1u);
+            if (rb < p) jst_release_u32(a.row_ver + rb, vin + 1u);
+          }
         }
-        grid_barrier(a.barrier, gen, a.wait, c);
+        if (a.row_ver == nullptr) grid_barrier(a.barrier, gen, a.wait, c);
       }
+      if (a.row_ver != nullptr) grid_barrier(a.barrier, gen, a.wait, P - 1);
       // ---- diagonal blocks, one warp per row
       const int tw = gridDim.x * kJointWarps;
       for (int i = blockIdx.x * kJointWarps + wid; i < p; i += tw) {

@@ -41,6 +41,8 @@ struct JointArgs {
   int stall_stop;            // end the launch when the residual stalls (kJStallSweeps)
   int eval_first;            // measure the starting point first (no sweep if it meets tol)
   unsigned* barrier;         // zeroed before the launch
+  unsigned* row_ver;         // [p] row versions, zeroed before the launch; nullptr: one grid
+                             // barrier per colour step instead
   WaitCtl wait;
   double* partials;          // 2 x gridDim.x x kJParts (double-buffered by sweep parity)
   double* hist;              // hist_len x kJHist

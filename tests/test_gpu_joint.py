@@ -151,16 +151,28 @@ def test_identical_populations_equal_the_single_estimate():
     assert np.abs(G1 - B).max() <= 1e-6 * np.abs(B).max()
 
 
-def test_omega_is_bitwise_independent_of_the_grid():
-    p, n = 150, 300
+@pytest.mark.parametrize("p", [150, 151])
+def test_omega_is_bitwise_independent_of_grid_and_synchronisation(p):
+    """Row-version dataflow and one grid barrier per colour, on 1, 7 and the
+    automatic number of CTAs: every W row receives the same updates in the
+    same order, so the iterates agree bit for bit (and with the oracle)."""
+    n = 300
     S1, S2 = grams(p, n, 51)
     outs = []
-    for grid in (1, 7, 0):
-        J = joint_state(S1, S2, grid=grid)
-        J.sweep(0.1, 0.03, 4)
-        outs.append((host(J.get_omega(0)), host(J.get_omega(1))))
+    for variant in (C.JOINT_ROWFLAGS, C.JOINT_BARRIER):
+        for grid in (1, 7, 0):
+            J = joint_state(S1, S2, grid=grid)
+            J.set_variant(variant)
+            J.sweep(0.1, 0.03, 4)
+            outs.append((host(J.get_omega(0)), host(J.get_omega(1))))
     for G1, G2 in outs[1:]:
         assert np.array_equal(G1, outs[0][0]) and np.array_equal(G2, outs[0][1])
+    A1, A2 = np.eye(p), np.eye(p)
+    for _ in range(4):
+        O.joint_sweep(S1, S2, A1, A2, 0.1, 0.03)
+    scale = max(np.abs(A1).max(), np.abs(A2).max())
+    assert np.abs(outs[0][0] - A1).max() <= 1e-10 * scale
+    assert np.abs(outs[0][1] - A2).max() <= 1e-10 * scale
 
 
 def test_zero_sweeps_only_evaluate():
