@@ -332,29 +332,38 @@ __global__ void __launch_bounds__(kJointThreads, 1) k_joint(const JointArgs<T> a
               if (d0 != (T)0 || d1 != (T)0) ++moved;
             }
           }
+          const bool mv = d0 != (T)0 || d1 != (T)0;  // the same on every lane
           if (lane == 0) {
             s_i[wid] = i;
             s_j[wid] = j;
             s_d[wid][0] = d0;
             s_d[wid][1] = d1;
           }
-          __syncthreads();
-          for (int w = 0; w < kJointWarps; ++w) {
-            const int i2 = s_i[w];
-            if (i2 < 0) continue;
-            const int j2 = s_j[w];
-#pragma unroll
-            for (int m = 0; m < 2; ++m) {
-              const T d = s_d[w][m];
-              if (d == (T)0) continue;
-              cta_axpy2<T>(a.W[m] + (size_t)i2 * ld, a.W[m] + (size_t)j2 * ld,
-                           a.S[m] + (size_t)i2 * ld, a.S[m] + (size_t)j2 * ld, d, ld);
-            }
-          }
-          __syncthreads();
-          if (a.row_ver != nullptr && lane == 0 && q < half) {
+          // A block that did not move (or a bye) left its rows untouched and
+          // its reads are complete: publish them now, so the readers of the
+          // next colour do not wait for this CTA's row updates.
+          if (a.row_ver != nullptr && lane == 0 && q < half && !mv) {
             if (ra < p) jst_release_u32(a.row_ver + ra, vin + 1u);
             if (rb < p) jst_release_u32(a.row_ver + rb, vin + 1u);
+          }
+          if (__syncthreads_or(lane == 0 && mv)) {
+            for (int w = 0; w < kJointWarps; ++w) {
+              const int i2 = s_i[w];
+              if (i2 < 0) continue;
+              const int j2 = s_j[w];
+#pragma unroll
+              for (int m = 0; m < 2; ++m) {
+                const T d = s_d[w][m];
+                if (d == (T)0) continue;
+                cta_axpy2<T>(a.W[m] + (size_t)i2 * ld, a.W[m] + (size_t)j2 * ld,
+                             a.S[m] + (size_t)i2 * ld, a.S[m] + (size_t)j2 * ld, d, ld);
+              }
+            }
+            __syncthreads();
+            if (a.row_ver != nullptr && lane == 0 && q < half && mv) {
+              if (ra < p) jst_release_u32(a.row_ver + ra, vin + 1u);
+              if (rb < p) jst_release_u32(a.row_ver + rb, vin + 1u);
+            }
           }
         }
         if (a.row_ver == nullptr) grid_barrier(a.barrier, gen, a.wait, c);
