@@ -53,6 +53,8 @@ def parse_args(argv=None):
                     help="skip the large sparse solve (p = 20000) section")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the differentiable-solve (implicit adjoint) section")
+    ap.add_argument("--section", choices=["joint"], default=None,
+                    help="run one extra section alone (one GPU) and print its JSON")
     ap.add_argument("--no-joint", action="store_true",
                     help="skip the joint two-population section")
     ap.add_argument("--no-path", action="store_true",
@@ -834,8 +836,28 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_section(args):
+    """One extra section alone on cuda:0 (profiling and quick checks); prints
+    {"section": name, ...} as one JSON line."""
+    import torch
+
+    from paper_2106_09382_gb300 import concord as C
+    from paper_2106_09382_gb300 import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    hbm_peak, _ = load_peaks()
+    out = {"section": args.section}
+    if args.section == "joint":
+        out.update(run_joint_section(C, synth, dev, stream, hbm_peak))
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.section:
+        run_section(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
