@@ -80,6 +80,28 @@ def test_no_gpu_means_error_not_fallback():
     assert np.all(out == 0)
 
 
+def test_joint_no_gpu_means_error_not_fallback():
+    """The joint estimator's entry points also refuse to run without a device
+    and reject bad arguments before touching one."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    lib = C.load()
+    jt = ctypes.c_void_p()
+    assert lib.concord_joint_create(ctypes.byref(jt), 10, C.FP64, -1) == C.E_CUDA
+    assert not jt.value
+    assert lib.concord_joint_create(ctypes.byref(jt), 1, C.FP64, -1) == C.E_ARG
+    assert lib.concord_joint_create(ctypes.byref(jt), 10, 7, -1) == C.E_ARG
+    assert lib.concord_joint_create(None, 10, C.FP64, -1) == C.E_ARG
+    r = C.ConcordResult()
+    assert lib.concord_joint_run(None, 0.1, 0.1, 1e-5, 10, ctypes.byref(r)) == C.E_ARG
+    assert lib.concord_joint_set_variant(None, C.JOINT_ROWFLAGS) == C.E_ARG
+    assert lib.concord_joint_destroy(None) == C.OK
+    with pytest.raises(C.ConcordError) as e:
+        C.Joint(10, device=0)
+    assert e.value.code == C.E_CUDA
+
+
 @pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 7, 12, 13, 100, 101, 333, 1000, 1001])
 def test_consecutive_partners_walk_the_ring(p):
     """Row v's partner at colour c + 1 follows from its partner at colour c:

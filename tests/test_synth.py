@@ -40,3 +40,40 @@ def test_block_diag_structure():
         off[s, s] = 0
     assert np.count_nonzero(off) == 0
     assert np.allclose(np.diag(Om) - np.abs(Om - np.diag(np.diag(Om))).sum(1), 0.5)
+
+
+def test_joint_ar1_structure():
+    """Two related precision matrices: a common AR(1) band, n_shared extra
+    edges with equal values in both, n_own edges in each alone; both
+    positive definite (each extra edge adds a PSD term)."""
+    p, ns, no = 200, 6, 4
+    Om1, Om2 = synth.joint_ar1(p, n_shared=ns, n_own=no, seed=5)
+    for Om in (Om1, Om2):
+        assert np.array_equal(Om, Om.T)
+        assert np.linalg.eigvalsh(Om).min() >= 1.0 / 3.0 - 1e-12
+        band = np.diag(Om, 1)
+        assert np.allclose(band, -0.5 / 0.75)
+    iu, ju = np.triu_indices(p, 2)
+    e1 = set(zip(iu[Om1[iu, ju] != 0], ju[Om1[iu, ju] != 0]))
+    e2 = set(zip(iu[Om2[iu, ju] != 0], ju[Om2[iu, ju] != 0]))
+    shared = e1 & e2
+    assert len(shared) == ns and len(e1 - e2) == no and len(e2 - e1) == no
+    assert all(Om1[a, b] == Om2[a, b] for a, b in shared)
+    assert all(0.3 <= abs(Om1[a, b]) <= 0.6 for a, b in e1)
+    # each diagonal carries its own extra edges' magnitudes
+    base = synth.ar1_extra(p, 0.5, 0, seed=5)
+    for Om in (Om1, Om2):
+        extra = np.abs(np.triu(Om, 2)) + np.abs(np.triu(Om, 2)).T
+        assert np.allclose(np.diag(Om) - np.diag(base), extra.sum(axis=1))
+
+
+def test_joint_ar1_rejects_impossible_edge_counts():
+    with pytest.raises(ValueError):
+        synth.joint_ar1(4, n_shared=2, n_own=2)
+
+
+def test_workload_joint_shapes():
+    w = synth.workload_joint(p=60, n=40)
+    assert w["X1"].shape == (40, 60) and w["X2"].shape == (40, 60)
+    assert not np.array_equal(w["X1"], w["X2"])
+    assert w["lam1"] > w["lam2"] > 0
