@@ -229,6 +229,27 @@ def cpu_baseline(X: np.ndarray, lam: float, sweeps: int, budget: float, sweeps_s
             "seconds_per_sweep": per_sweep, "updates_per_s": upd}
 
 
+def joint_cpu_baseline(w: dict, sweeps: int, sweeps_src: str):
+    """The joint oracle (single-threaded C, FP64, both blocks' gradients as
+    the direct sums of Eq. 3 / Eq. 2) timed on a bounded sample of the joint
+    workload: both Grams, then one joint sweep from Omega = I (every sweep
+    costs the same: the direct sums run over whole rows), scaled to a solve."""
+    import oracle as O
+    t0 = time.perf_counter()
+    S1 = O.gram(O.standardize(w["X1"]))
+    S2 = O.gram(O.standardize(w["X2"]))
+    t_gram = time.perf_counter() - t0
+    p = w["p"]
+    A1, A2 = np.eye(p), np.eye(p)
+    t0 = time.perf_counter()
+    O.joint_sweep(S1, S2, A1, A2, w["lam1"], w["lam2"])
+    per_sweep = time.perf_counter() - t0
+    return {"value": t_gram + sweeps * per_sweep, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": "both Grams + 1 joint sweep at p=%d; x %d sweeps (%s)" % (p, sweeps,
+                                                                              sweeps_src),
+            "seconds_per_sweep": per_sweep, "gram_seconds": t_gram}
+
+
 def golden_sweeps(p: int):
     path = os.path.join(ROOT, "oracle", "golden", "ar1_p%d.json" % p)
     try:
@@ -491,7 +512,7 @@ def run_adjoint_section(C, synth, dev, stream, steps=20, lr=0.003):
                               "cg_iterations": [int(v) for v in rows[:, 4]]}}
 
 
-def run_joint_section(C, synth, dev, stream, hbm_peak, reps=3):
+def run_joint_section(C, synth, dev, stream, hbm_peak, reps=3, with_oracle=True):
     """Joint two-population CONCORD (the extension closing Section 6) on the
     joint AR(1) workload (p = 1000, n = 500 per population, lambda1 = 0.2,
     lambda2 = 0.05, joint KKT <= 1e-5): mixed (FP32 sweeps + FP64 polish)
@@ -584,6 +605,9 @@ def run_joint_section(C, synth, dev, stream, hbm_peak, reps=3):
     scale = max(float(np.abs(omegas["fp64"][m]).max()) for m in (0, 1))
     out["mixed_vs_fp64"] = {"max_abs_dOmega_rel": d / scale,
                             "speedup": out["fp64"]["seconds"] / out["mixed"]["seconds"]}
+    if with_oracle:
+        out["cpu_baseline"] = joint_cpu_baseline(
+            w, out["fp64"]["sweeps"], "sweeps of the FP64 GPU joint solve on the same data")
     return out
 
 
@@ -821,7 +845,8 @@ def run_ours(args):
         if not args.no_large:
             out["large"] = run_large_section(C, synth, dev, stream, hbm_peak)
         if not args.no_joint:
-            out["joint"] = run_joint_section(C, synth, dev, stream, hbm_peak)
+            out["joint"] = run_joint_section(C, synth, dev, stream, hbm_peak,
+                                             with_oracle=(rank == 0))
         # ---------------- CPU oracle, bounded sample (rank 0 only)
         if rank == 0:
             gs, src = golden_sweeps(p)
