@@ -537,7 +537,7 @@ def run_joint_section(C, synth, dev, stream, hbm_peak, reps=3, with_oracle=True)
         J.set_stream(stream)
         J.set_S(0, S[0])
         J.set_S(1, S[1])
-        configs = {}
+        trial_s = {}
         names = {C.JOINT_ROWFLAGS: "rowflags", C.JOINT_BARRIER: "barrier"}
         trials = ([(v, g) for v in (C.JOINT_ROWFLAGS, C.JOINT_BARRIER) for g in (0, 16, 64, 152)]
                   if prec == C.MIXED else [(C.JOINT_ROWFLAGS, 0), (C.JOINT_BARRIER, 0)])
@@ -550,19 +550,19 @@ def run_joint_section(C, synth, dev, stream, hbm_peak, reps=3, with_oracle=True)
                 J.set_omega(1, eye)
                 r = J.run(l1, l2, tol=tol, max_sweeps=2000)
                 times.append(r.seconds)
-            configs["%s/%d" % (names[v], g)] = (statistics.mean(times[1:]), r)
-        best = min(configs, key=lambda k: configs[k][0])
+            trial_s["%s/%d" % (names[v], g)] = (statistics.mean(times[1:]), r)
+        best = min(trial_s, key=lambda k: trial_s[k][0])
         J.set_variant(C.JOINT_ROWFLAGS)
         J.set_grid(0)
         J.set_omega(0, eye)
         J.set_omega(1, eye)
         r = J.run(l1, l2, tol=tol, max_sweeps=2000)
-        sec = configs["rowflags/0"][0]
+        sec = trial_s["rowflags/0"][0]
         hist = J.history()
         rec = {"seconds": sec, "config": "rowflags/0 (default)", "sweeps": r.sweeps,
                "sweeps_fp32": r.sweeps_fp32, "kkt": r.kkt, "objective": r.objective,
                "status": r.status,
-               "ms_per_config": {k: round(v[0] * 1e3, 4) for k, v in configs.items()},
+               "ms_per_config": {k: round(v[0] * 1e3, 4) for k, v in trial_s.items()},
                "best_config": best}
         if prec == C.MIXED:
             # algorithmic bytes of the FP32 sweeps (element b = 4): per colour
