@@ -633,7 +633,9 @@ int concord_joint_get_omega(concord_joint *jt, int m, void *Om_dev, int dtype, i
  * no stopping rule; res receives the residual and objective after them
  * (res->lambda = lambda1).  n_sweeps = 0 only evaluates.
  * Errors: CONCORD_E_ARG (S not set, lambdas < 0), CONCORD_E_NONFINITE,
- * CONCORD_E_TIMEOUT, CONCORD_E_CUDA. */
+ * CONCORD_E_TIMEOUT (res->timeout_vertex = the row whose wait ran out, or
+ * -1 - CTA for a grid barrier; res->timeout_step = the colour step),
+ * CONCORD_E_CUDA. */
 int concord_joint_sweep(concord_joint *jt, double lambda1, double lambda2, int n_sweeps,
                         concord_result *res);
 /* Joint sweeps until the joint KKT residual <= tol or max_sweeps (mixed: FP32

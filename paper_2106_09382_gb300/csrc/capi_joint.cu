@@ -116,6 +116,7 @@ int demote(concord_joint* jt) {
 struct PhaseOut {
   int sweeps = 0, status = 0, first_delta = 0;
   double kkt = 0, obj = 0, delta = 0, moved = 0;
+  int timeout_where = 0, timeout_step = -1;  // on a wait that ran out: row (>= 0) or -1 - CTA
 };
 
 // One persistent launch in precision T (f32 selects the FP32 arrays).
@@ -203,9 +204,16 @@ int run_phase(concord_joint* jt, bool f32, double l1, double l2, double tol, int
   out->status = (int)r[kJResStatus];
   out->first_delta = (int)r[kJResFirstDelta];
   jt->hist_rows += out->sweeps < hist_left ? out->sweeps : (hist_left > 0 ? hist_left : 0);
-  if (h_abort[0] != 0 || out->status == kJStatusAborted)
-    return jfail(CONCORD_E_TIMEOUT, "joint sweep: a device wait ran out (CTA %d, step %d)",
+  if (h_abort[0] != 0 || out->status == kJStatusAborted) {
+    out->timeout_where = h_abort[1];
+    out->timeout_step = h_abort[2];
+    if (h_abort[1] >= 0)
+      return jfail(CONCORD_E_TIMEOUT,
+                   "joint sweep: the wait for row %d ran out (colour step %d)", h_abort[1],
+                   h_abort[2]);
+    return jfail(CONCORD_E_TIMEOUT, "joint sweep: a grid barrier wait ran out (CTA %d, step %d)",
                  -1 - h_abort[1], h_abort[2]);
+  }
   return CONCORD_OK;
 }
 
@@ -238,6 +246,10 @@ void fill_result(concord_result* res, const PhaseOut& o, int sweeps, int sweeps3
   res->seconds = seconds;
   res->timeout_vertex = -1;
   res->timeout_step = -1;
+  if (status == CONCORD_E_TIMEOUT) {
+    res->timeout_vertex = o.timeout_where;
+    res->timeout_step = o.timeout_step;
+  }
 }
 
 int map_status(const PhaseOut& o) {
@@ -480,6 +492,7 @@ int concord_joint_sweep(concord_joint* jt, double lambda1, double lambda2, int n
   JCK(cudaEventRecord(jt->ev0, jt->stream));
   PhaseOut o;
   rc = run_phase(jt, f32, lambda1, lambda2, 0.0, n_sweeps, false, false, &o);
+  if (rc == CONCORD_E_TIMEOUT) fill_result(res, o, o.sweeps, f32 ? o.sweeps : 0, lambda1, 0, 0.0, rc);
   if (rc != CONCORD_OK) return rc;
   JCK(cudaEventRecord(jt->ev1, jt->stream));
   JCK(cudaEventSynchronize(jt->ev1));
@@ -506,6 +519,7 @@ int concord_joint_run(concord_joint* jt, double lambda1, double lambda2, double 
     // FP32 phase: sweeps until the tolerance or the FP32 rounding floor
     if ((rc = demote(jt)) != CONCORD_OK) return rc;
     rc = run_phase(jt, true, lambda1, lambda2, tol, max_sweeps, true, true, &o1);
+    if (rc == CONCORD_E_TIMEOUT) fill_result(res, o1, o1.sweeps, o1.sweeps, lambda1, 0, 0.0, rc);
     if (rc != CONCORD_OK) return rc;
     if (o1.status == kJStatusNonfinite) return map_status(o1);
     sweeps32 = o1.sweeps;
@@ -517,6 +531,8 @@ int concord_joint_run(concord_joint* jt, double lambda1, double lambda2, double 
   if ((rc = promote(jt)) != CONCORD_OK) return rc;
   const int left = max_sweeps - sweeps32;
   rc = run_phase(jt, false, lambda1, lambda2, tol, left > 0 ? left : 0, false, true, &o2);
+  if (rc == CONCORD_E_TIMEOUT)
+    fill_result(res, o2, sweeps32 + o2.sweeps, sweeps32, lambda1, 0, 0.0, rc);
   if (rc != CONCORD_OK) return rc;
   if (!first_delta && o2.first_delta) first_delta = sweeps32 + o2.first_delta;
   JCK(cudaEventRecord(jt->ev1, jt->stream));
