@@ -135,3 +135,43 @@ def test_consecutive_partners_walk_the_ring(p):
                 assert w1 == w0 - 1
             elif w0 != 0 and w1 != 0:
                 assert w1 == nxt(w0), (v, c, w0, w1)
+
+
+def _c_rem(a, b):
+    """C's % (truncating), as the kernel's integer arithmetic computes it."""
+    r = abs(a) % b
+    return r if a >= 0 else -r
+
+
+def _joint_slot_pair(q, c, P, p):
+    """The joint sweep kernel's slot -> pair closed form (slot_pair in
+    csrc/joint.cu), restated: returns (i, j, ra, rb)."""
+    if q == 0:
+        a, b = 0, _c_rem(_c_rem(P - 1 - c, P) + P, P) + 1
+    else:
+        r = q - 1
+        a = _c_rem(_c_rem(r - c, P) + P, P) + 1
+        b = _c_rem(_c_rem(P - 2 - r - c, P) + P, P) + 1
+    i, j = min(a, b), max(a, b)
+    return (i if j < p else -1), j, a, b
+
+
+@pytest.mark.parametrize("p", list(range(2, 24)) + [99, 100, 999, 1000, 1001])
+def test_joint_slot_map_is_algorithm1_and_covers_every_vertex(p):
+    """Colour c's slots hold exactly Algorithm 1's pairs of colour c, and
+    every real vertex sits in exactly one slot of every colour (byes
+    included): the joint kernel's row-version protocol publishes every row
+    once per colour on this basis."""
+    pe = p + (p % 2)
+    P, half = pe - 1, pe // 2
+    sched = O.schedule(p)
+    for c in range(P):
+        seen, got = [], set()
+        for q in range(half):
+            i, j, a, b = _joint_slot_pair(q, c, P, p)
+            assert 0 <= a <= P and 0 <= b <= P and a != b
+            seen += [v for v in (a, b) if v < p]
+            if i >= 0:
+                got.add((i, j))
+        assert sorted(seen) == list(range(p))
+        assert got == {tuple(sorted(map(int, pr))) for pr in sched[c] if pr[0] >= 0}
