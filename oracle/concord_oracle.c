@@ -96,48 +96,54 @@ void oracle_gram_rows(const double *Z, int n, int p, const int32_t *rows, int nr
 }
 
 /* ------------------------------------------------------------------------ */
-/* Schedule: the circle method (Section 3.2) as Algorithm 1 runs it.         */
+/* Schedule: the circle method of Section 3.2.                               */
 /* ------------------------------------------------------------------------ */
 
-/* Fills pairs[(k * (pe/2) + q) * 2 + {0,1}] for colour k = 0..pe-2 and slot
- * q = 0..pe/2-1 with the 0-based vertices of the q-th matching pair of the
- * k-th target set, in Algorithm 1's order.  A pair that holds the extra
- * vertex p (1-based p+1, present only for odd p) is written as (-1, -1):
- * step (iii) of the circle method discards it.  Returns the number of colours
- * pe - 1, where pe = p for even p and p + 1 for odd p. */
+/* The round-robin table of Section 3.2, step (i), has two rows of pe/2
+ * cells.  Vertex 1 stays in the top-left cell; the other m = pe - 1 vertices
+ * sit on a circle that runs left to right along the top row (columns
+ * 2..pe/2) and then right to left along the bottom row (columns pe/2..1).
+ * Counting circle positions from 0 at the top of column 2, the top cell of
+ * column t >= 2 is position t - 2 and the bottom cell of column t >= 1 is
+ * position pe - 1 - t.  The first table fills the circle with 2, 3, ..., pe
+ * in that order, and every later table turns it one position clockwise, so
+ * in table k (1-based) position c holds the vertex that was at position
+ * c - (k - 1) in the first table. */
+static int circle_vertex(int c, int k, int pe)
+{
+    int m = pe - 1;
+    int shift = MUTANT(6) ? -(k - 1) : (k - 1); /* mutant: turned the wrong way */
+    int r = ((c - shift) % m + m) % m;
+    return 2 + r; /* 1-based vertex */
+}
+
+/* Fills pairs[(k * (pe/2) + q) * 2 + {0,1}] for colour k = 0..pe-2 and column
+ * q = 0..pe/2-1 with the 0-based (top, bottom) vertices of column q + 1 of
+ * table k + 1: step (ii) takes the two vertices of a column as a matching
+ * pair and the k-th table's columns as the k-th target set, step (iv) gives
+ * that set the k-th colour (Algorithm 1 visits the colours in this order).
+ * A column holding the extra vertex p + 1 (odd p only) is written as
+ * (-1, -1): step (iii) discards it.  Returns the number of colours pe - 1,
+ * with pe = p for even p and p + 1 for odd p. */
 int oracle_schedule(int p, int32_t *pairs)
 {
     if (p < 2) return OR_E_ARG;
     int pe = (p % 2 == 0) ? p : p + 1;
-    int *j = (int *)malloc(sizeof(int) * (size_t)(pe + 1)); /* j[1..pe], 1-based */
-    if (!j) return OR_E_ARG;
-    for (int m = 1; m <= pe; ++m) j[m] = m; /* (j_1, ..., j_pe) <- (1, ..., pe) */
     int half = pe / 2;
-    for (int k = 0; k < pe - 1; ++k) {
-        /* target set I = {(j_q, j_{pe-q+1}) : q = 1..pe/2} */
-        for (int q = 1; q <= half; ++q) {
-            int r = j[q], s = j[pe - q + 1];
-            int32_t *slot = pairs + ((size_t)k * half + (q - 1)) * 2;
-            if (r == p + 1 || s == p + 1) {
+    for (int k = 1; k <= pe - 1; ++k) {
+        for (int t = 1; t <= half; ++t) {
+            int top = (t == 1) ? 1 : circle_vertex(t - 2, k, pe);
+            int bottom = circle_vertex(pe - 1 - t, k, pe);
+            int32_t *slot = pairs + ((size_t)(k - 1) * half + (t - 1)) * 2;
+            if (top == p + 1 || bottom == p + 1) {
                 slot[0] = -1;
                 slot[1] = -1;
             } else {
-                slot[0] = r - 1;
-                slot[1] = s - 1;
+                slot[0] = top - 1;
+                slot[1] = bottom - 1;
             }
         }
-        /* tmp <- j_pe, (j_3..j_pe) <- (j_2..j_{pe-1}), j_2 <- tmp */
-        if (MUTANT(6)) {
-            int tmp = j[2];
-            for (int m = 2; m < pe; ++m) j[m] = j[m + 1];
-            j[pe] = tmp;
-        } else {
-            int tmp = j[pe];
-            for (int m = pe; m >= 3; --m) j[m] = j[m - 1];
-            j[2] = tmp;
-        }
     }
-    free(j);
     return pe - 1;
 }
 
