@@ -193,14 +193,15 @@ int concord_gram(const void *X_dev, int x_dtype, int n, int p, int ldx, int prep
  * plus a status word, held on every device that loads the library until the
  * process exits).  Hence:
  *   - p must be <= 16384; larger p returns CONCORD_E_ARG (use concord_gram);
- *   - the first call on a device looks up that array's device address
- *     (cudaGetSymbolAddress) and caches it: make that first call before any
- *     stream capture that includes it;
+ *   - the first call on a device, with that device current, looks up the
+ *     array's device address (cudaGetSymbolAddress) and caches it; make that
+ *     first call on each device before any stream capture begins;
  *   - every call shares the array and it keeps the last call's contents;
  *     the status word is cleared by each call; calls that overlap on the GPU
  *     (different streams or host threads at the same time) race on it and
  *     must be serialised by the caller.
- * The call synchronises `stream` to report a constant or non-finite column.
+ * Every call waits for `stream` to finish its work, then reads the status
+ * word back to report a constant or non-finite column.
  * Errors: CONCORD_E_ARG, CONCORD_E_NONPOS_DIAG, CONCORD_E_NONFINITE,
  * CONCORD_E_CUDA.
  */

@@ -196,23 +196,35 @@ def concord_gram(X, prep: int = PREP_STANDARDIZE, mode: int = GRAM_FP64, out_dty
     assert X.is_cuda and X.dim() == 2 and X.stride(1) == 1
     n, p = X.shape
     out_dtype = out_dtype or (torch.float64 if mode == GRAM_FP64 else torch.float32)
-    S = torch.empty((p, p), dtype=out_dtype, device=X.device)
-    _check(load().concord_gram(X.data_ptr(), _dtype_code(X), n, p, X.stride(0), prep, mode,
-                               S.data_ptr(), _dtype_code(S), p, _stream_ptr(stream)))
+    with torch.cuda.device(X.device):
+        S = torch.empty((p, p), dtype=out_dtype, device=X.device)
+        _check(load().concord_gram(X.data_ptr(), _dtype_code(X), n, p, X.stride(0), prep, mode,
+                                   S.data_ptr(), _dtype_code(S), p, _stream_ptr(stream)))
     return S
 
 
 def concord_gram_static(X, prep: int = PREP_STANDARDIZE, out=None, stream=None):
     """FP64 S = Z^T Z / n through the allocation-free entry point (the device
     statistics live in the library's fixed array; p <= 16384).  `out` may
-    give the p x p float64 output tensor."""
+    give the p x p float64 output tensor on X's device (row stride >= p).
+    The call runs with X's device current, on `stream` or that device's
+    current stream."""
     import torch
     assert X.is_cuda and X.dim() == 2 and X.stride(1) == 1
     n, p = X.shape
-    S = out if out is not None else torch.empty((p, p), dtype=torch.float64, device=X.device)
-    assert S.dtype == torch.float64 and S.is_cuda and S.stride(1) == 1
-    _check(load().concord_gram_static(X.data_ptr(), _dtype_code(X), n, p, X.stride(0), prep,
-                                      S.data_ptr(), S.stride(0), _stream_ptr(stream)))
+    with torch.cuda.device(X.device):
+        if out is None:
+            S = torch.empty((p, p), dtype=torch.float64, device=X.device)
+        else:
+            S = out
+            if S.device != X.device:
+                raise ValueError("out is on %s, X on %s" % (S.device, X.device))
+            if S.dtype != torch.float64 or S.dim() != 2 or tuple(S.shape) != (p, p):
+                raise ValueError("out must be a (%d, %d) float64 tensor" % (p, p))
+            if S.stride(1) != 1 or S.stride(0) < p:
+                raise ValueError("out must have unit column stride and row stride >= p")
+        _check(load().concord_gram_static(X.data_ptr(), _dtype_code(X), n, p, X.stride(0), prep,
+                                          S.data_ptr(), S.stride(0), _stream_ptr(stream)))
     return S
 
 

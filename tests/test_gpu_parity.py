@@ -1,7 +1,7 @@
 """GPU path (through the C ABI) against the FP64 CPU oracle on the same
 seeded inputs.
 
-Tolerances (derivations in the design doc):
+Tolerances (each derived from the arithmetic of the two sides):
   * FP64 Gram: |dS| <= 1e-13 (both sum n products in FP64, different order).
   * FP32 Gram: |dS| <= (n + 4) 2^-24 (|s_ij| <= 1 for standardized data).
   * FP64 sweeps vs oracle, sweep by sweep: max|dOmega| <= 1e-10 max|Omega|
@@ -78,7 +78,8 @@ def test_gram_tf32x3_tensor_cores(n, p):
     Each standardized value is split into 11 + 11 significant bits (error
     <= 2^-22 relative), so each product is off by <= 2^-21 |z_i z_k| once the
     lo*lo term is dropped; products are summed in FP32 over chunks of 128
-    (error <= 128 * 2^-24 of the chunk's absolute sum) and the chunks in FP64.
+    (error <= 128 * 2^-24 of the chunk's absolute sum) and the chunks are
+    combined in compensated FP32 (a TwoSum hi + lo pair per entry).
     With sum_k |z_i z_k| <= n for standardized columns the error of S is at
     most 128 * 2^-24 + 2^-20, whatever n."""
     X = data(n, p, 13 * n + p)

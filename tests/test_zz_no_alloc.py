@@ -11,6 +11,7 @@ the second must not see the first one's statistics.
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2106_09382_gb300 import concord as C
 
 pytestmark = pytest.mark.gpu
@@ -35,6 +36,10 @@ def test_static_gram_matches_allocating_gram_two_calls_in_a_row():
         torch.cuda.synchronize()
         assert torch.equal(got, got.T)
         assert float((got - want).abs().max()) <= 1e-13
+        # and directly against the oracle's triple-loop Gram (FP64 sums of
+        # the same n products in another order)
+        S_or = O.gram(O.standardize(X.cpu().numpy()))
+        assert np.abs(got.cpu().numpy() - S_or).max() <= 1e-13
 
 
 def test_static_gram_float32_input_and_centering():
@@ -61,3 +66,19 @@ def test_static_gram_limits_and_errors():
     got = C.concord_gram_static(Z)
     want = C.concord_gram(Z, C.PREP_STANDARDIZE, C.GRAM_FP64)
     assert float((got - want).abs().max()) <= 1e-13
+
+
+def test_static_gram_rejects_a_bad_output_tensor():
+    """The binding checks `out` before the library writes p rows into it."""
+    X = torch.as_tensor(_data(30, 40, 6), device="cuda")
+    for bad in (torch.empty((39, 40), dtype=torch.float64, device="cuda"),
+                torch.empty((40, 40), dtype=torch.float32, device="cuda"),
+                torch.empty((40, 80), dtype=torch.float64, device="cuda")[:, ::2],
+                torch.empty((40, 40), dtype=torch.float64)):
+        with pytest.raises(ValueError):
+            C.concord_gram_static(X, out=bad)
+    wide = torch.zeros((40, 48), dtype=torch.float64, device="cuda")
+    got = C.concord_gram_static(X, out=wide[:, :40])
+    want = C.concord_gram(X, C.PREP_STANDARDIZE, C.GRAM_FP64)
+    assert float((got - want).abs().max()) <= 1e-13
+    assert float(wide[:, 40:].abs().max()) == 0.0
