@@ -11,7 +11,7 @@ C source beside it:
     standardize      Section 2.1 (X centered columnwise; unit 1/n variance)
     gram, gram_rows  Algorithm 1, T <- X^T X (here divided by n); selected rows
     eq3, eq2         Eq. 3 / Eq. 2 for one entry from explicit rows
-    schedule         Section 3.2 circle method, Algorithm 1 index rotation
+    schedule         Section 3.2 circle method (round-robin table), colour order
     soft             Soft-threshold defined under Eq. 3
     offdiag_update   Eq. 3 with its two direct sums
     diag_update      Eq. 2 with its direct sum
@@ -19,6 +19,9 @@ C source beside it:
     objective        Eq. 1 / n from S; objective_data: Eq. 1 / n from the data
     kkt              subgradient optimality conditions of Eq. 1
     solve            Algorithm 1 repeated until KKT <= tol
+    solve_w, gram_w  the same solve with a maintained W = Omega S and the pairs
+                     of a colour on OpenMP threads (Lemma 1), and the Gram on
+                     threads: the timed CPU baseline (concord_oracle_w.c)
     joint_*          joint two-population CONCORD (the extension closing
                      Section 6): block update of (omega1_ij, omega2_ij) and of
                      the diagonal pair, sweep, objective, KKT, solve
@@ -38,6 +41,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "concord_oracle.c")
+_SRC_W = os.path.join(_HERE, "concord_oracle_w.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
@@ -72,6 +76,9 @@ _SIGNATURES = {
     "oracle_joint_kkt": ([_dp, _dp, _dp, _dp, _ci, _cd, _cd], _cd),
     "oracle_joint_solve": ([_dp, _dp, _ci, _cd, _cd, _cd, _cd, _ci, _dp, _dp, _dp, _dp, _dp,
                             _dp], _ci),
+    "oracle_w_threads": ([_ci], _ci),
+    "oracle_w_gram": ([_dp, _ci, _ci, _dp, _ci], _ci),
+    "oracle_solve_w": ([_dp, _ci, _cd, _cd, _cd, _ci, _dp, _dp, _dp, _dp, _ci], _ci),
 }
 
 
@@ -83,11 +90,11 @@ def build(force: bool = False, mutant: int = 0) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     lib = _LIB if mutant == 0 else os.path.join(_BUILD, "liboracle_mutant%d.so" % mutant)
     if (not force and os.path.exists(lib)
-            and os.path.getmtime(lib) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(lib) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_W))):
         return lib
     tmp = lib + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-DORACLE_MUTANT=%d" % int(mutant), "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-fopenmp",
+           "-DORACLE_MUTANT=%d" % int(mutant), "-o", tmp, _SRC, _SRC_W, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, lib)
     return lib
@@ -236,6 +243,45 @@ class Oracle:
         info = dict(converged=(rc == 0), sweeps=int(stats[0]), objective=float(stats[1]),
                     kkt=float(stats[2]), delta=float(stats[3]),
                     first_delta_sweep=int(stats[4]), nonzero_changes=int(stats[5]))
+        if hist is not None:
+            info["history"] = hist[: info["sweeps"]].copy()
+        return Om, info
+
+    # ------------------------------------------------ maintained-product mode
+    def threads(self, threads: int = 0) -> int:
+        """Threads the maintained-product mode runs with (0 = all cores)."""
+        return int(self.lib.oracle_w_threads(int(threads)))
+
+    def gram_w(self, Z, threads: int = 0) -> np.ndarray:
+        """S = Z^T Z / n on host threads (upper triangle, k ascending, mirrored)."""
+        Z = _f64(Z)
+        n, p = Z.shape
+        S = np.empty((p, p), dtype=np.float64)
+        if self.lib.oracle_w_gram(_ptr(Z), n, p, _ptr(S), int(threads)) != 0:
+            raise ValueError("oracle_w_gram: bad arguments")
+        return S
+
+    def solve_w(self, S, lam: float, tol: float = 1e-5, max_sweeps: int = 1000, Om0=None,
+                delta_tol: float = 1e-5, history: bool = False, threads: int = 0):
+        """The solve of `solve` with a maintained W = Omega S and the pairs of
+        each colour (and the diagonal updates) spread over host threads.
+        Returns (Omega, info dict) like `solve`, plus info["threads"]."""
+        S = _f64(S)
+        p = S.shape[0]
+        Om = np.empty((p, p), dtype=np.float64)
+        stats = np.zeros(7, dtype=np.float64)
+        hist = np.zeros((max(max_sweeps, 1), 3), dtype=np.float64) if history else None
+        o0 = _f64(Om0) if Om0 is not None else None
+        rc = self.lib.oracle_solve_w(_ptr(S), p, float(lam), float(tol), float(delta_tol),
+                                     int(max_sweeps), _ptr(o0) if o0 is not None else None,
+                                     _ptr(Om), _ptr(stats),
+                                     _ptr(hist) if hist is not None else None, int(threads))
+        if rc < 0:
+            raise ValueError("oracle_solve_w: status %d" % rc)
+        info = dict(converged=(rc == 0), sweeps=int(stats[0]), objective=float(stats[1]),
+                    kkt=float(stats[2]), delta=float(stats[3]),
+                    first_delta_sweep=int(stats[4]), nonzero_changes=int(stats[5]),
+                    threads=int(stats[6]))
         if hist is not None:
             info["history"] = hist[: info["sweeps"]].copy()
         return Om, info
@@ -399,6 +445,19 @@ def kkt(S, Om, lam):
 
 def solve(S, lam, tol=1e-5, max_sweeps=1000, Om0=None, delta_tol=1e-5, history=False):
     return default().solve(S, lam, tol, max_sweeps, Om0, delta_tol, history)
+
+
+def threads(n: int = 0) -> int:
+    return default().threads(n)
+
+
+def gram_w(Z, threads: int = 0):
+    return default().gram_w(Z, threads)
+
+
+def solve_w(S, lam, tol=1e-5, max_sweeps=1000, Om0=None, delta_tol=1e-5, history=False,
+            threads=0):
+    return default().solve_w(S, lam, tol, max_sweeps, Om0, delta_tol, history, threads)
 
 
 def lambda_max(S) -> float:

@@ -349,15 +349,17 @@ double oracle_kkt(const double *S, const double *Om, int p, double lambda)
 {
     double *W = (double *)malloc(sizeof(double) * (size_t)p * p);
     if (!W) return NAN;
-    for (int i = 0; i < p; ++i)
-        for (int j = 0; j < p; ++j) {
-            double acc = 0.0;
-            for (int u = 0; u < p; ++u) {
-                double o = Om[(size_t)i * p + u];
-                if (o != 0.0) acc += o * S[(size_t)u * p + j]; /* exact zeros add nothing */
-            }
-            W[(size_t)i * p + j] = acc;
+    /* W_ij = sum_u omega_iu s_uj with u ascending for every j; exact zeros of
+     * Omega add nothing and are skipped, so a row costs nnz(row) * p. */
+    for (int i = 0; i < p; ++i) {
+        double *w = W + (size_t)i * p;
+        for (int j = 0; j < p; ++j) w[j] = 0.0;
+        for (int u = 0; u < p; ++u) {
+            double o = Om[(size_t)i * p + u];
+            if (o == 0.0) continue;
+            for (int j = 0; j < p; ++j) w[j] += o * S[(size_t)u * p + j];
         }
+    }
     double worst = 0.0;
     for (int i = 0; i < p; ++i) {
         double wii = Om[(size_t)i * p + i];

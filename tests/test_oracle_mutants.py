@@ -1,12 +1,13 @@
 """Planted mistakes in the oracle are caught by its pins.
 
-``concord_oracle.c`` compiled with ``-DORACLE_MUTANT=k`` carries one plausible
-mistake (a dropped term, a wrong sign or index, a wrong normalisation, a
+``concord_oracle.c`` and ``concord_oracle_w.c`` compiled with
+``-DORACLE_MUTANT=k`` carry one plausible mistake (a dropped term, a wrong sign or index, a wrong normalisation, a
 reversed rotation).  Each must fail at least one of the pin checks below,
 which restate, against an arbitrary build, the independent references used in
 test_oracle.py: Table 1, the p=2 closed form, the brute-force minimiser, the
-data form of Eq. 1, finite-difference slopes of the objective, and the
-population (1/n) standardization.
+data form of Eq. 1, finite-difference slopes of the objective, the
+population (1/n) standardization, and (for the maintained-product mode)
+agreement with the definition mode.
 """
 import os
 
@@ -29,6 +30,9 @@ MUTANTS = {
     8: "objective drops the factor 1/2",
     9: "Gram is not divided by n",
     10: "standardization uses 1/(n-1)",
+    15: "maintained-product mode: Eq. 3 first sum keeps the u = j term",
+    16: "maintained-product mode: a pair change updates row i of W only",
+    17: "maintained-product mode: a diagonal change leaves W unchanged",
 }
 
 
@@ -115,8 +119,17 @@ def check_gram_and_standardize(o):
             and np.abs(np.diag(S) - 1).max() < 1e-13)
 
 
+def check_w_mode(o):
+    """The maintained-product mode against the definition mode of the same
+    build (the other checks pin the definition mode)."""
+    S = _S(60, 31, 5, mix=0.5)
+    Om1, i1 = o.solve(S, 0.05, tol=1e-9, max_sweeps=200)
+    Om2, i2 = o.solve_w(S, 0.05, tol=1e-9, max_sweeps=200)
+    return i1["sweeps"] == i2["sweeps"] and np.abs(Om1 - Om2).max() < 1e-12
+
+
 CHECKS = [check_table1, check_p2_closed_form, check_brute_force, check_objective_forms,
-          check_kkt_slopes, check_gram_and_standardize]
+          check_kkt_slopes, check_gram_and_standardize, check_w_mode]
 
 
 def test_normal_build_passes_every_check():
