@@ -125,6 +125,8 @@ typedef struct concord_result {
     int screen_redos;      /* screened sweeps redone after a pair outside the
                               candidates failed the verification */
     int dense_sweeps;      /* sweeps handed from the screened to the dense kernel */
+    int s_refined;         /* MIXED: entries of S recomputed in FP64 accuracy
+                              before the polish (concord_set_refine); 0 if none */
 } concord_result;
 
 /* KKT residual (absolute, S units), with W = Omega S and G = W + W^T:
@@ -345,6 +347,27 @@ int concord_set_rows_per_warp(concord_state *st, int rows);
  * default).
  */
 int concord_set_gram_mode(concord_state *st, int mode);
+
+/*
+ * concord_set_refine -- on (1, the default) or off (0): before the FP64
+ * polish of a MIXED solve whose S came from data through a reduced-precision
+ * Gram (CONCORD_GRAM_TF32X3, _BF16X3, _FP32), recompute in FP64 accuracy the
+ * entries of S that the optimality conditions of Eq. 1 read for the pairs
+ * that can be active: for every candidate pair (i, j) of the next sweep
+ * (w_ij != 0 or |G_ij| > 0.9 lambda) the entries s_kj, k in {i} u N(i), and
+ * s_ki, k in {j} u N(j), and for every vertex i the entries s_ki,
+ * k in {i} u N(i), where N(i) are the vertices paired with i among the
+ * candidates.  They are recomputed from the standardized data rounded to
+ * FP32 with compensated (double-float) sums and written into both copies of
+ * S kept by the state.  The tensor cores' FP32 accumulation rounds its sums
+ * with a bias (on the p = 5000 benchmark workload the 3xTF32 diagonal of S is
+ * 1.1e-6 low); with the refinement the polish solves the problem of the exact
+ * S instead of the perturbed one.  The count of recomputed entries is
+ * reported in concord_result.s_refined.  Results of FP64 states, of states
+ * whose S came from concord_set_S and of CONCORD_GRAM_FP64 are unaffected.
+ * Errors: CONCORD_E_ARG.
+ */
+int concord_set_refine(concord_state *st, int on);
 
 /*
  * concord_sweep -- run exactly n_sweeps outer iterations of Algorithm 1 at

@@ -42,7 +42,8 @@ class ConcordResult(ctypes.Structure):
                 ("delta", ctypes.c_double), ("lam", ctypes.c_double),
                 ("active_pairs", ctypes.c_longlong), ("seconds", ctypes.c_double),
                 ("timeout_vertex", ctypes.c_int), ("timeout_step", ctypes.c_int),
-                ("screen_redos", ctypes.c_int), ("dense_sweeps", ctypes.c_int)]
+                ("screen_redos", ctypes.c_int), ("dense_sweeps", ctypes.c_int),
+                ("s_refined", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
@@ -86,6 +87,7 @@ SIGNATURES = {
     "concord_get_W": ([_vp, _vp, _ci, _ci], _ci),
     "concord_get_history": ([_vp, _dp, _ci, _ip], _ci),
     "concord_set_gram_mode": ([_vp, _ci], _ci),
+    "concord_set_refine": ([_vp, _ci], _ci),
     "concord_set_rows_per_warp": ([_vp, _ci], _ci),
     "concord_set_sweep_variant": ([_vp, _ci], _ci),
     "concord_set_poll_sleep": ([_vp, _ci], _ci),
@@ -290,6 +292,11 @@ class State:
         _check(load().concord_set_gram_mode(self._ptr, int(mode)))
 
     # data
+    def set_refine(self, on: bool):
+        """Recompute the neighbourhood's S entries in FP64 accuracy before a
+        mixed solve's polish (concord_set_refine; on by default)."""
+        _check(load().concord_set_refine(self._ptr, 1 if on else 0))
+
     def set_S(self, S):
         assert S.is_cuda and S.dim() == 2 and S.stride(1) == 1
         _check(load().concord_set_S(self._ptr, S.data_ptr(), _dtype_code(S), S.stride(0)))

@@ -88,6 +88,19 @@ struct concord_state {
   double* Xstage = nullptr;  // n_cap x p FP64, host-data path
   float *zt_hi = nullptr, *zt_lo = nullptr;
   int n_pad = 0, p_pad = 0;
+  // mixed: the standardized data in FP32, transposed (p_pad x zt_ldn), kept
+  // for the FP64-accurate S entries recomputed before a polish
+  float* zt32 = nullptr;
+  int zt_ldn = 0, zt_n = 0;
+  bool zt_valid = false;  // zt32 holds the data S came from
+  bool refine = true;     // recompute the neighbourhood's S entries before a polish
+  struct {
+    int *cnt = nullptr, *off = nullptr, *cur = nullptr, *nbr = nullptr, *ctr = nullptr;
+    int2* cand = nullptr;
+    unsigned* bitmap = nullptr;
+    int nbr_cap = 0, cand_cap = 0;
+  } rf;
+  int* h_rf = nullptr;  // pinned: entries recomputed by the last promotion
   int gram_mode = CONCORD_GRAM_FP64;
   int rows_per_warp = 0;  // 0: automatic (one row per lane)
   int sweep_variant = 0;  // 0 auto, 1 grid, 2 cluster (CONCORD_SWEEP_*)
@@ -160,6 +173,7 @@ struct RunOut {
   bool stalled = false;
   int redos = 0, dense_sweeps = 0;  // screened runs
   int next_list = -1;               // screened: candidate list left for the next sweep
+  int s_refined = 0;                // S entries recomputed before the polish
 };
 
 // One persistent launch: n_sweeps outer iterations (fewer if the stopping
@@ -641,6 +655,7 @@ void fill_result(concord_result* res, const RunOut& o, int sweeps, int sweeps32,
   res->timeout_step = o.to_step;
   res->screen_redos = o.redos;
   res->dense_sweeps = o.dense_sweeps;
+  res->s_refined = o.s_refined;
 }
 
 int ensure_path(concord_state* st, int n_lambda, size_t n_rows) {
@@ -729,9 +744,84 @@ int path_impl(concord_state* st, const double* lambdas, int n, double tol, int m
   return CONCORD_OK;
 }
 
+// Buffers of the S refinement, sized for candidate lists of up to `list`
+// pairs (allocated on first use, grown when needed).
+int ensure_refine(concord_state* st, int list) {
+  const int p = st->p;
+  if (!st->rf.cnt) {
+    CK(cudaMalloc(&st->rf.cnt, sizeof(int) * (size_t)(p + 1)));
+    CK(cudaMalloc(&st->rf.off, sizeof(int) * (size_t)(p + 1)));
+    CK(cudaMalloc(&st->rf.cur, sizeof(int) * (size_t)(p + 1)));
+    CK(cudaMalloc(&st->rf.ctr, sizeof(int) * kRefineCtrs));
+    CK(cudaMalloc(&st->rf.bitmap, sizeof(unsigned) * refine_bitmap_words(p)));
+  }
+  if (!st->rf.cand) {
+    st->rf.cand_cap = 16 * p > (1 << 18) ? 16 * p : (1 << 18);
+    CK(cudaMalloc(&st->rf.cand, sizeof(int2) * (size_t)st->rf.cand_cap));
+  }
+  const int need = 2 * (list > st->rf.cand_cap ? list : st->rf.cand_cap);
+  if (need > st->rf.nbr_cap) {
+    if (st->rf.nbr) cudaFree(st->rf.nbr);
+    st->rf.nbr = nullptr;
+    CK(cudaMalloc(&st->rf.nbr, sizeof(int) * (size_t)need));
+    st->rf.nbr_cap = need;
+  }
+  return CONCORD_OK;
+}
+
+// mixed, S from data through a reduced-precision Gram: recompute the S
+// entries that the stationarity conditions of the candidate pairs (list
+// `list` of the screened kernel, or pairs collected from the FP32 iterate)
+// read, in FP64 accuracy from the FP32 data (refine.cu), in both copies of
+// S; then the diagonals and walk vectors derived from S.
+int refine_s(concord_state* st, double lambda, int list) {
+  const int p = st->p, ld = st->ld;
+  const bool have_list = list >= 0 && st->scr != nullptr;
+  int rc = ensure_refine(st, have_list ? st->nc_cap : 0);
+  if (rc != CONCORD_OK) return rc;
+  RefineArgs a;
+  memset(&a, 0, sizeof a);
+  a.p = p;
+  a.ld = ld;
+  a.n = st->zt_n;
+  a.ldn = st->zt_ldn;
+  a.sms = st->sms;
+  a.zt = st->zt32;
+  if (have_list) {
+    const ScreenWork<float> w = screen_work<float>(st);
+    a.cand = w.cand[list];
+    a.n_cand = w.ctr + kCtrCand + list;
+  }
+  a.Om32 = (const float*)st->Om;
+  a.W32 = (const float*)st->W;
+  a.thr = (float)((1.0 - kRefineMargin) * lambda);
+  a.own_cand = st->rf.cand;
+  a.own_cap = st->rf.cand_cap;
+  a.S64 = st->S64;
+  a.S32 = (float*)st->S;
+  a.nbr_cnt = st->rf.cnt;
+  a.nbr_off = st->rf.off;
+  a.nbr_cur = st->rf.cur;
+  a.nbr = st->rf.nbr;
+  a.bitmap = st->rf.bitmap;
+  a.ctr = st->rf.ctr;
+  CK(launch_refine_s(a, st->stream));
+  CK(cudaMemcpyAsync(st->h_rf, st->rf.ctr + kRefineDone, sizeof(int), cudaMemcpyDeviceToHost,
+                     st->stream));
+  CK(launch_extract_diag(st->S64, 0, ld, p, st->sdiag64, st->sdiagT, 1, st->flag, st->stream));
+  CK(launch_subdiag(st->S64, 0, ld, p, st->P, st->sd1_64, st->sd2_64, st->stream));
+  CK(launch_subdiag(st->S, 1, ld, p, st->P, st->sd1, st->sd2, st->stream));
+  return CONCORD_OK;
+}
+
 // mixed: FP32 iterate -> FP64 copies (Omega with its FP64 diagonal; W rebuilt
-// in FP64 from Omega and S)
-int promote_to_fp64(concord_state* st) {
+// in FP64 from Omega and S, after the S refinement when it applies)
+int promote_to_fp64(concord_state* st, double lambda, int list) {
+  *st->h_rf = 0;
+  if (st->refine && st->zt_valid) {
+    int rc = refine_s(st, lambda, list);
+    if (rc != CONCORD_OK) return rc;
+  }
   CK(launch_convert(st->Om, 1, st->ld, st->Om64, 0, st->ld, st->p, st->p, st->stream));
   CK(cudaMemcpy2DAsync(st->Om64, (size_t)(st->ld + 1) * sizeof(double), st->omdiag64,
                        sizeof(double), sizeof(double), st->p, cudaMemcpyDeviceToDevice,
@@ -794,7 +884,7 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
   }
   // ... then FP64 polishing from W rebuilt in FP64, its first sweep on the
   // candidate list the FP32 phase left (same lambda)
-  if ((rc = promote_to_fp64(st)) != CONCORD_OK) return rc;
+  if ((rc = promote_to_fp64(st, lambda, o1.next_list)) != CONCORD_OK) return rc;
   const int left = max_sweeps - o1.sweeps;
   st->start_list = left > 0 ? o1.next_list : -1;
   rc = launch_run<double>(st, st->S64, st->W64, st->Om64, st->sdiag64, nullptr, lambda, tol,
@@ -810,6 +900,7 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
   const int fd = o1.first_delta ? o1.first_delta : (o2.first_delta ? o1.sweeps + o2.first_delta : 0);
   o2.redos += o1.redos;
   o2.dense_sweeps += o1.dense_sweeps;
+  o2.s_refined = *st->h_rf;  // read back by the polish launch's synchronisation
   fill_result(res, o2, o1.sweeps + o2.sweeps, o1.sweeps, fd, lambda, ms * 1e-3);
   return rc != CONCORD_OK ? rc : o2.status;
 }
@@ -979,12 +1070,14 @@ int concord_create(concord_state** out, int p, int precision, int n_cap, int dev
       if (is_mixed(st)) {
         ALLOC(st->zt_hi, sizeof(float) * (size_t)st->n_pad * st->p_pad);
         ALLOC(st->zt_lo, sizeof(float) * (size_t)st->n_pad * st->p_pad);
+        ALLOC(st->zt32, sizeof(float) * (size_t)round_up(n_cap, 32) * st->p_pad);
       }
     }
     st->gram_mode = is_mixed(st) ? CONCORD_GRAM_TF32X3 : CONCORD_GRAM_FP64;
     if (cudaMallocHost((void**)&st->h_result, sizeof(double) * kRes) != cudaSuccess ||
         cudaMallocHost((void**)&st->h_abort, 3 * sizeof(int)) != cudaSuccess ||
-        cudaMallocHost((void**)&st->h_flag, sizeof(int)) != cudaSuccess) {
+        cudaMallocHost((void**)&st->h_flag, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost((void**)&st->h_rf, sizeof(int)) != cudaSuccess) {
       rc = fail(CONCORD_E_NOMEM, "cudaMallocHost failed");
       goto fail_out;
     }
@@ -1025,7 +1118,9 @@ int concord_destroy(concord_state* st) {
   if (st->stream) cudaStreamSynchronize(st->stream);
   void* dev[] = {st->path_lam, st->path_res, st->rows_dev, st->Wb, st->V, st->scr, st->sd1_64, st->sd2_64, st->mbox, st->barrier, st->abort_info, st->flag, st->lmax, st->partials,
                  st->hist, st->result, st->mean, st->inv_scale, st->Z, st->Xstage, st->zt_hi,
-                 st->zt_lo, st->sdiag64, st->sdiagT, st->omdiag64, st->S64, st->W64, st->Om64};
+                 st->zt_lo, st->sdiag64, st->sdiagT, st->omdiag64, st->S64, st->W64, st->Om64,
+                 st->zt32, st->rf.cnt, st->rf.off, st->rf.cur, st->rf.nbr, st->rf.ctr, st->rf.cand,
+                 st->rf.bitmap};
   for (void* d : dev)
     if (d) cudaFree(d);
   void* adj_dev[] = {st->adj.cnt, st->adj.rowptr, st->adj.bad, st->adj.col, st->adj.erow,
@@ -1048,6 +1143,7 @@ int concord_destroy(concord_state* st) {
   if (st->h_result) cudaFreeHost(st->h_result);
   if (st->h_abort) cudaFreeHost(st->h_abort);
   if (st->h_flag) cudaFreeHost(st->h_flag);
+  if (st->h_rf) cudaFreeHost(st->h_rf);
   if (st->ev0) cudaEventDestroy(st->ev0);
   if (st->ev1) cudaEventDestroy(st->ev1);
   for (int q = 0; q < 2 * kMaxTimedLaunches; ++q)
@@ -1091,6 +1187,7 @@ int concord_set_S(concord_state* st, const void* S_dev, int s_dtype, int lds) {
   if ((rc = read_flag(st, &bad))) return rc;
   if (bad & 2) return fail(CONCORD_E_NONFINITE, "S has a non-finite entry");
   if (bad & 1) return fail(CONCORD_E_ARG, "S is not symmetric");
+  st->zt_valid = false;  // no data behind this S: nothing to refine from
   CK(launch_convert(S_dev, f32, lds, st->S64, 0, ld, p, p, st->stream));
   if (is_mixed(st)) CK(launch_convert(S_dev, f32, lds, st->S, 1, ld, p, p, st->stream));
   return reset_iterate(st);
@@ -1343,6 +1440,13 @@ int concord_set_rows_per_warp(concord_state* st, int rows) {
   return CONCORD_OK;
 }
 
+int concord_set_refine(concord_state* st, int on) {
+  if (!st) return fail(CONCORD_E_ARG, "state is NULL");
+  if (on != 0 && on != 1) return fail(CONCORD_E_ARG, "on must be 0 or 1");
+  st->refine = on == 1;
+  return CONCORD_OK;
+}
+
 int concord_set_gram_mode(concord_state* st, int mode) {
   if (!st) return fail(CONCORD_E_ARG, "state is NULL");
   if (mode != CONCORD_GRAM_FP64 && mode != CONCORD_GRAM_FP32 && mode != CONCORD_GRAM_TF32X3 &&
@@ -1361,6 +1465,12 @@ static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, i
   // the FP64 W (free until the iterate is reset below) holds the column partials
   CK(launch_col_stats_chunked(X, x_f32, n, p, ldx, prep, st->mean, st->inv_scale, st->flag,
                               st->W64, st->stream));
+  // the reduced-precision Grams keep the FP32 data (transposed) for the S
+  // refinement of a later polish; the FP64 Gram is exact already
+  st->zt_valid = false;
+  st->zt_n = n;
+  st->zt_ldn = round_up(n, 32);
+  float* zt = (st->zt32 && is_mixed(st)) ? st->zt32 : nullptr;
   switch (st->gram_mode) {
     case CONCORD_GRAM_FP64:
       if (is_mixed(st)) {
@@ -1382,11 +1492,17 @@ static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, i
       CK(launch_apply_prep(X, x_f32, n, p, ldx, st->mean, st->inv_scale, Zf, 1, st->ldz, st->stream));
       CK(launch_syrk_f32(Zf, n, p, st->ldz, (float*)st->S, ld, 1.0f / n, st->stream));
       CK(launch_convert(st->S, 1, ld, st->S64, 0, ld, p, p, st->stream));
+      if (zt) {
+        CK(launch_split_tf32(X, x_f32, n, p, ldx, st->mean, st->inv_scale, nullptr, nullptr,
+                             st->zt_ldn, st->p_pad, st->stream, zt, st->zt_ldn));
+        st->zt_valid = true;
+      }
       break;
     }
     case CONCORD_GRAM_TF32X3: {
       CK(launch_split_tf32(X, x_f32, n, p, ldx, st->mean, st->inv_scale, st->zt_hi, st->zt_lo,
-                           round_up(n, 32), st->p_pad, st->stream));
+                           round_up(n, 32), st->p_pad, st->stream, zt, st->zt_ldn));
+      st->zt_valid = zt != nullptr;
       cudaError_t e = launch_gram_tf32x3(st->zt_hi, st->zt_lo, round_up(n, 32), st->p_pad, p,
                                          (float*)st->S, ld, 1.0f / n, st->flag, st->stream);
       if (e == cudaErrorNotSupported) return fail(CONCORD_E_CUDA, "tensor-core Gram unavailable");
@@ -1398,7 +1514,8 @@ static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, i
       uint16_t* hi = (uint16_t*)st->zt_hi;
       uint16_t* lo = (uint16_t*)st->zt_lo;
       CK(launch_split_bf16(X, x_f32, n, p, ldx, st->mean, st->inv_scale, hi, lo, round_up(n, 64),
-                           st->p_pad, st->stream));
+                           st->p_pad, st->stream, zt, st->zt_ldn));
+      st->zt_valid = zt != nullptr;
       cudaError_t e = launch_gram_bf16x3(hi, lo, round_up(n, 64), st->p_pad, p, (float*)st->S, ld,
                                          1.0f / n, st->flag, st->stream);
       if (e == cudaErrorNotSupported) return fail(CONCORD_E_CUDA, "tensor-core Gram unavailable");

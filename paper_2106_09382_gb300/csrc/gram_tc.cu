@@ -43,15 +43,19 @@ __device__ __forceinline__ float to_tf32(float x) {
 
 // Standardize, split and transpose: zt_hi[i * n_pad + k] = tf32(z_ki),
 // zt_lo[i * n_pad + k] = tf32(z_ki - hi) with z = (x - mean_i) * inv_scale_i
-// rounded to FP32.  32 x 32 tiles through shared memory; padding is zero.
+// rounded to FP32; when zt is given, also zt[i * ldz + k] = z (k < ldz).
+// hi / lo may be NULL (zt only).  32 x 32 tiles through shared memory;
+// padding is zero.
 template <typename TX>
 __global__ void __launch_bounds__(256) k_split_tf32(const TX* __restrict__ X, int n, int p, int ldx,
                                                     const double* __restrict__ mean,
                                                     const double* __restrict__ inv_scale,
                                                     float* __restrict__ hi, float* __restrict__ lo,
-                                                    int n_pad, int p_pad) {
+                                                    int n_pad, int p_pad, float* __restrict__ zt,
+                                                    int ldz) {
   __shared__ float th[32][33];
   __shared__ float tl[32][33];
+  __shared__ float tz[32][33];
   const int k0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int r = ty; r < 32; r += 8) {
@@ -61,42 +65,45 @@ __global__ void __launch_bounds__(256) k_split_tf32(const TX* __restrict__ X, in
     const float h = to_tf32(z);
     th[r][tx] = h;
     tl[r][tx] = to_tf32(z - h);
+    tz[r][tx] = z;
   }
   __syncthreads();
   for (int r = ty; r < 32; r += 8) {
     const int i = i0 + r, k = k0 + tx;
-    if (i < p_pad && k < n_pad) {
+    if (i < p_pad && k < n_pad && hi) {
       hi[(size_t)i * n_pad + k] = th[tx][r];
       lo[(size_t)i * n_pad + k] = tl[tx][r];
     }
+    if (zt && i < p_pad && k < ldz) zt[(size_t)i * ldz + k] = tz[tx][r];
   }
 }
 
 cudaError_t launch_split_tf32(const void* X, int x_f32, int n, int p, int ldx, const double* mean,
                               const double* inv_scale, float* zt_hi, float* zt_lo, int n_pad,
-                              int p_pad, cudaStream_t st) {
+                              int p_pad, cudaStream_t st, float* zt, int ldz) {
   dim3 grid((n_pad + 31) / 32, (p_pad + 31) / 32);
   if (x_f32)
     k_split_tf32<float><<<grid, 256, 0, st>>>((const float*)X, n, p, ldx, mean, inv_scale, zt_hi,
-                                              zt_lo, n_pad, p_pad);
+                                              zt_lo, n_pad, p_pad, zt, ldz);
   else
     k_split_tf32<double><<<grid, 256, 0, st>>>((const double*)X, n, p, ldx, mean, inv_scale, zt_hi,
-                                               zt_lo, n_pad, p_pad);
+                                               zt_lo, n_pad, p_pad, zt, ldz);
   note_launches(1);
   return cudaGetLastError();
 }
 
 // The same for the bf16 split: hi = bf16(z), lo = bf16(z - hi), both as raw
-// 16-bit patterns.
+// 16-bit patterns; zt as in k_split_tf32.
 template <typename TX>
 __global__ void __launch_bounds__(256) k_split_bf16(const TX* __restrict__ X, int n, int p, int ldx,
                                                     const double* __restrict__ mean,
                                                     const double* __restrict__ inv_scale,
                                                     uint16_t* __restrict__ hi,
                                                     uint16_t* __restrict__ lo, int n_pad,
-                                                    int p_pad) {
+                                                    int p_pad, float* __restrict__ zt, int ldz) {
   __shared__ uint16_t th[32][34];
   __shared__ uint16_t tl[32][34];
+  __shared__ float tz[32][33];
   const int k0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int r = ty; r < 32; r += 8) {
@@ -106,6 +113,7 @@ __global__ void __launch_bounds__(256) k_split_bf16(const TX* __restrict__ X, in
     const __nv_bfloat16 h = __float2bfloat16_rn(z);
     th[r][tx] = __bfloat16_as_ushort(h);
     tl[r][tx] = __bfloat16_as_ushort(__float2bfloat16_rn(z - __bfloat162float(h)));
+    tz[r][tx] = z;
   }
   __syncthreads();
   for (int r = ty; r < 32; r += 8) {
@@ -114,19 +122,20 @@ __global__ void __launch_bounds__(256) k_split_bf16(const TX* __restrict__ X, in
       hi[(size_t)i * n_pad + k] = th[tx][r];
       lo[(size_t)i * n_pad + k] = tl[tx][r];
     }
+    if (zt && i < p_pad && k < ldz) zt[(size_t)i * ldz + k] = tz[tx][r];
   }
 }
 
 cudaError_t launch_split_bf16(const void* X, int x_f32, int n, int p, int ldx, const double* mean,
                               const double* inv_scale, uint16_t* zt_hi, uint16_t* zt_lo, int n_pad,
-                              int p_pad, cudaStream_t st) {
+                              int p_pad, cudaStream_t st, float* zt, int ldz) {
   dim3 grid((n_pad + 31) / 32, (p_pad + 31) / 32);
   if (x_f32)
     k_split_bf16<float><<<grid, 256, 0, st>>>((const float*)X, n, p, ldx, mean, inv_scale, zt_hi,
-                                              zt_lo, n_pad, p_pad);
+                                              zt_lo, n_pad, p_pad, zt, ldz);
   else
     k_split_bf16<double><<<grid, 256, 0, st>>>((const double*)X, n, p, ldx, mean, inv_scale, zt_hi,
-                                               zt_lo, n_pad, p_pad);
+                                               zt_lo, n_pad, p_pad, zt, ldz);
   note_launches(1);
   return cudaGetLastError();
 }

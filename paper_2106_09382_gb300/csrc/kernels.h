@@ -212,10 +212,12 @@ cudaError_t launch_scale_f32(float* a, size_t n, float s, cudaStream_t st);
 
 // ---- tensor-core Gram (gram_tc.cu)
 // Splits each standardized element into tf32 hi + lo and writes them
-// transposed: Zt_hi / Zt_lo are p_pad x n_pad (K-major), zero padded.
+// transposed: Zt_hi / Zt_lo are p_pad x n_pad (K-major), zero padded.  With
+// zt (nullable) the FP32 value itself is also written transposed
+// (p_pad x ldz, ldz <= n_pad); hi / lo may be NULL when zt is given.
 cudaError_t launch_split_tf32(const void* X, int x_f32, int n, int p, int ldx, const double* mean,
                               const double* inv_scale, float* zt_hi, float* zt_lo, int n_pad,
-                              int p_pad, cudaStream_t st);
+                              int p_pad, cudaStream_t st, float* zt = nullptr, int ldz = 0);
 // S (p x lds, FP32) = (hi hi^T + hi lo^T + lo hi^T) * scale with tcgen05.mma
 // kind::tf32 (n_pad a multiple of 32, p_pad of 128).  A device-side wait that
 // runs out sets bit 4 of *status.  cudaErrorNotSupported if not sm_103.
@@ -225,7 +227,34 @@ cudaError_t launch_gram_tf32x3(const float* zt_hi, const float* zt_lo, int n_pad
 // n_pad a multiple of 64) and the Gram with tcgen05.mma kind::f16 (3xBF16).
 cudaError_t launch_split_bf16(const void* X, int x_f32, int n, int p, int ldx, const double* mean,
                               const double* inv_scale, uint16_t* zt_hi, uint16_t* zt_lo, int n_pad,
-                              int p_pad, cudaStream_t st);
+                              int p_pad, cudaStream_t st, float* zt = nullptr, int ldz = 0);
+
+// ---- FP64-accurate S on the solution's neighbourhood (refine.cu)
+// Pairs collected from a dense iterate: w_ij != 0 or |G_ij| > (1 - margin)
+// lambda (the screen's margin).
+constexpr double kRefineMargin = 0.1;
+constexpr int kRefineDone = 0;     // ctr: entries recomputed
+constexpr int kRefineOwn = 1;      // ctr: length of the collected list (no candidate list given)
+constexpr int kRefineDropped = 2;  // ctr: collected pairs that did not fit
+constexpr int kRefineCtrs = 4;
+struct RefineArgs {
+  int p, ld, n, ldn, sms;
+  const float* zt;           // p_pad x ldn: standardized data in FP32, transposed
+  const int2* cand;          // candidate pairs (i < j) of the next sweep, or NULL
+  const int* n_cand;         // device: their number
+  const float *Om32, *W32;   // the FP32 iterate (to collect pairs when cand is NULL)
+  float thr;                 // collection threshold on |W_ij + W_ji|
+  int2* own_cand;            // [own_cap] collected pairs
+  int own_cap;
+  double* S64;               // p x ld: entries recomputed in place (both triangles)
+  float* S32;                // p x ld: the same entries rounded to FP32
+  int *nbr_cnt, *nbr_off, *nbr_cur;  // [p + 1]
+  int* nbr;                  // [2 x max(list length)]
+  unsigned* bitmap;          // [refine_bitmap_words(p)]
+  int* ctr;                  // [kRefineCtrs]
+};
+size_t refine_bitmap_words(int p);
+cudaError_t launch_refine_s(const RefineArgs& a, cudaStream_t st);
 cudaError_t launch_gram_bf16x3(const uint16_t* zt_hi, const uint16_t* zt_lo, int n_pad, int p_pad,
                                int p, float* S, int lds, float scale, int* status, cudaStream_t st);
 

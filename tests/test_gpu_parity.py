@@ -575,3 +575,75 @@ def test_omega_csr_readout(precision):
         with pytest.raises(C.ConcordError) as e:
             st.get_omega_csr(cap=3)
         assert e.value.code == C.E_ARG
+
+
+# ------------------------------------------ the benchmark configuration itself
+def _exact_S(X):
+    """The oracle's S = Z^T Z / n (the threaded Gram of the oracle's
+    maintained-product mode: the same sums as its triple loop)."""
+    return O.gram_w(O.standardize(X))
+
+
+@pytest.mark.parametrize("p", [5000, 4999])
+def test_benchmark_configuration_matches_oracle(p):
+    """The timed configuration, unchanged: a mixed state with its default
+    Gram (3xTF32 on tensor cores), FP32 screened sweeps, the S refinement and
+    the FP64 polish, solved from X to KKT <= 1e-5.  Against the oracle's
+    solution of the same data (the recorded p = 5000 solve, a live solve of
+    the oracle's maintained-product mode at p = 4999), with the objective and
+    the KKT residual of the GPU's Omega evaluated by the oracle on the exact
+    S.  Both solutions stop at KKT <= 1e-5 from different trajectories, so
+    Omega agrees to the distance between two such points, which the
+    tolerance of the FP64 path (1e-6 relative) covers."""
+    w = synth.workload_ar1(p=p, n=2000, seed=0)
+    lam = w["lam"]
+    S = _exact_S(w["X"])
+    if p == 5000:
+        rec, ij, v = _golden(5000)
+        ref = np.zeros((p, p))
+        ref[ij[:, 0], ij[:, 1]] = v
+        ref = ref + np.triu(ref, 1).T
+        obj_ref = rec["objective"]
+    else:
+        ref, info = O.solve_w(S, lam, tol=1e-5, max_sweeps=200)
+        assert info["converged"]
+        obj_ref = info["objective"]
+    with C.State(p, C.MIXED, n_cap=2000) as st:
+        r = st.solve_device(dev(w["X"]), lam, tol=1e-5, max_sweeps=200)
+        G = host(st.get_omega())
+    assert r.status == C.OK and r.kkt <= 1e-5 and r.s_refined > p
+    scale = np.abs(ref).max()
+    assert np.abs(G - ref).max() <= 1e-6 * scale
+    f = O.objective(S, G, lam)
+    assert abs(f - obj_ref) <= 1e-7 * abs(obj_ref), (f, obj_ref)
+    assert O.kkt(S, G, lam) <= 1e-5
+    diff = (G != 0) != (ref != 0)
+    small = (np.abs(G) <= 1e-6 * scale) & (np.abs(ref) <= 1e-6 * scale)
+    assert not (diff & ~small).any()
+
+
+@pytest.mark.parametrize("mode", [C.GRAM_TF32X3, C.GRAM_BF16X3, C.GRAM_FP32])
+def test_refined_mixed_solve_matches_oracle_tightly(mode):
+    """With the S refinement the polish solves the exact problem: the mixed
+    solve from a reduced-precision Gram lands on the oracle's solution for
+    the exact S to within the FP32 rounding of the data (relative 2^-24 per
+    element, random), far inside the bound of the unrefined solve (20 x the
+    Gram's error bound)."""
+    w = synth.workload_small()
+    X = w["X"]
+    S = O.gram(O.standardize(X))
+    Om_or, info = O.solve(S, w["lam"], tol=1e-10, max_sweeps=5000)
+    with C.State(X.shape[1], C.MIXED, n_cap=X.shape[0]) as st:
+        st.set_gram_mode(mode)
+        r = st.solve_device(dev(X), w["lam"], tol=1e-10, max_sweeps=2000)
+        G = host(st.get_omega())
+        assert r.status == C.OK and r.s_refined > 0
+        st.set_refine(False)
+        r0 = st.solve_device(dev(X), w["lam"], tol=1e-10, max_sweeps=2000)
+        G0 = host(st.get_omega())
+        assert r0.s_refined == 0
+    scale = np.abs(Om_or).max()
+    err, err0 = np.abs(G - Om_or).max() / scale, np.abs(G0 - Om_or).max() / scale
+    assert err <= 1e-7, err
+    assert err < err0
+    assert abs(O.objective(S, G, w["lam"]) - info["objective"]) <= 1e-12 * info["objective"]
