@@ -8,8 +8,10 @@ whole solve from the data X resident in HBM: standardize + Gram + edge-
 coloured sweeps until the KKT residual <= 1e-5 (mixed precision: FP32 sweeps
 then FP64 polishing).  Reported beside it: the plain FP64 GPU solve, the
 sweep kernel's updates/s and roofline, a full-update bandwidth microbench,
-an end-to-end number through host buffers, clocks, and the CPU oracle's
-time estimated from a bounded sample.
+an end-to-end number through host buffers, clocks, the odd-p (4999) solve,
+and the CPU oracle timed on one whole solve of the same workload on all host
+cores (its maintained-product mode), whose solution also gives the GPU
+results' error against the oracle.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank solves its own replica; rank 0 prints one JSON line.
@@ -57,11 +59,13 @@ def parse_args(argv=None):
                     help="run one extra section alone (one GPU) and print its JSON")
     ap.add_argument("--no-joint", action="store_true",
                     help="skip the joint two-population section")
+    ap.add_argument("--no-odd", action="store_true",
+                    help="skip the odd-p (p - 1 = 4999) mixed solve")
     ap.add_argument("--no-path", action="store_true",
                     help="skip the regularisation-path / stability-selection section")
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the default sweep kernel without the variant trials")
-    ap.add_argument("--cpu-budget", type=float, default=20.0,
+    ap.add_argument("--cpu-budget", type=float, default=4.0,
                     help="seconds of oracle work for the CPU baseline sample")
     return ap.parse_args(argv)
 
@@ -150,6 +154,20 @@ def screened_sweep_bytes(p: int, b: int, changed: float) -> float:
     return p * p * b * (4.0 + 2.5) + 2.0 * changed * p * b
 
 
+def s8d_sweep_bytes(p: int, b: int, changed: float) -> float:
+    """Algorithmic bytes of one sweep by the scope table's formula, all
+    element sizes b: five scalar reads per pair (w_ij, W_ij, W_ji, s_ii,
+    s_jj), per changed pair two S rows read and two W rows read and written,
+    per diagonal update one S row read and one W row read and written, and
+    W and Omega read once by the convergence test."""
+    pairs = p * (p - 1) // 2
+    return pairs * 5.0 * b + changed * p * 6.0 * b + p * p * 3.0 * b + p * p * 2.0 * b
+
+
+def s8d_launch_bytes(p: int, b: int, hist_rows) -> float:
+    return float(sum(s8d_sweep_bytes(p, b, h[3]) for h in hist_rows))
+
+
 def launch_bytes(p: int, b: int, hist_rows, screened: bool = False) -> float:
     f = screened_sweep_bytes if screened else sweep_bytes
     return float(sum(f(p, b, h[3]) for h in hist_rows))
@@ -195,9 +213,39 @@ def profiled_traffic(variant: str):
 
 
 # ------------------------------------------------------------ CPU baseline
-def cpu_baseline(X: np.ndarray, lam: float, sweeps: int, budget: float, sweeps_src: str):
-    """The oracle (single-threaded C, FP64, Eq. 3 as direct sums) timed on a
-    bounded sample of the same workload and scaled to a whole solve."""
+def host_cpu() -> dict:
+    """CPU model and logical core count of this host."""
+    import platform
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"cpu_model": model or platform.processor() or platform.machine(),
+            "nproc": os.cpu_count()}
+
+
+def oracle_whole_solve(X: np.ndarray, lam: float, tol: float, max_sweeps: int):
+    """One whole solve by the oracle's maintained-product mode (FP64, the
+    pairs of each colour on all host threads): standardize, Gram, sweeps to
+    KKT <= tol.  Returns (S, Omega, info, gram seconds, sweep seconds)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    S = O.gram_w(O.standardize(X))
+    t1 = time.perf_counter()
+    Om, info = O.solve_w(S, lam, tol=tol, max_sweeps=max_sweeps)
+    t2 = time.perf_counter()
+    return S, Om, info, t1 - t0, t2 - t1
+
+
+def definition_mode_estimate(X: np.ndarray, lam: float, sweeps: int, budget: float):
+    """The definition mode (single thread, Eq. 3 as direct sums) timed on a
+    bounded sample of the same workload and scaled to a whole solve: a
+    secondary, extrapolated figure beside the measured baseline."""
     import oracle as O
     n, p = X.shape
     Z = O.standardize(X)
@@ -205,7 +253,7 @@ def cpu_baseline(X: np.ndarray, lam: float, sweeps: int, budget: float, sweeps_s
     t0 = time.perf_counter()
     O.gram(Z[:, :m])
     t_gram = (time.perf_counter() - t0) * (p / m) ** 2
-    S = Z.T @ Z / n  # input for the timing sample only
+    S = O.gram_w(Z)
     pairs = O.schedule(p)
     Om = np.eye(p)
     t0 = time.perf_counter()
@@ -219,14 +267,48 @@ def cpu_baseline(X: np.ndarray, lam: float, sweeps: int, budget: float, sweeps_s
     O.diag_step(S, Om)
     t_diag = time.perf_counter() - t0
     per_sweep = per_colour * pairs.shape[0] + t_diag
-    total = t_gram + sweeps * per_sweep
-    upd = p * (p + 1) / 2 / per_sweep
-    return {"value": total, "unit": "s", "cores": 1, "kind": "oracle",
+    return {"value": t_gram + sweeps * per_sweep, "unit": "s", "cores": 1,
+            "kind": "oracle (definition mode), extrapolated",
             "sample": ("Gram on %d of %d columns (x%.0f); %d of %d colour steps + 1 diagonal "
-                       "step at p=%d; x %d sweeps (%s)") % (m, p, (p / m) ** 2, k,
-                                                             pairs.shape[0], p, sweeps,
-                                                             sweeps_src),
-            "seconds_per_sweep": per_sweep, "updates_per_s": upd}
+                       "step; x %d sweeps") % (m, p, (p / m) ** 2, k, pairs.shape[0], sweeps),
+            "seconds_per_sweep": per_sweep}
+
+
+def cpu_baseline(X: np.ndarray, lam: float, tol: float, max_sweeps: int, budget: float):
+    """The timed CPU baseline: one whole oracle solve of the workload on all
+    host cores (no extrapolation), plus the single-thread definition-mode
+    estimate.  Returns (baseline dict, S, Omega, info) so the GPU results can
+    be checked against the same solve."""
+    n, p = X.shape
+    S, Om, info, t_gram, t_solve = oracle_whole_solve(X, lam, tol, max_sweeps)
+    sw = max(1, info["sweeps"])
+    base = {"value": t_gram + t_solve, "unit": "s", "cores": info["threads"], "kind": "oracle",
+            "sample": ("one whole solve, p=%d, n=%d, lambda=%g, KKT<=%g: standardize + Gram + "
+                       "%d sweeps (maintained-product mode, pairs of a colour on %d threads)")
+                      % (p, n, lam, tol, info["sweeps"], info["threads"]),
+            "gram_seconds": t_gram, "sweep_seconds": t_solve,
+            "seconds_per_sweep": t_solve / sw, "sweeps": info["sweeps"],
+            "kkt": info["kkt"], "objective": info["objective"],
+            "updates_per_s": sw * p * (p + 1) / 2 / max(t_solve, 1e-12)}
+    base.update(host_cpu())
+    if budget > 0:
+        base["definition_mode_estimate"] = definition_mode_estimate(X, lam, info["sweeps"],
+                                                                    budget)
+    return base, S, Om, info
+
+
+def accuracy_vs_oracle(S: np.ndarray, Om_ref: np.ndarray, obj_ref: float, lam: float,
+                       Om: np.ndarray) -> dict:
+    """A GPU solution against the oracle's solution of the same data: Omega
+    (relative to max |Omega_ref|), and its objective and KKT residual
+    evaluated by the oracle on the exact S."""
+    import oracle as O
+    scale = float(np.abs(Om_ref).max())
+    f = O.objective(S, Om, lam)
+    return {"omega_rel": float(np.abs(Om - Om_ref).max()) / scale,
+            "objective_on_exact_S": f, "objective_rel": abs(f - obj_ref) / abs(obj_ref),
+            "kkt_on_exact_S": O.kkt(S, Om, lam),
+            "support_entries_differing": int(np.count_nonzero((Om != 0) != (Om_ref != 0)))}
 
 
 def joint_cpu_baseline(w: dict, sweeps: int, sweeps_src: str):
@@ -250,15 +332,6 @@ def joint_cpu_baseline(w: dict, sweeps: int, sweeps_src: str):
             "seconds_per_sweep": per_sweep, "gram_seconds": t_gram}
 
 
-def golden_sweeps(p: int):
-    path = os.path.join(ROOT, "oracle", "golden", "ar1_p%d.json" % p)
-    try:
-        with open(path) as f:
-            return int(json.load(f)["sweeps"]), "oracle solve record"
-    except Exception:
-        return None, None
-
-
 # ------------------------------------------------------------------ arms
 def reduce_max(v: float, world: int, device=None) -> float:
     """Max of a per-rank scalar over the process group (identity at world 1)."""
@@ -279,31 +352,66 @@ def dist_setup(args):
 
 
 def run_reference(args):
+    """The reference arm: the oracle (FP64 C, its maintained-product mode on
+    all host cores), one whole solve of the benchmark workload per step."""
     world, rank, local = dist_setup(args)
     if rank != 0:
         return
     from paper_2106_09382_gb300 import synth
     w = synth.workload_ar1(args.p, args.n, 0)
-    sweeps, src = golden_sweeps(args.p)
-    if sweeps is None:
-        sweeps, src = 1, "no oracle solve record: one sweep, a lower bound"
-    vals = []
-    base = None
+    X = np.ascontiguousarray(w["X"])
+    vals, info = [], None
     for s in range(args.warmup + args.steps):
-        base = cpu_baseline(w["X"], args.lam, sweeps, max(2.0, args.cpu_budget / 4), src)
+        _, _, info, tg, ts = oracle_whole_solve(X, args.lam, args.tol, args.max_sweeps)
         if s >= args.warmup:
-            vals.append(base["value"])
+            vals.append(tg + ts)
     v = statistics.mean(vals)
-    base["value"] = v
+    base = {"value": v, "unit": "s", "cores": info["threads"], "kind": "oracle",
+            "sample": ("whole solves, p=%d, n=%d: standardize + Gram + %d sweeps to KKT<=%g "
+                       "(maintained-product mode, pairs of a colour on %d threads)")
+                      % (args.p, args.n, info["sweeps"], args.tol, info["threads"]),
+            "sweeps": info["sweeps"], "kkt": info["kkt"], "objective": info["objective"],
+            "step_seconds": vals}
+    base.update(host_cpu())
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic",
+           "data": "synthetic (seeded AR(1)+extras Gaussian data)",
            "config": {"workload": "AR(1)+1%% extra edges, p=%d, n=%d, lambda=%g, KKT<=%g"
-                      % (args.p, args.n, args.lam, args.tol), "p": args.p, "n": args.n},
+                      % (args.p, args.n, args.lam, args.tol), "p": args.p, "n": args.n,
+                      "lambda": args.lam, "tol": args.tol},
            "cpu_baseline": base,
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def run_odd_p_section(C, synth, dev, stream, flush, p, n, lam, tol, max_sweeps, steps):
+    """The mixed solve at odd p (one vertex sits out each colour step), timed
+    like the headline (data resident, L2 flushed between steps)."""
+    import torch
+    w = synth.workload_ar1(p, n, seed=0)
+    X = torch.as_tensor(np.ascontiguousarray(w["X"]), device=dev)
+    st = C.State(p, C.MIXED, n_cap=n, device=dev.index)
+    st.set_stream(stream)
+    for _ in range(2):
+        st.solve_device(X, lam, tol=tol, max_sweeps=max_sweeps)
+    times = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = st.solve_device(X, lam, tol=tol, max_sweeps=max_sweeps)
+        e1.record(stream)
+        stream.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    tim = st.timing()
+    st.close()
+    return {"workload": "AR(1)+1%% extra edges, p=%d, n=%d, lambda=%g, KKT<=%g" % (p, n, lam, tol),
+            "seconds": statistics.mean(times), "step_seconds": times, "sweeps": r.sweeps,
+            "sweeps_fp32": r.sweeps_fp32, "kkt": r.kkt, "objective": r.objective,
+            "status": r.status, "launch_ms": tim}
 
 
 def run_path_section(C, synth, dev, stream, p=1000, n=800, n_lambda=32, n_sub=8, workers=8):
@@ -707,7 +815,8 @@ def run_ours(args):
     h32 = hist_last[:sw32]
     hbm_peak, peak_src = load_peaks()
     screened = rows_best.startswith("screened")
-    bytes32 = launch_bytes(p, 4, h32, screened)
+    bytes32 = s8d_launch_bytes(p, 4, h32)
+    model32 = launch_bytes(p, 4, h32, screened)
     achieved = bytes32 / (ms32 * 1e-3) / 1e9
     updates = p * (p + 1) / 2
     ups = sw32 * updates / (ms32 * 1e-3)
@@ -716,6 +825,13 @@ def run_ours(args):
     tps = profiled_traffic(vname)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": None if tps is None else tps * sw32,
+                "bytes_source": ("scope-table formula per sweep: 5 scalar reads per pair, "
+                                 "6 rows per changed pair, 3 rows per diagonal update, "
+                                 "W and Omega once; x the launch's sweeps"),
+                "frac_design_model": model32 / (ms32 * 1e-3) / 1e9 / hbm_peak,
+                "design_model_bytes_per_launch": model32,
+                "frac_dram_measured": (None if tps is None else
+                                       tps * sw32 / (ms32 * 1e-3) / 1e9 / hbm_peak),
                 "traffic_source": ("ncu DRAM bytes per sweep of the same kernel source and "
                                    "variant x sweeps of this launch" if tps is not None else
                                    "no ncu capture of the current kernel source / variant"),
@@ -772,7 +888,8 @@ def run_ours(args):
             "max_abs_dOmega_rel": float(np.abs(Om_mix - Om_64).max()) / scale,
             "objective_rel": abs(r_last["objective"] - r64["objective"]) / abs(r64["objective"]),
             "support_entries_differing": supp_diff,
-            "note": "mixed uses the tensor-core (3xTF32) Gram; FP64 uses the FP64 Gram"}
+            "note": ("mixed uses the tensor-core (3xTF32) Gram with the S refinement; FP64 "
+                     "uses the FP64 Gram; each objective on its own S")}
         fp64_sweeps = r64["sweeps"]
         if not args.no_gram_study:
             out["gram_variants"] = run_gram_study(C, X, lam, tol, dev, stream, st64.get_omega(),
@@ -847,12 +964,24 @@ def run_ours(args):
         if not args.no_joint:
             out["joint"] = run_joint_section(C, synth, dev, stream, hbm_peak,
                                              with_oracle=(rank == 0))
-        # ---------------- CPU oracle, bounded sample (rank 0 only)
+        # ---------------- odd p: the bye-vertex schedule at p = 4999
+        if not args.no_odd:
+            out["odd_p"] = run_odd_p_section(C, synth, dev, stream, flush, p - 1, n, lam, tol,
+                                             args.max_sweeps, max(1, min(args.steps, 3)))
+        # ---------------- CPU oracle: one whole solve on all host cores (rank 0
+        #                  only); its solution gives the GPU results' error
         if rank == 0:
-            gs, src = golden_sweeps(p)
-            if gs is None:
-                gs, src = fp64_sweeps, "sweeps of the FP64 GPU solve on the same data"
-            out["cpu_baseline"] = cpu_baseline(Xh, lam, gs, args.cpu_budget, src)
+            base, S_or, Om_or, info_or = cpu_baseline(Xh, lam, tol, args.max_sweeps,
+                                                      args.cpu_budget)
+            out["cpu_baseline"] = base
+            out["accuracy_vs_oracle"] = {
+                "mixed": accuracy_vs_oracle(S_or, Om_or, info_or["objective"], lam, Om_mix),
+                "fp64": accuracy_vs_oracle(S_or, Om_or, info_or["objective"], lam, Om_64),
+                "oracle": {"sweeps": info_or["sweeps"], "kkt": info_or["kkt"],
+                           "objective": info_or["objective"]},
+                "note": ("both GPU solutions against the oracle's solve of the same data "
+                         "(maintained-product mode, FP64); objective and KKT of the GPU "
+                         "Omega evaluated by the oracle on the exact S")}
         st64.close()
     st.close()
     if rank == 0:

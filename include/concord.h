@@ -641,6 +641,14 @@ int concord_joint_set_grid(concord_joint *jt, int ctas);
                                      flags, release / acquire) */
 #define CONCORD_JOINT_BARRIER 1   /* one grid-wide barrier per colour step */
 int concord_joint_set_variant(concord_joint *jt, int variant);
+/* Failure-detection testing (CONCORD_JOINT_ROWFLAGS only): row >= 0 makes
+ * that row skip publishing its version at colour step `step` of the next
+ * launch (counted from the launch's first colour step over all its sweeps),
+ * so the wait of the pair that reads the row next runs out at the state's
+ * timeout: CONCORD_E_TIMEOUT with that row and colour step in
+ * timeout_vertex / timeout_step of the result.  One-shot; row < 0 clears
+ * it.  No kernel faults, traps or hangs.  Errors: CONCORD_E_ARG. */
+int concord_joint_set_fault(concord_joint *jt, int row, int step);
 
 /* Copies S of population m (0 or 1; p x p, element type s_dtype, row stride
  * lds) into the state and resets Omega_m to I (W_m = S_m).  Synchronises.

@@ -117,6 +117,7 @@ SIGNATURES = {
     "concord_joint_set_timeout": ([_vp, _cd], _ci),
     "concord_joint_set_grid": ([_vp, _ci], _ci),
     "concord_joint_set_variant": ([_vp, _ci], _ci),
+    "concord_joint_set_fault": ([_vp, _ci, _ci], _ci),
     "concord_joint_set_S": ([_vp, _ci, _vp, _ci, _ci], _ci),
     "concord_joint_set_omega": ([_vp, _ci, _vp, _ci, _ci], _ci),
     "concord_joint_get_omega": ([_vp, _ci, _vp, _ci, _ci], _ci),
@@ -563,6 +564,11 @@ class Joint:
 
     def set_variant(self, variant: int):
         _check(load().concord_joint_set_variant(self._ptr, int(variant)))
+
+    def set_fault(self, row: int, step: int = 0):
+        """Failure testing: `row` skips publishing its version at colour step
+        `step` of the next launch (concord_joint_set_fault)."""
+        _check(load().concord_joint_set_fault(self._ptr, int(row), int(step)))
 
     def set_S(self, m: int, S):
         assert S.is_cuda and S.dim() == 2 and S.stride(1) == 1

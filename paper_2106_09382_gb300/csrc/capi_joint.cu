@@ -58,6 +58,7 @@ struct concord_joint {
   double* result = nullptr;
   double* h_result = nullptr;  // pinned: kJRes doubles, then 3 ints of abort info, then bad
   double timeout_s = 2.0;
+  int fault_row = -1, fault_step = -1;  // one-shot failure-testing switch
   int grid_override = 0;
   int hist_rows = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -138,6 +139,9 @@ int run_phase(concord_joint* jt, bool f32, double l1, double l2, double tol, int
   w.info = jt->abort_info + 1;
   w.timeout_ns = (uint64_t)(jt->timeout_s * 1e9);
   const int hist_left = kJHistCap - jt->hist_rows;
+  const int fault_row = rv ? jt->fault_row : -1, fault_step = rv ? jt->fault_step : -1;
+  jt->fault_row = -1;  // one-shot
+  jt->fault_step = -1;
   if (f32) {
     JointArgs<float> a{};
     a.p = jt->p;
@@ -158,6 +162,8 @@ int run_phase(concord_joint* jt, bool f32, double l1, double l2, double tol, int
     a.barrier = jt->barrier;
     a.row_ver = rv;
     a.wait = w;
+    a.fault_row = fault_row;
+    a.fault_step = fault_step;
     a.partials = jt->partials;
     a.hist = jt->hist + (size_t)jt->hist_rows * kJHist;
     a.hist_len = hist_left > 0 ? hist_left : 0;
@@ -183,6 +189,8 @@ int run_phase(concord_joint* jt, bool f32, double l1, double l2, double tol, int
     a.barrier = jt->barrier;
     a.row_ver = rv;
     a.wait = w;
+    a.fault_row = fault_row;
+    a.fault_step = fault_step;
     a.partials = jt->partials;
     a.hist = jt->hist + (size_t)jt->hist_rows * kJHist;
     a.hist_len = hist_left > 0 ? hist_left : 0;
@@ -363,6 +371,15 @@ int concord_joint_set_timeout(concord_joint* jt, double seconds) {
   if (!(seconds > 0.0) || seconds > 3600.0)
     return jfail(CONCORD_E_ARG, "timeout must be in (0, 3600] s");
   jt->timeout_s = seconds;
+  return CONCORD_OK;
+}
+
+int concord_joint_set_fault(concord_joint* jt, int row, int step) {
+  if (!jt) return jfail(CONCORD_E_ARG, "joint state is NULL");
+  if (row >= jt->p) return jfail(CONCORD_E_ARG, "row must be < p (or < 0 to clear)");
+  if (row >= 0 && step < 0) return jfail(CONCORD_E_ARG, "step must be >= 0");
+  jt->fault_row = row < 0 ? -1 : row;
+  jt->fault_step = row < 0 ? -1 : step;
   return CONCORD_OK;
 }
 

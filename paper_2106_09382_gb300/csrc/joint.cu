@@ -282,6 +282,8 @@ __global__ void __launch_bounds__(kJointThreads, 1) k_joint(const JointArgs<T> a
           int i = -1, j = -1, ra = p, rb = p;
           if (q < half) slot_pair(q, c, P, p, i, j, ra, rb);
           const unsigned vin = (unsigned)(t * P + c);
+          // failure testing: the row that skips its publication at this step
+          const int skip = (a.fault_step >= 0 && vin == (unsigned)a.fault_step) ? a.fault_row : -1;
           if (a.row_ver != nullptr && q < half) {
             const int r = lane == 0 ? ra : rb;
             if (lane < 2 && r < p) wait_version(a.row_ver + r, vin, a.wait, r, c);
@@ -343,8 +345,8 @@ __global__ void __launch_bounds__(kJointThreads, 1) k_joint(const JointArgs<T> a
           // its reads are complete: publish them now, so the readers of the
           // next colour do not wait for this CTA's row updates.
           if (a.row_ver != nullptr && lane == 0 && q < half && !mv) {
-            if (ra < p) jst_release_u32(a.row_ver + ra, vin + 1u);
-            if (rb < p) jst_release_u32(a.row_ver + rb, vin + 1u);
+            if (ra < p && ra != skip) jst_release_u32(a.row_ver + ra, vin + 1u);
+            if (rb < p && rb != skip) jst_release_u32(a.row_ver + rb, vin + 1u);
           }
           if (__syncthreads_or(lane == 0 && mv)) {
             for (int w = 0; w < kJointWarps; ++w) {
@@ -361,8 +363,8 @@ __global__ void __launch_bounds__(kJointThreads, 1) k_joint(const JointArgs<T> a
             }
             __syncthreads();
             if (a.row_ver != nullptr && lane == 0 && q < half && mv) {
-              if (ra < p) jst_release_u32(a.row_ver + ra, vin + 1u);
-              if (rb < p) jst_release_u32(a.row_ver + rb, vin + 1u);
+              if (ra < p && ra != skip) jst_release_u32(a.row_ver + ra, vin + 1u);
+              if (rb < p && rb != skip) jst_release_u32(a.row_ver + rb, vin + 1u);
             }
           }
         }

@@ -44,6 +44,9 @@ struct JointArgs {
   unsigned* row_ver;         // [p] row versions, zeroed before the launch; nullptr: one grid
                              // barrier per colour step instead
   WaitCtl wait;
+  int fault_row = -1, fault_step = -1;  // failure testing (row flags only): row fault_row skips
+                              // publishing its version at colour step fault_step of the
+                              // launch (counted over all its sweeps); -1: none
   double* partials;          // 2 x gridDim.x x kJParts (double-buffered by sweep parity)
   double* hist;              // hist_len x kJHist
   int hist_len;

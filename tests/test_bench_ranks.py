@@ -62,4 +62,5 @@ def test_max_over_ranks_and_rank0_output():
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference" and rec["n_gpus"] == world
     assert rec["value"] > 0 and rec["cpu_baseline"]["kind"] == "oracle"
+    assert rec["cpu_baseline"]["cores"] >= 1 and rec["cpu_baseline"]["nproc"] >= 1
     assert rec["e2e"]["h2d_bytes_per_step"] == 0

@@ -229,3 +229,47 @@ def test_full_size_workload_converges_with_oracle_kkt():
     assert O.joint_kkt(S1h, S2h, G1, G2, w["lam1"], w["lam2"]) <= 1.5 * w["tol"]
     f = O.joint_objective(S1h, S2h, G1, G2, w["lam1"], w["lam2"])
     assert abs(r.objective - f) <= 1e-9 * abs(f)
+
+
+@pytest.mark.parametrize("precision", [C.FP64, C.MIXED])
+def test_joint_wait_timeout_is_reported_and_context_survives(precision):
+    """A row that skips one version publication makes the next reader's
+    bounded wait run out: CONCORD_E_TIMEOUT with that row and colour step,
+    and the device and the state stay usable.  Two CTAs hold the 31 pairs of
+    a colour (p = 61), so every CTA has pairs: the first wait to start, and so
+    the first to run out, is the colour-4 read of row 17 (a CTA without pairs
+    would wait at the end-of-sweep grid barrier from the start and run out
+    first)."""
+    S1, S2 = grams(61, 150, 5)
+    l1, l2 = 0.15, 0.05
+    with joint_state(S1, S2, precision, grid=2) as J:
+        J.set_timeout(0.25)
+        J.set_fault(17, 3)
+        with pytest.raises(C.ConcordError) as e:
+            J.sweep(l1, l2, 1)
+        assert e.value.code == C.E_TIMEOUT
+        assert J.last.timeout_vertex == 17 and J.last.timeout_step == 4
+        # the fault was one-shot: the same state solves to the oracle's answer
+        J.set_S(0, dev(S1))
+        J.set_S(1, dev(S2))
+        J.set_timeout(2.0)
+        r = J.run(l1, l2, tol=1e-9, max_sweeps=2000)
+        assert r.status == C.OK
+        G1 = host(J.get_omega(0))
+    A1, A2, info = O.joint_solve(S1, S2, l1, l2, tol=1e-11, max_sweeps=20000)
+    assert np.abs(G1 - A1).max() <= 1e-6 * np.abs(A1).max()
+    torch.cuda.synchronize()
+
+
+def test_joint_fault_switch_arguments():
+    S1, S2 = grams(20, 60, 6)
+    with joint_state(S1, S2) as J:
+        for row, step in ((20, 0), (3, -1)):
+            with pytest.raises(C.ConcordError) as e:
+                J.set_fault(row, step)
+            assert e.value.code == C.E_ARG
+        J.set_fault(-1, 0)  # clears
+        J.set_variant(C.JOINT_BARRIER)
+        J.set_fault(5, 2)  # ignored by the barrier variant
+        r = J.run(0.1, 0.02, tol=1e-8, max_sweeps=500)
+        assert r.status == C.OK
