@@ -414,7 +414,13 @@ def run_odd_p_section(C, synth, dev, stream, flush, p, n, lam, tol, max_sweeps, 
             "status": r.status, "launch_ms": tim}
 
 
-def run_path_section(C, synth, dev, stream, p=1000, n=800, n_lambda=32, n_sub=8, workers=8):
+def run_path_section(C, synth, dev, stream, p=1000, n=800, n_lambda=32, n_sub=64,
+                     max_sweeps=2000):
+    """Regularisation path and stability selection on the scale-free
+    workload: the path of 32 lambdas on the whole data (one state, one
+    persistent launch while screening pays, the dense kernel where it does
+    not), and the stability selection over all 64 subsamples as one batch
+    (concord_batch_*), every lambda run until KKT <= 1e-5."""
     import torch
     wl = synth.workload_path(p, n, 0)
     X = torch.as_tensor(wl["X"], device=dev)
@@ -424,34 +430,56 @@ def run_path_section(C, synth, dev, stream, p=1000, n=800, n_lambda=32, n_sub=8,
     torch.cuda.synchronize()
     st.set_S(S)
     lams = st.lambda_max() * np.logspace(0.0, -2.0, n_lambda)
-    tol, ms = 1e-5, 200
+    tol = 1e-5
     times = []
     for _ in range(2):  # one warm-up, one timed
         st.set_S(S)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = st.path(lams, tol=tol, max_sweeps=ms)
+        res = st.path(lams, tol=tol, max_sweeps=max_sweeps)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     subs = synth.subsamples(n, n_sub, 200, 800, seed=1)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    freq = st.stability(X, subs, lams, tol=tol, max_sweeps=ms, workers=workers)
-    torch.cuda.synchronize()
-    t_stab = time.perf_counter() - t0
-    f_mid = freq[n_lambda // 2].cpu().numpy()
+    rows = [torch.as_tensor(np.asarray(s_, dtype=np.int32), device=dev) for s_ in subs]
+    with C.Batch([p] * n_sub, C.MIXED, n_cap=n, device=dev.index) as bt:
+        bt.set_stream(stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for b in range(n_sub):
+            bt.gram(b, X, rows[b])
+        torch.cuda.synchronize()
+        t_gram = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        trial = bt.autotune(lams[n_lambda // 2], 2)
+        torch.cuda.synchronize()
+        t_tune = time.perf_counter() - t0
+        cnt = torch.zeros((n_lambda, p, p), dtype=torch.float32, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bres = bt.path(lams, tol=tol, max_sweeps=max_sweeps, support=cnt)
+        torch.cuda.synchronize()
+        t_path = time.perf_counter() - t0
+        binfo = bt.info()
+    sw = np.array([[r.sweeps for r in rr] for rr in bres])
+    conv = np.array([[r.status == C.OK for r in rr] for rr in bres])
+    freq = (cnt / n_sub)[n_lambda // 2].cpu().numpy()
     st.close()
     return {"workload": "scale-free (BA m=2) p=%d, n=%d; %d lambdas log-spaced lambda_max .. 0.01 "
                         "lambda_max, warm-started, KKT<=%g, <=%d sweeps per lambda, FP32 sweeps"
-                        % (p, n, n_lambda, tol, ms),
+                        % (p, n, n_lambda, tol, max_sweeps),
             "path_seconds": times[-1],
             "path_sweeps": int(sum(r.sweeps for r in res)),
             "path_dense_sweeps": int(sum(r.dense_sweeps for r in res)),
-            "lambdas_converged": int(sum(1 for r in res if r.kkt <= tol)),
-            "stability": {"subsamples": n_sub, "n_range": [200, 800], "workers": workers,
-                          "seconds": t_stab, "seconds_per_subsample": t_stab / n_sub,
-                          "estimated_seconds_64": t_stab / n_sub * 64,
-                          "edges_freq_ge_0.8_mid_lambda": int((np.triu(f_mid, 1) >= 0.8).sum()),
+            "lambdas_converged": int(sum(1 for r in res if r.status == C.OK)),
+            "path_sweeps_per_lambda": [int(r.sweeps) for r in res],
+            "stability": {"subsamples": n_sub, "n_range": [200, 800], "form": "one batch",
+                          "seconds": t_gram + t_path, "gram_seconds": t_gram,
+                          "path_seconds": t_path, "autotune_seconds": t_tune,
+                          "autotune_ms": trial, "layout": binfo,
+                          "problem_sweeps": int(sw.sum()),
+                          "ms_per_problem_sweep": t_path * 1e3 / max(1, int(sw.sum())),
+                          "lambdas_converged": int(conv.sum()), "of": int(conv.size),
+                          "edges_freq_ge_0.8_mid_lambda": int((np.triu(freq, 1) >= 0.8).sum()),
                           "true_edges": int((np.triu(wl["Om0"], 1) != 0).sum())}}
 
 
@@ -764,28 +792,11 @@ def run_ours(args):
         return times, recs
 
     def autotune(state):
-        """Pick the sweep kernel (screened or dense) and the dense kernel's
-        rows-per-warp layout (results do not depend on either) by the
-        measured sweep-kernel time per sweep on warm-up solves."""
-        trial = {}
-        for var, name in ((C.SWEEP_SCREENED, "screened"), (C.SWEEP_CLUSTER, "cluster"),
-                          (C.SWEEP_GRID, "grid")):
-            for rows in ((0,) if var == C.SWEEP_SCREENED else (32, 16, 8, 4)):
-                try:
-                    state.set_sweep_variant(var)
-                    state.set_rows_per_warp(rows)
-                    state.solve_device(X, lam, tol=tol, max_sweeps=args.max_sweeps)
-                except C.ConcordError:
-                    continue
-                tim = state.timing()
-                trial["%s/%d" % (name, rows)] = (sum(ms for ms, _ in tim)
-                                                 / max(1, sum(sw for _, sw in tim)))
-        best = min(trial, key=trial.get)
-        name, rows = best.split("/")
-        state.set_sweep_variant({"screened": C.SWEEP_SCREENED, "cluster": C.SWEEP_CLUSTER,
-                                 "grid": C.SWEEP_GRID}[name])
-        state.set_rows_per_warp(int(rows))
-        return best, trial
+        """The library's autotuner (concord_autotune): the sweep kernel and
+        layout with the least measured time per sweep on this workload
+        (results do not depend on the choice)."""
+        state.solve_device(X, lam, tol=tol, max_sweeps=args.max_sweeps)  # S from X
+        return state.autotune(lam, tol=tol, max_sweeps=args.max_sweeps)
 
     # ---------------- headline: mixed precision, data resident in HBM
     st = C.State(p, C.MIXED, n_cap=n, device=local)

@@ -323,6 +323,24 @@ int concord_set_sweep_variant(concord_state *st, int variant);
 int concord_get_sweep_variant(concord_state *st, int *variant, int *cluster_size);
 
 /*
+ * concord_autotune -- picks the sweep kernel and layout for the state's S
+ * and a representative lambda by measurement: from Omega = I it runs the
+ * solve (concord_run with tol, max_sweeps) once with each of the
+ * CONCORD_AUTOTUNE_CHOICES layouts -- the screened kernel; the dense kernel
+ * as one cluster at 32, 16, 8, 4 rows per warp; the dense kernel on the grid
+ * at 32, 16, 8, 4 rows per warp -- and keeps the one with the least device
+ * time per sweep (all launches of the solve).  ms_per_sweep (host,
+ * nullable, CONCORD_AUTOTUNE_CHOICES doubles) receives each time, -1 where
+ * a layout cannot run at this p; variant / rows_per_warp (nullable) the
+ * choice.  Results do not depend on the choice (every layout gives the same
+ * iterates).  The state ends at Omega = I.  Synchronises the stream.
+ * Errors: CONCORD_E_ARG, CONCORD_E_OCCUPANCY, CONCORD_E_TIMEOUT, CONCORD_E_CUDA.
+ */
+#define CONCORD_AUTOTUNE_CHOICES 9
+int concord_autotune(concord_state *st, double lambda, double tol, int max_sweeps,
+                     double *ms_per_sweep, int *variant, int *rows_per_warp);
+
+/*
  * concord_set_poll_sleep -- back-off, in nanoseconds (0..100000), between
  * two polls of a mailbox word in the sweep kernel (__nanosleep); a negative
  * value restores the default (0).  Trades wake-up latency against the load/store
@@ -420,12 +438,18 @@ int concord_path(concord_state *st, const double *lambdas, int n_lambda, double 
  * Gram of its rows (prep as concord_solve_device) and the lambda path over
  * lambdas from Omega = I; freq_dev (device, float, n_lambda x p x p, written
  * completely) receives for each lambda the fraction of subsamples whose
- * Omega has w_ij != 0.  n_workers subsamples run concurrently (0: up to 8),
- * each on a state of its own (own stream, 1 / n_workers of the SMs, created
- * and destroyed by the call, same precision, n_cap and Gram mode as st) with
- * one host thread; n_workers = 1 uses st itself, which then ends on the
- * last subsample's last lambda.  The frequencies do not depend on
- * n_workers (support counts are whole numbers added atomically).
+ * Omega has w_ij != 0.  n_workers = 0 (the default) solves every
+ * subsample as one problem of a batch (concord_batch_*: one persistent
+ * launch per wave of co-resident subsamples, each walking the path, the
+ * Gram 3xTF32 for MIXED and FP64 for FP64).  n_workers >= 1 runs that many
+ * subsamples concurrently, each on a state of its own (own stream,
+ * 1 / n_workers of the SMs, created and destroyed by the call, same
+ * precision, n_cap and Gram mode as st) with one host thread; n_workers = 1
+ * uses st itself, which then ends on the last subsample's last lambda.
+ * Every kernel gives the same iterates and support counts are whole numbers
+ * added atomically, so the frequencies agree between the forms whenever no
+ * lambda ends on the FP32 stall rule (whose count restarts when the
+ * single-state path hands a lambda to the dense kernel).
  */
 int concord_stability(concord_state *st, const void *X_dev, int x_dtype, int n, int ldx, int prep,
                       const int *rows, const int *set_sizes, int n_sets, const double *lambdas,
@@ -680,6 +704,98 @@ int concord_joint_run(concord_joint *jt, double lambda1, double lambda2, double 
  * concord_joint_sweep / _run call: min(max_rows, rows) rows into hist_host
  * (4 doubles each); *rows receives the number recorded. */
 int concord_joint_get_history(concord_joint *jt, double *hist_host, int max_rows, int *rows);
+
+/* ------------------------------------------------- batched independent problems */
+/*
+ * A batch holds many independent CONCORD problems (dimensions p[b], uneven
+ * allowed; data of uneven n) and solves them together: one persistent
+ * cooperative launch of the sweep kernel per wave of problems whose CTAs fit
+ * co-resident on the device, all problems of a wave in flight at once.  In
+ * the launch every problem owns a contiguous range of CTAs (its rows,
+ * mailbox ring, barrier counter and partial sums are its own), runs
+ * Algorithm 1's colour steps and diagonal step (Section 3.2, 3.3; Eq. 2,
+ * Eq. 3 in S units) at its own pace and walks a warm-started lambda path:
+ * after a lambda meets KKT <= tol (or max_sweeps, or in MIXED precision the
+ * FP32 stall rule of concord_run) it records the result, optionally adds the
+ * support of its Omega into the lambda's count matrix, and continues from its
+ * current iterate with the next lambda.  The problems share the launch and
+ * the abort word, nothing else.  This is the batched form of the parallel
+ * width the colour steps expose (Section 3.3): one problem at p = 1000 fills
+ * a small part of the GPU; many together fill it.
+ *
+ * Memory per problem (ld = p rounded up to 32, e = 4 for MIXED, 8 for FP64):
+ * S, W, Omega: 3 p ld e bytes, plus per-vertex vectors and a mailbox ring;
+ * plus, when n_cap > 0, staging for one problem's data and Gram at a time.
+ */
+typedef struct concord_batch concord_batch;
+
+/* n_problems >= 1 problems of dimensions p[0..n_problems) (each >= 2) on
+ * `device` (-1 = current) in CONCORD_MIXED (FP32 sweeps with the FP64
+ * diagonal root, KKT and objective) or CONCORD_FP64.  n_cap >= 0: most data
+ * rows concord_batch_gram will be given (0: S only through
+ * concord_batch_set_S).  Every Omega starts at I.
+ * Errors: CONCORD_E_ARG, CONCORD_E_NOMEM, CONCORD_E_CUDA (no sm_103 device). */
+int concord_batch_create(concord_batch **out, int n_problems, const int *p, int precision,
+                         int n_cap, int device);
+int concord_batch_destroy(concord_batch *bt);              /* NULL is accepted */
+int concord_batch_set_stream(concord_batch *bt, void *stream);  /* NULL: own stream */
+int concord_batch_set_timeout(concord_batch *bt, double seconds); /* device waits */
+
+/* S of problem b from a device buffer (p_b x p_b, dtype F64 / F32, row
+ * stride lds, symmetric); Omega_b <- I.  Synchronises the stream.
+ * Errors: CONCORD_E_ARG (index, not symmetric), CONCORD_E_NONFINITE,
+ * CONCORD_E_NONPOS_DIAG. */
+int concord_batch_set_S(concord_batch *bt, int b, const void *S_dev, int s_dtype, int lds);
+
+/* S of problem b from data: the rows rows_dev[0..n_rows) (device int32
+ * indices into X; NULL: all n rows) of X (device, n x p_b, row stride ldx,
+ * dtype F64 / F32), prepared by `prep` (CONCORD_PREP_*) and multiplied into
+ * S = Z^T Z / n_rows -- 3xTF32 on tensor cores for MIXED, FP64 for FP64
+ * (as concord_gram); Omega_b <- I.  Synchronises the stream.
+ * Errors: CONCORD_E_ARG (n_rows > n_cap, ...), CONCORD_E_NONPOS_DIAG
+ * (constant column), CONCORD_E_NONFINITE, CONCORD_E_CUDA. */
+int concord_batch_gram(concord_batch *bt, int b, const void *X_dev, int x_dtype, int n, int ldx,
+                       const int *rows_dev, int n_rows, int prep);
+
+/* Omega_b <- I and W_b <- S_b (S kept). */
+int concord_batch_reset(concord_batch *bt, int b);
+
+/* The lambda path lambdas[0..n_lambda) (host, each >= 0) on every problem,
+ * from its current iterate, each lambda until KKT <= tol or max_sweeps
+ * sweeps (MIXED: or the FP32 stall rule).  results (host, nullable) receives
+ * n_problems x n_lambda concord_result rows (problem-major; sweeps = sweeps
+ * at that lambda, status CONCORD_OK when KKT <= tol, else
+ * CONCORD_NOT_CONVERGED).  support_dev (device, nullable; all problems of one
+ * p) gains, for every problem and lambda k, 1.0 at [k][i][j] where
+ * w_ij != 0 (n_lambda x p x p floats, not cleared by the call).  When the
+ * rows per warp are not set, the call first autotunes them
+ * (concord_batch_autotune at the middle lambda, which resets every problem
+ * to Omega = I).  Synchronises the stream.
+ * Errors: CONCORD_E_ARG, CONCORD_E_OCCUPANCY, CONCORD_E_TIMEOUT, CONCORD_E_CUDA. */
+int concord_batch_path(concord_batch *bt, const double *lambdas, int n_lambda, double tol,
+                       int max_sweeps, concord_result *results, float *support_dev);
+
+/* The batch's work layout: each warp of a problem owns up to `rows` rows
+ * (2, 4, 8, 16 or 32; 0: autotune on the next concord_batch_path), so a
+ * problem of dimension p takes ceil(p / (16 rows)) CTAs of 512 threads and
+ * fewer rows per warp trade co-resident problems (waves) for row-update
+ * bandwidth.  Results do not depend on it. */
+int concord_batch_set_rows_per_warp(concord_batch *bt, int rows);
+
+/* Times `sweeps` sweeps at `lambda` on every problem for each rows-per-warp
+ * choice (32, 16, 8, 4, 2; ms_per_choice, host, nullable, receives the five
+ * times in ms, -1 where a choice cannot launch), keeps the fastest, and
+ * resets every problem to Omega = I.  Errors: as concord_batch_path. */
+int concord_batch_autotune(concord_batch *bt, double lambda, int sweeps, double *ms_per_choice);
+
+/* The layout of the last launch: rows per warp, the largest wave's CTAs,
+ * the number of waves, and the device time of the last path (or trial). */
+int concord_batch_info(concord_batch *bt, int *rows_per_warp, int *ctas, int *waves,
+                       double *seconds);
+
+/* Omega_b into a device buffer (dtype F64 / F32, row stride ldo >= p_b; for
+ * MIXED and F64 the diagonal is the FP64 one).  Synchronises the stream. */
+int concord_batch_get_omega(concord_batch *bt, int b, void *out_dev, int dtype, int ldo);
 
 #ifdef __cplusplus
 }

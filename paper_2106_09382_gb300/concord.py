@@ -88,6 +88,7 @@ SIGNATURES = {
     "concord_get_history": ([_vp, _dp, _ci, _ip], _ci),
     "concord_set_gram_mode": ([_vp, _ci], _ci),
     "concord_set_refine": ([_vp, _ci], _ci),
+    "concord_autotune": ([_vp, _cd, _cd, _ci, _dp, _ip, _ip], _ci),
     "concord_set_rows_per_warp": ([_vp, _ci], _ci),
     "concord_set_sweep_variant": ([_vp, _ci], _ci),
     "concord_set_poll_sleep": ([_vp, _ci], _ci),
@@ -125,6 +126,21 @@ SIGNATURES = {
     "concord_joint_run": ([_vp, _cd, _cd, _cd, _ci, _rp], _ci),
     "concord_joint_get_history": ([_vp, _dp, _ci, _ip], _ci),
 }
+
+SIGNATURES.update({
+    "concord_batch_create": ([ctypes.POINTER(_vp), _ci, _ip, _ci, _ci, _ci], _ci),
+    "concord_batch_destroy": ([_vp], _ci),
+    "concord_batch_set_stream": ([_vp, _vp], _ci),
+    "concord_batch_set_timeout": ([_vp, _cd], _ci),
+    "concord_batch_set_S": ([_vp, _ci, _vp, _ci, _ci], _ci),
+    "concord_batch_gram": ([_vp, _ci, _vp, _ci, _ci, _ci, _vp, _ci, _ci], _ci),
+    "concord_batch_reset": ([_vp, _ci], _ci),
+    "concord_batch_path": ([_vp, _dp, _ci, _cd, _ci, _rp, _vp], _ci),
+    "concord_batch_set_rows_per_warp": ([_vp, _ci], _ci),
+    "concord_batch_autotune": ([_vp, _cd, _ci, _dp], _ci),
+    "concord_batch_info": ([_vp, _ip, _ip, _ip, _dp], _ci),
+    "concord_batch_get_omega": ([_vp, _ci, _vp, _ci, _ci], _ci),
+})
 
 _lock = threading.Lock()
 _lib = None
@@ -293,6 +309,20 @@ class State:
         _check(load().concord_set_gram_mode(self._ptr, int(mode)))
 
     # data
+    AUTOTUNE_CHOICES = ("screened/0", "cluster/32", "cluster/16", "cluster/8", "cluster/4",
+                        "grid/32", "grid/16", "grid/8", "grid/4")
+
+    def autotune(self, lam: float, tol: float = 1e-5, max_sweeps: int = 1000):
+        """Pick the sweep kernel / layout by measured time per sweep
+        (concord_autotune); returns (choice name, {choice: ms per sweep})."""
+        ms = np.zeros(len(self.AUTOTUNE_CHOICES), dtype=np.float64)
+        v, r = ctypes.c_int(0), ctypes.c_int(0)
+        _check(load().concord_autotune(self._ptr, float(lam), float(tol), int(max_sweeps),
+                                       ms.ctypes.data_as(_dp), ctypes.byref(v), ctypes.byref(r)))
+        names = {SWEEP_SCREENED: "screened", SWEEP_CLUSTER: "cluster", SWEEP_GRID: "grid"}
+        trial = {k: float(x) for k, x in zip(self.AUTOTUNE_CHOICES, ms) if x >= 0}
+        return "%s/%d" % (names[v.value], r.value), trial
+
     def set_refine(self, on: bool):
         """Recompute the neighbourhood's S entries in FP64 accuracy before a
         mixed solve's polish (concord_set_refine; on by default)."""
@@ -615,4 +645,110 @@ class Joint:
         if n.value:
             _check(load().concord_joint_get_history(self._ptr, out.ctypes.data_as(_dp), n.value,
                                                     ctypes.byref(n)))
+        return out
+
+
+# ------------------------------------------------- batched independent problems
+class Batch:
+    """Many independent CONCORD problems solved together (concord_batch_*):
+    one persistent launch per wave of co-resident problems, each problem
+    walking a warm-started lambda path."""
+
+    def __init__(self, ps, precision: int = MIXED, n_cap: int = 0, device: int | None = None):
+        import torch
+        lib = load()
+        dev = torch.cuda.current_device() if device is None else int(device)
+        ps = np.ascontiguousarray(ps, dtype=np.int32)
+        self._ptr = ctypes.c_void_p()
+        _check(lib.concord_batch_create(ctypes.byref(self._ptr), len(ps),
+                                        ps.ctypes.data_as(_ip), int(precision), int(n_cap), dev))
+        self.ps = [int(x) for x in ps]
+        self.precision, self.n_cap, self.device = int(precision), int(n_cap), dev
+
+    def close(self):
+        if getattr(self, "_ptr", None) and self._ptr.value:
+            load().concord_batch_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __len__(self):
+        return len(self.ps)
+
+    def set_stream(self, stream=None):
+        _check(load().concord_batch_set_stream(self._ptr, _stream_ptr(stream)
+                                               if stream is not False else None))
+
+    def set_timeout(self, seconds: float):
+        _check(load().concord_batch_set_timeout(self._ptr, float(seconds)))
+
+    def set_S(self, b: int, S):
+        assert S.is_cuda and S.dim() == 2 and S.stride(1) == 1
+        _check(load().concord_batch_set_S(self._ptr, int(b), S.data_ptr(), _dtype_code(S),
+                                          S.stride(0)))
+
+    def gram(self, b: int, X, rows=None, prep: int = PREP_STANDARDIZE):
+        """S_b from the rows `rows` (CUDA int32 tensor, or None for all) of X."""
+        assert X.is_cuda and X.dim() == 2 and X.stride(1) == 1
+        n = X.shape[0]
+        if rows is not None:
+            import torch
+            assert rows.is_cuda and rows.dtype == torch.int32 and rows.dim() == 1
+            rp, nr = rows.data_ptr(), rows.numel()
+        else:
+            rp, nr = None, n
+        _check(load().concord_batch_gram(self._ptr, int(b), X.data_ptr(), _dtype_code(X), n,
+                                         X.stride(0), rp, int(nr), int(prep)))
+
+    def reset(self, b: int):
+        _check(load().concord_batch_reset(self._ptr, int(b)))
+
+    def set_rows_per_warp(self, rows: int):
+        _check(load().concord_batch_set_rows_per_warp(self._ptr, int(rows)))
+
+    def autotune(self, lam: float, sweeps: int = 2):
+        ms = np.zeros(5, dtype=np.float64)
+        _check(load().concord_batch_autotune(self._ptr, float(lam), int(sweeps),
+                                             ms.ctypes.data_as(_dp)))
+        return dict(zip((32, 16, 8, 4, 2), ms.tolist()))
+
+    def info(self) -> dict:
+        r, c, w = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        sec = ctypes.c_double(0.0)
+        _check(load().concord_batch_info(self._ptr, ctypes.byref(r), ctypes.byref(c),
+                                         ctypes.byref(w), ctypes.byref(sec)))
+        return {"rows_per_warp": r.value, "ctas": c.value, "waves": w.value,
+                "seconds": sec.value}
+
+    def path(self, lambdas, tol: float = 1e-5, max_sweeps: int = 1000, support=None):
+        """Returns res[b][k] (ConcordResult of problem b at lambda k)."""
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        B, K = len(self.ps), len(lam)
+        res = (ConcordResult * (B * K))()
+        sp = None
+        if support is not None:
+            import torch
+            assert support.is_cuda and support.dtype == torch.float32
+            assert support.numel() >= K * self.ps[0] * self.ps[0]
+            sp = support.data_ptr()
+        _check(load().concord_batch_path(self._ptr, lam.ctypes.data_as(_dp), K, float(tol),
+                                         int(max_sweeps), res, sp))
+        return [[res[b * K + k] for k in range(K)] for b in range(B)]
+
+    def get_omega(self, b: int, dtype=None):
+        import torch
+        p = self.ps[b]
+        out = torch.empty((p, p), dtype=dtype or torch.float64, device="cuda:%d" % self.device)
+        _check(load().concord_batch_get_omega(self._ptr, int(b), out.data_ptr(), _dtype_code(out),
+                                              out.stride(0)))
         return out

@@ -113,6 +113,7 @@ struct concord_state {
   int nc_cap = 0, term_cap = 0;
   int screened_grid = 0;
   int max_ctas = 0;  // > 0: persistent launches use at most this many CTAs (concurrent workers)
+  int last_batch_rows = 0;  // rows per warp the last batched stability run used
   // lambda path / stability selection buffers (allocated on demand)
   double *path_lam = nullptr, *path_res = nullptr;
   int path_cap = 0;
@@ -1342,7 +1343,7 @@ int concord_stability(concord_state* st, const void* X_dev, int x_dtype, int n, 
       n < 1 || ldx < p || prep < 0 || prep > 2 || !(tol > 0.0) || max_sweeps < 1 ||
       n_workers < 0 || (x_dtype != CONCORD_F64 && x_dtype != CONCORD_F32))
     return fail(CONCORD_E_ARG, "bad argument to concord_stability");
-  if (n_workers == 0) n_workers = n_sets < 8 ? n_sets : 8;
+  const bool batched = n_workers == 0;
   if (n_workers > n_sets) n_workers = n_sets;
   if (n_workers > st->sms) n_workers = st->sms;
   size_t total = 0;
@@ -1363,7 +1364,27 @@ int concord_stability(concord_state* st, const void* X_dev, int x_dtype, int n, 
   CK(cudaStreamSynchronize(st->stream));
   std::vector<size_t> offs(n_sets);
   for (int b = 0, o = 0; b < n_sets; o += set_sizes[b], ++b) offs[b] = (size_t)o;
-  if (n_workers <= 1) {
+  if (batched) {
+    // every subsample one problem of a batch: one persistent launch per wave
+    // of co-resident problems (concord_batch_*), support counts added by the
+    // kernel after each lambda
+    int n_max = 2;
+    for (int b = 0; b < n_sets; ++b) n_max = set_sizes[b] > n_max ? set_sizes[b] : n_max;
+    std::vector<int> ps(n_sets, p);
+    concord_batch* bt = nullptr;
+    rc = concord_batch_create(&bt, n_sets, ps.data(), st->precision, n_max, st->device);
+    if (rc != CONCORD_OK) return rc;
+    concord_batch_set_stream(bt, st->stream);
+    concord_batch_set_timeout(bt, st->timeout_s);
+    for (int b = 0; b < n_sets && rc == CONCORD_OK; ++b)
+      rc = concord_batch_gram(bt, b, X_dev, x_dtype, n, ldx, st->rows_dev + offs[b], set_sizes[b],
+                              prep);
+    if (rc == CONCORD_OK)
+      rc = concord_batch_path(bt, lambdas, n_lambda, tol, max_sweeps, nullptr, freq_dev);
+    if (rc == CONCORD_OK) concord_batch_info(bt, &st->last_batch_rows, nullptr, nullptr, nullptr);
+    concord_batch_destroy(bt);
+    if (rc != CONCORD_OK) return rc;
+  } else if (n_workers <= 1) {
     std::string err;
     rc = stability_worker(st, X_dev, x_dtype, ldx, prep, st->rows_dev, offs.data(), set_sizes,
                           n_sets, 0, 1, lambdas, n_lambda, tol, max_sweeps, freq_dev, &err);
@@ -1424,6 +1445,61 @@ int concord_set_sweep_variant(concord_state* st, int variant) {
   if (variant < 0 || variant > 4) return fail(CONCORD_E_ARG, "variant must be 0..4 (CONCORD_SWEEP_*)");
   st->sweep_variant = variant;
   return CONCORD_OK;
+}
+
+int concord_autotune(concord_state* st, double lambda, double tol, int max_sweeps,
+                     double* ms_per_sweep, int* variant, int* rows_per_warp) {
+  int rc = check_state(st);
+  if (rc) return rc;
+  if (!(lambda >= 0.0) || !(tol > 0.0) || max_sweeps < 1)
+    return fail(CONCORD_E_ARG, "lambda >= 0, tol > 0, max_sweeps >= 1 required");
+  // screened; dense cluster and grid layouts at 32, 16, 8, 4 rows per warp
+  struct Choice { int variant, rows; };
+  const Choice choices[kAutotuneChoices] = {
+      {CONCORD_SWEEP_SCREENED, 0}, {CONCORD_SWEEP_CLUSTER, 32}, {CONCORD_SWEEP_CLUSTER, 16},
+      {CONCORD_SWEEP_CLUSTER, 8},  {CONCORD_SWEEP_CLUSTER, 4},  {CONCORD_SWEEP_GRID, 32},
+      {CONCORD_SWEEP_GRID, 16},    {CONCORD_SWEEP_GRID, 8},     {CONCORD_SWEEP_GRID, 4}};
+  const int keep_variant = st->sweep_variant, keep_rows = st->rows_per_warp;
+  int best = -1;
+  double best_ms = 0.0;
+  for (int c = 0; c < kAutotuneChoices; ++c) {
+    if (ms_per_sweep) ms_per_sweep[c] = -1.0;
+    st->sweep_variant = choices[c].variant;
+    st->rows_per_warp = choices[c].rows;
+    if ((rc = reset_iterate(st)) != CONCORD_OK) break;
+    concord_result r;
+    rc = run_impl(st, lambda, tol, max_sweeps, CONCORD_STOP_KKT, 0.0, 0, &r);
+    if (rc == CONCORD_E_ARG || rc == CONCORD_E_OCCUPANCY) {  // layout not launchable here
+      rc = CONCORD_OK;
+      continue;
+    }
+    if (rc != CONCORD_OK && rc != CONCORD_NOT_CONVERGED) break;
+    rc = CONCORD_OK;
+    double ms = 0.0;
+    int sw = 0;
+    for (int q = 0; q < st->n_launch; ++q) {
+      ms += st->launch_ms[q];
+      sw += st->launch_sweeps[q];
+    }
+    const double per = ms / (sw > 0 ? sw : 1);
+    if (ms_per_sweep) ms_per_sweep[c] = per;
+    if (best < 0 || per < best_ms) {
+      best = c;
+      best_ms = per;
+    }
+  }
+  if (rc != CONCORD_OK || best < 0) {
+    st->sweep_variant = keep_variant;
+    st->rows_per_warp = keep_rows;
+    if (rc == CONCORD_OK) rc = fail(CONCORD_E_OCCUPANCY, "no sweep layout could run");
+    reset_iterate(st);
+    return rc;
+  }
+  st->sweep_variant = choices[best].variant;
+  st->rows_per_warp = choices[best].rows;
+  if (variant) *variant = choices[best].variant;
+  if (rows_per_warp) *rows_per_warp = choices[best].rows;
+  return reset_iterate(st);
 }
 
 int concord_get_sweep_variant(concord_state* st, int* variant, int* cluster_size) {

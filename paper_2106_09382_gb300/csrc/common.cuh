@@ -147,25 +147,27 @@ struct Mailbox<double> {
 };
 
 // ---------------------------------------------------------------------------
-// Grid barrier for a cooperative (co-resident) launch.  `gen` counts the
-// barriers this launch has passed; the counter is zeroed before the launch.
-// Returns with every CTA past the barrier or with the abort word set.
+// Barrier of `count` co-resident CTAs (a cooperative launch, or a group of
+// its CTAs with their own counter).  `gen` counts the barriers this group has
+// passed; the counter is zeroed before the launch.  Returns with every CTA of
+// the group past the barrier or with the abort word set; a wait that runs out
+// records -1 - who (the CTA) and `where`.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void grid_barrier(unsigned* counter, unsigned& gen,
-                                             const WaitCtl& w, int where) {
+__device__ __forceinline__ void group_barrier(unsigned* counter, unsigned& gen, unsigned count,
+                                              const WaitCtl& w, int where, int who) {
   __syncthreads();
   ++gen;
   if (threadIdx.x == 0) {
     __threadfence();
     red_release_add_u32(counter, 1u);
-    const unsigned target = gen * gridDim.x;
+    const unsigned target = gen * count;
     uint64_t t0 = globaltimer_ns();
     unsigned it = 0;
     while (ld_acquire_u32(counter) < target) {
       if ((++it & 15u) == 0) {
         if (ld_relaxed_s32(w.abort) != 0) break;
         if (globaltimer_ns() - t0 > w.timeout_ns) {
-          record_timeout(w, -1 - (int)blockIdx.x, where);
+          record_timeout(w, -1 - who, where);
           break;
         }
       }
@@ -173,6 +175,12 @@ __device__ __forceinline__ void grid_barrier(unsigned* counter, unsigned& gen,
     __threadfence();
   }
   __syncthreads();
+}
+
+// The whole grid (every CTA of a cooperative launch) as one group.
+__device__ __forceinline__ void grid_barrier(unsigned* counter, unsigned& gen,
+                                             const WaitCtl& w, int where) {
+  group_barrier(counter, gen, gridDim.x, w, where, (int)blockIdx.x);
 }
 
 }  // namespace concord

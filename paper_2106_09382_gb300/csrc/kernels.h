@@ -17,6 +17,7 @@ void note_launches(unsigned n);
 unsigned long long launches_so_far();
 
 constexpr int kSweepThreads = 512;   // the sweep kernel's block size
+constexpr int kAutotuneChoices = 9;  // layouts concord_autotune measures
 constexpr int kPendCap = 8;          // pending row updates kept per row before a flush
 constexpr int kDepth = 16;           // mailbox ring depth (a power of two, >= 4)
 
@@ -42,6 +43,25 @@ constexpr int kResSweeps = 0, kResKkt = 1, kResObj = 2, kResDelta = 3, kResActiv
               kResList = 9;  // screened: candidate list of the next sweep (-1: none valid)
 constexpr int kRes = 10;
 constexpr int kHist = 4;  // per sweep: delta, kkt, objective, active pairs
+
+// One problem of a batched launch of the sweep kernel: its own dimension,
+// arrays, mailbox ring, barrier counter and range of CTAs.
+template <typename T>
+struct BatchProblem {
+  int p, P, ld;
+  int cta0, ctas;            // CTAs [cta0, cta0 + ctas) of the launch serve this problem
+  T* W;                      // p x ld, W = Omega S
+  T* Om;                     // p x ld, Omega
+  const T* S;                // p x ld, S (padding columns zero)
+  const T *sdiag, *sd1, *sd2;
+  const double* sdiag64;     // s_ii in FP64
+  double* omdiag64;          // FP64 diagonal of Omega (mixed precision only)
+  unsigned long long* mbox;  // depth x (P+1) x words, tags below the launch's first
+  unsigned* barrier;         // zeroed before the launch
+  double* partials;          // ctas x kParts
+  double* result;            // n_lambda x kRes: the result of each lambda
+  float* cnt;                // nullable: slice k (p x p) += [w_ij != 0] after lambda k
+};
 
 template <typename T>
 struct SweepArgs {
@@ -69,6 +89,13 @@ struct SweepArgs {
   unsigned poll_ns;          // back-off between mailbox polls (0: none)
   unsigned tag_base;
   int fault_vertex, fault_step;
+  // batched launch (launch_sweep_batch): problems and the lambda path every
+  // problem walks (warm-started, n_sweeps sweeps at most per lambda)
+  const BatchProblem<T>* probs;
+  int n_probs;
+  const double* lambdas;
+  int n_lambda;
+  float* batch_cnt;          // (set per problem inside the kernel) its support counts
 };
 
 // cluster = true: the whole grid is one thread-block cluster (grid <= 16).
@@ -77,6 +104,14 @@ cudaError_t launch_sweep(const SweepArgs<double>& a, int grid, int block, bool c
 cudaError_t launch_sweep(const SweepArgs<float>& a, int grid, int block, bool cluster,
                          cudaStream_t st);
 cudaError_t sweep_occupancy(bool mixed, int block, int* blocks_per_sm);
+// Batched launch: a.probs[0..n_probs) with their CTA ranges covering
+// [0, grid); each problem runs the lambda path a.lambdas[0..n_lambda) from
+// its current iterate, stopping each lambda on a.stop_rule / a.tol, on the
+// FP32 stall rule (stall_stop) or after a.n_sweeps sweeps, and writes one
+// result row per lambda.  Problems are independent: they share the launch,
+// the abort word and nothing else.
+cudaError_t launch_sweep_batch(const SweepArgs<double>& a, int grid, int block, cudaStream_t st);
+cudaError_t launch_sweep_batch(const SweepArgs<float>& a, int grid, int block, cudaStream_t st);
 // Largest launchable cluster (power of two <= 16; 0 if none).
 cudaError_t sweep_cluster_size(bool mixed, int block, int row_warps, int rows_per_warp, int* cs);
 

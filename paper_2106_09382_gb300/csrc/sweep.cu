@@ -91,7 +91,7 @@ __device__ __forceinline__ T soft_threshold(T x, T tau) {
 
 // Block reduction of the per-thread partials into partials[blockIdx.x*kParts+k].
 __device__ __forceinline__ void block_reduce_parts(double (&v)[kParts], double* out,
-                                                   double (*red)[kParts]) {
+                                                   double (*red)[kParts], int slot) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int k = 0; k < kParts; ++k) {
@@ -109,7 +109,7 @@ __device__ __forceinline__ void block_reduce_parts(double (&v)[kParts], double* 
       double x = red[0][k];
       for (int w = 1; w < nw; ++w)
         x = (k == kPartKkt || k == kPartDelta) ? fmax(x, red[w][k]) : x + red[w][k];
-      out[(size_t)blockIdx.x * kParts + k] = x;
+      out[(size_t)slot * kParts + k] = x;
     }
   }
   __syncthreads();
@@ -223,7 +223,18 @@ __device__ __forceinline__ bool box_read<double>(const unsigned long long* local
 //     word a row reads lives in its own CTA's shared memory and the partner
 //     stores into it through distributed shared memory (lower latency), with
 //     per-row progress counters guarding slot reuse.
-template <typename T, bool MIXED, bool CLUSTER>
+//   BATCH = true (grid form): the launch serves a.n_probs independent
+//     problems; each CTA belongs to one problem (its CTA range), whose rows,
+//     mailbox ring, barriers and partial sums are its own, and each problem
+//     walks the lambda path a.lambdas (warm-started) at its own pace.
+template <typename T>
+__device__ __forceinline__ const SweepArgs<T>& pick_args(const SweepArgs<T>& batch,
+                                                          const SweepArgs<T>& single,
+                                                          bool use_batch) {
+  return use_batch ? batch : single;
+}
+
+template <typename T, bool MIXED, bool CLUSTER, bool BATCH>
 __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a) {
   using MB = Mailbox<T>;
   constexpr unsigned FULL = 0xffffffffu;
@@ -231,26 +242,72 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
   constexpr int BW = sizeof(T) / 4;  // cluster mailbox words per value
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
-  const bool row_warp = wid < a.row_warps;
-  const int p = a.p, P = a.P, ld = a.ld;
+  // The CTA's problem: the launch's own arguments, or (batch) a copy with the
+  // problem's dimension, arrays and counters; G / cta are the CTA count and
+  // index within the problem's group.
+  __shared__ SweepArgs<T> s_args;
+  __shared__ int s_gc[2];
+  int G = gridDim.x, cta = blockIdx.x;
+  if constexpr (BATCH) {
+    if (threadIdx.x == 0) {
+      int lo = 0, hi = a.n_probs - 1;
+      while (lo < hi) {  // last problem whose range starts at or before this CTA
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.probs[mid].cta0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+      }
+      const BatchProblem<T>& q = a.probs[lo];
+      s_args = a;
+      s_args.p = q.p;
+      s_args.P = q.P;
+      s_args.ld = q.ld;
+      s_args.W = q.W;
+      s_args.Om = q.Om;
+      s_args.S = q.S;
+      s_args.sdiag = q.sdiag;
+      s_args.sd1 = q.sd1;
+      s_args.sd2 = q.sd2;
+      s_args.sdiag64 = q.sdiag64;
+      s_args.omdiag64 = q.omdiag64;
+      s_args.mbox = q.mbox;
+      s_args.barrier = q.barrier;
+      s_args.partials = q.partials;
+      s_args.result = q.result;
+      s_args.batch_cnt = q.cnt;
+      s_args.hist_len = 0;
+      s_args.fault_vertex = -1;
+      s_args.fault_step = -1;
+      s_args.lambda = a.lambdas[0];
+      s_gc[0] = q.ctas;
+      s_gc[1] = (int)blockIdx.x - q.cta0;
+    }
+    __syncthreads();
+    G = s_gc[0];
+    cta = s_gc[1];
+  }
+  const SweepArgs<T>& A = pick_args<T>(s_args, a, BATCH);
+  const bool row_warp = wid < A.row_warps;
+  const int p = A.p, P = A.P, ld = A.ld;
   const int pe = P + 1;
-  const int R = a.rows_per_warp;
-  const int CS = gridDim.x;                   // cluster: CTAs in the cluster (a power of two)
+  const int R = A.rows_per_warp;
+  const int CS = G;                   // cluster: CTAs in the cluster (a power of two)
   const int cs_log2 = __ffs(CS) - 1;
-  const int cap = a.row_warps * R;            // cluster: rows a CTA can hold
+  const int cap = A.row_warps * R;            // cluster: rows a CTA can hold
   const int li = wid * R + lane;              // cluster: local index of this lane's row
   int myrow;
   if constexpr (CLUSTER) {
-    myrow = li * CS + (int)blockIdx.x;
+    myrow = li * CS + (int)cta;
   } else {
-    myrow = (blockIdx.x * a.row_warps + wid) + lane * (gridDim.x * a.row_warps);
+    myrow = (cta * A.row_warps + wid) + lane * (G * A.row_warps);
   }
   const bool has_row = row_warp && lane < R && myrow < p;
-  const T lam = (T)a.lambda;
-  const WaitCtl& wc = a.wait;
+  // the lambda in force (batch: walks the path, index kl)
+  double lam_cur = A.lambda;
+  T lam = (T)lam_cur;
+  int kl = 0;
+  const WaitCtl& wc = A.wait;
 
   __shared__ double red[kSweepThreads / 32][kParts];
-  __shared__ int s_stop;
+  __shared__ int s_stop, s_lam_end;
   __shared__ double s_res[kRes];
   // Dynamic shared memory: pending (not yet applied) row updates of every
   // owned row -- entry k of lane l of row warp w at ((w * KC + k) * R + l) --
@@ -258,16 +315,16 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
   // the per-row progress counters prog[cap].
   extern __shared__ __align__(16) unsigned char dyn[];
   T* pd_all = reinterpret_cast<T*>(dyn);
-  int* pu_all = reinterpret_cast<int*>(dyn + sizeof(T) * (size_t)a.row_warps * KC * R);
+  int* pu_all = reinterpret_cast<int*>(dyn + sizeof(T) * (size_t)A.row_warps * KC * R);
   unsigned long long* box = reinterpret_cast<unsigned long long*>(
-      dyn + (sizeof(T) + sizeof(int)) * (size_t)a.row_warps * KC * R);
+      dyn + (sizeof(T) + sizeof(int)) * (size_t)A.row_warps * KC * R);
   unsigned* prog = reinterpret_cast<unsigned*>(box + (size_t)kDepth * cap * BW);
   const int pst = R;
   T* pd = pd_all + (size_t)(row_warp ? wid : 0) * KC * R + (lane < R ? lane : 0);
   int* pu = pu_all + (size_t)(row_warp ? wid : 0) * KC * R + (lane < R ? lane : 0);
 
   // cluster: step tags restart at 1 every launch (fresh shared memory)
-  const unsigned tag_base = CLUSTER ? 1u : a.tag_base;
+  const unsigned tag_base = CLUSTER ? 1u : A.tag_base;
   if constexpr (CLUSTER) {
     for (int e = threadIdx.x; e < kDepth * cap * BW; e += blockDim.x) box[e] = 0ull;
     for (int e = threadIdx.x; e < cap; e += blockDim.x) prog[e] = 0u;
@@ -278,13 +335,14 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
   int first_delta = 0;
   double best_kkt = 1e300;
   int since_best = 0;
-  int t = 0;
-  T* __restrict__ Wrow = a.W + (size_t)(has_row ? myrow : 0) * ld;
-  T* __restrict__ Orow = a.Om + (size_t)(has_row ? myrow : 0) * ld;
-  const T s_mine = has_row ? a.sdiag[myrow] : (T)1;
+  int t = 0;      // sweeps of this launch (mailbox tags)
+  int t_lam = 0;  // batch: sweeps at the current lambda
+  T* __restrict__ Wrow = A.W + (size_t)(has_row ? myrow : 0) * ld;
+  T* __restrict__ Orow = A.Om + (size_t)(has_row ? myrow : 0) * ld;
+  const T s_mine = has_row ? A.sdiag[myrow] : (T)1;
 
   for (;;) {
-    const bool do_sweep = !a.kkt_only && t < a.n_sweeps;
+    const bool do_sweep = !A.kkt_only && (BATCH ? t_lam : t) < A.n_sweeps;
     double dmax = 0.0, nact = 0.0;
     if (do_sweep && row_warp) {
       const unsigned step0 = tag_base + (unsigned)(t * P);
@@ -313,27 +371,27 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
       int nA = 0;
       if (has_row && j < p) {
         om = Orow[j];
-        so = a.sdiag[j];
+        so = A.sdiag[j];
         if (j1 < p) {
           if (myrow == 0)
-            sjn = a.sd1[j];
+            sjn = A.sd1[j];
           else if (j != 0 && j1 != 0)
-            sjn = a.sd2[j];
+            sjn = A.sd2[j];
           else
-            sjn = __ldg(a.S + (size_t)j * ld + j1);
+            sjn = __ldg(A.S + (size_t)j * ld + j1);
         }
       }
       if (has_row && j1 < p) wA = Wrow[j1];
       // Step 0 of a sweep reuses a slot whose reader finished the previous
       // sweep (barrier) or launch: no check needed.
-      if (has_row && !(myrow == a.fault_vertex && t * P == a.fault_step)) {
+      if (has_row && !(myrow == A.fault_vertex && t * P == A.fault_step)) {
         if constexpr (CLUSTER) {
           if (j < p)
             box_store<T>((unsigned long long*)map_rank(
                              box + ((size_t)(step0 & (kDepth - 1)) * cap + (j >> cs_log2)) * BW, j & (CS - 1)),
                          step0, pub);
         } else {
-          MB::publish(a.mbox + ((size_t)(step0 & (kDepth - 1)) * pe + myrow) * MB::kWords, step0,
+          MB::publish(A.mbox + ((size_t)(step0 & (kDepth - 1)) * pe + myrow) * MB::kWords, step0,
                       pub);
         }
       }
@@ -353,7 +411,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
         if constexpr (CLUSTER)
           src = box + ((size_t)slot * cap + (li < cap ? li : 0)) * BW;
         else
-          src = a.mbox + ((size_t)slot * pe + (paired ? j : 0)) * MB::kWords;
+          src = A.mbox + ((size_t)slot * pe + (paired ? j : 0)) * MB::kWords;
         bool done;
         if constexpr (CLUSTER)
           done = !paired || box_read<T>(src, step, wji);
@@ -369,18 +427,18 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
         T om_n = (T)0, so_n = (T)1, sjn_n = (T)0;
         if (has_row && jn < p) {
           om_n = Orow[jn];
-          so_n = a.sdiag[jn];
+          so_n = A.sdiag[jn];
           // S[j_(c+1)][j_(c+2)]: consecutive partners are neighbours on the
           // cyclic ring (second sub-diagonal; the first for row 0) except
           // around vertex 0, so this is a walk through a p-vector, not a
           // random row of S.
           if (jnn < p) {
             if (myrow == 0)
-              sjn_n = a.sd1[jn];
+              sjn_n = A.sd1[jn];
             else if (jn != 0 && jnn != 0)
-              sjn_n = a.sd2[jn];
+              sjn_n = A.sd2[jn];
             else
-              sjn_n = __ldg(a.S + (size_t)jn * ld + jnn);
+              sjn_n = __ldg(A.S + (size_t)jn * ld + jnn);
           }
         }
         // -- slot-reuse guard, read two steps ahead: the value used now was
@@ -412,7 +470,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
               const int jo = (myrow == 0) ? (P - (c + 3 - kDepth))
                                           : ring_partner(ring_norm(rr - 4 + 2 * kDepth, P), myrow);
               if (jo < p) {
-                rw_new = a.mbox + ((size_t)((step + 4u) & (kDepth - 1)) * pe + jo) * MB::kWords;
+                rw_new = A.mbox + ((size_t)((step + 4u) & (kDepth - 1)) * pe + jo) * MB::kWords;
                 rtag_new = MB::read_tag(rw_new);
               }
             }
@@ -426,7 +484,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
           while (!__all_sync(FULL, done)) {
             // back off between polls: spinning warps would otherwise crowd the
             // load/store pipe that the working warps need
-            if (a.poll_ns) __nanosleep(a.poll_ns);
+            if (A.poll_ns) __nanosleep(A.poll_ns);
             if (!done) {
               if constexpr (CLUSTER)
                 done = box_read<T>(src, step, wji);
@@ -481,7 +539,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
               uint64_t t0 = globaltimer_ns();
               unsigned it = 0;
               while (ld_cluster_u32(rprog) < need - 1u) {
-                if (a.poll_ns) __nanosleep(a.poll_ns);
+                if (A.poll_ns) __nanosleep(A.poll_ns);
                 if ((++it & 63u) == 0) {
                   if (ld_relaxed_s32(wc.abort) != 0) break;
                   if (globaltimer_ns() - t0 > wc.timeout_ns) {
@@ -491,7 +549,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
                 }
               }
             }
-            if (jn < p && !(myrow == a.fault_vertex && t * P + c + 1 == a.fault_step))
+            if (jn < p && !(myrow == A.fault_vertex && t * P + c + 1 == A.fault_step))
               box_store<T>((unsigned long long*)map_rank(
                                box + ((size_t)((step + 1u) & (kDepth - 1)) * cap + (jn >> cs_log2)) * BW,
                                jn & (CS - 1)),
@@ -501,7 +559,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
               uint64_t t0 = globaltimer_ns();
               unsigned it = 0;
               while (MB::read_tag(rw) < need) {
-                if (a.poll_ns) __nanosleep(a.poll_ns);
+                if (A.poll_ns) __nanosleep(A.poll_ns);
                 if ((++it & 63u) == 0) {
                   if (ld_relaxed_s32(wc.abort) != 0) break;
                   if (globaltimer_ns() - t0 > wc.timeout_ns) {
@@ -511,8 +569,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
                 }
               }
             }
-            if (!(myrow == a.fault_vertex && t * P + c + 1 == a.fault_step))
-              MB::publish(a.mbox + ((size_t)((step + 1u) & (kDepth - 1)) * pe + myrow) * MB::kWords,
+            if (!(myrow == A.fault_vertex && t * P + c + 1 == A.fault_step))
+              MB::publish(A.mbox + ((size_t)((step + 1u) & (kDepth - 1)) * pe + myrow) * MB::kWords,
                           step + 1u, pub);
           }
         }
@@ -527,8 +585,8 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
           nA = cnt;
 #pragma unroll
           for (int k = 0; k < KC; ++k)
-            if (k < cnt) g[k] = __ldg(a.S + (size_t)pu[k * pst] * ld + jnn);
-          if (delta != (T)0) sprev = __ldg(a.S + (size_t)j * ld + jnn);
+            if (k < cnt) g[k] = __ldg(A.S + (size_t)pu[k * pst] * ld + jnn);
+          if (delta != (T)0) sprev = __ldg(A.S + (size_t)j * ld + jnn);
         }
         dprev = delta;
         if (delta != (T)0) {
@@ -545,7 +603,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
             const int k = __ffs(full) - 1;
             full &= full - 1;
             const int i = __shfl_sync(FULL, myrow, k);
-            flush_row(a.W + (size_t)i * ld, a.S, pu_all + (size_t)wid * KC * R + k,
+            flush_row(A.W + (size_t)i * ld, A.S, pu_all + (size_t)wid * KC * R + k,
                       pd_all + (size_t)wid * KC * R + k, pst, KC, ld, lane);
           }
           __syncwarp();
@@ -568,7 +626,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
           left &= left - 1;
           const int i = __shfl_sync(FULL, myrow, k);
           const int n = __shfl_sync(FULL, cnt, k);
-          flush_row(a.W + (size_t)i * ld, a.S, pu_all + (size_t)wid * KC * R + k,
+          flush_row(A.W + (size_t)i * ld, A.S, pu_all + (size_t)wid * KC * R + k,
                     pd_all + (size_t)wid * KC * R + k, pst, n, ld, lane);
         }
         __syncwarp();
@@ -577,12 +635,12 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
       //    w_ii <- (-c_i + sqrt(c_i^2 + 4 s_ii)) / (2 s_ii), W_i += dw S_i
       T dd = (T)0;
       if (has_row && ld_relaxed_s32(wc.abort) == 0) {
-        const double sii = a.sdiag64[myrow];
+        const double sii = A.sdiag64[myrow];
         const double wii = (double)Wrow[myrow];
-        const double oii = MIXED ? a.omdiag64[myrow] : (double)Orow[myrow];
+        const double oii = MIXED ? A.omdiag64[myrow] : (double)Orow[myrow];
         const double ci = wii - oii * sii;
         const double nw = (-ci + sqrt(ci * ci + 4.0 * sii)) / (2.0 * sii);
-        if (MIXED) a.omdiag64[myrow] = nw;
+        if (MIXED) A.omdiag64[myrow] = nw;
         Orow[myrow] = (T)nw;
         dd = (T)(nw - oii);
         dmax = fmax(dmax, fabs(nw - oii));
@@ -593,7 +651,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
         act &= act - 1;
         const int i = __shfl_sync(FULL, myrow, k);
         const T d = __shfl_sync(FULL, dd, k);
-        axpy_row(a.W + (size_t)i * ld, a.S + (size_t)i * ld, d, ld, lane);
+        axpy_row(A.W + (size_t)i * ld, A.S + (size_t)i * ld, d, ld, lane);
       }
       __syncwarp();
     }
@@ -602,7 +660,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
     if constexpr (CLUSTER)
       cluster_sync_all();
     else
-      grid_barrier(a.barrier, gen, wc, 1000000 + t);
+      group_barrier(A.barrier, gen, G, wc, 1000000 + t, cta);
     double v[kParts];
 #pragma unroll
     for (int k = 0; k < kParts; ++k) v[k] = 0.0;
@@ -617,11 +675,11 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
       using V = typename VT::V;
       constexpr int NV = 8 / VT::N;
       const int nb = (p + kTile - 1) / kTile;
-      const double lamd = a.lambda;
-      const float lamf = (float)a.lambda;
+      const double lamd = lam_cur;
+      const float lamf = (float)lam_cur;
       const int units = nb * nb * 4;
-      const int gwarps = gridDim.x * (blockDim.x >> 5);
-      for (int u = blockIdx.x * (blockDim.x >> 5) + wid; u < units; u += gwarps) {
+      const int gwarps = G * (blockDim.x >> 5);
+      for (int u = cta * (blockDim.x >> 5) + wid; u < units; u += gwarps) {
         const int tau = u >> 2, r0 = (u & 3) * 8;
         const int ta = tau / nb, tb = tau % nb;
         if (ta > tb) continue;
@@ -634,11 +692,11 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
         for (int r = 0; r < 8; ++r) {
           const int i = i0 + r;
           const bool ok = jv && i < p;
-          w1[r] = ok ? __ldcg(a.W + (size_t)i * ld + j) : (T)0;
-          om8[r] = ok ? __ldcg(a.Om + (size_t)i * ld + j) : (T)0;
+          w1[r] = ok ? __ldcg(A.W + (size_t)i * ld + j) : (T)0;
+          om8[r] = ok ? __ldcg(A.Om + (size_t)i * ld + j) : (T)0;
         }
         if (jv) {
-          const V* src = reinterpret_cast<const V*>(a.W + (size_t)j * ld + i0);
+          const V* src = reinterpret_cast<const V*>(A.W + (size_t)j * ld + i0);
 #pragma unroll
           for (int q = 0; q < NV; ++q) {
             V x = __ldcg(src + q);
@@ -684,7 +742,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
             if (!isfinite(g) || !isfinite(om)) v[kPartBad] += 1.0;
           } else if (i == j) {
             const double wii = (double)w1[r];
-            const double oii = MIXED ? __ldcg(a.omdiag64 + i) : (double)om8[r];
+            const double oii = MIXED ? __ldcg(A.omdiag64 + i) : (double)om8[r];
             if (oii > 0.0 && isfinite(wii) && isfinite(oii)) {
               v[kPartKkt] = fmax(v[kPartKkt], fabs(wii - 1.0 / oii));
               v[kPartQuad] += oii * wii;
@@ -696,17 +754,17 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
         }
       }
     }
-    block_reduce_parts(v, a.partials, red);
+    block_reduce_parts(v, A.partials, red, cta);
     if constexpr (CLUSTER)
       cluster_sync_all();
     else
-      grid_barrier(a.barrier, gen, wc, 2000000 + t);
+      group_barrier(A.barrier, gen, G, wc, 2000000 + t, cta);
 
     // ---------------- every CTA reduces the partials identically
     if (threadIdx.x == 0) {
       double kkt = 0.0, quad = 0.0, pen = 0.0, lg = 0.0, dl = 0.0, ac = 0.0, bad = 0.0;
-      for (int b = 0; b < (int)gridDim.x; ++b) {
-        const double* q = a.partials + (size_t)b * kParts;
+      for (int b = 0; b < (int)G; ++b) {
+        const double* q = A.partials + (size_t)b * kParts;
         kkt = fmax(kkt, __ldcg(q + kPartKkt));
         quad += __ldcg(q + kPartQuad);
         pen += __ldcg(q + kPartPen);
@@ -715,12 +773,13 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
         ac += __ldcg(q + kPartActive);
         bad += __ldcg(q + kPartBad);
       }
-      const double obj = -lg + 0.5 * quad + a.lambda * pen;
+      const double obj = -lg + 0.5 * quad + lam_cur * pen;
       const bool aborted = ld_relaxed_s32(wc.abort) != 0;
       const bool nonfinite = bad > 0.0 || !isfinite(obj) || !isfinite(kkt);
-      const int sweeps_done = do_sweep ? t + 1 : t;
-      if (do_sweep && first_delta == 0 && dl < a.delta_tol) first_delta = sweeps_done;
-      bool conv = (a.stop_rule == 1) ? (do_sweep && dl < a.tol) : (kkt <= a.tol);
+      const int t_count = BATCH ? t_lam : t;
+      const int sweeps_done = do_sweep ? t_count + 1 : t_count;
+      if (do_sweep && first_delta == 0 && dl < A.delta_tol) first_delta = sweeps_done;
+      bool conv = (A.stop_rule == 1) ? (do_sweep && dl < A.tol) : (kkt <= A.tol);
       // stall: the KKT residual has not dropped by 10% for 4 sweeps (FP32
       // phase at its rounding floor); the host then switches to FP64
       bool stalled = false;
@@ -728,7 +787,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
         if (kkt < 0.9 * best_kkt) {
           best_kkt = kkt;
           since_best = 0;
-        } else if (++since_best >= 4 && a.stall_stop) {
+        } else if (++since_best >= 4 && A.stall_stop) {
           stalled = true;
         }
       }
@@ -739,22 +798,59 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
       s_res[kResActive] = ac * 0.5;  // each pair is counted by both owners
       s_res[kResFirstDelta] = first_delta;
       s_res[kResStatus] = aborted ? 3.0 : (nonfinite ? 2.0 : (conv ? 0.0 : (stalled ? 4.0 : 1.0)));
-      s_stop = (aborted || nonfinite || conv || stalled || a.kkt_only || sweeps_done >= a.n_sweeps)
+      s_stop = (aborted || nonfinite || conv || stalled || A.kkt_only || sweeps_done >= A.n_sweeps)
                    ? 1
                    : 0;
-      if (blockIdx.x == 0) {
-        if (do_sweep && t < a.hist_len) {
-          double* h = a.hist + (size_t)t * kHist;
+      if constexpr (BATCH) {
+        // the lambda is finished; the problem stops after the last one (or
+        // on an abort / a non-finite value) and otherwise moves to the next
+        s_lam_end = s_stop;
+        if (s_stop && !aborted && !nonfinite && kl + 1 < A.n_lambda) s_stop = 0;
+        if (cta == 0 && s_lam_end)
+          for (int k = 0; k < kRes; ++k) A.result[(size_t)kl * kRes + k] = s_res[k];
+      }
+      if (cta == 0) {
+        if (do_sweep && t < A.hist_len) {
+          double* h = A.hist + (size_t)t * kHist;
           h[0] = dl;
           h[1] = kkt;
           h[2] = obj;
           h[3] = ac * 0.5;
         }
-        if (s_stop)
-          for (int k = 0; k < kRes; ++k) a.result[k] = s_res[k];
+        if (!BATCH && s_stop)
+          for (int k = 0; k < kRes; ++k) A.result[k] = s_res[k];
       }
     }
     __syncthreads();
+    if constexpr (BATCH) {
+      if (s_lam_end) {
+        // support of this lambda's solution over the rows this warp owns (no
+        // other warp writes them, so no barrier is needed before the next
+        // lambda's sweeps)
+        if (A.batch_cnt && row_warp && ld_relaxed_s32(wc.abort) == 0) {
+          float* cnt_k = A.batch_cnt + (size_t)kl * p * p;
+          unsigned own = __ballot_sync(FULL, has_row);
+          while (own) {
+            const int k = __ffs(own) - 1;
+            own &= own - 1;
+            const int i = __shfl_sync(FULL, myrow, k);
+            const T* orow = A.Om + (size_t)i * ld;
+            for (int x = lane; x < p; x += 32)
+              if (orow[x] != (T)0) atomicAdd(cnt_k + (size_t)i * p + x, 1.0f);
+          }
+        }
+        if (!s_stop) {
+          ++kl;
+          lam_cur = A.lambdas[kl];
+          lam = (T)lam_cur;
+          best_kkt = 1e300;
+          since_best = 0;
+          first_delta = 0;
+          t_lam = -1;
+        }
+      }
+      ++t_lam;
+    }
     if (s_stop) break;
     ++t;
   }
@@ -763,7 +859,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
 template <typename T, bool MIXED, bool CLUSTER>
 cudaError_t launch_sweep_impl(const SweepArgs<T>& args, int grid, int block, cudaStream_t st) {
   const size_t dyn = sweep_dyn_smem(sizeof(T), args.row_warps, args.rows_per_warp, CLUSTER);
-  const void* fn = (const void*)k_sweep<T, MIXED, CLUSTER>;
+  const void* fn = (const void*)k_sweep<T, MIXED, CLUSTER, false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (e != cudaSuccess) return e;
   note_launches(1);
@@ -782,7 +878,7 @@ cudaError_t launch_sweep_impl(const SweepArgs<T>& args, int grid, int block, cud
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_sweep<T, MIXED, CLUSTER>, args);
+    return cudaLaunchKernelEx(&cfg, k_sweep<T, MIXED, CLUSTER, false>, args);
   } else {
     void* kargs[] = {(void*)&args};
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), kargs, dyn, st);
@@ -792,11 +888,11 @@ cudaError_t launch_sweep_impl(const SweepArgs<T>& args, int grid, int block, cud
 template <typename T, bool MIXED>
 cudaError_t sweep_occupancy_impl(int block, int* blocks_per_sm) {
   const size_t dyn = sweep_dyn_smem(sizeof(T), block / 32, 32, false);
-  cudaError_t e = cudaFuncSetAttribute((const void*)k_sweep<T, MIXED, false>,
+  cudaError_t e = cudaFuncSetAttribute((const void*)k_sweep<T, MIXED, false, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_sweep<T, MIXED, false>,
-                                                       block, dyn);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
+                                                       k_sweep<T, MIXED, false, false>, block, dyn);
 }
 
 // Largest cluster the cluster variant can launch with (a power of two <= 16),
@@ -804,7 +900,7 @@ cudaError_t sweep_occupancy_impl(int block, int* blocks_per_sm) {
 template <typename T, bool MIXED>
 cudaError_t sweep_cluster_size_impl(int block, int row_warps, int rows_per_warp, int* cs) {
   const size_t dyn = sweep_dyn_smem(sizeof(T), row_warps, rows_per_warp, true);
-  const void* fn = (const void*)k_sweep<T, MIXED, true>;
+  const void* fn = (const void*)k_sweep<T, MIXED, true, false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
@@ -823,7 +919,7 @@ cudaError_t sweep_cluster_size_impl(int block, int row_warps, int rows_per_warp,
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int n = 0;
-    e = cudaOccupancyMaxActiveClusters(&n, k_sweep<T, MIXED, true>, &cfg);
+    e = cudaOccupancyMaxActiveClusters(&n, k_sweep<T, MIXED, true, false>, &cfg);
     if (e == cudaSuccess && n >= 1) {
       *cs = c;
       return cudaSuccess;
@@ -843,6 +939,24 @@ cudaError_t launch_sweep(const SweepArgs<float>& a, int grid, int block, bool cl
   return cluster ? launch_sweep_impl<float, true, true>(a, grid, block, st)
                  : launch_sweep_impl<float, true, false>(a, grid, block, st);
 }
+template <typename T, bool MIXED>
+cudaError_t launch_sweep_batch_impl(const SweepArgs<T>& args, int grid, int block, cudaStream_t st) {
+  const size_t dyn = sweep_dyn_smem(sizeof(T), args.row_warps, args.rows_per_warp, false);
+  const void* fn = (const void*)k_sweep<T, MIXED, false, true>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (e != cudaSuccess) return e;
+  note_launches(1);
+  void* kargs[] = {(void*)&args};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), kargs, dyn, st);
+}
+
+cudaError_t launch_sweep_batch(const SweepArgs<double>& a, int grid, int block, cudaStream_t st) {
+  return launch_sweep_batch_impl<double, false>(a, grid, block, st);
+}
+cudaError_t launch_sweep_batch(const SweepArgs<float>& a, int grid, int block, cudaStream_t st) {
+  return launch_sweep_batch_impl<float, true>(a, grid, block, st);
+}
+
 cudaError_t sweep_occupancy(bool mixed, int block, int* blocks_per_sm) {
   return mixed ? sweep_occupancy_impl<float, true>(block, blocks_per_sm)
                : sweep_occupancy_impl<double, false>(block, blocks_per_sm);
