@@ -127,6 +127,8 @@ typedef struct concord_result {
     int dense_sweeps;      /* sweeps handed from the screened to the dense kernel */
     int s_refined;         /* MIXED: entries of S recomputed in FP64 accuracy
                               before the polish (concord_set_refine); 0 if none */
+    int lazy_sweeps;       /* screened sweeps that skipped the verification
+                              pass (concord_set_lazy_verify) */
 } concord_result;
 
 /* KKT residual (absolute, S units), with W = Omega S and G = W + W^T:
@@ -386,6 +388,21 @@ int concord_set_gram_mode(concord_state *st, int mode);
  * Errors: CONCORD_E_ARG.
  */
 int concord_set_refine(concord_state *st, int on);
+
+/*
+ * concord_set_lazy_verify -- on (1, the default) or off (0).  The screened
+ * kernel visits only candidate pairs (w_ij != 0 or |G_ij| > 0.9 lambda when
+ * the list was screened) and then verifies that no other pair would have
+ * left zero, re-screening for the next sweep.  A change d of a candidate
+ * (i, u) moves G_ij of a pair outside the list by at most |d| m_u, and a
+ * diagonal change by at most |dw| m_i (m_u = max_{x != u} |s_ux|).  While
+ * the sum of these bounds since the list was screened stays within 0.09
+ * lambda, no pair outside it can reach the threshold, so the sweep skips the
+ * verification pass and keeps the list (and its build) for the next sweep.
+ * The iterates are the same either way; concord_result.lazy_sweeps counts
+ * the skipped verifications.  Errors: CONCORD_E_ARG.
+ */
+int concord_set_lazy_verify(concord_state *st, int on);
 
 /*
  * concord_sweep -- run exactly n_sweeps outer iterations of Algorithm 1 at
@@ -762,10 +779,18 @@ int concord_batch_reset(concord_batch *bt, int b);
 
 /* The lambda path lambdas[0..n_lambda) (host, each >= 0) on every problem,
  * from its current iterate, each lambda until KKT <= tol or max_sweeps
- * sweeps (MIXED: or the FP32 stall rule).  results (host, nullable) receives
+ * sweeps.  MIXED: FP32 sweeps; a lambda whose FP32 sweeps stop falling by
+ * 10% over 4 sweeps (the FP32 rounding floor of the maintained W, or
+ * progress too slow to tell apart from it) is polished in FP64 -- W rebuilt
+ * in FP64 from Omega and an FP64 copy of S, FP64 sweeps to tol within the
+ * lambda's remaining sweeps, one launch for every problem that stalled --
+ * and its walk resumes in FP32 from the polished iterate
+ * (concord_batch_set_polish(bt, 0): a stalled lambda just ends, not
+ * converged, and the walk goes on).  results (host, nullable) receives
  * n_problems x n_lambda concord_result rows (problem-major; sweeps = sweeps
  * at that lambda, status CONCORD_OK when KKT <= tol, else
- * CONCORD_NOT_CONVERGED).  support_dev (device, nullable; all problems of one
+ * CONCORD_NOT_CONVERGED; MIXED: sweeps_fp32 = its FP32 sweeps).
+ * support_dev (device, nullable; all problems of one
  * p) gains, for every problem and lambda k, 1.0 at [k][i][j] where
  * w_ij != 0 (n_lambda x p x p floats, not cleared by the call).  When the
  * rows per warp are not set, the call first autotunes them
@@ -781,6 +806,10 @@ int concord_batch_path(concord_batch *bt, const double *lambdas, int n_lambda, d
  * fewer rows per warp trade co-resident problems (waves) for row-update
  * bandwidth.  Results do not depend on it. */
 int concord_batch_set_rows_per_warp(concord_batch *bt, int rows);
+
+/* MIXED: FP64 polish of stalled lambdas in concord_batch_path (1, the
+ * default) or not (0). */
+int concord_batch_set_polish(concord_batch *bt, int on);
 
 /* Times `sweeps` sweeps at `lambda` on every problem for each rows-per-warp
  * choice (32, 16, 8, 4, 2; ms_per_choice, host, nullable, receives the five

@@ -43,7 +43,7 @@ class ConcordResult(ctypes.Structure):
                 ("active_pairs", ctypes.c_longlong), ("seconds", ctypes.c_double),
                 ("timeout_vertex", ctypes.c_int), ("timeout_step", ctypes.c_int),
                 ("screen_redos", ctypes.c_int), ("dense_sweeps", ctypes.c_int),
-                ("s_refined", ctypes.c_int)]
+                ("s_refined", ctypes.c_int), ("lazy_sweeps", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
@@ -88,6 +88,7 @@ SIGNATURES = {
     "concord_get_history": ([_vp, _dp, _ci, _ip], _ci),
     "concord_set_gram_mode": ([_vp, _ci], _ci),
     "concord_set_refine": ([_vp, _ci], _ci),
+    "concord_set_lazy_verify": ([_vp, _ci], _ci),
     "concord_autotune": ([_vp, _cd, _cd, _ci, _dp, _ip, _ip], _ci),
     "concord_set_rows_per_warp": ([_vp, _ci], _ci),
     "concord_set_sweep_variant": ([_vp, _ci], _ci),
@@ -137,6 +138,7 @@ SIGNATURES.update({
     "concord_batch_reset": ([_vp, _ci], _ci),
     "concord_batch_path": ([_vp, _dp, _ci, _cd, _ci, _rp, _vp], _ci),
     "concord_batch_set_rows_per_warp": ([_vp, _ci], _ci),
+    "concord_batch_set_polish": ([_vp, _ci], _ci),
     "concord_batch_autotune": ([_vp, _cd, _ci, _dp], _ci),
     "concord_batch_info": ([_vp, _ip, _ip, _ip, _dp], _ci),
     "concord_batch_get_omega": ([_vp, _ci, _vp, _ci, _ci], _ci),
@@ -322,6 +324,11 @@ class State:
         names = {SWEEP_SCREENED: "screened", SWEEP_CLUSTER: "cluster", SWEEP_GRID: "grid"}
         trial = {k: float(x) for k, x in zip(self.AUTOTUNE_CHOICES, ms) if x >= 0}
         return "%s/%d" % (names[v.value], r.value), trial
+
+    def set_lazy_verify(self, on: bool):
+        """Skip the screened kernel's verification pass when the changes
+        provably keep every other pair at zero (concord_set_lazy_verify)."""
+        _check(load().concord_set_lazy_verify(self._ptr, 1 if on else 0))
 
     def set_refine(self, on: bool):
         """Recompute the neighbourhood's S entries in FP64 accuracy before a
@@ -715,6 +722,9 @@ class Batch:
 
     def set_rows_per_warp(self, rows: int):
         _check(load().concord_batch_set_rows_per_warp(self._ptr, int(rows)))
+
+    def set_polish(self, on: bool):
+        _check(load().concord_batch_set_polish(self._ptr, 1 if on else 0))
 
     def autotune(self, lam: float, sweeps: int = 2):
         ms = np.zeros(5, dtype=np.float64)

@@ -61,6 +61,8 @@ struct concord_state {
   void *S = nullptr, *W = nullptr, *Om = nullptr, *sdiagT = nullptr;
   double* sdiag64 = nullptr;
   double* omdiag64 = nullptr;  // mixed only
+  float* mrow = nullptr;       // [p] m[u] >= max_{x != u} |s_ux| (lazy verification bound)
+  bool lazy_verify = true;
   void *sd1 = nullptr, *sd2 = nullptr;    // sub-diagonal walk vectors, working precision
   double *sd1_64 = nullptr, *sd2_64 = nullptr;  // FP64 versions (mixed polish)
   // FP64 copies (mixed) or aliases of the working set (fp64)
@@ -114,6 +116,7 @@ struct concord_state {
   int screened_grid = 0;
   int max_ctas = 0;  // > 0: persistent launches use at most this many CTAs (concurrent workers)
   int last_batch_rows = 0;  // rows per warp the last batched stability run used
+  bool path_polish = true;  // mixed paths: FP64 polish of a lambda whose FP32 sweeps stall
   // lambda path / stability selection buffers (allocated on demand)
   double *path_lam = nullptr, *path_res = nullptr;
   int path_cap = 0;
@@ -175,6 +178,7 @@ struct RunOut {
   int redos = 0, dense_sweeps = 0;  // screened runs
   int next_list = -1;               // screened: candidate list left for the next sweep
   int s_refined = 0;                // S entries recomputed before the polish
+  int lazy = 0;                     // screened sweeps that skipped the verification
 };
 
 // One persistent launch: n_sweeps outer iterations (fewer if the stopping
@@ -347,7 +351,7 @@ int launch_dense(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* 
 // lists and per-candidate arrays, carved below.
 struct ScreenLayout {
   size_t ctr, cand0, cand1, cnt_r0, cnt_r1, fail, off_r, cur_r, nd_pi, nd_pj, row_ent, term_ptr, term_pred, term_s, nd_rec, nd_delta, nd_new, nd_d2, jac,
-      diag_old, omdiag_old, diag_new, total;
+      diag_old, omdiag_old, diag_new, dpart, total;
 };
 
 ScreenLayout screen_layout(int p, int P, int nc, int tc) {
@@ -381,6 +385,7 @@ ScreenLayout screen_layout(int p, int P, int nc, int tc) {
 
   L.omdiag_old = take(sizeof(double) * (size_t)p);
   L.diag_new = take(sizeof(double) * (size_t)p);
+  L.dpart = take(sizeof(double) * 1024);
   L.total = off;
   return L;
 }
@@ -449,6 +454,7 @@ ScreenWork<T> screen_work(concord_state* st) {
 
   w.omdiag_old = (double*)(b + L.omdiag_old);
   w.diag_new = (double*)(b + L.diag_new);
+  w.dpart = (double*)(b + L.dpart);
   w.nc_cap = st->nc_cap;
   w.term_cap = st->term_cap;
   w.fail_cap = st->nc_cap;
@@ -463,6 +469,7 @@ struct PathArgs {
   void* om;
   int ldo;
   float* cnt;
+  int break_stall;  // a stalled lambda ends the launch (the host polishes it)
 };
 
 // One persistent launch of the screened sweep kernel; out->status_code is
@@ -516,6 +523,8 @@ int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, d
   a.stall_stop = stall_stop;
   a.max_redo = 8;
   a.start_list = start_list;
+  a.mrow = st->mrow;
+  a.lazy_verify = st->lazy_verify ? 1 : 0;
   if (path) {
     a.path_lambda = path->lam;
     a.path_n = path->n;
@@ -524,6 +533,7 @@ int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, d
     a.path_om = (T*)path->om;
     a.path_ldo = path->ldo;
     a.path_cnt = path->cnt;
+    a.path_break_stall = path->break_stall;
   }
   st->last_variant = CONCORD_SWEEP_SCREENED;
 
@@ -548,6 +558,7 @@ int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, d
   out->first_delta = (int)r[kResFirstDelta];
   out->redos = (int)r[kResRedo];
   out->next_list = (int)r[kResList];
+  out->lazy = (int)r[kResLazy];
   if (slot_ev >= 0) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, st->lev[2 * slot_ev], st->lev[2 * slot_ev + 1]));
@@ -657,6 +668,7 @@ void fill_result(concord_result* res, const RunOut& o, int sweeps, int sweeps32,
   res->screen_redos = o.redos;
   res->dense_sweeps = o.dense_sweeps;
   res->s_refined = o.s_refined;
+  res->lazy_sweeps = o.lazy;
 }
 
 int ensure_path(concord_state* st, int n_lambda, size_t n_rows) {
@@ -699,6 +711,32 @@ void result_from_row(concord_result* r, const double* row, double lambda) {
 // st->path_lam): one screened launch walks the lambdas, warm-starting each
 // from the previous; a lambda whose sweeps need the dense kernel runs through
 // the single-lambda dispatcher and the path resumes after it.
+int demote_from_fp64(concord_state* st);
+
+// A path lambda whose FP32 sweeps ended on the stall rule (the FP32 rounding
+// floor, or progress too slow to tell apart from it): FP64 copies from the
+// FP32 iterate (W rebuilt in FP64 from Omega and S64), FP64 sweeps to tol
+// (at most `left`), then the FP32 working set back from the FP64 copies.
+int polish_path_lambda(concord_state* st, double lambda, double tol, int left, RunOut* o2) {
+  CK(launch_convert(st->Om, 1, st->ld, st->Om64, 0, st->ld, st->p, st->p, st->stream));
+  CK(cudaMemcpy2DAsync(st->Om64, (size_t)(st->ld + 1) * sizeof(double), st->omdiag64,
+                       sizeof(double), sizeof(double), st->p, cudaMemcpyDeviceToDevice,
+                       st->stream));
+  CK(launch_refresh_w(st->Om64, st->S64, st->W64, st->p, st->ld, st->sms, st->stream));
+  const int start_list = st->start_list;
+  st->start_list = -1;
+  int rc = launch_run<double>(st, st->S64, st->W64, st->Om64, st->sdiag64, nullptr, lambda, tol,
+                              CONCORD_STOP_KKT, left > 0 ? left : 1, 0, 0, 0, o2);
+  st->start_list = start_list;
+  if (rc != CONCORD_OK) return rc;
+  return demote_from_fp64(st);
+}
+
+// Warm-started lambda path.  The screened kernel walks the lambdas in one
+// launch until a lambda's candidates overflow (that lambda then runs on the
+// single-lambda dispatcher and the path resumes after it) or, in mixed
+// precision, until a lambda's FP32 sweeps stall (that lambda is polished in
+// FP64 and the path resumes after it).
 template <typename T>
 int path_impl(concord_state* st, const double* lambdas, int n, double tol, int max_sweeps,
               concord_result* results, void* om_out, int ldo, float* cnt) {
@@ -711,34 +749,58 @@ int path_impl(concord_state* st, const double* lambdas, int n, double tol, int m
   std::vector<double> rows((size_t)kRes * n);
   int start = 0;
   st->n_launch = 0;
+  // the lambda `k` is finished on the current iterate: its Omega and support
+  auto finish = [&](int k, bool polished) -> int {
+    if (om_out)
+      CK(cudaMemcpy2DAsync((T*)om_out + (size_t)k * st->p * ldo, sizeof(T) * ldo, Om,
+                           sizeof(T) * st->ld, sizeof(T) * st->p, st->p, cudaMemcpyDeviceToDevice,
+                           st->stream));
+    if (cnt) {
+      if (polished)
+        CK(launch_support_add(st->Om64, 0, st->ld, st->p, cnt + (size_t)k * st->p * st->p,
+                              st->stream));
+      else
+        CK(launch_support_add(Om, mixed ? 1 : 0, st->ld, st->p, cnt + (size_t)k * st->p * st->p,
+                              st->stream));
+    }
+    return CONCORD_OK;
+  };
+  const int brk = mixed && st->path_polish ? 1 : 0;
   while (start < n) {
     RunOut o;
     int code = 0;
-    PathArgs pa{st->path_lam, n, start, st->path_res, om_out, ldo, cnt};
+    PathArgs pa{st->path_lam, n, start, st->path_res, om_out, ldo, cnt, brk};
     int rc = launch_screened_run<T>(st, S, W, Om, sd, omd, lambdas[start], tol, CONCORD_STOP_KKT,
                                     max_sweeps, 0, 0, mixed ? 1 : 0, &o, &code, &pa);
     if (rc != CONCORD_OK && rc != CONCORD_NOT_CONVERGED) return rc;
     CK(cudaMemcpy(rows.data(), st->path_res, sizeof(double) * kRes * n, cudaMemcpyDeviceToHost));
-    const int stop = code == kStatusDense ? (int)st->h_result[kResPath] : n;
+    const bool stalled = brk && code == 4;
+    const int stop = (code == kStatusDense || stalled) ? (int)st->h_result[kResPath] : n;
     for (int k = start; k < stop && k < n; ++k)
       if (results) result_from_row(results + k, rows.data() + (size_t)kRes * k, lambdas[k]);
-    if (code != kStatusDense) break;
+    if (code != kStatusDense && !stalled) break;
     // lambda `stop` on the dense-capable dispatcher (after the sweeps the
     // path launch already did at it), then the rest of the path
-    const int done = (int)st->h_result[kResSweeps];
-    RunOut od;
-    rc = launch_run<T>(st, S, W, Om, sd, omd, lambdas[stop], tol, CONCORD_STOP_KKT,
-                       max_sweeps > done ? max_sweeps - done : 1, 0, 0, mixed ? 1 : 0, &od);
-    if (rc != CONCORD_OK) return rc;
-    if (results) fill_result(results + stop, od, done + od.sweeps, mixed ? done + od.sweeps : 0,
-                             od.first_delta, lambdas[stop], 0.0);
-    if (om_out)
-      CK(cudaMemcpy2DAsync((T*)om_out + (size_t)stop * st->p * ldo, sizeof(T) * ldo, Om,
-                           sizeof(T) * st->ld, sizeof(T) * st->p, st->p, cudaMemcpyDeviceToDevice,
-                           st->stream));
-    if (cnt)
-      CK(launch_support_add(Om, mixed ? 1 : 0, st->ld, st->p, cnt + (size_t)stop * st->p * st->p,
-                            st->stream));
+    int done = (int)st->h_result[kResSweeps];
+    RunOut od = o;
+    bool stall_now = stalled;
+    if (code == kStatusDense) {
+      rc = launch_run<T>(st, S, W, Om, sd, omd, lambdas[stop], tol, CONCORD_STOP_KKT,
+                         max_sweeps > done ? max_sweeps - done : 1, 0, 0, mixed ? 1 : 0, &od);
+      if (rc != CONCORD_OK) return rc;
+      done += od.sweeps;
+      stall_now = brk && od.stalled;
+    }
+    if (stall_now) {
+      RunOut o2;
+      if ((rc = polish_path_lambda(st, lambdas[stop], tol, max_sweeps - done, &o2)) != CONCORD_OK)
+        return rc;
+      if (results) fill_result(results + stop, o2, done + o2.sweeps, done, od.first_delta,
+                               lambdas[stop], 0.0);
+    } else if (results) {
+      fill_result(results + stop, od, done, mixed ? done : 0, od.first_delta, lambdas[stop], 0.0);
+    }
+    if ((rc = finish(stop, stall_now)) != CONCORD_OK) return rc;
     start = stop + 1;
   }
   CK(cudaStreamSynchronize(st->stream));
@@ -806,6 +868,7 @@ int refine_s(concord_state* st, double lambda, int list) {
   a.nbr = st->rf.nbr;
   a.bitmap = st->rf.bitmap;
   a.ctr = st->rf.ctr;
+  a.mrow = st->mrow;
   CK(launch_refine_s(a, st->stream));
   CK(cudaMemcpyAsync(st->h_rf, st->rf.ctr + kRefineDone, sizeof(int), cudaMemcpyDeviceToHost,
                      st->stream));
@@ -901,6 +964,7 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
   const int fd = o1.first_delta ? o1.first_delta : (o2.first_delta ? o1.sweeps + o2.first_delta : 0);
   o2.redos += o1.redos;
   o2.dense_sweeps += o1.dense_sweeps;
+  o2.lazy += o1.lazy;
   o2.s_refined = *st->h_rf;  // read back by the polish launch's synchronisation
   fill_result(res, o2, o1.sweeps + o2.sweeps, o1.sweeps, fd, lambda, ms * 1e-3);
   return rc != CONCORD_OK ? rc : o2.status;
@@ -918,6 +982,10 @@ int reset_iterate(concord_state* st) {
                        st->stream));
   CK(launch_subdiag(st->S64, 0, ld, p, st->P, st->sd1_64, st->sd2_64, st->stream));
   if (is_mixed(st)) CK(launch_subdiag(st->S, 1, ld, p, st->P, st->sd1, st->sd2, st->stream));
+  // row bounds of S for the screened kernel's lazy verification (from the
+  // working-precision S; they bound the FP64 copy too)
+  CK(launch_row_absmax(is_mixed(st) ? st->S : (const void*)st->S64, is_mixed(st) ? 1 : 0, ld, p,
+                       st->mrow, st->stream));
   if (is_mixed(st)) {
     CK(launch_set_identity(st->Om, 1, p, ld, st->stream));
     CK(cudaMemcpyAsync(st->W, st->S, sizeof(float) * (size_t)p * ld, cudaMemcpyDeviceToDevice,
@@ -1043,6 +1111,7 @@ int concord_create(concord_state** out, int p, int precision, int n_cap, int dev
       st->Om = st->Om64;
     }
     ALLOC(st->sdiag64, sizeof(double) * p);
+    ALLOC(st->mrow, sizeof(float) * p);
     ALLOC(st->sd1_64, sizeof(double) * p);
     ALLOC(st->sd2_64, sizeof(double) * p);
     if (is_mixed(st)) {
@@ -1121,7 +1190,7 @@ int concord_destroy(concord_state* st) {
                  st->hist, st->result, st->mean, st->inv_scale, st->Z, st->Xstage, st->zt_hi,
                  st->zt_lo, st->sdiag64, st->sdiagT, st->omdiag64, st->S64, st->W64, st->Om64,
                  st->zt32, st->rf.cnt, st->rf.off, st->rf.cur, st->rf.nbr, st->rf.ctr, st->rf.cand,
-                 st->rf.bitmap};
+                 st->rf.bitmap, st->mrow};
   for (void* d : dev)
     if (d) cudaFree(d);
   void* adj_dev[] = {st->adj.cnt, st->adj.rowptr, st->adj.bad, st->adj.col, st->adj.erow,
@@ -1513,6 +1582,13 @@ int concord_set_rows_per_warp(concord_state* st, int rows) {
   if (!st) return fail(CONCORD_E_ARG, "state is NULL");
   if (rows < 0 || rows > 32) return fail(CONCORD_E_ARG, "rows per warp must be in 0..32");
   st->rows_per_warp = rows;
+  return CONCORD_OK;
+}
+
+int concord_set_lazy_verify(concord_state* st, int on) {
+  if (!st) return fail(CONCORD_E_ARG, "state is NULL");
+  if (on != 0 && on != 1) return fail(CONCORD_E_ARG, "on must be 0 or 1");
+  st->lazy_verify = on == 1;
   return CONCORD_OK;
 }
 

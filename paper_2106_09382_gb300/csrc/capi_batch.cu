@@ -51,9 +51,16 @@ struct Prob {
   void *S = nullptr, *W = nullptr, *Om = nullptr, *sdiagT = nullptr, *sd1 = nullptr,
        *sd2 = nullptr;
   double *sdiag64 = nullptr, *omdiag64 = nullptr, *partials = nullptr;
+  // MIXED: FP64 copies for the polish of a lambda whose FP32 sweeps stall
+  double *S64 = nullptr, *W64 = nullptr, *Om64 = nullptr, *sd1_64 = nullptr, *sd2_64 = nullptr;
   unsigned long long* mbox = nullptr;
   unsigned* barrier = nullptr;
   bool have_S = false;
+};
+
+// One problem's share of a launch: it walks lambdas[k0 .. k0 + nk).
+struct Item {
+  int b, k0, nk, stall_break, n_sweeps;
 };
 
 }  // namespace
@@ -64,6 +71,7 @@ struct concord_batch {
   std::vector<Prob> probs;
   double timeout_s = 2.0;
   int rows_per_warp = 0;  // 0: autotune on the first path call
+  bool polish = true;     // MIXED: FP64 polish of a lambda whose FP32 sweeps stall
   int last_ctas = 0, last_waves = 0;
   // data staging for concord_batch_gram (one problem at a time)
   double *Xg = nullptr, *mean = nullptr, *inv = nullptr, *part = nullptr;
@@ -89,8 +97,9 @@ bool is_mixed(const concord_batch* bt) { return bt->precision == CONCORD_MIXED; 
 size_t esz(const concord_batch* bt) { return is_mixed(bt) ? 4 : 8; }
 
 void free_prob(Prob& q) {
-  void* d[] = {q.S, q.W, q.Om, q.sdiagT, q.sd1, q.sd2, q.sdiag64, q.omdiag64, q.partials, q.mbox,
-               q.barrier};
+  void* d[] = {q.S,        q.W,      q.Om,     q.sdiagT, q.sd1,    q.sd2,  q.sdiag64,
+               q.omdiag64, q.partials, q.mbox, q.barrier, q.S64, q.W64, q.Om64,
+               q.sd1_64,   q.sd2_64};
   for (void* x : d)
     if (x) cudaFree(x);
   q = Prob();
@@ -121,14 +130,15 @@ int reset_prob(concord_batch* bt, Prob& q) {
   const int f32 = is_mixed(bt) ? 1 : 0;
   cudaStream_t s = bt->stream;
   BCK(cudaMemsetAsync(bt->flag, 0, sizeof(int), s));
-  if (f32) {
-    BCK(launch_extract_diag(q.S, 1, q.ld, q.p, q.sdiag64, q.sdiagT, 1, bt->flag, s));
+  if (f32) {  // the FP64 diagonal from the FP64 copy of S, as a single state keeps it
+    BCK(launch_extract_diag(q.S64, 0, q.ld, q.p, q.sdiag64, q.sdiagT, 1, bt->flag, s));
     BCK(launch_fill_f64(q.omdiag64, 1.0, q.p, s));
   } else {
     BCK(launch_extract_diag(q.S, 0, q.ld, q.p, q.sdiag64, nullptr, 0, bt->flag, s));
     BCK(cudaMemcpyAsync(q.sdiagT, q.sdiag64, sizeof(double) * q.p, cudaMemcpyDeviceToDevice, s));
   }
   BCK(launch_subdiag(q.S, f32, q.ld, q.p, q.P, q.sd1, q.sd2, s));
+  if (f32) BCK(launch_subdiag(q.S64, 0, q.ld, q.p, q.P, q.sd1_64, q.sd2_64, s));
   BCK(launch_set_identity(q.Om, f32, q.p, q.ld, s));
   BCK(cudaMemcpyAsync(q.W, q.S, esz(bt) * (size_t)q.p * q.ld, cudaMemcpyDeviceToDevice, s));
   BCK(cudaMemcpyAsync(bt->h_flag, bt->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -145,37 +155,26 @@ int ctas_for(int p, int rows) {
   return (p + per_cta - 1) / per_cta;
 }
 
-// Greedy waves of consecutive problems whose CTAs fit co-resident.
-std::vector<std::pair<int, int>> make_waves(const concord_batch* bt, int rows, int capacity) {
-  std::vector<std::pair<int, int>> waves;
-  const int B = (int)bt->probs.size();
-  int b0 = 0, used = 0;
-  for (int b = 0; b < B; ++b) {
-    const int c = ctas_for(bt->probs[b].p, rows);
-    if (used + c > capacity && b > b0) {
-      waves.push_back({b0, b});
-      b0 = b;
-      used = 0;
-    }
-    used += c;
-  }
-  if (b0 < B) waves.push_back({b0, B});
-  return waves;
-}
-
+// One launch per wave of co-resident items.  T = float: the FP32 arrays of
+// a MIXED batch; T = double: the arrays of an FP64 batch, or the FP64 copies
+// of a MIXED batch (its polish).  Result rows land at [b][k] of the batch's
+// n_problems x n_lambda table, copied back into res_host.
 template <typename T>
-int run_waves(concord_batch* bt, int rows, const double* lambdas_host, int n_lambda, double tol,
-              int max_sweeps, float* support_dev, std::vector<double>* res_host) {
+int run_waves(concord_batch* bt, int rows, const std::vector<Item>& items,
+              const double* lambdas_host, int n_lambda, double tol, int max_sweeps, int stall_stop,
+              float* support_dev, std::vector<double>* res_host) {
   cudaStream_t s = bt->stream;
   const int B = (int)bt->probs.size();
+  const int nI = (int)items.size();
+  const bool copies = sizeof(T) == 8 && is_mixed(bt);
   int occ = 0;
-  BCK(sweep_occupancy(is_mixed(bt), kSweepThreads, &occ));
+  BCK(sweep_occupancy(sizeof(T) == 4, kSweepThreads, &occ));
   if (occ < 1) return bfail(CONCORD_E_OCCUPANCY, "sweep kernel cannot be resident");
   const int capacity = bt->sms * occ;
-  for (const auto& q : bt->probs)
-    if (ctas_for(q.p, rows) > capacity)
-      return bfail(CONCORD_E_ARG, "p=%d needs more than %d CTAs at %d rows per warp", q.p,
-                   capacity, rows);
+  for (const auto& it : items)
+    if (ctas_for(bt->probs[it.b].p, rows) > capacity)
+      return bfail(CONCORD_E_ARG, "p=%d needs more than %d CTAs at %d rows per warp",
+                   bt->probs[it.b].p, capacity, rows);
   // device copies of the lambdas, the result rows and the problem table
   if (n_lambda > bt->lam_cap) {
     if (bt->lam_dev) cudaFree(bt->lam_dev);
@@ -193,19 +192,34 @@ int run_waves(concord_batch* bt, int rows, const double* lambdas_host, int n_lam
     bt->res_cap = nres;
   }
   BCK(cudaMemsetAsync(bt->res_dev, 0, sizeof(double) * nres, s));
-  if ((size_t)B * sizeof(BatchProblem<T>) > bt->probs_cap) {
+  if ((size_t)nI * sizeof(BatchProblem<T>) > bt->probs_cap) {
     if (bt->probs_dev) cudaFree(bt->probs_dev);
     bt->probs_dev = nullptr;
-    BCK(cudaMalloc(&bt->probs_dev, (size_t)B * sizeof(BatchProblem<T>)));
-    bt->probs_cap = (size_t)B * sizeof(BatchProblem<T>);
+    BCK(cudaMalloc(&bt->probs_dev, (size_t)nI * sizeof(BatchProblem<T>)));
+    bt->probs_cap = (size_t)nI * sizeof(BatchProblem<T>);
   }
-  const auto waves = make_waves(bt, rows, capacity);
-  std::vector<BatchProblem<T>> table(B);
+  // greedy waves of consecutive items whose CTAs fit co-resident
+  std::vector<std::pair<int, int>> waves;
+  {
+    int i0 = 0, used = 0;
+    for (int i = 0; i < nI; ++i) {
+      const int c = ctas_for(bt->probs[items[i].b].p, rows);
+      if (used + c > capacity && i > i0) {
+        waves.push_back({i0, i});
+        i0 = i;
+        used = 0;
+      }
+      used += c;
+    }
+    if (i0 < nI) waves.push_back({i0, nI});
+  }
+  std::vector<BatchProblem<T>> table(nI);
   for (const auto& w : waves) {
     int cta0 = 0;
-    for (int b = w.first; b < w.second; ++b) {
-      Prob& q = bt->probs[b];
-      BatchProblem<T>& e = table[b];
+    for (int i = w.first; i < w.second; ++i) {
+      const Item& it = items[i];
+      Prob& q = bt->probs[it.b];
+      BatchProblem<T>& e = table[i];
       memset(&e, 0, sizeof e);
       e.p = q.p;
       e.P = q.P;
@@ -213,25 +227,29 @@ int run_waves(concord_batch* bt, int rows, const double* lambdas_host, int n_lam
       e.cta0 = cta0;
       e.ctas = ctas_for(q.p, rows);
       cta0 += e.ctas;
-      e.W = (T*)q.W;
-      e.Om = (T*)q.Om;
-      e.S = (const T*)q.S;
-      e.sdiag = (const T*)q.sdiagT;
-      e.sd1 = (const T*)q.sd1;
-      e.sd2 = (const T*)q.sd2;
+      e.W = (T*)(copies ? (void*)q.W64 : q.W);
+      e.Om = (T*)(copies ? (void*)q.Om64 : q.Om);
+      e.S = (const T*)(copies ? (void*)q.S64 : q.S);
+      e.sdiag = (const T*)(copies ? (void*)q.sdiag64 : q.sdiagT);
+      e.sd1 = (const T*)(copies ? (void*)q.sd1_64 : q.sd1);
+      e.sd2 = (const T*)(copies ? (void*)q.sd2_64 : q.sd2);
       e.sdiag64 = q.sdiag64;
-      e.omdiag64 = is_mixed(bt) ? q.omdiag64 : nullptr;
+      e.omdiag64 = sizeof(T) == 4 ? q.omdiag64 : nullptr;
       e.mbox = q.mbox;
       e.barrier = q.barrier;
       e.partials = q.partials;
-      e.result = bt->res_dev + (size_t)b * n_lambda * kRes;
-      e.cnt = support_dev;
+      e.result = bt->res_dev + ((size_t)it.b * n_lambda + it.k0) * kRes;
+      e.cnt = support_dev ? support_dev + (size_t)it.k0 * q.p * q.p : nullptr;
+      e.k0 = it.k0;
+      e.nk = it.nk;
+      e.stall_break = it.stall_break;
+      e.n_sweeps = it.n_sweeps;
       // fresh mailboxes: this launch's step tags start at 1
       BCK(cudaMemsetAsync(q.mbox, 0, sizeof(unsigned long long) * 2 * (size_t)kDepth * q.pe, s));
       BCK(cudaMemsetAsync(q.barrier, 0, sizeof(unsigned), s));
     }
   }
-  BCK(cudaMemcpyAsync(bt->probs_dev, table.data(), (size_t)B * sizeof(BatchProblem<T>),
+  BCK(cudaMemcpyAsync(bt->probs_dev, table.data(), (size_t)nI * sizeof(BatchProblem<T>),
                       cudaMemcpyHostToDevice, s));
   BCK(cudaMemsetAsync(bt->abort_info, 0, 3 * sizeof(int), s));
   BCK(cudaEventRecord(bt->ev0, s));
@@ -254,7 +272,7 @@ int run_waves(concord_batch* bt, int rows, const double* lambdas_host, int n_lam
     a.delta_tol = 1e-5;
     a.stop_rule = CONCORD_STOP_KKT;
     a.n_sweeps = max_sweeps;
-    a.stall_stop = is_mixed(bt) ? 1 : 0;
+    a.stall_stop = stall_stop;
     a.tag_base = 1;
     a.fault_vertex = -1;
     a.fault_step = -1;
@@ -263,7 +281,7 @@ int run_waves(concord_batch* bt, int rows, const double* lambdas_host, int n_lam
     a.lambdas = bt->lam_dev;
     a.n_lambda = n_lambda;
     int grid = 0;
-    for (int b = w.first; b < w.second; ++b) grid += table[b].ctas;
+    for (int i = w.first; i < w.second; ++i) grid += table[i].ctas;
     total_ctas = std::max(total_ctas, grid);
     BCK(launch_sweep_batch(a, grid, kSweepThreads, s));
   }
@@ -275,25 +293,125 @@ int run_waves(concord_batch* bt, int rows, const double* lambdas_host, int n_lam
   BCK(cudaMemcpyAsync(h_abort, bt->abort_info, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
   BCK(cudaStreamSynchronize(s));
   BCK(cudaGetLastError());
-  BCK(cudaEventElapsedTime(&bt->last_ms, bt->ev0, bt->ev1));
-  bt->last_ctas = total_ctas;
-  bt->last_waves = (int)waves.size();
+  float ms = 0.f;
+  BCK(cudaEventElapsedTime(&ms, bt->ev0, bt->ev1));
+  bt->last_ms = ms;
+  bt->last_ctas = std::max(bt->last_ctas, total_ctas);
+  bt->last_waves = std::max(bt->last_waves, (int)waves.size());
   if (h_abort[0] != 0)
     return bfail(CONCORD_E_TIMEOUT, "batched sweep: a device wait ran out (where %d, step %d)",
                  h_abort[1], h_abort[2]);
   return CONCORD_OK;
 }
 
+std::vector<Item> all_items(const concord_batch* bt, int n_lambda, int stall_break) {
+  std::vector<Item> items;
+  for (int b = 0; b < (int)bt->probs.size(); ++b) items.push_back({b, 0, n_lambda, stall_break, 0});
+  return items;
+}
+
 int run_any(concord_batch* bt, int rows, const double* lambdas, int n_lambda, double tol,
             int max_sweeps, float* support_dev, std::vector<double>* res) {
-  return is_mixed(bt) ? run_waves<float>(bt, rows, lambdas, n_lambda, tol, max_sweeps,
+  const auto items = all_items(bt, n_lambda, 0);
+  bt->last_ctas = bt->last_waves = 0;
+  return is_mixed(bt) ? run_waves<float>(bt, rows, items, lambdas, n_lambda, tol, max_sweeps, 1,
                                          support_dev, res)
-                      : run_waves<double>(bt, rows, lambdas, n_lambda, tol, max_sweeps,
+                      : run_waves<double>(bt, rows, items, lambdas, n_lambda, tol, max_sweeps, 0,
                                           support_dev, res);
 }
 
-void fill_results(const std::vector<double>& r, int B, int n_lambda, const double* lambdas,
-                  concord_result* out) {
+// MIXED polish of problem b: FP64 copies from the FP32 iterate (W rebuilt in
+// FP64 from Omega and S64) / the FP32 working set back from them.
+int promote(concord_batch* bt, Prob& q) {
+  cudaStream_t s = bt->stream;
+  BCK(launch_convert(q.Om, 1, q.ld, q.Om64, 0, q.ld, q.p, q.p, s));
+  BCK(cudaMemcpy2DAsync(q.Om64, (size_t)(q.ld + 1) * sizeof(double), q.omdiag64, sizeof(double),
+                        sizeof(double), q.p, cudaMemcpyDeviceToDevice, s));
+  BCK(launch_refresh_w(q.Om64, q.S64, q.W64, q.p, q.ld, bt->sms, s));
+  return CONCORD_OK;
+}
+int demote(concord_batch* bt, Prob& q) {
+  cudaStream_t s = bt->stream;
+  BCK(launch_convert(q.Om64, 0, q.ld, q.Om, 1, q.ld, q.p, q.p, s));
+  BCK(launch_convert(q.W64, 0, q.ld, q.W, 1, q.ld, q.p, q.p, s));
+  BCK(cudaMemcpy2DAsync(q.omdiag64, sizeof(double), q.Om64, (size_t)(q.ld + 1) * sizeof(double),
+                        sizeof(double), q.p, cudaMemcpyDeviceToDevice, s));
+  return CONCORD_OK;
+}
+
+// The MIXED path with polish: the FP32 launches walk every problem's path
+// until a lambda's sweeps stall (the problem's walk ends there); those
+// lambdas are polished in FP64 (one launch for all of them), their support
+// counted from the FP64 iterate, and the walks resume after them.
+int mixed_path(concord_batch* bt, int rows, const double* lambdas, int n_lambda, double tol,
+               int max_sweeps, float* support_dev, std::vector<double>* R,
+               std::vector<int>* sweeps32) {
+  const int B = (int)bt->probs.size();
+  R->assign((size_t)B * n_lambda * kRes, 0.0);
+  sweeps32->assign((size_t)B * n_lambda, 0);
+  std::vector<int> next(B, 0);
+  std::vector<double> res;
+  bt->last_ctas = bt->last_waves = 0;
+  float total_ms = 0.f;
+  for (;;) {
+    std::vector<Item> items;
+    for (int b = 0; b < B; ++b)
+      if (next[b] < n_lambda) items.push_back({b, next[b], n_lambda - next[b], 1, 0});
+    if (items.empty()) break;
+    int rc = run_waves<float>(bt, rows, items, lambdas, n_lambda, tol, max_sweeps, 1, support_dev,
+                              &res);
+    if (rc != CONCORD_OK) return rc;
+    total_ms += bt->last_ms;
+    std::vector<Item> pol;
+    for (const Item& it : items) {
+      int k = it.k0;
+      for (; k < n_lambda; ++k) {
+        const double* x = res.data() + ((size_t)it.b * n_lambda + k) * kRes;
+        const size_t o = ((size_t)it.b * n_lambda + k) * kRes;
+        for (int q = 0; q < kRes; ++q) (*R)[o + q] = x[q];
+        (*sweeps32)[(size_t)it.b * n_lambda + k] = (int)x[kResSweeps];
+        const int code = (int)x[kResStatus];
+        if (code == 4) break;              // stalled: polish it
+        if (code == 2 || code == 3) {      // non-finite / aborted: the walk ended
+          k = n_lambda;
+          break;
+        }
+      }
+      if (k < n_lambda) {
+        const int done = (*sweeps32)[(size_t)it.b * n_lambda + k];
+        pol.push_back({it.b, k, 1, 0, max_sweeps > done ? max_sweeps - done : 1});
+        next[it.b] = k;
+      } else {
+        next[it.b] = n_lambda;
+      }
+    }
+    if (pol.empty()) break;
+    for (const Item& it : pol)
+      if ((rc = promote(bt, bt->probs[it.b])) != CONCORD_OK) return rc;
+    rc = run_waves<double>(bt, rows, pol, lambdas, n_lambda, tol, max_sweeps, 0, nullptr, &res);
+    if (rc != CONCORD_OK) return rc;
+    total_ms += bt->last_ms;
+    for (const Item& it : pol) {
+      Prob& q = bt->probs[it.b];
+      if ((rc = demote(bt, q)) != CONCORD_OK) return rc;
+      if (support_dev)
+        BCK(launch_support_add(q.Om64, 0, q.ld, q.p, support_dev + (size_t)it.k0 * q.p * q.p,
+                               bt->stream));
+      const size_t o = ((size_t)it.b * n_lambda + it.k0) * kRes;
+      const double* x = res.data() + o;
+      const double s32 = (*R)[o + kResSweeps];
+      for (int q2 = 0; q2 < kRes; ++q2) (*R)[o + q2] = x[q2];
+      (*R)[o + kResSweeps] = s32 + x[kResSweeps];
+      next[it.b] = it.k0 + 1;
+    }
+  }
+  BCK(cudaStreamSynchronize(bt->stream));
+  bt->last_ms = total_ms;
+  return CONCORD_OK;
+}
+
+void fill_results(const std::vector<double>& r, const std::vector<int>* sweeps32, int B,
+                  int n_lambda, const double* lambdas, concord_result* out) {
   for (int b = 0; b < B; ++b)
     for (int k = 0; k < n_lambda; ++k) {
       const double* x = r.data() + ((size_t)b * n_lambda + k) * kRes;
@@ -314,6 +432,7 @@ void fill_results(const std::vector<double>& r, int B, int n_lambda, const doubl
       o.timeout_vertex = -1;
       o.timeout_step = -1;
       o.dense_sweeps = o.sweeps;
+      if (sweeps32) o.sweeps_fp32 = (*sweeps32)[(size_t)b * n_lambda + k];
     }
 }
 
@@ -376,6 +495,16 @@ int concord_batch_create(concord_batch** out, int n_problems, const int* p, int 
     BALLOC(q.partials, sizeof(double) * kParts * (size_t)ctas_for(q.p, 2));
     BALLOC(q.mbox, sizeof(unsigned long long) * 2 * (size_t)kDepth * q.pe);
     BALLOC(q.barrier, sizeof(unsigned));
+    if (e == 4) {
+      const size_t mat64 = sizeof(double) * (size_t)q.p * q.ld;
+      BALLOC(q.S64, mat64);
+      BALLOC(q.W64, mat64);
+      BALLOC(q.Om64, mat64);
+      BALLOC(q.sd1_64, sizeof(double) * (q.P + 1));
+      BALLOC(q.sd2_64, sizeof(double) * (q.P + 1));
+      cudaMemsetAsync(q.S64, 0, mat64, bt->stream);
+      launch_set_identity(q.S64, 0, q.p, q.ld, bt->stream);
+    }
     cudaMemsetAsync(q.S, 0, mat, bt->stream);
     launch_set_identity(q.S, e == 4 ? 1 : 0, q.p, q.ld, bt->stream);
   }
@@ -437,6 +566,13 @@ int concord_batch_set_timeout(concord_batch* bt, double seconds) {
   return CONCORD_OK;
 }
 
+int concord_batch_set_polish(concord_batch* bt, int on) {
+  if (!bt) return bfail(CONCORD_E_ARG, "batch is NULL");
+  if (on != 0 && on != 1) return bfail(CONCORD_E_ARG, "on must be 0 or 1");
+  bt->polish = on == 1;
+  return CONCORD_OK;
+}
+
 int concord_batch_set_rows_per_warp(concord_batch* bt, int rows) {
   if (!bt) return bfail(CONCORD_E_ARG, "batch is NULL");
   if (rows != 0 && rows != 2 && rows != 4 && rows != 8 && rows != 16 && rows != 32)
@@ -470,6 +606,8 @@ int concord_batch_set_S(concord_batch* bt, int b, const void* S_dev, int s_dtype
   if (*bt->h_flag & 2) return bfail(CONCORD_E_NONFINITE, "S has a non-finite entry");
   if (*bt->h_flag & 1) return bfail(CONCORD_E_ARG, "S is not symmetric");
   BCK(launch_convert(S_dev, f32, lds, q.S, is_mixed(bt) ? 1 : 0, q.ld, q.p, q.p, bt->stream));
+  if (is_mixed(bt))
+    BCK(launch_convert(S_dev, f32, lds, q.S64, 0, q.ld, q.p, q.p, bt->stream));
   return reset_prob(bt, q);
 }
 
@@ -505,6 +643,7 @@ int concord_batch_gram(concord_batch* bt, int b, const void* X_dev, int x_dtype,
                                        1.0f / nr, bt->flag, s);
     if (e == cudaErrorNotSupported) return bfail(CONCORD_E_CUDA, "tensor-core Gram unavailable");
     BCK(e);
+    BCK(launch_convert(q.S, 1, q.ld, q.S64, 0, q.ld, p, p, s));
   } else {
     const int ldz = rup(p, kTile);
     BCK(launch_apply_prep(bt->Xg, 0, nr, p, p, bt->mean, bt->inv, bt->Z, 0, ldz, s));
@@ -578,9 +717,23 @@ int concord_batch_path(concord_batch* bt, const double* lambdas, int n_lambda, d
       return rc;
   }
   std::vector<double> res;
+  if (is_mixed(bt) && bt->polish) {
+    std::vector<int> s32;
+    rc = mixed_path(bt, bt->rows_per_warp, lambdas, n_lambda, tol, max_sweeps, support_dev, &res,
+                    &s32);
+    if (rc != CONCORD_OK) return rc;
+    if (results) fill_results(res, &s32, (int)bt->probs.size(), n_lambda, lambdas, results);
+    return CONCORD_OK;
+  }
   rc = run_any(bt, bt->rows_per_warp, lambdas, n_lambda, tol, max_sweeps, support_dev, &res);
   if (rc != CONCORD_OK) return rc;
-  if (results) fill_results(res, (int)bt->probs.size(), n_lambda, lambdas, results);
+  if (results) {
+    std::vector<int> s32;
+    if (is_mixed(bt))
+      for (size_t q = 0; q < res.size() / kRes; ++q) s32.push_back((int)res[q * kRes + kResSweeps]);
+    fill_results(res, is_mixed(bt) ? &s32 : nullptr, (int)bt->probs.size(), n_lambda, lambdas,
+                 results);
+  }
   return CONCORD_OK;
 }
 

@@ -40,8 +40,9 @@ constexpr int kParts = 8;
 constexpr int kResSweeps = 0, kResKkt = 1, kResObj = 2, kResDelta = 3, kResActive = 4,
               kResFirstDelta = 5, kResStatus = 6, kResRedo = 7,  // kResRedo: screened only
               kResPath = 8,  // screened path: index of the lambda a dense hand-over stopped at
-              kResList = 9;  // screened: candidate list of the next sweep (-1: none valid)
-constexpr int kRes = 10;
+              kResList = 9,  // screened: candidate list of the next sweep (-1: none valid)
+              kResLazy = 10; // screened: sweeps that skipped the verification (lazy)
+constexpr int kRes = 11;
 constexpr int kHist = 4;  // per sweep: delta, kkt, objective, active pairs
 
 // One problem of a batched launch of the sweep kernel: its own dimension,
@@ -59,8 +60,11 @@ struct BatchProblem {
   unsigned long long* mbox;  // depth x (P+1) x words, tags below the launch's first
   unsigned* barrier;         // zeroed before the launch
   double* partials;          // ctas x kParts
-  double* result;            // n_lambda x kRes: the result of each lambda
-  float* cnt;                // nullable: slice k (p x p) += [w_ij != 0] after lambda k
+  double* result;            // nk x kRes: the result of each lambda it walks
+  float* cnt;                // nullable: slice k (p x p) += [w_ij != 0] after its lambda k
+  int k0, nk;                // it walks lambdas[k0 .. k0 + nk)
+  int stall_break;           // a lambda that ends on the stall rule ends the problem's walk
+  int n_sweeps;              // > 0: its sweep limit per lambda (else the launch's)
 };
 
 template <typename T>
@@ -96,6 +100,7 @@ struct SweepArgs {
   const double* lambdas;
   int n_lambda;
   float* batch_cnt;          // (set per problem inside the kernel) its support counts
+  int stall_break;           // (set per problem inside the kernel)
 };
 
 // cluster = true: the whole grid is one thread-block cluster (grid <= 16).
@@ -151,6 +156,7 @@ struct ScreenWork {
   T* diag_old;              // [p] diagonal before the sweep (for a redo)
   double* omdiag_old;       // [p] FP64 diagonal before the sweep (mixed precision)
   double* diag_new;         // [p] the sweep's new FP64 diagonal, committed after the row pass
+  double* dpart;            // [grid] per-CTA largest row bound of the sweep (lazy verification)
   int nc_cap, term_cap, fail_cap;
 };
 
@@ -186,6 +192,13 @@ struct ScreenArgs {
   T* path_om;               // nullable: Omega after each lambda, slice k at k p ldo
   int path_ldo;
   float* path_cnt;          // nullable: slice k (p x p) += [w_ij != 0] after lambda k (atomic)
+  // lazy verification: a sweep whose changes provably keep every pair outside
+  // the candidates below the threshold skips the verification pass and keeps
+  // its candidate list (and the build of it) for the next sweep
+  const float* mrow;        // [p] m[u] >= max_{x != u} |s_ux|
+  int lazy_verify;
+  int path_break_stall;     // a lambda that ends on the stall rule ends the launch (the
+                            // host polishes it in FP64 and resumes the path after it)
 };
 
 size_t screened_dyn_smem(bool mixed);
@@ -228,6 +241,9 @@ cudaError_t launch_subdiag(const void* S, int s_f32, int ld, int p, int P, void*
                            cudaStream_t st);
 // a[0..n) = v.
 cudaError_t launch_fill_f64(double* a, double v, int n, cudaStream_t st);
+// m[u] >= max_{x != u} |S[u][x]| (float, rounded up; for FP32 S one step
+// above, so it also bounds an FP64 copy of S rounded to this S).
+cudaError_t launch_row_absmax(const void* S, int s_f32, int ld, int p, float* m, cudaStream_t st);
 // A (p x ld, type) = identity with zero padding.
 cudaError_t launch_set_identity(void* A, int a_f32, int p, int ld, cudaStream_t st);
 // bad |= 1 if |A - A^T| != 0 anywhere or a non-finite entry is met.
@@ -283,6 +299,7 @@ struct RefineArgs {
   int own_cap;
   double* S64;               // p x ld: entries recomputed in place (both triangles)
   float* S32;                // p x ld: the same entries rounded to FP32
+  float* mrow;               // [p] row bounds max_{x != u} |s_ux|, raised where an entry grows
   int *nbr_cnt, *nbr_off, *nbr_cur;  // [p + 1]
   int* nbr;                  // [2 x max(list length)]
   unsigned* bitmap;          // [refine_bitmap_words(p)]

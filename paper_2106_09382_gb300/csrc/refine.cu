@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(256) k_refine(const int2* __restrict__ cand,
                                                 const float* __restrict__ zt, int ldn, double inv_n,
                                                 double* __restrict__ S64, float* __restrict__ S32,
                                                 int ld, unsigned* __restrict__ bitmap,
+                                                float* __restrict__ mrow,
                                                 int* __restrict__ n_done) {
   const int lane = threadIdx.x & 31;
   const int nc = *n_cand;
@@ -223,6 +224,11 @@ __global__ void __launch_bounds__(256) k_refine(const int2* __restrict__ cand,
           S64[(size_t)b * ld + a] = v;
           S32[(size_t)a * ld + b] = (float)v;
           S32[(size_t)b * ld + a] = (float)v;
+          if (a != b && mrow) {  // keep the row bounds valid (nonnegative floats order as ints)
+            const int mb = __float_as_int(nextafterf(__double2float_ru(fabs(v)), INFINITY));
+            atomicMax(reinterpret_cast<int*>(mrow) + a, mb);
+            atomicMax(reinterpret_cast<int*>(mrow) + b, mb);
+          }
           ++done;
         }
       }
@@ -257,7 +263,7 @@ cudaError_t launch_refine_s(const RefineArgs& a, cudaStream_t st) {
   k_nbr_scan<<<1, 1024, 0, st>>>(a.nbr_cnt, p, a.nbr_off, a.nbr_cur);
   k_nbr_fill<<<a.sms * 4, 256, 0, st>>>(cand, n_cand, a.nbr_cur, a.nbr);
   k_refine<<<a.sms * 8, 256, 0, st>>>(cand, n_cand, a.nbr_off, a.nbr, p, a.zt, a.ldn,
-                                      1.0 / a.n, a.S64, a.S32, a.ld, a.bitmap,
+                                      1.0 / a.n, a.S64, a.S32, a.ld, a.bitmap, a.mrow,
                                       a.ctr + kRefineDone);
   note_launches(4);
   return cudaGetLastError();

@@ -45,6 +45,20 @@ namespace concord {
 // fail the verification and force a redo of the sweep.
 constexpr double kScreenMargin = 0.1;
 
+// Lazy verification.  Every pair outside the candidate list had
+// |G_ij| <= (1 - kScreenMargin) lambda when the list was screened.  A change d
+// of a candidate (i, u) moves W_ix by d s_ux for x != u, so by at most
+// |d| m_u (m_u = max_{x != u} |s_ux|), and a diagonal change moves W_ix by at
+// most |dw| m_i.  With D_i the sum of those bounds over a sweep's changes of
+// row i, G_ij of a pair outside the list moves by at most D_i + D_j <=
+// 2 max_i D_i per sweep.  While the bounds accumulated since the screen stay
+// within (kScreenMargin - kLazySlack) lambda, no such pair can reach the
+// threshold at its visit (so the verification would pass) nor at the sweep's
+// end (so its KKT term is zero): the sweep skips the verification pass, and
+// the list, with its build, serves the next sweep too.  kLazySlack lambda is
+// left for rounding (far more than FP32 accumulates on W over a few sweeps).
+constexpr double kLazySlack = 0.01;
+
 // Candidates of one row sorted by a warp in shared memory (longer rows: one
 // thread, insertion sort).
 constexpr int kSortCap = 512;
@@ -456,6 +470,9 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
   __shared__ int s_tmp[32];
   __shared__ double s_res[kRes];
   __shared__ int s_stop;
+  __shared__ unsigned long long s_dmax;  // the CTA's largest row bound D_i of the sweep (bits)
+  __shared__ int s_fast;
+  __shared__ double s_dsweep;
   extern __shared__ __align__(128) unsigned char dyn[];
 
   unsigned gen = 0;
@@ -469,6 +486,12 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
   const bool kkt0 = a.kkt_only || a.n_sweeps <= 0;  // objective / KKT only
   int redo_total = 0;
   bool need_scan = true;  // row offsets of the current list still to be computed
+  // lazy verification (see kLazySlack): bound accumulated on the pairs outside
+  // the current list since it was screened, and whether the list's build is
+  // kept from the previous sweep
+  double acc = 0.0;
+  bool reuse = false;
+  int n_lazy = 0;
 
   // ---------------- screen the starting point (and its KKT for kkt_only);
   //                  the host zeroed the counters and row counts.  Or take
@@ -478,6 +501,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
   if (a.start_list >= 0 && !kkt0) {
     cur = a.start_list;
     need_scan = false;  // its row offsets and term count are in place
+    acc = INFINITY;     // screened by another launch: the first sweep verifies
   } else {
     double v[kParts];
 #pragma unroll
@@ -492,9 +516,11 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
     double v[kParts];
 #pragma unroll
     for (int k = 0; k < kParts; ++k) v[k] = 0.0;
+    bool fast = false;  // this sweep skipped the verification (lazy)
     if (do_sweep) {
       int redo = 0;
       for (;;) {  // until the verification passes
+        if (threadIdx.x == 0) s_dmax = 0ull;
         const int N = ldi(w.ctr + kCtrCand + cur);
         if (N > w.nc_cap || ld_relaxed_s32(wc.abort) != 0) {
           status = kStatusDense;
@@ -503,7 +529,9 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         const int2* cand = w.cand[cur];
         // ---- build: row buckets of the current list (counted at the push),
         //      each row's candidates in colour-step order, and per candidate
-        //      its record and correction terms
+        //      its record and correction terms (kept from the previous sweep
+        //      when it reused its list: only the records are refreshed)
+        if (!reuse) {
         if (need_scan) {  // else the previous sweep's reduce phase scanned the counts
           if (blockIdx.x == 0) {
             cta_scan([&](int k) { return ldi(w.cnt_r[cur] + k); }, p, w.off_r, w.cur_r, s_tmp);
@@ -577,6 +605,9 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
           }
         }
         grid_barrier(a.barrier, gen, wc, ++where);
+        } else {
+          need_scan = true;
+        }
         // operands; each candidate's terms (row i's earlier candidates, then
         // row j's) get a contiguous range from a shared counter -- where the
         // range lies does not affect any value
@@ -587,6 +618,10 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
           rec[0] = __ldcg(Wa + (size_t)i * ld + j);
           rec[1] = __ldcg(Wa + (size_t)j * ld + i);
           rec[2] = __ldcg(a.Om + (size_t)i * ld + j);
+          if (reuse) {  // terms and s_ii + s_jj as the previous sweep built them
+            w.nd_delta[k] = (T)0;
+            continue;
+          }
           rec[3] = a.sdiag[i] + a.sdiag[j];
           const int bi = ldi(w.off_r + i), pi = ldi(w.nd_pi + k);
           const int bj = ldi(w.off_r + j), pj = ldi(w.nd_pj + k);
@@ -774,6 +809,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
             // every lane), then the root (Eq. 2) on lane 0
             T wii = __ldcg(Wa + (size_t)i * ld + i);
             int my_u = -1;  // lane m < 32: partner of the row's m-th candidate
+            double dsum = 0.0;  // lazy verification: sum of |d| m_u over the row's changes
             for (int m0 = 0; m0 < ne; m0 += 32) {
               const int m = m0 + lane;
               T d = (T)0, sv = (T)0;
@@ -783,7 +819,10 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
                 const int u = qp.x == i ? qp.y : qp.x;
                 if (m0 == 0) my_u = u;
                 d = __ldcg(w.nd_delta + q);
-                if (d != (T)0) sv = __ldg(a.S + (size_t)u * ld + i);
+                if (d != (T)0) {
+                  sv = __ldg(a.S + (size_t)u * ld + i);
+                  if (half == 0) dsum += fabs((double)d) * (double)__ldg(a.mrow + u);
+                }
               }
               const int nm = min(32, ne - m0);
               for (int r = 0; r < nm; ++r) {
@@ -822,6 +861,14 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
             }
             dd = __shfl_sync(FULL, dd, 0);
             v[kPartDelta] = fmax(v[kPartDelta], dd64);
+            if (half == 0) {  // the row's bound D_i into the CTA's maximum
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(FULL, dsum, o);
+              if (lane == 0) {
+                const double di = dsum + dd64 * (double)__ldg(a.mrow + i);
+                atomicMax(&s_dmax, (unsigned long long)__double_as_longlong(di));
+              }
+            }
             // the row's changes in step order, in chunks of kRowList
             const T* Srow = a.S + (size_t)i * ld;
             int c_last = -1;  // step of the last change of the previous chunks
@@ -967,6 +1014,8 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
             __syncwarp();
           }
         }
+        __syncthreads();
+        if (threadIdx.x == 0) w.dpart[blockIdx.x] = __longlong_as_double((long long)s_dmax);
         // ---- commit the candidates' new values (both triangles)
         for (int k = gtid; k < N; k += gthreads) {
           const T d = __ldcg(w.nd_delta + k);
@@ -980,6 +1029,15 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
           }
         }
         grid_barrier(a.barrier, gen, wc, ++where);
+        // ---- lazy verification: every CTA forms the same decision
+        if (threadIdx.x == 0) {
+          double dm = 0.0;
+          for (int c = 0; c < (int)gridDim.x; ++c) dm = fmax(dm, __ldcg(w.dpart + c));
+          s_dsweep = dm;
+          s_fast = (a.lazy_verify && acc + 2.0 * dm <= (kScreenMargin - kLazySlack) * lamd) ? 1 : 0;
+        }
+        __syncthreads();
+        fast = s_fast != 0;
         // ---- the new diagonal (both halves of a row read the old one above)
         for (int k = gtid; k < p; k += gthreads) {
           const double nw = __ldcg(w.diag_new + k);
@@ -987,7 +1045,9 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
           if (MIXED) a.omdiag64[k] = nw;
         }
         // ---- verify the other pairs; objective / KKT; screen the next sweep
-        verify_pass<T>(a, Wn, a.V, 1 - cur, lamd, v, lane, gwarp, gwarps);
+        //      (skipped by a lazy sweep: none of them can have reached the
+        //      threshold, their KKT terms are zero, and the list stays)
+        if (!fast) verify_pass<T>(a, Wn, a.V, 1 - cur, lamd, v, lane, gwarp, gwarps);
         // the candidates' own terms (and their screen: every nonzero stays a
         // candidate); warp-uniform trip count for the list pushes
         for (int k0 = gwarp * 32; k0 < N; k0 += gwarps * 32) {
@@ -1008,8 +1068,8 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
             v[kPartPen] += fabs(om);
             if (!isfinite(g) || !isfinite(om)) v[kPartBad] += 1.0;
           }
-          push_cand(next, i, j, w.cand[1 - cur], w.ctr + kCtrCand + 1 - cur, w.cnt_r[1 - cur],
-                    w.nc_cap, lane);
+          push_cand(next && !fast, i, j, w.cand[1 - cur], w.ctr + kCtrCand + 1 - cur,
+                    w.cnt_r[1 - cur], w.nc_cap, lane);
         }
         grid_barrier(a.barrier, gen, wc, ++where);
         const int nf = ldi(w.ctr + kCtrFail);
@@ -1041,6 +1101,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
 #pragma unroll
         for (int k = 0; k < kParts; ++k) v[k] = 0.0;
         ++redo_total;
+        reuse = false;  // the list grew: build it again
         grid_barrier(a.barrier, gen, wc, ++where);
         if (add < min(nf, w.fail_cap) || ++redo > a.max_redo) {
           status = kStatusDense;
@@ -1052,12 +1113,18 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         break;
       }
       reduce_parts(v, a.partials, red);
-      // row offsets of the next sweep's list (its pushes are complete)
-      if (blockIdx.x == 0) {
+      // row offsets of the next sweep's list (its pushes are complete); a
+      // lazy sweep keeps its list, offsets and build
+      if (blockIdx.x == 0 && !fast) {
         cta_scan([&](int k) { return ldi(w.cnt_r[1 - cur] + k); }, p, w.off_r, w.cur_r, s_tmp);
         cta_count_terms([&](int k) { return ldi(w.cnt_r[1 - cur] + k); }, p, w.ctr + kCtrTermsPred);
       }
+      if (blockIdx.x == 0 && fast)  // fresh cursors for a later build of the kept list
+        for (int k = threadIdx.x; k <= p; k += blockDim.x) w.cur_r[k] = ldi(w.off_r + k);
       need_scan = false;
+      acc = fast ? acc + 2.0 * s_dsweep : 0.0;
+      reuse = fast;
+      n_lazy += fast ? 1 : 0;
       grid_barrier(a.barrier, gen, wc, ++where);
     }
 
@@ -1103,7 +1170,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         }
       }
       // the next sweep's candidates overflowed: hand over to the dense kernel
-      const bool dense_next = ldi(w.ctr + kCtrCand + (1 - cur)) > w.nc_cap;
+      const bool dense_next = !fast && ldi(w.ctr + kCtrCand + (1 - cur)) > w.nc_cap;
       s_res[kResSweeps] = sweeps_done;
       s_res[kResKkt] = kkt;
       s_res[kResObj] = obj;
@@ -1112,7 +1179,10 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
       s_res[kResFirstDelta] = first_delta;
       s_res[kResRedo] = redo_total;
       s_res[kResPath] = pk;
-      s_res[kResList] = (do_sweep && !aborted && !nonfinite && !dense_next) ? (double)(1 - cur) : -1.0;
+      s_res[kResLazy] = n_lazy;
+      s_res[kResList] = (do_sweep && !aborted && !nonfinite && !dense_next)
+                            ? (double)(fast ? cur : 1 - cur)
+                            : -1.0;
       s_res[kResStatus] = aborted      ? 3.0
                           : nonfinite  ? 2.0
                           : conv       ? 0.0
@@ -1145,13 +1215,14 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
     T* tmp = Wa;
     Wa = Wn;
     Wn = tmp;
-    cur = 1 - cur;
+    if (!fast) cur = 1 - cur;
     if (do_sweep) ++tt;
     if (s_stop) {
       // lambda path: on to the next lambda unless this one ended in an error
       // or needs the dense kernel
       const int code = (int)s_res[kResStatus];
-      if (a.path_n == 0 || pk + 1 >= a.path_n || code == 2 || code == 3 || code == kStatusDense)
+      if (a.path_n == 0 || pk + 1 >= a.path_n || code == 2 || code == 3 || code == kStatusDense ||
+          (code == 4 && a.path_break_stall))
         break;
       // this lambda's Omega (copy and / or support count), the next lambda's
       // screen from scratch
@@ -1187,6 +1258,8 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         screen_pass<T, MIXED>(a, Wa, cur, false, lamd, vz, lane, gwarp, gwarps);
       }
       need_scan = true;
+      acc = 0.0;  // a fresh screen of the current iterate
+      reuse = false;
       grid_barrier(a.barrier, gen, wc, ++where);
       continue;
     }
@@ -1194,7 +1267,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
   }
   // the last lambda's Omega (path)
   if (a.path_n > 0 && status != kStatusDense && (int)s_res[kResStatus] != 2 &&
-      (int)s_res[kResStatus] != 3) {
+      (int)s_res[kResStatus] != 3 && !((int)s_res[kResStatus] == 4 && a.path_break_stall)) {
     if (a.path_om) {
       T* out = a.path_om + (size_t)pk * p * a.path_ldo;
       for (size_t e = gtid; e < (size_t)p * p; e += gthreads) {

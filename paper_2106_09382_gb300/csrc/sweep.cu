@@ -273,10 +273,14 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
       s_args.partials = q.partials;
       s_args.result = q.result;
       s_args.batch_cnt = q.cnt;
+      s_args.stall_break = q.stall_break;
+      if (q.n_sweeps > 0) s_args.n_sweeps = q.n_sweeps;
+      s_args.lambdas = a.lambdas + q.k0;
+      s_args.n_lambda = q.nk;
       s_args.hist_len = 0;
       s_args.fault_vertex = -1;
       s_args.fault_step = -1;
-      s_args.lambda = a.lambdas[0];
+      s_args.lambda = a.lambdas[q.k0];
       s_gc[0] = q.ctas;
       s_gc[1] = (int)blockIdx.x - q.cta0;
     }
@@ -307,7 +311,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
   const WaitCtl& wc = A.wait;
 
   __shared__ double red[kSweepThreads / 32][kParts];
-  __shared__ int s_stop, s_lam_end;
+  __shared__ int s_stop, s_lam_end, s_lam_count;
   __shared__ double s_res[kRes];
   // Dynamic shared memory: pending (not yet applied) row updates of every
   // owned row -- entry k of lane l of row warp w at ((w * KC + k) * R + l) --
@@ -804,8 +808,13 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
       if constexpr (BATCH) {
         // the lambda is finished; the problem stops after the last one (or
         // on an abort / a non-finite value) and otherwise moves to the next
+        // (a lambda that ends on the stall rule ends the walk when asked: the
+        // host polishes it in FP64 and resumes after it; its support is the
+        // polished one, so it is not counted here)
         s_lam_end = s_stop;
-        if (s_stop && !aborted && !nonfinite && kl + 1 < A.n_lambda) s_stop = 0;
+        const bool brk = stalled && A.stall_break;
+        s_lam_count = s_stop && !brk;
+        if (s_stop && !aborted && !nonfinite && !brk && kl + 1 < A.n_lambda) s_stop = 0;
         if (cta == 0 && s_lam_end)
           for (int k = 0; k < kRes; ++k) A.result[(size_t)kl * kRes + k] = s_res[k];
       }
@@ -827,7 +836,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
         // support of this lambda's solution over the rows this warp owns (no
         // other warp writes them, so no barrier is needed before the next
         // lambda's sweeps)
-        if (A.batch_cnt && row_warp && ld_relaxed_s32(wc.abort) == 0) {
+        if (A.batch_cnt && s_lam_count && row_warp && ld_relaxed_s32(wc.abort) == 0) {
           float* cnt_k = A.batch_cnt + (size_t)kl * p * p;
           unsigned own = __ballot_sync(FULL, has_row);
           while (own) {

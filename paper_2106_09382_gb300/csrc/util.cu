@@ -93,6 +93,41 @@ cudaError_t launch_subdiag(const void* S, int s_f32, int ld, int p, int P, void*
   return cudaGetLastError();
 }
 
+// m[u] = an upper bound, as a float, of max_{x != u} |S[u][x]|: the exact
+// maximum rounded up (for FP32 S also one float step above it, so that it
+// bounds the FP64 copy of the same matrix as well).  One warp per row.
+template <typename T>
+__global__ void k_row_absmax(const T* __restrict__ S, int ld, int p, float* __restrict__ m) {
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < p; u += warps) {
+    const T* row = S + (size_t)u * ld;
+    T mx = (T)0;
+    for (int x = lane; x < p; x += 32)
+      if (x != u) mx = fmax(mx, fabs(row[x]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+      float f;
+      if (sizeof(T) == 4)
+        f = nextafterf((float)mx, INFINITY);
+      else
+        f = __double2float_ru((double)mx);
+      m[u] = f;
+    }
+  }
+}
+
+cudaError_t launch_row_absmax(const void* S, int s_f32, int ld, int p, float* m, cudaStream_t st) {
+  const int grid = (p + 7) / 8 < 152 * 8 ? (p + 7) / 8 : 152 * 8;
+  if (s_f32)
+    k_row_absmax<float><<<grid, 256, 0, st>>>((const float*)S, ld, p, m);
+  else
+    k_row_absmax<double><<<grid, 256, 0, st>>>((const double*)S, ld, p, m);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 __global__ void k_fill_f64(double* a, double v, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
 }

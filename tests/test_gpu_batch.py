@@ -148,3 +148,42 @@ def test_batch_arguments():
         bt.set_S(0, dev(np.eye(5), torch.float32))
         with pytest.raises(C.ConcordError):
             bt.set_S(1, dev(np.ones((7, 7)) + np.diag(np.arange(7.0)) - np.tri(7), torch.float32))
+
+
+def test_mixed_batch_polishes_stalled_lambdas():
+    """A tolerance below what FP32 sweeps reach makes every lambda stall in
+    FP32; each is polished in FP64 (W rebuilt from Omega and the FP64 S) and
+    converges.  With S given in FP64 the polished path ends on the oracle's
+    path end (both at KKT <= 1e-8), and the batch agrees bit for bit with a
+    single state's path, which polishes the same way."""
+    sizes = [(200, 100), (90, 57), (150, 64)]
+    Ss = [O.gram(O.standardize(data(n, p, 11 * p + n))) for n, p in sizes]
+    lams = np.array([0.3, 0.2, 0.1])
+    tol = 1e-8
+    with C.Batch([p for _, p in sizes], C.MIXED) as bt:
+        for b, S in enumerate(Ss):
+            bt.set_S(b, dev(S))
+        res = bt.path(lams, tol=tol, max_sweeps=2000)
+        G = [host(bt.get_omega(b)) for b in range(len(sizes))]
+    for b, S in enumerate(Ss):
+        for k in range(len(lams)):
+            r = res[b][k]
+            assert r.status == C.OK and r.kkt <= tol, (b, k, r.as_dict())
+            assert 0 < r.sweeps_fp32 < r.sweeps
+        ref = oracle_path(S, lams, tol, 5000)[-1][0]
+        assert np.abs(G[b] - ref).max() <= 1e-6 * np.abs(ref).max(), b
+        with C.State(S.shape[0], C.MIXED) as st:
+            st.set_S(dev(S))
+            rs = st.path(lams, tol=tol, max_sweeps=2000)
+            want = host(st.get_omega())
+        assert [x.sweeps for x in rs] == [x.sweeps for x in res[b]], b
+        assert np.array_equal(G[b], want), b
+
+
+def test_mixed_batch_without_polish_reports_the_stall():
+    S = O.gram(O.standardize(data(200, 100, 4)))
+    with C.Batch([100], C.MIXED) as bt:
+        bt.set_polish(False)
+        bt.set_S(0, dev(S))
+        res = bt.path([0.3, 0.2], tol=1e-9, max_sweeps=2000)
+    assert all(r.status == C.NOT_CONVERGED and r.sweeps < 2000 for r in res[0])

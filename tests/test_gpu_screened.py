@@ -161,3 +161,55 @@ def test_screened_warm_start_and_kkt_only():
         assert r0.sweeps == 0 and r0.kkt <= 1e-9
         assert abs(r0.objective - r1.objective) <= 1e-12 * abs(r1.objective)
         assert np.array_equal(host(st.get_omega()), G)
+
+
+@pytest.mark.parametrize("precision", [C.FP64, C.MIXED])
+@pytest.mark.parametrize("p,n,lam,kind", [(333, 400, 0.15, "plain"), (517, 300, 0.1, "plain"),
+                                          (100, 60, 0.2, "corr"), (257, 500, 0.12, "plain")])
+def test_lazy_verification_keeps_the_iterates(precision, p, n, lam, kind):
+    """Many sweeps in one launch: sweeps whose changes provably keep every
+    pair outside the candidates at zero skip the verification pass and reuse
+    their list; Omega, W and the per-sweep history are those of the screened
+    kernel verifying every sweep and of the dense kernel, bit for bit (the
+    objective to its summation order)."""
+    X = correlated(p, p, n) if kind == "corr" else plain(p, p, n)
+    S = O.gram(O.standardize(X))
+    Sd = dev(S, torch.float32 if precision == C.MIXED else torch.float64)
+    out = []
+    for variant, lazy in ((C.SWEEP_SCREENED, True), (C.SWEEP_SCREENED, False), (C.SWEEP_GRID, True)):
+        with C.State(p, precision) as st:
+            st.set_sweep_variant(variant)
+            st.set_lazy_verify(lazy)
+            st.set_S(Sd)
+            r = st.sweep(lam, 14)
+            out.append((r, host(st.get_omega()), host(st.get_W()), st.history()))
+    (r1, O1, W1, H1), (r2, O2, W2, H2), (r3, O3, W3, H3) = out
+    for (r, Om, W, H) in ((r2, O2, W2, H2), (r3, O3, W3, H3)):
+        assert np.array_equal(O1, Om) and np.array_equal(W1, W)
+        assert np.array_equal(H1[:, [0, 1, 3]], H[:, [0, 1, 3]])
+        np.testing.assert_allclose(H1[:, 2], H[:, 2], rtol=1e-13)
+    assert r2.lazy_sweeps == 0
+    if (p, lam) == (333, 0.15):  # converges within the 14 sweeps: its late sweeps are lazy
+        assert r1.lazy_sweeps >= 3, r1.lazy_sweeps
+
+
+@pytest.mark.parametrize("precision", [C.FP64, C.MIXED])
+def test_lazy_verification_benchmark_solve(precision):
+    """The p = 5000 benchmark solve: the same sweeps, Omega and KKT with and
+    without lazy verification, and most late sweeps lazy."""
+    w = synth.workload_ar1(p=5000, n=2000, seed=0)
+    X = dev(w["X"])
+    res = []
+    for lazy in (True, False):
+        with C.State(5000, precision, n_cap=2000) as st:
+            st.set_lazy_verify(lazy)
+            r = st.solve_device(X, w["lam"], tol=1e-5, max_sweeps=200)
+            res.append((r, host(st.get_omega()), st.history()))
+    (ra, Ga, Ha), (rb, Gb, Hb) = res
+    assert ra.status == C.OK and rb.status == C.OK
+    assert ra.sweeps == rb.sweeps and ra.kkt == rb.kkt
+    assert np.array_equal(Ga, Gb)
+    assert np.array_equal(Ha[:, [0, 1, 3]], Hb[:, [0, 1, 3]])
+    assert ra.lazy_sweeps >= 3 and rb.lazy_sweeps == 0
+    # the polish launch starts from the list the FP32 launch kept: still screened
+    assert ra.dense_sweeps == 0 and rb.dense_sweeps == 0
