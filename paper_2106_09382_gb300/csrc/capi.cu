@@ -63,6 +63,7 @@ struct concord_state {
   double* omdiag64 = nullptr;  // mixed only
   float* mrow = nullptr;       // [p] m[u] >= max_{x != u} |s_ux| (lazy verification bound)
   bool lazy_verify = true;
+  bool screen_keep_w = true;   // one-shot: false lets the next screened launch drop deferred W updates
   void *sd1 = nullptr, *sd2 = nullptr;    // sub-diagonal walk vectors, working precision
   double *sd1_64 = nullptr, *sd2_64 = nullptr;  // FP64 versions (mixed polish)
   // FP64 copies (mixed) or aliases of the working set (fp64)
@@ -351,7 +352,8 @@ int launch_dense(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* 
 // lists and per-candidate arrays, carved below.
 struct ScreenLayout {
   size_t ctr, cand0, cand1, cnt_r0, cnt_r1, fail, off_r, cur_r, nd_pi, nd_pj, row_ent, term_ptr, term_pred, term_s, nd_rec, nd_delta, nd_new, nd_d2, jac,
-      diag_old, omdiag_old, diag_new, dpart, total;
+      diag_old, omdiag_old, diag_new, dpart, dfill, diag_dd, pend_u, pend_d, pend_n, pend_new,
+      total;
 };
 
 ScreenLayout screen_layout(int p, int P, int nc, int tc) {
@@ -386,6 +388,12 @@ ScreenLayout screen_layout(int p, int P, int nc, int tc) {
   L.omdiag_old = take(sizeof(double) * (size_t)p);
   L.diag_new = take(sizeof(double) * (size_t)p);
   L.dpart = take(sizeof(double) * 1024);
+  L.dfill = take(sizeof(int) * 1024);
+  L.diag_dd = take(sizeof(double) * (size_t)p);
+  L.pend_u = take(sizeof(int) * (size_t)p * kPendRow);
+  L.pend_d = take(sizeof(double) * (size_t)p * kPendRow);
+  L.pend_n = take(sizeof(int) * (size_t)p);
+  L.pend_new = take(sizeof(int) * (size_t)p);
   L.total = off;
   return L;
 }
@@ -455,6 +463,12 @@ ScreenWork<T> screen_work(concord_state* st) {
   w.omdiag_old = (double*)(b + L.omdiag_old);
   w.diag_new = (double*)(b + L.diag_new);
   w.dpart = (double*)(b + L.dpart);
+  w.dfill = (int*)(b + L.dfill);
+  w.diag_dd = (T*)(b + L.diag_dd);
+  w.pend_u = (int*)(b + L.pend_u);
+  w.pend_d = (T*)(b + L.pend_d);
+  w.pend_n = (int*)(b + L.pend_n);
+  w.pend_new = (int*)(b + L.pend_new);
   w.nc_cap = st->nc_cap;
   w.term_cap = st->term_cap;
   w.fail_cap = st->nc_cap;
@@ -487,6 +501,7 @@ int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, d
   st->start_list = -1;
   CK(cudaMemsetAsync(st->barrier, 0, sizeof(unsigned), st->stream));
   CK(cudaMemsetAsync(st->abort_info, 0, 3 * sizeof(int), st->stream));
+  CK(cudaMemsetAsync((char*)st->scr + L.pend_n, 0, sizeof(int) * (size_t)st->p, st->stream));
   if (start_list < 0) {
     CK(cudaMemsetAsync((char*)st->scr + L.ctr, 0, sizeof(int) * kCtrs, st->stream));
     CK(cudaMemsetAsync((char*)st->scr + L.cnt_r0, 0, sizeof(int) * (size_t)(st->p + 1), st->stream));
@@ -525,6 +540,8 @@ int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, d
   a.start_list = start_list;
   a.mrow = st->mrow;
   a.lazy_verify = st->lazy_verify ? 1 : 0;
+  a.keep_w = st->screen_keep_w ? 1 : 0;
+  st->screen_keep_w = true;  // one-shot
   if (path) {
     a.path_lambda = path->lam;
     a.path_n = path->n;
@@ -933,9 +950,13 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
   if (!exact && tol1 < tol) tol1 = tol;
   // the FP32 working set follows the FP64 copies lazily (after a polish)
   if (st->om64_current && (rc = demote_from_fp64(st)) != CONCORD_OK) return rc;
+  // the polish rebuilds W in FP64 from Omega: the FP32 launch need not bring
+  // W up to date at its end (deferred updates of lazy sweeps may be dropped)
+  st->screen_keep_w = exact != 0;
   rc = launch_run<float>(st, (float*)st->S, (float*)st->W, (float*)st->Om,
                          (const float*)st->sdiagT, st->omdiag64, lambda, tol1, stop_rule,
                          max_sweeps, 0, 0, exact ? 0 : 1, &o1);
+  st->screen_keep_w = true;
   st->om64_current = false;
   st->hist_rows = o1.sweeps;
   if (rc != CONCORD_OK || exact) {

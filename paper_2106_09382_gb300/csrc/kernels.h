@@ -135,6 +135,7 @@ constexpr int kCtrTermsPred = 6;  // correction terms the current list needs (su
 constexpr int kCtrs = 8;
 constexpr int kJacMax = 64;       // fixed-point iterations of the chain before the dense kernel takes the sweep
 constexpr int kStatusDense = 5;   // result status: the next sweep needs the dense kernel
+constexpr int kPendRow = 32;      // deferred W updates a row holds (lazy sweeps)
 
 template <typename T>
 struct ScreenWork {
@@ -157,6 +158,14 @@ struct ScreenWork {
   double* omdiag_old;       // [p] FP64 diagonal before the sweep (mixed precision)
   double* diag_new;         // [p] the sweep's new FP64 diagonal, committed after the row pass
   double* dpart;            // [grid] per-CTA largest row bound of the sweep (lazy verification)
+  int* dfill;               // [grid] per-CTA largest pending-list fill the sweep would need
+  // deferred row updates of lazy sweeps: row i's true W is its stored row with
+  // pend (u, d) applied in order, w <- d S_u + w; pend_n[i] entries are valid,
+  // the slots up to pend_new[i] hold the current sweep's tentative ones
+  T* diag_dd;               // [p] the sweep's diagonal change in T (W_i += dd S_i)
+  int* pend_u;              // [p x kPendRow]
+  T* pend_d;                // [p x kPendRow]
+  int *pend_n, *pend_new;   // [p] (zeroed before the launch)
   int nc_cap, term_cap, fail_cap;
 };
 
@@ -197,6 +206,8 @@ struct ScreenArgs {
   // its candidate list (and the build of it) for the next sweep
   const float* mrow;        // [p] m[u] >= max_{x != u} |s_ux|
   int lazy_verify;
+  int keep_w;               // 1: W is left up to date at the end; 0: deferred updates may
+                            // be dropped (the host rebuilds W from Omega before using it)
   int path_break_stall;     // a lambda that ends on the stall rule ends the launch (the
                             // host polishes it in FP64 and resumes the path after it)
 };

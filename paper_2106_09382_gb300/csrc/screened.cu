@@ -58,6 +58,8 @@ constexpr double kScreenMargin = 0.1;
 // the list, with its build, serves the next sweep too.  kLazySlack lambda is
 // left for rounding (far more than FP32 accumulates on W over a few sweeps).
 constexpr double kLazySlack = 0.01;
+// How a sweep ends (see the decision in the kernel).
+constexpr int kModeFull = 0, kModeLazy = 1, kModeDefer = 2;
 
 // Candidates of one row sorted by a warp in shared memory (longer rows: one
 // thread, insertion sort).
@@ -366,6 +368,55 @@ __device__ void screen_pass(const ScreenArgs<T>& a, const T* __restrict__ W, int
   }
 }
 
+// Deferred row updates (lazy sweeps).  Row i's true W_ix is its stored value
+// with the row's pending (u, d) entries applied in order, w <- d S_ux + w:
+// the FMA chain the dense kernel applies when the updates happen.
+template <typename T>
+__device__ __forceinline__ T pend_fold(const ScreenArgs<T>& a, int i, int n, int x, T wv) {
+  const int* pu = a.w.pend_u + (size_t)i * kPendRow;
+  const T* pd = a.w.pend_d + (size_t)i * kPendRow;
+  for (int k = 0; k < n; ++k) wv = fma_t(__ldcg(pd + k), __ldg(a.S + (size_t)ldi(pu + k) * a.ld + x), wv);
+  return wv;
+}
+
+// Brings every stored row with pending entries up to date, in place: two work
+// items per row (halves of its columns), each lane its own 16-byte vectors,
+// the entries read by every lane (the same addresses: broadcast loads) and
+// applied in order.  The caller zeroes the pending counts after a barrier
+// (both halves read them here).
+template <typename T>
+__device__ void flush_pending(const ScreenArgs<T>& a, T* __restrict__ W, int lane, int gwarp,
+                              int gwarps) {
+  using VT = Vec<T>;
+  using VV = typename VT::V;
+  constexpr int VN = VT::N;
+  const int p = a.p, ld = a.ld;
+  const ScreenWork<T>& w = a.w;
+  const int nv = ld / VN;
+  for (int item = gwarp; item < 2 * p; item += gwarps) {
+    const int i = item >> 1, half = item & 1;
+    const int np = ldi(w.pend_n + i);
+    if (np == 0) continue;
+    const int qbeg = half ? nv / 2 : 0, qend = half ? nv : nv / 2;
+    const int* pu = w.pend_u + (size_t)i * kPendRow;
+    const T* pd = w.pend_d + (size_t)i * kPendRow;
+    VV* row = reinterpret_cast<VV*>(W + (size_t)i * ld);
+    for (int q = qbeg + lane; q < qend; q += 32) {
+      T acc[VN];
+      VT::split(__ldcg(row + q), acc);
+      for (int k = 0; k < np; ++k) {
+        const int u = ldi(pu + k);
+        const T d = __ldcg(pd + k);
+        T sv[VN];
+        VT::split(__ldg(reinterpret_cast<const VV*>(a.S + (size_t)u * ld) + q), sv);
+#pragma unroll
+        for (int e = 0; e < VN; ++e) acc[e] = fma_t(d, sv[e], acc[e]);
+      }
+      row[q] = VT::join(acc);
+    }
+  }
+}
+
 // After a sweep, over the pairs outside the candidates (V_ij not NaN; every
 // such pair has w_ij = 0): the verification |(0 - V_ij) - V_ji| <= lambda
 // (Eq. 3's test for staying at zero; a failing pair joins the fail list),
@@ -471,6 +522,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
   __shared__ double s_res[kRes];
   __shared__ int s_stop;
   __shared__ unsigned long long s_dmax;  // the CTA's largest row bound D_i of the sweep (bits)
+  __shared__ int s_fill;                 // the CTA's largest pending fill the sweep would need
   __shared__ int s_fast;
   __shared__ double s_dsweep;
   extern __shared__ __align__(128) unsigned char dyn[];
@@ -492,6 +544,9 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
   double acc = 0.0;
   bool reuse = false;
   int n_lazy = 0;
+  // deferred row updates: some stored rows of Wa lag behind their pending
+  // entries (after a deferring sweep, until a flush)
+  bool have_pend = false;
 
   // ---------------- screen the starting point (and its KKT for kkt_only);
   //                  the host zeroed the counters and row counts.  Or take
@@ -516,11 +571,15 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
     double v[kParts];
 #pragma unroll
     for (int k = 0; k < kParts; ++k) v[k] = 0.0;
-    bool fast = false;  // this sweep skipped the verification (lazy)
+    bool fast = false;       // this sweep skipped the verification (lazy)
+    int mode = kModeFull;    // and (kModeDefer) its row pass
     if (do_sweep) {
       int redo = 0;
       for (;;) {  // until the verification passes
-        if (threadIdx.x == 0) s_dmax = 0ull;
+        if (threadIdx.x == 0) {
+          s_dmax = 0ull;
+          s_fill = 0;
+        }
         const int N = ldi(w.ctr + kCtrCand + cur);
         if (N > w.nc_cap || ld_relaxed_s32(wc.abort) != 0) {
           status = kStatusDense;
@@ -615,8 +674,13 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
           const int2 pr = __ldcg(cand + k);
           const int i = pr.x, j = pr.y;
           T* rec = w.nd_rec + 4 * (size_t)k;
-          rec[0] = __ldcg(Wa + (size_t)i * ld + j);
-          rec[1] = __ldcg(Wa + (size_t)j * ld + i);
+          T w1 = __ldcg(Wa + (size_t)i * ld + j), w2 = __ldcg(Wa + (size_t)j * ld + i);
+          if (have_pend) {  // the rows' deferred updates, in order
+            w1 = pend_fold(a, i, ldi(w.pend_n + i), j, w1);
+            w2 = pend_fold(a, j, ldi(w.pend_n + j), i, w2);
+          }
+          rec[0] = w1;
+          rec[1] = w2;
           rec[2] = __ldcg(a.Om + (size_t)i * ld + j);
           if (reuse) {  // terms and s_ii + s_jj as the previous sweep built them
             w.nd_delta[k] = (T)0;
@@ -783,239 +847,113 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
           status = kStatusDense;
           break;
         }
-        // ---- rows: W after the colour steps, Eq. 2, W += dw S_i, V
+        // ---- reset the next list's counters
         if (gtid == 0) {
           w.ctr[kCtrCand + (1 - cur)] = 0;
           w.ctr[kCtrFail] = 0;
         }
         for (int k = gtid; k <= p; k += gthreads) w.cnt_r[1 - cur][k] = 0;
-        {
-          int* l_u = reinterpret_cast<int*>(dyn) + wid * kRowList * 2;
-          int* l_c = l_u + kRowList;
-          T* l_d = reinterpret_cast<T*>(reinterpret_cast<int*>(dyn) + nwarps * kRowList * 2) +
-                   wid * kRowList;
-          // two work items per row, one per half of its columns (vectors
-          // [0, nv/2) and [nv/2, nv)), so rows spread evenly over the warps;
-          // both halves form the row's diagonal root from the same inputs,
-          // the first half records it (committed after the next barrier)
-          const int nv = ld / VN;
-          for (int item = gwarp; item < 2 * p; item += gwarps) {
-            const int i = item >> 1, half = item & 1;
-            const int qbeg = half ? nv / 2 : 0, qend = half ? nv : nv / 2;
-            const int cbeg = qbeg * VN, cend = qend * VN;  // the half's columns
-            const int b = ldi(w.off_r + i), ne = ldi(w.off_r + i + 1) - b;
-            // diagonal: W_ii after the row's changes (lanes load the changes
-            // and their S_ui in parallel; the FMAs run in step order on
-            // every lane), then the root (Eq. 2) on lane 0
-            T wii = __ldcg(Wa + (size_t)i * ld + i);
-            int my_u = -1;  // lane m < 32: partner of the row's m-th candidate
-            double dsum = 0.0;  // lazy verification: sum of |d| m_u over the row's changes
-            for (int m0 = 0; m0 < ne; m0 += 32) {
-              const int m = m0 + lane;
-              T d = (T)0, sv = (T)0;
-              if (m < ne) {
-                const int q = ldi(w.row_ent + b + m);
-                const int2 qp = __ldcg(w.cand[cur] + q);
-                const int u = qp.x == i ? qp.y : qp.x;
-                if (m0 == 0) my_u = u;
-                d = __ldcg(w.nd_delta + q);
-                if (d != (T)0) {
-                  sv = __ldg(a.S + (size_t)u * ld + i);
-                  if (half == 0) dsum += fabs((double)d) * (double)__ldg(a.mrow + u);
-                }
-              }
-              const int nm = min(32, ne - m0);
-              for (int r = 0; r < nm; ++r) {
-                const T dr = __shfl_sync(FULL, d, r), sr = __shfl_sync(FULL, sv, r);
-                if (dr != (T)0) wii = fma_t(dr, sr, wii);
+        // ---- diagonal (Eq. 2), one warp per row: W_ii after the row's
+        //      pending updates and this sweep's changes (the dense kernel's FMA
+        //      chain), the root in FP64, the diagonal's objective / KKT terms,
+        //      the row's lazy-verification bound D_i, and tentatively the row's
+        //      new pending entries (its changes in step order, then the
+        //      diagonal change)
+        for (int i = gwarp; i < p; i += gwarps) {
+          const int b = ldi(w.off_r + i), ne = ldi(w.off_r + i + 1) - b;
+          const int np = have_pend ? ldi(w.pend_n + i) : 0;
+          int* pu = w.pend_u + (size_t)i * kPendRow;
+          T* pdv = w.pend_d + (size_t)i * kPendRow;
+          T wii = __ldcg(Wa + (size_t)i * ld + i);
+          for (int m0 = 0; m0 < np; m0 += 32) {
+            const int m = m0 + lane;
+            T d = (T)0, sv = (T)0;
+            if (m < np) {
+              d = __ldcg(pdv + m);
+              sv = __ldg(a.S + (size_t)ldi(pu + m) * ld + i);
+            }
+            const int nm = min(32, np - m0);
+            for (int r = 0; r < nm; ++r) {  // pending entries are nonzero
+              const T dr = __shfl_sync(FULL, d, r), sr = __shfl_sync(FULL, sv, r);
+              wii = fma_t(dr, sr, wii);
+            }
+          }
+          double dsum = 0.0;  // sum of |d| m_u over the row's changes
+          int nchg = 0;
+          for (int m0 = 0; m0 < ne; m0 += 32) {
+            const int m = m0 + lane;
+            T d = (T)0, sv = (T)0;
+            int u = 0;
+            if (m < ne) {
+              const int q = ldi(w.row_ent + b + m);
+              const int2 qp = __ldcg(w.cand[cur] + q);
+              u = qp.x == i ? qp.y : qp.x;
+              d = __ldcg(w.nd_delta + q);
+              if (d != (T)0) {
+                sv = __ldg(a.S + (size_t)u * ld + i);
+                dsum += fabs((double)d) * (double)__ldg(a.mrow + u);
               }
             }
-            double dd64 = 0.0;
-            T dd = (T)0;
-            if (lane == 0) {
-              const double sii = a.sdiag64[i];
-              const T o_old = __ldcg(a.Om + (size_t)i * ld + i);
-              const double oii = MIXED ? __ldcg(a.omdiag64 + i) : (double)o_old;
-              const double ci = (double)wii - oii * sii;
-              const double nw = (-ci + sqrt(ci * ci + 4.0 * sii)) / (2.0 * sii);
-              if (half == 0) {
-                w.diag_old[i] = o_old;
-                if (MIXED) w.omdiag_old[i] = oii;
-                w.diag_new[i] = nw;
-              }
-              dd = (T)(nw - oii);
-              dd64 = half == 0 ? fabs(nw - oii) : 0.0;
-              // objective / KKT terms of the diagonal after the sweep
-              const T wend = dd != (T)0 ? fma_t(dd, __ldg(a.S + (size_t)i * ld + i), wii) : wii;
-              const double wd = (double)wend;
-              const double od = MIXED ? nw : (double)(T)nw;
-              if (half == 0) {
-                if (od > 0.0 && isfinite(wd) && isfinite(od)) {
-                  v[kPartKkt] = fmax(v[kPartKkt], fabs(wd - 1.0 / od));
-                  v[kPartQuad] += od * wd;
-                  v[kPartLog] += log(od);
-                } else {
-                  v[kPartBad] += 1.0;
-                }
+            const unsigned nz = __ballot_sync(FULL, d != (T)0);
+            if (d != (T)0) {
+              const int slot = np + nchg + __popc(nz & ((1u << lane) - 1u));
+              if (slot < kPendRow) {
+                pu[slot] = u;
+                pdv[slot] = d;
               }
             }
-            dd = __shfl_sync(FULL, dd, 0);
+            nchg += __popc(nz);
+            const int nm = min(32, ne - m0);
+            for (int r = 0; r < nm; ++r) {
+              const T dr = __shfl_sync(FULL, d, r), sr = __shfl_sync(FULL, sv, r);
+              if (dr != (T)0) wii = fma_t(dr, sr, wii);
+            }
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(FULL, dsum, o);
+          if (lane == 0) {
+            const double sii = a.sdiag64[i];
+            const T o_old = __ldcg(a.Om + (size_t)i * ld + i);
+            const double oii = MIXED ? __ldcg(a.omdiag64 + i) : (double)o_old;
+            const double ci = (double)wii - oii * sii;
+            const double nw = (-ci + sqrt(ci * ci + 4.0 * sii)) / (2.0 * sii);
+            w.diag_old[i] = o_old;
+            if (MIXED) w.omdiag_old[i] = oii;
+            w.diag_new[i] = nw;
+            const T dd = (T)(nw - oii);
+            w.diag_dd[i] = dd;
+            const double dd64 = fabs(nw - oii);
             v[kPartDelta] = fmax(v[kPartDelta], dd64);
-            if (half == 0) {  // the row's bound D_i into the CTA's maximum
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(FULL, dsum, o);
-              if (lane == 0) {
-                const double di = dsum + dd64 * (double)__ldg(a.mrow + i);
-                atomicMax(&s_dmax, (unsigned long long)__double_as_longlong(di));
-              }
-            }
-            // the row's changes in step order, in chunks of kRowList
-            const T* Srow = a.S + (size_t)i * ld;
-            int c_last = -1;  // step of the last change of the previous chunks
-            int done = 0;
-            bool first = true;
-            do {
-              int cnt = 0;
-              int m0 = done;
-              // compact the next changes (d != 0) into the warp's list
-              while (m0 < ne && cnt < kRowList) {
-                const int m = m0 + lane;
-                int q = -1;
-                T d = (T)0;
-                if (m < ne) {
-                  q = ldi(w.row_ent + b + m);
-                  d = __ldcg(w.nd_delta + q);
-                }
-                const bool nz = m < ne && d != (T)0;
-                const unsigned bal = __ballot_sync(FULL, nz);
-                const int room = kRowList - cnt;
-                // take whole 32-entry groups only when they fit
-                if (__popc(bal) > room) break;
-                if (nz) {
-                  const int slot = cnt + __popc(bal & ((1u << lane) - 1u));
-                  const int2 qp = __ldcg(w.cand[cur] + q);
-                  const int u = qp.x == i ? qp.y : qp.x;
-                  l_u[slot] = u;
-                  l_c[slot] = pair_step(min(i, u), max(i, u), P);
-                  l_d[slot] = d;
-                }
-                cnt += __popc(bal);
-                m0 = min(ne, m0 + 32);
-              }
-              __syncwarp();
-              const bool last = m0 >= ne;
-              const T* src = (first ? Wa : Wn) + (size_t)i * ld;
-              // U 16-byte vectors per lane per iteration; lane l takes vectors
-              // q0 + 32 u, u < U (two, so that the paired S-row loads below fit
-              // in registers)
-              constexpr int U = 2;
-              for (int q0 = qbeg + lane; q0 < qend; q0 += 32 * U) {
-                T acc[U][VN], vv[U][VN];
-                int cx[U][VN];
-                bool cap[U][VN];  // V captured (in this chunk or an earlier one)
-#pragma unroll
-                for (int uu = 0; uu < U; ++uu) {
-                  const int q = q0 + 32 * uu;
-                  if (q < qend)
-                    VT::split(__ldcg(reinterpret_cast<const VV*>(src) + q), acc[uu]);
-                  else
-#pragma unroll
-                    for (int e = 0; e < VN; ++e) acc[uu][e] = (T)0;
-#pragma unroll
-                  for (int e = 0; e < VN; ++e) {
-                    const int x = q * VN + e;
-                    cx[uu][e] = (x < p && x != i) ? pair_step(min(i, x), max(i, x), P) : 0x7fffffff;
-                    cap[uu][e] = c_last >= cx[uu][e];
-                    vv[uu][e] = (T)0;
-                  }
-                }
-                // the diagonal's S row (last chunk) and the changes' S rows two
-                // at a time are requested before their values are used, so
-                // each lane keeps several independent loads in flight
-                T si[U][VN];
-                if (last && dd != (T)0) {
-#pragma unroll
-                  for (int uu = 0; uu < U; ++uu) {
-                    const int q = q0 + 32 * uu;
-                    if (q < qend) VT::split(__ldg(reinterpret_cast<const VV*>(Srow) + q), si[uu]);
-                  }
-                }
-                auto load_row = [&](int u, T (&sv)[U][VN]) {
-                  const VV* su = reinterpret_cast<const VV*>(a.S + (size_t)u * ld);
-#pragma unroll
-                  for (int uu = 0; uu < U; ++uu) {
-                    const int q = q0 + 32 * uu;
-                    if (q < qend) VT::split(__ldg(su + q), sv[uu]);
-                    else
-#pragma unroll
-                      for (int e = 0; e < VN; ++e) sv[uu][e] = (T)0;
-                  }
-                };
-                auto apply = [&](int cm, T d, const T (&sv)[U][VN]) {
-#pragma unroll
-                  for (int uu = 0; uu < U; ++uu)
-#pragma unroll
-                    for (int e = 0; e < VN; ++e) {
-                      // V: W before the first change at or after the pair's step
-                      if (!cap[uu][e] && cm >= cx[uu][e]) {
-                        vv[uu][e] = acc[uu][e];
-                        cap[uu][e] = true;
-                      }
-                      acc[uu][e] = fma_t(d, sv[uu][e], acc[uu][e]);
-                    }
-                };
-                int m = 0;
-                for (; m + 1 < cnt; m += 2) {
-                  T sa[U][VN], sb[U][VN];
-                  load_row(l_u[m], sa);
-                  load_row(l_u[m + 1], sb);
-                  apply(l_c[m], l_d[m], sa);
-                  apply(l_c[m + 1], l_d[m + 1], sb);
-                }
-                if (m < cnt) {
-                  T sa[U][VN];
-                  load_row(l_u[m], sa);
-                  apply(l_c[m], l_d[m], sa);
-                }
-#pragma unroll
-                for (int uu = 0; uu < U; ++uu) {
-                  const int q = q0 + 32 * uu;
-                  if (q >= qend) continue;
-                  T out[VN];
-                  T* vrow = a.V + (size_t)i * ld + q * VN;
-#pragma unroll
-                  for (int e = 0; e < VN; ++e) {
-                    // not captured: every change so far precedes the pair's step
-                    if (!cap[uu][e]) vv[uu][e] = acc[uu][e];
-                    out[e] = (last && dd != (T)0) ? fma_t(dd, si[uu][e], acc[uu][e]) : acc[uu][e];
-                    if (c_last < cx[uu][e]) vrow[e] = vv[uu][e];
-                  }
-                  reinterpret_cast<VV*>(Wn + (size_t)i * ld)[q] = VT::join(out);
-                }
-              }
-              if (cnt > 0) c_last = l_c[cnt - 1];
-              __syncwarp();
-              first = false;
-              done = m0;
-              if (last) break;
-            } while (true);
-            // candidates of this row (changed or not) and the diagonal are not verified
-            __syncwarp();
-            if (ne <= 32) {
-              if (my_u >= cbeg && my_u < cend) a.V[(size_t)i * ld + my_u] = nan_t((T)0);
+            // objective / KKT terms of the diagonal after the sweep
+            const T wend = dd != (T)0 ? fma_t(dd, __ldg(a.S + (size_t)i * ld + i), wii) : wii;
+            const double wd = (double)wend;
+            const double od = MIXED ? nw : (double)(T)nw;
+            if (od > 0.0 && isfinite(wd) && isfinite(od)) {
+              v[kPartKkt] = fmax(v[kPartKkt], fabs(wd - 1.0 / od));
+              v[kPartQuad] += od * wd;
+              v[kPartLog] += log(od);
             } else {
-              for (int m = lane; m < ne; m += 32) {
-                const int2 qp = __ldcg(w.cand[cur] + ldi(w.row_ent + b + m));
-                const int u = qp.x == i ? qp.y : qp.x;
-                if (u >= cbeg && u < cend) a.V[(size_t)i * ld + u] = nan_t((T)0);
-              }
+              v[kPartBad] += 1.0;
             }
-            if (lane == 0 && i >= cbeg && i < cend) a.V[(size_t)i * ld + i] = nan_t((T)0);
-            __syncwarp();
+            const double di = dsum + dd64 * (double)__ldg(a.mrow + i);
+            atomicMax(&s_dmax, (unsigned long long)__double_as_longlong(di));
+            int need = np + nchg;
+            if (dd != (T)0) {
+              if (need < kPendRow) {
+                pu[need] = i;
+                pdv[need] = dd;
+              }
+              ++need;
+            }
+            w.pend_new[i] = need;
+            atomicMax(&s_fill, need);
           }
         }
         __syncthreads();
-        if (threadIdx.x == 0) w.dpart[blockIdx.x] = __longlong_as_double((long long)s_dmax);
+        if (threadIdx.x == 0) {
+          w.dpart[blockIdx.x] = __longlong_as_double((long long)s_dmax);
+          w.dfill[blockIdx.x] = s_fill;
+        }
         // ---- commit the candidates' new values (both triangles)
         for (int k = gtid; k < N; k += gthreads) {
           const T d = __ldcg(w.nd_delta + k);
@@ -1029,27 +967,220 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
           }
         }
         grid_barrier(a.barrier, gen, wc, ++where);
-        // ---- lazy verification: every CTA forms the same decision
+        // ---- lazy verification: every CTA forms the same decision.  FULL:
+        //      row pass with V, verification, fresh screen.  LAZY (the bound
+        //      holds): row pass without V, no verification, the list stays.
+        //      DEFER (the bound holds and every row's pending entries fit):
+        //      no row pass either; the rows' changes and diagonal changes stay
+        //      pending on the stored W
         if (threadIdx.x == 0) {
           double dm = 0.0;
-          for (int c = 0; c < (int)gridDim.x; ++c) dm = fmax(dm, __ldcg(w.dpart + c));
+          int fm = 0;
+          for (int c = 0; c < (int)gridDim.x; ++c) {
+            dm = fmax(dm, __ldcg(w.dpart + c));
+            fm = max(fm, ldi(w.dfill + c));
+          }
           s_dsweep = dm;
-          s_fast = (a.lazy_verify && acc + 2.0 * dm <= (kScreenMargin - kLazySlack) * lamd) ? 1 : 0;
+          const bool ok = a.lazy_verify && acc + 2.0 * dm <= (kScreenMargin - kLazySlack) * lamd;
+          s_fast = !ok ? kModeFull : (fm <= kPendRow ? kModeDefer : kModeLazy);
         }
         __syncthreads();
-        fast = s_fast != 0;
-        // ---- the new diagonal (both halves of a row read the old one above)
+        mode = s_fast;
+        fast = mode != kModeFull;
+        const bool full = mode == kModeFull;
+        if (mode == kModeDefer) {
+          for (int i = gtid; i < p; i += gthreads) w.pend_n[i] = ldi(w.pend_new + i);
+        } else {
+          if (have_pend) {  // the stored rows catch up before the row pass reads them
+            flush_pending(a, Wa, lane, gwarp, gwarps);
+            grid_barrier(a.barrier, gen, wc, ++where);
+            for (int i = gtid; i < p; i += gthreads) w.pend_n[i] = 0;
+            have_pend = false;
+          }
+          // ---- rows: W after the colour steps, W += dw S_i, V (FULL)
+          {
+            int* l_u = reinterpret_cast<int*>(dyn) + wid * kRowList * 2;
+            int* l_c = l_u + kRowList;
+            T* l_d = reinterpret_cast<T*>(reinterpret_cast<int*>(dyn) + nwarps * kRowList * 2) +
+                     wid * kRowList;
+            // two work items per row, one per half of its columns (vectors
+            // [0, nv/2) and [nv/2, nv)), so rows spread evenly over the warps
+            const int nv = ld / VN;
+            for (int item = gwarp; item < 2 * p; item += gwarps) {
+              const int i = item >> 1, half = item & 1;
+              const int qbeg = half ? nv / 2 : 0, qend = half ? nv : nv / 2;
+              const int cbeg = qbeg * VN, cend = qend * VN;  // the half's columns
+              const int b = ldi(w.off_r + i), ne = ldi(w.off_r + i + 1) - b;
+              // the row's first candidate partners (lane m < 32, for the V marks
+              // below) and the diagonal change the diagonal pass formed
+              int my_u = -1;
+              if (lane < ne) {
+                const int2 qp = __ldcg(w.cand[cur] + ldi(w.row_ent + b + lane));
+                my_u = qp.x == i ? qp.y : qp.x;
+              }
+              const T dd = __ldcg(w.diag_dd + i);
+              // the row's changes in step order, in chunks of kRowList
+              const T* Srow = a.S + (size_t)i * ld;
+              int c_last = -1;  // step of the last change of the previous chunks
+              int done = 0;
+              bool first = true;
+              do {
+                int cnt = 0;
+                int m0 = done;
+                // compact the next changes (d != 0) into the warp's list
+                while (m0 < ne && cnt < kRowList) {
+                  const int m = m0 + lane;
+                  int q = -1;
+                  T d = (T)0;
+                  if (m < ne) {
+                    q = ldi(w.row_ent + b + m);
+                    d = __ldcg(w.nd_delta + q);
+                  }
+                  const bool nz = m < ne && d != (T)0;
+                  const unsigned bal = __ballot_sync(FULL, nz);
+                  const int room = kRowList - cnt;
+                  // take whole 32-entry groups only when they fit
+                  if (__popc(bal) > room) break;
+                  if (nz) {
+                    const int slot = cnt + __popc(bal & ((1u << lane) - 1u));
+                    const int2 qp = __ldcg(w.cand[cur] + q);
+                    const int u = qp.x == i ? qp.y : qp.x;
+                    l_u[slot] = u;
+                    l_c[slot] = pair_step(min(i, u), max(i, u), P);
+                    l_d[slot] = d;
+                  }
+                  cnt += __popc(bal);
+                  m0 = min(ne, m0 + 32);
+                }
+                __syncwarp();
+                const bool last = m0 >= ne;
+                const T* src = (first ? Wa : Wn) + (size_t)i * ld;
+                // U 16-byte vectors per lane per iteration; lane l takes vectors
+                // q0 + 32 u, u < U (two, so that the paired S-row loads below fit
+                // in registers)
+                constexpr int U = 2;
+                for (int q0 = qbeg + lane; q0 < qend; q0 += 32 * U) {
+                  T acc[U][VN], vv[U][VN];
+                  int cx[U][VN];
+                  bool cap[U][VN];  // V captured (in this chunk or an earlier one)
+  #pragma unroll
+                  for (int uu = 0; uu < U; ++uu) {
+                    const int q = q0 + 32 * uu;
+                    if (q < qend)
+                      VT::split(__ldcg(reinterpret_cast<const VV*>(src) + q), acc[uu]);
+                    else
+  #pragma unroll
+                      for (int e = 0; e < VN; ++e) acc[uu][e] = (T)0;
+  #pragma unroll
+                    for (int e = 0; e < VN; ++e) {
+                      const int x = q * VN + e;
+                      cx[uu][e] = (x < p && x != i) ? pair_step(min(i, x), max(i, x), P) : 0x7fffffff;
+                      cap[uu][e] = c_last >= cx[uu][e];
+                      vv[uu][e] = (T)0;
+                    }
+                  }
+                  // the diagonal's S row (last chunk) and the changes' S rows two
+                  // at a time are requested before their values are used, so
+                  // each lane keeps several independent loads in flight
+                  T si[U][VN];
+                  if (last && dd != (T)0) {
+  #pragma unroll
+                    for (int uu = 0; uu < U; ++uu) {
+                      const int q = q0 + 32 * uu;
+                      if (q < qend) VT::split(__ldg(reinterpret_cast<const VV*>(Srow) + q), si[uu]);
+                    }
+                  }
+                  auto load_row = [&](int u, T (&sv)[U][VN]) {
+                    const VV* su = reinterpret_cast<const VV*>(a.S + (size_t)u * ld);
+  #pragma unroll
+                    for (int uu = 0; uu < U; ++uu) {
+                      const int q = q0 + 32 * uu;
+                      if (q < qend) VT::split(__ldg(su + q), sv[uu]);
+                      else
+  #pragma unroll
+                        for (int e = 0; e < VN; ++e) sv[uu][e] = (T)0;
+                    }
+                  };
+                  auto apply = [&](int cm, T d, const T (&sv)[U][VN]) {
+  #pragma unroll
+                    for (int uu = 0; uu < U; ++uu)
+  #pragma unroll
+                      for (int e = 0; e < VN; ++e) {
+                        // V: W before the first change at or after the pair's step
+                        if (!cap[uu][e] && cm >= cx[uu][e]) {
+                          vv[uu][e] = acc[uu][e];
+                          cap[uu][e] = true;
+                        }
+                        acc[uu][e] = fma_t(d, sv[uu][e], acc[uu][e]);
+                      }
+                  };
+                  int m = 0;
+                  for (; m + 1 < cnt; m += 2) {
+                    T sa[U][VN], sb[U][VN];
+                    load_row(l_u[m], sa);
+                    load_row(l_u[m + 1], sb);
+                    apply(l_c[m], l_d[m], sa);
+                    apply(l_c[m + 1], l_d[m + 1], sb);
+                  }
+                  if (m < cnt) {
+                    T sa[U][VN];
+                    load_row(l_u[m], sa);
+                    apply(l_c[m], l_d[m], sa);
+                  }
+  #pragma unroll
+                  for (int uu = 0; uu < U; ++uu) {
+                    const int q = q0 + 32 * uu;
+                    if (q >= qend) continue;
+                    T out[VN];
+                    T* vrow = a.V + (size_t)i * ld + q * VN;
+  #pragma unroll
+                    for (int e = 0; e < VN; ++e) {
+                      // not captured: every change so far precedes the pair's step
+                      if (!cap[uu][e]) vv[uu][e] = acc[uu][e];
+                      out[e] = (last && dd != (T)0) ? fma_t(dd, si[uu][e], acc[uu][e]) : acc[uu][e];
+                      if (full && c_last < cx[uu][e]) vrow[e] = vv[uu][e];
+                    }
+                    reinterpret_cast<VV*>(Wn + (size_t)i * ld)[q] = VT::join(out);
+                  }
+                }
+                if (cnt > 0) c_last = l_c[cnt - 1];
+                __syncwarp();
+                first = false;
+                done = m0;
+                if (last) break;
+              } while (true);
+              // candidates of this row (changed or not) and the diagonal are not verified
+              __syncwarp();
+              if (!full) continue;
+              if (ne <= 32) {
+                if (my_u >= cbeg && my_u < cend) a.V[(size_t)i * ld + my_u] = nan_t((T)0);
+              } else {
+                for (int m = lane; m < ne; m += 32) {
+                  const int2 qp = __ldcg(w.cand[cur] + ldi(w.row_ent + b + m));
+                  const int u = qp.x == i ? qp.y : qp.x;
+                  if (u >= cbeg && u < cend) a.V[(size_t)i * ld + u] = nan_t((T)0);
+                }
+              }
+              if (lane == 0 && i >= cbeg && i < cend) a.V[(size_t)i * ld + i] = nan_t((T)0);
+              __syncwarp();
+            }
+          }
+          grid_barrier(a.barrier, gen, wc, ++where);
+        }
+        // ---- the new diagonal
         for (int k = gtid; k < p; k += gthreads) {
           const double nw = __ldcg(w.diag_new + k);
           a.Om[(size_t)k * ld + k] = (T)nw;
           if (MIXED) a.omdiag64[k] = nw;
         }
         // ---- verify the other pairs; objective / KKT; screen the next sweep
-        //      (skipped by a lazy sweep: none of them can have reached the
+        //      (FULL only: otherwise none of them can have reached the
         //      threshold, their KKT terms are zero, and the list stays)
-        if (!fast) verify_pass<T>(a, Wn, a.V, 1 - cur, lamd, v, lane, gwarp, gwarps);
+        if (full) verify_pass<T>(a, Wn, a.V, 1 - cur, lamd, v, lane, gwarp, gwarps);
         // the candidates' own terms (and their screen: every nonzero stays a
-        // candidate); warp-uniform trip count for the list pushes
+        // candidate); warp-uniform trip count for the list pushes.  Their W
+        // after the sweep: the row pass's rows, or (DEFER) the stored rows
+        // with the pending entries
         for (int k0 = gwarp * 32; k0 < N; k0 += gwarps * 32) {
           const int k = k0 + lane;
           bool next = false;
@@ -1060,7 +1191,14 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
             j = pr.y;
             const T d = __ldcg(w.nd_delta + k);
             const T omk = d != (T)0 ? __ldcg(w.nd_new + k) : __ldcg(w.nd_rec + 4 * (size_t)k + 2);
-            const T w1 = __ldcg(Wn + (size_t)i * ld + j), w2 = __ldcg(Wn + (size_t)j * ld + i);
+            T w1, w2;
+            if (mode == kModeDefer) {
+              w1 = pend_fold(a, i, ldi(w.pend_new + i), j, __ldcg(Wa + (size_t)i * ld + j));
+              w2 = pend_fold(a, j, ldi(w.pend_new + j), i, __ldcg(Wa + (size_t)j * ld + i));
+            } else {
+              w1 = __ldcg(Wn + (size_t)i * ld + j);
+              w2 = __ldcg(Wn + (size_t)j * ld + i);
+            }
             const double om = (double)omk, g = (double)w1 + (double)w2;
             next = omk != (T)0 || (fabs(((T)0 - w1) - w2) - lam_s > (T)0);
             v[kPartKkt] = fmax(v[kPartKkt], kkt_offdiag(om, g, lamd));
@@ -1125,6 +1263,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
       acc = fast ? acc + 2.0 * s_dsweep : 0.0;
       reuse = fast;
       n_lazy += fast ? 1 : 0;
+      if (mode == kModeDefer) have_pend = true;
       grid_barrier(a.barrier, gen, wc, ++where);
     }
 
@@ -1211,10 +1350,13 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
     }
     __syncthreads();
     if (kkt0) break;
-    // the accepted sweep's W becomes current
-    T* tmp = Wa;
-    Wa = Wn;
-    Wn = tmp;
+    // the accepted sweep's W becomes current (a deferring sweep left its
+    // updates pending on the stored rows)
+    if (mode != kModeDefer) {
+      T* tmp = Wa;
+      Wa = Wn;
+      Wn = tmp;
+    }
     if (!fast) cur = 1 - cur;
     if (do_sweep) ++tt;
     if (s_stop) {
@@ -1250,6 +1392,12 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
       best_kkt = 1e300;
       if (gtid == 0) w.ctr[kCtrCand + cur] = 0;
       for (int k = gtid; k <= p; k += gthreads) w.cnt_r[cur][k] = 0;
+      if (have_pend) {  // the screen reads the true W
+        flush_pending(a, Wa, lane, gwarp, gwarps);
+        grid_barrier(a.barrier, gen, wc, ++where);
+        for (int i = gtid; i < p; i += gthreads) w.pend_n[i] = 0;
+        have_pend = false;
+      }
       grid_barrier(a.barrier, gen, wc, ++where);
       {
         double vz[kParts];
@@ -1297,6 +1445,12 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
     a.result[kResRedo] = redo_total;
     a.result[kResList] = -1.0;
     a.result[kResStatus] = ld_relaxed_s32(wc.abort) != 0 ? 3.0 : (double)kStatusDense;
+  }
+  // deferred updates into the stored rows, unless the host rebuilds W itself
+  // (a dense hand-over always needs them)
+  if (have_pend && (a.keep_w || status == kStatusDense)) {
+    flush_pending(a, Wa, lane, gwarp, gwarps);
+    grid_barrier(a.barrier, gen, wc, ++where);
   }
   // leave W in the caller's buffer
   if (Wa != a.W) {

@@ -836,7 +836,9 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep(const SweepArgs<T> a
         // support of this lambda's solution over the rows this warp owns (no
         // other warp writes them, so no barrier is needed before the next
         // lambda's sweeps)
-        if (A.batch_cnt && s_lam_count && row_warp && ld_relaxed_s32(wc.abort) == 0) {
+        // (warp-uniform conditions only: the loop below shuffles)
+        const bool live = __shfl_sync(FULL, ld_relaxed_s32(wc.abort) == 0 ? 1 : 0, 0) != 0;
+        if (A.batch_cnt && s_lam_count && row_warp && live) {
           float* cnt_k = A.batch_cnt + (size_t)kl * p * p;
           unsigned own = __ballot_sync(FULL, has_row);
           while (own) {

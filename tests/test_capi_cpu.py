@@ -175,3 +175,23 @@ def test_joint_slot_map_is_algorithm1_and_covers_every_vertex(p):
                 got.add((i, j))
         assert sorted(seen) == list(range(p))
         assert got == {tuple(sorted(map(int, pr))) for pr in sched[c] if pr[0] >= 0}
+
+
+def test_pair_colour_closed_form_used_by_the_large_gpu_test():
+    """The closed-form colour of a pair that tests/test_gpu_large.py uses to
+    order sampled entries at p = 20000 equals the oracle schedule's colour."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "tgl", os.path.join(os.path.dirname(__file__), "test_gpu_large.py"))
+    tgl = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(tgl)
+    for p in list(range(2, 30)) + [99, 100, 517]:
+        s = O.schedule(p)
+        col = np.full((p, p), -1)
+        for k in range(s.shape[0]):
+            ok = s[k, :, 0] >= 0
+            col[s[k, ok, 0], s[k, ok, 1]] = k
+            col[s[k, ok, 1], s[k, ok, 0]] = k
+        for v in range(p):
+            assert np.array_equal(tgl._colours_of(v, p), col[v]), (p, v)

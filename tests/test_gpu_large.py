@@ -37,6 +37,25 @@ def _kkt(Om, S, lam):
     return max(d.abs().max().item(), off.max().item())
 
 
+def _colours_of(v, p):
+    """Colour (0-based) of every pair (v, u) under the circle method (u = v:
+    -1): in the round-robin table of colour k vertex w >= 2 (1-based) sits at
+    circle position (w - 2 + k) mod m, m = pe - 1; vertex 1 faces position
+    m - 1 and positions c, c' face each other when c + c' = m - 2.  Checked
+    against the oracle's schedule on the CPU (tests/test_capi_cpu.py)."""
+    pe = p + p % 2
+    m = pe - 1
+    inv2 = (m + 1) // 2
+    V, U = v + 1, np.arange(p) + 1
+    if V == 1:
+        k = (m + 1 - U) % m
+    else:
+        k = np.where(U == 1, (m + 1 - V) % m, ((m + 2 - V - U) % m) * inv2 % m)
+    k = k.astype(np.int64)
+    k[v] = -1
+    return k
+
+
 @pytest.fixture(scope="module")
 def large():
     return synth.workload_large()
@@ -71,3 +90,55 @@ def test_large_sparse_solve(large):
         Om64 = st.get_omega()
     assert abs(r.objective - r64.objective) <= 1e-5 * abs(r64.objective)
     assert (Om - Om64).abs().max().item() <= 1e-3 * Om64.abs().max().item()
+
+
+def test_large_sampled_sweep_entries_against_oracle(large):
+    """Sampled outputs of one FP64 sweep at p = 20000, recomputed one by one
+    by the oracle: each sampled off-diagonal entry of sweep t+1 from Eq. 3
+    with the state the colour order implies (entries of earlier colours from
+    Omega^(t+1), later ones from Omega^(t)), each sampled diagonal from Eq. 2
+    with the final off-diagonals.  The S rows are the oracle's standardization
+    multiplied out (numpy); the GPU state holds the FP64 Gram of the same
+    data (within 1e-13 of it), so the entries agree to 1e-9."""
+    w = large
+    X, p, n, lam = w["X"], w["p"], w["n"], w["lam"]
+    S64 = C.concord_gram(X, C.PREP_STANDARDIZE, C.GRAM_FP64)
+    rng = np.random.default_rng(20000)
+    rows = np.sort(rng.choice(p, 8, replace=False))
+    with C.State(p, C.FP64) as st:
+        st.set_S(S64)
+        st.sweep(lam, 3)
+        G3 = st.get_omega()
+        st.sweep(lam, 1)
+        G4 = st.get_omega()
+        cols = {}
+        for i in rows:
+            nz = torch.nonzero(G4[i]).flatten().cpu().numpy()
+            js = rng.choice(np.delete(np.arange(p), i), 5, replace=False)
+            cols[int(i)] = np.unique(np.concatenate([js, nz[nz != i][:5]]))
+        need = np.unique(np.concatenate([rows] + list(cols.values())))
+        R3 = G3[torch.as_tensor(need, device=G3.device)].cpu().numpy()
+        R4 = G4[torch.as_tensor(need, device=G4.device)].cpu().numpy()
+        del G3, G4
+    pos = {int(v): k for k, v in enumerate(need)}
+    Z = O.standardize(X.double().cpu().numpy())
+    S_need = Z[:, need].T @ Z / n
+    del Z
+    checked = 0
+    for i in rows:
+        a = pos[int(i)]
+        col_i = _colours_of(int(i), p)
+        for j in cols[int(i)]:
+            b = pos[int(j)]
+            k = col_i[j]
+            col_j = _colours_of(int(j), p)  # column j of Omega is row j (symmetric)
+            ri = np.where(col_i < k, R4[a], R3[a])
+            ri[i] = R3[a, i]
+            cj = np.where(col_j < k, R4[b], R3[b])
+            cj[j] = R3[b, j]
+            want = O.eq3(ri, cj, S_need[a], S_need[b], int(i), int(j), lam)
+            assert abs(R4[a, j] - want) <= 1e-9 * max(1.0, abs(want)), (i, j, R4[a, j], want)
+            checked += 1
+        d_want = O.eq2(R4[a], S_need[a], int(i))
+        assert abs(R4[a, i] - d_want) <= 1e-9 * d_want
+    assert checked >= 8 * 5
