@@ -108,7 +108,7 @@ extern "C" {
 
 /* ------------------------------------------------------------- results */
 /* Filled by concord_sweep / concord_run / concord_solve*.  Plain C layout:
- * 4 ints, 4 doubles, 1 int64, 1 double, 4 ints (see concord_result_size). */
+ * 4 ints, 4 doubles, 1 int64, 1 double, 8 ints (see concord_result_size). */
 typedef struct concord_result {
     int status;            /* CONCORD_OK, CONCORD_NOT_CONVERGED or an error  */
     int sweeps;            /* outer iterations of Algorithm 1 done (all phases) */
@@ -128,7 +128,10 @@ typedef struct concord_result {
     int s_refined;         /* MIXED: entries of S recomputed in FP64 accuracy
                               before the polish (concord_set_refine); 0 if none */
     int lazy_sweeps;       /* screened sweeps that skipped the verification
-                              pass (concord_set_lazy_verify) */
+                              pass (concord_set_lazy_verify); sparse polish
+                              sweeps count as well */
+    int sparse_sweeps;     /* MIXED: polish sweeps run by the sparse polish
+                              (concord_set_sparse_polish) */
 } concord_result;
 
 /* KKT residual (absolute, S units), with W = Omega S and G = W + W^T:
@@ -403,6 +406,23 @@ int concord_set_refine(concord_state *st, int on);
  * the skipped verifications.  Errors: CONCORD_E_ARG.
  */
 int concord_set_lazy_verify(concord_state *st, int on);
+
+/*
+ * concord_set_sparse_polish -- on (1, the default) or off (0); CONCORD_MIXED
+ * states only (others ignore it).  The FP64 polish of a mixed solve extends
+ * the bound of concord_set_lazy_verify across the change from the FP32 to
+ * the FP64 S (2 max_i ||Omega_i||_1 max|dS|, dS the refined entries' change
+ * or FP32 rounding).  While it holds, the polish sweeps (Eq. 3 and Eq. 2 as
+ * their direct sums over the nonzeros of Omega) change only the FP32 phase's
+ * last candidates and W = Omega S is never rebuilt in FP64.  A sweep that
+ * would break the bound is not committed; W is then rebuilt and the screened
+ * polish (which verifies every pair) takes the remaining sweeps.  Compared
+ * with the screened polish the iterates agree to FP64 rounding (the sums run
+ * in another order).  After a sparse polish the state's FP64 W is rebuilt
+ * when it is next needed (concord_get_W, warm starts).
+ * Errors: CONCORD_E_ARG.
+ */
+int concord_set_sparse_polish(concord_state *st, int on);
 
 /*
  * concord_sweep -- run exactly n_sweeps outer iterations of Algorithm 1 at

@@ -43,7 +43,8 @@ class ConcordResult(ctypes.Structure):
                 ("active_pairs", ctypes.c_longlong), ("seconds", ctypes.c_double),
                 ("timeout_vertex", ctypes.c_int), ("timeout_step", ctypes.c_int),
                 ("screen_redos", ctypes.c_int), ("dense_sweeps", ctypes.c_int),
-                ("s_refined", ctypes.c_int), ("lazy_sweeps", ctypes.c_int)]
+                ("s_refined", ctypes.c_int), ("lazy_sweeps", ctypes.c_int),
+                ("sparse_sweeps", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
@@ -89,6 +90,7 @@ SIGNATURES = {
     "concord_set_gram_mode": ([_vp, _ci], _ci),
     "concord_set_refine": ([_vp, _ci], _ci),
     "concord_set_lazy_verify": ([_vp, _ci], _ci),
+    "concord_set_sparse_polish": ([_vp, _ci], _ci),
     "concord_autotune": ([_vp, _cd, _cd, _ci, _dp, _ip, _ip], _ci),
     "concord_set_rows_per_warp": ([_vp, _ci], _ci),
     "concord_set_sweep_variant": ([_vp, _ci], _ci),
@@ -329,6 +331,11 @@ class State:
         """Skip the screened kernel's verification pass when the changes
         provably keep every other pair at zero (concord_set_lazy_verify)."""
         _check(load().concord_set_lazy_verify(self._ptr, 1 if on else 0))
+
+    def set_sparse_polish(self, on: bool):
+        """Mixed states: FP64 polish on the FP32 phase's candidates without
+        rebuilding W while the lazy bound holds (concord_set_sparse_polish)."""
+        _check(load().concord_set_sparse_polish(self._ptr, 1 if on else 0))
 
     def set_refine(self, on: bool):
         """Recompute the neighbourhood's S entries in FP64 accuracy before a

@@ -104,6 +104,14 @@ struct concord_state {
     int nbr_cap = 0, cand_cap = 0;
   } rf;
   int* h_rf = nullptr;  // pinned: entries recomputed by the last promotion
+  // sparse FP64 polish (polish.cu): one device block carved into its arrays
+  struct {
+    void* mem = nullptr;
+    int nc_cap = 0, term_cap = 0;
+    PolishWork w;
+  } pol;
+  bool sparse_polish = true;  // mixed: polish on the candidates without rebuilding W
+  bool w64_stale = false;     // mixed: W64 does not hold Omega64 S64 (after a sparse polish)
   int gram_mode = CONCORD_GRAM_FP64;
   int rows_per_warp = 0;  // 0: automatic (one row per lane)
   int sweep_variant = 0;  // 0 auto, 1 grid, 2 cluster (CONCORD_SWEEP_*)
@@ -179,7 +187,9 @@ struct RunOut {
   int redos = 0, dense_sweeps = 0;  // screened runs
   int next_list = -1;               // screened: candidate list left for the next sweep
   int s_refined = 0;                // S entries recomputed before the polish
+  double acc = 0;                   // screened: lazy bound accumulated on the next sweep's list
   int lazy = 0;                     // screened sweeps that skipped the verification
+  int sparse = 0;                   // polish sweeps run by the sparse polish
 };
 
 // One persistent launch: n_sweeps outer iterations (fewer if the stopping
@@ -576,6 +586,7 @@ int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, d
   out->redos = (int)r[kResRedo];
   out->next_list = (int)r[kResList];
   out->lazy = (int)r[kResLazy];
+  out->acc = r[kResAcc];
   if (slot_ev >= 0) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, st->lev[2 * slot_ev], st->lev[2 * slot_ev + 1]));
@@ -686,6 +697,7 @@ void fill_result(concord_result* res, const RunOut& o, int sweeps, int sweeps32,
   res->dense_sweeps = o.dense_sweeps;
   res->s_refined = o.s_refined;
   res->lazy_sweeps = o.lazy;
+  res->sparse_sweeps = o.sparse;
 }
 
 int ensure_path(concord_state* st, int n_lambda, size_t n_rows) {
@@ -740,6 +752,7 @@ int polish_path_lambda(concord_state* st, double lambda, double tol, int left, R
                        sizeof(double), sizeof(double), st->p, cudaMemcpyDeviceToDevice,
                        st->stream));
   CK(launch_refresh_w(st->Om64, st->S64, st->W64, st->p, st->ld, st->sms, st->stream));
+  st->w64_stale = false;
   const int start_list = st->start_list;
   st->start_list = -1;
   int rc = launch_run<double>(st, st->S64, st->W64, st->Om64, st->sdiag64, nullptr, lambda, tol,
@@ -895,9 +908,164 @@ int refine_s(concord_state* st, double lambda, int list) {
   return CONCORD_OK;
 }
 
+// Buffers of the sparse polish for lists of up to st->nc_cap candidates and
+// `term_cap` terms (one block, reallocated when the terms outgrow it).
+int ensure_polish(concord_state* st, int term_cap) {
+  if (st->pol.mem && st->pol.nc_cap >= st->nc_cap && st->pol.term_cap >= term_cap)
+    return CONCORD_OK;
+  if (st->pol.mem) cudaFree(st->pol.mem);
+  st->pol.mem = nullptr;
+  const size_t p = (size_t)st->p, nc = (size_t)st->nc_cap, tc = (size_t)term_cap;
+  const size_t grid = (size_t)(st->max_grid > 0 ? st->max_grid : st->sms);
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t ints = al(sizeof(int) * kPolCtrs) + 3 * al(sizeof(int) * (p + 1)) +
+                      al(sizeof(int) * p) + 3 * al(sizeof(int) * 2 * nc) + al(sizeof(int) * tc);
+  const size_t dbls = al(8 * tc) + 5 * al(8 * nc) + al(8 * 2 * nc) + 2 * al(8 * p) + al(8 * grid);
+  char* m = nullptr;
+  CK(cudaMalloc((void**)&m, ints + dbls));
+  st->pol.mem = m;
+  st->pol.nc_cap = st->nc_cap;
+  st->pol.term_cap = term_cap;
+  PolishWork& w = st->pol.w;
+  size_t o = 0;
+  auto take = [&](size_t b) { char* r = m + o; o += al(b); return (void*)r; };
+  w.ctr = (int*)take(sizeof(int) * kPolCtrs);
+  w.deg = (int*)take(sizeof(int) * (p + 1));
+  w.off = (int*)take(sizeof(int) * (p + 1));
+  w.toff = (int*)take(sizeof(int) * (p + 1));
+  w.cur = (int*)take(sizeof(int) * p);
+  w.ent0 = (int*)take(sizeof(int) * 2 * nc);
+  w.ent = (int*)take(sizeof(int) * 2 * nc);
+  w.pos = (int*)take(sizeof(int) * 2 * nc);
+  w.term_q = (int*)take(sizeof(int) * tc);
+  w.term_s = (double*)take(8 * tc);
+  w.om = (double*)take(8 * nc);
+  w.den = (double*)take(8 * nc);
+  w.d0 = (double*)take(8 * nc);
+  w.d1 = (double*)take(8 * nc);
+  w.nw = (double*)take(8 * nc);
+  w.base = (double*)take(8 * 2 * nc);
+  w.diag = (double*)take(8 * p);
+  w.diag_new = (double*)take(8 * p);
+  w.dpart = (double*)take(8 * grid);
+  w.nc_cap = st->nc_cap;
+  w.term_cap = term_cap;
+  return CONCORD_OK;
+}
+
+// The sparse FP64 polish (polish.cu) of the promoted iterate, on candidate
+// list `list` of the FP32 launch with its accumulated bound `acc`.  *code is
+// the kernel's status: 0 / 1 / 2 / 3 as the sweep kernels, kStatusNeedW when
+// the bound (or the fixed point) failed before a sweep was committed (the
+// sweeps already done stand; W must be rebuilt for the rest).
+int polish_sparse(concord_state* st, double lambda, double tol, int stop_rule, int n_sweeps,
+                  int hist_offset, int list, double acc, RunOut* out, int* code) {
+  int term_cap = st->pol.term_cap > 0 ? st->pol.term_cap : 16 * st->nc_cap;
+  const ScreenWork<float> sw = screen_work<float>(st);
+  for (int attempt = 0;; ++attempt) {
+    int rc = ensure_polish(st, term_cap);
+    if (rc != CONCORD_OK) return rc;
+    const PolishWork& w = st->pol.w;
+    CK(cudaMemsetAsync(w.ctr, 0, sizeof(int) * kPolCtrs, st->stream));
+    CK(cudaMemsetAsync(w.deg, 0, sizeof(int) * (size_t)(st->p + 1), st->stream));
+    CK(cudaMemsetAsync(st->barrier, 0, sizeof(unsigned), st->stream));
+    CK(cudaMemsetAsync(st->abort_info, 0, 3 * sizeof(int), st->stream));
+    PolishArgs a;
+    memset(&a, 0, sizeof a);
+    a.p = st->p;
+    a.P = st->P;
+    a.ld = st->ld;
+    a.Om = st->Om64;
+    a.S = st->S64;
+    a.sdiag = st->sdiag64;
+    a.mrow = st->mrow;
+    a.cand = sw.cand[list];
+    a.n_cand = sw.ctr + kCtrCand + list;
+    a.ds_bits = (st->refine && st->zt_valid && st->rf.ctr) ? st->rf.ctr + kRefineDs : nullptr;
+    a.acc0 = acc;
+    a.w = w;
+    a.barrier = st->barrier;
+    a.wait.abort = st->abort_info;
+    a.wait.info = st->abort_info + 1;
+    a.wait.timeout_ns = (uint64_t)(st->timeout_s * 1e9);
+    a.partials = st->partials;
+    a.hist = st->hist + (size_t)hist_offset * kHist;
+    a.hist_len = kHistCap - hist_offset;
+    a.result = st->result;
+    a.lambda = lambda;
+    a.tol = tol;
+    a.delta_tol = 1e-5;
+    a.stop_rule = stop_rule;
+    a.n_sweeps = n_sweeps;
+    const int slot_ev = st->n_launch < kMaxTimedLaunches ? st->n_launch : -1;
+    if (slot_ev >= 0) CK(cudaEventRecord(st->lev[2 * slot_ev], st->stream));
+    const int grid = st->max_ctas > 0 && st->max_ctas < st->sms ? st->max_ctas : st->sms;
+    CK(launch_polish(a, grid, st->stream));
+    if (slot_ev >= 0) CK(cudaEventRecord(st->lev[2 * slot_ev + 1], st->stream));
+    CK(cudaMemcpyAsync(st->h_result, st->result, kRes * sizeof(double), cudaMemcpyDeviceToHost,
+                       st->stream));
+    CK(cudaMemcpyAsync(st->h_abort, st->abort_info, 3 * sizeof(int), cudaMemcpyDeviceToHost,
+                       st->stream));
+    CK(cudaMemcpyAsync(st->h_flag, w.ctr + kPolOverflow, sizeof(int), cudaMemcpyDeviceToHost,
+                       st->stream));
+    CK(cudaStreamSynchronize(st->stream));
+    CK(cudaGetLastError());
+    const double* r = st->h_result;
+    *code = (int)r[kResStatus];
+    if (*code == kStatusCapacity) {
+      // the terms did not fit: grow once to what they need (bounded), else
+      // leave the polish to the screened kernel
+      const int need = *st->h_flag;
+      if (attempt == 0 && need > term_cap && need <= (1 << 26)) {
+        term_cap = need;
+        continue;
+      }
+      *code = kStatusNeedW;
+    }
+    if (slot_ev >= 0) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, st->lev[2 * slot_ev], st->lev[2 * slot_ev + 1]));
+      st->launch_ms[slot_ev] = ms;
+      st->launch_sweeps[slot_ev] = (int)r[kResSweeps];
+      st->n_launch = slot_ev + 1;
+    }
+    out->sweeps = (int)r[kResSweeps];
+    out->kkt = r[kResKkt];
+    out->obj = r[kResObj];
+    out->delta = r[kResDelta];
+    out->active = r[kResActive];
+    out->first_delta = (int)r[kResFirstDelta];
+    out->redos = 0;
+    out->next_list = -1;
+    out->lazy = (int)r[kResLazy];
+    out->acc = r[kResAcc];
+    if (st->h_abort[0] != 0) {
+      out->status = CONCORD_E_TIMEOUT;
+      out->to_vertex = st->h_abort[1];
+      out->to_step = st->h_abort[2];
+      return fail(CONCORD_E_TIMEOUT, "device wait ran out (phase %d)", st->h_abort[2]);
+    }
+    out->status = *code == 0 ? CONCORD_OK
+                  : *code == 2 ? CONCORD_E_NONFINITE
+                               : CONCORD_NOT_CONVERGED;
+    if (*code == 2)
+      return fail(CONCORD_E_NONFINITE, "non-finite objective or KKT residual after sweep %d",
+                  out->sweeps);
+    return CONCORD_OK;
+  }
+}
+
+// mixed: W64 = Omega64 S64 again where a sparse polish left it out of date
+int ensure_w64(concord_state* st) {
+  if (!st->w64_stale) return CONCORD_OK;
+  CK(launch_refresh_w(st->Om64, st->S64, st->W64, st->p, st->ld, st->sms, st->stream));
+  st->w64_stale = false;
+  return CONCORD_OK;
+}
+
 // mixed: FP32 iterate -> FP64 copies (Omega with its FP64 diagonal; W rebuilt
 // in FP64 from Omega and S, after the S refinement when it applies)
-int promote_to_fp64(concord_state* st, double lambda, int list) {
+int promote_to_fp64(concord_state* st, double lambda, int list, bool rebuild_w = true) {
   *st->h_rf = 0;
   if (st->refine && st->zt_valid) {
     int rc = refine_s(st, lambda, list);
@@ -907,13 +1075,17 @@ int promote_to_fp64(concord_state* st, double lambda, int list) {
   CK(cudaMemcpy2DAsync(st->Om64, (size_t)(st->ld + 1) * sizeof(double), st->omdiag64,
                        sizeof(double), sizeof(double), st->p, cudaMemcpyDeviceToDevice,
                        st->stream));
-  CK(launch_refresh_w(st->Om64, st->S64, st->W64, st->p, st->ld, st->sms, st->stream));
+  if (rebuild_w)
+    CK(launch_refresh_w(st->Om64, st->S64, st->W64, st->p, st->ld, st->sms, st->stream));
+  st->w64_stale = !rebuild_w;
   st->om64_current = true;
   return CONCORD_OK;
 }
 
 // mixed: FP64 copies -> FP32 working set
 int demote_from_fp64(concord_state* st) {
+  int rc = ensure_w64(st);
+  if (rc != CONCORD_OK) return rc;
   CK(launch_convert(st->Om64, 0, st->ld, st->Om, 1, st->ld, st->p, st->p, st->stream));
   CK(launch_convert(st->W64, 0, st->ld, st->W, 1, st->ld, st->p, st->p, st->stream));
   CK(cudaMemcpy2DAsync(st->omdiag64, sizeof(double), st->Om64, (size_t)(st->ld + 1) * sizeof(double),
@@ -969,12 +1141,35 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
   }
   // ... then FP64 polishing from W rebuilt in FP64, its first sweep on the
   // candidate list the FP32 phase left (same lambda)
-  if ((rc = promote_to_fp64(st, lambda, o1.next_list)) != CONCORD_OK) return rc;
+  // (sparse polish: sweeps on the candidates alone while the lazy bound
+  // holds, W not rebuilt; the screened polish from a rebuilt W otherwise, or
+  // for the sweeps left when the bound fails)
   const int left = max_sweeps - o1.sweeps;
-  st->start_list = left > 0 ? o1.next_list : -1;
-  rc = launch_run<double>(st, st->S64, st->W64, st->Om64, st->sdiag64, nullptr, lambda, tol,
-                          stop_rule, left, left == 0 ? 1 : 0, o1.sweeps, 0, &o2);
-  st->start_list = -1;
+  const bool sparse = st->sparse_polish && left > 0 && o1.next_list >= 0;
+  if ((rc = promote_to_fp64(st, lambda, o1.next_list, !sparse)) != CONCORD_OK) return rc;
+  int code = kStatusNeedW, done = 0;
+  if (sparse) {
+    rc = polish_sparse(st, lambda, tol, stop_rule, left, o1.sweeps, o1.next_list, o1.acc, &o2,
+                       &code);
+    done = o2.sweeps;
+    o2.sparse = done;
+  }
+  if (rc == CONCORD_OK && code == kStatusNeedW) {
+    if ((rc = ensure_w64(st)) != CONCORD_OK) return rc;
+    const int left2 = left - done;
+    RunOut o3;
+    st->start_list = left2 > 0 ? o1.next_list : -1;
+    rc = launch_run<double>(st, st->S64, st->W64, st->Om64, st->sdiag64, nullptr, lambda, tol,
+                            stop_rule, left2, left2 == 0 ? 1 : 0, o1.sweeps + done, 0, &o3);
+    st->start_list = -1;
+    if (done > 0) {
+      o3.first_delta = o2.first_delta ? o2.first_delta : (o3.first_delta ? done + o3.first_delta : 0);
+      o3.sweeps += done;
+      o3.lazy += o2.lazy;
+    }
+    o3.sparse = done;
+    o2 = o3;
+  }
   st->hist_rows = o1.sweeps + o2.sweeps;
   // the FP64 copies now hold the iterate (om64_current); the FP32 working
   // set is refreshed from them when an FP32 phase next needs it
@@ -1211,7 +1406,7 @@ int concord_destroy(concord_state* st) {
                  st->hist, st->result, st->mean, st->inv_scale, st->Z, st->Xstage, st->zt_hi,
                  st->zt_lo, st->sdiag64, st->sdiagT, st->omdiag64, st->S64, st->W64, st->Om64,
                  st->zt32, st->rf.cnt, st->rf.off, st->rf.cur, st->rf.nbr, st->rf.ctr, st->rf.cand,
-                 st->rf.bitmap, st->mrow};
+                 st->rf.bitmap, st->mrow, st->pol.mem};
   for (void* d : dev)
     if (d) cudaFree(d);
   void* adj_dev[] = {st->adj.cnt, st->adj.rowptr, st->adj.bad, st->adj.col, st->adj.erow,
@@ -1299,6 +1494,7 @@ int concord_set_omega(concord_state* st, const void* Om_dev, int dtype, int ld_i
   if (bad & 1) return fail(CONCORD_E_ARG, "Omega0 is not symmetric with a positive diagonal");
   CK(launch_convert(Om_dev, f32, ld_in, st->Om64, 0, ld, p, p, st->stream));
   CK(launch_refresh_w(st->Om64, st->S64, st->W64, p, ld, st->sms, st->stream));
+  st->w64_stale = false;
   if (is_mixed(st)) {
     st->om64_current = true;
     if ((rc = demote_from_fp64(st))) return rc;
@@ -1314,6 +1510,7 @@ static int get_matrix(concord_state* st, bool omega, void* out, int dtype, int l
     return fail(CONCORD_E_ARG, "out non-NULL, dtype F64/F32, ld >= p required");
   const int p = st->p, ld = st->ld, f32 = dtype == CONCORD_F32;
   if (!is_mixed(st) || st->om64_current) {
+    if (!omega && (rc = ensure_w64(st)) != CONCORD_OK) return rc;
     CK(launch_convert(omega ? st->Om64 : st->W64, 0, ld, out, f32, ld_out, p, p, st->stream));
   } else {
     CK(launch_convert(omega ? st->Om : st->W, 1, ld, out, f32, ld_out, p, p, st->stream));
@@ -1610,6 +1807,13 @@ int concord_set_lazy_verify(concord_state* st, int on) {
   if (!st) return fail(CONCORD_E_ARG, "state is NULL");
   if (on != 0 && on != 1) return fail(CONCORD_E_ARG, "on must be 0 or 1");
   st->lazy_verify = on == 1;
+  return CONCORD_OK;
+}
+
+int concord_set_sparse_polish(concord_state* st, int on) {
+  if (!st) return fail(CONCORD_E_ARG, "state is NULL");
+  if (on != 0 && on != 1) return fail(CONCORD_E_ARG, "on must be 0 or 1");
+  st->sparse_polish = on == 1;
   return CONCORD_OK;
 }
 

@@ -183,4 +183,37 @@ __device__ __forceinline__ void grid_barrier(unsigned* counter, unsigned& gen,
   group_barrier(counter, gen, gridDim.x, w, where, (int)blockIdx.x);
 }
 
+// ---------------------------------------------------------------------------
+// Helpers of the screened sweep and the sparse polish.
+// ---------------------------------------------------------------------------
+// Colour step (0-based) at which the circle method pairs i < j (Section 3.2,
+// Algorithm 1): solving the closed form of cm_partner for the colour gives
+// 2c = -(i + j) (mod P) for i >= 1, and c = P - j for i = 0.  P is odd, so
+// halving mod P is n / 2 for even n and (n + P) / 2 for odd n.
+__device__ __forceinline__ int pair_step(int i, int j, int P) {
+  if (i == 0) return P - j;
+  int s = i + j;  // i, j <= P, so s < 2P
+  if (s >= P) s -= P;
+  if (s >= P) s -= P;
+  const int neg = s == 0 ? 0 : P - s;
+  return (neg & 1) ? (neg + P) >> 1 : neg >> 1;
+}
+
+template <typename T>
+__device__ __forceinline__ T soft(T x, T tau) {
+  T a = fabs(x) - tau;
+  if (!(a > (T)0)) return (T)0;
+  return x > (T)0 ? a : -a;
+}
+
+// KKT residual term of an off-diagonal pair (absolute, S units) with
+// G = W_ij + W_ji in FP64.
+__device__ __forceinline__ double kkt_offdiag(double om, double g, double lam) {
+  if (om > 0.0) return fabs(g + lam);
+  if (om < 0.0) return fabs(g - lam);
+  return fmax(fabs(g) - lam, 0.0);
+}
+
+__device__ __forceinline__ int ldi(const int* p) { return __ldcg(p); }
+
 }  // namespace concord

@@ -41,8 +41,9 @@ constexpr int kResSweeps = 0, kResKkt = 1, kResObj = 2, kResDelta = 3, kResActiv
               kResFirstDelta = 5, kResStatus = 6, kResRedo = 7,  // kResRedo: screened only
               kResPath = 8,  // screened path: index of the lambda a dense hand-over stopped at
               kResList = 9,  // screened: candidate list of the next sweep (-1: none valid)
-              kResLazy = 10; // screened: sweeps that skipped the verification (lazy)
-constexpr int kRes = 11;
+              kResLazy = 10, // screened: sweeps that skipped the verification (lazy)
+              kResAcc = 11;  // screened: accumulated lazy bound of the next sweep's list
+constexpr int kRes = 12;
 constexpr int kHist = 4;  // per sweep: delta, kkt, objective, active pairs
 
 // One problem of a batched launch of the sweep kernel: its own dimension,
@@ -298,6 +299,7 @@ constexpr double kRefineMargin = 0.1;
 constexpr int kRefineDone = 0;     // ctr: entries recomputed
 constexpr int kRefineOwn = 1;      // ctr: length of the collected list (no candidate list given)
 constexpr int kRefineDropped = 2;  // ctr: collected pairs that did not fit
+constexpr int kRefineDs = 3;       // ctr: float bits of max |new - old| over recomputed entries
 constexpr int kRefineCtrs = 4;
 struct RefineArgs {
   int p, ld, n, ldn, sms;
@@ -317,6 +319,86 @@ struct RefineArgs {
   int* ctr;                  // [kRefineCtrs]
 };
 size_t refine_bitmap_words(int p);
+
+// Screening margin: a pair is a candidate of the next sweep when its value is
+// nonzero or |G_ij| > (1 - kScreenMargin) lambda at the sweep's start.  Any
+// superset of the pairs that change gives the same iterates (a candidate
+// that stays below the threshold gets a zero change); the margin catches the
+// pairs that cross the threshold during the sweep, which would otherwise
+// fail the verification and force a redo of the sweep.
+constexpr double kScreenMargin = 0.1;
+
+// Lazy verification.  Every pair outside the candidate list had
+// |G_ij| <= (1 - kScreenMargin) lambda when the list was screened.  A change d
+// of a candidate (i, u) moves W_ix by d s_ux for x != u, so by at most
+// |d| m_u (m_u = max_{x != u} |s_ux|), and a diagonal change moves W_ix by at
+// most |dw| m_i.  With D_i the sum of those bounds over a sweep's changes of
+// row i, G_ij of a pair outside the list moves by at most D_i + D_j <=
+// 2 max_i D_i per sweep.  While the bounds accumulated since the screen stay
+// within (kScreenMargin - kLazySlack) lambda, no such pair can reach the
+// threshold at its visit (so the verification would pass) nor at the sweep's
+// end (so its KKT term is zero): the sweep skips the verification pass, and
+// the list, with its build, serves the next sweep too.  kLazySlack lambda is
+// left for rounding (far more than FP32 accumulates on W over a few sweeps).
+constexpr double kLazySlack = 0.01;
+
+// ---- sparse FP64 polish (polish.cu).  FP64 sweeps of a mixed solve that
+// keep every pair outside the FP32 phase's candidate list at zero (the lazy
+// verification bound, carried over with the FP32 -> FP64 change of S): each
+// W entry a sweep reads is formed from the nonzeros of Omega and S, so W is
+// never materialised.
+constexpr int kStatusNeedW = 6;       // result status: the bound failed; W must be rebuilt
+constexpr int kStatusCapacity = 7;    // result status: the terms did not fit (ctr holds the need)
+constexpr int kPolishThreads = 512;
+constexpr int kPolishMaxRounds = 1024;  // fixed-point rounds per sweep before giving up
+constexpr int kPolChg = 0;            // ctr[0..2]: changed flags of the chain's rounds
+constexpr int kPolOverflow = 3;       // ctr: terms needed when they do not fit (0: fit)
+constexpr int kPolRowMax = 4;         // ctr[4..5]: max_i sum_u |omega_iu| (double bits)
+constexpr int kPolSMax = 6;           // ctr[6..7]: max |s_ux| (double bits)
+constexpr int kPolCtrs = 8;
+struct PolishWork {
+  int* ctr;          // [kPolCtrs] (zeroed before the launch)
+  int* deg;          // [p + 1] entries per row (zeroed before the launch)
+  int* off;          // [p + 1] row offsets of the entries
+  int* toff;         // [p + 1] row offsets of the terms (deg (deg - 1) per row)
+  int* cur;          // [p] fill cursors
+  int* ent0;         // [2 nc_cap] row entries (candidate numbers) as filled
+  int* ent;          // [2 nc_cap] row entries in colour-step order
+  int* pos;          // [2 nc_cap] rank of candidate k in row i (2k) and in row j (2k + 1)
+  int* term_q;       // [term_cap] candidate of each term
+  double* term_s;    // [term_cap] the S entry it multiplies
+  double* om;        // [nc_cap] value of each candidate
+  double* den;       // [nc_cap] s_ii + s_jj
+  double* base;      // [2 nc_cap] W_ij - omega_ij s_jj (2k) and W_ji - omega_ij s_ii (2k + 1)
+  double* d0;        // [nc_cap] fixed-point iterates of the changes
+  double* d1;        // [nc_cap]
+  double* nw;        // [nc_cap] new value of each candidate
+  double* diag;      // [p] the diagonal of Omega
+  double* diag_new;  // [p]
+  double* dpart;     // [grid] per-CTA largest row bound of a sweep
+  int nc_cap, term_cap;
+};
+struct PolishArgs {
+  int p, P, ld;
+  double* Om;              // p x ld FP64 Omega (diagonal included), in and out
+  const double* S;         // p x ld FP64 S
+  const double* sdiag;     // [p] s_ii
+  const float* mrow;       // [p] m[u] >= max_{x != u} |s_ux|
+  const int2* cand;        // candidate pairs (i < j) left by the FP32 phase
+  const int* n_cand;       // device: their number
+  const int* ds_bits;      // nullable: float bits of max |S64 - S32 used by the FP32 phase|
+  double acc0;             // lazy bound accumulated by the FP32 phase since its screen
+  PolishWork w;
+  unsigned* barrier;       // zeroed before the launch
+  WaitCtl wait;
+  double* partials;        // grid x kParts
+  double* hist;
+  int hist_len;
+  double* result;          // kRes
+  double lambda, tol, delta_tol;
+  int stop_rule, n_sweeps;
+};
+cudaError_t launch_polish(const PolishArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_refine_s(const RefineArgs& a, cudaStream_t st);
 cudaError_t launch_gram_bf16x3(const uint16_t* zt_hi, const uint16_t* zt_lo, int n_pad, int p_pad,
                                int p, float* S, int lds, float scale, int* status, cudaStream_t st);

@@ -185,7 +185,8 @@ __global__ void __launch_bounds__(256) k_refine(const int2* __restrict__ cand,
                                                 double* __restrict__ S64, float* __restrict__ S32,
                                                 int ld, unsigned* __restrict__ bitmap,
                                                 float* __restrict__ mrow,
-                                                int* __restrict__ n_done) {
+                                                int* __restrict__ n_done,
+                                                int* __restrict__ ds_max) {
   const int lane = threadIdx.x & 31;
   const int nc = *n_cand;
   const int warps = gridDim.x * (blockDim.x >> 5);
@@ -220,6 +221,11 @@ __global__ void __launch_bounds__(256) k_refine(const int2* __restrict__ cand,
         if (!__shfl_sync(FULL, claimed, 0)) continue;
         const double v = warp_dot(zt + (size_t)k * ldn, zc, ldn4, lane) * inv_n;
         if (lane == 0) {
+          // the largest change of an entry against the FP32 S the sweeps so
+          // far have used (float bits, rounded up; nonnegative floats order
+          // as ints)
+          const double dv = fabs(v - (double)S32[(size_t)a * ld + b]);
+          if (dv > 0.0) atomicMax(ds_max, __float_as_int(nextafterf(__double2float_ru(dv), INFINITY)));
           S64[(size_t)a * ld + b] = v;
           S64[(size_t)b * ld + a] = v;
           S32[(size_t)a * ld + b] = (float)v;
@@ -264,7 +270,7 @@ cudaError_t launch_refine_s(const RefineArgs& a, cudaStream_t st) {
   k_nbr_fill<<<a.sms * 4, 256, 0, st>>>(cand, n_cand, a.nbr_cur, a.nbr);
   k_refine<<<a.sms * 8, 256, 0, st>>>(cand, n_cand, a.nbr_off, a.nbr, p, a.zt, a.ldn,
                                       1.0 / a.n, a.S64, a.S32, a.ld, a.bitmap, a.mrow,
-                                      a.ctr + kRefineDone);
+                                      a.ctr + kRefineDone, a.ctr + kRefineDs);
   note_launches(4);
   return cudaGetLastError();
 }

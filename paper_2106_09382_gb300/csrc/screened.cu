@@ -37,27 +37,6 @@
 
 namespace concord {
 
-// Screening margin: a pair is a candidate of the next sweep when its value is
-// nonzero or |G_ij| > (1 - kScreenMargin) lambda at the sweep's start.  Any
-// superset of the pairs that change gives the same iterates (a candidate
-// that stays below the threshold gets a zero change); the margin catches the
-// pairs that cross the threshold during the sweep, which would otherwise
-// fail the verification and force a redo of the sweep.
-constexpr double kScreenMargin = 0.1;
-
-// Lazy verification.  Every pair outside the candidate list had
-// |G_ij| <= (1 - kScreenMargin) lambda when the list was screened.  A change d
-// of a candidate (i, u) moves W_ix by d s_ux for x != u, so by at most
-// |d| m_u (m_u = max_{x != u} |s_ux|), and a diagonal change moves W_ix by at
-// most |dw| m_i.  With D_i the sum of those bounds over a sweep's changes of
-// row i, G_ij of a pair outside the list moves by at most D_i + D_j <=
-// 2 max_i D_i per sweep.  While the bounds accumulated since the screen stay
-// within (kScreenMargin - kLazySlack) lambda, no such pair can reach the
-// threshold at its visit (so the verification would pass) nor at the sweep's
-// end (so its KKT term is zero): the sweep skips the verification pass, and
-// the list, with its build, serves the next sweep too.  kLazySlack lambda is
-// left for rounding (far more than FP32 accumulates on W over a few sweeps).
-constexpr double kLazySlack = 0.01;
 // How a sweep ends (see the decision in the kernel).
 constexpr int kModeFull = 0, kModeLazy = 1, kModeDefer = 2;
 
@@ -67,26 +46,6 @@ constexpr int kSortCap = 512;
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-
-// Colour step (0-based) at which the circle method pairs i < j (Section 3.2,
-// Algorithm 1): solving the closed form of cm_partner for the colour gives
-// 2c = -(i + j) (mod P) for i >= 1, and c = P - j for i = 0.  P is odd, so
-// halving mod P is n / 2 for even n and (n + P) / 2 for odd n.
-__device__ __forceinline__ int pair_step(int i, int j, int P) {
-  if (i == 0) return P - j;
-  int s = i + j;  // i, j <= P, so s < 2P
-  if (s >= P) s -= P;
-  if (s >= P) s -= P;
-  const int neg = s == 0 ? 0 : P - s;
-  return (neg & 1) ? (neg + P) >> 1 : neg >> 1;
-}
-
-template <typename T>
-__device__ __forceinline__ T soft(T x, T tau) {
-  T a = fabs(x) - tau;
-  if (!(a > (T)0)) return (T)0;
-  return x > (T)0 ? a : -a;
-}
 
 __device__ __forceinline__ float fma_t(float d, float s, float w) { return fmaf(d, s, w); }
 __device__ __forceinline__ double fma_t(double d, double s, double w) { return ::fma(d, s, w); }
@@ -193,7 +152,6 @@ __device__ void cta_count_terms(F f, int n, int* out) {
   __syncthreads();
 }
 
-__device__ __forceinline__ int ldi(const int* p) { return __ldcg(p); }
 
 // Barrier among the CTAs that increment `counter` (zeroed before first use):
 // returns when it reaches `target` (participants x rounds so far) or the
@@ -291,13 +249,6 @@ __device__ __forceinline__ void push_cand(bool pred, int i, int j, int2* list, i
   }
 }
 
-// KKT residual term of an off-diagonal pair (absolute, S units) with
-// G = W_ij + W_ji in FP64.
-__device__ __forceinline__ double kkt_offdiag(double om, double g, double lam) {
-  if (om > 0.0) return fabs(g + lam);
-  if (om < 0.0) return fabs(g - lam);
-  return fmax(fabs(g) - lam, 0.0);
-}
 
 // Screen of a launch's starting point over the upper triangle, in 8-row
 // chunks of 32 x 32 tiles (lane l takes column j = tb*32 + l; W_ji comes from
@@ -1319,6 +1270,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
       s_res[kResRedo] = redo_total;
       s_res[kResPath] = pk;
       s_res[kResLazy] = n_lazy;
+      s_res[kResAcc] = acc;  // the lazy bound accumulated on the next sweep's list
       s_res[kResList] = (do_sweep && !aborted && !nonfinite && !dense_next)
                             ? (double)(fast ? cur : 1 - cur)
                             : -1.0;

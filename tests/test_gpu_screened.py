@@ -139,6 +139,7 @@ def test_screened_solve_matches_dense_solve(precision):
     for variant in (C.SWEEP_SCREENED, C.SWEEP_DENSE):
         with C.State(S.shape[0], precision) as st:
             st.set_sweep_variant(variant)
+            st.set_sparse_polish(False)  # the same (screened) polish after both
             st.set_S(dev(S))
             r = st.run(w["lam"], tol=w["tol"], max_sweeps=500)
             out.append((r, host(st.get_omega())))
@@ -203,6 +204,7 @@ def test_lazy_verification_benchmark_solve(precision):
     for lazy in (True, False):
         with C.State(5000, precision, n_cap=2000) as st:
             st.set_lazy_verify(lazy)
+            st.set_sparse_polish(False)  # the screened polish in both arms
             r = st.solve_device(X, w["lam"], tol=1e-5, max_sweeps=200)
             res.append((r, host(st.get_omega()), st.history()))
     (ra, Ga, Ha), (rb, Gb, Hb) = res
