@@ -43,6 +43,7 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kWarps = kPolishThreads / 32;
 constexpr int kSortCap = 256;  // row entries whose steps a warp stages in shared memory
+constexpr int kQ = 4;          // terms per side of a thread's first candidate kept in registers
 
 __device__ __forceinline__ int other_end(int2 pr, int r) { return pr.x == r ? pr.y : pr.x; }
 
@@ -160,6 +161,10 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int gwarp = gtid >> 5, gwarps = gthreads >> 5;
+  // per-candidate and per-row loops run in this order (a permutation of the
+  // thread ids): consecutive items go to different CTAs, so the FP64 work of
+  // a few thousand candidates spreads over every SM
+  const int sid = threadIdx.x * gridDim.x + blockIdx.x;
   const WaitCtl wc = a.wait;
   const double lam = a.lambda;
   unsigned gen = 0;
@@ -175,7 +180,7 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
 
   // ---- counts per row, the candidates' values, the diagonal, max |s|
   double smax = 0.0;
-  for (int k = gtid; k < N; k += gthreads) {
+  for (int k = sid; k < N; k += gthreads) {
     const int2 pr = __ldg(a.cand + k);
     atomicAdd(w.deg + pr.x, 1);
     atomicAdd(w.deg + pr.y, 1);
@@ -205,7 +210,7 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
   if (overflow) status = kStatusCapacity;
   if (!overflow) {
     // ---- row entries (in any order), then ranked by colour step
-    for (int k = gtid; k < N; k += gthreads) {
+    for (int k = sid; k < N; k += gthreads) {
       const int2 pr = __ldg(a.cand + k);
       w.ent0[atomicAdd(w.cur + pr.x, 1)] = k;
       w.ent0[atomicAdd(w.cur + pr.y, 1)] = k;
@@ -254,7 +259,7 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
     // ---- terms of each (candidate, side): the other entries of the row, in
     //      colour-step order (the first pos of them precede the candidate),
     //      with the S entry each multiplies in the candidate's sum
-    for (int x = gtid; x < 2 * N; x += gthreads) {
+    for (int x = sid; x < 2 * N; x += gthreads) {
       const int k = x >> 1, sd = x & 1;
       const int2 pr = __ldg(a.cand + k);
       const int r = sd ? pr.y : pr.x, c = sd ? pr.x : pr.y;
@@ -285,7 +290,7 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
     for (int t = 0; t < a.n_sweeps; ++t) {
       // ---- base sums at the sweep's start (fixed order: diagonal, then the
       //      row's other entries in colour-step order)
-      for (int x = gtid; x < 2 * N; x += gthreads) {
+      for (int x = sid; x < 2 * N; x += gthreads) {
         const int k = x >> 1, sd = x & 1;
         const int2 pr = __ldg(a.cand + k);
         const int r = sd ? pr.y : pr.x, c = sd ? pr.x : pr.y;
@@ -298,14 +303,68 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
         if (!sd) w.d0[k] = 0.0;
       }
       grid_barrier(a.barrier, gen, wc, ++where);
-      // ---- the chain: fixed-point rounds of Eq. 3 over the candidates
+      // ---- the chain: fixed-point rounds of Eq. 3 over the candidates.
+      //      The thread's first candidate keeps what the rounds reuse in
+      //      registers (its sums at the sweep start, its denominator, value,
+      //      and the first kQ terms of each side), so a round waits on one
+      //      level of loads: the earlier candidates' current changes
       double* dc = w.d0;
       double* dn = w.d1;
       bool settled = false;
+      const int k0 = sid;
+      double c_a1 = 0.0, c_a2 = 0.0, c_den = 1.0, c_om = 0.0, c_d = 0.0;
+      int c_pi = 0, c_pj = 0;
+      size_t c_ti = 0, c_tj = 0;
+      int c_qi[kQ], c_qj[kQ];
+      double c_si[kQ], c_sj[kQ];
+      if (k0 < N) {
+        const int2 pr = __ldg(a.cand + k0);
+        const int ni = ldi(w.off + pr.x + 1) - ldi(w.off + pr.x);
+        const int nj = ldi(w.off + pr.y + 1) - ldi(w.off + pr.y);
+        c_pi = ldi(w.pos + 2 * k0);
+        c_pj = ldi(w.pos + 2 * k0 + 1);
+        c_ti = (size_t)ldi(w.toff + pr.x) + (size_t)c_pi * (ni - 1);
+        c_tj = (size_t)ldi(w.toff + pr.y) + (size_t)c_pj * (nj - 1);
+        c_a1 = __ldcg(w.base + 2 * k0);
+        c_a2 = __ldcg(w.base + 2 * k0 + 1);
+        c_den = __ldcg(w.den + k0);
+        c_om = __ldcg(w.om + k0);
+      }
+#pragma unroll
+      for (int m = 0; m < kQ; ++m) {
+        c_qi[m] = m < c_pi ? ldi(w.term_q + c_ti + m) : 0;
+        c_si[m] = m < c_pi ? __ldcg(w.term_s + c_ti + m) : 0.0;
+        c_qj[m] = m < c_pj ? ldi(w.term_q + c_tj + m) : 0;
+        c_sj[m] = m < c_pj ? __ldcg(w.term_s + c_tj + m) : 0.0;
+      }
       for (int rnd = 0; rnd < kPolishMaxRounds; ++rnd, ++gr) {
         if (gtid == 0) w.ctr[kPolChg + (gr + 1) % 3] = 0;  // read two barriers ago
         bool chg = false;
-        for (int k = gtid; k < N; k += gthreads) {
+        if (k0 < N) {
+          double x1[kQ], x2[kQ];
+#pragma unroll
+          for (int m = 0; m < kQ; ++m) {  // issued together, then summed in order
+            x1[m] = m < c_pi ? __ldcg(dc + c_qi[m]) : 0.0;
+            x2[m] = m < c_pj ? __ldcg(dc + c_qj[m]) : 0.0;
+          }
+          double a1 = c_a1, a2 = c_a2;
+#pragma unroll
+          for (int m = 0; m < kQ; ++m) {
+            if (m < c_pi) a1 = ::fma(x1[m], c_si[m], a1);
+            if (m < c_pj) a2 = ::fma(x2[m], c_sj[m], a2);
+          }
+          for (int m = kQ; m < c_pi; ++m)
+            a1 = ::fma(__ldcg(dc + ldi(w.term_q + c_ti + m)), __ldcg(w.term_s + c_ti + m), a1);
+          for (int m = kQ; m < c_pj; ++m)
+            a2 = ::fma(__ldcg(dc + ldi(w.term_q + c_tj + m)), __ldcg(w.term_s + c_tj + m), a2);
+          const double nv = soft(-a1 - a2, lam) / c_den;
+          const double d = nv - c_om;
+          chg |= __double_as_longlong(d) != __double_as_longlong(c_d);
+          c_d = d;
+          dn[k0] = d;
+          w.nw[k0] = nv;
+        }
+        for (int k = sid + gthreads; k < N; k += gthreads) {
           const int2 pr = __ldg(a.cand + k);
           const int ni = ldi(w.off + pr.x + 1) - ldi(w.off + pr.x);
           const int nj = ldi(w.off + pr.y + 1) - ldi(w.off + pr.y);
@@ -350,7 +409,7 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
 #pragma unroll
       for (int k = 0; k < kParts; ++k) v[k] = 0.0;
       double dmax = 0.0;
-      for (int r = gtid; r < p; r += gthreads) {
+      for (int r = sid; r < p; r += gthreads) {
         const int b = ldi(w.off + r), n = ldi(w.off + r + 1) - b;
         double cr = 0.0, dsum = 0.0;
         for (int m = 0; m < n; ++m) {
@@ -393,7 +452,7 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
         break;
       }
       // ---- commit
-      for (int k = gtid; k < N; k += gthreads) {
+      for (int k = sid; k < N; k += gthreads) {
         const double d = __ldcg(dc + k);
         if (d != 0.0) {
           w.om[k] = __ldcg(w.nw + k);
@@ -401,12 +460,12 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
           v[kPartActive] += 2.0;
         }
       }
-      for (int r = gtid; r < p; r += gthreads) w.diag[r] = __ldcg(w.diag_new + r);
+      for (int r = sid; r < p; r += gthreads) w.diag[r] = __ldcg(w.diag_new + r);
       grid_barrier(a.barrier, gen, wc, ++where);
       // ---- the candidates' objective / KKT terms after the sweep:
       //      W_ij = omega_ii s_ij + sum_{u in N(i), u != j} omega_iu s_uj +
       //      omega_ij s_jj (and W_ji alike), G = W_ij + W_ji
-      for (int k = gtid; k < N; k += gthreads) {
+      for (int k = sid; k < N; k += gthreads) {
         const int2 pr = __ldg(a.cand + k);
         const double om = __ldcg(w.om + k);
         double g = 0.0;
@@ -481,7 +540,7 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
       if (s_stop) break;
     }
     // ---- the iterate back into the dense FP64 Omega (both triangles)
-    for (int k = gtid; k < N; k += gthreads) {
+    for (int k = sid; k < N; k += gthreads) {
       const int2 pr = __ldg(a.cand + k);
       const double om = __ldcg(w.om + k);
       a.Om[(size_t)pr.x * ld + pr.y] = om;
