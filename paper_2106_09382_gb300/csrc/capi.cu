@@ -976,6 +976,8 @@ int polish_sparse(concord_state* st, double lambda, double tol, int stop_rule, i
     a.P = st->P;
     a.ld = st->ld;
     a.Om = st->Om64;
+    a.Om32 = (const float*)st->Om;
+    a.omdiag = st->omdiag64;
     a.S = st->S64;
     a.sdiag = st->sdiag64;
     a.mrow = st->mrow;
@@ -1071,12 +1073,18 @@ int promote_to_fp64(concord_state* st, double lambda, int list, bool rebuild_w =
     int rc = refine_s(st, lambda, list);
     if (rc != CONCORD_OK) return rc;
   }
-  CK(launch_convert(st->Om, 1, st->ld, st->Om64, 0, st->ld, st->p, st->p, st->stream));
-  CK(cudaMemcpy2DAsync(st->Om64, (size_t)(st->ld + 1) * sizeof(double), st->omdiag64,
-                       sizeof(double), sizeof(double), st->p, cudaMemcpyDeviceToDevice,
-                       st->stream));
-  if (rebuild_w)
+  if (rebuild_w) {
+    CK(launch_convert(st->Om, 1, st->ld, st->Om64, 0, st->ld, st->p, st->p, st->stream));
+    CK(cudaMemcpy2DAsync(st->Om64, (size_t)(st->ld + 1) * sizeof(double), st->omdiag64,
+                         sizeof(double), sizeof(double), st->p, cudaMemcpyDeviceToDevice,
+                         st->stream));
     CK(launch_refresh_w(st->Om64, st->S64, st->W64, st->p, st->ld, st->sms, st->stream));
+  } else {
+    // the sparse polish takes Omega from the FP32 iterate (its nonzeros are
+    // candidates of the list) and writes the FP64 candidates and diagonal
+    // into a zeroed FP64 Omega
+    CK(cudaMemsetAsync(st->Om64, 0, sizeof(double) * (size_t)st->p * st->ld, st->stream));
+  }
   st->w64_stale = !rebuild_w;
   st->om64_current = true;
   return CONCORD_OK;
@@ -1868,7 +1876,6 @@ static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, i
       if (!is_mixed(st)) return fail(CONCORD_E_ARG, "FP32 Gram feeds the mixed state only");
       CK(launch_apply_prep(X, x_f32, n, p, ldx, st->mean, st->inv_scale, Zf, 1, st->ldz, st->stream));
       CK(launch_syrk_f32(Zf, n, p, st->ldz, (float*)st->S, ld, 1.0f / n, st->stream));
-      CK(launch_convert(st->S, 1, ld, st->S64, 0, ld, p, p, st->stream));
       if (zt) {
         CK(launch_split_tf32(X, x_f32, n, p, ldx, st->mean, st->inv_scale, nullptr, nullptr,
                              st->zt_ldn, st->p_pad, st->stream, zt, st->zt_ldn));
@@ -1884,7 +1891,6 @@ static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, i
                                          (float*)st->S, ld, 1.0f / n, st->flag, st->stream);
       if (e == cudaErrorNotSupported) return fail(CONCORD_E_CUDA, "tensor-core Gram unavailable");
       CK(e);
-      CK(launch_convert(st->S, 1, ld, st->S64, 0, ld, p, p, st->stream));
       break;
     }
     case CONCORD_GRAM_BF16X3: {
@@ -1897,18 +1903,44 @@ static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, i
                                          1.0f / n, st->flag, st->stream);
       if (e == cudaErrorNotSupported) return fail(CONCORD_E_CUDA, "tensor-core Gram unavailable");
       CK(e);
-      CK(launch_convert(st->S, 1, ld, st->S64, 0, ld, p, p, st->stream));
       break;
     }
     default:
       return fail(CONCORD_E_ARG, "unknown Gram mode");
+  }
+  // mixed state from an FP32 S: the FP64 copy and the starting iterate in
+  // one pass over S (checks in bits 8 and 16 of the same flag, one read)
+  const bool fused = is_mixed(st) && st->gram_mode != CONCORD_GRAM_FP64;
+  if (fused) {
+    ResetMixedArgs ra;
+    ra.S = (const float*)st->S;
+    ra.ld = ld;
+    ra.p = p;
+    ra.P = st->P;
+    ra.W = (float*)st->W;
+    ra.Om = (float*)st->Om;
+    ra.S64 = st->S64;
+    ra.mrow = st->mrow;
+    ra.sdiag64 = st->sdiag64;
+    ra.sdiag32 = (float*)st->sdiagT;
+    ra.sd1 = (float*)st->sd1;
+    ra.sd2 = (float*)st->sd2;
+    ra.sd1_64 = st->sd1_64;
+    ra.sd2_64 = st->sd2_64;
+    ra.omdiag64 = st->omdiag64;
+    ra.bad = st->flag;
+    CK(launch_reset_mixed(ra, st->stream));
   }
   int bad = 0, rc;
   if ((rc = read_flag(st, &bad))) return rc;
   if (bad & 4) return fail(CONCORD_E_TIMEOUT, "tensor-core Gram: a device-side wait ran out");
   if (bad & 2) return fail(CONCORD_E_NONFINITE, "X has a non-finite entry");
   if (bad & 1) return fail(CONCORD_E_NONPOS_DIAG, "X has a constant column");
-  return reset_iterate(st);
+  if (!fused) return reset_iterate(st);
+  if (bad & 8) return fail(CONCORD_E_NONFINITE, "S has a non-finite diagonal entry");
+  if (bad & 16) return fail(CONCORD_E_NONPOS_DIAG, "S has a diagonal entry <= 0 (constant column?)");
+  st->om64_current = false;
+  return CONCORD_OK;
 }
 
 int concord_gram(const void* X_dev, int x_dtype, int n, int p, int ldx, int prep, int mode,

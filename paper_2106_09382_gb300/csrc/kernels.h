@@ -258,6 +258,25 @@ cudaError_t launch_fill_f64(double* a, double v, int n, cudaStream_t st);
 cudaError_t launch_row_absmax(const void* S, int s_f32, int ld, int p, float* m, cudaStream_t st);
 // A (p x ld, type) = identity with zero padding.
 cudaError_t launch_set_identity(void* A, int a_f32, int p, int ld, cudaStream_t st);
+// Mixed-precision start after a Gram into the FP32 S (p x ld, zero padding),
+// in one pass over S: W = S, Omega = I, S64 = S widened, m[u] as
+// launch_row_absmax, the diagonal (FP64 and FP32; bad |= 8 if non-finite,
+// 16 if not > 0), the walk vectors of launch_subdiag in both precisions, and
+// the FP64 diagonal of Omega = 1.
+struct ResetMixedArgs {
+  const float* S;
+  int ld, p, P;
+  float *W, *Om;
+  double* S64;
+  float* mrow;
+  double* sdiag64;
+  float* sdiag32;
+  float *sd1, *sd2;
+  double *sd1_64, *sd2_64;
+  double* omdiag64;
+  int* bad;
+};
+cudaError_t launch_reset_mixed(const ResetMixedArgs& a, cudaStream_t st);
 // bad |= 1 if |A - A^T| != 0 anywhere or a non-finite entry is met.
 cudaError_t launch_check_symmetric(const void* A, int a_f32, int p, int lda, int* bad,
                                    cudaStream_t st);
@@ -380,7 +399,9 @@ struct PolishWork {
 };
 struct PolishArgs {
   int p, P, ld;
-  double* Om;              // p x ld FP64 Omega (diagonal included), in and out
+  double* Om;              // p x ld FP64 Omega (zeroed): the result, diagonal included
+  const float* Om32;       // p x ld FP32 Omega of the FP32 phase (its off-diagonal values)
+  const double* omdiag;    // [p] its FP64 diagonal
   const double* S;         // p x ld FP64 S
   const double* sdiag;     // [p] s_ii
   const float* mrow;       // [p] m[u] >= max_{x != u} |s_ux|

@@ -184,11 +184,11 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
     const int2 pr = __ldg(a.cand + k);
     atomicAdd(w.deg + pr.x, 1);
     atomicAdd(w.deg + pr.y, 1);
-    w.om[k] = a.Om[(size_t)pr.x * ld + pr.y];
+    w.om[k] = (double)__ldg(a.Om32 + (size_t)pr.x * ld + pr.y);
     w.den[k] = __ldg(a.sdiag + pr.x) + __ldg(a.sdiag + pr.y);
   }
   for (int i = gtid; i < p; i += gthreads) {
-    w.diag[i] = a.Om[(size_t)i * ld + i];
+    w.diag[i] = __ldg(a.omdiag + i);
     smax = fmax(smax, fmax((double)__ldg(a.mrow + i), fabs(__ldg(a.sdiag + i))));
   }
   {
@@ -539,19 +539,21 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
       status = (int)s_res[kResStatus];
       if (s_stop) break;
     }
-    // ---- the iterate back into the dense FP64 Omega (both triangles)
-    for (int k = sid; k < N; k += gthreads) {
-      const int2 pr = __ldg(a.cand + k);
-      const double om = __ldcg(w.om + k);
-      a.Om[(size_t)pr.x * ld + pr.y] = om;
-      a.Om[(size_t)pr.y * ld + pr.x] = om;
-    }
-    for (int r = gtid; r < p; r += gthreads) a.Om[(size_t)r * ld + r] = __ldcg(w.diag + r);
     if (threadIdx.x == 0) {
       s_res[kResFirstDelta] = first_delta;
       s_res[kResAcc] = acc;
     }
   }
+  // ---- the iterate into the zeroed FP64 Omega (both triangles; every
+  //      nonzero off the diagonal is a candidate), also when the terms did
+  //      not fit (the values loaded at the start)
+  for (int k = sid; k < N; k += gthreads) {
+    const int2 pr = __ldg(a.cand + k);
+    const double om = __ldcg(w.om + k);
+    a.Om[(size_t)pr.x * ld + pr.y] = om;
+    a.Om[(size_t)pr.y * ld + pr.x] = om;
+  }
+  for (int r = gtid; r < p; r += gthreads) a.Om[(size_t)r * ld + r] = __ldcg(w.diag + r);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     s_res[kResSweeps] = sweeps;
     s_res[kResStatus] = status;

@@ -267,4 +267,65 @@ cudaError_t launch_scale_f32(float* a, size_t n, float s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// One warp per row u of S: 16-byte vectors of S in, of W, Omega and the FP64
+// copy out; lane 0 then writes the row's scalars.
+__global__ void __launch_bounds__(256) k_reset_mixed(const ResetMixedArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  const int nv = a.ld >> 2;  // float4 vectors per row (ld is a multiple of 32)
+  for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < a.p; u += warps) {
+    const float4* srow = reinterpret_cast<const float4*>(a.S + (size_t)u * a.ld);
+    float4* wrow = reinterpret_cast<float4*>(a.W + (size_t)u * a.ld);
+    float4* orow = reinterpret_cast<float4*>(a.Om + (size_t)u * a.ld);
+    double2* drow = reinterpret_cast<double2*>(a.S64 + (size_t)u * a.ld);
+    float mx = 0.f;
+    for (int q = lane; q < nv; q += 32) {
+      const float4 v = __ldg(srow + q);
+      wrow[q] = v;
+      const int c0 = 4 * q;
+      float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (u >= c0 && u < c0 + 4) (&o.x)[u - c0] = 1.f;
+      orow[q] = o;
+      drow[2 * q] = make_double2((double)v.x, (double)v.y);
+      drow[2 * q + 1] = make_double2((double)v.z, (double)v.w);
+      // padding columns are zero; the diagonal is left out
+      if (c0 != u) mx = fmaxf(mx, fabsf(v.x));
+      if (c0 + 1 != u) mx = fmaxf(mx, fabsf(v.y));
+      if (c0 + 2 != u) mx = fmaxf(mx, fabsf(v.z));
+      if (c0 + 3 != u) mx = fmaxf(mx, fabsf(v.w));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+      const float* row = a.S + (size_t)u * a.ld;
+      a.mrow[u] = nextafterf(mx, INFINITY);
+      const float d = row[u];
+      if (!isfinite(d))
+        atomicOr(a.bad, 8);
+      else if (!(d > 0.f))
+        atomicOr(a.bad, 16);
+      a.sdiag64[u] = (double)d;
+      a.sdiag32[u] = d;
+      a.omdiag64[u] = 1.0;
+      float s1 = 0.f, s2 = 0.f;
+      if (u > 0) {
+        s1 = row[u - 1];
+        const int nx = (u >= 3) ? u - 2 : u - 2 + a.P;
+        s2 = nx < a.p ? row[nx] : 0.f;
+      }
+      a.sd1[u] = s1;
+      a.sd2[u] = s2;
+      a.sd1_64[u] = (double)s1;
+      a.sd2_64[u] = (double)s2;
+    }
+  }
+}
+
+cudaError_t launch_reset_mixed(const ResetMixedArgs& a, cudaStream_t st) {
+  const int grid = (a.p + 7) / 8 < 152 * 8 ? (a.p + 7) / 8 : 152 * 8;
+  k_reset_mixed<<<grid, 256, 0, st>>>(a);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace concord
