@@ -326,7 +326,20 @@ template <typename T>
 __device__ __forceinline__ T pend_fold(const ScreenArgs<T>& a, int i, int n, int x, T wv) {
   const int* pu = a.w.pend_u + (size_t)i * kPendRow;
   const T* pd = a.w.pend_d + (size_t)i * kPendRow;
-  for (int k = 0; k < n; ++k) wv = fma_t(__ldcg(pd + k), __ldg(a.S + (size_t)ldi(pu + k) * a.ld + x), wv);
+  for (int k0 = 0; k0 < n; k0 += 8) {  // loads in batches, then the FMAs in order
+    int u[8];
+    T d[8], sv[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      u[r] = k0 + r < n ? ldi(pu + k0 + r) : -1;
+      d[r] = k0 + r < n ? __ldcg(pd + k0 + r) : (T)0;
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) sv[r] = u[r] >= 0 ? __ldg(a.S + (size_t)u[r] * a.ld + x) : (T)0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+      if (u[r] >= 0) wv = fma_t(d[r], sv[r], wv);
+  }
   return wv;
 }
 
@@ -458,6 +471,11 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
   const int nwarps = blockDim.x >> 5;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
   const int gwarp = blockIdx.x * nwarps + wid, gwarps = gridDim.x * nwarps;
+  // per-candidate loops take threads (warps) in this order: consecutive
+  // candidates land on different CTAs, so a few thousand candidates spread
+  // their scattered loads over every SM's load pipeline
+  const int sid = threadIdx.x * (int)gridDim.x + (int)blockIdx.x;
+  const int swarp = wid * (int)gridDim.x + (int)blockIdx.x;
   const int p = a.p, P = a.P, ld = a.ld;
   const ScreenWork<T>& w = a.w;
   const WaitCtl& wc = a.wait;
@@ -621,7 +639,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         // operands; each candidate's terms (row i's earlier candidates, then
         // row j's) get a contiguous range from a shared counter -- where the
         // range lies does not affect any value
-        for (int k = gtid; k < N; k += gthreads) {
+        for (int k = sid; k < N; k += gthreads) {
           const int2 pr = __ldcg(cand + k);
           const int i = pr.x, j = pr.y;
           T* rec = w.nd_rec + 4 * (size_t)k;
@@ -680,14 +698,14 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         //      round per link.  Thread gtid owns candidate gtid (operands in
         //      registers); further candidates (N > threads) reload theirs.
         // only the CTAs that own candidates iterate (barrier among them);
-        // the others wait at the phase's closing grid barrier.  In FP64 only
-        // the first kJacThreads threads of a CTA own candidates (enough for
-        // one candidate per thread over all SMs, at least two warps), so
-        // that the rounds' FP64 arithmetic (the division of Eq. 3) is spread
-        // over the SMs (FP64 throughput per SM is small on this part)
+        // the others wait at the phase's closing grid barrier.  Only the
+        // first kJacThreads threads of a CTA own candidates (enough for one
+        // candidate per thread over all SMs, at least two warps), so that
+        // the rounds' scattered loads (and in FP64 the division of Eq. 3,
+        // FP64 throughput per SM being small on this part) spread over the
+        // SMs
         const int kJacThreads =
-            sizeof(T) == 8 ? min(kScreenThreads, max(64, ((N + (int)gridDim.x - 1) / (int)gridDim.x + 31) / 32 * 32))
-                           : kScreenThreads;
+            min(kScreenThreads, max(64, ((N + (int)gridDim.x - 1) / (int)gridDim.x + 31) / 32 * 32));
         const int jac_ctas = min((int)gridDim.x, (N + kJacThreads - 1) / kJacThreads);
         const int jac_span = jac_ctas * kJacThreads;  // candidates owned one per thread
         if ((int)blockIdx.x < jac_ctas) {
@@ -810,59 +828,50 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         //      the row's lazy-verification bound D_i, and tentatively the row's
         //      new pending entries (its changes in step order, then the
         //      diagonal change)
-        for (int i = gwarp; i < p; i += gwarps) {
+        // (one thread per row, rows spread over the CTAs: the row's loads are
+        // a few dependent levels, so all rows proceed at once; the FMAs run
+        // in the same order as the dense kernel's)
+        for (int i = threadIdx.x * (int)gridDim.x + (int)blockIdx.x; i < p; i += gthreads) {
           const int b = ldi(w.off_r + i), ne = ldi(w.off_r + i + 1) - b;
           const int np = have_pend ? ldi(w.pend_n + i) : 0;
           int* pu = w.pend_u + (size_t)i * kPendRow;
           T* pdv = w.pend_d + (size_t)i * kPendRow;
-          T wii = __ldcg(Wa + (size_t)i * ld + i);
-          for (int m0 = 0; m0 < np; m0 += 32) {
-            const int m = m0 + lane;
-            T d = (T)0, sv = (T)0;
-            if (m < np) {
-              d = __ldcg(pdv + m);
-              sv = __ldg(a.S + (size_t)ldi(pu + m) * ld + i);
-            }
-            const int nm = min(32, np - m0);
-            for (int r = 0; r < nm; ++r) {  // pending entries are nonzero
-              const T dr = __shfl_sync(FULL, d, r), sr = __shfl_sync(FULL, sv, r);
-              wii = fma_t(dr, sr, wii);
-            }
-          }
+          T wii = pend_fold(a, i, np, i, __ldcg(Wa + (size_t)i * ld + i));
           double dsum = 0.0;  // sum of |d| m_u over the row's changes
           int nchg = 0;
-          for (int m0 = 0; m0 < ne; m0 += 32) {
-            const int m = m0 + lane;
-            T d = (T)0, sv = (T)0;
-            int u = 0;
-            if (m < ne) {
-              const int q = ldi(w.row_ent + b + m);
-              const int2 qp = __ldcg(w.cand[cur] + q);
-              u = qp.x == i ? qp.y : qp.x;
-              d = __ldcg(w.nd_delta + q);
-              if (d != (T)0) {
-                sv = __ldg(a.S + (size_t)u * ld + i);
-                dsum += fabs((double)d) * (double)__ldg(a.mrow + u);
+          for (int m0 = 0; m0 < ne; m0 += 8) {
+            int qv[8];
+            T dv[8], sv[8];
+            int uv[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) qv[r] = m0 + r < ne ? ldi(w.row_ent + b + m0 + r) : -1;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+              dv[r] = (T)0;
+              uv[r] = 0;
+              if (qv[r] >= 0) {
+                const int2 qp = __ldcg(w.cand[cur] + qv[r]);
+                uv[r] = qp.x == i ? qp.y : qp.x;
+                dv[r] = __ldcg(w.nd_delta + qv[r]);
               }
             }
-            const unsigned nz = __ballot_sync(FULL, d != (T)0);
-            if (d != (T)0) {
-              const int slot = np + nchg + __popc(nz & ((1u << lane) - 1u));
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+              sv[r] = dv[r] != (T)0 ? __ldg(a.S + (size_t)uv[r] * ld + i) : (T)0;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+              if (dv[r] == (T)0) continue;
+              dsum += fabs((double)dv[r]) * (double)__ldg(a.mrow + uv[r]);
+              const int slot = np + nchg;
               if (slot < kPendRow) {
-                pu[slot] = u;
-                pdv[slot] = d;
+                pu[slot] = uv[r];
+                pdv[slot] = dv[r];
               }
-            }
-            nchg += __popc(nz);
-            const int nm = min(32, ne - m0);
-            for (int r = 0; r < nm; ++r) {
-              const T dr = __shfl_sync(FULL, d, r), sr = __shfl_sync(FULL, sv, r);
-              if (dr != (T)0) wii = fma_t(dr, sr, wii);
+              ++nchg;
+              wii = fma_t(dv[r], sv[r], wii);
             }
           }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(FULL, dsum, o);
-          if (lane == 0) {
+          {
             const double sii = a.sdiag64[i];
             const T o_old = __ldcg(a.Om + (size_t)i * ld + i);
             const double oii = MIXED ? __ldcg(a.omdiag64 + i) : (double)o_old;
@@ -906,7 +915,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
           w.dfill[blockIdx.x] = s_fill;
         }
         // ---- commit the candidates' new values (both triangles)
-        for (int k = gtid; k < N; k += gthreads) {
+        for (int k = sid; k < N; k += gthreads) {
           const T d = __ldcg(w.nd_delta + k);
           if (d != (T)0) {
             const int2 pr = __ldcg(cand + k);
@@ -1132,7 +1141,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         // candidate); warp-uniform trip count for the list pushes.  Their W
         // after the sweep: the row pass's rows, or (DEFER) the stored rows
         // with the pending entries
-        for (int k0 = gwarp * 32; k0 < N; k0 += gwarps * 32) {
+        for (int k0 = swarp * 32; k0 < N; k0 += gwarps * 32) {
           const int k = k0 + lane;
           bool next = false;
           int i = 0, j = 0;
