@@ -158,7 +158,9 @@ __device__ __forceinline__ void group_barrier(unsigned* counter, unsigned& gen, 
   __syncthreads();
   ++gen;
   if (threadIdx.x == 0) {
-    __threadfence();
+    // the release add publishes the CTA's writes (ordered before it by the
+    // CTA barrier); the acquire load that sees the last arrival makes every
+    // other CTA's writes visible to the CTA after its closing barrier
     red_release_add_u32(counter, 1u);
     const unsigned target = gen * count;
     uint64_t t0 = globaltimer_ns();
@@ -172,7 +174,6 @@ __device__ __forceinline__ void group_barrier(unsigned* counter, unsigned& gen, 
         }
       }
     }
-    __threadfence();
   }
   __syncthreads();
 }
