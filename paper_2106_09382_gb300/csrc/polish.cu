@@ -131,10 +131,12 @@ __device__ __forceinline__ void block_parts(double (&v)[kParts], double (*s_p)[k
   for (int k = 0; k < kParts; ++k) {
     double x = v[k];
     const bool mx = k == kPartKkt || k == kPartDelta;
+    if (__any_sync(FULL, x != 0.0)) {  // skip the FP64 tree of warps without terms
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double y = __shfl_xor_sync(FULL, x, o);
-      x = mx ? fmax(x, y) : x + y;
+      for (int o = 16; o > 0; o >>= 1) {
+        const double y = __shfl_xor_sync(FULL, x, o);
+        x = mx ? fmax(x, y) : x + y;
+      }
     }
     v[k] = x;
   }

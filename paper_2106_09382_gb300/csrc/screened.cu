@@ -160,7 +160,9 @@ __device__ __forceinline__ void sub_barrier(unsigned* counter, unsigned target, 
                                             int where) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
+    // the release add publishes the CTA's writes (ordered before it by the
+    // CTA barrier); the acquire load that sees the last arrival makes every
+    // other CTA's writes visible to the CTA after its closing barrier
     red_release_add_u32(counter, 1u);
     const uint64_t t0 = globaltimer_ns();
     unsigned it = 0;
@@ -173,7 +175,6 @@ __device__ __forceinline__ void sub_barrier(unsigned* counter, unsigned target, 
         }
       }
     }
-    __threadfence();
   }
   __syncthreads();
 }
@@ -196,10 +197,15 @@ __device__ __forceinline__ void reduce_parts(double (&v)[kParts], double* out,
 #pragma unroll
   for (int k = 0; k < kParts; ++k) {
     double x = v[k];
+    // most warps hold no terms of a part: skip their FP64 shuffle tree (the
+    // FP64 pipe is narrow on this part, and 512 threads x 8 parts x 5 levels
+    // of it cost microseconds per sweep)
+    if (__any_sync(FULL, x != 0.0)) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double y = __shfl_down_sync(FULL, x, o);
-      x = (k == kPartKkt || k == kPartDelta) ? fmax(x, y) : x + y;
+      for (int o = 16; o > 0; o >>= 1) {
+        const double y = __shfl_down_sync(FULL, x, o);
+        x = (k == kPartKkt || k == kPartDelta) ? fmax(x, y) : x + y;
+      }
     }
     if (lane == 0) red[wid][k] = x;
   }
