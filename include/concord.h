@@ -108,7 +108,7 @@ extern "C" {
 
 /* ------------------------------------------------------------- results */
 /* Filled by concord_sweep / concord_run / concord_solve*.  Plain C layout:
- * 4 ints, 4 doubles, 1 int64, 1 double, 8 ints (see concord_result_size). */
+ * 4 ints, 4 doubles, 1 int64, 1 double, 9 ints (see concord_result_size). */
 typedef struct concord_result {
     int status;            /* CONCORD_OK, CONCORD_NOT_CONVERGED or an error  */
     int sweeps;            /* outer iterations of Algorithm 1 done (all phases) */
@@ -132,6 +132,9 @@ typedef struct concord_result {
                               sweeps count as well */
     int sparse_sweeps;     /* MIXED: polish sweeps run by the sparse polish
                               (concord_set_sparse_polish) */
+    int partial_sweeps;    /* lazy sweeps (FP32 screened or sparse polish) that
+                              verified only the pairs of the rows whose bound
+                              left half the margin */
 } concord_result;
 
 /* KKT residual (absolute, S units), with W = Omega S and G = W + W^T:
@@ -402,8 +405,12 @@ int concord_set_refine(concord_state *st, int on);
  * the sum of these bounds since the list was screened stays within 0.09
  * lambda, no pair outside it can reach the threshold, so the sweep skips the
  * verification pass and keeps the list (and its build) for the next sweep.
- * The iterates are the same either way; concord_result.lazy_sweeps counts
- * the skipped verifications.  Errors: CONCORD_E_ARG.
+ * The bound is kept per row (the sum of its changes' bounds since the row's
+ * pairs were screened): when only a few rows exceed half the margin,
+ * only their pairs are verified and screened (a partial sweep), from the
+ * stored rows and their deferred updates.  The iterates are the same either
+ * way; concord_result.lazy_sweeps counts the skipped full verifications,
+ * partial_sweeps the partial ones among them.  Errors: CONCORD_E_ARG.
  */
 int concord_set_lazy_verify(concord_state *st, int on);
 

@@ -44,7 +44,7 @@ class ConcordResult(ctypes.Structure):
                 ("timeout_vertex", ctypes.c_int), ("timeout_step", ctypes.c_int),
                 ("screen_redos", ctypes.c_int), ("dense_sweeps", ctypes.c_int),
                 ("s_refined", ctypes.c_int), ("lazy_sweeps", ctypes.c_int),
-                ("sparse_sweeps", ctypes.c_int)]
+                ("sparse_sweeps", ctypes.c_int), ("partial_sweeps", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}

@@ -190,6 +190,7 @@ struct RunOut {
   double acc = 0;                   // screened: lazy bound accumulated on the next sweep's list
   int lazy = 0;                     // screened sweeps that skipped the verification
   int sparse = 0;                   // polish sweeps run by the sparse polish
+  int partial = 0;                  // screened sweeps that verified only their loud rows
 };
 
 // One persistent launch: n_sweeps outer iterations (fewer if the stopping
@@ -363,7 +364,7 @@ int launch_dense(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, double* 
 struct ScreenLayout {
   size_t ctr, cand0, cand1, cnt_r0, cnt_r1, fail, off_r, cur_r, nd_pi, nd_pj, row_ent, term_ptr, term_pred, term_s, nd_rec, nd_delta, nd_new, nd_d2, jac,
       diag_old, omdiag_old, diag_new, dpart, dfill, diag_dd, pend_u, pend_d, pend_n, pend_new,
-      total;
+      rowacc, rowa_new, apart, loud, loudf, total;
 };
 
 ScreenLayout screen_layout(int p, int P, int nc, int tc) {
@@ -404,6 +405,11 @@ ScreenLayout screen_layout(int p, int P, int nc, int tc) {
   L.pend_d = take(sizeof(double) * (size_t)p * kPendRow);
   L.pend_n = take(sizeof(int) * (size_t)p);
   L.pend_new = take(sizeof(int) * (size_t)p);
+  L.rowacc = take(sizeof(double) * (size_t)p);
+  L.rowa_new = take(sizeof(double) * (size_t)p);
+  L.apart = take(sizeof(double) * 1024);
+  L.loud = take(sizeof(int) * kLoudMax);
+  L.loudf = take(sizeof(int) * (size_t)p);
   L.total = off;
   return L;
 }
@@ -479,6 +485,11 @@ ScreenWork<T> screen_work(concord_state* st) {
   w.pend_d = (T*)(b + L.pend_d);
   w.pend_n = (int*)(b + L.pend_n);
   w.pend_new = (int*)(b + L.pend_new);
+  w.rowacc = (double*)(b + L.rowacc);
+  w.rowa_new = (double*)(b + L.rowa_new);
+  w.apart = (double*)(b + L.apart);
+  w.loud = (int*)(b + L.loud);
+  w.loudf = (int*)(b + L.loudf);
   w.nc_cap = st->nc_cap;
   w.term_cap = st->term_cap;
   w.fail_cap = st->nc_cap;
@@ -587,6 +598,7 @@ int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, d
   out->next_list = (int)r[kResList];
   out->lazy = (int)r[kResLazy];
   out->acc = r[kResAcc];
+  out->partial = (int)r[kResPartial];
   if (slot_ev >= 0) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, st->lev[2 * slot_ev], st->lev[2 * slot_ev + 1]));
@@ -698,6 +710,7 @@ void fill_result(concord_result* res, const RunOut& o, int sweeps, int sweeps32,
   res->s_refined = o.s_refined;
   res->lazy_sweeps = o.lazy;
   res->sparse_sweeps = o.sparse;
+  res->partial_sweeps = o.partial;
 }
 
 int ensure_path(concord_state* st, int n_lambda, size_t n_rows) {
@@ -920,7 +933,8 @@ int ensure_polish(concord_state* st, int term_cap) {
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t ints = al(sizeof(int) * kPolCtrs) + 3 * al(sizeof(int) * (p + 1)) +
                       al(sizeof(int) * p) + 3 * al(sizeof(int) * 2 * nc) + al(sizeof(int) * tc);
-  const size_t dbls = al(8 * tc) + 5 * al(8 * nc) + al(8 * 2 * nc) + 2 * al(8 * p) + al(8 * grid);
+  const size_t dbls = al(8 * tc) + 5 * al(8 * nc) + al(8 * 2 * nc) + 4 * al(8 * p) + al(8 * grid) +
+                      al(sizeof(int) * kPolLoudMax) + al(sizeof(int) * p);
   char* m = nullptr;
   CK(cudaMalloc((void**)&m, ints + dbls));
   st->pol.mem = m;
@@ -948,6 +962,10 @@ int ensure_polish(concord_state* st, int term_cap) {
   w.diag = (double*)take(8 * p);
   w.diag_new = (double*)take(8 * p);
   w.dpart = (double*)take(8 * grid);
+  w.rowa = (double*)take(8 * p);
+  w.rowb = (double*)take(8 * p);
+  w.loud = (int*)take(sizeof(int) * kPolLoudMax);
+  w.loudf = (int*)take(sizeof(int) * p);
   w.nc_cap = st->nc_cap;
   w.term_cap = term_cap;
   return CONCORD_OK;
@@ -985,6 +1003,7 @@ int polish_sparse(concord_state* st, double lambda, double tol, int stop_rule, i
     a.n_cand = sw.ctr + kCtrCand + list;
     a.ds_bits = (st->refine && st->zt_valid && st->rf.ctr) ? st->rf.ctr + kRefineDs : nullptr;
     a.acc0 = acc;
+    a.rowacc = sw.rowacc;  // the FP32 launch's per-row bound on this list
     a.w = w;
     a.barrier = st->barrier;
     a.wait.abort = st->abort_info;
@@ -1041,6 +1060,7 @@ int polish_sparse(concord_state* st, double lambda, double tol, int stop_rule, i
     out->next_list = -1;
     out->lazy = (int)r[kResLazy];
     out->acc = r[kResAcc];
+    out->partial = (int)r[kResPartial];
     if (st->h_abort[0] != 0) {
       out->status = CONCORD_E_TIMEOUT;
       out->to_vertex = st->h_abort[1];
@@ -1189,6 +1209,7 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
   o2.redos += o1.redos;
   o2.dense_sweeps += o1.dense_sweeps;
   o2.lazy += o1.lazy;
+  o2.partial += o1.partial;
   o2.s_refined = *st->h_rf;  // read back by the polish launch's synchronisation
   fill_result(res, o2, o1.sweeps + o2.sweeps, o1.sweeps, fd, lambda, ms * 1e-3);
   return rc != CONCORD_OK ? rc : o2.status;

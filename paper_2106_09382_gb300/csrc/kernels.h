@@ -42,8 +42,9 @@ constexpr int kResSweeps = 0, kResKkt = 1, kResObj = 2, kResDelta = 3, kResActiv
               kResPath = 8,  // screened path: index of the lambda a dense hand-over stopped at
               kResList = 9,  // screened: candidate list of the next sweep (-1: none valid)
               kResLazy = 10, // screened: sweeps that skipped the verification (lazy)
-              kResAcc = 11;  // screened: accumulated lazy bound of the next sweep's list
-constexpr int kRes = 12;
+              kResAcc = 11,  // screened: accumulated lazy bound of the next sweep's list
+              kResPartial = 12;  // screened: sweeps that verified only their loud rows' pairs
+constexpr int kRes = 13;
 constexpr int kHist = 4;  // per sweep: delta, kkt, objective, active pairs
 
 // One problem of a batched launch of the sweep kernel: its own dimension,
@@ -133,8 +134,10 @@ constexpr int kCtrTerms = 3;      // correction terms of the current candidate s
 constexpr int kCtrJacBar = 4;     // barrier counter of the fixed-point iteration
 constexpr int kCtrJacDone = 5;    // the fixed-point iteration settled
 constexpr int kCtrTermsPred = 6;  // correction terms the current list needs (sum over rows of k (k - 1) / 2)
+constexpr int kCtrLoud = 7;       // rows whose lazy bound left half the margin this sweep
 constexpr int kCtrs = 8;
 constexpr int kJacMax = 64;       // fixed-point iterations of the chain before the dense kernel takes the sweep
+constexpr int kLoudMax = 256;     // rows a partial verification takes (more: a full sweep)
 constexpr int kStatusDense = 5;   // result status: the next sweep needs the dense kernel
 constexpr int kPendRow = 32;      // deferred W updates a row holds (lazy sweeps)
 
@@ -167,6 +170,15 @@ struct ScreenWork {
   int* pend_u;              // [p x kPendRow]
   T* pend_d;                // [p x kPendRow]
   int *pend_n, *pend_new;   // [p] (zeroed before the launch)
+  // per-row lazy bound: rowacc[i] bounds how far G_ij of a pair outside the
+  // list has moved since row i's pairs were screened (through row i's
+  // changes); rowa_new is rowacc + this sweep's D_i, loudf marks the rows
+  // whose rowa_new exceeds half the margin (listed in loud when they fit)
+  double* rowacc;           // [p]
+  double* rowa_new;         // [p]
+  double* apart;            // [grid] per-CTA largest rowa_new of the quiet rows
+  int* loud;                // [kLoudMax]
+  int* loudf;               // [p]
   int nc_cap, term_cap, fail_cap;
 };
 
@@ -374,7 +386,10 @@ constexpr int kPolChg = 0;            // ctr[0..2]: changed flags of the chain's
 constexpr int kPolOverflow = 3;       // ctr: terms needed when they do not fit (0: fit)
 constexpr int kPolRowMax = 4;         // ctr[4..5]: max_i sum_u |omega_iu| (double bits)
 constexpr int kPolSMax = 6;           // ctr[6..7]: max |s_ux| (double bits)
-constexpr int kPolCtrs = 8;
+constexpr int kPolLoud = 8;           // ctr: rows whose bound leaves half the margin this sweep
+constexpr int kPolFail = 9;           // ctr: a verified pair would have left zero
+constexpr int kPolCtrs = 10;
+constexpr int kPolLoudMax = 256;      // rows one polish sweep verifies (more: W is rebuilt)
 struct PolishWork {
   int* ctr;          // [kPolCtrs] (zeroed before the launch)
   int* deg;          // [p + 1] entries per row (zeroed before the launch)
@@ -395,6 +410,13 @@ struct PolishWork {
   double* diag;      // [p] the diagonal of Omega
   double* diag_new;  // [p]
   double* dpart;     // [grid] per-CTA largest row bound of a sweep
+  // per-row bound on how far G_ij of a pair outside the list has moved since
+  // the screen (pair bound rowa_i + rowa_j); rows beyond half the margin are
+  // verified exactly (their W entries are short sums over Omega's nonzeros)
+  double* rowa;      // [p]
+  double* rowb;      // [p] rowa + this sweep's D_i
+  int* loud;         // [kPolLoudMax]
+  int* loudf;        // [p] 0: quiet; 2: loud, its pairs within 0.9 lambda; 1: loud, some beyond
   int nc_cap, term_cap;
 };
 struct PolishArgs {
@@ -409,6 +431,8 @@ struct PolishArgs {
   const int* n_cand;       // device: their number
   const int* ds_bits;      // nullable: float bits of max |S64 - S32 used by the FP32 phase|
   double acc0;             // lazy bound accumulated by the FP32 phase since its screen
+  const double* rowacc;    // nullable: the FP32 phase's per-row bound (pair bound a_i + a_j);
+                           // without it every row starts at acc0 / 2
   PolishWork w;
   unsigned* barrier;       // zeroed before the launch
   WaitCtl wait;

@@ -29,9 +29,13 @@
 //            satisfies every equation, so it is the sequential solution;
 //   diagonal Eq. 2 per row with the new off-diagonal values, the row bound
 //            D_i, and the diagonal's objective / KKT terms;
-//   decision if the accumulated bound would leave the margin, nothing is
-//            committed and the launch returns kStatusNeedW (the host then
-//            rebuilds W and runs the screened polish, which verifies);
+//   decision the bound is kept per row (rowa_i: pair bound rowa_i + rowa_j,
+//            from the FP32 phase's per-row bound plus the change of S).
+//            Rows beyond half the margin have their pairs verified exactly
+//            (their W entries are short sums too); too many such rows or a
+//            pair that would leave zero: nothing is committed and the launch
+//            returns kStatusNeedW (the host then rebuilds W and runs the
+//            screened polish, which verifies everything);
 //   terms    objective and KKT terms of the candidates after the sweep.
 // Each candidate row's entries are kept in colour-step order; every sum runs
 // in a fixed order, so the iterates do not depend on the launch layout.
@@ -156,6 +160,65 @@ __device__ __forceinline__ void block_parts(double (&v)[kParts], double (*s_p)[k
   }
 }
 
+// The pairs (i, j) of the loud rows i that are not candidates, once each (a
+// pair of two loud rows by the smaller row); one warp per (loud row, 32
+// columns).  W_ij at the pair's visit takes the entries of row i visited
+// before it at their new values and the others (and the diagonal) at their
+// old ones; after the sweep all at their new values.  A pair whose Eq. 3
+// would leave zero sets the fail flag; a pair beyond the screen's 0.9 lambda
+// after the sweep keeps its rows' bounds (loudf 1); the KKT terms are added.
+__device__ __forceinline__ void row_sums(const PolishArgs& a, int r, int c, int c_step, int P,
+                                         double& at_visit, double& after) {
+  const PolishWork& w = a.w;
+  const int ld = a.ld;
+  const double src = __ldg(a.S + (size_t)r * ld + c);
+  double vis = __ldcg(w.diag + r) * src, end = __ldcg(w.diag_new + r) * src;
+  const int b = ldi(w.off + r), n = ldi(w.off + r + 1) - b;
+  for (int m = 0; m < n; ++m) {
+    const int q = ldi(w.ent + b + m);
+    const int2 pr = __ldg(a.cand + q);
+    const double s = __ldg(a.S + (size_t)other_end(pr, r) * ld + c);
+    const double nv = __ldcg(w.nw + q);
+    vis = ::fma(pair_step(pr.x, pr.y, P) < c_step ? nv : __ldcg(w.om + q), s, vis);
+    end = ::fma(nv, s, end);
+  }
+  at_visit = vis;
+  after = end;
+}
+
+__device__ __noinline__ void verify_loud(const PolishArgs& a, int nloud, double lam,
+                                         double (&v)[kParts], int lane, int swarp, int gwarps,
+                                         int P) {
+  const PolishWork& w = a.w;
+  const int p = a.p;
+  const int nchunk = (p + 31) >> 5;
+  const double lam_s = (1.0 - kScreenMargin) * lam;
+  for (int item = swarp; item < nloud * nchunk; item += gwarps) {
+    const int i = ldi(w.loud + item / nchunk);
+    const int j = (item % nchunk) * 32 + lane;
+    bool pair = j < p && j != i;
+    if (pair && j < i && ldi(w.loudf + j) != 0) pair = false;
+    {  // candidates are not verified
+      const int b = ldi(w.off + i), n = ldi(w.off + i + 1) - b;
+      for (int m = 0; m < n && pair; ++m)
+        if (other_end(__ldg(a.cand + ldi(w.ent + b + m)), i) == j) pair = false;
+    }
+    if (!pair) continue;
+    const int c_step = pair_step(min(i, j), max(i, j), P);
+    double vi, ei, vj, ej;
+    row_sums(a, i, j, c_step, P, vi, ei);
+    row_sums(a, j, i, c_step, P, vj, ej);
+    if (soft(-vi - vj, lam) != 0.0) atomicOr(w.ctr + kPolFail, 1);
+    const double g = ei + ej;
+    if (fabs(g) > lam_s) {
+      w.loudf[i] = 1;
+      if (ldi(w.loudf + j) != 0) w.loudf[j] = 1;
+    }
+    v[kPartKkt] = fmax(v[kPartKkt], fmax(fabs(g) - lam, 0.0));
+    if (!isfinite(g)) v[kPartBad] += 1.0;
+  }
+}
+
 __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a) {
   const int p = a.p, P = a.P, ld = a.ld;
   const PolishWork& w = a.w;
@@ -167,6 +230,7 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
   // thread ids): consecutive items go to different CTAs, so the FP64 work of
   // a few thousand candidates spreads over every SM
   const int sid = threadIdx.x * gridDim.x + blockIdx.x;
+  const int swarp = wid * (int)gridDim.x + (int)blockIdx.x;  // the same for warps
   const WaitCtl wc = a.wait;
   const double lam = a.lambda;
   unsigned gen = 0;
@@ -175,7 +239,7 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
   __shared__ double s_p[kWarps][kParts];
   __shared__ int s_steps[kWarps][kSortCap];
   __shared__ double s_res[kRes];
-  __shared__ int s_stop, s_ok;
+  __shared__ int s_stop;
   const int N = min(__ldg(a.n_cand), w.nc_cap);
   if (threadIdx.x == 0)
     for (int k = 0; k < kRes; ++k) s_res[k] = 0.0;
@@ -218,7 +282,6 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
       w.ent0[atomicAdd(w.cur + pr.y, 1)] = k;
     }
     grid_barrier(a.barrier, gen, wc, ++where);
-    double rowmax = 0.0;  // max_r sum_u |omega_ru| (diagonal included)
     for (int r = gwarp; r < p; r += gwarps) {
       const int b = ldi(w.off + r), n = ldi(w.off + r + 1) - b;
       const bool staged = n <= kSortCap;
@@ -250,12 +313,7 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(FULL, rs, o);
-      rowmax = fmax(rowmax, rs + fabs(__ldcg(w.diag + r)));
       __syncwarp();
-    }
-    {
-      const double m = block_max(rowmax, s_w);
-      if (threadIdx.x == 0) atomic_max_nonneg(w.ctr + kPolRowMax, m);
     }
     grid_barrier(a.barrier, gen, wc, ++where);
     // ---- terms of each (candidate, side): the other entries of the row, in
@@ -278,20 +336,32 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
         ++t;
       }
     }
+    // per-row bound carried from the FP32 phase, plus the change of S under
+    // the iterate: |G_ij(S64) - G_ij(S32)| <= (||Omega_i||_1 + ||Omega_j||_1)
+    // max|dS|, with max|dS| the refined entries' largest change or FP32
+    // rounding of S
+    {
+      const double ds_ref = a.ds_bits ? (double)__int_as_float(__ldg(a.ds_bits)) : 0.0;
+      const double ds = fmax(ds_ref, ld_nonneg(w.ctr + kPolSMax) * 0x1p-24);
+      for (int r = sid; r < p; r += gthreads) {
+        const int b = ldi(w.off + r), n = ldi(w.off + r + 1) - b;
+        double rs = fabs(__ldcg(w.diag + r));
+        for (int m = 0; m < n; ++m) rs += fabs(__ldcg(w.om + ldi(w.ent + b + m)));
+        w.rowa[r] = (a.rowacc ? __ldcg(a.rowacc + r) : 0.5 * a.acc0) + rs * ds;
+      }
+    }
     grid_barrier(a.barrier, gen, wc, ++where);
-
-    // bound carried from the FP32 phase, plus the change of S under the
-    // iterate: |G_ij(S64) - G_ij(S32)| <= 2 max_r ||Omega_r||_1 max|dS|, with
-    // max|dS| the refined entries' largest change or FP32 rounding of S
-    const double ds_ref = a.ds_bits ? (double)__int_as_float(__ldg(a.ds_bits)) : 0.0;
-    const double ds = fmax(ds_ref, ld_nonneg(w.ctr + kPolSMax) * 0x1p-24);
-    double acc = a.acc0 + 2.0 * ld_nonneg(w.ctr + kPolRowMax) * ds;
-    const double bound = (kScreenMargin - kLazySlack) * lam;
+    const double half_bound = 0.5 * (kScreenMargin - kLazySlack) * lam;
     int gr = 0;  // fixed-point rounds so far (all sweeps): selects the flag slot
     int first_delta = 0;
+  int n_partial = 0;  // sweeps that verified loud rows
     for (int t = 0; t < a.n_sweeps; ++t) {
       // ---- base sums at the sweep's start (fixed order: diagonal, then the
       //      row's other entries in colour-step order)
+      if (gtid == 0) {
+        w.ctr[kPolLoud] = 0;
+        w.ctr[kPolFail] = 0;
+      }
       for (int x = sid; x < 2 * N; x += gthreads) {
         const int k = x >> 1, sd = x & 1;
         const int2 pr = __ldg(a.cand + k);
@@ -410,7 +480,6 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
       double v[kParts];
 #pragma unroll
       for (int k = 0; k < kParts; ++k) v[k] = 0.0;
-      double dmax = 0.0;
       for (int r = sid; r < p; r += gthreads) {
         const int b = ldi(w.off + r), n = ldi(w.off + r + 1) - b;
         double cr = 0.0, dsum = 0.0;
@@ -424,7 +493,14 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
         const double nd = (-cr + sqrt(cr * cr + 4.0 * sii)) / (2.0 * sii);
         const double dw = nd - oii;
         w.diag_new[r] = nd;
-        dmax = fmax(dmax, dsum + fabs(dw) * (double)__ldg(a.mrow + r));
+        const double rb = __ldcg(w.rowa + r) + dsum + fabs(dw) * (double)__ldg(a.mrow + r);
+        w.rowb[r] = rb;
+        const bool loud = !(rb <= half_bound);
+        w.loudf[r] = loud ? 2 : 0;  // 2: loud, its pairs within 0.9 lambda so far
+        if (loud) {
+          const int slot = atomicAdd(w.ctr + kPolLoud, 1);
+          if (slot < kPolLoudMax) w.loud[slot] = r;
+        }
         const double wd = ::fma(nd, sii, cr);  // W_rr after the sweep
         v[kPartDelta] = fmax(v[kPartDelta], fabs(dw));
         if (nd > 0.0 && isfinite(wd) && isfinite(nd)) {
@@ -435,23 +511,28 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
           v[kPartBad] += 1.0;
         }
       }
-      {
-        const double m = block_max(dmax, s_w);
-        if (threadIdx.x == 0) w.dpart[blockIdx.x] = m;
-      }
       grid_barrier(a.barrier, gen, wc, ++where);
-      // ---- decision (every CTA alike): the bound after this sweep
-      if (threadIdx.x == 0) {
-        double dm = 0.0;
-        for (int c = 0; c < (int)gridDim.x; ++c) dm = fmax(dm, __ldcg(w.dpart + c));
-        s_w[0] = dm;
-        s_ok = acc + 2.0 * dm <= bound ? 1 : 0;
-      }
-      __syncthreads();
-      const double dsweep = s_w[0];
-      if (!s_ok) {
-        status = kStatusNeedW;  // nothing of this sweep is committed
+      // ---- decision (every CTA alike).  A pair outside the list has moved
+      //      by at most rowb_i + rowb_j since it was screened: pairs of two
+      //      rows within half the margin stay at zero.  The pairs of the
+      //      other rows (a few) are verified exactly: Eq. 3's zero test at
+      //      their visit, from the sums over the nonzeros of rows i and j
+      //      with the values each had at that step.  Too many such rows, or
+      //      a pair that would have left zero: nothing of this sweep is
+      //      committed (W is rebuilt and the screened polish takes over)
+      const int nloud = ldi(w.ctr + kPolLoud);
+      if (nloud > kPolLoudMax) {
+        status = kStatusNeedW;
         break;
+      }
+      if (nloud > 0) {
+        ++n_partial;
+        verify_loud(a, nloud, lam, v, lane, swarp, gwarps, P);
+        grid_barrier(a.barrier, gen, wc, ++where);
+        if (ldi(w.ctr + kPolFail) != 0) {
+          status = kStatusNeedW;
+          break;
+        }
       }
       // ---- commit
       for (int k = sid; k < N; k += gthreads) {
@@ -462,7 +543,12 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
           v[kPartActive] += 2.0;
         }
       }
-      for (int r = sid; r < p; r += gthreads) w.diag[r] = __ldcg(w.diag_new + r);
+      for (int r = sid; r < p; r += gthreads) {
+        w.diag[r] = __ldcg(w.diag_new + r);
+        // a verified row whose pairs all stayed within 0.9 lambda restarts
+        // its bound; every other row keeps its bound, grown by the sweep
+        w.rowa[r] = ldi(w.loudf + r) == 2 ? 0.0 : __ldcg(w.rowb + r);
+      }
       grid_barrier(a.barrier, gen, wc, ++where);
       // ---- the candidates' objective / KKT terms after the sweep:
       //      W_ij = omega_ii s_ij + sum_{u in N(i), u != j} omega_iu s_uj +
@@ -514,7 +600,6 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
           bad += __shfl_xor_sync(FULL, bad, o);
         }
       }
-      acc += 2.0 * dsweep;
       sweeps = t + 1;
       if (threadIdx.x == 0) {
         const double obj = -lg + 0.5 * quad + lam * pen;
@@ -543,7 +628,8 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
     }
     if (threadIdx.x == 0) {
       s_res[kResFirstDelta] = first_delta;
-      s_res[kResAcc] = acc;
+      s_res[kResAcc] = 0.0;
+      s_res[kResPartial] = n_partial;
     }
   }
   // ---- the iterate into the zeroed FP64 Omega (both triangles; every

@@ -38,7 +38,7 @@
 namespace concord {
 
 // How a sweep ends (see the decision in the kernel).
-constexpr int kModeFull = 0, kModeLazy = 1, kModeDefer = 2;
+constexpr int kModeFull = 0, kModeLazy = 1, kModeDefer = 2, kModePartial = 3;
 
 // Candidates of one row sorted by a warp in shared memory (longer rows: one
 // thread, insertion sort).
@@ -395,6 +395,83 @@ __device__ void flush_pending(const ScreenArgs<T>& a, T* __restrict__ W, int lan
 // list and the diagonal's from the row pass.  Kept out of line: compiled
 // inside the sweep kernel's body its loads were scheduled less well (the
 // pass ran about 10% of a sweep slower).
+// Partial verification (a sweep whose per-row bound fails only on a few
+// "loud" rows): the pairs (i, j) of the loud rows i that are not candidates,
+// with the same tests as verify_pass -- Eq. 3's zero test at the visit, the
+// next sweep's screen and the KKT term after the sweep.  W_ij at the visit
+// and after the sweep come from the stored row with its pending entries
+// (the rows are not updated in such a sweep): the old entries, then the
+// sweep's changes in step order (the visit value is taken before the first
+// change at a later step), then the diagonal change -- the FMA order of a
+// flush followed by the row pass, so the decisions are the full pass's.
+// One warp per (loud row, 32 columns); a pair of two loud rows is taken by
+// the smaller row.  Failing pairs go to the fail list, screened pairs to the
+// next list's slot (merged into the kept list once the sweep stands).
+template <typename T>
+__device__ __forceinline__ void row_at_visit(const ScreenArgs<T>& a, const T* __restrict__ W, int r,
+                                             int c, int c_step, T& at_visit, T& after) {
+  const ScreenWork<T>& w = a.w;
+  const int P = a.P, ld = a.ld;
+  const int npo = ldi(w.pend_n + r), npn = ldi(w.pend_new + r);
+  const int* pu = w.pend_u + (size_t)r * kPendRow;
+  const T* pd = w.pend_d + (size_t)r * kPendRow;
+  T acc = pend_fold(a, r, npo, c, __ldcg(W + (size_t)r * ld + c));
+  T vis = acc;
+  bool cap = false;
+  for (int m = npo; m < npn; ++m) {
+    const int u = ldi(pu + m);
+    // the diagonal change (u == r) follows every colour step
+    const int cm = u == r ? 0x7fffffff : pair_step(min(r, u), max(r, u), P);
+    if (!cap && cm > c_step) {
+      vis = acc;
+      cap = true;
+    }
+    acc = fma_t(__ldcg(pd + m), __ldg(a.S + (size_t)u * ld + c), acc);
+  }
+  at_visit = cap ? vis : acc;
+  after = acc;
+}
+
+template <typename T>
+__device__ __noinline__ void partial_verify(const ScreenArgs<T>& a, const T* __restrict__ W, int cur,
+                                            int nloud, double lamd, double (&v)[kParts], int lane,
+                                            int swarp, int gwarps) {
+  const int p = a.p, P = a.P;
+  const ScreenWork<T>& w = a.w;
+  const T lam = (T)lamd;
+  const T lam_s = (T)(lamd * (1.0 - kScreenMargin));
+  const int nchunk = (p + 31) >> 5;
+  const int nxt = 1 - cur;
+  for (int item = swarp; item < nloud * nchunk; item += gwarps) {
+    const int i = ldi(w.loud + item / nchunk);
+    const int j = (item % nchunk) * 32 + lane;
+    bool pair = j < p && j != i;
+    if (pair && j < i && ldi(w.loudf + j) != 0) pair = false;
+    {  // candidates are not verified
+      const int b = ldi(w.off_r + i), ne = ldi(w.off_r + i + 1) - b;
+      for (int m = 0; m < ne; ++m) {
+        const int2 qp = __ldcg(w.cand[cur] + ldi(w.row_ent + b + m));
+        if ((qp.x == i ? qp.y : qp.x) == j) pair = false;
+      }
+    }
+    bool bad = false, next = false;
+    if (pair) {
+      const int c_step = pair_step(min(i, j), max(i, j), P);
+      T vij, wij, vji, wji;
+      row_at_visit(a, W, i, j, c_step, vij, wij);
+      row_at_visit(a, W, j, i, c_step, vji, wji);
+      bad = fabs(((T)0 - vij) - vji) - lam > (T)0;
+      next = fabs(((T)0 - wij) - wji) - lam_s > (T)0;
+      const double g = (double)wij + (double)wji;
+      v[kPartKkt] = fmax(v[kPartKkt], fmax(fabs(g) - lamd, 0.0));
+      if (!isfinite(g)) v[kPartBad] += 1.0;
+    }
+    const int lo = min(i, j), hi = max(i, j);
+    push_list(bad, lo, hi, w.fail, w.ctr + kCtrFail, w.fail_cap, lane);
+    push_cand(next, lo, hi, w.cand[nxt], w.ctr + kCtrCand + nxt, w.cnt_r[nxt], w.nc_cap, lane);
+  }
+}
+
 template <typename T>
 __device__ __noinline__ void verify_pass(const ScreenArgs<T>& a, const T* __restrict__ W,
                             const T* __restrict__ V, int nxt, double lamd, double (&v)[kParts],
@@ -496,10 +573,12 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
   __shared__ int s_tmp[32];
   __shared__ double s_res[kRes];
   __shared__ int s_stop;
-  __shared__ unsigned long long s_dmax;  // the CTA's largest row bound D_i of the sweep (bits)
+  __shared__ unsigned long long s_dmax;  // the CTA's largest rowacc + D_i of the sweep (bits)
+  __shared__ unsigned long long s_qmax;  // the same over the rows that stay quiet (bits)
   __shared__ int s_fill;                 // the CTA's largest pending fill the sweep would need
   __shared__ int s_fast;
   __shared__ double s_dsweep;
+  __shared__ int s_nloud;
   extern __shared__ __align__(128) unsigned char dyn[];
 
   unsigned gen = 0;
@@ -518,7 +597,12 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
   // kept from the previous sweep
   double acc = 0.0;
   bool reuse = false;
-  int n_lazy = 0;
+  // per-row form of the bound (w.rowacc): valid once every pair was screened
+  // by this launch; force_full: a partial sweep could not keep all of its
+  // new candidates, so the next sweep verifies everything
+  bool rows_valid = a.start_list < 0 || kkt0;
+  bool force_full = false;
+  int n_lazy = 0, n_partial = 0;
   // deferred row updates: some stored rows of Wa lag behind their pending
   // entries (after a deferring sweep, until a flush)
   bool have_pend = false;
@@ -537,6 +621,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
 #pragma unroll
     for (int k = 0; k < kParts; ++k) v[k] = 0.0;
     screen_pass<T, MIXED>(a, Wa, cur, kkt0, lamd, v, lane, gwarp, gwarps);
+    for (int i = gtid; i < p; i += gthreads) w.rowacc[i] = 0.0;
     if (kkt0) reduce_parts(v, a.partials, red);
     grid_barrier(a.barrier, gen, wc, ++where);
   }
@@ -548,14 +633,17 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
     for (int k = 0; k < kParts; ++k) v[k] = 0.0;
     bool fast = false;       // this sweep skipped the verification (lazy)
     int mode = kModeFull;    // and (kModeDefer) its row pass
+    int n_cur = 0;           // candidates of the sweep's list
     if (do_sweep) {
       int redo = 0;
       for (;;) {  // until the verification passes
         if (threadIdx.x == 0) {
           s_dmax = 0ull;
+          s_qmax = 0ull;
           s_fill = 0;
         }
         const int N = ldi(w.ctr + kCtrCand + cur);
+        n_cur = N;
         if (N > w.nc_cap || ld_relaxed_s32(wc.abort) != 0) {
           status = kStatusDense;
           break;
@@ -684,6 +772,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
           }
         }
         if (gtid < kJacMax) w.jac[gtid] = 0;
+        if (gtid == 0) w.ctr[kCtrLoud] = 0;
         if (gtid == 0) {
           w.ctr[kCtrJacBar] = 0;
           w.ctr[kCtrJacDone] = 0;
@@ -902,7 +991,19 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
               v[kPartBad] += 1.0;
             }
             const double di = dsum + dd64 * (double)__ldg(a.mrow + i);
-            atomicMax(&s_dmax, (unsigned long long)__double_as_longlong(di));
+            // the row's bound since its pairs were screened, and whether it
+            // leaves half the margin (its pairs then need a verification)
+            const double ai = rows_valid ? __ldcg(w.rowacc + i) + di : INFINITY;
+            const bool is_loud = !(ai <= 0.5 * (kScreenMargin - kLazySlack) * lamd);
+            w.rowa_new[i] = ai;
+            w.loudf[i] = is_loud ? 1 : 0;
+            if (is_loud) {
+              const int slot = atomicAdd(w.ctr + kCtrLoud, 1);
+              if (slot < kLoudMax) w.loud[slot] = i;
+            } else {
+              atomicMax(&s_qmax, (unsigned long long)__double_as_longlong(ai));
+            }
+            if (rows_valid) atomicMax(&s_dmax, (unsigned long long)__double_as_longlong(ai));
             int need = np + nchg;
             if (dd != (T)0) {
               if (need < kPendRow) {
@@ -918,6 +1019,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         __syncthreads();
         if (threadIdx.x == 0) {
           w.dpart[blockIdx.x] = __longlong_as_double((long long)s_dmax);
+          w.apart[blockIdx.x] = __longlong_as_double((long long)s_qmax);
           w.dfill[blockIdx.x] = s_fill;
         }
         // ---- commit the candidates' new values (both triangles)
@@ -933,29 +1035,45 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
           }
         }
         grid_barrier(a.barrier, gen, wc, ++where);
-        // ---- lazy verification: every CTA forms the same decision.  FULL:
-        //      row pass with V, verification, fresh screen.  LAZY (the bound
-        //      holds): row pass without V, no verification, the list stays.
-        //      DEFER (the bound holds and every row's pending entries fit):
-        //      no row pass either; the rows' changes and diagonal changes stay
-        //      pending on the stored W
+        // ---- lazy verification: every CTA forms the same decision.  A pair
+        //      outside the list has moved by at most rowacc_i + rowacc_j (+
+        //      this sweep's D_i + D_j) since it was screened.  LAZY (every
+        //      row within half the margin): row pass without V, no
+        //      verification, the list stays.  DEFER (the same, and every
+        //      row's pending entries fit): no row pass either; the rows'
+        //      changes and diagonal changes stay pending on the stored W.
+        //      PARTIAL (a few rows beyond half the margin, the entries fit):
+        //      as DEFER, and the pairs of those rows are verified and
+        //      screened (partial_verify).  FULL: row pass with V,
+        //      verification, fresh screen
         if (threadIdx.x == 0) {
-          double dm = 0.0;
+          double dm = 0.0, qm = 0.0;
           int fm = 0;
           for (int c = 0; c < (int)gridDim.x; ++c) {
             dm = fmax(dm, __ldcg(w.dpart + c));
+            qm = fmax(qm, __ldcg(w.apart + c));
             fm = max(fm, ldi(w.dfill + c));
           }
-          s_dsweep = dm;
-          const bool ok = a.lazy_verify && acc + 2.0 * dm <= (kScreenMargin - kLazySlack) * lamd;
-          s_fast = !ok ? kModeFull : (fm <= kPendRow ? kModeDefer : kModeLazy);
+          const int nl = ldi(w.ctr + kCtrLoud);
+          const bool may = a.lazy_verify && rows_valid && !force_full;
+          const bool all_quiet = may && nl == 0;
+          const bool partial = may && nl > 0 && nl <= kLoudMax && fm <= kPendRow;
+          s_fast = all_quiet ? (fm <= kPendRow ? kModeDefer : kModeLazy)
+                             : (partial ? kModePartial : kModeFull);
+          // largest rowacc after the sweep (verified rows restart from 0)
+          s_dsweep = partial ? qm : dm;
+          s_nloud = nl;
         }
         __syncthreads();
         mode = s_fast;
         fast = mode != kModeFull;
         const bool full = mode == kModeFull;
+        const bool deferred = mode == kModeDefer || mode == kModePartial;
         if (mode == kModeDefer) {
           for (int i = gtid; i < p; i += gthreads) w.pend_n[i] = ldi(w.pend_new + i);
+        } else if (mode == kModePartial) {
+          // pend_n still counts the old entries: the verification reads the
+          // rows at the visit; the counts advance once the sweep stands
         } else {
           if (have_pend) {  // the stored rows catch up before the row pass reads them
             flush_pending(a, Wa, lane, gwarp, gwarps);
@@ -1143,6 +1261,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         //      (FULL only: otherwise none of them can have reached the
         //      threshold, their KKT terms are zero, and the list stays)
         if (full) verify_pass<T>(a, Wn, a.V, 1 - cur, lamd, v, lane, gwarp, gwarps);
+        if (mode == kModePartial) partial_verify<T>(a, Wa, cur, s_nloud, lamd, v, lane, swarp, gwarps);
         // the candidates' own terms (and their screen: every nonzero stays a
         // candidate); warp-uniform trip count for the list pushes.  Their W
         // after the sweep: the row pass's rows, or (DEFER) the stored rows
@@ -1158,7 +1277,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
             const T d = __ldcg(w.nd_delta + k);
             const T omk = d != (T)0 ? __ldcg(w.nd_new + k) : __ldcg(w.nd_rec + 4 * (size_t)k + 2);
             T w1, w2;
-            if (mode == kModeDefer) {
+            if (deferred) {
               w1 = pend_fold(a, i, ldi(w.pend_new + i), j, __ldcg(Wa + (size_t)i * ld + j));
               w2 = pend_fold(a, j, ldi(w.pend_new + j), i, __ldcg(Wa + (size_t)j * ld + i));
             } else {
@@ -1217,6 +1336,33 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         break;
       }
       reduce_parts(v, a.partials, red);
+      // the per-row bounds after the sweep: 0 after a full verification,
+      // and for the rows a partial one verified; else grown by D_i
+      for (int i = gtid; i < p; i += gthreads)
+        w.rowacc[i] = (mode == kModeFull || (mode == kModePartial && ldi(w.loudf + i) != 0))
+                          ? 0.0
+                          : __ldcg(w.rowa_new + i);
+      bool grew = false;
+      if (mode == kModePartial) {
+        // the sweep stands: its pending entries count, and the pairs it
+        // screened join the kept list (a list that cannot take them all
+        // makes the next sweep a full one)
+        for (int i = gtid; i < p; i += gthreads) w.pend_n[i] = ldi(w.pend_new + i);
+        const int pushed = ldi(w.ctr + kCtrCand + 1 - cur);
+        const int add = min(min(pushed, w.nc_cap), w.nc_cap - n_cur);
+        for (int f = gtid; f < add; f += gthreads) {
+          const int2 pr = __ldcg(w.cand[1 - cur] + f);
+          w.cand[cur][n_cur + f] = pr;
+          atomicAdd(w.cnt_r[cur] + pr.x, 1);
+          atomicAdd(w.cnt_r[cur] + pr.y, 1);
+        }
+        if (gtid == 0) w.ctr[kCtrCand + cur] = n_cur + add;
+        grew = pushed > 0;
+        force_full = add < pushed;
+      } else {
+        force_full = false;
+      }
+      if (mode == kModeFull) rows_valid = true;
       // row offsets of the next sweep's list (its pushes are complete); a
       // lazy sweep keeps its list, offsets and build
       if (blockIdx.x == 0 && !fast) {
@@ -1225,11 +1371,12 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
       }
       if (blockIdx.x == 0 && fast)  // fresh cursors for a later build of the kept list
         for (int k = threadIdx.x; k <= p; k += blockDim.x) w.cur_r[k] = ldi(w.off_r + k);
-      need_scan = false;
-      acc = fast ? acc + 2.0 * s_dsweep : 0.0;
-      reuse = fast;
+      need_scan = grew;  // a grown list is counted again by the next build
+      acc = fast ? 2.0 * s_dsweep : 0.0;
+      reuse = fast && !grew;
       n_lazy += fast ? 1 : 0;
-      if (mode == kModeDefer) have_pend = true;
+      n_partial += mode == kModePartial ? 1 : 0;
+      if (mode == kModeDefer || mode == kModePartial) have_pend = true;
       grid_barrier(a.barrier, gen, wc, ++where);
     }
 
@@ -1286,6 +1433,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
       s_res[kResPath] = pk;
       s_res[kResLazy] = n_lazy;
       s_res[kResAcc] = acc;  // the lazy bound accumulated on the next sweep's list
+      s_res[kResPartial] = n_partial;
       s_res[kResList] = (do_sweep && !aborted && !nonfinite && !dense_next)
                             ? (double)(fast ? cur : 1 - cur)
                             : -1.0;
@@ -1319,7 +1467,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
     if (kkt0) break;
     // the accepted sweep's W becomes current (a deferring sweep left its
     // updates pending on the stored rows)
-    if (mode != kModeDefer) {
+    if (mode != kModeDefer && mode != kModePartial) {
       T* tmp = Wa;
       Wa = Wn;
       Wn = tmp;
@@ -1372,6 +1520,9 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         for (int k = 0; k < kParts; ++k) vz[k] = 0.0;
         screen_pass<T, MIXED>(a, Wa, cur, false, lamd, vz, lane, gwarp, gwarps);
       }
+      for (int i = gtid; i < p; i += gthreads) w.rowacc[i] = 0.0;
+      rows_valid = true;
+      force_full = false;
       need_scan = true;
       acc = 0.0;  // a fresh screen of the current iterate
       reuse = false;

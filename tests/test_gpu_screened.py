@@ -213,5 +213,8 @@ def test_lazy_verification_benchmark_solve(precision):
     assert np.array_equal(Ga, Gb)
     assert np.array_equal(Ha[:, [0, 1, 3]], Hb[:, [0, 1, 3]])
     assert ra.lazy_sweeps >= 3 and rb.lazy_sweeps == 0
+    # the fourth FP32 sweep's bound fails on a few dozen rows only: their
+    # pairs are verified alone (a partial sweep), with the same iterates
+    assert ra.partial_sweeps >= 1 and rb.partial_sweeps == 0
     # the polish launch starts from the list the FP32 launch kept: still screened
     assert ra.dense_sweeps == 0 and rb.dense_sweeps == 0
