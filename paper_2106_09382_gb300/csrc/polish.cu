@@ -174,13 +174,27 @@ __device__ __forceinline__ void row_sums(const PolishArgs& a, int r, int c, int 
   const double src = __ldg(a.S + (size_t)r * ld + c);
   double vis = __ldcg(w.diag + r) * src, end = __ldcg(w.diag_new + r) * src;
   const int b = ldi(w.off + r), n = ldi(w.off + r + 1) - b;
-  for (int m = 0; m < n; ++m) {
-    const int q = ldi(w.ent + b + m);
-    const int2 pr = __ldg(a.cand + q);
-    const double s = __ldg(a.S + (size_t)other_end(pr, r) * ld + c);
-    const double nv = __ldcg(w.nw + q);
-    vis = ::fma(pair_step(pr.x, pr.y, P) < c_step ? nv : __ldcg(w.om + q), s, vis);
-    end = ::fma(nv, s, end);
+  for (int m0 = 0; m0 < n; m0 += 8) {  // loads in batches, then the FMAs in order
+    int q[8];
+    int2 pr[8];
+    double s[8], nv[8], ov[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) q[k] = m0 + k < n ? ldi(w.ent + b + m0 + k) : -1;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      pr[k] = q[k] >= 0 ? __ldg(a.cand + q[k]) : make_int2(0, 0);
+      nv[k] = q[k] >= 0 ? __ldcg(w.nw + q[k]) : 0.0;
+      ov[k] = q[k] >= 0 ? __ldcg(w.om + q[k]) : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      s[k] = q[k] >= 0 ? __ldg(a.S + (size_t)other_end(pr[k], r) * ld + c) : 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (q[k] < 0) break;
+      vis = ::fma(pair_step(pr[k].x, pr[k].y, P) < c_step ? nv[k] : ov[k], s[k], vis);
+      end = ::fma(nv[k], s[k], end);
+    }
   }
   at_visit = vis;
   after = end;
@@ -198,10 +212,15 @@ __device__ __noinline__ void verify_loud(const PolishArgs& a, int nloud, double 
     const int j = (item % nchunk) * 32 + lane;
     bool pair = j < p && j != i;
     if (pair && j < i && ldi(w.loudf + j) != 0) pair = false;
-    {  // candidates are not verified
+    {  // candidates are not verified: the row's partners, 32 at a time
       const int b = ldi(w.off + i), n = ldi(w.off + i + 1) - b;
-      for (int m = 0; m < n && pair; ++m)
-        if (other_end(__ldg(a.cand + ldi(w.ent + b + m)), i) == j) pair = false;
+      for (int m0 = 0; m0 < n; m0 += 32) {
+        const int mine =
+            m0 + lane < n ? other_end(__ldg(a.cand + ldi(w.ent + b + m0 + lane)), i) : -1;
+        const int nm = min(32, n - m0);
+        for (int m = 0; m < nm; ++m)
+          if (__shfl_sync(FULL, mine, m) == j) pair = false;
+      }
     }
     if (!pair) continue;
     const int c_step = pair_step(min(i, j), max(i, j), P);

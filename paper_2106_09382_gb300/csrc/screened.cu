@@ -418,15 +418,27 @@ __device__ __forceinline__ void row_at_visit(const ScreenArgs<T>& a, const T* __
   T acc = pend_fold(a, r, npo, c, __ldcg(W + (size_t)r * ld + c));
   T vis = acc;
   bool cap = false;
-  for (int m = npo; m < npn; ++m) {
-    const int u = ldi(pu + m);
-    // the diagonal change (u == r) follows every colour step
-    const int cm = u == r ? 0x7fffffff : pair_step(min(r, u), max(r, u), P);
-    if (!cap && cm > c_step) {
-      vis = acc;
-      cap = true;
+  for (int m0 = npo; m0 < npn; m0 += 8) {  // loads in batches, then the FMAs in order
+    int u[8];
+    T d[8], sv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      u[q] = m0 + q < npn ? ldi(pu + m0 + q) : -1;
+      d[q] = m0 + q < npn ? __ldcg(pd + m0 + q) : (T)0;
     }
-    acc = fma_t(__ldcg(pd + m), __ldg(a.S + (size_t)u * ld + c), acc);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sv[q] = u[q] >= 0 ? __ldg(a.S + (size_t)u[q] * ld + c) : (T)0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (u[q] < 0) break;
+      // the diagonal change (u == r) follows every colour step
+      const int cm = u[q] == r ? 0x7fffffff : pair_step(min(r, u[q]), max(r, u[q]), P);
+      if (!cap && cm > c_step) {
+        vis = acc;
+        cap = true;
+      }
+      acc = fma_t(d[q], sv[q], acc);
+    }
   }
   at_visit = cap ? vis : acc;
   after = acc;
@@ -447,11 +459,17 @@ __device__ __noinline__ void partial_verify(const ScreenArgs<T>& a, const T* __r
     const int j = (item % nchunk) * 32 + lane;
     bool pair = j < p && j != i;
     if (pair && j < i && ldi(w.loudf + j) != 0) pair = false;
-    {  // candidates are not verified
+    {  // candidates are not verified: the row's partners, 32 at a time
       const int b = ldi(w.off_r + i), ne = ldi(w.off_r + i + 1) - b;
-      for (int m = 0; m < ne; ++m) {
-        const int2 qp = __ldcg(w.cand[cur] + ldi(w.row_ent + b + m));
-        if ((qp.x == i ? qp.y : qp.x) == j) pair = false;
+      for (int m0 = 0; m0 < ne; m0 += 32) {
+        int mine = -1;
+        if (m0 + lane < ne) {
+          const int2 qp = __ldcg(w.cand[cur] + ldi(w.row_ent + b + m0 + lane));
+          mine = qp.x == i ? qp.y : qp.x;
+        }
+        const int nm = min(32, ne - m0);
+        for (int m = 0; m < nm; ++m)
+          if (__shfl_sync(FULL, mine, m) == j) pair = false;
       }
     }
     bool bad = false, next = false;
