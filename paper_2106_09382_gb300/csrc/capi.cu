@@ -70,6 +70,11 @@ struct concord_state {
   double *S64 = nullptr, *W64 = nullptr, *Om64 = nullptr;
   bool om64_current = false;  // mixed: FP64 copies hold the latest iterate
   int start_list = -1;        // one-shot: the next screened launch starts from this list
+  bool start_scan = false;    // one-shot, with start_list: the list's row offsets still to scan
+  // a start screen made with the one-pass start (list 0, for prescreen_lambda):
+  // the next mixed run at that lambda starts from it
+  bool prescreen = false;
+  double prescreen_lambda = 0.0;
   unsigned long long* mbox = nullptr;
   int depth = kMailboxDepth;
   unsigned* barrier = nullptr;
@@ -393,7 +398,7 @@ ScreenLayout screen_layout(int p, int P, int nc, int tc) {
   L.nd_delta = take(sizeof(double) * (size_t)nc);
   L.nd_new = take(sizeof(double) * (size_t)nc);
   L.nd_d2 = take(sizeof(double) * (size_t)nc);
-  L.jac = take(sizeof(int) * kJacMax);
+  L.jac = take(sizeof(unsigned long long) * kJacMax);
   L.diag_old = take(sizeof(double) * (size_t)p);
 
   L.omdiag_old = take(sizeof(double) * (size_t)p);
@@ -473,7 +478,7 @@ ScreenWork<T> screen_work(concord_state* st) {
   w.nd_delta = (T*)(b + L.nd_delta);
   w.nd_new = (T*)(b + L.nd_new);
   w.nd_d2 = (T*)(b + L.nd_d2);
-  w.jac = (int*)(b + L.jac);
+  w.jac = (unsigned long long*)(b + L.jac);
   w.diag_old = (T*)(b + L.diag_old);
 
   w.omdiag_old = (double*)(b + L.omdiag_old);
@@ -519,7 +524,9 @@ int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, d
   const ScreenLayout L = screen_layout(st->p, st->P, st->nc_cap, st->term_cap);
   // a list left by the previous launch (one-shot), else screen from scratch
   const int start_list = (!kkt_only && n_sweeps > 0 && !path) ? st->start_list : -1;
+  const int start_scan = start_list >= 0 && st->start_scan ? 1 : 0;
   st->start_list = -1;
+  st->start_scan = false;
   CK(cudaMemsetAsync(st->barrier, 0, sizeof(unsigned), st->stream));
   CK(cudaMemsetAsync(st->abort_info, 0, 3 * sizeof(int), st->stream));
   CK(cudaMemsetAsync((char*)st->scr + L.pend_n, 0, sizeof(int) * (size_t)st->p, st->stream));
@@ -559,6 +566,7 @@ int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, d
   a.stall_stop = stall_stop;
   a.max_redo = 8;
   a.start_list = start_list;
+  a.start_scan = start_scan;
   a.mrow = st->mrow;
   a.lazy_verify = st->lazy_verify ? 1 : 0;
   a.keep_w = st->screen_keep_w ? 1 : 0;
@@ -931,7 +939,7 @@ int ensure_polish(concord_state* st, int term_cap) {
   const size_t p = (size_t)st->p, nc = (size_t)st->nc_cap, tc = (size_t)term_cap;
   const size_t grid = (size_t)(st->max_grid > 0 ? st->max_grid : st->sms);
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-  const size_t ints = al(sizeof(int) * kPolCtrs) + 3 * al(sizeof(int) * (p + 1)) +
+  const size_t ints = al(sizeof(int) * kPolCtrs) + al(8 * 3) + 3 * al(sizeof(int) * (p + 1)) +
                       al(sizeof(int) * p) + 3 * al(sizeof(int) * 2 * nc) + al(sizeof(int) * tc);
   const size_t dbls = al(8 * tc) + 5 * al(8 * nc) + al(8 * 2 * nc) + 4 * al(8 * p) + al(8 * grid) +
                       al(sizeof(int) * kPolLoudMax) + al(sizeof(int) * p);
@@ -944,6 +952,7 @@ int ensure_polish(concord_state* st, int term_cap) {
   size_t o = 0;
   auto take = [&](size_t b) { char* r = m + o; o += al(b); return (void*)r; };
   w.ctr = (int*)take(sizeof(int) * kPolCtrs);
+  w.rslot = (unsigned long long*)take(8 * 3);
   w.deg = (int*)take(sizeof(int) * (p + 1));
   w.off = (int*)take(sizeof(int) * (p + 1));
   w.toff = (int*)take(sizeof(int) * (p + 1));
@@ -985,6 +994,7 @@ int polish_sparse(concord_state* st, double lambda, double tol, int stop_rule, i
     if (rc != CONCORD_OK) return rc;
     const PolishWork& w = st->pol.w;
     CK(cudaMemsetAsync(w.ctr, 0, sizeof(int) * kPolCtrs, st->stream));
+    CK(cudaMemsetAsync(w.rslot, 0, 8 * 3, st->stream));
     CK(cudaMemsetAsync(w.deg, 0, sizeof(int) * (size_t)(st->p + 1), st->stream));
     CK(cudaMemsetAsync(st->barrier, 0, sizeof(unsigned), st->stream));
     CK(cudaMemsetAsync(st->abort_info, 0, 3 * sizeof(int), st->stream));
@@ -1127,6 +1137,9 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
     return fail(CONCORD_E_ARG, "lambda >= 0, max_sweeps >= 0, stop_rule in {0,1} required");
   if (!exact && !(tol > 0.0)) return fail(CONCORD_E_ARG, "tol must be > 0");
   const double run_tol = exact ? -1.0 : tol;
+  // a start screen of this state's current S and starting point (one-shot)
+  const bool pre = st->prescreen && st->prescreen_lambda == lambda;
+  st->prescreen = false;
   st->hist_rows = 0;
   st->n_launch = 0;
   CK(cudaEventRecord(st->ev0, st->stream));
@@ -1150,6 +1163,13 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
   if (!exact && tol1 < tol) tol1 = tol;
   // the FP32 working set follows the FP64 copies lazily (after a polish)
   if (st->om64_current && (rc = demote_from_fp64(st)) != CONCORD_OK) return rc;
+  // the one-pass start screened the starting point for this lambda: the
+  // FP32 launch starts from that list (its first build scans the counts)
+  const int sv0 = st->sweep_variant;
+  if (pre && st->fault_vertex < 0 && (sv0 == CONCORD_SWEEP_AUTO || sv0 == CONCORD_SWEEP_SCREENED)) {
+    st->start_list = 0;
+    st->start_scan = true;
+  }
   // the polish rebuilds W in FP64 from Omega: the FP32 launch need not bring
   // W up to date at its end (deferred updates of lazy sweeps may be dropped)
   st->screen_keep_w = exact != 0;
@@ -1157,6 +1177,8 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
                          (const float*)st->sdiagT, st->omdiag64, lambda, tol1, stop_rule,
                          max_sweeps, 0, 0, exact ? 0 : 1, &o1);
   st->screen_keep_w = true;
+  st->start_list = -1;  // one-shot, also when the sweeps did not take it
+  st->start_scan = false;
   st->om64_current = false;
   st->hist_rows = o1.sweeps;
   if (rc != CONCORD_OK || exact) {
@@ -1219,6 +1241,7 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
 // bookkeeping: diagonals, Omega = I, W = S.
 int reset_iterate(concord_state* st) {
   const int p = st->p, ld = st->ld;
+  st->prescreen = false;
   CK(cudaMemsetAsync(st->flag, 0, sizeof(int), st->stream));
   CK(launch_extract_diag(st->S64, 0, ld, p, st->sdiag64, is_mixed(st) ? st->sdiagT : nullptr, 1,
                          st->flag, st->stream));
@@ -1514,6 +1537,7 @@ int concord_set_omega(concord_state* st, const void* Om_dev, int dtype, int ld_i
   if (!Om_dev || (dtype != CONCORD_F64 && dtype != CONCORD_F32) || ld_in < st->p)
     return fail(CONCORD_E_ARG, "Omega0 non-NULL, dtype F64/F32, ld >= p required");
   const int p = st->p, ld = st->ld, f32 = dtype == CONCORD_F32;
+  st->prescreen = false;
   CK(cudaMemsetAsync(st->flag, 0, sizeof(int), st->stream));
   CK(launch_check_symmetric(Om_dev, f32, p, ld_in, st->flag, st->stream));
   CK(launch_extract_diag(Om_dev, f32, ld_in, p, nullptr, nullptr, 0, st->flag, st->stream));
@@ -1598,7 +1622,8 @@ int concord_run(concord_state* st, double lambda, double tol, int max_sweeps, in
   return run_impl(st, lambda, tol, max_sweeps, stop_rule, switch_tol, 0, res);
 }
 
-static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, int ldx, int prep);
+static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, int ldx, int prep,
+                           double screen_lambda = 0.0);
 
 int concord_path(concord_state* st, const double* lambdas, int n_lambda, double tol,
                  int max_sweeps, concord_result* results, void* omega_out_dev, int ld_out) {
@@ -1865,7 +1890,9 @@ int concord_set_gram_mode(concord_state* st, int mode) {
 }
 
 // X (device) -> S in the state, per the state's Gram mode.
-static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, int ldx, int prep) {
+static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, int ldx, int prep,
+                           double screen_lambda) {
+  st->prescreen = false;
   const int p = st->p, ld = st->ld;
   CK(cudaMemsetAsync(st->flag, 0, sizeof(int), st->stream));
   // the FP64 W (free until the iterate is reset below) holds the column partials
@@ -1932,6 +1959,7 @@ static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, i
   // mixed state from an FP32 S: the FP64 copy and the starting iterate in
   // one pass over S (checks in bits 8 and 16 of the same flag, one read)
   const bool fused = is_mixed(st) && st->gram_mode != CONCORD_GRAM_FP64;
+  bool screened_start = false;
   if (fused) {
     ResetMixedArgs ra;
     ra.S = (const float*)st->S;
@@ -1950,6 +1978,27 @@ static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, i
     ra.sd2_64 = st->sd2_64;
     ra.omdiag64 = st->omdiag64;
     ra.bad = st->flag;
+    ra.lam_s = 0.f;
+    // the start screen of the coming solve (the screened kernel's own
+    // predicate on W = S, Omega = I), when its lambda is known and the solve
+    // will take the screened kernel
+    const int sv = st->sweep_variant;
+    if (screen_lambda > 0.0 && st->fault_vertex < 0 &&
+        (sv == CONCORD_SWEEP_AUTO || sv == CONCORD_SWEEP_SCREENED)) {
+      int rc2 = ensure_screen(st);
+      if (rc2 != CONCORD_OK) return rc2;
+      const ScreenLayout L = screen_layout(p, st->P, st->nc_cap, st->term_cap);
+      CK(cudaMemsetAsync((char*)st->scr + L.ctr, 0, sizeof(int) * kCtrs, st->stream));
+      CK(cudaMemsetAsync((char*)st->scr + L.cnt_r0, 0, sizeof(int) * (size_t)(p + 1), st->stream));
+      CK(cudaMemsetAsync((char*)st->scr + L.cnt_r1, 0, sizeof(int) * (size_t)(p + 1), st->stream));
+      const ScreenWork<float> sw = screen_work<float>(st);
+      ra.lam_s = (float)(screen_lambda * (1.0 - kScreenMargin));
+      ra.cand = sw.cand[0];
+      ra.n_cand = sw.ctr + kCtrCand;
+      ra.cnt_r = sw.cnt_r[0];
+      ra.nc_cap = st->nc_cap;
+      screened_start = true;
+    }
     CK(launch_reset_mixed(ra, st->stream));
   }
   int bad = 0, rc;
@@ -1961,6 +2010,10 @@ static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, i
   if (bad & 8) return fail(CONCORD_E_NONFINITE, "S has a non-finite diagonal entry");
   if (bad & 16) return fail(CONCORD_E_NONPOS_DIAG, "S has a diagonal entry <= 0 (constant column?)");
   st->om64_current = false;
+  if (screened_start) {
+    st->prescreen = true;
+    st->prescreen_lambda = screen_lambda;
+  }
   return CONCORD_OK;
 }
 
@@ -2078,7 +2131,7 @@ int concord_solve_device(concord_state* st, const void* X_dev, int x_dtype, int 
   cudaEvent_t e0;
   CK(cudaEventCreate(&e0));
   CK(cudaEventRecord(e0, st->stream));
-  rc = gram_into_state(st, X_dev, x_dtype == CONCORD_F32, n, ldx, prep);
+  rc = gram_into_state(st, X_dev, x_dtype == CONCORD_F32, n, ldx, prep, lambda);
   if (rc == CONCORD_OK) {
     concord_result r;
     rc = run_impl(st, lambda, tol, max_sweeps, stop_rule, 0.0, 0, &r);

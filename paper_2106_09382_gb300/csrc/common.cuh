@@ -178,6 +178,45 @@ __device__ __forceinline__ void group_barrier(unsigned* counter, unsigned& gen, 
   __syncthreads();
 }
 
+// One round of a group of `count` CTAs that also agree on whether any of
+// them set a flag: every CTA adds 1 (+ 2^32 when its flag is set) to the
+// round's own 64-bit slot (zeroed before the round) with a release add and
+// waits, with acquire loads, until all `count` have arrived -- the arrival
+// count and the flags travel together, so the round costs one atomic and
+// one wait.  Every CTA reads the same complete sum.  A wait that runs out
+// (or an abort) records -1 - who and `where` and reports the flag as set.
+__device__ __forceinline__ bool round_barrier_any(unsigned long long* slot, unsigned count,
+                                                  bool flag, const WaitCtl& w, int where,
+                                                  int who) {
+  __shared__ int s_any;
+  const bool f = __syncthreads_or(flag) != 0;
+  if (threadIdx.x == 0) {
+    const unsigned long long add = 1ull + (f ? (1ull << 32) : 0ull);
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(slot), "l"(add) : "memory");
+    const uint64_t t0 = globaltimer_ns();
+    unsigned it = 0;
+    int any = 1;
+    for (;;) {
+      unsigned long long v;
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(slot) : "memory");
+      if ((unsigned)(v & 0xffffffffull) >= count) {
+        any = (v >> 32) != 0ull ? 1 : 0;
+        break;
+      }
+      if ((++it & 15u) == 0) {
+        if (ld_relaxed_s32(w.abort) != 0) break;
+        if (globaltimer_ns() - t0 > w.timeout_ns) {
+          record_timeout(w, -1 - who, where);
+          break;
+        }
+      }
+    }
+    s_any = any;
+  }
+  __syncthreads();
+  return s_any != 0;
+}
+
 // The whole grid (every CTA of a cooperative launch) as one group.
 __device__ __forceinline__ void grid_barrier(unsigned* counter, unsigned& gen,
                                              const WaitCtl& w, int where) {

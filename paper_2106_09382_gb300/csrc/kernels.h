@@ -131,7 +131,6 @@ constexpr int kRowList = 64;      // changes of one row staged per warp in the r
 constexpr int kCtrCand = 0;       // ctr[0], ctr[1]: lengths of the two candidate lists
 constexpr int kCtrFail = 2;       // failing pairs found by the verification
 constexpr int kCtrTerms = 3;      // correction terms of the current candidate set
-constexpr int kCtrJacBar = 4;     // barrier counter of the fixed-point iteration
 constexpr int kCtrJacDone = 5;    // the fixed-point iteration settled
 constexpr int kCtrTermsPred = 6;  // correction terms the current list needs (sum over rows of k (k - 1) / 2)
 constexpr int kCtrLoud = 7;       // rows whose lazy bound left half the margin this sweep
@@ -157,7 +156,7 @@ struct ScreenWork {
   T* nd_rec;                // [4 nc_cap] per candidate: W_ij, W_ji, w_ij at the sweep start, s_ii + s_jj
   T *nd_delta, *nd_new;     // change and new value of each candidate
   T* nd_d2;                 // [nc_cap] second buffer of the fixed-point iteration
-  int* jac;                 // [kJacMax] candidates whose change moved, per iteration
+  unsigned long long* jac;  // [kJacMax] per fixed-point round: arrivals + (CTAs whose changes moved) << 32
   T* diag_old;              // [p] diagonal before the sweep (for a redo)
   double* omdiag_old;       // [p] FP64 diagonal before the sweep (mixed precision)
   double* diag_new;         // [p] the sweep's new FP64 diagonal, committed after the row pass
@@ -206,6 +205,8 @@ struct ScreenArgs {
   int start_list;           // >= 0: the first sweep uses candidate list start_list as the
                             // previous launch left it (counts, row offsets, term count);
                             // -1: screen the starting point
+  int start_scan;           // with start_list: only its counts are in place (a list
+                            // screened outside the kernel); the first build scans them
   // lambda path (path_n > 0): lambdas path_lambda[path_start .. path_n), each
   // swept until its stopping rule, warm-started from the previous one
   const double* path_lambda;
@@ -287,6 +288,14 @@ struct ResetMixedArgs {
   double *sd1_64, *sd2_64;
   double* omdiag64;
   int* bad;
+  // optional screen of the starting point (Omega = I, W = S) for one lambda:
+  // pairs i < j with |(0 - s_ij) - s_ji| > lam_s join cand, as the screened
+  // kernel's own start screen would push them (lam_s <= 0: no screen)
+  float lam_s;
+  int2* cand;
+  int* n_cand;
+  int* cnt_r;
+  int nc_cap;
 };
 cudaError_t launch_reset_mixed(const ResetMixedArgs& a, cudaStream_t st);
 // bad |= 1 if |A - A^T| != 0 anywhere or a non-finite entry is met.
@@ -382,9 +391,7 @@ constexpr int kStatusNeedW = 6;       // result status: the bound failed; W must
 constexpr int kStatusCapacity = 7;    // result status: the terms did not fit (ctr holds the need)
 constexpr int kPolishThreads = 512;
 constexpr int kPolishMaxRounds = 1024;  // fixed-point rounds per sweep before giving up
-constexpr int kPolChg = 0;            // ctr[0..2]: changed flags of the chain's rounds
 constexpr int kPolOverflow = 3;       // ctr: terms needed when they do not fit (0: fit)
-constexpr int kPolRowMax = 4;         // ctr[4..5]: max_i sum_u |omega_iu| (double bits)
 constexpr int kPolSMax = 6;           // ctr[6..7]: max |s_ux| (double bits)
 constexpr int kPolLoud = 8;           // ctr: rows whose bound leaves half the margin this sweep
 constexpr int kPolFail = 9;           // ctr: a verified pair would have left zero
@@ -392,6 +399,7 @@ constexpr int kPolCtrs = 10;
 constexpr int kPolLoudMax = 256;      // rows one polish sweep verifies (more: W is rebuilt)
 struct PolishWork {
   int* ctr;          // [kPolCtrs] (zeroed before the launch)
+  unsigned long long* rslot;  // [3] the fixed-point rounds' arrivals and flags, in turn (zeroed)
   int* deg;          // [p + 1] entries per row (zeroed before the launch)
   int* off;          // [p + 1] row offsets of the entries
   int* toff;         // [p + 1] row offsets of the terms (deg (deg - 1) per row)

@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
         c_sj[m] = m < c_pj ? __ldcg(w.term_s + c_tj + m) : 0.0;
       }
       for (int rnd = 0; rnd < kPolishMaxRounds; ++rnd, ++gr) {
-        if (gtid == 0) w.ctr[kPolChg + (gr + 1) % 3] = 0;  // read two barriers ago
+        if (gtid == 0) w.rslot[(gr + 1) % 3] = 0ull;  // waited on two rounds ago
         bool chg = false;
         if (k0 < N) {
           double x1[kQ], x2[kQ];
@@ -473,9 +473,8 @@ __global__ void __launch_bounds__(kPolishThreads, 1) k_polish(const PolishArgs a
           dn[k] = d;
           w.nw[k] = nv;
         }
-        if (__syncthreads_or(chg) && threadIdx.x == 0) atomicOr(w.ctr + kPolChg + gr % 3, 1);
-        grid_barrier(a.barrier, gen, wc, ++where);
-        const bool moved = ldi(w.ctr + kPolChg + gr % 3) != 0;
+        const bool moved = round_barrier_any(w.rslot + gr % 3, gridDim.x, chg, wc, ++where,
+                                             (int)blockIdx.x);
         double* tmp = dc;
         dc = dn;
         dn = tmp;

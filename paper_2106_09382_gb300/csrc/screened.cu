@@ -153,31 +153,6 @@ __device__ void cta_count_terms(F f, int n, int* out) {
 }
 
 
-// Barrier among the CTAs that increment `counter` (zeroed before first use):
-// returns when it reaches `target` (participants x rounds so far) or the
-// abort word is set; a wait that runs out records a timeout.
-__device__ __forceinline__ void sub_barrier(unsigned* counter, unsigned target, const WaitCtl& w,
-                                            int where) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    // the release add publishes the CTA's writes (ordered before it by the
-    // CTA barrier); the acquire load that sees the last arrival makes every
-    // other CTA's writes visible to the CTA after its closing barrier
-    red_release_add_u32(counter, 1u);
-    const uint64_t t0 = globaltimer_ns();
-    unsigned it = 0;
-    while (ld_acquire_u32(counter) < target) {
-      if ((++it & 15u) == 0) {
-        if (ld_relaxed_s32(w.abort) != 0) break;
-        if (globaltimer_ns() - t0 > w.timeout_ns) {
-          record_timeout(w, -1 - (int)blockIdx.x, where);
-          break;
-        }
-      }
-    }
-  }
-  __syncthreads();
-}
 
 
 
@@ -632,7 +607,7 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
   //                  keeps the iterates exact whatever the list)
   if (a.start_list >= 0 && !kkt0) {
     cur = a.start_list;
-    need_scan = false;  // its row offsets and term count are in place
+    need_scan = a.start_scan != 0;  // else its row offsets and term count are in place
     acc = INFINITY;     // screened by another launch: the first sweep verifies
   } else {
     double v[kParts];
@@ -792,7 +767,6 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         if (gtid < kJacMax) w.jac[gtid] = 0;
         if (gtid == 0) w.ctr[kCtrLoud] = 0;
         if (gtid == 0) {
-          w.ctr[kCtrJacBar] = 0;
           w.ctr[kCtrJacDone] = 0;
         }
         grid_barrier(a.barrier, gen, wc, ++where);
@@ -907,13 +881,12 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
               dnext[k] = delta;
               w.nd_new[k] = nw;
             }
-            if (__syncthreads_or(changed) && threadIdx.x == 0) atomicAdd(w.jac + r, 1);
-            sub_barrier((unsigned*)(w.ctr + kCtrJacBar), (unsigned)(r + 1) * jac_ctas, wc,
-                        ++where);
+            const bool moved = round_barrier_any(w.jac + r, (unsigned)jac_ctas, changed, wc,
+                                                 ++where, (int)blockIdx.x);
             const T* tmp = dcur;
             dcur = dnext;
             dnext = const_cast<T*>(tmp);
-            if (ldi(w.jac + r) == 0) {
+            if (!moved) {
               // the solution sits in dcur; keep it in nd_delta
               if (dcur != w.nd_delta)
                 for (int k = gtid; k < N; k += jac_ctas * (int)blockDim.x)

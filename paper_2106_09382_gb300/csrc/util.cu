@@ -279,6 +279,32 @@ __global__ void __launch_bounds__(256) k_reset_mixed(const ResetMixedArgs a) {
     float4* orow = reinterpret_cast<float4*>(a.Om + (size_t)u * a.ld);
     double2* drow = reinterpret_cast<double2*>(a.S64 + (size_t)u * a.ld);
     float mx = 0.f;
+    if (a.lam_s > 0.f) {  // the starting point's screen, upper triangle
+      for (int q0 = 0; q0 < nv; q0 += 32) {  // warp-uniform trips for the pushes
+        const int q = q0 + lane;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q < nv) v = __ldg(srow + q);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int x = 4 * q + e;
+          const float s = (&v.x)[e];
+          const bool pred = q < nv && x > u && x < a.p && fabsf((0.f - s) - s) - a.lam_s > 0.f;
+          const unsigned m = __ballot_sync(0xffffffffu, pred);
+          if (!m) continue;
+          int base = 0;
+          if (lane == __ffs(m) - 1) base = atomicAdd(a.n_cand, __popc(m));
+          base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+          if (pred) {
+            const int r = base + __popc(m & ((1u << lane) - 1u));
+            if (r < a.nc_cap) {  // a longer list is seen by its count
+              a.cand[r] = make_int2(u, x);
+              atomicAdd(a.cnt_r + u, 1);
+              atomicAdd(a.cnt_r + x, 1);
+            }
+          }
+        }
+      }
+    }
     for (int q = lane; q < nv; q += 32) {
       const float4 v = __ldg(srow + q);
       wrow[q] = v;

@@ -218,3 +218,26 @@ def test_lazy_verification_benchmark_solve(precision):
     assert ra.partial_sweeps >= 1 and rb.partial_sweeps == 0
     # the polish launch starts from the list the FP32 launch kept: still screened
     assert ra.dense_sweeps == 0 and rb.dense_sweeps == 0
+
+
+def test_start_screen_of_the_one_pass_start():
+    """solve_device screens the starting point inside the one-pass start
+    (k_reset_mixed, for the solve's lambda) instead of the screened kernel's
+    own start screen: the FP32 sweeps are the same either way (history bit
+    for bit, objective to its summation order)."""
+    w = synth.workload_ar1(p=1000, n=800, seed=3)
+    X = dev(w["X"])
+    with C.State(1000, C.MIXED, n_cap=800) as st:
+        st.set_gram_mode(C.GRAM_TF32X3)
+        ra = st.solve_device(X, w["lam"], tol=1e-5, max_sweeps=200)
+        Ha = st.history()
+    S32 = C.concord_gram(X, C.PREP_STANDARDIZE, C.GRAM_TF32X3)
+    with C.State(1000, C.MIXED) as st:
+        st.set_S(S32)
+        rb = st.run(w["lam"], tol=1e-5, max_sweeps=200)
+        Hb = st.history()
+    assert ra.status == C.OK and rb.status == C.OK
+    f = ra.sweeps_fp32
+    assert f == rb.sweeps_fp32 and f >= 3
+    assert np.array_equal(Ha[:f, [0, 1, 3]], Hb[:f, [0, 1, 3]])
+    np.testing.assert_allclose(Ha[:f, 2], Hb[:f, 2], rtol=1e-13)
