@@ -75,6 +75,9 @@ struct concord_state {
   // the next mixed run at that lambda starts from it
   bool prescreen = false;
   double prescreen_lambda = 0.0;
+  // the Gram's and the one-pass start's checks (flag) not read yet: the next
+  // screened launch reads the word on the device and the host after it
+  bool flag_pending = false;
   unsigned long long* mbox = nullptr;
   int depth = kMailboxDepth;
   unsigned* barrier = nullptr;
@@ -173,6 +176,18 @@ bool is_mixed(const concord_state* st) { return st->precision == CONCORD_MIXED; 
 int check_state(concord_state* st) {
   if (!st) return fail(CONCORD_E_ARG, "state is NULL");
   CK(cudaSetDevice(st->device));
+  return CONCORD_OK;
+}
+
+// The errors behind the bits of the data checks (Gram: 1 constant column,
+// 2 non-finite entry, 4 device wait ran out; one-pass start: 8 non-finite
+// diagonal, 16 diagonal <= 0).
+int input_flag_error(int bad) {
+  if (bad & 4) return fail(CONCORD_E_TIMEOUT, "tensor-core Gram: a device-side wait ran out");
+  if (bad & 2) return fail(CONCORD_E_NONFINITE, "X has a non-finite entry");
+  if (bad & 1) return fail(CONCORD_E_NONPOS_DIAG, "X has a constant column");
+  if (bad & 8) return fail(CONCORD_E_NONFINITE, "S has a non-finite diagonal entry");
+  if (bad & 16) return fail(CONCORD_E_NONPOS_DIAG, "S has a diagonal entry <= 0 (constant column?)");
   return CONCORD_OK;
 }
 
@@ -567,6 +582,9 @@ int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, d
   a.max_redo = 8;
   a.start_list = start_list;
   a.start_scan = start_scan;
+  const bool check_flag = st->flag_pending;
+  st->flag_pending = false;
+  a.input_flag = check_flag ? st->flag : nullptr;
   a.mrow = st->mrow;
   a.lazy_verify = st->lazy_verify ? 1 : 0;
   a.keep_w = st->screen_keep_w ? 1 : 0;
@@ -593,8 +611,14 @@ int launch_screened_run(concord_state* st, T* S, T* W, T* Om, const T* sdiagT, d
                      st->stream));
   CK(cudaMemcpyAsync(st->h_abort, st->abort_info, 3 * sizeof(int), cudaMemcpyDeviceToHost,
                      st->stream));
+  if (check_flag)
+    CK(cudaMemcpyAsync(st->h_flag, st->flag, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
   CK(cudaStreamSynchronize(st->stream));
   CK(cudaGetLastError());
+  if (check_flag && *st->h_flag != 0) {
+    const int rc_in = input_flag_error(*st->h_flag);
+    if (rc_in != CONCORD_OK) return rc_in;
+  }
   const double* r = st->h_result;
   out->sweeps = (int)r[kResSweeps];
   out->kkt = r[kResKkt];
@@ -1138,8 +1162,14 @@ int run_impl(concord_state* st, double lambda, double tol, int max_sweeps, int s
   if (!exact && !(tol > 0.0)) return fail(CONCORD_E_ARG, "tol must be > 0");
   const double run_tol = exact ? -1.0 : tol;
   // a start screen of this state's current S and starting point (one-shot)
-  const bool pre = st->prescreen && st->prescreen_lambda == lambda;
+  const bool pre = st->prescreen && st->prescreen_lambda == lambda && is_mixed(st);
   st->prescreen = false;
+  if (st->flag_pending && !pre) {  // the data checks, read here after all
+    st->flag_pending = false;
+    int bad = 0, rc0 = read_flag(st, &bad);
+    if (rc0 != CONCORD_OK) return rc0;
+    if ((rc0 = input_flag_error(bad)) != CONCORD_OK) return rc0;
+  }
   st->hist_rows = 0;
   st->n_launch = 0;
   CK(cudaEventRecord(st->ev0, st->stream));
@@ -2001,20 +2031,22 @@ static int gram_into_state(concord_state* st, const void* X, int x_f32, int n, i
     }
     CK(launch_reset_mixed(ra, st->stream));
   }
-  int bad = 0, rc;
-  if ((rc = read_flag(st, &bad))) return rc;
-  if (bad & 4) return fail(CONCORD_E_TIMEOUT, "tensor-core Gram: a device-side wait ran out");
-  if (bad & 2) return fail(CONCORD_E_NONFINITE, "X has a non-finite entry");
-  if (bad & 1) return fail(CONCORD_E_NONPOS_DIAG, "X has a constant column");
-  if (!fused) return reset_iterate(st);
-  if (bad & 8) return fail(CONCORD_E_NONFINITE, "S has a non-finite diagonal entry");
-  if (bad & 16) return fail(CONCORD_E_NONPOS_DIAG, "S has a diagonal entry <= 0 (constant column?)");
   st->om64_current = false;
   if (screened_start) {
+    // the solve's screened launch comes next: it reads the checks' word on
+    // the device and the host reads it with the launch's result (no wait here)
     st->prescreen = true;
     st->prescreen_lambda = screen_lambda;
+    st->flag_pending = true;
+    return CONCORD_OK;
   }
-  return CONCORD_OK;
+  int bad = 0, rc;
+  if ((rc = read_flag(st, &bad))) return rc;
+  if ((bad & 7) || !fused) {
+    if ((rc = input_flag_error(bad & 7))) return rc;
+    return reset_iterate(st);
+  }
+  return input_flag_error(bad);
 }
 
 int concord_gram(const void* X_dev, int x_dtype, int n, int p, int ldx, int prep, int mode,

@@ -207,6 +207,8 @@ struct ScreenArgs {
                             // -1: screen the starting point
   int start_scan;           // with start_list: only its counts are in place (a list
                             // screened outside the kernel); the first build scans them
+  const int* input_flag;    // nullable: nonzero when a check of the input failed (the
+                            // launch then ends before its first sweep, status 2)
   // lambda path (path_n > 0): lambdas path_lambda[path_start .. path_n), each
   // swept until its stopping rule, warm-started from the previous one
   const double* path_lambda;

@@ -574,6 +574,16 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
   __shared__ int s_nloud;
   extern __shared__ __align__(128) unsigned char dyn[];
 
+  // the data checks of the kernels before this launch were not read by the
+  // host yet: when one failed, end at once (every CTA reads the same word)
+  if (a.input_flag != nullptr && ld_relaxed_s32(a.input_flag) != 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      for (int k = 0; k < kRes; ++k) a.result[k] = 0.0;
+      a.result[kResStatus] = 2.0;
+      a.result[kResList] = -1.0;
+    }
+    return;
+  }
   unsigned gen = 0;
   int where = 0;
   T* Wa = a.W;

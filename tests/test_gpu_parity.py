@@ -376,6 +376,35 @@ def test_state_argument_errors():
             st.run(-1.0)
 
 
+@pytest.mark.parametrize("gram", [C.GRAM_TF32X3, C.GRAM_FP64])
+def test_solve_device_data_errors(gram):
+    """A mixed solve from data reports a constant column and a non-finite
+    entry (with a reduced-precision Gram the checks are read with the FP32
+    launch's result: that launch ends before its first sweep), and the state
+    solves good data afterwards."""
+    p, n = 64, 60  # n <= p: the FP64 Gram of a mixed state stages Z in W
+    rng = np.random.default_rng(9)
+    good = rng.standard_normal((n, p))
+    const = good.copy()
+    const[:, 5] = 2.0
+    bad = good.copy()
+    bad[7, 9] = np.nan
+    with C.State(p, C.MIXED, n_cap=n) as st:
+        st.set_gram_mode(gram)
+        with pytest.raises(C.ConcordError) as e:
+            st.solve_device(dev(const), 0.3, tol=1e-6)
+        assert e.value.code == C.E_NONPOS_DIAG
+        with pytest.raises(C.ConcordError) as e:
+            st.solve_device(dev(bad), 0.3, tol=1e-6)
+        assert e.value.code == C.E_NONFINITE
+        r = st.solve_device(dev(good), 0.3, tol=1e-6)
+        assert r.status == C.OK and r.kkt <= 1e-6
+        S = O.gram(O.standardize(good))
+        Om_or, _ = O.solve(S, 0.3, tol=1e-10, max_sweeps=500)
+        G = host(st.get_omega())
+        assert np.abs(G - Om_or).max() <= 1e-5 * np.abs(Om_or).max()
+
+
 @pytest.mark.parametrize("variant", [C.SWEEP_GRID, C.SWEEP_CLUSTER])
 @pytest.mark.parametrize("precision", [C.FP64, C.MIXED])
 def test_wait_timeout_is_reported_and_context_survives(small, precision, variant):
