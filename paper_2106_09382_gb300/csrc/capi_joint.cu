@@ -70,10 +70,10 @@ bool mixed(const concord_joint* jt) { return jt->precision == CONCORD_MIXED; }
 
 int default_grid(const concord_joint* jt) {
   if (jt->grid_override > 0) return jt->grid_override < jt->sms ? jt->grid_override : jt->sms;
-  const int half = (jt->P + 1) / 2;
-  int g = (half + kJointWarps - 1) / kJointWarps;
-  if (g < 16) g = 16;
-  return g < jt->sms ? g : jt->sms;
+  // every SM: the colour steps are latency-bound chains, and more warps in
+  // flight shorten them (measured at p = 1000: 50.2 ms with one CTA per 16
+  // pairs of a colour, 43.6 ms with one CTA per SM)
+  return jt->sms;
 }
 
 void free_all(concord_joint* jt) {

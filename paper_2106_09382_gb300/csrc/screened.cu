@@ -97,7 +97,8 @@ __device__ void cta_scan(F f, int n, int* out, int* out2, int* s_tmp) {
   const int per = (n + nt - 1) / nt;
   const int b = min(n, threadIdx.x * per), e = min(n, b + per);
   int sum = 0;
-  for (int k = b; k < e; ++k) sum += f(k);
+#pragma unroll 8
+  for (int k = b; k < e; ++k) sum += f(k);  // independent loads: unrolled, in flight together
   int x = sum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -117,6 +118,7 @@ __device__ void cta_scan(F f, int n, int* out, int* out2, int* s_tmp) {
   }
   __syncthreads();
   int run = x - sum + (wid > 0 ? s_tmp[wid - 1] : 0);
+#pragma unroll 8
   for (int k = b; k < e; ++k) {
     const int c = f(k);
     out[k] = run;
@@ -736,29 +738,45 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         // operands; each candidate's terms (row i's earlier candidates, then
         // row j's) get a contiguous range from a shared counter -- where the
         // range lies does not affect any value
-        for (int k = sid; k < N; k += gthreads) {
-          const int2 pr = __ldcg(cand + k);
-          const int i = pr.x, j = pr.y;
-          T* rec = w.nd_rec + 4 * (size_t)k;
-          T w1 = __ldcg(Wa + (size_t)i * ld + j), w2 = __ldcg(Wa + (size_t)j * ld + i);
-          if (have_pend) {  // the rows' deferred updates, in order
-            w1 = pend_fold(a, i, ldi(w.pend_n + i), j, w1);
-            w2 = pend_fold(a, j, ldi(w.pend_n + j), i, w2);
+        // (warp-uniform trips: a warp takes 32 consecutive candidates and
+        // allocates their term ranges with one atomic)
+        for (int k0 = swarp * 32; k0 < N; k0 += gwarps * 32) {
+          const int k = k0 + lane;
+          const bool valid = k < N;
+          int i = 0, j = 0;
+          if (valid) {
+            const int2 pr = __ldcg(cand + k);
+            i = pr.x;
+            j = pr.y;
+            T* rec = w.nd_rec + 4 * (size_t)k;
+            T w1 = __ldcg(Wa + (size_t)i * ld + j), w2 = __ldcg(Wa + (size_t)j * ld + i);
+            if (have_pend) {  // the rows' deferred updates, in order
+              w1 = pend_fold(a, i, ldi(w.pend_n + i), j, w1);
+              w2 = pend_fold(a, j, ldi(w.pend_n + j), i, w2);
+            }
+            rec[0] = w1;
+            rec[1] = w2;
+            rec[2] = __ldcg(a.Om + (size_t)i * ld + j);
+            w.nd_delta[k] = (T)0;  // the fixed-point iteration starts from no change
+            if (!reuse) rec[3] = a.sdiag[i] + a.sdiag[j];
           }
-          rec[0] = w1;
-          rec[1] = w2;
-          rec[2] = __ldcg(a.Om + (size_t)i * ld + j);
-          if (reuse) {  // terms and s_ii + s_jj as the previous sweep built them
-            w.nd_delta[k] = (T)0;
-            continue;
+          if (reuse) continue;  // terms and s_ii + s_jj as the previous sweep built them
+          const int bi = valid ? ldi(w.off_r + i) : 0, pi = valid ? ldi(w.nd_pi + k) : 0;
+          const int bj = valid ? ldi(w.off_r + j) : 0, pj = valid ? ldi(w.nd_pj + k) : 0;
+          const int cnt = pi + pj;
+          int incl = cnt;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
           }
-          rec[3] = a.sdiag[i] + a.sdiag[j];
-          const int bi = ldi(w.off_r + i), pi = ldi(w.nd_pi + k);
-          const int bj = ldi(w.off_r + j), pj = ldi(w.nd_pj + k);
-          int tp = pi + pj > 0 ? atomicAdd(w.ctr + kCtrTerms, pi + pj) : 0;
+          int base = 0;
+          if (lane == 31 && incl > 0) base = atomicAdd(w.ctr + kCtrTerms, incl);
+          base = __shfl_sync(FULL, base, 31);
+          int tp = base + incl - cnt;
+          if (!valid) continue;
           w.term_ptr[k] = tp;
-          w.nd_delta[k] = (T)0;  // the fixed-point iteration starts from no change
-          if (tp + pi + pj > w.term_cap) continue;  // overflow: the sweep goes dense
+          if (tp + cnt > w.term_cap) continue;  // overflow: the sweep goes dense
           for (int m = 0; m < pi; ++m, ++tp) {
             const int q = ldi(w.row_ent + bi + m);
             const int2 qp = __ldcg(cand + q);
