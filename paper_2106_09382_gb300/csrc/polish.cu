@@ -134,12 +134,18 @@ __device__ __forceinline__ void block_parts(double (&v)[kParts], double (*s_p)[k
 #pragma unroll
   for (int k = 0; k < kParts; ++k) {
     double x = v[k];
-    const bool mx = k == kPartKkt || k == kPartDelta;
-    if (__any_sync(FULL, x != 0.0)) {  // skip the FP64 tree of warps without terms
+    // skip the tree of warps without terms (tested on the bits); the maxima
+    // are of nonnegative values, whose bit patterns order as integers
+    const long long xb = __double_as_longlong(x);
+    if (__any_sync(FULL, (xb << 1) != 0ll)) {
+      if (k == kPartKkt || k == kPartDelta) {
+        long long m = xb;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double y = __shfl_xor_sync(FULL, x, o);
-        x = mx ? fmax(x, y) : x + y;
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL, m, o));
+        x = __longlong_as_double(m);
+      } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
       }
     }
     v[k] = x;

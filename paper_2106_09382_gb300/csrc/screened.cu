@@ -92,13 +92,29 @@ __device__ __forceinline__ unsigned mag_hi_below(double bound) {
 // Exclusive prefix sum by one CTA: out[k] = sum_{q<k} f(q) for k <= n (and
 // the same into out2 when given).
 template <typename F>
-__device__ void cta_scan(F f, int n, int* out, int* out2, int* s_tmp) {
+__device__ void cta_scan(F f, int n, int* out, int* out2, int* s_tmp, int* terms_out = nullptr) {
   const int nt = blockDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int per = (n + nt - 1) / nt;
   const int b = min(n, threadIdx.x * per), e = min(n, b + per);
   int sum = 0;
+  unsigned long long terms = 0ull;  // sum over the rows of c (c - 1) / 2
 #pragma unroll 8
-  for (int k = b; k < e; ++k) sum += f(k);  // independent loads: unrolled, in flight together
+  for (int k = b; k < e; ++k) {  // independent loads: unrolled, in flight together
+    const int c = f(k);
+    sum += c;
+    terms += (unsigned long long)c * (unsigned long long)(c > 0 ? c - 1 : 0) / 2ull;
+  }
+  if (terms_out != nullptr) {
+    __shared__ unsigned long long s_terms_sum;
+    if (threadIdx.x == 0) s_terms_sum = 0ull;
+    __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) terms += __shfl_down_sync(FULL, terms, o);
+    if (lane == 0) atomicAdd(&s_terms_sum, terms);
+    __syncthreads();
+    if (threadIdx.x == 0)
+      *terms_out = s_terms_sum > 0x7fffffffull ? 0x7fffffff : (int)s_terms_sum;
+  }
   int x = sum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -136,23 +152,6 @@ __device__ void cta_scan(F f, int n, int* out, int* out2, int* s_tmp) {
 // candidates 0 + 1 + ... + (k - 1) terms; written to *out, saturated at
 // INT_MAX, so a sweep whose terms cannot fit goes to the dense kernel before
 // any is built.
-template <typename F>
-__device__ void cta_count_terms(F f, int n, int* out) {
-  __shared__ unsigned long long s_terms;
-  if (threadIdx.x == 0) s_terms = 0ull;
-  __syncthreads();
-  unsigned long long t = 0ull;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const unsigned long long c = (unsigned long long)f(k);
-    t += c * (c - (c > 0 ? 1ull : 0ull)) / 2ull;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(FULL, t, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(&s_terms, t);
-  __syncthreads();
-  if (threadIdx.x == 0) *out = s_terms > 0x7fffffffull ? 0x7fffffff : (int)s_terms;
-  __syncthreads();
-}
 
 
 
@@ -174,14 +173,21 @@ __device__ __forceinline__ void reduce_parts(double (&v)[kParts], double* out,
 #pragma unroll
   for (int k = 0; k < kParts; ++k) {
     double x = v[k];
-    // most warps hold no terms of a part: skip their FP64 shuffle tree (the
-    // FP64 pipe is narrow on this part, and 512 threads x 8 parts x 5 levels
-    // of it cost microseconds per sweep)
-    if (__any_sync(FULL, x != 0.0)) {
+    // most warps hold no terms of a part: skip their shuffle tree (tested on
+    // the bits, with integer operations: the FP64 pipe is narrow on this
+    // part, and 512 threads x 8 parts of FP64 compares and trees cost
+    // microseconds per sweep).  The maxima are of nonnegative values, whose
+    // bit patterns order as integers
+    const long long xb = __double_as_longlong(x);
+    if (__any_sync(FULL, (xb << 1) != 0ll)) {
+      if (k == kPartKkt || k == kPartDelta) {
+        long long m = xb;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double y = __shfl_down_sync(FULL, x, o);
-        x = (k == kPartKkt || k == kPartDelta) ? fmax(x, y) : x + y;
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(FULL, m, o));
+        x = __longlong_as_double(m);
+      } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(FULL, x, o);
       }
     }
     if (lane == 0) red[wid][k] = x;
@@ -661,8 +667,8 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
         if (!reuse) {
         if (need_scan) {  // else the previous sweep's reduce phase scanned the counts
           if (blockIdx.x == 0) {
-            cta_scan([&](int k) { return ldi(w.cnt_r[cur] + k); }, p, w.off_r, w.cur_r, s_tmp);
-            cta_count_terms([&](int k) { return ldi(w.cnt_r[cur] + k); }, p, w.ctr + kCtrTermsPred);
+            cta_scan([&](int k) { return ldi(w.cnt_r[cur] + k); }, p, w.off_r, w.cur_r, s_tmp,
+                     w.ctr + kCtrTermsPred);
           }
           grid_barrier(a.barrier, gen, wc, ++where);
         }
@@ -1385,8 +1391,8 @@ __global__ void __launch_bounds__(kScreenThreads, 1) k_screened(const ScreenArgs
       // row offsets of the next sweep's list (its pushes are complete); a
       // lazy sweep keeps its list, offsets and build
       if (blockIdx.x == 0 && !fast) {
-        cta_scan([&](int k) { return ldi(w.cnt_r[1 - cur] + k); }, p, w.off_r, w.cur_r, s_tmp);
-        cta_count_terms([&](int k) { return ldi(w.cnt_r[1 - cur] + k); }, p, w.ctr + kCtrTermsPred);
+        cta_scan([&](int k) { return ldi(w.cnt_r[1 - cur] + k); }, p, w.off_r, w.cur_r, s_tmp,
+                 w.ctr + kCtrTermsPred);
       }
       if (blockIdx.x == 0 && fast)  // fresh cursors for a later build of the kept list
         for (int k = threadIdx.x; k <= p; k += blockDim.x) w.cur_r[k] = ldi(w.off_r + k);
