@@ -155,13 +155,23 @@ __device__ __forceinline__ void block_parts(double (&v)[kParts], double (*s_p)[k
 #pragma unroll
     for (int k = 0; k < kParts; ++k) s_p[threadIdx.x >> 5][k] = v[k];
   __syncthreads();
-  if (threadIdx.x == 0) {
+  // the warps' values, part by part, over the lanes of warp 0 (a fixed tree)
+  if ((threadIdx.x >> 5) == 0) {
+    const int lane = threadIdx.x & 31;
     double* q = partials + (size_t)blockIdx.x * kParts;
+#pragma unroll
     for (int k = 0; k < kParts; ++k) {
-      const bool mx = k == kPartKkt || k == kPartDelta;
-      double x = 0.0;  // the max entries are nonnegative
-      for (int w = 0; w < kWarps; ++w) x = mx ? fmax(x, s_p[w][k]) : x + s_p[w][k];
-      q[k] = x;
+      double x = lane < kWarps ? s_p[lane][k] : 0.0;  // 0: the identity of both
+      if (k == kPartKkt || k == kPartDelta) {
+        long long m = __double_as_longlong(x);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(FULL, m, o));
+        x = __longlong_as_double(m);
+      } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(FULL, x, o);
+      }
+      if (lane == 0) q[k] = x;
     }
   }
 }
