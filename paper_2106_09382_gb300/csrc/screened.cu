@@ -148,13 +148,9 @@ __device__ void cta_scan(F f, int n, int* out, int* out2, int* s_tmp, int* terms
   __syncthreads();
 }
 
-// Correction terms a list needs (one CTA): a row with k candidates gives its
-// candidates 0 + 1 + ... + (k - 1) terms; written to *out, saturated at
-// INT_MAX, so a sweep whose terms cannot fit goes to the dense kernel before
-// any is built.
-
-
-
+// Correction terms a list needs come with the scan (terms_out): a row with c
+// candidates gives them 0 + 1 + ... + (c - 1) terms, saturated at INT_MAX, so
+// a sweep whose terms cannot fit goes to the dense kernel before any is built.
 
 
 template <typename T>
@@ -193,12 +189,22 @@ __device__ __forceinline__ void reduce_parts(double (&v)[kParts], double* out,
     if (lane == 0) red[wid][k] = x;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  // the warps' values, part by part, over the lanes of warp 0 (a fixed tree;
+  // one thread adding them in turn was a chain of ~128 FP64 operations)
+  if (wid == 0) {
+#pragma unroll
     for (int k = 0; k < kParts; ++k) {
-      double x = red[0][k];
-      for (int w = 1; w < nw; ++w)
-        x = (k == kPartKkt || k == kPartDelta) ? fmax(x, red[w][k]) : x + red[w][k];
-      out[(size_t)blockIdx.x * kParts + k] = x;
+      double x = lane < nw ? red[lane][k] : 0.0;  // 0: the identity of both
+      if (k == kPartKkt || k == kPartDelta) {
+        long long m = __double_as_longlong(x);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(FULL, m, o));
+        x = __longlong_as_double(m);
+      } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(FULL, x, o);
+      }
+      if (lane == 0) out[(size_t)blockIdx.x * kParts + k] = x;
     }
   }
   __syncthreads();
