@@ -21,8 +21,8 @@
 //     4 K blocks) and commits each stage back to its producer barrier;
 //   * eight epilogue warps drain each finished accumulator (tcgen05.ld, each
 //     warp its own 32 lanes and 64 columns) into compensated FP32 running
-//     sums (TwoSum: a high and a low part) kept in the other half of tensor
-//     memory, then scale by 1/n and store S[i][j] and S[j][i] for i <= j.
+//     sums (TwoSum: a high and a low part) held in registers, then scale by
+//     1/n and store S[i][j] and S[j][i] for i <= j.
 // Every wait is bounded (%globaltimer); a wait that runs out sets bit 4 of
 // the caller's status word.
 #include <cuda.h>
@@ -149,8 +149,7 @@ constexpr int kStageBytes = 4 * kOpBytes;         // A_hi, A_lo, B_hi, B_lo
 constexpr int kChunkKb = 4;                       // K blocks summed per FP32 accumulator chunk
 constexpr int kEpiWarps = 8;                      // epilogue warps (2 per TMEM lane quadrant)
 constexpr int kGramThreads = 32 * (2 + kEpiWarps);  // producer, MMA issuer, epilogue
-constexpr int kTmemCols = 512;                    // two 128-column FP32 accumulators + sums
-constexpr int kSumHi = 256, kSumLo = 384;         // tensor-memory columns of the running sums
+constexpr int kTmemCols = 2 * kTM;                // two 128-column FP32 accumulators
 constexpr size_t kGramSmem = (size_t)kStages * kStageBytes + 1024;  // + alignment slack
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -284,18 +283,6 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_st_32x32b_x32(uint32_t taddr, const uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
-      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
-      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
-      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]),
-      "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]),
-      "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
-      : "memory");
-}
-
 // hi + lo += x with the rounding error of hi + x kept exactly (Knuth's
 // TwoSum: six FP32 additions, no ordering assumption on |hi| and |x|).
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
@@ -304,6 +291,81 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
   const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
   hi = s;
   lo = __fadd_rn(lo, err);
+}
+
+// Order of the upper-triangle tiles over the grid: bands of kGroupRows tile
+// rows; within a band the tile columns in increasing order and, per column,
+// the band's rows bi <= bj.  The CTAs resident at one time then read a few
+// dozen operand row blocks (the band's own and a run of columns), each from
+// several CTAs at nearly the same K, so L2 serves the repeats; in row-major
+// order every resident CTA streams its own column block from HBM.
+constexpr int kGroupRows = 8;
+
+__host__ __device__ inline void gram_tile(int t, int nbt, int group, int& bi, int& bj) {
+  int r0 = 0;
+  for (;;) {
+    const int g = nbt - r0 < group ? nbt - r0 : group;
+    const int tri = g * (g + 1) / 2;  // columns r0 .. r0 + g - 1: rows r0 .. bj
+    const int cnt = tri + (nbt - r0 - g) * g;
+    if (t < cnt) {
+      if (t < tri) {
+        int c = 0;
+        while (t > c) {
+          t -= c + 1;
+          ++c;
+        }
+        bj = r0 + c;
+        bi = r0 + t;
+      } else {
+        t -= tri;
+        bj = r0 + g + t / g;
+        bi = r0 + t % g;
+      }
+      return;
+    }
+    t -= cnt;
+    r0 += g;
+  }
+}
+
+// Packed FP32 pair arithmetic (add / sub .f32x2, round to nearest on each
+// element: the same results as two scalar operations, one instruction).
+__device__ __forceinline__ void add_f32x2(float& d0, float& d1, float a0, float a1, float b0,
+                                          float b1) {
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d0), "=f"(d1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
+__device__ __forceinline__ void sub_f32x2(float& d0, float& d1, float a0, float a1, float b0,
+                                          float b1) {
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d0), "=f"(d1)
+      : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
+// two_sum_acc on two running sums at once: the same operations in the same
+// order on each element, as packed pairs.
+__device__ __forceinline__ void two_sum_acc2(float& h0, float& h1, float& l0, float& l1, float x0,
+                                             float x1) {
+  float s0, s1, b0, b1, t0, t1, u0, u1, v0, v1, e0, e1;
+  add_f32x2(s0, s1, h0, h1, x0, x1);  // s = hi + x
+  sub_f32x2(b0, b1, s0, s1, h0, h1);  // bp = s - hi
+  sub_f32x2(t0, t1, s0, s1, b0, b1);  // s - bp
+  sub_f32x2(u0, u1, h0, h1, t0, t1);  // hi - (s - bp)
+  sub_f32x2(v0, v1, x0, x1, b0, b1);  // x - bp
+  add_f32x2(e0, e1, u0, u1, v0, v1);  // err
+  h0 = s0;
+  h1 = s1;
+  add_f32x2(l0, l1, l0, l1, e0, e1);  // lo += err
 }
 
 // One CTA per 128 x 128 tile of the upper triangle.  The K reduction is cut
@@ -316,7 +378,8 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
 template <typename F>
 __global__ void __launch_bounds__(kGramThreads, 1)
     k_gram_3x(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
-              int nkb, int p, float* __restrict__ S, int lds, float scale, int nbt, int* status) {
+              int nkb, int p, float* __restrict__ S, int lds, float scale, int nbt, int group,
+              int* status) {
   constexpr int kTK = F::kTK;
   extern __shared__ unsigned char gsm_raw[];
   __shared__ __align__(8) uint64_t full[kStages];
@@ -327,13 +390,8 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   // 1024-byte aligned operand ring (the 128-byte swizzle repeats every 1024)
   unsigned char* ring = (unsigned char*)(((uintptr_t)gsm_raw + 1023) & ~(uintptr_t)1023);
 
-  // tile index -> (bi, bj), bi <= bj, row-major over the upper triangle
-  int tt = blockIdx.x, bi = 0;
-  while (tt >= nbt - bi) {
-    tt -= nbt - bi;
-    ++bi;
-  }
-  const int bj = bi + tt;
+  int bi, bj;
+  gram_tile(blockIdx.x, nbt, group, bi, bj);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunks = (nkb + kChunkKb - 1) / kChunkKb;
 
@@ -411,67 +469,68 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     }
   } else {
     // ---- epilogue: warp e owns TMEM lanes 32 (warp % 4) .. +31 (tile rows)
-    //      and tile columns 64 * (e / 4) .. +63; compensated sums across chunks
+    //      and tile columns 64 * (e / 4) .. +63; the compensated sums across
+    //      chunks stay in registers (hi, lo per element, fully unrolled), so
+    //      a drain is two tensor-memory loads and no stores
     const int e = warp - 2;
     const int quad = warp & 3;
     const int col0 = 64 * (e >> 2);
     const uint32_t lanes = (uint32_t)(quad * 32) << 16;
+    float sh[64], sl[64];
+#pragma unroll
+    for (int q = 0; q < 64; ++q) {
+      sh[q] = 0.f;
+      sl[q] = 0.f;
+    }
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
       const int b = c & 1;
       ok = __all_sync(0xffffffffu, ok && mbar_wait(&acc_full[b], (c >> 1) & 1, status));
       __syncwarp();
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t v[32];
+      const uint32_t acc = tbase + lanes + (uint32_t)(b * kTM + col0);
       if (ok) {
-#pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t cc = (uint32_t)(col0 + 32 * h);
-          uint32_t v[32], hi[32], lo[32];
-          tmem_ld_32x32b_x32(tbase + lanes + (uint32_t)(b * kTM) + cc, v);
-          if (c == 0) {
+        tmem_ld_32x32b_x32(acc, v);
 #pragma unroll
-            for (int q = 0; q < 32; ++q) lo[q] = 0u;
-            tmem_st_32x32b_x32(tbase + lanes + kSumHi + cc, v);
-          } else {
-            tmem_ld_32x32b_x32(tbase + lanes + kSumHi + cc, hi);
-            tmem_ld_32x32b_x32(tbase + lanes + kSumLo + cc, lo);
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-              float fh = __uint_as_float(hi[q]), fl = __uint_as_float(lo[q]);
-              two_sum_acc(fh, fl, __uint_as_float(v[q]));
-              hi[q] = __float_as_uint(fh);
-              lo[q] = __float_as_uint(fl);
-            }
-            tmem_st_32x32b_x32(tbase + lanes + kSumHi + cc, hi);
-          }
-          tmem_st_32x32b_x32(tbase + lanes + kSumLo + cc, lo);
-          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        }
+        for (int q = 0; q < 32; q += 2)
+          two_sum_acc2(sh[q], sh[q + 1], sl[q], sl[q + 1], __uint_as_float(v[q]),
+                       __uint_as_float(v[q + 1]));
+        tmem_ld_32x32b_x32(acc + 32, v);
       }
+      // the buffer is free once both loads have completed
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&acc_empty[b]);
       if (!ok) break;
+#pragma unroll
+      for (int q = 0; q < 32; q += 2)
+        two_sum_acc2(sh[32 + q], sh[33 + q], sl[32 + q], sl[33 + q], __uint_as_float(v[q]),
+                     __uint_as_float(v[q + 1]));
     }
     if (ok) {
-      const int i = bi * kTM + quad * 32 + lane;
-#pragma unroll 1
-      for (int h = 0; h < 2; ++h) {
-        const uint32_t cc = (uint32_t)(col0 + 32 * h);
-        uint32_t hi[32], lo[32];
-        tmem_ld_32x32b_x32(tbase + lanes + kSumHi + cc, hi);
-        tmem_ld_32x32b_x32(tbase + lanes + kSumLo + cc, lo);
-        if (i < p) {
+      // S[j][i] straight from the registers (the lanes hold consecutive i:
+      // one coalesced row segment per column); S[i][j] through a shared-
+      // memory transpose, one row segment per store.  The operand ring is
+      // idle here: every load was consumed and the last MMA has completed.
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      float* T = reinterpret_cast<float*>(ring) + e * (32 * 65);
+      const int i0 = bi * kTM + quad * 32;
+      const int i = i0 + lane;
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            const int j = bj * kTM + (int)cc + q;
-            if (j < p && i <= j) {
-              // (hi + lo) * scale in one rounding of hi * scale plus the
-              // (tiny) lo * scale: within an FP32 ulp of the exact product
-              const float val = fmaf(__uint_as_float(hi[q]), scale, __uint_as_float(lo[q]) * scale);
-              S[(size_t)i * lds + j] = val;
-              S[(size_t)j * lds + i] = val;
-            }
-          }
+      for (int q = 0; q < 64; ++q) {
+        // (hi + lo) * scale in one rounding of hi * scale plus the
+        // (tiny) lo * scale: within an FP32 ulp of the exact product
+        const float val = fmaf(sh[q], scale, sl[q] * scale);
+        const int j = bj * kTM + col0 + q;
+        if (i < p && j < p && i <= j) S[(size_t)j * lds + i] = val;
+        T[lane * 65 + q] = val;
+      }
+      __syncwarp();
+      for (int r = 0; r < 32 && i0 + r < p; ++r) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = bj * kTM + col0 + 32 * h + lane;
+          if (j < p && i0 + r <= j) S[(size_t)(i0 + r) * lds + j] = T[r * 65 + 32 * h + lane];
         }
       }
     }
@@ -528,7 +587,8 @@ namespace {
 
 template <typename F>
 cudaError_t launch_gram_3x(const void* zt_hi, const void* zt_lo, int n_pad, int p_pad, int p, float* S,
-                           int lds, float scale, int* status, cudaStream_t st) {
+                           int lds, float scale, int* status, cudaStream_t st,
+                           int group = kGroupRows) {
   constexpr bool bf16 = F::kTK == Bf16Fmt::kTK;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -547,8 +607,9 @@ cudaError_t launch_gram_3x(const void* zt_hi, const void* zt_lo, int n_pad, int 
   if (e != cudaSuccess) return e;
   const int nbt = p_pad / kTM;
   const int tiles = nbt * (nbt + 1) / 2;
+  if (group < 1) return cudaErrorInvalidValue;
   k_gram_3x<F><<<tiles, kGramThreads, kGramSmem, st>>>(m_hi, m_lo, n_pad / F::kTK, p, S, lds, scale,
-                                                      nbt, status);
+                                                      nbt, group, status);
   note_launches(1);
   return cudaGetLastError();
 }
