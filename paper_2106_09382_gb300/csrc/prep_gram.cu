@@ -2,12 +2,13 @@
 // 1/n variance) and the CUDA-core Gram S = Z^T Z / n (Algorithm 1's
 // T <- X^T X, divided by n).
 #include "prep_stats.h"
+#include "fp_bits.cuh"
 
 namespace concord {
 
 template <typename TX>
 __device__ __forceinline__ double ld_x(const TX* X, size_t i) {
-  return (double)__ldg(X + i);
+  return to_f64(__ldg(X + i));
 }
 
 // One CTA per 32 columns; kStatThreads / 32 row groups per column sum
@@ -33,7 +34,7 @@ __global__ void __launch_bounds__(kStatThreads) k_col_stats(const TX* __restrict
     for (int k = ty; k < n; k += G) {
       const double v = ld_x(X, (size_t)k * ldx + col);
       acc += v;
-      if (!isfinite(v)) nonfinite = 1;
+      if (!finite_bits(v)) nonfinite = 1;
     }
   }
   part[ty][tx] = acc;
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(kStatCols) k_col_partial(const TX* __restrict_
       acc += d * d;
     } else {
       acc += v;
-      if (!isfinite(v)) nonfinite = 1;
+      if (!finite_bits(v)) nonfinite = 1;
     }
   }
   part[(size_t)blockIdx.y * p + col] = acc;

@@ -2,6 +2,7 @@
 #include <atomic>
 
 #include "kernels.h"
+#include "fp_bits.cuh"
 
 namespace concord {
 
@@ -279,11 +280,13 @@ __global__ void __launch_bounds__(256) k_reset_mixed(const ResetMixedArgs a) {
     float4* orow = reinterpret_cast<float4*>(a.Om + (size_t)u * a.ld);
     double2* drow = reinterpret_cast<double2*>(a.S64 + (size_t)u * a.ld);
     float mx = 0.f;
-    if (a.lam_s > 0.f) {  // the starting point's screen, upper triangle
-      for (int q0 = 0; q0 < nv; q0 += 32) {  // warp-uniform trips for the pushes
-        const int q = q0 + lane;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (q < nv) v = __ldg(srow + q);
+    // one pass over the row: the starting point's screen (upper triangle,
+    // warp-uniform trips for the pushes), W = S, Omega = I, the FP64 copy
+    for (int q0 = 0; q0 < nv; q0 += 32) {
+      const int q = q0 + lane;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (q < nv) v = __ldg(srow + q);
+      if (a.lam_s > 0.f) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int x = 4 * q + e;
@@ -304,21 +307,20 @@ __global__ void __launch_bounds__(256) k_reset_mixed(const ResetMixedArgs a) {
           }
         }
       }
-    }
-    for (int q = lane; q < nv; q += 32) {
-      const float4 v = __ldg(srow + q);
-      wrow[q] = v;
-      const int c0 = 4 * q;
-      float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (u >= c0 && u < c0 + 4) (&o.x)[u - c0] = 1.f;
-      orow[q] = o;
-      drow[2 * q] = make_double2((double)v.x, (double)v.y);
-      drow[2 * q + 1] = make_double2((double)v.z, (double)v.w);
-      // padding columns are zero; the diagonal is left out
-      if (c0 != u) mx = fmaxf(mx, fabsf(v.x));
-      if (c0 + 1 != u) mx = fmaxf(mx, fabsf(v.y));
-      if (c0 + 2 != u) mx = fmaxf(mx, fabsf(v.z));
-      if (c0 + 3 != u) mx = fmaxf(mx, fabsf(v.w));
+      if (q < nv) {
+        wrow[q] = v;
+        const int c0 = 4 * q;
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (u >= c0 && u < c0 + 4) (&o.x)[u - c0] = 1.f;
+        orow[q] = o;
+        drow[2 * q] = make_double2(widen_f32(v.x), widen_f32(v.y));
+        drow[2 * q + 1] = make_double2(widen_f32(v.z), widen_f32(v.w));
+        // padding columns are zero; the diagonal is left out
+        if (c0 != u) mx = fmaxf(mx, fabsf(v.x));
+        if (c0 + 1 != u) mx = fmaxf(mx, fabsf(v.y));
+        if (c0 + 2 != u) mx = fmaxf(mx, fabsf(v.z));
+        if (c0 + 3 != u) mx = fmaxf(mx, fabsf(v.w));
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
