@@ -26,6 +26,24 @@ __device__ __forceinline__ double widen_f32(float f) {
 __device__ __forceinline__ double to_f64(double v) { return v; }
 __device__ __forceinline__ double to_f64(float v) { return widen_f32(v); }
 
+// FP64 -> FP32 rounding to nearest (ties to even) with integer operations
+// for results in the FP32 normal range: the exponent is rebiased from 1023 to
+// 127, the significand keeps its top 23 bits and is rounded on the 29 bits
+// dropped; a carry out of the significand moves into the exponent (up to
+// infinity past the largest float), as IEEE 754 rounding does.  Inputs below
+// the normal range (subnormal or zero results), infinities and NaNs take the
+// conversion instruction.  Bit-identical to cvt.rn.f32.f64.
+__device__ __forceinline__ float narrow_f64(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned e = (unsigned)(u >> 52) & 0x7ffu;
+  if (e < 897u || e > 1150u) return (float)d;
+  const unsigned long long m = u & 0xfffffffffffffull;
+  unsigned f = ((unsigned)(u >> 63) << 31) | ((e - 896u) << 23) | (unsigned)(m >> 29);
+  const unsigned rem = (unsigned)(m & 0x1fffffffull);
+  if (rem > 0x10000000u || (rem == 0x10000000u && (f & 1u))) ++f;
+  return __uint_as_float(f);
+}
+
 // isfinite on the bit pattern (exponent field not all ones), integer only.
 __device__ __forceinline__ bool finite_bits(double v) {
   return ((__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256) k_split_tf32(const TX* __restrict__ X, in
   for (int r = ty; r < 32; r += 8) {
     const int k = k0 + r, i = i0 + tx;
     float z = 0.f;
-    if (k < n && i < p) z = (float)((to_f64(X[(size_t)k * ldx + i]) - mean[i]) * inv_scale[i]);
+    if (k < n && i < p) z = narrow_f64((to_f64(X[(size_t)k * ldx + i]) - mean[i]) * inv_scale[i]);
     const float h = to_tf32(z);
     th[r][tx] = h;
     tl[r][tx] = to_tf32(z - h);
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) k_split_bf16(const TX* __restrict__ X, in
   for (int r = ty; r < 32; r += 8) {
     const int k = k0 + r, i = i0 + tx;
     float z = 0.f;
-    if (k < n && i < p) z = (float)((to_f64(X[(size_t)k * ldx + i]) - mean[i]) * inv_scale[i]);
+    if (k < n && i < p) z = narrow_f64((to_f64(X[(size_t)k * ldx + i]) - mean[i]) * inv_scale[i]);
     const __nv_bfloat16 h = __float2bfloat16_rn(z);
     th[r][tx] = __bfloat16_as_ushort(h);
     tl[r][tx] = __bfloat16_as_ushort(__float2bfloat16_rn(z - __bfloat162float(h)));

@@ -118,6 +118,26 @@ def test_gram_centre_and_none():
     assert np.abs(S0 - X.T @ X / 40).max() <= 1e-12
 
 
+def test_fp32_data_widened_exactly():
+    """FP32 data enter the FP64 arithmetic through a widening done with
+    integer operations (exponent rebiased, significand moved up; zeros,
+    subnormals, infinities and NaNs through the conversion instruction),
+    which must equal the IEEE conversion bit for bit.  With one row and no
+    preparation the FP64 Gram is S_ij = z_i z_j, a single rounded product,
+    so it equals the product of the converted values exactly, here over
+    floats of every exponent, both signs and subnormals."""
+    rng = np.random.default_rng(11)
+    e = rng.integers(-149, 128, 3000)
+    x = (np.ldexp(rng.uniform(1.0, 2.0, 3000), e) * rng.choice([-1.0, 1.0], 3000))
+    x = x.astype(np.float32)
+    x = x[(x != 0) & np.isfinite(x)]
+    assert (np.abs(x) < np.finfo(np.float32).tiny).sum() > 10  # subnormals present
+    X = torch.as_tensor(x, device="cuda").view(1, -1)  # one row, row stride p
+    S = C.concord_gram(X, C.PREP_NONE, C.GRAM_FP64)
+    z = torch.as_tensor(x.astype(np.float64), device="cuda")
+    assert torch.equal(S, z[:, None] * z[None, :])
+
+
 def test_gram_constant_column_is_an_error():
     X = data(30, 20, 5)
     X[:, 4] = 1.25
