@@ -21,8 +21,9 @@
 //     4 K blocks) and commits each stage back to its producer barrier;
 //   * eight epilogue warps drain each finished accumulator (tcgen05.ld, each
 //     warp its own 32 lanes and 64 columns) into compensated FP32 running
-//     sums (TwoSum: a high and a low part) held in registers, then scale by
-//     1/n and store S[i][j] and S[j][i] for i <= j.
+//     sums (TwoSum: the high parts in registers, the low parts in the upper
+//     half of tensor memory), then scale by 1/n and store S[i][j] and
+//     S[j][i] for i <= j through a shared-memory transpose.
 // Every wait is bounded (%globaltimer); a wait that runs out sets bit 4 of
 // the caller's status word.
 #include <cuda.h>
@@ -150,7 +151,8 @@ constexpr int kStageBytes = 4 * kOpBytes;         // A_hi, A_lo, B_hi, B_lo
 constexpr int kChunkKb = 4;                       // K blocks summed per FP32 accumulator chunk
 constexpr int kEpiWarps = 8;                      // epilogue warps (2 per TMEM lane quadrant)
 constexpr int kGramThreads = 32 * (2 + kEpiWarps);  // producer, MMA issuer, epilogue
-constexpr int kTmemCols = 2 * kTM;                // two 128-column FP32 accumulators
+constexpr int kTmemCols = 512;                    // two 128-column FP32 accumulators + low parts
+constexpr int kSumLo = 2 * kTM;                   // tensor-memory columns of the sums' low parts
 constexpr size_t kGramSmem = (size_t)kStages * kStageBytes + 1024;  // + alignment slack
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -282,6 +284,18 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)
         "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_st_32x32b_x32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]),
+      "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]),
+      "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
 }
 
 // hi + lo += x with the rounding error of hi + x kept exactly (Knuth's
@@ -470,67 +484,87 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     }
   } else {
     // ---- epilogue: warp e owns TMEM lanes 32 (warp % 4) .. +31 (tile rows)
-    //      and tile columns 64 * (e / 4) .. +63; the compensated sums across
-    //      chunks stay in registers (hi, lo per element, fully unrolled), so
-    //      a drain is two tensor-memory loads and no stores
+    //      and tile columns 64 * (e / 4) .. +63.  The compensated sums across
+    //      chunks keep their high parts in registers (fully unrolled) and
+    //      their low parts in tensor memory: with both parts in registers the
+    //      drain spilled to local memory, whose traffic shares the SRAM the
+    //      MMAs read their operands from
     const int e = warp - 2;
     const int quad = warp & 3;
     const int col0 = 64 * (e >> 2);
     const uint32_t lanes = (uint32_t)(quad * 32) << 16;
-    float sh[64], sl[64];
+    float sh[64];
 #pragma unroll
-    for (int q = 0; q < 64; ++q) {
-      sh[q] = 0.f;
-      sl[q] = 0.f;
-    }
+    for (int q = 0; q < 64; ++q) sh[q] = 0.f;
+    const uint32_t lo_t = tbase + lanes + (uint32_t)(kSumLo + col0);
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
       const int b = c & 1;
       ok = __all_sync(0xffffffffu, ok && mbar_wait(&acc_full[b], (c >> 1) & 1, status));
       __syncwarp();
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      uint32_t v[32];
       const uint32_t acc = tbase + lanes + (uint32_t)(b * kTM + col0);
       if (ok) {
-        tmem_ld_32x32b_x32(acc, v);
 #pragma unroll
-        for (int q = 0; q < 32; q += 2)
-          two_sum_acc2(sh[q], sh[q + 1], sl[q], sl[q + 1], __uint_as_float(v[q]),
-                       __uint_as_float(v[q + 1]));
-        tmem_ld_32x32b_x32(acc + 32, v);
+        for (int h = 0; h < 2; ++h) {
+          uint32_t v[32], l[32];
+          tmem_ld_32x32b_x32(acc + 32 * h, v);
+          if (c == 0) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) l[q] = 0u;
+          } else {
+            tmem_ld_32x32b_x32(lo_t + 32 * h, l);
+          }
+#pragma unroll
+          for (int q = 0; q < 32; q += 2) {
+            float l0 = __uint_as_float(l[q]), l1 = __uint_as_float(l[q + 1]);
+            two_sum_acc2(sh[32 * h + q], sh[32 * h + q + 1], l0, l1, __uint_as_float(v[q]),
+                         __uint_as_float(v[q + 1]));
+            l[q] = __float_as_uint(l0);
+            l[q + 1] = __float_as_uint(l1);
+          }
+          tmem_st_32x32b_x32(lo_t + 32 * h, l);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       }
-      // the buffer is free once both loads have completed
+      // the accumulator is free once its loads have completed
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&acc_empty[b]);
       if (!ok) break;
+    }
+    float sl[64];
+    if (ok) {
 #pragma unroll
-      for (int q = 0; q < 32; q += 2)
-        two_sum_acc2(sh[32 + q], sh[33 + q], sl[32 + q], sl[33 + q], __uint_as_float(v[q]),
-                     __uint_as_float(v[q + 1]));
+      for (int h = 0; h < 2; ++h) {
+        uint32_t l[32];
+        tmem_ld_32x32b_x32(lo_t + 32 * h, l);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) sl[32 * h + q] = __uint_as_float(l[q]);
+      }
     }
     if (ok) {
-      // S[j][i] straight from the registers (the lanes hold consecutive i:
-      // one coalesced row segment per column); S[i][j] through a shared-
-      // memory transpose, one row segment per store.  The operand ring is
-      // idle here: every load was consumed and the last MMA has completed.
+      // (hi + lo) * scale -- one rounding of hi * scale plus the (tiny)
+      // lo * scale: within an FP32 ulp of the exact product -- staged in
+      // shared memory (the operand ring is idle here: every load was consumed
+      // and the last MMA has completed), then written as S[j][i] (lanes over
+      // i) and S[i][j] (lanes over j): one coalesced row segment per store
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       float* T = reinterpret_cast<float*>(ring) + e * (32 * 65);
-      const int i0 = bi * kTM + quad * 32;
-      const int i = i0 + lane;
 #pragma unroll
-      for (int q = 0; q < 64; ++q) {
-        // (hi + lo) * scale in one rounding of hi * scale plus the
-        // (tiny) lo * scale: within an FP32 ulp of the exact product
-        const float val = fmaf(sh[q], scale, sl[q] * scale);
-        const int j = bj * kTM + col0 + q;
-        if (i < p && j < p && i <= j) S[(size_t)j * lds + i] = val;
-        T[lane * 65 + q] = val;
-      }
+      for (int q = 0; q < 64; ++q) T[lane * 65 + q] = fmaf(sh[q], scale, sl[q] * scale);
       __syncwarp();
+      const int i0 = bi * kTM + quad * 32;
+      const int j0 = bj * kTM + col0;
+      const int i = i0 + lane;
+      if (i < p)
+        for (int q = 0; q < 64; ++q) {
+          const int j = j0 + q;
+          if (j < p && i <= j) S[(size_t)j * lds + i] = T[lane * 65 + q];
+        }
       for (int r = 0; r < 32 && i0 + r < p; ++r) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int j = bj * kTM + col0 + 32 * h + lane;
+          const int j = j0 + 32 * h + lane;
           if (j < p && i0 + r <= j) S[(size_t)(i0 + r) * lds + j] = T[r * 65 + 32 * h + lane];
         }
       }
